@@ -1,0 +1,133 @@
+/*
+ * dmrgscf.h -- C-ABI of the GB300 spin-adapted DMRG / CAS-SCF hot path.
+ *
+ * Method: arXiv:2503.20700, "Orbital optimization of large active spaces via
+ * AI-accelerators".  The library implements the DMRG-CI side of the paper's
+ * DMRG-SCF: the spin-adapted (SU(2) x U(1)) two-site DMRG sweep of Sec. II.B-D
+ * (Davidson with the effective-Hamiltonian product H_eff psi, decimation to
+ * D SU(2) multiplets, operator renormalisation), the one- and two-particle
+ * RDMs of Eqs. onerdm/twordm/rdm1_su2, and the integral transformation and
+ * orbital gradient of the CAS-SCF step of Sec. II.A.
+ *
+ * Conventions shared by all entry points
+ *  - All array arguments are HOST pointers to row-major float64 data unless
+ *    stated otherwise; the library copies inputs and writes caller-allocated
+ *    outputs.  The caller keeps ownership of every pointer.
+ *  - Integrals are in chemists' notation: eri[((p*n+q)*n+r)*n+s] = (pq|rs),
+ *    the Hamiltonian of Sec. II.A being
+ *        H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps).
+ *  - Spin quantum numbers are passed doubled (two_s = 2S).
+ *  - Every call returns a dmrg_status; the library never aborts or exits.
+ *    On error the message is available from dmrg_last_error().
+ *  - All floating-point work runs on the CUDA device (sm_103a).  There is no
+ *    host fallback: without a usable GPU the calls return DMRG_ECUDA.
+ */
+#ifndef DMRGSCF_H
+#define DMRGSCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_ctx dmrg_ctx;
+
+typedef enum {
+  DMRG_OK = 0,
+  DMRG_EINVAL = -1,    /* bad argument (sizes, parity, NULL pointer)        */
+  DMRG_ENOMEM = -2,    /* device allocation failed                           */
+  DMRG_ECUDA = -3,     /* CUDA error or no usable device                     */
+  DMRG_ENOCONV = -4,   /* Davidson did not reach the tolerance               */
+  DMRG_ETIMEOUT = -5,  /* a bounded device wait ran out                      */
+  DMRG_ESTATE = -6,    /* call out of order (e.g. RDMs before any sweep)     */
+  DMRG_EINTERNAL = -7  /* internal inconsistency (reported, never aborted)   */
+} dmrg_status;
+
+typedef enum {
+  DMRG_FP64 = 0,        /* all GEMMs in float64                              */
+  DMRG_SPLIT_TF32 = 1,  /* H_eff psi / renormalisation GEMMs as 3xTF32 with
+                           FP32 accumulation; Davidson, eigensolver and the
+                           final reductions stay float64                      */
+  DMRG_BF16X9 = 2       /* reserved: BF16x9 split products                    */
+} dmrg_precision;
+
+typedef struct {
+  int D;                  /* bond dimension in SU(2) multiplets (Sec. II.C)  */
+  int max_davidson_iter;  /* per bond                                        */
+  double davidson_tol;    /* ||H_eff psi - E psi|| with ||psi|| = 1 (Sec. II.D) */
+  int precision;          /* dmrg_precision                                  */
+  int max_space;          /* Davidson subspace size before restart           */
+  int verbose;            /* 0 quiet, 1 per bond, 2 per Davidson step        */
+  int device;             /* CUDA device ordinal                             */
+} dmrg_opts;
+
+/* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24. */
+void dmrg_default_opts(dmrg_opts* o);
+
+/*
+ * dmrg_init -- set up the DMRG-CI problem of one active space.
+ *   n         number of active orbitals (sites), n >= 2
+ *   h         n*n one-electron integrals (symmetric)
+ *   eri       n^4 two-electron integrals (pq|rs), or NULL if chol is given
+ *   chol      rank*n*n Cholesky vectors L^k_pq with (pq|rs) = sum_k L^k_pq L^k_rs,
+ *             or NULL if eri is given
+ *   e_core    constant energy added to every reported energy
+ *   n_elec    number of active electrons N (0..2n)
+ *   two_s     2S of the target multiplet (parity of n_elec)
+ *   opts      options, or NULL for the defaults
+ *   occ       optional n site occupations (0/1/2) of the initial product state
+ *   two_s_right optional n+1 doubled spins of the right blocks of that state
+ *             (sites i..n-1, coupled from the right); both NULL for the
+ *             default state (electrons spread evenly, minimal spins)
+ * The initial right blocks are built on the device before returning.
+ * Returns DMRG_EINVAL for inconsistent sizes/parities, DMRG_ECUDA without a
+ * device, DMRG_ENOMEM if the device memory is exhausted.
+ */
+dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const double* chol,
+                      int rank, double e_core, int n, int n_elec, int two_s, const dmrg_opts* opts,
+                      const int* occ, const int* two_s_right);
+
+/*
+ * dmrg_sweep -- run n_sweeps full sweeps (L->R over bonds 0..n-3, then R->L
+ * over bonds n-2..1; Sec. II.B two-site DMRG).  *energy receives the Davidson
+ * eigenvalue of the last bond plus e_core, *max_trunc_err the largest
+ * discarded weight of the last sweep.  Either output may be NULL.
+ */
+dmrg_status dmrg_sweep(dmrg_ctx* ctx, int n_sweeps, double* energy, double* max_trunc_err);
+
+/* Change the bond dimension used by subsequent sweeps. */
+dmrg_status dmrg_set_bond_dim(dmrg_ctx* ctx, int D);
+
+/* Change the GEMM precision used by subsequent sweeps (dmrg_precision). */
+dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int precision);
+
+/* Energy of the last sweep (incl. e_core).  DMRG_ESTATE before any sweep. */
+dmrg_status dmrg_energy(const dmrg_ctx* ctx, double* energy);
+
+/*
+ * Statistics of the last sweep: total H_eff psi FLOPs (algorithmic, 2mnk per
+ * product), time spent in H_eff psi (s), number of H_eff psi calls, total
+ * Davidson iterations and the sweep wall time (s).  NULL outputs are skipped.
+ */
+dmrg_status dmrg_last_sweep_stats(const dmrg_ctx* ctx, double* hpsi_flops, double* hpsi_seconds,
+                                  int* hpsi_calls, int* davidson_iters, double* sweep_seconds);
+
+/* Bond energies (incl. e_core) of every optimised bond so far, in order.
+ * *count receives the number available; at most cap values are written. */
+dmrg_status dmrg_bond_energies(const dmrg_ctx* ctx, double* out, int cap, int* count);
+
+/* Multiplet counts of the left blocks L(m), m = 0..n (-1 where not held). */
+dmrg_status dmrg_block_dims(const dmrg_ctx* ctx, int* left, int* right);
+
+/* Release every resource of the context (NULL is accepted). */
+void dmrg_free(dmrg_ctx* ctx);
+
+/* Message of the last error of ctx, or of the calling thread if ctx is NULL. */
+const char* dmrg_last_error(const dmrg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRGSCF_H */

@@ -1,0 +1,180 @@
+"""GB300 spin-adapted DMRG / CAS-SCF hot path: Python binding of the C-ABI.
+
+The binding only marshals arguments to ``include/dmrgscf.h`` (loaded with
+ctypes from the in-tree shared library ``libdmrgscf.so`` built by
+``build.py``).  Every step of the path runs in the library's CUDA kernels;
+when the library cannot be loaded the calls raise instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_NAME = "libdmrgscf.so"
+
+DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA = 0, -1, -2, -3
+DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE, DMRG_EINTERNAL = -4, -5, -6, -7
+FP64, SPLIT_TF32 = 0, 1
+
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
+           -5: "ETIMEOUT", -6: "ESTATE", -7: "EINTERNAL"}
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("max_davidson_iter", ctypes.c_int),
+                ("davidson_tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("max_space", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+_lib = None
+_lib_path = None
+
+
+def lib_path():
+    return os.environ.get("DMRGSCF_LIB", os.path.join(HERE, LIB_NAME))
+
+
+def load(path=None):
+    """Load the shared library (raises if it is missing)."""
+    global _lib, _lib_path
+    path = path or lib_path()
+    if _lib is not None and _lib_path == path:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.dmrg_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.dmrg_init.argtypes = [ctypes.POINTER(P), dp, dp, dp, I, D, I, I, I,
+                              ctypes.POINTER(Opts), ip, ip]
+    lib.dmrg_init.restype = I
+    lib.dmrg_sweep.argtypes = [P, I, dp, dp]
+    lib.dmrg_sweep.restype = I
+    lib.dmrg_set_bond_dim.argtypes = [P, I]
+    lib.dmrg_set_bond_dim.restype = I
+    lib.dmrg_set_precision.argtypes = [P, I]
+    lib.dmrg_set_precision.restype = I
+    lib.dmrg_energy.argtypes = [P, dp]
+    lib.dmrg_energy.restype = I
+    lib.dmrg_last_sweep_stats.argtypes = [P, dp, dp, ip, ip, dp]
+    lib.dmrg_last_sweep_stats.restype = I
+    lib.dmrg_bond_energies.argtypes = [P, dp, I, ip]
+    lib.dmrg_bond_energies.restype = I
+    lib.dmrg_block_dims.argtypes = [P, ip, ip]
+    lib.dmrg_block_dims.restype = I
+    lib.dmrg_free.argtypes = [P]
+    lib.dmrg_free.restype = None
+    lib.dmrg_last_error.argtypes = [P]
+    lib.dmrg_last_error.restype = ctypes.c_char_p
+    _lib, _lib_path = lib, path
+    from . import ops as _ops  # noqa: F401  (registers kernel-level entry points)
+    _ops.bind(lib)
+    return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _check(lib, ctx, st):
+    if st != DMRG_OK:
+        msg = lib.dmrg_last_error(ctx).decode() if lib else ""
+        raise DmrgError(st, msg)
+
+
+class DMRG:
+    """Spin-adapted two-site DMRG context (dmrg_init ... dmrg_free)."""
+
+    def __init__(self, h, eri=None, chol=None, n_elec=None, two_s=0, D=64, e_core=0.0,
+                 tol=1e-10, precision=FP64, max_iter=200, max_space=24, verbose=0,
+                 device=0, occ=None, two_s_right=None):
+        lib = load()
+        self._lib = lib
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        n = h.shape[0]
+        if n_elec is None:
+            n_elec = n
+        eri_a = None if eri is None else np.ascontiguousarray(eri, dtype=np.float64)
+        chol_a = None if chol is None else np.ascontiguousarray(chol, dtype=np.float64)
+        rank = 0 if chol_a is None else chol_a.shape[0]
+        o = Opts()
+        lib.dmrg_default_opts(ctypes.byref(o))
+        o.D, o.davidson_tol, o.precision = D, tol, precision
+        o.max_davidson_iter, o.max_space, o.verbose, o.device = max_iter, max_space, verbose, device
+        occ_a = None if occ is None else np.ascontiguousarray(occ, dtype=np.int32)
+        path_a = None if two_s_right is None else np.ascontiguousarray(two_s_right, dtype=np.int32)
+        ctx = ctypes.c_void_p()
+        st = lib.dmrg_init(ctypes.byref(ctx), _dp(h), _dp(eri_a), _dp(chol_a), rank,
+                           float(e_core), n, int(n_elec), int(two_s), ctypes.byref(o),
+                           _ip(occ_a), _ip(path_a))
+        _check(lib, None, st)
+        self._ctx = ctx
+        self.n = n
+
+    def sweep(self, n_sweeps=1):
+        e = ctypes.c_double()
+        t = ctypes.c_double()
+        _check(self._lib, self._ctx, self._lib.dmrg_sweep(self._ctx, n_sweeps, ctypes.byref(e),
+                                                         ctypes.byref(t)))
+        return e.value, t.value
+
+    def set_bond_dim(self, D):
+        _check(self._lib, self._ctx, self._lib.dmrg_set_bond_dim(self._ctx, D))
+
+    def set_precision(self, p):
+        _check(self._lib, self._ctx, self._lib.dmrg_set_precision(self._ctx, p))
+
+    def energy(self):
+        e = ctypes.c_double()
+        _check(self._lib, self._ctx, self._lib.dmrg_energy(self._ctx, ctypes.byref(e)))
+        return e.value
+
+    def stats(self):
+        f, s, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        c, it = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_stats(
+            self._ctx, ctypes.byref(f), ctypes.byref(s), ctypes.byref(c), ctypes.byref(it),
+            ctypes.byref(sw)))
+        return {"hpsi_flops": f.value, "hpsi_seconds": s.value, "hpsi_calls": c.value,
+                "davidson_iters": it.value, "sweep_seconds": sw.value}
+
+    def bond_energies(self):
+        cnt = ctypes.c_int()
+        self._lib.dmrg_bond_energies(self._ctx, None, 0, ctypes.byref(cnt))
+        out = np.zeros(cnt.value)
+        _check(self._lib, self._ctx, self._lib.dmrg_bond_energies(self._ctx, _dp(out), cnt.value,
+                                                                 ctypes.byref(cnt)))
+        return out
+
+    def block_dims(self):
+        left = np.zeros(self.n + 1, dtype=np.int32)
+        right = np.zeros(self.n + 1, dtype=np.int32)
+        _check(self._lib, self._ctx, self._lib.dmrg_block_dims(self._ctx, _ip(left), _ip(right)))
+        return left, right
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.dmrg_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

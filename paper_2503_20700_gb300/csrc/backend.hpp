@@ -1,0 +1,91 @@
+// Device primitives used by the host planner.
+//
+// Every floating-point step of the DMRG sweep runs through this interface,
+// and the only implementation in the library is the CUDA one (backend_cuda.cu);
+// there is no host fallback.  All pointers in task lists are device pointers.
+//
+// The two workhorses are "segment-sum" primitives with owner-computes
+// accumulation (one output block is reduced by one CTA in a fixed order, so
+// results are deterministic and need no atomics):
+//   place:  C += sum_s alpha_s * op_s(S_s)                  (elementwise)
+//   gemm :  C += sum_s alpha_s * op_s(A_s) * op_s(B_s)      (matrix products)
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dmrg {
+
+enum class Precision : int { FP64 = 0, SPLIT_TF32 = 1, BF16X9 = 2 };
+
+struct PlaceSeg {
+  const double* src;
+  int ld;          // leading dimension of src (row-major)
+  int trans;       // 0: src[r*ld + c], 1: src[c*ld + r]
+  double alpha;
+};
+struct PlaceGroup {
+  double* dst;
+  int rows, cols, ld;
+  int seg_begin, seg_count;  // into the segment array
+};
+
+struct GemmSeg {
+  const double* A;
+  const double* B;
+  int k;
+  int lda, ldb;
+  int transA, transB;  // A: 0 -> m x k row-major, 1 -> stored k x m; B: 0 -> k x n, 1 -> stored n x k
+  double alpha;
+};
+struct GemmGroup {
+  double* C;
+  int m, n, ldc;
+  int seg_begin, seg_count;
+};
+
+struct EighTask {
+  const double* A;  // n x n symmetric, row-major (read only)
+  double* w;        // n eigenvalues, ascending
+  double* V;        // n x n eigenvectors as columns (row-major storage)
+  int n;
+};
+
+class Backend {
+ public:
+  virtual ~Backend() = default;
+  virtual std::string name() const = 0;
+  virtual void* alloc(size_t bytes) = 0;
+  virtual void free(void* p) = 0;
+  virtual size_t bytes_in_use() const = 0;
+  virtual void memset0(void* p, size_t bytes) = 0;
+  virtual void copy_d2d(void* dst, const void* src, size_t bytes) = 0;
+  virtual void copy_h2d(void* dst, const void* src, size_t bytes) = 0;
+  virtual void copy_d2h(void* dst, const void* src, size_t bytes) = 0;
+  virtual void sync() = 0;
+
+  virtual void place(const std::vector<PlaceGroup>& groups, const std::vector<PlaceSeg>& segs) = 0;
+  virtual void gemm(const std::vector<GemmGroup>& groups, const std::vector<GemmSeg>& segs,
+                    Precision prec) = 0;
+
+  // Davidson vector algebra on contiguous float64 vectors of length len.
+  // out[i] = sum_t V[i*ld + t] * x[t] for i < m   (out is a device array)
+  virtual void dots(const double* V, int m, size_t len, size_t ld, const double* x, double* out) = 0;
+  // y = beta * y + sum_i c[i] * V[i*ld + :]   (c is a device array of m)
+  virtual void combine(double* y, double beta, const double* V, int m, size_t len, size_t ld,
+                       const double* c) = 0;
+  virtual void axpby(double* y, double a, const double* x, double b, size_t len) = 0;
+  // y[t] = x[t] / (d[t] - e) with a guarded denominator (Davidson preconditioner)
+  virtual void precondition(double* y, const double* x, const double* d, double e, size_t len) = 0;
+  // Symmetric eigendecompositions (FP64, one CTA per matrix).
+  virtual void eigh(const std::vector<EighTask>& tasks) = 0;
+
+  // Counters (for the FLOP/byte accounting of the benchmark).
+  double gemm_flops = 0.0;   // algorithmic 2*m*n*k summed over segments
+  double place_bytes = 0.0;
+};
+
+Backend* make_cuda_backend(int device, std::string* err);
+
+}  // namespace dmrg

@@ -1,0 +1,1496 @@
+// Host planner of the spin-adapted two-site DMRG (see dmrg.hpp).
+#include "dmrg.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+namespace dmrg {
+
+namespace {
+thread_local std::string g_last_error;
+const double kSqrt2 = std::sqrt(2.0);
+const double kSqrt3 = std::sqrt(3.0);
+// Spinor recoupling constants in the Clebsch-Gordan convention of su2.hpp
+// (verified against explicit fermion matrices; see the test suite):
+//   sum_{st} a+_ps a+_qt a_rt a_ss = sum_k alpha_k [[a+_p a+_q]^k [a~_r a~_s]^k]^0
+//   sum_{st} a+_ps a_rt a+_qt a_ss = sum_k beta_k  [[a+_p a~_r]^k [a+_q a~_s]^k]^0
+const double kAlpha[2] = {-1.0, std::sqrt(3.0)};
+const double kBeta[2] = {1.0, -std::sqrt(3.0)};
+// Mixed terms of the three-index complementary operator S~_p when a block
+// grows by one site s (L: block left of s; R: block right of s):
+//   M2: sum_t a+_qt a_st a_t'sigma      ->  c2  [[a+_q a~_t']^k (x) a~_s]
+//   M3: sum_t a+_st a_rt a_t'sigma      ->  c3  [[a~_r a~_t']^k (x) a+_s]
+//   M5: sum_t a+_st a_rt a_s sigma      ->  c5  [a~_r (x) [a+_s a~_s]^k]
+const double kC2L[2] = {1.0 / std::sqrt(2.0), std::sqrt(1.5)};
+const double kC2R[2] = {1.0 / std::sqrt(2.0), -std::sqrt(1.5)};
+const double kC5L[2] = {1.0 / std::sqrt(2.0), -std::sqrt(1.5)};
+const double kC5R[2] = {1.0 / std::sqrt(2.0), std::sqrt(1.5)};
+const double kC6 = 1.0 / std::sqrt(2.0);
+// [a+_s a~_r]^k = kSwapB[k] [a~_r (x) a+_s]^k for two distinct sites (either order)
+const double kSwapB[2] = {1.0, -1.0};
+// adj([a+_a a~_b]^k) = kAdjB[k] [a+_b a~_a]^k ;  adj([a+_a a+_b]^k) = -[a~_a a~_b]^k
+const double kAdjB[2] = {1.0, -1.0};
+}  // namespace
+
+std::string last_error() { return g_last_error; }
+void set_last_error(const std::string& e) { g_last_error = e; }
+
+// ============================================================ op sets
+OpSet::~OpSet() {
+  if (be)
+    for (void* p : mem) be->free(p);
+}
+
+static Layout make_layout(const Basis& bra, const Basis& ket, int dn, int k2) {
+  Layout L;
+  L.dn = dn;
+  L.k2 = k2;
+  L.nket = (int)ket.sec.size();
+  L.lut.assign(bra.sec.size() * ket.sec.size(), -1);
+  size_t off = 0;
+  for (size_t kb = 0; kb < ket.sec.size(); ++kb)
+    for (size_t bb = 0; bb < bra.sec.size(); ++bb) {
+      const Sector& K = ket.sec[kb];
+      const Sector& B = bra.sec[bb];
+      if (B.n != K.n + dn || !triangle(K.j, k2, B.j)) continue;
+      L.lut[bb * ket.sec.size() + kb] = (int)L.blk.size();
+      L.blk.push_back({(int)bb, (int)kb, B.dim, K.dim, off});
+      off += (size_t)B.dim * K.dim;
+    }
+  L.size = off;
+  return L;
+}
+
+const Layout& OpSet::layout(int dn, int k2) {
+  auto key = std::make_pair(dn, k2);
+  auto it = layouts.find(key);
+  if (it != layouts.end()) return it->second;
+  return layouts.emplace(key, make_layout(basis, basis, dn, k2)).first->second;
+}
+
+void OpSet::allocate(const std::vector<OpKey>& keys) {
+  std::map<std::pair<int, int>, std::vector<OpKey>> by;
+  for (auto& k : keys) by[{kind_dn(k.kind), k.k2}].push_back(k);
+  for (auto& [lk, ks] : by) {
+    const Layout& L = layout(lk.first, lk.second);
+    if (L.size == 0) continue;
+    size_t bytes = L.size * ks.size() * sizeof(double);
+    double* p = (double*)be->alloc(bytes);
+    be->memset0(p, bytes);
+    mem.push_back(p);
+    for (size_t i = 0; i < ks.size(); ++i) ops[ks[i]] = p + i * L.size;
+  }
+}
+
+size_t OpSet::bytes() const {
+  size_t b = 0;
+  for (auto& [k, p] : ops) {
+    auto it = layouts.find({kind_dn(k.kind), k.k2});
+    if (it != layouts.end()) b += it->second.size * sizeof(double);
+  }
+  return b;
+}
+
+// ============================================================ operands
+struct Operand {
+  enum T { ID, BLK, SITE } t = ID;
+  OpKey key{0, 0, 0, 0};
+  int adj = 0;
+  SiteOp s;
+  int k2 = 0, dn = 0, par = 0;
+};
+
+Operand op_id() { return Operand(); }
+Operand op_blk(int kind, int i, int j, int k2, int adj = 0) {
+  Operand o;
+  o.t = Operand::BLK;
+  o.key = {kind, i, j, k2};
+  o.adj = adj;
+  o.k2 = k2;
+  o.dn = adj ? -kind_dn(kind) : kind_dn(kind);
+  o.par = kind_parity(kind);
+  return o;
+}
+Operand op_site(const SiteOp& s) {
+  Operand o;
+  o.t = Operand::SITE;
+  o.s = s;
+  o.k2 = s.k2;
+  o.dn = s.dn;
+  o.par = s.parity;
+  return o;
+}
+// adjoint of an operand
+Operand op_adj(const Operand& x) {
+  Operand o = x;
+  if (x.t == Operand::BLK) {
+    o.adj = !x.adj;
+    o.dn = -x.dn;
+  } else if (x.t == Operand::SITE) {
+    SiteOp s;
+    s.k2 = x.s.k2;
+    s.dn = -x.s.dn;
+    s.parity = x.s.parity;
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a)
+        s.m[b][a] = adjoint_coef(kSiteJ[b], kSiteJ[a], x.s.k2) * x.s.m[a][b];
+    o.s = s;
+    o.dn = s.dn;
+  }
+  return o;
+}
+SiteOp site_add(const SiteOp& a, const SiteOp& b, double cb) {
+  SiteOp o = a;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o.m[i][j] += cb * b.m[i][j];
+  return o;
+}
+
+struct Term {
+  Operand x, y;  // x acts on the left part, y on the right part
+  int k2;        // coupled rank of [x (x) y]
+  double coef;
+};
+
+// A member of a bipartition: a single site or a block.
+struct Side {
+  bool is_site = false;
+  int site = -1;
+  const Block* blk = nullptr;
+  std::vector<int> sites;
+  bool normal = true;
+  bool has(int p) const { return std::find(sites.begin(), sites.end(), p) != sites.end(); }
+};
+
+// Operands of a side; integral-dependent site operators are built here.
+struct SideOps {
+  const Engine* e;
+  const SiteAlgebra& sa = site_algebra();
+  const Side& s;
+  double (*gfun)(const Engine*, int, int, int, int);
+  double (*hfun)(const Engine*, int, int);
+  SideOps(const Engine* e_, const Side& s_, double (*g_)(const Engine*, int, int, int, int),
+          double (*h_)(const Engine*, int, int))
+      : e(e_), s(s_), gfun(g_), hfun(h_) {}
+  double g(int p, int q, int r, int t) const { return gfun(e, p, q, r, t); }
+  Operand C(int p) const { return s.is_site ? op_site(sa.C) : op_blk(K_C, p, 0, 1); }
+  Operand S(int p) const {  // S~_p, p outside the side
+    if (!s.is_site) return op_blk(K_S, p, 0, 1);
+    int t = s.site;
+    SiteOp o = sa.D.scaled(0.5 * hfun(e, p, t));
+    o = site_add(o, sa.NnD, g(p, t, t, t));
+    return op_site(o);
+  }
+  // normal pair operators (p <= q inside the side)
+  Operand A(int p, int q, int k) const {
+    if (s.is_site) return k == 0 ? op_site(sa.CC0) : op_site(SiteOp());
+    return op_blk(K_A, p, q, 2 * k);
+  }
+  Operand B(int p, int q, int k) const {
+    if (s.is_site) return op_site(sa.CD[k]);
+    return op_blk(K_B, p, q, 2 * k);
+  }
+  // complementary pair operators (p <= q outside the side)
+  Operand P(int p, int q, int k) const {
+    if (s.is_site) {
+      int t = s.site;
+      if (k == 1) return op_site(SiteOp());
+      return op_site(sa.DD0.scaled(g(p, q, t, t)));
+    }
+    return op_blk(K_P, p, q, 2 * k);
+  }
+  Operand QJ(int p, int q) const {
+    if (s.is_site) {
+      int t = s.site;
+      return op_site(sa.CD[0].scaled(g(p, t, t, q)));
+    }
+    return op_blk(K_QJ, p, q, 0);
+  }
+  Operand QK(int p, int q, int k) const {
+    if (s.is_site) {
+      int t = s.site;
+      return op_site(sa.CD[k].scaled(g(p, t, q, t)));
+    }
+    return op_blk(K_QK, p, q, 2 * k);
+  }
+};
+
+static double g_acc(const Engine* e, int p, int q, int r, int s);
+static double h_acc(const Engine* e, int p, int q);
+
+namespace {
+bool operand_zero(const Operand& o) {
+  return o.t == Operand::SITE && o.s.zero();
+}
+void push(std::vector<Term>& out, const Operand& x, const Operand& y, int k2, double c) {
+  if (c == 0.0 || operand_zero(x) || operand_zero(y)) return;
+  out.push_back({x, y, k2, c});
+}
+// h.c. of a scalar term: ([x (x) y]^0)^+ = (-1)^(px py) [x~ (x) y~]^0
+void push_hc(std::vector<Term>& out, const Operand& x, const Operand& y, double c) {
+  push(out, x, y, 0, c);
+  double eps = (x.par && y.par) ? -1.0 : 1.0;
+  push(out, op_adj(x), op_adj(y), 0, eps * c);
+}
+}  // namespace
+
+// Interaction terms between a left part X and a right part Y (X left of Y in
+// the Jordan-Wigner order), as scalar couplings [x (x) y]^0.
+static void emit_cross(const Engine* e, const Side& X, const Side& Y, std::vector<Term>& out) {
+  SideOps ox(e, X, g_acc, h_acc), oy(e, Y, g_acc, h_acc);
+  // one-index / three-index terms
+  for (int p : X.sites) push_hc(out, ox.C(p), oy.S(p), -kSqrt2);
+  for (int p : Y.sites) push_hc(out, ox.S(p), oy.C(p), -kSqrt2);
+  // pair terms: normal operators on side N, complementary on the other
+  bool x_normal;
+  if (!X.is_site && !Y.is_site) {
+    if (X.normal == Y.normal) throw std::runtime_error("both sides have the same pair type");
+    x_normal = X.normal;
+  } else if (X.is_site && Y.is_site) {
+    x_normal = true;
+  } else if (X.is_site) {
+    x_normal = !Y.normal;  // site normal iff the block is complementary
+  } else {
+    x_normal = X.normal;
+  }
+  const SideOps& on = x_normal ? ox : oy;
+  const SideOps& oc = x_normal ? oy : ox;
+  const Side& N = x_normal ? X : Y;
+  for (size_t a = 0; a < N.sites.size(); ++a)
+    for (size_t b = a; b < N.sites.size(); ++b) {
+      int p = N.sites[a], q = N.sites[b];
+      double w = (p == q) ? 1.0 : 2.0;
+      for (int k = 0; k < 2; ++k) {
+        if (p == q && k == 1) continue;
+        Operand nA = on.A(p, q, k), cP = oc.P(p, q, k);
+        double c = w * 0.5 * kAlpha[k];
+        if (x_normal) push_hc(out, nA, cP, c);
+        else push_hc(out, cP, nA, c);
+      }
+      // B-type (Coulomb + exchange)
+      for (int k = 0; k < 2; ++k) {
+        Operand nB = on.B(p, q, k);
+        std::vector<std::pair<Operand, double>> comp;
+        if (k == 0) comp.push_back({oc.QJ(p, q), 2.0});
+        comp.push_back({oc.QK(p, q, k), -kBeta[k]});
+        for (auto& [cq, c] : comp) {
+          if (p == q) {
+            if (x_normal) push(out, nB, cq, 0, c);
+            else push(out, cq, nB, 0, c);
+          } else {
+            if (x_normal) push_hc(out, nB, cq, c);
+            else push_hc(out, cq, nB, c);
+          }
+        }
+      }
+    }
+}
+
+// ============================================================ engine basics
+struct EngineAccess {
+  static double g(const Engine* e, int p, int q, int r, int s) { return e->g(p, q, r, s); }
+  static double h(const Engine* e, int p, int q) { return e->hh(p, q); }
+};
+static double g_acc(const Engine* e, int p, int q, int r, int s) {
+  return EngineAccess::g(e, p, q, r, s);
+}
+static double h_acc(const Engine* e, int p, int q) { return EngineAccess::h(e, p, q); }
+
+namespace {
+std::vector<int> block_sites(const Block& b, int n) {
+  std::vector<int> s;
+  if (b.left)
+    for (int p = 0; p < b.nsites; ++p) s.push_back(p);
+  else
+    for (int p = n - b.nsites; p < n; ++p) s.push_back(p);
+  return s;
+}
+bool in_sites(const std::vector<int>& v, int p) { return std::find(v.begin(), v.end(), p) != v.end(); }
+
+// Keys of all operators a block with the given sites carries.
+std::vector<OpKey> op_keys(const std::vector<int>& sites, int n, bool normal) {
+  std::vector<OpKey> k;
+  k.push_back({K_H, 0, 0, 0});
+  std::vector<int> out;
+  for (int p = 0; p < n; ++p)
+    if (!in_sites(sites, p)) out.push_back(p);
+  for (int p : sites) k.push_back({K_C, p, 0, 1});
+  for (int p : out) k.push_back({K_S, p, 0, 1});
+  const std::vector<int>& ps = normal ? sites : out;
+  for (size_t a = 0; a < ps.size(); ++a)
+    for (size_t b = a; b < ps.size(); ++b) {
+      int p = ps[a], q = ps[b];
+      if (normal) {
+        k.push_back({K_A, p, q, 0});
+        if (p != q) k.push_back({K_A, p, q, 2});
+        k.push_back({K_B, p, q, 0});
+        k.push_back({K_B, p, q, 2});
+      } else {
+        k.push_back({K_P, p, q, 0});
+        if (p != q) k.push_back({K_P, p, q, 2});
+        k.push_back({K_QJ, p, q, 0});
+        k.push_back({K_QK, p, q, 0});
+        k.push_back({K_QK, p, q, 2});
+      }
+    }
+  return k;
+}
+
+// Collects place segments grouped by destination sub-block.
+struct PlaceBuilder {
+  std::map<std::tuple<double*, int, int, int>, std::vector<PlaceSeg>> groups;
+  void add(double* dst, int rows, int cols, int ld, const PlaceSeg& s) {
+    if (s.alpha == 0.0 || rows == 0 || cols == 0) return;
+    groups[{dst, rows, cols, ld}].push_back(s);
+  }
+  void run(Backend* be) {
+    std::vector<PlaceGroup> g;
+    std::vector<PlaceSeg> segs;
+    for (auto& [k, v] : groups) {
+      PlaceGroup pg;
+      pg.dst = std::get<0>(k);
+      pg.rows = std::get<1>(k);
+      pg.cols = std::get<2>(k);
+      pg.ld = std::get<3>(k);
+      pg.seg_begin = (int)segs.size();
+      pg.seg_count = (int)v.size();
+      segs.insert(segs.end(), v.begin(), v.end());
+      g.push_back(pg);
+    }
+    if (!g.empty()) be->place(g, segs);
+    groups.clear();
+  }
+};
+
+struct GemmBuilder {
+  std::map<double*, std::pair<std::array<int, 3>, std::vector<GemmSeg>>> groups;
+  void add(double* C, int m, int n, int ldc, const GemmSeg& s) {
+    if (s.alpha == 0.0 || m == 0 || n == 0 || s.k == 0) return;
+    auto& g = groups[C];
+    g.first = {m, n, ldc};
+    g.second.push_back(s);
+  }
+  void run(Backend* be, Precision prec) {
+    std::vector<GemmGroup> gs;
+    std::vector<GemmSeg> segs;
+    for (auto& [C, v] : groups) {
+      GemmGroup gg;
+      gg.C = C;
+      gg.m = v.first[0];
+      gg.n = v.first[1];
+      gg.ldc = v.first[2];
+      gg.seg_begin = (int)segs.size();
+      gg.seg_count = (int)v.second.size();
+      segs.insert(segs.end(), v.second.begin(), v.second.end());
+      gs.push_back(gg);
+    }
+    if (!gs.empty()) be->gemm(gs, segs, prec);
+    groups.clear();
+  }
+};
+}  // namespace
+
+Engine::~Engine() = default;
+
+int Engine::left_dim(int m) const {
+  if (m < 0 || m >= (int)L_.size() || !L_[m]) return -1;
+  int t = 0;
+  for (auto& s : L_[m]->ops->basis.sec) t += s.dim;
+  return t;
+}
+int Engine::right_dim(int m) const {
+  if (m < 0 || m >= (int)R_.size() || !R_[m]) return -1;
+  int t = 0;
+  for (auto& s : R_[m]->ops->basis.sec) t += s.dim;
+  return t;
+}
+
+std::unique_ptr<Block> Engine::vacuum(bool left) {
+  auto b = std::make_unique<Block>();
+  b->left = left;
+  b->nsites = 0;
+  b->normal = true;
+  b->ops = std::make_unique<OpSet>();
+  b->ops->be = be_;
+  b->ops->basis.sec.push_back({0, 0, 1, 0});
+  b->ops->basis.total = 1;
+  b->ops->allocate(op_keys({}, n_, true));
+  return b;
+}
+
+// Blocking: enlarged block = b (x) site (left) or site (x) b (right).
+std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
+  const SiteAlgebra& sa = site_algebra();
+  auto e = std::make_unique<Block>();
+  e->left = b.left;
+  e->nsites = b.nsites + 1;
+  e->normal = b.normal;
+  e->parent = &b.ops->basis;
+  e->ops = std::make_unique<OpSet>();
+  e->ops->be = be_;
+  const Basis& bb = b.ops->basis;
+  // enlarged sectors: collect (n, j) -> list of (bsec, site)
+  std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> es;
+  for (size_t s = 0; s < bb.sec.size(); ++s)
+    for (int t = 0; t < 3; ++t) {
+      int jb = bb.sec[s].j, jt = kSiteJ[t];
+      for (int J = std::abs(jb - jt); J <= jb + jt; J += 2)
+        es[{bb.sec[s].n + kSiteN[t], J}].push_back({(int)s, t});
+    }
+  Basis& eb = e->ops->basis;
+  int off = 0;
+  for (auto& [key, list] : es) {
+    Sector sec{key.first, key.second, 0, off};
+    int loc = 0;
+    int esec = (int)eb.sec.size();
+    for (auto& [s, t] : list) {
+      e->comps.push_back({s, t, esec, loc});
+      loc += bb.sec[s].dim;
+    }
+    sec.dim = loc;
+    off += loc;
+    eb.sec.push_back(sec);
+  }
+  eb.total = off;
+  std::vector<int> bsites = block_sites(b, n_);
+  std::vector<int> esites = bsites;
+  if (b.left) esites.push_back(site);
+  else esites.insert(esites.begin(), site);
+  auto keys = op_keys(esites, n_, e->normal);
+  e->ops->allocate(keys);
+
+  // ---- blocking terms, target by target
+  Side bs;
+  bs.blk = &b;
+  bs.sites = bsites;
+  bs.normal = b.normal;
+  Side ss;
+  ss.is_site = true;
+  ss.site = site;
+  ss.sites = {site};
+  const bool L = b.left;
+  std::vector<std::pair<OpKey, Term>> terms;
+  auto T = [&](const OpKey& tk, const Operand& blk_op, const Operand& site_op, double c) {
+    if (c == 0.0 || operand_zero(site_op)) return;
+    // left part = block for L growth, site for R growth
+    Term t;
+    t.k2 = tk.k2;
+    t.coef = c;
+    if (L) { t.x = blk_op; t.y = site_op; }
+    else { t.x = site_op; t.y = blk_op; }
+    terms.push_back({tk, t});
+  };
+  Operand I = op_id();
+  const int s = site;
+  std::vector<int> outs;
+  for (int p = 0; p < n_; ++p)
+    if (!in_sites(esites, p)) outs.push_back(p);
+
+  // H
+  {
+    OpKey tk{K_H, 0, 0, 0};
+    T(tk, op_blk(K_H, 0, 0, 0), op_site(sa.I), 1.0);
+    SiteOp hs = site_add(sa.N.scaled(hh(s, s)), sa.Hu, g(s, s, s, s));
+    T(tk, I, op_site(hs), 1.0);
+    std::vector<Term> cr;
+    if (L) emit_cross(this, bs, ss, cr);
+    else emit_cross(this, ss, bs, cr);
+    for (auto& t : cr) terms.push_back({tk, t});
+  }
+  // C_p
+  for (int p : esites) {
+    OpKey tk{K_C, p, 0, 1};
+    if (p == s) T(tk, I, op_site(sa.C), 1.0);
+    else T(tk, op_blk(K_C, p, 0, 1), op_site(sa.I), 1.0);
+  }
+  // temporaries for the S recurrence when the block holds normal pairs
+  std::unique_ptr<OpSet> tmp;
+  auto comp_op = [&](int kind, int p, int q, int k2) -> Operand {
+    // complementary operator of the block for the pair (p, q), any order
+    if (!b.normal) {
+      if (p <= q) return op_blk(kind, p, q, k2);
+      // (p, q) from (q, p): P^k_pq = (-1)^k P^k_qp, QJ symmetric, QK^k_pq = c_k adj(QK^k_qp)
+      Operand o = op_blk(kind, q, p, k2);
+      if (kind == K_QK) return o;  // adjoint handled by caller through flag below
+      return o;
+    }
+    return op_blk(kind, p, q, k2);  // looked up in tmp
+  };
+  if (b.normal && b.nsites > 0) {
+    tmp = std::make_unique<OpSet>();
+    tmp->be = be_;
+    tmp->basis = bb;
+    std::vector<OpKey> tk;
+    for (int p : outs) {
+      tk.push_back({K_QJ, p, s, 0});
+      tk.push_back({K_QK, p, s, 0});
+      tk.push_back({K_QK, p, s, 2});
+      tk.push_back({K_P, p, s, 0});
+      tk.push_back({K_P, p, s, 2});
+    }
+    tmp->allocate(tk);
+    build_comp_from_normal(b, *tmp, tk);
+  }
+  // S_p, p outside the enlarged block
+  for (int p : outs) {
+    OpKey tk{K_S, p, 0, 1};
+    T(tk, op_blk(K_S, p, 0, 1), op_site(sa.I), 1.0);
+    SiteOp so = site_add(sa.D.scaled(0.5 * hh(p, s)), sa.NnD, g(p, s, s, s));
+    T(tk, I, op_site(so), 1.0);
+    if (b.nsites == 0) continue;
+    // pair operators of the block for (p, s), with the sign/adjoint fixes of a stored (s, p)
+    auto pair = [&](int kind, int k2, double& sign, int& adj) -> Operand {
+      sign = 1.0;
+      adj = 0;
+      if (b.normal || p <= s) return op_blk(kind, p, s, k2);
+      if (kind == K_P && k2 == 2) sign = -1.0;
+      if (kind == K_QK) {
+        adj = 1;
+        sign = kAdjB[k2 / 2];
+      }
+      return op_blk(kind, s, p, k2, adj);
+    };
+    double sg;
+    int ad;
+    // M1: -sqrt2 [QJ_ps (x) a~_s]
+    {
+      Operand q = pair(K_QJ, 0, sg, ad);
+      T(tk, q, op_site(sa.D), -kSqrt2 * sg);
+    }
+    // M2: c2_k [QK^k_ps (x) a~_s]
+    for (int k = 0; k < 2; ++k) {
+      Operand q = pair(K_QK, 2 * k, sg, ad);
+      T(tk, q, op_site(sa.D), (L ? kC2L[k] : kC2R[k]) * sg);
+    }
+    // M3: c3_k [P^k_ps (x) a+_s]   (c3 equals c2 on both sides)
+    for (int k = 0; k < 2; ++k) {
+      Operand q = pair(K_P, 2 * k, sg, ad);
+      T(tk, q, op_site(sa.C), (L ? kC2L[k] : kC2R[k]) * sg);
+    }
+    for (int r : bsites) {
+      // M4: g_psst [a~_t (x) n_s]
+      T(tk, op_blk(K_C, r, 0, 1, 1), op_site(sa.N), g(p, s, s, r));
+      // M5: g_psrs c5_k [a~_r (x) [a+_s a~_s]^k]
+      for (int k = 0; k < 2; ++k)
+        T(tk, op_blk(K_C, r, 0, 1, 1), op_site(sa.CD[k]), g(p, s, r, s) * (L ? kC5L[k] : kC5R[k]));
+      // M6: g_pqss c6 [a+_q (x) [a~_s a~_s]^0]
+      T(tk, op_blk(K_C, r, 0, 1), op_site(sa.DD0), g(p, r, s, s) * kC6);
+    }
+  }
+  (void)comp_op;
+  if (e->normal) {
+    for (size_t a = 0; a < esites.size(); ++a)
+      for (size_t c = a; c < esites.size(); ++c) {
+        int p = esites[a], q = esites[c];
+        for (int k = 0; k < 2; ++k) {
+          OpKey ta{K_A, p, q, 2 * k}, tb{K_B, p, q, 2 * k};
+          if (p != s && q != s) {
+            if (!(p == q && k == 1)) T(ta, op_blk(K_A, p, q, 2 * k), op_site(sa.I), 1.0);
+            T(tb, op_blk(K_B, p, q, 2 * k), op_site(sa.I), 1.0);
+          } else if (p == s && q == s) {
+            if (k == 0) T(ta, I, op_site(sa.CC0), 1.0);
+            T(tb, I, op_site(sa.CD[k]), 1.0);
+          } else {
+            // one index on the site: L growth has q == s, R growth has p == s
+            int r = (p == s) ? q : p;
+            T(ta, op_blk(K_C, r, 0, 1), op_site(sa.C), 1.0);
+            T(tb, op_blk(K_C, r, 0, 1, L ? 0 : 1), op_site(L ? sa.D : sa.C), 1.0);
+          }
+        }
+      }
+  } else {
+    for (size_t a = 0; a < outs.size(); ++a)
+      for (size_t c = a; c < outs.size(); ++c) {
+        int p = outs[a], q = outs[c];
+        for (int k = 0; k < 2; ++k) {
+          double sk = k ? -1.0 : 1.0;
+          OpKey tp{K_P, p, q, 2 * k}, tq{K_QK, p, q, 2 * k};
+          if (!(p == q && k == 1)) {
+            T(tp, op_blk(K_P, p, q, 2 * k), op_site(sa.I), 1.0);
+            if (k == 0) T(tp, I, op_site(sa.DD0), g(p, q, s, s));
+            for (int r : bsites) {
+              double c = L ? (g(p, q, r, s) + sk * g(p, q, s, r)) : (sk * g(p, q, r, s) + g(p, q, s, r));
+              T(tp, op_blk(K_C, r, 0, 1, 1), op_site(sa.D), c);
+            }
+          }
+          T(tq, op_blk(K_QK, p, q, 2 * k), op_site(sa.I), 1.0);
+          T(tq, I, op_site(sa.CD[k]), g(p, s, q, s));
+          for (int r : bsites) {
+            if (L) {
+              T(tq, op_blk(K_C, r, 0, 1), op_site(sa.D), g(p, r, q, s));
+              T(tq, op_blk(K_C, r, 0, 1, 1), op_site(sa.C), g(p, s, q, r) * kSwapB[k]);
+            } else {
+              T(tq, op_blk(K_C, r, 0, 1, 1), op_site(sa.C), g(p, s, q, r));
+              T(tq, op_blk(K_C, r, 0, 1), op_site(sa.D), g(p, r, q, s) * kSwapB[k]);
+            }
+          }
+        }
+        OpKey tj{K_QJ, p, q, 0};
+        T(tj, op_blk(K_QJ, p, q, 0), op_site(sa.I), 1.0);
+        T(tj, I, op_site(sa.CD[0]), g(p, s, s, q));
+        for (int r : bsites) {
+          if (L) {
+            T(tj, op_blk(K_C, r, 0, 1), op_site(sa.D), g(p, r, s, q));
+            T(tj, op_blk(K_C, r, 0, 1, 1), op_site(sa.C), g(p, s, r, q) * kSwapB[0]);
+          } else {
+            T(tj, op_blk(K_C, r, 0, 1, 1), op_site(sa.C), g(p, s, r, q));
+            T(tj, op_blk(K_C, r, 0, 1), op_site(sa.D), g(p, r, s, q) * kSwapB[0]);
+          }
+        }
+      }
+  }
+  place_terms(b, tmp.get(), *e, terms);
+  return e;
+}
+
+// ============================================================ place_terms
+namespace {
+struct SrcBlock {
+  const double* ptr = nullptr;  // nullptr: identity
+  int trans = 0;
+  int ld = 0;
+  double coef = 1.0;
+  bool ok = false;
+};
+// Block (bra, ket) of a block operand on `basis`, honouring the adjoint flag.
+SrcBlock find_block(OpSet& set, const OpSet* tmp, const Operand& x, int bra, int ket) {
+  SrcBlock r;
+  const Basis& B = set.basis;
+  if (x.t == Operand::ID) {
+    if (bra != ket) return r;
+    r.ok = true;
+    r.ld = B.sec[bra].dim;
+    return r;
+  }
+  double* base = set.get(x.key);
+  OpSet* owner = &set;
+  if (!base && tmp) {
+    base = tmp->get(x.key);
+    owner = const_cast<OpSet*>(tmp);
+  }
+  if (!base) return r;
+  int dn = kind_dn(x.key.kind);
+  const Layout& L = owner->layout(dn, x.key.k2);
+  if (!x.adj) {
+    int bi = L.find(bra, ket);
+    if (bi < 0) return r;
+    r.ptr = base + L.blk[bi].off;
+    r.ld = L.blk[bi].cols;
+    r.ok = true;
+  } else {
+    int bi = L.find(ket, bra);
+    if (bi < 0) return r;
+    r.ptr = base + L.blk[bi].off;
+    r.ld = L.blk[bi].cols;
+    r.trans = 1;
+    r.coef = adjoint_coef(B.sec[bra].j, B.sec[ket].j, x.key.k2);
+    r.ok = true;
+  }
+  return r;
+}
+double site_val(const Operand& y, int bra, int ket) {
+  if (y.t == Operand::ID) return bra == ket ? 1.0 : 0.0;
+  return y.s.m[bra][ket];
+}
+}  // namespace
+
+void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
+                         const std::vector<std::pair<OpKey, Term>>& terms) {
+  OpSet& bo = *b.ops;
+  OpSet& eo = *e.ops;
+  const Basis& bb = bo.basis;
+  const Basis& eb = eo.basis;
+  std::vector<std::vector<const EnlComp*>> by(eb.sec.size());
+  for (auto& c : e.comps) by[c.esec].push_back(&c);
+  const bool L = e.left;
+  PlaceBuilder pb;
+  for (auto& [tk, t] : terms) {
+    double* dst = eo.get(tk);
+    if (!dst) continue;
+    const Layout& TL = eo.layout(kind_dn(tk.kind), tk.k2);
+    const Operand& bop = L ? t.x : t.y;   // operand on the block part
+    const Operand& sop = L ? t.y : t.x;   // operand on the site part
+    if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
+    for (auto& blk : TL.blk) {
+      int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
+      for (const EnlComp* cp : by[blk.bra])
+        for (const EnlComp* c : by[blk.ket]) {
+          double sv = site_val(sop, cp->site, c->site);
+          if (sv == 0.0) continue;
+          SrcBlock src = find_block(bo, tmp, bop, cp->bsec, c->bsec);
+          if (!src.ok) continue;
+          int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
+          int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
+          double tp;
+          int nleft, pright;
+          if (L) {
+            tp = tensor_product_coef(jb_p, jb, bop.k2, js_p, js, sop.k2, Jp, J, t.k2);
+            nleft = bb.sec[c->bsec].n;
+            pright = sop.par;
+          } else {
+            tp = tensor_product_coef(js_p, js, sop.k2, jb_p, jb, bop.k2, Jp, J, t.k2);
+            nleft = kSiteN[c->site];
+            pright = bop.par;
+          }
+          if (tp == 0.0) continue;
+          double sign = ((pright & nleft) & 1) ? -1.0 : 1.0;
+          double alpha = t.coef * tp * sv * sign * src.coef;
+          int rows = bb.sec[cp->bsec].dim, cols = bb.sec[c->bsec].dim;
+          double* d = dst + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
+          pb.add(d, rows, cols, blk.cols, PlaceSeg{src.ptr, src.ld, src.trans, alpha});
+        }
+    }
+  }
+  pb.run(be_);
+}
+
+// ============================================================ complementary from normal
+// P^k_pq = sum_{a,b in blk} g_pqab [a~_a a~_b]^k,  QJ_pq = sum g_pabq B^0_ab,
+// QK^k_pq = sum g_paqb B^k_ab, built from the stored normal operators
+// (A^k_ab, B^k_ab with a <= b) by one dense GEMM per source layout
+// (coefficient matrix times the stacked operators) and an adjoint placement.
+void Engine::build_comp_from_normal(const Block& b, OpSet& dst, const std::vector<OpKey>& keys) {
+  OpSet& src = *b.ops;
+  std::vector<int> bs = block_sites(b, n_);
+  // source ops of a layout in allocation order
+  auto stacked = [&](int dn, int k2, std::vector<OpKey>& order) -> const double* {
+    const double* base = nullptr;
+    std::vector<std::pair<const double*, OpKey>> v;
+    for (auto& [k, p] : src.ops)
+      if (kind_dn(k.kind) == dn && k.k2 == k2) v.push_back({p, k});
+    std::sort(v.begin(), v.end(), [](auto& x, auto& y) { return x.first < y.first; });
+    for (auto& [p, k] : v) order.push_back(k);
+    if (!v.empty()) base = v.front().first;
+    return base;
+  };
+  for (int kind : {K_P, K_QJ, K_QK})
+    for (int k2 : {0, 2}) {
+      if (kind == K_QJ && k2 == 2) continue;
+      std::vector<OpKey> tk;
+      for (auto& k : keys)
+        if (k.kind == kind && k.k2 == k2 && dst.get(k)) tk.push_back(k);
+      if (tk.empty()) continue;
+      int sdn = (kind == K_P) ? 2 : 0;
+      std::vector<OpKey> order;
+      const double* X = stacked(sdn, k2, order);
+      if (!X) continue;
+      const Layout& SL = src.layout(sdn, k2);
+      int K = (int)order.size(), M = (int)tk.size();
+      std::map<OpKey, int> col;
+      for (int i = 0; i < K; ++i) col[order[i]] = i;
+      std::vector<double> Gd((size_t)M * K, 0.0), Ga((size_t)M * K, 0.0);
+      double sk = (k2 == 2) ? -1.0 : 1.0;
+      for (int m = 0; m < M; ++m) {
+        int p = tk[m].i, q = tk[m].j;
+        for (size_t ia = 0; ia < bs.size(); ++ia)
+          for (size_t ib = ia; ib < bs.size(); ++ib) {
+            int a = bs[ia], c = bs[ib];
+            if (kind == K_P) {
+              if (a == c && k2 == 2) continue;
+              auto it = col.find({K_A, a, c, k2});
+              if (it == col.end()) continue;
+              double v = g(p, q, a, c) + (a != c ? sk * g(p, q, c, a) : 0.0);
+              Ga[(size_t)m * K + it->second] += -v;  // P = -adj(sum v A)
+            } else {
+              auto it = col.find({K_B, a, c, k2});
+              if (it == col.end()) continue;
+              if (kind == K_QJ) {
+                Gd[(size_t)m * K + it->second] += g(p, a, c, q);
+                if (a != c) Ga[(size_t)m * K + it->second] += g(p, c, a, q);
+              } else {
+                Gd[(size_t)m * K + it->second] += g(p, a, q, c);
+                if (a != c) Ga[(size_t)m * K + it->second] += kAdjB[k2 / 2] * g(p, c, q, a);
+              }
+            }
+          }
+      }
+      size_t N = SL.size;
+      for (int pass = 0; pass < 2; ++pass) {
+        std::vector<double>& G = pass == 0 ? Gd : Ga;
+        bool any = false;
+        for (double v : G) if (v != 0.0) { any = true; break; }
+        if (!any) continue;
+        double* Gdev = (double*)be_->alloc(G.size() * sizeof(double));
+        be_->copy_h2d(Gdev, G.data(), G.size() * sizeof(double));
+        double* Y = (double*)be_->alloc((size_t)M * N * sizeof(double));
+        be_->memset0(Y, (size_t)M * N * sizeof(double));
+        GemmBuilder gb;
+        // the N dimension can be large: split into column panels
+        const size_t panel = 1 << 20;
+        for (size_t c0 = 0; c0 < N; c0 += panel) {
+          int nc = (int)std::min(panel, N - c0);
+          gb.add(Y + c0, M, nc, (int)N, GemmSeg{Gdev, X + c0, K, K, (int)N, 0, 0, 1.0});
+        }
+        gb.run(be_, opt_.prec);
+        // place rows of Y into the targets (directly, or as adjoint)
+        PlaceBuilder pb;
+        const Layout& DL = dst.layout(kind_dn(kind), k2);
+        for (int m = 0; m < M; ++m) {
+          double* d = dst.get(tk[m]);
+          const double* y = Y + (size_t)m * N;
+          for (auto& blk : DL.blk) {
+            if (pass == 0) {
+              int si = SL.find(blk.bra, blk.ket);
+              if (si < 0) continue;
+              pb.add(d + blk.off, blk.rows, blk.cols, blk.cols,
+                     PlaceSeg{y + SL.blk[si].off, SL.blk[si].cols, 0, 1.0});
+            } else {
+              int si = SL.find(blk.ket, blk.bra);
+              if (si < 0) continue;
+              double c = adjoint_coef(dst.basis.sec[blk.bra].j, dst.basis.sec[blk.ket].j, k2);
+              pb.add(d + blk.off, blk.rows, blk.cols, blk.cols,
+                     PlaceSeg{y + SL.blk[si].off, SL.blk[si].cols, 1, c});
+            }
+          }
+        }
+        pb.run(be_);
+        be_->sync();
+        be_->free(Y);
+        be_->free(Gdev);
+      }
+    }
+}
+
+// ============================================================ renormalisation
+// O'(a', a) = U_a'^T O(a', a) U_a with Ut[a] = kept eigenvectors as rows.
+std::unique_ptr<Block> Engine::renormalize(Block& enl, const std::vector<int>& kept,
+                                           const std::vector<double*>& ut, bool switch_to_comp) {
+  auto nb = std::make_unique<Block>();
+  nb->left = enl.left;
+  nb->nsites = enl.nsites;
+  nb->normal = enl.normal;
+  nb->ops = std::make_unique<OpSet>();
+  nb->ops->be = be_;
+  const Basis& eb = enl.ops->basis;
+  Basis& b = nb->ops->basis;
+  std::vector<int> map(eb.sec.size(), -1);
+  int off = 0;
+  for (size_t s = 0; s < eb.sec.size(); ++s) {
+    if (kept[s] <= 0) continue;
+    map[s] = (int)b.sec.size();
+    b.sec.push_back({eb.sec[s].n, eb.sec[s].j, kept[s], off});
+    off += kept[s];
+  }
+  b.total = off;
+  std::vector<OpKey> keys;
+  for (auto& [k, p] : enl.ops->ops) keys.push_back(k);
+  nb->ops->allocate(keys);
+  // per layout: T = E U (temp), O' = U^T T
+  std::map<std::pair<int, int>, std::vector<OpKey>> by;
+  for (auto& k : keys) by[{kind_dn(k.kind), k.k2}].push_back(k);
+  for (auto& [lk, ks] : by) {
+    const Layout& EL = enl.ops->layout(lk.first, lk.second);
+    const Layout& NL = nb->ops->layout(lk.first, lk.second);
+    if (NL.size == 0) continue;
+    // temp layout sizes: block (a', a) -> m_a' x kept_a
+    std::vector<size_t> toff(EL.blk.size(), 0);
+    size_t tsz = 0;
+    for (size_t i = 0; i < EL.blk.size(); ++i) {
+      auto& bl = EL.blk[i];
+      toff[i] = tsz;
+      if (map[bl.bra] >= 0 && map[bl.ket] >= 0) tsz += (size_t)bl.rows * kept[bl.ket];
+    }
+    if (tsz == 0) continue;
+    // chunk operators to bound the temporary
+    size_t per = std::max<size_t>(1, (size_t)(256u << 20) / (tsz * sizeof(double)));
+    double* T = (double*)be_->alloc(std::min(per, ks.size()) * tsz * sizeof(double));
+    for (size_t c0 = 0; c0 < ks.size(); c0 += per) {
+      size_t c1 = std::min(ks.size(), c0 + per);
+      be_->memset0(T, (c1 - c0) * tsz * sizeof(double));
+      GemmBuilder g1, g2;
+      for (size_t oi = c0; oi < c1; ++oi) {
+        const double* E = enl.ops->get(ks[oi]);
+        double* O = nb->ops->get(ks[oi]);
+        if (!E || !O) continue;
+        double* Tb = T + (oi - c0) * tsz;
+        for (size_t i = 0; i < EL.blk.size(); ++i) {
+          auto& bl = EL.blk[i];
+          int na = map[bl.bra], nk = map[bl.ket];
+          if (na < 0 || nk < 0) continue;
+          int ka = kept[bl.ket], kap = kept[bl.bra];
+          // T(a',a) = E(a',a) * Ut_a^T
+          g1.add(Tb + toff[i], bl.rows, ka, ka,
+                 GemmSeg{E + bl.off, ut[bl.ket], bl.cols, bl.cols, bl.cols, 0, 1, 1.0});
+          int ni = NL.find(na, nk);
+          auto& nbk = NL.blk[ni];
+          // O'(a',a) = Ut_a' * T(a',a)
+          g2.add(O + nbk.off, kap, ka, ka,
+                 GemmSeg{ut[bl.bra], Tb + toff[i], bl.rows, bl.rows, ka, 0, 0, 1.0});
+        }
+      }
+      g1.run(be_, opt_.prec);
+      g2.run(be_, opt_.prec);
+    }
+    be_->sync();
+    be_->free(T);
+  }
+  if (switch_to_comp) {
+    // new complementary block: H, C, S copied, P/QJ/QK built from the normal pairs
+    auto cb = std::make_unique<Block>();
+    cb->left = nb->left;
+    cb->nsites = nb->nsites;
+    cb->normal = false;
+    cb->ops = std::make_unique<OpSet>();
+    cb->ops->be = be_;
+    cb->ops->basis = nb->ops->basis;
+    std::vector<int> sites = block_sites(*nb, n_);
+    auto ck = op_keys(sites, n_, false);
+    cb->ops->allocate(ck);
+    for (auto& k : ck) {
+      if (k.kind == K_H || k.kind == K_C || k.kind == K_S) {
+        double* d = cb->ops->get(k);
+        const double* s = nb->ops->get(k);
+        if (d && s) {
+          size_t sz = cb->ops->layout(kind_dn(k.kind), k.k2).size;
+          be_->copy_d2d(d, s, sz * sizeof(double));
+        }
+      }
+    }
+    build_comp_from_normal(*nb, *cb->ops, ck);
+    be_->sync();
+    return cb;
+  }
+  return nb;
+}
+
+// ============================================================ bond: psi, H psi
+namespace {
+struct PsiLayout {
+  struct Blk {
+    int a, b, rows, cols;
+    size_t off;
+  };
+  std::vector<Blk> blk;
+  std::vector<int> lut;  // a * nb + b
+  int nb = 0;
+  size_t size = 0;
+  int find(int a, int b) const { return lut[(size_t)a * nb + b]; }
+};
+PsiLayout make_psi(const Basis& L, const Basis& R, int N, int S) {
+  PsiLayout P;
+  P.nb = (int)R.sec.size();
+  P.lut.assign(L.sec.size() * R.sec.size(), -1);
+  for (size_t a = 0; a < L.sec.size(); ++a)
+    for (size_t b = 0; b < R.sec.size(); ++b) {
+      if (L.sec[a].n + R.sec[b].n != N || !triangle(L.sec[a].j, R.sec[b].j, S)) continue;
+      P.lut[a * R.sec.size() + b] = (int)P.blk.size();
+      P.blk.push_back({(int)a, (int)b, L.sec[a].dim, R.sec[b].dim, P.size});
+      P.size += (size_t)L.sec[a].dim * R.sec[b].dim;
+    }
+  return P;
+}
+// bra sectors reachable from ket sector `ket` through operand x on basis B
+std::vector<std::pair<int, SrcBlock>> reach(OpSet& set, const Operand& x, int ket) {
+  std::vector<std::pair<int, SrcBlock>> out;
+  const Basis& B = set.basis;
+  if (x.t == Operand::ID) {
+    SrcBlock s;
+    s.ok = true;
+    s.ld = B.sec[ket].dim;
+    out.push_back({ket, s});
+    return out;
+  }
+  for (size_t bra = 0; bra < B.sec.size(); ++bra) {
+    if (B.sec[bra].n != B.sec[ket].n + x.dn || !triangle(B.sec[ket].j, x.k2, B.sec[bra].j)) continue;
+    SrcBlock s = find_block(set, nullptr, x, (int)bra, ket);
+    if (s.ok) out.push_back({(int)bra, s});
+  }
+  return out;
+}
+}  // namespace
+
+struct HPsiPlan {
+  PsiLayout psi;
+  double* in = nullptr;   // psi input buffer
+  double* out = nullptr;  // sigma output buffer
+  double* X = nullptr;    // phase-1 intermediates
+  size_t xsize = 0;
+  std::vector<GemmGroup> g1, g2;
+  std::vector<GemmSeg> s1, s2;
+  double flops = 0.0;
+};
+
+void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
+  OpSet& lo = *Le.ops;
+  OpSet& ro = *Re.ops;
+  plan.psi = make_psi(lo.basis, ro.basis, n_elec_, two_s_);
+  const PsiLayout& P = plan.psi;
+  std::vector<Term> terms;
+  terms.push_back({op_blk(K_H, 0, 0, 0), op_id(), 0, 1.0});
+  terms.push_back({op_id(), op_blk(K_H, 0, 0, 0), 0, 1.0});
+  Side ls, rs;
+  ls.blk = &Le;
+  ls.sites = block_sites(Le, n_);
+  ls.normal = Le.normal;
+  rs.blk = &Re;
+  rs.sites = block_sites(Re, n_);
+  rs.normal = Re.normal;
+  emit_cross(this, ls, rs, terms);
+  // phase-1 slots
+  struct Slot {
+    const double* A;
+    int lda, transA;
+    const double* B;
+    int ldb;
+    int m, n, k;
+    double alpha;
+  };
+  std::vector<Slot> slots;
+  std::map<double*, std::vector<GemmSeg>> p2;
+  std::map<double*, std::array<int, 3>> p2dim;
+  std::vector<std::pair<size_t, std::pair<double*, GemmSeg>>> p2x;  // slot offset -> (sigma, seg)
+  size_t xoff = 0;
+  plan.flops = 0.0;
+  for (auto& t : terms) {
+    for (auto& kb : P.blk) {
+      auto lr = reach(lo, t.x, kb.a);
+      if (lr.empty()) continue;
+      auto rr = reach(ro, t.y, kb.b);
+      if (rr.empty()) continue;
+      const Sector& sa = lo.basis.sec[kb.a];
+      const Sector& sb = ro.basis.sec[kb.b];
+      double sign = ((t.y.par & sa.n) & 1) ? -1.0 : 1.0;
+      for (auto& [ap, xs] : lr)
+        for (auto& [bp, ys] : rr) {
+          int pi = P.find(ap, bp);
+          if (pi < 0) continue;
+          const Sector& sap = lo.basis.sec[ap];
+          const Sector& sbp = ro.basis.sec[bp];
+          // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
+          int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
+          double hc = hpsi_coef(sap.j, sbp.j, sa.j, sb.j, kop, two_s_);
+          if (hc == 0.0) continue;
+          double alpha = t.coef * hc * sign * xs.coef * ys.coef;
+          double* sig = plan.out + P.blk[pi].off;
+          const double* psi = plan.in + kb.off;
+          int ma = sa.dim, mb = sb.dim, map_ = sap.dim, mbp = sbp.dim;
+          p2dim[sig] = {map_, mbp, mbp};
+          if (t.x.t == Operand::ID) {
+            // sigma(a, b') += alpha psi(a,b) y^T
+            GemmSeg s{psi, ys.ptr, mb, mb, ys.ld, 0, ys.trans ? 0 : 1, alpha};
+            p2[sig].push_back(s);
+            plan.flops += 2.0 * ma * mbp * mb;
+          } else if (t.y.t == Operand::ID) {
+            GemmSeg s{xs.ptr, psi, ma, xs.ld, mb, xs.trans, 0, alpha};
+            p2[sig].push_back(s);
+            plan.flops += 2.0 * map_ * mb * ma;
+          } else {
+            slots.push_back({xs.ptr, xs.ld, xs.trans, psi, mb, map_, mb, ma, alpha});
+            GemmSeg s{nullptr, ys.ptr, mb, mb, ys.ld, 0, ys.trans ? 0 : 1, 1.0};
+            p2x.push_back({xoff, {sig, s}});
+            xoff += (size_t)map_ * mb;
+            plan.flops += 2.0 * map_ * mb * ma + 2.0 * map_ * mbp * mb;
+          }
+        }
+    }
+  }
+  plan.xsize = xoff;
+  if (plan.X) be_->free(plan.X);
+  plan.X = xoff ? (double*)be_->alloc(xoff * sizeof(double)) : nullptr;
+  size_t off = 0;
+  plan.g1.clear();
+  plan.s1.clear();
+  for (auto& sl : slots) {
+    plan.g1.push_back({plan.X + off, sl.m, sl.n, sl.n, (int)plan.s1.size(), 1});
+    plan.s1.push_back({sl.A, sl.B, sl.k, sl.lda, sl.ldb, sl.transA, 0, sl.alpha});
+    off += (size_t)sl.m * sl.n;
+  }
+  for (auto& [xo, pr] : p2x) {
+    GemmSeg s = pr.second;
+    s.A = plan.X + xo;
+    p2[pr.first].push_back(s);
+  }
+  plan.g2.clear();
+  plan.s2.clear();
+  for (auto& [sig, segs] : p2) {
+    auto d = p2dim[sig];
+    plan.g2.push_back({sig, d[0], d[1], d[2], (int)plan.s2.size(), (int)segs.size()});
+    plan.s2.insert(plan.s2.end(), segs.begin(), segs.end());
+  }
+}
+
+void Engine::apply_hpsi(HPsiPlan& plan) {
+  be_->memset0(plan.out, plan.psi.size * sizeof(double));
+  if (plan.xsize) {
+    be_->memset0(plan.X, plan.xsize * sizeof(double));
+    be_->gemm(plan.g1, plan.s1, opt_.prec);
+  }
+  be_->gemm(plan.g2, plan.s2, opt_.prec);
+}
+
+// ============================================================ Davidson
+namespace {
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+}  // namespace
+
+double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
+  const size_t len = plan.psi.size;
+  const int M = std::max(4, opt_.max_space);
+  double* V = (double*)be_->alloc((size_t)M * len * sizeof(double));
+  double* HV = (double*)be_->alloc((size_t)M * len * sizeof(double));
+  double* dv = (double*)be_->alloc((size_t)(M * M + 4 * M + 8) * sizeof(double));
+  double* dA = dv;
+  double* dw = dv + M * M;
+  double* dZ = dw + M;        // reused for coefficient vectors (M)
+  double* dc = dZ + M;
+  double* dEv = (double*)be_->alloc((size_t)M * M * sizeof(double));
+  std::vector<double> A((size_t)M * M, 0.0), w(M), Z((size_t)M * M), c(M), tmpv(M);
+  // guess: provided psi (if nonzero) else a deterministic pseudo-random vector
+  {
+    std::vector<double> h(len);
+    be_->copy_d2h(h.data(), psi, len * sizeof(double));
+    double nrm = 0.0;
+    for (double x : h) nrm += x * x;
+    if (!(nrm > 1e-20)) {
+      for (size_t i = 0; i < len; ++i)
+        h[i] = ((splitmix64(i + 12345) >> 11) * (1.0 / 9007199254740992.0)) - 0.5;
+      nrm = 0.0;
+      for (double x : h) nrm += x * x;
+    }
+    nrm = std::sqrt(nrm);
+    for (double& x : h) x /= nrm;
+    be_->copy_h2d(V, h.data(), len * sizeof(double));
+  }
+  auto dot_host = [&](const double* a, const double* b) {
+    be_->dots(a, 1, len, len, b, dc);
+    double r;
+    be_->copy_d2h(&r, dc, sizeof(double));
+    return r;
+  };
+  auto apply = [&](int i) {
+    be_->copy_d2d(plan.in, V + (size_t)i * len, len * sizeof(double));
+    auto t0 = std::chrono::steady_clock::now();
+    apply_hpsi(plan);
+    be_->sync();
+    auto t1 = std::chrono::steady_clock::now();
+    stats_.hpsi_seconds += std::chrono::duration<double>(t1 - t0).count();
+    stats_.hpsi_flops += plan.flops;
+    stats_.hpsi_calls += 1;
+    be_->copy_d2d(HV + (size_t)i * len, plan.out, len * sizeof(double));
+  };
+  int m = 1;
+  apply(0);
+  double e = 0.0;
+  double* x = psi;  // result vector
+  double* r = plan.in;  // residual workspace (psi-in buffer reused between applies)
+  int it = 0;
+  for (it = 1; it <= opt_.max_davidson_iter; ++it) {
+    // projected matrix: row/col m-1
+    be_->dots(V, m, len, len, HV + (size_t)(m - 1) * len, dc);
+    be_->copy_d2h(tmpv.data(), dc, m * sizeof(double));
+    for (int i = 0; i < m; ++i) A[(size_t)i * M + (m - 1)] = A[(size_t)(m - 1) * M + i] = tmpv[i];
+    // small eigenproblem on the device
+    std::vector<double> Am((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Am[(size_t)i * m + j] = 0.5 * (A[(size_t)i * M + j] + A[(size_t)j * M + i]);
+    be_->copy_h2d(dA, Am.data(), Am.size() * sizeof(double));
+    be_->eigh({EighTask{dA, dw, dEv, m}});
+    be_->copy_d2h(w.data(), dw, m * sizeof(double));
+    be_->copy_d2h(Z.data(), dEv, (size_t)m * m * sizeof(double));
+    // lowest eigenpair = last row (eigenvalues descending)
+    e = w[m - 1];
+    for (int i = 0; i < m; ++i) c[i] = Z[(size_t)(m - 1) * m + i];
+    be_->copy_h2d(dZ, c.data(), m * sizeof(double));
+    be_->combine(x, 0.0, V, m, len, len, dZ);
+    be_->combine(r, 0.0, HV, m, len, len, dZ);
+    be_->axpby(r, 1.0, x, -e, len);
+    double rn = std::sqrt(std::max(0.0, dot_host(r, r)));
+    if (opt_.verbose > 1) std::fprintf(stderr, "  davidson it %d m %d E %.12f res %.3e\n", it, m, e, rn);
+    if (rn < opt_.davidson_tol) break;
+    if (m >= M) {
+      // restart with the lowest two Ritz vectors
+      std::vector<double> c2((size_t)2 * m);
+      for (int i = 0; i < m; ++i) {
+        c2[i] = Z[(size_t)(m - 1) * m + i];
+        c2[m + i] = Z[(size_t)(m - 2) * m + i];
+      }
+      double* nV = (double*)be_->alloc((size_t)2 * len * sizeof(double));
+      double* nH = (double*)be_->alloc((size_t)2 * len * sizeof(double));
+      for (int q = 0; q < 2; ++q) {
+        be_->copy_h2d(dZ, c2.data() + (size_t)q * m, m * sizeof(double));
+        be_->combine(nV + (size_t)q * len, 0.0, V, m, len, len, dZ);
+        be_->combine(nH + (size_t)q * len, 0.0, HV, m, len, len, dZ);
+      }
+      be_->copy_d2d(V, nV, 2 * len * sizeof(double));
+      be_->copy_d2d(HV, nH, 2 * len * sizeof(double));
+      be_->free(nV);
+      be_->free(nH);
+      std::fill(A.begin(), A.end(), 0.0);
+      A[0] = w[m - 1];
+      A[(size_t)1 * M + 1] = w[m - 2];
+      m = 2;
+    }
+    // new direction t = r, orthogonalised twice against V
+    double* t = V + (size_t)m * len;
+    be_->copy_d2d(t, r, len * sizeof(double));
+    for (int pass = 0; pass < 2; ++pass) {
+      be_->dots(V, m, len, len, t, dc);
+      be_->copy_d2h(tmpv.data(), dc, m * sizeof(double));
+      for (int i = 0; i < m; ++i) tmpv[i] = -tmpv[i];
+      be_->copy_h2d(dZ, tmpv.data(), m * sizeof(double));
+      be_->combine(t, 1.0, V, m, len, len, dZ);
+    }
+    double tn = std::sqrt(std::max(0.0, dot_host(t, t)));
+    if (tn < 1e-14) break;
+    be_->axpby(t, 0.0, t, 1.0 / tn, len);
+    apply(m);
+    ++m;
+  }
+  if (iters) *iters = it;
+  be_->sync();
+  be_->free(V);
+  be_->free(HV);
+  be_->free(dv);
+  be_->free(dEv);
+  return e;
+}
+
+// ============================================================ decimation
+namespace {
+struct Cand {
+  double lam;
+  int n, j, rank, sec;
+};
+std::vector<int> select(std::vector<Cand>& c, int D) {
+  const double lam_min = 1e-12, tie = 1e-9;
+  std::vector<int> idx;
+  for (size_t i = 0; i < c.size(); ++i)
+    if (c[i].lam >= lam_min) idx.push_back((int)i);
+  auto key_less = [&](int a, int b) {
+    if (c[a].lam != c[b].lam) return c[a].lam > c[b].lam;
+    if (c[a].n != c[b].n) return c[a].n < c[b].n;
+    if (c[a].j != c[b].j) return c[a].j < c[b].j;
+    return c[a].rank < c[b].rank;
+  };
+  std::sort(idx.begin(), idx.end(), key_less);
+  if ((int)idx.size() <= D) return idx;
+  double ld = c[idx[D - 1]].lam;
+  std::vector<int> hi, ti;
+  for (int i : idx) {
+    if (c[i].lam > ld * (1 + tie)) hi.push_back(i);
+    else if (std::abs(c[i].lam - ld) <= ld * tie) ti.push_back(i);
+  }
+  std::sort(ti.begin(), ti.end(), [&](int a, int b) {
+    if (c[a].n != c[b].n) return c[a].n < c[b].n;
+    if (c[a].j != c[b].j) return c[a].j < c[b].j;
+    return c[a].rank < c[b].rank;
+  });
+  for (int i : ti) {
+    if ((int)hi.size() >= D) break;
+    hi.push_back(i);
+  }
+  return hi;
+}
+}  // namespace
+
+// rho per sector of the enlarged block being truncated; returns Ut pointers
+// (device, rows = kept eigenvectors) and kept counts; discarded weight out.
+double Engine::decimate(Block& enl, const HPsiPlan& plan, const double* psi, bool left,
+                        std::vector<int>& kept, std::vector<double*>& ut, void** storage) {
+  const Basis& B = enl.ops->basis;
+  const PsiLayout& P = plan.psi;
+  size_t tot = 0;
+  std::vector<size_t> roff(B.sec.size());
+  for (size_t s = 0; s < B.sec.size(); ++s) {
+    roff[s] = tot;
+    tot += (size_t)B.sec[s].dim * B.sec[s].dim;
+  }
+  // rho, eigenvectors, eigenvalues in one buffer
+  size_t wtot = B.total;
+  double* buf = (double*)be_->alloc((2 * tot + wtot) * sizeof(double));
+  be_->memset0(buf, (2 * tot + wtot) * sizeof(double));
+  double* rho = buf;
+  double* vec = buf + tot;
+  double* wv = buf + 2 * tot;
+  GemmBuilder gb;
+  for (auto& bl : P.blk) {
+    const double* pb = psi + bl.off;
+    if (left) {
+      int s = bl.a, m = bl.rows, k = bl.cols;
+      gb.add(rho + roff[s], m, m, m, GemmSeg{pb, pb, k, k, k, 0, 1, 1.0});
+    } else {
+      int s = bl.b, m = bl.cols, k = bl.rows;
+      gb.add(rho + roff[s], m, m, m, GemmSeg{pb, pb, k, m, m, 1, 0, 1.0});
+    }
+  }
+  gb.run(be_, Precision::FP64);
+  std::vector<EighTask> tasks;
+  std::vector<size_t> woff(B.sec.size());
+  size_t wo = 0;
+  for (size_t s = 0; s < B.sec.size(); ++s) {
+    woff[s] = wo;
+    wo += B.sec[s].dim;
+    if (B.sec[s].dim > 0) tasks.push_back({rho + roff[s], wv + woff[s], vec + roff[s], B.sec[s].dim});
+  }
+  be_->eigh(tasks);
+  std::vector<double> w(wtot);
+  be_->copy_d2h(w.data(), wv, wtot * sizeof(double));
+  std::vector<Cand> cands;
+  double total = 0.0;
+  for (size_t s = 0; s < B.sec.size(); ++s)
+    for (int r = 0; r < B.sec[s].dim; ++r) {
+      double lam = w[woff[s] + r];
+      total += lam;
+      cands.push_back({lam, B.sec[s].n, B.sec[s].j, r, (int)s});
+    }
+  auto keep = select(cands, opt_.D);
+  kept.assign(B.sec.size(), 0);
+  double kw = 0.0;
+  for (int i : keep) {
+    kept[cands[i].sec] = std::max(kept[cands[i].sec], cands[i].rank + 1);
+    kw += cands[i].lam;
+  }
+  // ranks kept per sector are a prefix (eigenvalues descending)
+  ut.assign(B.sec.size(), nullptr);
+  for (size_t s = 0; s < B.sec.size(); ++s) ut[s] = vec + roff[s];
+  *storage = buf;
+  return std::max(0.0, total - kw);
+}
+
+// ============================================================ engine
+Engine::Engine(Backend* be, int n, const double* h, const double* eri, double e_core, int n_elec,
+               int two_s, const Options& opt, const int* occ, const int* two_s_right)
+    : be_(be), n_(n), n_elec_(n_elec), two_s_(two_s), e_core_(e_core), opt_(opt) {
+  if (n < 2) throw std::invalid_argument("need at least two orbitals");
+  if (n_elec < 0 || n_elec > 2 * n) throw std::invalid_argument("n_elec out of range");
+  if (two_s < 0 || ((n_elec - two_s) & 1)) throw std::invalid_argument("two_s parity");
+  h_.assign(h, h + (size_t)n * n);
+  g_.resize((size_t)n * n * n * n);
+  // g_pqrs = (ps|qr) from chemists' integrals eri[p,q,r,s] = (pq|rs)
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        for (int s = 0; s < n; ++s)
+          g_[(((size_t)p * n + q) * n + r) * n + s] = eri[(((size_t)p * n + s) * n + q) * n + r];
+  tL_ = (n - 1) / 2;
+  tR_ = n - 1 - tL_;
+  occ_.assign(occ, occ + n);
+  path_.assign(two_s_right, two_s_right + n + 1);
+  if (path_[0] != two_s || path_[n] != 0) throw std::invalid_argument("bad initial spin path");
+  L_.resize(n + 1);
+  R_.resize(n + 1);
+  L_[0] = vacuum(true);
+  L_[0]->normal = left_normal(0);
+  if (!L_[0]->normal) {
+    L_[0]->ops = std::make_unique<OpSet>();
+    L_[0]->ops->be = be_;
+    L_[0]->ops->basis.sec.push_back({0, 0, 1, 0});
+    L_[0]->ops->basis.total = 1;
+    L_[0]->ops->allocate(op_keys({}, n_, false));
+  }
+  build_initial_right();
+}
+
+void Engine::build_initial_right() {
+  R_[0] = vacuum(false);
+  R_[0]->normal = right_normal(0);
+  if (!R_[0]->normal) {
+    R_[0]->ops = std::make_unique<OpSet>();
+    R_[0]->ops->be = be_;
+    R_[0]->ops->basis.sec.push_back({0, 0, 1, 0});
+    R_[0]->ops->basis.total = 1;
+    R_[0]->ops->allocate(op_keys({}, n_, false));
+  }
+  int nr = 0;
+  for (int r = 1; r <= n_ - 2; ++r) {
+    int site = n_ - r;
+    nr += occ_[site];
+    auto e = enlarge(*R_[r - 1], site);
+    const Basis& eb = e->ops->basis;
+    int target = eb.find(nr, path_[site]);
+    if (target < 0) throw std::runtime_error("initial state sector missing");
+    std::vector<int> kept(eb.sec.size(), 0);
+    kept[target] = 1;
+    // the single multiplet: component (bsec 0, site occupation) of the target sector
+    int eoff = -1;
+    for (auto& c : e->comps)
+      if (c.esec == target && c.site == occ_[site] && c.bsec == 0) eoff = c.eoff;
+    if (eoff < 0) throw std::runtime_error("initial state component missing");
+    int m = eb.sec[target].dim;
+    std::vector<double> row(m, 0.0);
+    row[eoff] = 1.0;
+    std::vector<double*> ut(eb.sec.size(), nullptr);
+    double* u = (double*)be_->alloc(m * sizeof(double));
+    be_->copy_h2d(u, row.data(), m * sizeof(double));
+    ut[target] = u;
+    bool sw = e->normal && !right_normal(r);
+    R_[r] = renormalize(*e, kept, ut, sw);
+    be_->sync();
+    be_->free(u);
+  }
+}
+
+double Engine::optimize_bond(int i, bool l2r, double* trunc) {
+  auto Le = enlarge(*L_[i], i);
+  auto Re = enlarge(*R_[n_ - i - 2], i + 1);
+  HPsiPlan plan;
+  plan.psi = make_psi(Le->ops->basis, Re->ops->basis, n_elec_, two_s_);
+  size_t len = plan.psi.size;
+  if (len == 0) throw std::runtime_error("empty two-site space at bond " + std::to_string(i));
+  plan.in = (double*)be_->alloc(len * sizeof(double));
+  plan.out = (double*)be_->alloc(len * sizeof(double));
+  double* psi = (double*)be_->alloc(len * sizeof(double));
+  be_->memset0(psi, len * sizeof(double));
+  plan_hpsi(*Le, *Re, plan);
+  int its = 0;
+  double e = davidson(plan, psi, &its) + e_core_;
+  stats_.davidson_iters += its;
+  std::vector<int> kept;
+  std::vector<double*> ut;
+  void* store = nullptr;
+  if (l2r) {
+    *trunc = decimate(*Le, plan, psi, true, kept, ut, &store);
+    bool sw = Le->normal && !left_normal(i + 1);
+    L_[i + 1] = renormalize(*Le, kept, ut, sw);
+  } else {
+    *trunc = decimate(*Re, plan, psi, false, kept, ut, &store);
+    bool sw = Re->normal && !right_normal(n_ - i - 1);
+    R_[n_ - i - 1] = renormalize(*Re, kept, ut, sw);
+  }
+  be_->sync();
+  be_->free(store);
+  be_->free(psi);
+  be_->free(plan.in);
+  be_->free(plan.out);
+  if (plan.X) be_->free(plan.X);
+  last_bond_ = i;
+  bond_e_.push_back(e);
+  if (opt_.verbose)
+    std::fprintf(stderr, "bond %d %s E %.12f trunc %.3e it %d len %zu flops %.3e\n", i,
+                 l2r ? "LR" : "RL", e, *trunc, its, len, plan.flops);
+  return e;
+}
+
+SweepStats Engine::sweep() {
+  stats_ = SweepStats();
+  auto t0 = std::chrono::steady_clock::now();
+  double e = 0.0, tr = 0.0, tmax = 0.0;
+  for (int i = 0; i <= n_ - 3; ++i) {
+    e = optimize_bond(i, true, &tr);
+    tmax = std::max(tmax, tr);
+    if (n_ - i - 2 > 0) R_[n_ - i - 2].reset();
+  }
+  for (int i = n_ - 2; i >= 1; --i) {
+    e = optimize_bond(i, false, &tr);
+    tmax = std::max(tmax, tr);
+    if (i > 0) L_[i].reset();
+  }
+  be_->sync();
+  energy_ = e;
+  stats_.energy = e;
+  stats_.max_trunc = tmax;
+  sweep_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return stats_;
+}
+
+}  // namespace dmrg

@@ -1,0 +1,200 @@
+// Spin-adapted (SU(2) x U(1)) two-site DMRG: host planner.
+//
+// The planner owns the quantum-number bookkeeping of Sec. II.B-C of the paper
+// (MPS over SU(2) multiplet sectors, D counted in multiplets) and turns every
+// step of a sweep into task lists for the device primitives of backend.hpp:
+//   * blocking   (block (x) site -> enlarged block operators):   place tasks
+//   * H_eff psi  (sigma = sum_t c_t O^L_t psi O^R_t^T):          grouped GEMMs
+//   * decimation (rho = psi psi^T per sector, eigh, selection):  GEMM + eigh
+//   * renormalisation (O' = U^T O U):                            grouped GEMMs
+// The SU(2) recoupling coefficients (6j/9j) are folded into the task lists on
+// the host; the device only sees scaled dense sector blocks.
+//
+// Operators carried by a block of sites (normal/complementary scheme of ab
+// initio DMRG, with the pair operators on the side with fewer sites):
+//   H            block Hamiltonian
+//   C_p          a+_p spinor (rank 1/2), p in block
+//   S_p          complementary three-index spinor, p outside the block
+//   A^k_pq, B^k_pq   normal pair operators [a+a+]^k, [a+a~]^k, p<=q in block
+//   P^k_pq, QJ_pq, QK^k_pq   complementary pair operators, p<=q outside
+#pragma once
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "backend.hpp"
+#include "su2.hpp"
+
+namespace dmrg {
+
+struct Sector {
+  int n, j, dim, off;
+};
+
+struct Basis {
+  std::vector<Sector> sec;
+  int total = 0;
+  int find(int n, int j) const {
+    for (size_t i = 0; i < sec.size(); ++i)
+      if (sec[i].n == n && sec[i].j == j) return (int)i;
+    return -1;
+  }
+};
+
+// Component of an enlarged basis: block sector bsec coupled with site
+// multiplet `site` sits in enlarged sector esec at multiplet offset eoff.
+struct EnlComp {
+  int bsec, site, esec, eoff;
+};
+
+struct Layout {
+  int dn = 0, k2 = 0;
+  struct Blk {
+    int bra, ket, rows, cols;
+    size_t off;
+  };
+  std::vector<Blk> blk;
+  size_t size = 0;
+  int nket = 0;
+  std::vector<int> lut;  // bra * nket + ket -> block index (or -1)
+  int find(int bra, int ket) const { return lut[(size_t)bra * nket + ket]; }
+};
+
+enum Kind { K_H = 0, K_C, K_S, K_A, K_B, K_P, K_QJ, K_QK };
+
+struct OpKey {
+  int kind, i, j, k2;
+  bool operator<(const OpKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (i != o.i) return i < o.i;
+    if (j != o.j) return j < o.j;
+    return k2 < o.k2;
+  }
+};
+
+inline int kind_dn(int kind) {
+  switch (kind) {
+    case K_C: return 1;
+    case K_S: return -1;
+    case K_A: return 2;
+    case K_P: return -2;
+    default: return 0;
+  }
+}
+inline int kind_parity(int kind) { return (kind == K_C || kind == K_S) ? 1 : 0; }
+
+// A set of operators on one basis, with one device allocation per layout.
+struct OpSet {
+  Basis basis;
+  std::map<std::pair<int, int>, Layout> layouts;   // (dn, k2)
+  std::map<OpKey, double*> ops;
+  std::vector<void*> mem;
+  Backend* be = nullptr;
+  ~OpSet();
+  const Layout& layout(int dn, int k2);
+  double* get(const OpKey& k) const {
+    auto it = ops.find(k);
+    return it == ops.end() ? nullptr : it->second;
+  }
+  // allocate (zeroed) storage for the given keys
+  void allocate(const std::vector<OpKey>& keys);
+  size_t bytes() const;
+};
+
+struct Block {
+  bool left = true;
+  int nsites = 0;      // left: sites 0..nsites-1; right: sites n-nsites..n-1
+  bool normal = true;  // pair operators normal (own pairs) or complementary
+  std::unique_ptr<OpSet> ops;
+  // enlarged-block bookkeeping (set when the block was made by blocking)
+  std::vector<EnlComp> comps;
+  const Basis* parent = nullptr;
+};
+
+struct Options {
+  int D = 64;
+  int max_davidson_iter = 200;
+  double davidson_tol = 1e-10;
+  Precision prec = Precision::FP64;
+  int max_space = 24;
+  int verbose = 0;
+};
+
+struct SweepStats {
+  double energy = 0.0;
+  double max_trunc = 0.0;
+  int davidson_iters = 0;
+  double hpsi_flops = 0.0;
+  double hpsi_seconds = 0.0;
+  int hpsi_calls = 0;
+};
+
+class Engine {
+ public:
+  Engine(Backend* be, int n, const double* h, const double* eri, double e_core, int n_elec,
+         int two_s, const Options& opt, const int* occ, const int* two_s_right);
+  ~Engine();
+
+  // One full sweep (L->R then R->L).  Returns the Davidson energy of the last
+  // bond (including e_core).
+  SweepStats sweep();
+  double energy() const { return energy_; }
+  int n() const { return n_; }
+  void set_D(int D) { opt_.D = D; }
+  void set_precision(Precision p) { opt_.prec = p; }
+  const std::vector<double>& bond_energies() const { return bond_e_; }
+  // Multiplet count of the left block L(m) / right block R(m) (sites counted)
+  int left_dim(int m) const;
+  int right_dim(int m) const;
+  // Two-site wavefunction at the last optimised bond (for RDMs / checks)
+  int last_bond() const { return last_bond_; }
+
+  Backend* backend() const { return be_; }
+
+ private:
+  friend struct EngineAccess;
+  Backend* be_;
+  int n_, n_elec_, two_s_;
+  double e_core_;
+  Options opt_;
+  std::vector<double> h_, g_;  // h_pq and g_pqrs = (ps|qr)
+  std::vector<std::unique_ptr<Block>> L_, R_;  // L_[m]: sites 0..m-1, R_[m]: last m sites
+  int tL_, tR_;
+  double energy_ = 0.0;
+  std::vector<double> bond_e_;
+  int last_bond_ = -1;
+  std::vector<int> occ_, path_;
+
+  double hh(int p, int q) const { return h_[(size_t)p * n_ + q]; }
+  double g(int p, int q, int r, int s) const {
+    return g_[(((size_t)p * n_ + q) * n_ + r) * n_ + s];
+  }
+  bool left_normal(int m) const { return m < tL_; }
+  bool right_normal(int m) const { return m < tR_; }
+
+  SweepStats stats_;
+  std::unique_ptr<Block> vacuum(bool left);
+  std::unique_ptr<Block> enlarge(const Block& b, int site);
+  void place_terms(const Block& b, const OpSet* tmp, Block& e,
+                   const std::vector<std::pair<OpKey, struct Term>>& terms);
+  void build_comp_from_normal(const Block& b, OpSet& dst, const std::vector<OpKey>& keys);
+  std::unique_ptr<Block> renormalize(Block& enl, const std::vector<int>& kept,
+                                     const std::vector<double*>& ut, bool switch_to_comp);
+  void build_initial_right();
+  void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
+  void apply_hpsi(struct HPsiPlan& plan);
+  double davidson(struct HPsiPlan& plan, double* psi, int* iters);
+  double decimate(Block& enl, const struct HPsiPlan& plan, const double* psi, bool left,
+                  std::vector<int>& kept, std::vector<double*>& ut, void** storage);
+  double optimize_bond(int i, bool left_to_right, double* trunc);
+
+ public:
+  // ---- accounting
+  double sweep_seconds = 0.0;
+};
+
+std::string last_error();
+void set_last_error(const std::string& e);
+
+}  // namespace dmrg
