@@ -121,11 +121,78 @@ dmrg_status dmrg_bond_energies(const dmrg_ctx* ctx, double* out, int cap, int* c
 /* Multiplet counts of the left blocks L(m), m = 0..n (-1 where not held). */
 dmrg_status dmrg_block_dims(const dmrg_ctx* ctx, int* left, int* right);
 
+/* Turn per-launch CUDA-event timing of the GEMM kernels on (1) or off (0);
+ * turning it on resets the counters. */
+dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
+
+/* Device time (ms), algorithmic FLOPs and launch count of the GEMM kernels
+ * since profiling was turned on.  which = 1: the H_eff psi launches,
+ * which = 0: all other GEMM launches (renormalisation, complementary
+ * operators, density matrices). */
+dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
+                              int64_t* launches);
+
+/* Device time of the last sweep in milliseconds, measured with CUDA events
+ * recorded on the library's stream at the start and the end of the sweep. */
+dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* ctx, double* ms);
+
+/* Device memory held by the context now and at its high-water mark (bytes). */
+dmrg_status dmrg_memory(const dmrg_ctx* ctx, int64_t* in_use, int64_t* peak);
+
+/* Number of device kernel launches issued by the context so far. */
+dmrg_status dmrg_launch_count(const dmrg_ctx* ctx, int64_t* launches);
+
 /* Release every resource of the context (NULL is accepted). */
 void dmrg_free(dmrg_ctx* ctx);
 
 /* Message of the last error of ctx, or of the calling thread if ctx is NULL. */
 const char* dmrg_last_error(const dmrg_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points (host buffers in, host buffers out).  They run
+ * one launch of the device primitives the sweep is made of, so the kernels
+ * can be checked element by element against a plain CPU evaluation.
+ * ---------------------------------------------------------------------- */
+
+/* One segment of a grouped GEMM: C_g += alpha * op(A) * op(B), where op(A) is
+ * m x k (trans_a: A stored k x m) and op(B) is k x n (trans_b: B stored n x k).
+ * Offsets are element offsets into the A / B host arrays; lda/ldb are the
+ * row lengths of the stored matrices. */
+typedef struct {
+  int64_t a_off, b_off;
+  int k, lda, ldb, trans_a, trans_b;
+  double alpha;
+} dmrg_gemm_seg;
+
+/* Output block g: rows m, cols n at element offset c_off of C with row length
+ * ldc; its segments are seg[seg_begin .. seg_begin + seg_count). */
+typedef struct {
+  int64_t c_off;
+  int m, n, ldc, seg_begin, seg_count;
+} dmrg_gemm_group;
+
+/*
+ * dmrg_grouped_gemm -- the segment-sum GEMM used by H_eff psi (the contraction
+ * sigma = sum_t c_t A_t psi B_t^T of Sec. II.B, one output sector block per
+ * group), by renormalisation and by the complementary-operator contractions.
+ * C (c_len doubles) is read and updated in place; A and B are read only.
+ * Output blocks must not overlap.  precision: DMRG_FP64 or DMRG_SPLIT_TF32.
+ * Returns DMRG_EINVAL for out-of-range offsets, DMRG_ECUDA without a device.
+ */
+dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, int64_t b_len,
+                              double* C, int64_t c_len, const dmrg_gemm_group* groups,
+                              int n_groups, const dmrg_gemm_seg* segs, int n_segs, int precision,
+                              int device);
+
+/*
+ * dmrg_eigh_batched -- symmetric eigendecompositions in float64 on the device
+ * (the sector density matrices of the decimation step, Sec. II.C).  mats holds
+ * the row-major matrices back to back (sizes n[i]); w receives eigenvalues in
+ * descending order and vecs the eigenvectors as rows (same packing as mats).
+ * Largest-magnitude component of every eigenvector is made positive.
+ */
+dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, double* w, double* vecs,
+                              int device);
 
 #ifdef __cplusplus
 }

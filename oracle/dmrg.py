@@ -152,6 +152,9 @@ class OracleDMRG:
         self.psi_full = full0.vecs[self.states, k].copy()
         self.energy = None
         self.record = SweepRecord()
+        self.heff_flops = 0.0     # executed flops of the H_eff applications
+        self.heff_seconds = 0.0
+        self.heff_calls = 0
 
     # ----- embedding of the two-site subspace -----
     def _blocks(self, i):
@@ -202,8 +205,24 @@ class OracleDMRG:
         def proj(v):
             return self._project(L, R, v, self.states)[mask]
 
+        n = self.n
+        la, lb = L.vecs.shape[0], R.vecs.shape[0]
+        ml, mr = L.vecs.shape[1], R.vecs.shape[1]
+        # floating-point operations one application executes (embedding and
+        # projection contractions, the E_pq maps and the integral contraction)
+        nmap = sum(m.src_pos.size for p in range(n) for q in range(n)
+                   for m in self.H.ops.e_maps(p, q))
+        fl = (2 * (2.0 * la * ml * 16 * mr + 2.0 * la * 16 * mr * lb)
+              + 2 * 2.0 * nmap + 2.0 * n ** 4 * self.H.dim)
+
         def apply(X):
-            return np.stack([proj(self.H.apply(embed(X[:, k]))) for k in range(X.shape[1])], 1)
+            import time as _t
+            t0 = _t.perf_counter()
+            out = np.stack([proj(self.H.apply(embed(X[:, k]))) for k in range(X.shape[1])], 1)
+            self.heff_seconds += _t.perf_counter() - t0
+            self.heff_flops += fl * X.shape[1]
+            self.heff_calls += X.shape[1]
+            return out
 
         def spin_project(v):
             v = v.reshape(-1, 1) if v.ndim == 1 else v

@@ -74,6 +74,16 @@ def load(path=None):
     lib.dmrg_bond_energies.restype = I
     lib.dmrg_block_dims.argtypes = [P, ip, ip]
     lib.dmrg_block_dims.restype = I
+    lib.dmrg_profile.argtypes = [P, I]
+    lib.dmrg_profile.restype = I
+    lib.dmrg_kernel_stats.argtypes = [P, I, dp, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dmrg_kernel_stats.restype = I
+    lib.dmrg_last_sweep_device_ms.argtypes = [P, dp]
+    lib.dmrg_last_sweep_device_ms.restype = I
+    lib.dmrg_memory.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.dmrg_memory.restype = I
+    lib.dmrg_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.dmrg_launch_count.restype = I
     lib.dmrg_free.argtypes = [P]
     lib.dmrg_free.restype = None
     lib.dmrg_last_error.argtypes = [P]
@@ -167,6 +177,32 @@ class DMRG:
         right = np.zeros(self.n + 1, dtype=np.int32)
         _check(self._lib, self._ctx, self._lib.dmrg_block_dims(self._ctx, _ip(left), _ip(right)))
         return left, right
+
+    def profile(self, on=True):
+        _check(self._lib, self._ctx, self._lib.dmrg_profile(self._ctx, 1 if on else 0))
+
+    def kernel_stats(self, which=1):
+        """(device ms, algorithmic flops, launches) of the GEMM kernels."""
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib, self._ctx, self._lib.dmrg_kernel_stats(
+            self._ctx, which, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+        return ms.value, fl.value, n.value
+
+    def sweep_device_ms(self):
+        ms = ctypes.c_double()
+        _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_device_ms(self._ctx, ctypes.byref(ms)))
+        return ms.value
+
+    def memory(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib, self._ctx, self._lib.dmrg_memory(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(self._lib, self._ctx, self._lib.dmrg_launch_count(self._ctx, ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "_ctx", None):

@@ -84,6 +84,19 @@ class Backend {
   // Counters (for the FLOP/byte accounting of the benchmark).
   double gemm_flops = 0.0;   // algorithmic 2*m*n*k summed over segments
   double place_bytes = 0.0;
+  // Kernel timing with CUDA events on the launching stream.  While profiling
+  // is on, every gemm launch is bracketed by two events and accounted under
+  // the current tag (0: other GEMMs, 1: H_eff psi).
+  int tag = 0;
+  long launches = 0;     // kernel launches issued by this backend
+  size_t peak_bytes = 0; // high-water mark of bytes_in_use()
+  // Device-side interval on the backend stream (CUDA events): mark_begin()
+  // then mark_end() returns the elapsed milliseconds.
+  virtual void mark_begin() = 0;
+  virtual double mark_end() = 0;
+  virtual void set_profile(bool on) = 0;
+  // total device time (ms), algorithmic flops and launches of one tag
+  virtual void kernel_stats(int tag, double* ms, double* flops, long* launches) = 0;
 };
 
 Backend* make_cuda_backend(int device, std::string* err);

@@ -1,0 +1,654 @@
+// CUDA implementation of the device primitives (backend.hpp) for sm_103a.
+//
+// Kernels:
+//   place_kernel        C += sum_s alpha_s op(S_s)            (HBM-bound block copies)
+//   gemm_f64_kernel     C += sum_s alpha_s op(A_s) op(B_s)    (FP64 reference path, DFMA)
+//   gemm_tf32x3 (gemm_split.cu)                                (split-FP32 tensor-core path)
+//   dots/combine/axpby  Davidson vector algebra (FP64, deterministic two-stage reductions)
+//   jacobi_kernel       parallel cyclic Jacobi eigensolver, one CTA per matrix (FP64)
+// All kernels are bounded loops over their inputs; none waits on another CTA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "backend.hpp"
+#include "gemm_split.cuh"
+
+namespace dmrg {
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess)                                                             \
+      throw std::runtime_error(std::string("cuda: ") + #x + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ place
+struct PlaceTile {
+  int group, r0, c0, pad;
+};
+
+__global__ void place_kernel(const PlaceGroup* __restrict__ groups, const PlaceSeg* __restrict__ segs,
+                             const PlaceTile* __restrict__ tiles) {
+  const PlaceTile t = tiles[blockIdx.x];
+  const PlaceGroup g = groups[t.group];
+  // 32 x 32 tile, 256 threads: 4 rows per thread
+  const int c = t.c0 + (threadIdx.x & 31);
+  const int rb = t.r0 + (threadIdx.x >> 5);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (c < g.cols) {
+    for (int s = g.seg_begin; s < g.seg_begin + g.seg_count; ++s) {
+      const PlaceSeg sg = segs[s];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int r = rb + 8 * i;
+        if (r >= g.rows) break;
+        double v;
+        if (sg.src == nullptr) v = (r == c) ? 1.0 : 0.0;
+        else v = sg.trans ? sg.src[(size_t)c * sg.ld + r] : sg.src[(size_t)r * sg.ld + c];
+        acc[i] += sg.alpha * v;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r = rb + 8 * i;
+      if (r >= g.rows) break;
+      g.dst[(size_t)r * g.ld + c] += acc[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP64 GEMM
+struct GemmTile {
+  int group, r0, c0, pad;
+};
+
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmGroup* __restrict__ groups,
+                                                       const GemmSeg* __restrict__ segs,
+                                                       const GemmTile* __restrict__ tiles) {
+  __shared__ double As[kTK][kTM + 1];
+  __shared__ double Bs[kTK][kTN + 1];
+  const GemmTile t = tiles[blockIdx.x];
+  const GemmGroup g = groups[t.group];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int s = g.seg_begin; s < g.seg_begin + g.seg_count; ++s) {
+    const GemmSeg sg = segs[s];
+    for (int k0 = 0; k0 < sg.k; k0 += kTK) {
+      // A tile (kTM x kTK) -> As[kk][i], scaled by alpha
+      for (int e = threadIdx.x; e < kTM * kTK; e += 256) {
+        int i, kk;
+        if (!sg.transA) { i = e / kTK; kk = e % kTK; }
+        else { kk = e / kTM; i = e % kTM; }
+        int gi = t.r0 + i, gk = k0 + kk;
+        double v = 0.0;
+        if (gi < g.m && gk < sg.k)
+          v = sg.transA ? sg.A[(size_t)gk * sg.lda + gi] : sg.A[(size_t)gi * sg.lda + gk];
+        As[kk][i] = sg.alpha * v;
+      }
+      for (int e = threadIdx.x; e < kTN * kTK; e += 256) {
+        int j, kk;
+        if (!sg.transB) { kk = e / kTN; j = e % kTN; }
+        else { j = e / kTK; kk = e % kTK; }
+        int gj = t.c0 + j, gk = k0 + kk;
+        double v = 0.0;
+        if (gj < g.n && gk < sg.k)
+          v = sg.transB ? sg.B[(size_t)gj * sg.ldb + gk] : sg.B[(size_t)gk * sg.ldb + gj];
+        Bs[kk][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kTK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gi = t.r0 + ty + 16 * i;
+    if (gi >= g.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gj = t.c0 + tx + 16 * j;
+      if (gj < g.n) g.C[(size_t)gi * g.ldc + gj] += acc[i][j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ vectors
+constexpr int kRedBlocks = 152;  // one partial per SM for the reductions
+
+__global__ void dots_partial(const double* __restrict__ V, int m, size_t len, size_t ld,
+                             const double* __restrict__ x, double* __restrict__ part) {
+  // blockIdx.y = vector index, blockIdx.x = chunk
+  __shared__ double sh[256];
+  const int i = blockIdx.y;
+  double s = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+       t += (size_t)gridDim.x * blockDim.x)
+    s = fma(V[(size_t)i * ld + t], x[t], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void dots_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += part[(size_t)blockIdx.x * nparts + t];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+__global__ void combine_kernel(double* __restrict__ y, double beta, const double* __restrict__ V,
+                               int m, size_t len, size_t ld, const double* __restrict__ c) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+       t += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s = fma(c[i], V[(size_t)i * ld + t], s);
+    y[t] = (beta == 0.0) ? s : fma(beta, y[t], s);
+  }
+}
+
+__global__ void axpby_kernel(double* __restrict__ y, double a, const double* __restrict__ x, double b,
+                             size_t len) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+       t += (size_t)gridDim.x * blockDim.x)
+    y[t] = (a == 0.0) ? b * x[t] : fma(a, y[t], b * x[t]);
+}
+
+__global__ void precond_kernel(double* __restrict__ y, const double* __restrict__ x,
+                               const double* __restrict__ d, double e, size_t len) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+       t += (size_t)gridDim.x * blockDim.x) {
+    double den = d[t] - e;
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    y[t] = x[t] / den;
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Parallel cyclic Jacobi (round-robin pairing) on a symmetric n x n matrix
+// held in global memory (destroyed).  Eigenvalues descending in w, the
+// eigenvectors as rows of V.  Bounded: at most kMaxSweeps sweeps.
+constexpr int kMaxSweeps = 40;
+
+__global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict__ tasks, double* __restrict__ work) {
+  const EighTask tk = tasks[blockIdx.x];
+  const int n = tk.n;
+  double* a = const_cast<double*>(tk.A);
+  double* W = work + (size_t)blockIdx.x * 0;  // unused
+  (void)W;
+  double* v = tk.V;  // V[k*n + j]: column j = eigenvector j during the iteration
+  extern __shared__ double sm[];
+  const int np = (n + 1) & ~1;  // even count, with a dummy index when n is odd
+  double* cs = sm;              // np/2 cosines
+  double* sn = sm + np / 2;     // np/2 sines
+  int* pp = (int*)(sm + np);    // pairs
+  int* qq = pp + np / 2;
+  int* perm = qq + np / 2;      // round-robin order (np entries)
+  __shared__ double red[256];
+  __shared__ int done;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) v[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  // Frobenius norm for the stopping rule
+  double fro = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) fro += a[e] * a[e];
+  red[threadIdx.x] = fro;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double fro2 = red[0];
+  __syncthreads();
+  for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
+    double off = 0.0;
+    for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+      int r = (int)(e / n), c = (int)(e % n);
+      if (r != c) off += a[e] * a[e];
+    }
+    red[threadIdx.x] = off;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) done = (red[0] <= 1e-30 * fro2 || red[0] < 1e-300);
+    __syncthreads();
+    if (done) break;
+    for (int round = 0; round < np - 1; ++round) {
+      // pairs of this round: perm[i] with perm[np-1-i]
+      for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
+        int p = perm[i], q = perm[np - 1 - i];
+        if (p > q) { int t = p; p = q; q = t; }
+        pp[i] = p;
+        qq[i] = q;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = a[(size_t)p * n + q];
+          if (apq != 0.0) {
+            double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+            double theta = (aqq - app) / (2.0 * apq);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (size_t e = threadIdx.x; e < (size_t)(np / 2) * n; e += blockDim.x) {
+        int i = (int)(e / n), k = (int)(e % n);
+        int p = pp[i], q = qq[i];
+        if (q >= n || sn[i] == 0.0) continue;
+        double c = cs[i], s = sn[i];
+        double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+        a[(size_t)p * n + k] = c * apk - s * aqk;
+        a[(size_t)q * n + k] = s * apk + c * aqk;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (size_t e = threadIdx.x; e < (size_t)(np / 2) * n; e += blockDim.x) {
+        int i = (int)(e / n), k = (int)(e % n);
+        int p = pp[i], q = qq[i];
+        if (q >= n || sn[i] == 0.0) continue;
+        double c = cs[i], s = sn[i];
+        double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+        a[(size_t)k * n + p] = c * akp - s * akq;
+        a[(size_t)k * n + q] = s * akp + c * akq;
+        double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+        v[(size_t)k * n + p] = c * vkp - s * vkq;
+        v[(size_t)k * n + q] = s * vkp + c * vkq;
+      }
+      __syncthreads();
+      // rotate the round-robin order (perm[0] fixed)
+      if (threadIdx.x == 0) {
+        int last = perm[np - 1];
+        for (int i = np - 1; i > 1; --i) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues descending (selection, one thread) and write rows of V
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = 0; i < n; ++i) {
+      int best = i;
+      for (int j = i + 1; j < n; ++j)
+        if (a[(size_t)perm[j] * n + perm[j]] > a[(size_t)perm[best] * n + perm[best]]) best = j;
+      int t = perm[i]; perm[i] = perm[best]; perm[best] = t;
+    }
+    for (int i = 0; i < n; ++i) tk.w[i] = a[(size_t)perm[i] * n + perm[i]];
+  }
+  __syncthreads();
+  // transpose columns of v into rows of the output (in place via the a buffer)
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) a[e] = v[e];
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+    int r = (int)(e / n), k = (int)(e % n);
+    v[e] = a[(size_t)k * n + perm[r]];
+  }
+  __syncthreads();
+  // sign convention: largest-magnitude component of each eigenvector positive
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double best = 0.0;
+    int bi = 0;
+    for (int k = 0; k < n; ++k) {
+      double x = fabs(v[(size_t)r * n + k]);
+      if (x > best + 1e-12) { best = x; bi = k; }
+    }
+    if (v[(size_t)r * n + bi] < 0)
+      for (int k = 0; k < n; ++k) v[(size_t)r * n + k] = -v[(size_t)r * n + k];
+  }
+}
+
+// ------------------------------------------------------------------ backend
+class CudaBackend : public Backend {
+ public:
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  size_t used = 0;
+  std::vector<std::pair<void*, size_t>> live;
+  // staging for task lists
+  void* dtask = nullptr;
+  size_t dtask_cap = 0;
+  void* htask = nullptr;
+  size_t htask_cap = 0;
+  double* part = nullptr;
+  size_t part_cap = 0;
+  // profiling
+  bool profiling = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    double flops;
+    int tag;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double acc_ms[2] = {0, 0}, acc_flops[2] = {0, 0};
+  long acc_launch[2] = {0, 0};
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  void drain() {
+    for (auto& r : recs) {
+      CK(cudaEventSynchronize(r.b));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      int t = r.tag ? 1 : 0;
+      acc_ms[t] += ms;
+      acc_flops[t] += r.flops;
+      acc_launch[t] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  cudaEvent_t mb_ = nullptr, me_ = nullptr;
+  void mark_begin() override {
+    if (!mb_) { CK(cudaEventCreate(&mb_)); CK(cudaEventCreate(&me_)); }
+    CK(cudaEventRecord(mb_, st));
+  }
+  double mark_end() override {
+    CK(cudaEventRecord(me_, st));
+    CK(cudaEventSynchronize(me_));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, mb_, me_));
+    return ms;
+  }
+  void set_profile(bool on) override {
+    drain();
+    profiling = on;
+    for (int t = 0; t < 2; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
+  }
+  void kernel_stats(int t, double* ms, double* flops, long* launches) override {
+    drain();
+    t = t ? 1 : 0;
+    if (ms) *ms = acc_ms[t];
+    if (flops) *flops = acc_flops[t];
+    if (launches) *launches = acc_launch[t];
+  }
+
+  explicit CudaBackend(int device) : dev(device) {
+    CK(cudaSetDevice(dev));
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaMemPool_t pool;
+    CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  ~CudaBackend() override {
+    cudaStreamSynchronize(st);
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+    if (dtask) cudaFreeAsync(dtask, st);
+    if (part) cudaFreeAsync(part, st);
+    if (htask) cudaFreeHost(htask);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  std::string name() const override { return "cuda"; }
+  void* alloc(size_t b) override {
+    void* p = nullptr;
+    if (b == 0) b = 8;
+    cudaError_t e = cudaMallocAsync(&p, b, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::runtime_error("out of device memory (" + std::to_string(b) + " bytes)");
+    }
+    used += b;
+    peak_bytes = std::max(peak_bytes, used);
+    live.push_back({p, b});
+    return p;
+  }
+  void free(void* p) override {
+    if (!p) return;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i].first == p) {
+        used -= live[i].second;
+        live[i] = live.back();
+        live.pop_back();
+        break;
+      }
+    CK(cudaFreeAsync(p, st));
+  }
+  size_t bytes_in_use() const override { return used; }
+  void memset0(void* p, size_t b) override { if (b) CK(cudaMemsetAsync(p, 0, b, st)); }
+  void copy_d2d(void* d, const void* s, size_t b) override {
+    if (b) CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToDevice, st));
+  }
+  void copy_h2d(void* d, const void* s, size_t b) override {
+    if (b) {
+      CK(cudaMemcpyAsync(d, s, b, cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  void copy_d2h(void* d, const void* s, size_t b) override {
+    if (b) {
+      CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  void sync() override { CK(cudaStreamSynchronize(st)); }
+
+  // upload a packed task buffer; returns the device base pointer
+  char* upload(const std::vector<std::pair<const void*, size_t>>& parts, std::vector<size_t>& offs) {
+    size_t tot = 0;
+    offs.clear();
+    for (auto& p : parts) {
+      offs.push_back(tot);
+      tot += (p.second + 255) & ~size_t(255);
+    }
+    if (tot > htask_cap) {
+      CK(cudaStreamSynchronize(st));
+      if (htask) CK(cudaFreeHost(htask));
+      htask_cap = std::max(tot, htask_cap * 2);
+      CK(cudaMallocHost(&htask, htask_cap));
+    }
+    if (tot > dtask_cap) {
+      if (dtask) CK(cudaFreeAsync(dtask, st));
+      dtask_cap = std::max(tot, dtask_cap * 2);
+      CK(cudaMallocAsync(&dtask, dtask_cap, st));
+    }
+    // the pinned staging buffer may still be in use by a previous copy
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < parts.size(); ++i)
+      std::memcpy((char*)htask + offs[i], parts[i].first, parts[i].second);
+    CK(cudaMemcpyAsync(dtask, htask, tot, cudaMemcpyHostToDevice, st));
+    return (char*)dtask;
+  }
+
+  void place(const std::vector<PlaceGroup>& groups, const std::vector<PlaceSeg>& segs) override {
+    std::vector<PlaceTile> tiles;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      auto& g = groups[gi];
+      for (int r = 0; r < g.rows; r += 32)
+        for (int c = 0; c < g.cols; c += 32) tiles.push_back({(int)gi, r, c, 0});
+      place_bytes += 16.0 * g.rows * g.cols * std::max(1, g.seg_count);
+    }
+    if (tiles.empty()) return;
+    std::vector<size_t> off;
+    char* d = upload({{groups.data(), groups.size() * sizeof(PlaceGroup)},
+                      {segs.data(), segs.size() * sizeof(PlaceSeg)},
+                      {tiles.data(), tiles.size() * sizeof(PlaceTile)}},
+                     off);
+    place_kernel<<<(unsigned)tiles.size(), 256, 0, st>>>((const PlaceGroup*)(d + off[0]),
+                                                          (const PlaceSeg*)(d + off[1]),
+                                                          (const PlaceTile*)(d + off[2]));
+    ++launches;
+    CK(cudaGetLastError());
+  }
+
+  void gemm(const std::vector<GemmGroup>& groups, const std::vector<GemmSeg>& segs,
+            Precision prec) override {
+    if (groups.empty()) return;
+    double fl = 0.0;
+    for (auto& g : groups)
+      for (int s = g.seg_begin; s < g.seg_begin + g.seg_count; ++s)
+        fl += 2.0 * g.m * g.n * segs[s].k;
+    gemm_flops += fl;
+    if (profiling) {
+      // upload first so the events bracket the kernel only
+      Rec r{ev(), ev(), fl, tag};
+      recs.push_back(r);
+      gemm_impl(groups, segs, prec, &recs.back());
+      if (recs.size() > 4096) drain();
+      return;
+    }
+    gemm_impl(groups, segs, prec, nullptr);
+  }
+
+  void gemm_impl(const std::vector<GemmGroup>& groups, const std::vector<GemmSeg>& segs,
+                 Precision prec, Rec* rec) {
+    if (prec != Precision::FP64) {
+      gemm_split_launch(groups, segs, prec, st,
+                        [&](const std::vector<std::pair<const void*, size_t>>& parts,
+                            std::vector<size_t>& offs) {
+                          char* d = upload(parts, offs);
+                          if (rec) CK(cudaEventRecord(rec->a, st));
+                          return d;
+                        });
+      ++launches;
+      if (rec) CK(cudaEventRecord(rec->b, st));
+      return;
+    }
+    std::vector<GemmTile> tiles;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      auto& g = groups[gi];
+      for (int r = 0; r < g.m; r += kTM)
+        for (int c = 0; c < g.n; c += kTN) tiles.push_back({(int)gi, r, c, 0});
+    }
+    std::vector<size_t> off;
+    char* d = upload({{groups.data(), groups.size() * sizeof(GemmGroup)},
+                      {segs.data(), segs.size() * sizeof(GemmSeg)},
+                      {tiles.data(), tiles.size() * sizeof(GemmTile)}},
+                     off);
+    if (rec) CK(cudaEventRecord(rec->a, st));
+    // grid.x is limited to 2^31-1; task lists stay far below
+    gemm_f64_kernel<<<(unsigned)tiles.size(), 256, 0, st>>>((const GemmGroup*)(d + off[0]),
+                                                             (const GemmSeg*)(d + off[1]),
+                                                             (const GemmTile*)(d + off[2]));
+    ++launches;
+    CK(cudaGetLastError());
+    if (rec) CK(cudaEventRecord(rec->b, st));
+  }
+
+  void ensure_part(size_t n) {
+    if (n <= part_cap) return;
+    if (part) CK(cudaFreeAsync(part, st));
+    part_cap = std::max(n, 2 * part_cap);
+    CK(cudaMallocAsync((void**)&part, part_cap * sizeof(double), st));
+  }
+  void dots(const double* V, int m, size_t len, size_t ld, const double* x, double* out) override {
+    if (m <= 0) return;
+    int nb = (int)std::min<size_t>(kRedBlocks, (len + 255) / 256);
+    if (nb < 1) nb = 1;
+    ensure_part((size_t)m * nb);
+    dots_partial<<<dim3(nb, m), 256, 0, st>>>(V, m, len, ld, x, part);
+    ++launches;
+    dots_final<<<m, 256, 0, st>>>(part, nb, out);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  void combine(double* y, double beta, const double* V, int m, size_t len, size_t ld,
+               const double* c) override {
+    int nb = (int)std::min<size_t>(152 * 8, (len + 255) / 256);
+    if (nb < 1) nb = 1;
+    combine_kernel<<<nb, 256, 0, st>>>(y, beta, V, m, len, ld, c);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  void axpby(double* y, double a, const double* x, double b, size_t len) override {
+    int nb = (int)std::min<size_t>(152 * 8, (len + 255) / 256);
+    if (nb < 1) nb = 1;
+    axpby_kernel<<<nb, 256, 0, st>>>(y, a, x, b, len);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  void precondition(double* y, const double* x, const double* d, double e, size_t len) override {
+    int nb = (int)std::min<size_t>(152 * 8, (len + 255) / 256);
+    if (nb < 1) nb = 1;
+    precond_kernel<<<nb, 256, 0, st>>>(y, x, d, e, len);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  void eigh(const std::vector<EighTask>& tasks) override {
+    if (tasks.empty()) return;
+    int nmax = 1;
+    for (auto& t : tasks) nmax = std::max(nmax, t.n);
+    int np = (nmax + 1) & ~1;
+    size_t smem = (size_t)np * sizeof(double) + (size_t)(np / 2) * 2 * sizeof(int) + (size_t)np * sizeof(int);
+    if (smem > 200 * 1024) throw std::runtime_error("internal: eigensolver matrix too large");
+    if (smem > 48 * 1024)
+      CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    std::vector<size_t> off;
+    char* d = upload({{tasks.data(), tasks.size() * sizeof(EighTask)}}, off);
+    jacobi_kernel<<<(unsigned)tasks.size(), 256, smem, st>>>((const EighTask*)(d + off[0]), nullptr);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+};
+
+Backend* make_cuda_backend(int device, std::string* err) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    if (err) *err = std::string("cuda: no usable device (") + cudaGetErrorString(e) + ")";
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (device < 0 || device >= count) {
+    if (err) *err = "cuda: device ordinal out of range";
+    return nullptr;
+  }
+  try {
+    return new CudaBackend(device);
+  } catch (const std::exception& ex) {
+    if (err) *err = ex.what();
+    return nullptr;
+  }
+}
+
+}  // namespace dmrg

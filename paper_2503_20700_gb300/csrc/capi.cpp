@@ -1,4 +1,5 @@
 // extern "C" entry points (include/dmrgscf.h).
+#include <algorithm>
 #include <cstring>
 #include <exception>
 #include <memory>
@@ -213,6 +214,48 @@ dmrg_status dmrg_block_dims(const dmrg_ctx* c, int* left, int* right) {
   return DMRG_OK;
 }
 
+dmrg_status dmrg_profile(dmrg_ctx* c, int on) {
+  if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
+  try {
+    c->be->set_profile(on != 0);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_kernel_stats(dmrg_ctx* c, int which, double* ms, double* flops, int64_t* launches) {
+  if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
+  try {
+    long l = 0;
+    c->be->kernel_stats(which, ms, flops, &l);
+    if (launches) *launches = l;
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* c, double* ms) {
+  if (!c || !c->eng || !ms) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
+  if (c->sweeps_done == 0) return fail(const_cast<dmrg_ctx*>(c), DMRG_ESTATE, "no sweep has run");
+  *ms = c->eng->sweep_device_ms;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_memory(const dmrg_ctx* c, int64_t* in_use, int64_t* peak) {
+  if (!c || !c->be) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid context");
+  if (in_use) *in_use = (int64_t)c->be->bytes_in_use();
+  if (peak) *peak = (int64_t)c->be->peak_bytes;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_launch_count(const dmrg_ctx* c, int64_t* n) {
+  if (!c || !c->be || !n) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
+  *n = c->be->launches;
+  return DMRG_OK;
+}
+
 void dmrg_free(dmrg_ctx* c) {
   if (!c) return;
   c->eng.reset();
@@ -223,6 +266,100 @@ void dmrg_free(dmrg_ctx* c) {
 const char* dmrg_last_error(const dmrg_ctx* c) {
   if (c) return c->err.c_str();
   return tl_err.c_str();
+}
+
+// ---------------------------------------------------------------- kernel level
+dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, int64_t b_len,
+                              double* C, int64_t c_len, const dmrg_gemm_group* groups,
+                              int n_groups, const dmrg_gemm_seg* segs, int n_segs, int precision,
+                              int device) {
+  if (!A || !B || !C || (!groups && n_groups) || (!segs && n_segs) || n_groups < 0 || n_segs < 0)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  if (precision < 0 || precision > 1) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
+  // validate every access range on the host before any launch
+  for (int g = 0; g < n_groups; ++g) {
+    const auto& G = groups[g];
+    if (G.m < 0 || G.n < 0 || G.ldc < G.n || G.seg_begin < 0 || G.seg_count < 0 ||
+        G.seg_begin + G.seg_count > n_segs || G.c_off < 0)
+      return fail(nullptr, DMRG_EINVAL, "bad group");
+    if (G.m > 0 && G.n > 0 && G.c_off + (int64_t)(G.m - 1) * G.ldc + G.n > c_len)
+      return fail(nullptr, DMRG_EINVAL, "C block out of range");
+    for (int s = G.seg_begin; s < G.seg_begin + G.seg_count; ++s) {
+      const auto& S = segs[s];
+      if (S.k < 0) return fail(nullptr, DMRG_EINVAL, "bad k");
+      int64_t ar = S.trans_a ? S.k : G.m, ac = S.trans_a ? G.m : S.k;
+      int64_t br = S.trans_b ? G.n : S.k, bc = S.trans_b ? S.k : G.n;
+      if (ar > 0 && ac > 0 && (S.lda < ac || S.a_off < 0 || S.a_off + (ar - 1) * S.lda + ac > a_len))
+        return fail(nullptr, DMRG_EINVAL, "A block out of range");
+      if (br > 0 && bc > 0 && (S.ldb < bc || S.b_off < 0 || S.b_off + (br - 1) * S.ldb + bc > b_len))
+        return fail(nullptr, DMRG_EINVAL, "B block out of range");
+    }
+  }
+  std::string err;
+  std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  try {
+    double* dA = (double*)be->alloc(std::max<int64_t>(a_len, 1) * sizeof(double));
+    double* dB = (double*)be->alloc(std::max<int64_t>(b_len, 1) * sizeof(double));
+    double* dC = (double*)be->alloc(std::max<int64_t>(c_len, 1) * sizeof(double));
+    be->copy_h2d(dA, A, a_len * sizeof(double));
+    be->copy_h2d(dB, B, b_len * sizeof(double));
+    be->copy_h2d(dC, C, c_len * sizeof(double));
+    std::vector<dmrg::GemmGroup> gg(n_groups);
+    std::vector<dmrg::GemmSeg> ss(n_segs);
+    for (int g = 0; g < n_groups; ++g)
+      gg[g] = {dC + groups[g].c_off, groups[g].m, groups[g].n, groups[g].ldc, groups[g].seg_begin,
+               groups[g].seg_count};
+    for (int s = 0; s < n_segs; ++s)
+      ss[s] = {dA + segs[s].a_off, dB + segs[s].b_off, segs[s].k, segs[s].lda, segs[s].ldb,
+               segs[s].trans_a, segs[s].trans_b, segs[s].alpha};
+    be->gemm(gg, ss, (dmrg::Precision)precision);
+    be->copy_d2h(C, dC, c_len * sizeof(double));
+    be->free(dA);
+    be->free(dB);
+    be->free(dC);
+    be->sync();
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, double* w, double* vecs,
+                              int device) {
+  if (!mats || !n || !w || !vecs || count < 0) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  size_t tot = 0, wt = 0;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > 4096) return fail(nullptr, DMRG_EINVAL, "matrix size out of range");
+    tot += (size_t)n[i] * n[i];
+    wt += n[i];
+  }
+  std::string err;
+  std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  try {
+    double* dA = (double*)be->alloc(std::max<size_t>(tot, 1) * sizeof(double));
+    double* dV = (double*)be->alloc(std::max<size_t>(tot, 1) * sizeof(double));
+    double* dw = (double*)be->alloc(std::max<size_t>(wt, 1) * sizeof(double));
+    be->copy_h2d(dA, mats, tot * sizeof(double));
+    std::vector<dmrg::EighTask> t;
+    size_t o = 0, ow = 0;
+    for (int i = 0; i < count; ++i) {
+      t.push_back({dA + o, dw + ow, dV + o, n[i]});
+      o += (size_t)n[i] * n[i];
+      ow += n[i];
+    }
+    be->eigh(t);
+    be->copy_d2h(w, dw, wt * sizeof(double));
+    be->copy_d2h(vecs, dV, tot * sizeof(double));
+    be->free(dA);
+    be->free(dV);
+    be->free(dw);
+    be->sync();
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
+  }
+  return DMRG_OK;
 }
 
 }  // extern "C"

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
@@ -1004,14 +1005,21 @@ std::vector<std::pair<int, SrcBlock>> reach(OpSet& set, const Operand& x, int ke
 }
 }  // namespace
 
+// H_eff psi as batches of (phase 1: X = c x psi, phase 2: sigma += X y^T)
+// grouped GEMMs; the batches bound the memory of the X intermediates.
+struct HPsiBatch {
+  std::vector<GemmGroup> g1, g2;
+  std::vector<GemmSeg> s1, s2;
+  std::vector<size_t> x1off;  // X offset of every phase-1 output
+  size_t xsize = 0;
+};
 struct HPsiPlan {
   PsiLayout psi;
   double* in = nullptr;   // psi input buffer
   double* out = nullptr;  // sigma output buffer
-  double* X = nullptr;    // phase-1 intermediates
+  double* X = nullptr;    // phase-1 intermediates (largest batch)
   size_t xsize = 0;
-  std::vector<GemmGroup> g1, g2;
-  std::vector<GemmSeg> s1, s2;
+  std::vector<HPsiBatch> batches;
   double flops = 0.0;
 };
 
@@ -1089,38 +1097,84 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
         }
     }
   }
-  plan.xsize = xoff;
+  // split into batches so that the X intermediates stay within a budget
+  const size_t budget = x_budget_elems();
+  const size_t kNoX = (size_t)-1;
+  plan.batches.clear();
+  std::vector<std::vector<size_t>> xrel_of_batch;  // per batch: X offset of each s2 entry or kNoX
+  size_t maxx = 0;
+  size_t si = 0;
+  bool first = true;
+  while (first || si < slots.size()) {
+    HPsiBatch b;
+    std::map<double*, std::vector<std::pair<GemmSeg, size_t>>> bp2;
+    if (first) {
+      for (auto& [sig, segs] : p2)
+        for (auto& sg : segs) bp2[sig].push_back({sg, kNoX});
+      first = false;
+    }
+    size_t xo = 0;
+    std::vector<size_t> g1off;
+    while (si < slots.size()) {
+      auto& sl = slots[si];
+      size_t sz = (size_t)sl.m * sl.n;
+      if (xo > 0 && xo + sz > budget) break;
+      g1off.push_back(xo);
+      b.g1.push_back({nullptr, sl.m, sl.n, sl.n, (int)b.s1.size(), 1});
+      b.s1.push_back({sl.A, sl.B, sl.k, sl.lda, sl.ldb, sl.transA, 0, sl.alpha});
+      bp2[p2x[si].second.first].push_back({p2x[si].second.second, xo});
+      xo += sz;
+      ++si;
+    }
+    b.xsize = xo;
+    maxx = std::max(maxx, xo);
+    std::vector<size_t> xr;
+    for (auto& [sig, segs] : bp2) {
+      auto d = p2dim[sig];
+      b.g2.push_back({sig, d[0], d[1], d[2], (int)b.s2.size(), (int)segs.size()});
+      for (auto& [sg, off] : segs) {
+        b.s2.push_back(sg);
+        xr.push_back(off);
+      }
+    }
+    xrel_of_batch.push_back(std::move(xr));
+    // remember phase-1 offsets in the (unused) pad of the group via a side table
+    b.x1off = std::move(g1off);
+    plan.batches.push_back(std::move(b));
+  }
   if (plan.X) be_->free(plan.X);
-  plan.X = xoff ? (double*)be_->alloc(xoff * sizeof(double)) : nullptr;
-  size_t off = 0;
-  plan.g1.clear();
-  plan.s1.clear();
-  for (auto& sl : slots) {
-    plan.g1.push_back({plan.X + off, sl.m, sl.n, sl.n, (int)plan.s1.size(), 1});
-    plan.s1.push_back({sl.A, sl.B, sl.k, sl.lda, sl.ldb, sl.transA, 0, sl.alpha});
-    off += (size_t)sl.m * sl.n;
+  plan.xsize = maxx;
+  plan.X = maxx ? (double*)be_->alloc(maxx * sizeof(double)) : nullptr;
+  for (size_t bi = 0; bi < plan.batches.size(); ++bi) {
+    auto& b = plan.batches[bi];
+    for (size_t q = 0; q < b.g1.size(); ++q) b.g1[q].C = plan.X + b.x1off[q];
+    for (size_t q = 0; q < b.s2.size(); ++q)
+      if (xrel_of_batch[bi][q] != kNoX) b.s2[q].A = plan.X + xrel_of_batch[bi][q];
   }
-  for (auto& [xo, pr] : p2x) {
-    GemmSeg s = pr.second;
-    s.A = plan.X + xo;
-    p2[pr.first].push_back(s);
+}
+
+size_t Engine::x_budget_elems() const {
+  // float64 elements of H_eff psi intermediates per batch: 4 GiB by default,
+  // DMRGSCF_X_BUDGET_MB overrides (memory knob; the work done is unchanged)
+  const char* e = std::getenv("DMRGSCF_X_BUDGET_MB");
+  if (e && *e) {
+    double mb = std::atof(e);
+    if (mb > 0) return std::max<size_t>(1, (size_t)(mb * 1048576.0 / sizeof(double)));
   }
-  plan.g2.clear();
-  plan.s2.clear();
-  for (auto& [sig, segs] : p2) {
-    auto d = p2dim[sig];
-    plan.g2.push_back({sig, d[0], d[1], d[2], (int)plan.s2.size(), (int)segs.size()});
-    plan.s2.insert(plan.s2.end(), segs.begin(), segs.end());
-  }
+  return (size_t)1 << 29;
 }
 
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
-  if (plan.xsize) {
-    be_->memset0(plan.X, plan.xsize * sizeof(double));
-    be_->gemm(plan.g1, plan.s1, opt_.prec);
+  be_->tag = 1;
+  for (auto& b : plan.batches) {
+    if (b.xsize) {
+      be_->memset0(plan.X, b.xsize * sizeof(double));
+      be_->gemm(b.g1, b.s1, opt_.prec);
+    }
+    be_->gemm(b.g2, b.s2, opt_.prec);
   }
-  be_->gemm(plan.g2, plan.s2, opt_.prec);
+  be_->tag = 0;
 }
 
 // ============================================================ Davidson
@@ -1474,6 +1528,7 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
 SweepStats Engine::sweep() {
   stats_ = SweepStats();
   auto t0 = std::chrono::steady_clock::now();
+  be_->mark_begin();
   double e = 0.0, tr = 0.0, tmax = 0.0;
   for (int i = 0; i <= n_ - 3; ++i) {
     e = optimize_bond(i, true, &tr);
@@ -1485,6 +1540,7 @@ SweepStats Engine::sweep() {
     tmax = std::max(tmax, tr);
     if (i > 0) L_[i].reset();
   }
+  sweep_device_ms = be_->mark_end();
   be_->sync();
   energy_ = e;
   stats_.energy = e;

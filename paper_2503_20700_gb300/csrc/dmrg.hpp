@@ -184,6 +184,7 @@ class Engine {
   void build_initial_right();
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);
+  size_t x_budget_elems() const;
   double davidson(struct HPsiPlan& plan, double* psi, int* iters);
   double decimate(Block& enl, const struct HPsiPlan& plan, const double* psi, bool left,
                   std::vector<int>& kept, std::vector<double*>& ut, void** storage);
@@ -192,6 +193,7 @@ class Engine {
  public:
   // ---- accounting
   double sweep_seconds = 0.0;
+  double sweep_device_ms = 0.0;  // CUDA-event time of the last sweep
 };
 
 std::string last_error();

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Tolerances: float64 path 1e-8 Eh per sweep energy (the requirement for the
+FP64 GPU path); split-FP32 (3xTF32) path 1e-6 Eh against the float64 path.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dmrg import OracleDMRG
+from oracle.fci import fci
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2503_20700_gb300 as p
+    p.load()
+    return p
+
+
+def _case(name):
+    if name == "hub6":
+        h, eri, ec = W.hubbard_chain(6, u=4.0)
+        return h, eri, ec, 6, 0, 8, 3
+    if name == "benzene_ppp":
+        h, eri, ec = W.ppp_acene(1)
+        return h, eri, ec, 6, 0, 10, 3
+    if name == "rand6_s0":
+        h, L = W.cholesky_random(6, 12, seed=1)
+        return h, W.eri_from_cholesky(L), 0.0, 6, 0, 8, 3
+    if name == "rand6_s2":
+        h, L = W.cholesky_random(6, 12, seed=1)
+        return h, W.eri_from_cholesky(L), 0.0, 6, 2, 8, 3
+    if name == "rand7_s1":
+        h, L = W.cholesky_random(7, 14, seed=3)
+        return h, W.eri_from_cholesky(L), 0.0, 7, 1, 12, 3
+    if name == "rand8_n6":
+        h, L = W.cholesky_random(8, 16, seed=2)
+        return h, W.eri_from_cholesky(L), 0.0, 6, 0, 10, 2
+    if name == "rand8_n10":
+        h, L = W.cholesky_random(8, 16, seed=2)
+        return h, W.eri_from_cholesky(L), 0.0, 10, 0, 10, 2
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["hub6", "benzene_ppp", "rand6_s0", "rand6_s2", "rand7_s1",
+                                  "rand8_n6", "rand8_n10"])
+def test_sweep_energies_match_oracle(pkg, name):
+    h, eri, ec, N, S, D, sw = _case(name)
+    g = pkg.DMRG(h, eri=eri, n_elec=N, two_s=S, D=D, e_core=ec)
+    eg = [g.sweep()[0] for _ in range(sw)]
+    bg = g.bond_energies()
+    o = OracleDMRG(h, eri, N, S, D=D, e_core=ec)
+    eo = o.sweep(sw)
+    bo = np.array([b[3] for b in o.record.bond_energies])
+    assert np.abs(np.array(eg) - np.array(eo)).max() < 1e-8
+    assert len(bg) == len(bo)
+    assert np.abs(bg - bo).max() < 1e-8
+
+
+def test_exact_at_full_bond_dimension(pkg):
+    h, L = W.cholesky_random(6, 12, seed=1)
+    eri = W.eri_from_cholesky(L)
+    e_fci, _, _ = fci(h, eri, 6, 0)
+    g = pkg.DMRG(h, eri=eri, n_elec=6, two_s=0, D=500)
+    e = [g.sweep()[0] for _ in range(3)]
+    assert e[-1] == pytest.approx(e_fci, abs=1e-9)
+
+
+def test_cholesky_input_equals_eri_input(pkg):
+    h, L = W.cholesky_random(6, 12, seed=4)
+    eri = W.eri_from_cholesky(L)
+    e1 = pkg.DMRG(h, eri=eri, n_elec=6, D=8).sweep(2)[0]
+    e2 = pkg.DMRG(h, chol=L, n_elec=6, D=8).sweep(2)[0]
+    assert e1 == pytest.approx(e2, abs=1e-11)
+
+
+def test_naphthalene_d64_against_oracle_and_fci(pkg):
+    """PPP naphthalene, D=64, 4 sweeps (the plain FP64 workload)."""
+    path = os.path.join(GOLD, "naphthalene_ppp_d64.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file missing")
+    gold = json.load(open(path))
+    h, eri, ec = W.ppp_acene(2)
+    g = pkg.DMRG(h, eri=eri, n_elec=10, two_s=0, D=64, e_core=ec)
+    eg = [g.sweep()[0] for _ in range(4)]
+    assert np.abs(np.array(eg) - np.array(gold["e_dmrg_sweeps"])).max() < 1e-8
+    assert eg[-1] >= gold["e_fci"] - 1e-10          # variational bound
+    assert eg[-1] - gold["e_fci"] < 1e-3            # D=64 is close to FCI here
+
+
+def test_split_tf32_energy_close_to_fp64(pkg):
+    h, L = W.cholesky_random(8, 16, seed=2)
+    eri = W.eri_from_cholesky(L)
+    e64 = pkg.DMRG(h, eri=eri, n_elec=8, D=16).sweep(3)[0]
+    e32 = pkg.DMRG(h, eri=eri, n_elec=8, D=16, precision=pkg.SPLIT_TF32).sweep(3)[0]
+    assert abs(e32 - e64) < 1e-6
+
+
+def test_bad_arguments_return_einval(pkg):
+    h = np.zeros((4, 4))
+    eri = np.zeros((4, 4, 4, 4))
+    with pytest.raises(pkg.DmrgError) as ei:
+        pkg.DMRG(h, eri=eri, n_elec=4, two_s=1)
+    assert ei.value.status == pkg.DMRG_EINVAL
+    with pytest.raises(pkg.DmrgError) as ei:
+        pkg.DMRG(h, eri=eri, n_elec=9)
+    assert ei.value.status == pkg.DMRG_EINVAL
+
+
+# ---------------------------------------------------------------- kernels
+def _random_groups(rng, n_groups, max_dim, max_k, max_segs):
+    A_parts, B_parts, groups, segs, refs = [], [], [], [], []
+    a_off = b_off = c_off = 0
+    C_len = 0
+    for g in range(n_groups):
+        m = int(rng.integers(1, max_dim))
+        n = int(rng.integers(1, max_dim))
+        ns = int(rng.integers(1, max_segs + 1))
+        ref = np.zeros((m, n))
+        sb = len(segs)
+        for _ in range(ns):
+            k = int(rng.integers(1, max_k))
+            ta, tb = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+            a = rng.standard_normal((k, m) if ta else (m, k))
+            b = rng.standard_normal((n, k) if tb else (k, n))
+            alpha = float(rng.standard_normal())
+            ref += alpha * (a.T if ta else a) @ (b.T if tb else b)
+            segs.append((a_off, b_off, k, a.shape[1], b.shape[1], ta, tb, alpha))
+            A_parts.append(a.ravel())
+            B_parts.append(b.ravel())
+            a_off += a.size
+            b_off += b.size
+        groups.append((c_off, m, n, n, sb, ns))
+        refs.append((c_off, m, n, ref))
+        c_off += m * n
+    return (np.concatenate(A_parts), np.concatenate(B_parts), c_off, groups, segs, refs)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6)])
+def test_grouped_gemm_against_numpy(pkg, prec, tol):
+    rng = np.random.default_rng(7)
+    # ragged sizes spanning several 64x64 tiles with tails
+    A, B, clen, groups, segs, refs = _random_groups(rng, 24, 200, 300, 4)
+    C0 = rng.standard_normal(clen)
+    C = C0.copy()
+    pkg.ops.grouped_gemm(A, B, C, groups, segs, precision=prec)
+    for off, m, n, ref in refs:
+        got = C[off:off + m * n].reshape(m, n) - C0[off:off + m * n].reshape(m, n)
+        scale = np.abs(ref).max() + 1e-300
+        assert np.abs(got - ref).max() <= tol * scale * 10
+
+
+def test_grouped_gemm_rejects_out_of_range(pkg):
+    A = np.zeros(10)
+    B = np.zeros(10)
+    C = np.zeros(10)
+    with pytest.raises(pkg.DmrgError):
+        pkg.ops.grouped_gemm(A, B, C, [(0, 4, 4, 4, 0, 1)], [(0, 0, 4, 4, 4, 0, 0, 1.0)])
+
+
+def test_eigh_against_numpy(pkg):
+    rng = np.random.default_rng(3)
+    mats = []
+    for n in (1, 2, 5, 17, 64, 150):
+        x = rng.standard_normal((n, n))
+        mats.append(x + x.T)
+    res = pkg.ops.eigh_batched(mats)
+    for M, (w, V) in zip(mats, res):
+        ref = np.sort(np.linalg.eigvalsh(M))[::-1]
+        assert np.abs(w - ref).max() < 1e-11 * max(1.0, np.abs(ref).max())
+        assert np.abs(V @ M - w[:, None] * V).max() < 1e-10 * max(1.0, np.abs(ref).max())
+        assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-12
