@@ -50,7 +50,9 @@ typedef enum {
   DMRG_SPLIT_TF32 = 1,  /* H_eff psi / renormalisation GEMMs as 3xTF32 with
                            FP32 accumulation; Davidson, eigensolver and the
                            final reductions stay float64                      */
-  DMRG_BF16X9 = 2       /* reserved: BF16x9 split products                    */
+  DMRG_BF16X9 = 2,      /* reserved: BF16x9 split products (not available)   */
+  DMRG_SPLIT_HPSI = 3   /* 3xTF32 in the H_eff psi GEMMs only; renormalisation
+                           and complementary-operator GEMMs in float64          */
 } dmrg_precision;
 
 typedef struct {
@@ -193,6 +195,45 @@ dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, i
  */
 dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, double* w, double* vecs,
                               int device);
+
+/* ------------------------------------------------------------------------
+ * CAS-SCF side (Sec. II.A).  Orbitals are ordered core (ncore), active
+ * (ncas), virtual (the rest); nb is the total number of orbitals.  Cholesky
+ * vectors chol[k, p, q] = L^k_pq give (pq|rs) = sum_k L^k_pq L^k_rs.
+ * Host arrays in and out, float64 row-major; all arithmetic on the device.
+ * ---------------------------------------------------------------------- */
+
+/* R = expm(-K) for the real antisymmetric K with K[p,q] = kappa_pq (p > q):
+ * U = exp(-kappa^) of Sec. II.A rotates the integrals as h' = R^T h R. */
+dmrg_status casscf_rotation(const double* K, int nb, double* R, int device);
+
+/* Backward of R = expm(-K): given G = dE/dR (nb x nb) return the
+ * antisymmetric dK with dK[p,q] = dE/dkappa_pq (p > q), dK[q,p] = -dK[p,q]
+ * (adjoint Frechet derivative of the exponential, via the 2nb x 2nb block
+ * exponential). */
+dmrg_status casscf_rotation_backward(const double* K, const double* G, int nb, double* dK,
+                                     int device);
+
+/* Integral transformation: h_out = R^T h R, chol_out[k] = R^T chol[k] R. */
+dmrg_status casscf_transform(const double* R, const double* h, const double* chol, int rank,
+                             int nb, double* h_out, double* chol_out, int device);
+
+/* Active-space problem handed to DMRG: e_core (closed-shell core energy),
+ * h_act = inactive Fock matrix on the active block (ncas x ncas) and
+ * eri_act = (tu|vw) of the active orbitals (ncas^4). */
+dmrg_status casscf_active_space(const double* h, const double* chol, int rank, int nb, int ncore,
+                                int ncas, double* e_core, double* h_act, double* eri_act,
+                                int device);
+
+/* Orbital gradient at the current orbitals (kappa = 0) from the spin-free
+ * RDMs of the active space (gamma: ncas^2; Gamma: ncas^4 in the operator
+ * order of Eq. twordm):  grad = 2 (F - F^T) with the generalised Fock matrix
+ * F (textbook closed-shell-core form), grad[p,q] = dE/dkappa_pq for p > q,
+ * active-active block zero (those rotations are not used, Sec. II.C).
+ * fock (optional, may be NULL) receives F. */
+dmrg_status casscf_orbital_gradient(const double* h, const double* chol, int rank, int nb,
+                                    int ncore, int ncas, const double* gamma, const double* Gamma,
+                                    double* grad, double* fock, int device);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,11 @@ struct EighTask {
   int n;
 };
 
+struct HpsiBlock;
+struct HpsiItem;
+struct HpsiTask;
+struct HpsiReduce;
+
 class Backend {
  public:
   virtual ~Backend() = default;
@@ -64,10 +69,19 @@ class Backend {
   virtual void copy_h2d(void* dst, const void* src, size_t bytes) = 0;
   virtual void copy_d2h(void* dst, const void* src, size_t bytes) = 0;
   virtual void sync() = 0;
+  // the stream every primitive is issued on (cudaStream_t)
+  virtual void* stream() = 0;
 
   virtual void place(const std::vector<PlaceGroup>& groups, const std::vector<PlaceSeg>& segs) = 0;
   virtual void gemm(const std::vector<GemmGroup>& groups, const std::vector<GemmSeg>& segs,
                     Precision prec) = 0;
+
+  // Fused H_eff psi (hpsi_fused.cuh); all lists are device arrays prepared by
+  // the caller, scratch holds the partial tiles.  flops: algorithmic count
+  // of the launch (for the accounting under tag 1).
+  virtual void hpsi(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
+                    const HpsiReduce* reds, int nreds, double* scratch, Precision prec,
+                    double flops) = 0;
 
   // Davidson vector algebra on contiguous float64 vectors of length len.
   // out[i] = sum_t V[i*ld + t] * x[t] for i < m   (out is a device array)

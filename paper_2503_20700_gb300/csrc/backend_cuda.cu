@@ -19,6 +19,7 @@
 
 #include "backend.hpp"
 #include "gemm_split.cuh"
+#include "hpsi_fused.cuh"
 
 namespace dmrg {
 
@@ -472,6 +473,7 @@ class CudaBackend : public Backend {
     }
   }
   void sync() override { CK(cudaStreamSynchronize(st)); }
+  void* stream() override { return (void*)st; }
 
   // upload a packed task buffer; returns the device base pointer
   char* upload(const std::vector<std::pair<const void*, size_t>>& parts, std::vector<size_t>& offs) {
@@ -573,6 +575,21 @@ class CudaBackend : public Backend {
     ++launches;
     CK(cudaGetLastError());
     if (rec) CK(cudaEventRecord(rec->b, st));
+  }
+
+  void hpsi(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
+            const HpsiReduce* reds, int nreds, double* scratch, Precision prec, double flops) override {
+    gemm_flops += flops;
+    Rec* rec = nullptr;
+    if (profiling) {
+      recs.push_back(Rec{ev(), ev(), flops, 1});
+      rec = &recs.back();
+      CK(cudaEventRecord(rec->a, st));
+    }
+    hpsi_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, prec, st);
+    launches += (ntasks > 0) + (nreds > 0);
+    if (rec) CK(cudaEventRecord(rec->b, st));
+    if (recs.size() > 4096) drain();
   }
 
   void ensure_part(size_t n) {

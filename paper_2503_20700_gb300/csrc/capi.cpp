@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dmrgscf.h"
+#include "casscf.hpp"
 #include "dmrg.hpp"
 
 struct dmrg_ctx {
@@ -98,7 +99,8 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
   if (opts) o = *opts;
   if (o.D < 1 || o.max_space < 4 || o.davidson_tol <= 0 || o.max_davidson_iter < 1)
     return fail(nullptr, DMRG_EINVAL, "bad options");
-  if (o.precision < 0 || o.precision > 1) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
+  if (o.precision < 0 || o.precision > 3 || o.precision == 2)
+    return fail(nullptr, DMRG_EINVAL, "unsupported precision");
   auto ctx = std::make_unique<dmrg_ctx>();
   ctx->n = n;
   try {
@@ -134,7 +136,8 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     eo.D = o.D;
     eo.max_davidson_iter = o.max_davidson_iter;
     eo.davidson_tol = o.davidson_tol;
-    eo.prec = (dmrg::Precision)o.precision;
+    eo.prec = o.precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32;
+    eo.prec_renorm = o.precision == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64;
     eo.max_space = o.max_space;
     eo.verbose = o.verbose;
     ctx->eng = std::make_unique<dmrg::Engine>(ctx->be.get(), n, h, g, e_core, n_elec, two_s, eo,
@@ -172,8 +175,11 @@ dmrg_status dmrg_set_bond_dim(dmrg_ctx* c, int D) {
 
 dmrg_status dmrg_set_precision(dmrg_ctx* c, int precision) {
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
-  if (precision < 0 || precision > 1) return fail(c, DMRG_EINVAL, "unsupported precision");
-  c->eng->set_precision((dmrg::Precision)precision);
+  if (precision < 0 || precision > 3 || precision == 2)
+    return fail(c, DMRG_EINVAL, "unsupported precision");
+  c->eng->set_precision(
+      precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32,
+      precision == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64);
   return DMRG_OK;
 }
 
@@ -360,6 +366,66 @@ dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, doubl
     return translate(nullptr, e);
   }
   return DMRG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- CAS-SCF
+namespace {
+template <class F>
+dmrg_status with_casscf(int device, F&& f) {
+  std::string err;
+  std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  try {
+    dmrg::Casscf c(be.get());
+    f(c);
+    be->sync();
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
+  }
+  return DMRG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dmrg_status casscf_rotation(const double* K, int nb, double* R, int device) {
+  if (!K || !R || nb < 1 || nb > 8192) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) { c.rotation(K, nb, R); });
+}
+
+dmrg_status casscf_rotation_backward(const double* K, const double* G, int nb, double* dK, int device) {
+  if (!K || !G || !dK || nb < 1 || nb > 4096) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) { c.rotation_backward(K, G, nb, dK); });
+}
+
+dmrg_status casscf_transform(const double* R, const double* h, const double* chol, int rank, int nb,
+                             double* h_out, double* chol_out, int device) {
+  if (!R || !h || !chol || !h_out || !chol_out || rank < 1 || nb < 1)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) { c.transform(R, h, chol, rank, nb, h_out, chol_out); });
+}
+
+dmrg_status casscf_active_space(const double* h, const double* chol, int rank, int nb, int ncore,
+                                int ncas, double* e_core, double* h_act, double* eri_act, int device) {
+  if (!h || !chol || !e_core || !h_act || !eri_act || rank < 1 || ncore < 0 || ncas < 1 ||
+      ncore + ncas > nb)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) {
+    c.active_space(h, chol, rank, nb, ncore, ncas, e_core, h_act, eri_act);
+  });
+}
+
+dmrg_status casscf_orbital_gradient(const double* h, const double* chol, int rank, int nb, int ncore,
+                                    int ncas, const double* gamma, const double* Gamma, double* grad,
+                                    double* fock, int device) {
+  if (!h || !chol || !gamma || !Gamma || !grad || rank < 1 || ncore < 0 || ncas < 1 ||
+      ncore + ncas > nb)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) {
+    c.gradient(h, chol, rank, nb, ncore, ncas, gamma, Gamma, grad, fock);
+  });
 }
 
 }  // extern "C"

@@ -1,0 +1,393 @@
+// CAS-SCF side of the hot path (Sec. II.A): orbital rotation U = exp(-kappa),
+// integral transformation in Cholesky form, the active-space problem handed to
+// DMRG, and the orbital gradient from the one- and two-particle RDMs.
+//
+// Everything runs on the device in float64.  The contractions over the
+// Cholesky index go through the grouped segment-sum GEMM of the backend; the
+// small elementwise / reduction steps are the kernels below.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "backend.hpp"
+#include "casscf.hpp"
+
+namespace dmrg {
+
+namespace {
+
+// v[k] = sum_{i<ncore} L[k,i,i];  w[k] = sum_{t,u} gamma[t,u] L[k,c+t,c+u]
+__global__ void k_diag_contract(const double* __restrict__ L, int nb, int ncore, int ncas,
+                                const double* __restrict__ gamma, double* __restrict__ v,
+                                double* __restrict__ w) {
+  const int k = blockIdx.x;
+  const double* Lk = L + (size_t)k * nb * nb;
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < ncore; i += blockDim.x) a += Lk[(size_t)i * nb + i];
+  if (gamma)
+    for (int e = threadIdx.x; e < ncas * ncas; e += blockDim.x) {
+      int t = e / ncas, u = e % ncas;
+      b += gamma[e] * Lk[(size_t)(ncore + t) * nb + ncore + u];
+    }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      s1[threadIdx.x] += s1[threadIdx.x + st];
+      s2[threadIdx.x] += s2[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v[k] = s1[0];
+    if (w) w[k] = s2[0];
+  }
+}
+
+// gather the active block of every Cholesky vector: La[k, t*ncas+u] = L[k, c+t, c+u]
+__global__ void k_gather_active(const double* __restrict__ L, int rank, int nb, int ncore, int ncas,
+                                double* __restrict__ La) {
+  size_t tot = (size_t)rank * ncas * ncas;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t k = e / ((size_t)ncas * ncas);
+    int r = (int)(e % ((size_t)ncas * ncas));
+    int t = r / ncas, u = r % ncas;
+    La[e] = L[(k * nb + ncore + t) * nb + ncore + u];
+  }
+}
+
+// d[t,u,v,w] = Gamma[t,v,w,u] (paper operator order -> chemists' order)
+__global__ void k_permute_rdm2(const double* __restrict__ G, int n, double* __restrict__ d) {
+  size_t tot = (size_t)n * n * n * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t r = e;
+    int w = (int)(r % n); r /= n;
+    int v = (int)(r % n); r /= n;
+    int u = (int)(r % n); r /= n;
+    int t = (int)r;
+    d[e] = G[(((size_t)t * n + v) * n + w) * n + u];
+  }
+}
+
+// out = a*X + b*Y + c*Z elementwise (any pointer may be null)
+__global__ void k_axpbypcz(double* __restrict__ out, size_t len, double a, const double* X, double b,
+                           const double* Y, double c, const double* Z) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (X) s += a * X[e];
+    if (Y) s += b * Y[e];
+    if (Z) s += c * Z[e];
+    out[e] = s;
+  }
+}
+
+// generalised Fock F (nb x nb) from its pieces; rows: core, active, virtual
+//   F[i,q] = 2 (FI[q,i] + FA[q,i]);  F[t,q] = sum_u gamma[t,u] FI[q,c+u] + F2[t,q];  F[a,q] = 0
+__global__ void k_assemble_fock(const double* __restrict__ FI, const double* __restrict__ FA,
+                                const double* __restrict__ gamma, const double* __restrict__ F2,
+                                int nb, int ncore, int ncas, double* __restrict__ F) {
+  size_t tot = (size_t)nb * nb;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int p = (int)(e / nb), q = (int)(e % nb);
+    double v = 0.0;
+    if (p < ncore) {
+      v = 2.0 * (FI[(size_t)q * nb + p] + FA[(size_t)q * nb + p]);
+    } else if (p < ncore + ncas) {
+      int t = p - ncore;
+      for (int u = 0; u < ncas; ++u) v += gamma[(size_t)t * ncas + u] * FI[(size_t)q * nb + ncore + u];
+      v += F2[(size_t)t * nb + q];
+    }
+    F[e] = v;
+  }
+}
+
+// grad = 2 (F - F^T) with the active-active block zeroed
+__global__ void k_gradient(const double* __restrict__ F, int nb, int ncore, int ncas,
+                           double* __restrict__ g) {
+  size_t tot = (size_t)nb * nb;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int p = (int)(e / nb), q = (int)(e % nb);
+    bool aa = p >= ncore && p < ncore + ncas && q >= ncore && q < ncore + ncas;
+    g[e] = aa ? 0.0 : 2.0 * (F[e] - F[(size_t)q * nb + p]);
+  }
+}
+
+// e = sum_i (h[i,i] + FI[i,i]) over core orbitals (single block)
+__global__ void k_core_energy(const double* __restrict__ h, const double* __restrict__ FI, int nb,
+                              int ncore, double* __restrict__ e) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < ncore; i += blockDim.x) a += h[(size_t)i * nb + i] + FI[(size_t)i * nb + i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *e = s[0];
+}
+
+// copy a sub-block: out[r*lo + c] = in[(r0+r)*li + c0 + c]
+__global__ void k_subblock(const double* __restrict__ in, int li, int r0, int c0, int rows, int cols,
+                           double* __restrict__ out, int lo) {
+  size_t tot = (size_t)rows * cols;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(e / cols), c = (int)(e % cols);
+    out[(size_t)r * lo + c] = in[(size_t)(r0 + r) * li + c0 + c];
+  }
+}
+
+// A[i,i] += s
+__global__ void k_add_diag(double* A, int n, double s) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    A[(size_t)i * n + i] += s;
+}
+
+#define ST ((cudaStream_t)be_->stream())
+int grid_for(size_t n) { return (int)std::min<size_t>(152 * 16, std::max<size_t>(1, (n + 255) / 256)); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- helpers
+struct Casscf::Dev {
+  Backend* be;
+  std::vector<void*> mem;
+  explicit Dev(Backend* b) : be(b) {}
+  ~Dev() {
+    be->sync();
+    for (void* p : mem) be->free(p);
+  }
+  double* alloc(size_t n) {
+    double* p = (double*)be->alloc(std::max<size_t>(n, 1) * sizeof(double));
+    be->memset0(p, std::max<size_t>(n, 1) * sizeof(double));
+    mem.push_back(p);
+    return p;
+  }
+  double* upload(const double* h, size_t n) {
+    double* p = alloc(n);
+    be->copy_h2d(p, h, n * sizeof(double));
+    return p;
+  }
+};
+
+static void gemm1(Backend* be, double* C, int m, int n, int ldc, const double* A, int lda, int ta,
+                  const double* B, int ldb, int tb, int k, double alpha) {
+  std::vector<GemmGroup> g{{C, m, n, ldc, 0, 1}};
+  std::vector<GemmSeg> s{{A, B, k, lda, ldb, ta, tb, alpha}};
+  be->gemm(g, s, Precision::FP64);
+}
+
+Casscf::Casscf(Backend* be) : be_(be) {}
+
+// R = expm(-K): scaling and squaring with a degree-18 Taylor polynomial
+// (Horner form) of the scaled matrix.
+void Casscf::expm_neg(const double* dK, int n, double* dR, double sign) {
+  // host copy for the norm (1-norm of the scaled argument <= 1/4)
+  std::vector<double> K((size_t)n * n);
+  be_->copy_d2h(K.data(), dK, K.size() * sizeof(double));
+  double nrm = 0.0;
+  for (int c = 0; c < n; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s += std::abs(K[(size_t)r * n + c]);
+    nrm = std::max(nrm, s);
+  }
+  int sq = 0;
+  while (nrm / std::ldexp(1.0, sq) > 0.25 && sq < 60) ++sq;
+  double scale = sign / std::ldexp(1.0, sq);
+  Dev d(be_);
+  double* X = d.alloc((size_t)n * n);
+  double* T = d.alloc((size_t)n * n);
+  k_axpbypcz<<<grid_for((size_t)n * n), 256, 0, ST>>>(X, (size_t)n * n, scale, dK, 0, nullptr, 0, nullptr);
+  // Horner: P = I + X/18;  P = I + X P / j  for j = 17 .. 1
+  const int deg = 18;
+  be_->memset0(dR, (size_t)n * n * sizeof(double));
+  k_add_diag<<<grid_for(n), 256, 0, ST>>>(dR, n, 1.0);
+  for (int j = deg; j >= 1; --j) {
+    be_->memset0(T, (size_t)n * n * sizeof(double));
+    gemm1(be_, T, n, n, n, X, n, 0, dR, n, 0, n, 1.0 / j);
+    k_add_diag<<<grid_for(n), 256, 0, ST>>>(T, n, 1.0);
+    be_->copy_d2d(dR, T, (size_t)n * n * sizeof(double));
+  }
+  for (int s = 0; s < sq; ++s) {
+    be_->memset0(T, (size_t)n * n * sizeof(double));
+    gemm1(be_, T, n, n, n, dR, n, 0, dR, n, 0, n, 1.0);
+    be_->copy_d2d(dR, T, (size_t)n * n * sizeof(double));
+  }
+  be_->sync();
+}
+
+void Casscf::rotation(const double* K, int nb, double* R) {
+  Dev d(be_);
+  double* dK = d.upload(K, (size_t)nb * nb);
+  double* dR = d.alloc((size_t)nb * nb);
+  expm_neg(dK, nb, dR, -1.0);
+  be_->copy_d2h(R, dR, (size_t)nb * nb * sizeof(double));
+}
+
+// dE/dK for R = expm(-K) given G = dE/dR: with X = -K, dE/dX = L_exp(X^T, G)
+// = upper-right block of expm([[K, G], [0, K]]) (X^T = K for antisymmetric K),
+// so dE/dK = -L and the parameter gradient is antisymmetrised.
+void Casscf::rotation_backward(const double* K, const double* G, int nb, double* dK) {
+  int n2 = 2 * nb;
+  std::vector<double> B((size_t)n2 * n2, 0.0);
+  for (int r = 0; r < nb; ++r)
+    for (int c = 0; c < nb; ++c) {
+      B[(size_t)r * n2 + c] = K[(size_t)r * nb + c];
+      B[(size_t)(r + nb) * n2 + c + nb] = K[(size_t)r * nb + c];
+      B[(size_t)r * n2 + c + nb] = G[(size_t)r * nb + c];
+    }
+  Dev d(be_);
+  double* dB = d.upload(B.data(), B.size());
+  double* dE = d.alloc(B.size());
+  expm_neg(dB, n2, dE, 1.0);
+  std::vector<double> E(B.size());
+  be_->copy_d2h(E.data(), dE, E.size() * sizeof(double));
+  for (int r = 0; r < nb; ++r)
+    for (int c = 0; c < nb; ++c) {
+      double a = -E[(size_t)r * n2 + c + nb], b = -E[(size_t)c * n2 + r + nb];
+      dK[(size_t)r * nb + c] = a - b;
+    }
+}
+
+// h' = R^T h R and L'^k = R^T L^k R (batched over the Cholesky index)
+void Casscf::transform(const double* R, const double* h, const double* L, int rank, int nb,
+                       double* h_out, double* L_out) {
+  Dev d(be_);
+  size_t nn = (size_t)nb * nb;
+  double* dR = d.upload(R, nn);
+  double* dh = d.upload(h, nn);
+  double* dL = d.upload(L, nn * rank);
+  double* T = d.alloc(nn * (rank + 1));
+  double* out = d.alloc(nn * (rank + 1));
+  std::vector<GemmGroup> g1, g2;
+  std::vector<GemmSeg> s1, s2;
+  for (int k = 0; k <= rank; ++k) {
+    const double* Mk = (k == 0) ? dh : dL + nn * (k - 1);
+    g1.push_back({T + nn * k, nb, nb, nb, (int)s1.size(), 1});
+    s1.push_back({Mk, dR, nb, nb, nb, 0, 0, 1.0});
+    g2.push_back({out + nn * k, nb, nb, nb, (int)s2.size(), 1});
+    s2.push_back({dR, T + nn * k, nb, nb, nb, 1, 0, 1.0});
+  }
+  be_->gemm(g1, s1, Precision::FP64);
+  be_->gemm(g2, s2, Precision::FP64);
+  be_->copy_d2h(h_out, out, nn * sizeof(double));
+  be_->copy_d2h(L_out, out + nn, nn * rank * sizeof(double));
+}
+
+// Pieces shared by the active-space problem and the gradient.
+struct FockParts {
+  double *FI, *FA, *La, *v, *w;
+};
+
+static FockParts fock_parts(Backend* be, Casscf::Dev& d, const double* dh, const double* dL, int rank,
+                            int nb, int ncore, int ncas, const double* dgamma) {
+  size_t nn = (size_t)nb * nb;
+  Backend* be_ = be;  // stream of the launches below
+  FockParts f{};
+  f.v = d.alloc(rank);
+  f.w = d.alloc(rank);
+  k_diag_contract<<<rank, 256, 0, ST>>>(dL, nb, ncore, ncas, dgamma, f.v, f.w);
+  // J = sum_k v_k L^k  (1 x rank) x (rank x nb^2)
+  double* J = d.alloc(nn);
+  gemm1(be, J, 1, (int)nn, (int)nn, f.v, rank, 0, dL, (int)nn, 0, rank, 1.0);
+  // Kc = sum_k L^k[:, core] L^k[core, :]
+  double* Kc = d.alloc(nn);
+  if (ncore > 0) {
+    std::vector<GemmGroup> g{{Kc, nb, nb, nb, 0, rank}};
+    std::vector<GemmSeg> s;
+    for (int k = 0; k < rank; ++k) s.push_back({dL + nn * k, dL + nn * k, ncore, nb, nb, 0, 0, 1.0});
+    be->gemm(g, s, Precision::FP64);
+  }
+  f.FI = d.alloc(nn);
+  k_axpbypcz<<<grid_for(nn), 256, 0, ST>>>(f.FI, nn, 1.0, dh, 2.0, J, -1.0, Kc);
+  f.FA = nullptr;
+  if (dgamma) {
+    double* JA = d.alloc(nn);
+    gemm1(be, JA, 1, (int)nn, (int)nn, f.w, rank, 0, dL, (int)nn, 0, rank, 1.0);
+    // M^k = L^k[:, act] gamma ; KA = sum_k M^k L^k[act, :]
+    double* M = d.alloc((size_t)rank * nb * ncas);
+    std::vector<GemmGroup> g1;
+    std::vector<GemmSeg> s1;
+    for (int k = 0; k < rank; ++k) {
+      g1.push_back({M + (size_t)k * nb * ncas, nb, ncas, ncas, (int)s1.size(), 1});
+      s1.push_back({dL + nn * k + ncore, dgamma, ncas, nb, ncas, 0, 0, 1.0});
+    }
+    be->gemm(g1, s1, Precision::FP64);
+    double* KA = d.alloc(nn);
+    std::vector<GemmGroup> g2{{KA, nb, nb, nb, 0, rank}};
+    std::vector<GemmSeg> s2;
+    for (int k = 0; k < rank; ++k)
+      s2.push_back({M + (size_t)k * nb * ncas, dL + nn * k + (size_t)ncore * nb, ncas, ncas, nb, 0, 0, 1.0});
+    be->gemm(g2, s2, Precision::FP64);
+    f.FA = d.alloc(nn);
+    k_axpbypcz<<<grid_for(nn), 256, 0, ST>>>(f.FA, nn, 1.0, JA, -0.5, KA, 0.0, nullptr);
+  }
+  f.La = d.alloc((size_t)rank * ncas * ncas);
+  k_gather_active<<<grid_for((size_t)rank * ncas * ncas), 256, 0, ST>>>(dL, rank, nb, ncore, ncas, f.La);
+  return f;
+}
+
+void Casscf::active_space(const double* h, const double* L, int rank, int nb, int ncore, int ncas,
+                          double* e_core, double* h_act, double* eri_act) {
+  Dev d(be_);
+  size_t nn = (size_t)nb * nb;
+  double* dh = d.upload(h, nn);
+  double* dL = d.upload(L, nn * rank);
+  FockParts f = fock_parts(be_, d, dh, dL, rank, nb, ncore, ncas, nullptr);
+  double* de = d.alloc(1);
+  k_core_energy<<<1, 256, 0, ST>>>(dh, f.FI, nb, ncore, de);
+  double* ha = d.alloc((size_t)ncas * ncas);
+  k_subblock<<<grid_for((size_t)ncas * ncas), 256, 0, ST>>>(f.FI, nb, ncore, ncore, ncas, ncas, ha, ncas);
+  // (tu|vw) = sum_k La[k,tu] La[k,vw]
+  int a2 = ncas * ncas;
+  double* eri = d.alloc((size_t)a2 * a2);
+  gemm1(be_, eri, a2, a2, a2, f.La, a2, 1, f.La, a2, 0, rank, 1.0);
+  be_->copy_d2h(e_core, de, sizeof(double));
+  be_->copy_d2h(h_act, ha, (size_t)ncas * ncas * sizeof(double));
+  be_->copy_d2h(eri_act, eri, (size_t)a2 * a2 * sizeof(double));
+}
+
+void Casscf::gradient(const double* h, const double* L, int rank, int nb, int ncore, int ncas,
+                      const double* gamma, const double* Gamma, double* grad, double* fock) {
+  Dev d(be_);
+  size_t nn = (size_t)nb * nb;
+  int a2 = ncas * ncas;
+  double* dh = d.upload(h, nn);
+  double* dL = d.upload(L, nn * rank);
+  double* dg = d.upload(gamma, (size_t)a2);
+  double* dG = d.upload(Gamma, (size_t)a2 * a2);
+  FockParts f = fock_parts(be_, d, dh, dL, rank, nb, ncore, ncas, dg);
+  // d[t,u,v,w] = Gamma[t,v,w,u];  W (rank x a2) = La (rank x a2) d^T (a2 x a2)
+  double* dd = d.alloc((size_t)a2 * a2);
+  k_permute_rdm2<<<grid_for((size_t)a2 * a2), 256, 0, ST>>>(dG, ncas, dd);
+  double* W = d.alloc((size_t)rank * a2);
+  gemm1(be_, W, rank, a2, a2, f.La, a2, 0, dd, a2, 1, a2, 1.0);
+  // F2[t, q] = sum_k sum_u W^k[t,u] L^k[q, c+u]
+  double* F2 = d.alloc((size_t)ncas * nb);
+  std::vector<GemmGroup> g{{F2, ncas, nb, nb, 0, rank}};
+  std::vector<GemmSeg> s;
+  for (int k = 0; k < rank; ++k)
+    s.push_back({W + (size_t)k * a2, dL + nn * k + ncore, ncas, ncas, nb, 0, 1, 1.0});
+  be_->gemm(g, s, Precision::FP64);
+  double* F = d.alloc(nn);
+  k_assemble_fock<<<grid_for(nn), 256, 0, ST>>>(f.FI, f.FA, dg, F2, nb, ncore, ncas, F);
+  double* dgr = d.alloc(nn);
+  k_gradient<<<grid_for(nn), 256, 0, ST>>>(F, nb, ncore, ncas, dgr);
+  be_->copy_d2h(grad, dgr, nn * sizeof(double));
+  if (fock) be_->copy_d2h(fock, F, nn * sizeof(double));
+}
+
+}  // namespace dmrg

@@ -1,7 +1,9 @@
 // Host planner of the spin-adapted two-site DMRG (see dmrg.hpp).
 #include "dmrg.hpp"
+#include "hpsi_fused.cuh"
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -396,7 +398,10 @@ struct GemmBuilder {
 };
 }  // namespace
 
-Engine::~Engine() = default;
+Engine::~Engine() {
+  if (prev_.psi && be_) be_->free(prev_.psi);
+  if (ones_ && be_) be_->free(ones_);
+}
 
 int Engine::left_dim(int m) const {
   if (m < 0 || m >= (int)L_.size() || !L_[m]) return -1;
@@ -827,7 +832,7 @@ void Engine::build_comp_from_normal(const Block& b, OpSet& dst, const std::vecto
           int nc = (int)std::min(panel, N - c0);
           gb.add(Y + c0, M, nc, (int)N, GemmSeg{Gdev, X + c0, K, K, (int)N, 0, 0, 1.0});
         }
-        gb.run(be_, opt_.prec);
+        gb.run(be_, opt_.prec_renorm);
         // place rows of Y into the targets (directly, or as adjoint)
         PlaceBuilder pb;
         const Layout& DL = dst.layout(kind_dn(kind), k2);
@@ -859,8 +864,11 @@ void Engine::build_comp_from_normal(const Block& b, OpSet& dst, const std::vecto
 
 // ============================================================ renormalisation
 // O'(a', a) = U_a'^T O(a', a) U_a with Ut[a] = kept eigenvectors as rows.
-std::unique_ptr<Block> Engine::renormalize(Block& enl, const std::vector<int>& kept,
-                                           const std::vector<double*>& ut, bool switch_to_comp) {
+std::unique_ptr<Block> Engine::renormalize(Block& enl, const SavedU& U, bool switch_to_comp) {
+  const std::vector<int>& kept = U.kept;
+  std::vector<const double*> ut(U.off.size(), nullptr);
+  for (size_t s = 0; s < U.off.size(); ++s)
+    if (kept[s] > 0) ut[s] = U.ut((int)s);
   auto nb = std::make_unique<Block>();
   nb->left = enl.left;
   nb->nsites = enl.nsites;
@@ -924,8 +932,8 @@ std::unique_ptr<Block> Engine::renormalize(Block& enl, const std::vector<int>& k
                  GemmSeg{ut[bl.bra], Tb + toff[i], bl.rows, bl.rows, ka, 0, 0, 1.0});
         }
       }
-      g1.run(be_, opt_.prec);
-      g2.run(be_, opt_.prec);
+      g1.run(be_, opt_.prec_renorm);
+      g2.run(be_, opt_.prec_renorm);
     }
     be_->sync();
     be_->free(T);
@@ -1005,22 +1013,23 @@ std::vector<std::pair<int, SrcBlock>> reach(OpSet& set, const Operand& x, int ke
 }
 }  // namespace
 
-// H_eff psi as batches of (phase 1: X = c x psi, phase 2: sigma += X y^T)
-// grouped GEMMs; the batches bound the memory of the X intermediates.
-struct HPsiBatch {
-  std::vector<GemmGroup> g1, g2;
-  std::vector<GemmSeg> s1, s2;
-  std::vector<size_t> x1off;  // X offset of every phase-1 output
-  size_t xsize = 0;
-};
+// H_eff psi as one fused launch: per sigma block, the list of items
+// alpha op(A) P op(B)^T (left operator block, psi block, right operator block).
 struct HPsiPlan {
   PsiLayout psi;
   double* in = nullptr;   // psi input buffer
   double* out = nullptr;  // sigma output buffer
-  double* X = nullptr;    // phase-1 intermediates (largest batch)
-  size_t xsize = 0;
-  std::vector<HPsiBatch> batches;
+  // device copies of the task lists (built once per bond)
+  void* dev = nullptr;
+  HpsiBlock* d_blocks = nullptr;
+  HpsiItem* d_items = nullptr;
+  HpsiTask* d_tasks = nullptr;
+  HpsiReduce* d_reds = nullptr;
+  double* scratch = nullptr;
+  int ntasks = 0, nreds = 0;
+  size_t nitems = 0;
   double flops = 0.0;
+  double* diag = nullptr;  // diagonal of H_eff (Davidson preconditioner)
 };
 
 void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
@@ -1039,22 +1048,12 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   rs.sites = block_sites(Re, n_);
   rs.normal = Re.normal;
   emit_cross(this, ls, rs, terms);
-  // phase-1 slots
-  struct Slot {
-    const double* A;
-    int lda, transA;
-    const double* B;
-    int ldb;
-    int m, n, k;
-    double alpha;
-  };
-  std::vector<Slot> slots;
-  std::map<double*, std::vector<GemmSeg>> p2;
-  std::map<double*, std::array<int, 3>> p2dim;
-  std::vector<std::pair<size_t, std::pair<double*, GemmSeg>>> p2x;  // slot offset -> (sigma, seg)
-  size_t xoff = 0;
+  std::vector<std::vector<HpsiItem>> per(P.blk.size());
+  std::vector<std::pair<int, HpsiItem>> diag_items;
   plan.flops = 0.0;
   for (auto& t : terms) {
+    // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
+    int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
     for (auto& kb : P.blk) {
       auto lr = reach(lo, t.x, kb.a);
       if (lr.empty()) continue;
@@ -1069,112 +1068,100 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
           if (pi < 0) continue;
           const Sector& sap = lo.basis.sec[ap];
           const Sector& sbp = ro.basis.sec[bp];
-          // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
-          int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
           double hc = hpsi_coef(sap.j, sbp.j, sa.j, sb.j, kop, two_s_);
           if (hc == 0.0) continue;
-          double alpha = t.coef * hc * sign * xs.coef * ys.coef;
-          double* sig = plan.out + P.blk[pi].off;
-          const double* psi = plan.in + kb.off;
-          int ma = sa.dim, mb = sb.dim, map_ = sap.dim, mbp = sbp.dim;
-          p2dim[sig] = {map_, mbp, mbp};
-          if (t.x.t == Operand::ID) {
-            // sigma(a, b') += alpha psi(a,b) y^T
-            GemmSeg s{psi, ys.ptr, mb, mb, ys.ld, 0, ys.trans ? 0 : 1, alpha};
-            p2[sig].push_back(s);
-            plan.flops += 2.0 * ma * mbp * mb;
-          } else if (t.y.t == Operand::ID) {
-            GemmSeg s{xs.ptr, psi, ma, xs.ld, mb, xs.trans, 0, alpha};
-            p2[sig].push_back(s);
-            plan.flops += 2.0 * map_ * mb * ma;
-          } else {
-            slots.push_back({xs.ptr, xs.ld, xs.trans, psi, mb, map_, mb, ma, alpha});
-            GemmSeg s{nullptr, ys.ptr, mb, mb, ys.ld, 0, ys.trans ? 0 : 1, 1.0};
-            p2x.push_back({xoff, {sig, s}});
-            xoff += (size_t)map_ * mb;
-            plan.flops += 2.0 * map_ * mb * ma + 2.0 * map_ * mbp * mb;
-          }
+          HpsiItem it;
+          it.A = (t.x.t == Operand::ID) ? nullptr : xs.ptr;
+          it.lda = xs.ld;
+          it.transA = xs.trans;
+          it.P = plan.in + kb.off;
+          it.ldp = sb.dim;
+          it.B = (t.y.t == Operand::ID) ? nullptr : ys.ptr;
+          it.ldb = ys.ld;
+          it.transB = ys.trans;
+          it.ka = sa.dim;
+          it.kb = sb.dim;
+          it.alpha = t.coef * hc * sign * xs.coef * ys.coef;
+          per[pi].push_back(it);
+          if (it.A) plan.flops += 2.0 * sap.dim * sa.dim * sb.dim;
+          if (it.B) plan.flops += 2.0 * sap.dim * sbp.dim * sb.dim;
+          if (ap == kb.a && bp == kb.b) diag_items.push_back({pi, it});
         }
     }
   }
-  // split into batches so that the X intermediates stay within a budget
-  const size_t budget = x_budget_elems();
-  const size_t kNoX = (size_t)-1;
-  plan.batches.clear();
-  std::vector<std::vector<size_t>> xrel_of_batch;  // per batch: X offset of each s2 entry or kNoX
-  size_t maxx = 0;
-  size_t si = 0;
-  bool first = true;
-  while (first || si < slots.size()) {
-    HPsiBatch b;
-    std::map<double*, std::vector<std::pair<GemmSeg, size_t>>> bp2;
-    if (first) {
-      for (auto& [sig, segs] : p2)
-        for (auto& sg : segs) bp2[sig].push_back({sg, kNoX});
-      first = false;
-    }
-    size_t xo = 0;
-    std::vector<size_t> g1off;
-    while (si < slots.size()) {
-      auto& sl = slots[si];
-      size_t sz = (size_t)sl.m * sl.n;
-      if (xo > 0 && xo + sz > budget) break;
-      g1off.push_back(xo);
-      b.g1.push_back({nullptr, sl.m, sl.n, sl.n, (int)b.s1.size(), 1});
-      b.s1.push_back({sl.A, sl.B, sl.k, sl.lda, sl.ldb, sl.transA, 0, sl.alpha});
-      bp2[p2x[si].second.first].push_back({p2x[si].second.second, xo});
-      xo += sz;
-      ++si;
-    }
-    b.xsize = xo;
-    maxx = std::max(maxx, xo);
-    std::vector<size_t> xr;
-    for (auto& [sig, segs] : bp2) {
-      auto d = p2dim[sig];
-      b.g2.push_back({sig, d[0], d[1], d[2], (int)b.s2.size(), (int)segs.size()});
-      for (auto& [sg, off] : segs) {
-        b.s2.push_back(sg);
-        xr.push_back(off);
-      }
-    }
-    xrel_of_batch.push_back(std::move(xr));
-    // remember phase-1 offsets in the (unused) pad of the group via a side table
-    b.x1off = std::move(g1off);
-    plan.batches.push_back(std::move(b));
+  std::vector<HpsiBlock> blocks;
+  std::vector<HpsiItem> items;
+  long long tile_items = 0;
+  for (size_t b = 0; b < P.blk.size(); ++b) {
+    HpsiBlock hb;
+    hb.C = plan.out + P.blk[b].off;
+    hb.m = P.blk[b].rows;
+    hb.n = P.blk[b].cols;
+    hb.ldc = P.blk[b].cols;
+    hb.item_begin = (int)items.size();
+    hb.item_count = (int)per[b].size();
+    items.insert(items.end(), per[b].begin(), per[b].end());
+    blocks.push_back(hb);
+    tile_items += (long long)per[b].size() * ((hb.m + 63) / 64) * ((hb.n + 63) / 64);
   }
-  if (plan.X) be_->free(plan.X);
-  plan.xsize = maxx;
-  plan.X = maxx ? (double*)be_->alloc(maxx * sizeof(double)) : nullptr;
-  for (size_t bi = 0; bi < plan.batches.size(); ++bi) {
-    auto& b = plan.batches[bi];
-    for (size_t q = 0; q < b.g1.size(); ++q) b.g1[q].C = plan.X + b.x1off[q];
-    for (size_t q = 0; q < b.s2.size(); ++q)
-      if (xrel_of_batch[bi][q] != kNoX) b.s2[q].A = plan.X + xrel_of_batch[bi][q];
+  // chunk the items of a tile so the launch has several waves of CTAs
+  int max_items = (int)std::max<long long>(4, tile_items / (8 * 152) + 1);
+  std::vector<HpsiTask> tasks;
+  std::vector<HpsiReduce> reds;
+  size_t scr = hpsi_plan_tasks(blocks, max_items, tasks, reds);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t ob = 0, oi = al(ob + blocks.size() * sizeof(HpsiBlock));
+  size_t ot = al(oi + items.size() * sizeof(HpsiItem));
+  size_t orr = al(ot + tasks.size() * sizeof(HpsiTask));
+  size_t os = al(orr + reds.size() * sizeof(HpsiReduce));
+  size_t total = os + scr * sizeof(double) + 256;
+  if (plan.dev) be_->free(plan.dev);
+  plan.dev = be_->alloc(total);
+  char* d = (char*)plan.dev;
+  plan.d_blocks = (HpsiBlock*)(d + ob);
+  plan.d_items = (HpsiItem*)(d + oi);
+  plan.d_tasks = (HpsiTask*)(d + ot);
+  plan.d_reds = (HpsiReduce*)(d + orr);
+  plan.scratch = (double*)(d + os);
+  if (!blocks.empty()) be_->copy_h2d(plan.d_blocks, blocks.data(), blocks.size() * sizeof(HpsiBlock));
+  if (!items.empty()) be_->copy_h2d(plan.d_items, items.data(), items.size() * sizeof(HpsiItem));
+  if (!tasks.empty()) be_->copy_h2d(plan.d_tasks, tasks.data(), tasks.size() * sizeof(HpsiTask));
+  if (!reds.empty()) be_->copy_h2d(plan.d_reds, reds.data(), reds.size() * sizeof(HpsiReduce));
+  plan.ntasks = (int)tasks.size();
+  plan.nreds = (int)reds.size();
+  plan.nitems = items.size();
+  // diagonal: sigma_diag(a,b)[i,j] = sum alpha A(a,a)[i,i] B(b,b)[j,j] over the
+  // items whose ket block equals their sigma block (outer products, k = 1)
+  if (plan.diag) be_->free(plan.diag);
+  plan.diag = (double*)be_->alloc(std::max<size_t>(P.size, 1) * sizeof(double));
+  be_->memset0(plan.diag, std::max<size_t>(P.size, 1) * sizeof(double));
+  int mx = 1;
+  for (auto& b : P.blk) mx = std::max(mx, std::max(b.rows, b.cols));
+  if (ones_len_ < (size_t)mx) {
+    if (ones_) be_->free(ones_);
+    std::vector<double> o(mx, 1.0);
+    ones_ = (double*)be_->alloc(mx * sizeof(double));
+    be_->copy_h2d(ones_, o.data(), mx * sizeof(double));
+    ones_len_ = mx;
   }
+  GemmBuilder gd;
+  for (auto& [pi, it] : diag_items) {
+    const auto& bl = P.blk[pi];
+    const double* a = it.A ? it.A : ones_;
+    const double* b = it.B ? it.B : ones_;
+    int lda = it.A ? it.lda + 1 : 1;
+    int ldb = it.B ? it.ldb + 1 : 1;
+    gd.add(plan.diag + bl.off, bl.rows, bl.cols, bl.cols, GemmSeg{a, b, 1, lda, ldb, 0, 1, it.alpha});
+  }
+  gd.run(be_, Precision::FP64);
 }
 
-size_t Engine::x_budget_elems() const {
-  // float64 elements of H_eff psi intermediates per batch: 4 GiB by default,
-  // DMRGSCF_X_BUDGET_MB overrides (memory knob; the work done is unchanged)
-  const char* e = std::getenv("DMRGSCF_X_BUDGET_MB");
-  if (e && *e) {
-    double mb = std::atof(e);
-    if (mb > 0) return std::max<size_t>(1, (size_t)(mb * 1048576.0 / sizeof(double)));
-  }
-  return (size_t)1 << 29;
-}
+size_t Engine::x_budget_elems() const { return 0; }
 
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
-  be_->tag = 1;
-  for (auto& b : plan.batches) {
-    if (b.xsize) {
-      be_->memset0(plan.X, b.xsize * sizeof(double));
-      be_->gemm(b.g1, b.s1, opt_.prec);
-    }
-    be_->gemm(b.g2, b.s2, opt_.prec);
-  }
-  be_->tag = 0;
+  be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
+            plan.scratch, opt_.prec, plan.flops);
 }
 
 // ============================================================ Davidson
@@ -1284,9 +1271,10 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
       A[(size_t)1 * M + 1] = w[m - 2];
       m = 2;
     }
-    // new direction t = r, orthogonalised twice against V
+    // new direction t = (D - E)^-1 r, orthogonalised twice against V
     double* t = V + (size_t)m * len;
-    be_->copy_d2d(t, r, len * sizeof(double));
+    if (plan.diag) be_->precondition(t, r, plan.diag, e, len);
+    else be_->copy_d2d(t, r, len * sizeof(double));
     for (int pass = 0; pass < 2; ++pass) {
       be_->dots(V, m, len, len, t, dc);
       be_->copy_d2h(tmpv.data(), dc, m * sizeof(double));
@@ -1347,10 +1335,10 @@ std::vector<int> select(std::vector<Cand>& c, int D) {
 }
 }  // namespace
 
-// rho per sector of the enlarged block being truncated; returns Ut pointers
-// (device, rows = kept eigenvectors) and kept counts; discarded weight out.
-double Engine::decimate(Block& enl, const HPsiPlan& plan, const double* psi, bool left,
-                        std::vector<int>& kept, std::vector<double*>& ut, void** storage) {
+// rho per sector of the enlarged block being truncated, its eigenvectors, the
+// selection of D multiplets; returns the kept eigenvectors (rows) per sector.
+std::unique_ptr<SavedU> Engine::decimate(Block& enl, const HPsiPlan& plan, const double* psi,
+                                         bool left, double* trunc) {
   const Basis& B = enl.ops->basis;
   const PsiLayout& P = plan.psi;
   size_t tot = 0;
@@ -1359,7 +1347,6 @@ double Engine::decimate(Block& enl, const HPsiPlan& plan, const double* psi, boo
     roff[s] = tot;
     tot += (size_t)B.sec[s].dim * B.sec[s].dim;
   }
-  // rho, eigenvectors, eigenvalues in one buffer
   size_t wtot = B.total;
   double* buf = (double*)be_->alloc((2 * tot + wtot) * sizeof(double));
   be_->memset0(buf, (2 * tot + wtot) * sizeof(double));
@@ -1398,17 +1385,231 @@ double Engine::decimate(Block& enl, const HPsiPlan& plan, const double* psi, boo
       cands.push_back({lam, B.sec[s].n, B.sec[s].j, r, (int)s});
     }
   auto keep = select(cands, opt_.D);
-  kept.assign(B.sec.size(), 0);
+  auto U = std::make_unique<SavedU>();
+  U->be = be_;
+  U->enl = B;
+  U->comps = enl.comps;
+  if (enl.parent) U->parent = *enl.parent;
+  U->kept.assign(B.sec.size(), 0);
   double kw = 0.0;
   for (int i : keep) {
-    kept[cands[i].sec] = std::max(kept[cands[i].sec], cands[i].rank + 1);
+    U->kept[cands[i].sec] = std::max(U->kept[cands[i].sec], cands[i].rank + 1);
     kw += cands[i].lam;
   }
-  // ranks kept per sector are a prefix (eigenvalues descending)
-  ut.assign(B.sec.size(), nullptr);
-  for (size_t s = 0; s < B.sec.size(); ++s) ut[s] = vec + roff[s];
-  *storage = buf;
-  return std::max(0.0, total - kw);
+  // compact copy of the kept rows (eigenvalues descending: a prefix of rows)
+  U->off.assign(B.sec.size(), 0);
+  U->map.assign(B.sec.size(), -1);
+  size_t uo = 0;
+  int off = 0;
+  for (size_t s = 0; s < B.sec.size(); ++s) {
+    U->off[s] = uo;
+    if (U->kept[s] > 0) {
+      U->map[s] = (int)U->next.sec.size();
+      U->next.sec.push_back({B.sec[s].n, B.sec[s].j, U->kept[s], off});
+      off += U->kept[s];
+    }
+    uo += (size_t)U->kept[s] * B.sec[s].dim;
+  }
+  U->next.total = off;
+  U->buf = (double*)be_->alloc(std::max<size_t>(uo, 1) * sizeof(double));
+  for (size_t s = 0; s < B.sec.size(); ++s)
+    if (U->kept[s] > 0)
+      be_->copy_d2d(U->buf + U->off[s], vec + roff[s], (size_t)U->kept[s] * B.sec[s].dim * sizeof(double));
+  be_->sync();
+  be_->free(buf);
+  *trunc = std::max(0.0, total - kw);
+  return U;
+}
+
+// ============================================================ wavefunction guess
+namespace {
+// <((l s) a, r) S | (l, (s r) b) S>, all doubled
+double recouple(int l, int s, int r, int a, int b, int S) {
+  double six = wigner6j(l, s, a, r, S, b);
+  if (six == 0.0) return 0.0;
+  return phase2(l + s + r + S) * std::sqrt((a + 1.0) * (b + 1.0)) * six;
+}
+}  // namespace
+
+void Engine::save_prev(int bond, const Block& Le, const Block& Re, const HPsiPlan& plan,
+                       const double* psi) {
+  if (prev_.psi) be_->free(prev_.psi);
+  prev_.valid = true;
+  prev_.bond = bond;
+  prev_.Lb = Le.ops->basis;
+  prev_.Rb = Re.ops->basis;
+  prev_.Lc = Le.comps;
+  prev_.Rc = Re.comps;
+  prev_.blk.clear();
+  for (auto& b : plan.psi.blk) prev_.blk.push_back({b.a, b.b, b.rows, b.cols, (int)b.off});
+  prev_.len = plan.psi.size;
+  prev_.psi = (double*)be_->alloc(std::max<size_t>(prev_.len, 1) * sizeof(double));
+  be_->copy_d2d(prev_.psi, psi, prev_.len * sizeof(double));
+}
+
+// Predicted two-site wavefunction of bond `bond` from the state of the
+// previous bond (one step of the sweep): project with the new block's kept
+// eigenvectors, recouple the site that changes side (6j), expand the other
+// block with its stored MPS tensor.  Falls back to zero (random start) when
+// no previous state exists; the first bond uses the initial product state.
+void Engine::guess(int bond, bool l2r, const Block& Le, const Block& Re, const HPsiPlan& plan,
+                   double* psi) {
+  be_->memset0(psi, plan.psi.size * sizeof(double));
+  const PsiLayout& P = plan.psi;
+  const Basis& LB = Le.ops->basis;
+  const Basis& RB = Re.ops->basis;
+  if (!prev_.valid) {
+    // product state: L' = site 0 multiplet occ[0], R' = (site 1 (x) R(2)) multiplet path[1]
+    if (bond != 0) return;
+    int a = LB.find(occ_[0], kSiteJ[occ_[0]]);
+    int nr = 0;
+    for (int p = 1; p < n_; ++p) nr += occ_[p];
+    int b = RB.find(nr, path_[1]);
+    if (a < 0 || b < 0) return;
+    int pi = P.find(a, b);
+    if (pi < 0) return;
+    int ca = -1, cb = -1;
+    for (auto& c : Le.comps)
+      if (c.esec == a && c.site == occ_[0]) ca = c.eoff;
+    for (auto& c : Re.comps)
+      if (c.esec == b && c.site == occ_[1] && c.bsec == 0) cb = c.eoff;
+    if (ca < 0 || cb < 0) return;
+    double one = 1.0;
+    be_->copy_h2d(psi + P.blk[pi].off + (size_t)ca * P.blk[pi].cols + cb, &one, sizeof(double));
+    return;
+  }
+  const int S = two_s_;
+  (void)l2r;  // the move follows the position of the previous bond (turns included)
+  if (prev_.bond == bond - 1) {
+    const SavedU& U = *LU_[bond];          // L'(bond-1) -> L_[bond]
+    const SavedU& V = *RU_[n_ - bond - 1]; // E ~ R'(bond) -> R_[n-bond-1]
+    const Basis& Lnew = U.next;            // L_[bond]
+    const Basis& Rmid = V.next;            // R_[n-bond-1] = parent of prev R'
+    // phi(l, b) = Ut_a psi(a, b)
+    PsiLayout phiL = make_psi(Lnew, prev_.Rb, n_elec_, S);
+    PsiLayout mid = make_psi(LB, Rmid, n_elec_, S);
+    double* phi = (double*)be_->alloc(std::max<size_t>(phiL.size, 1) * sizeof(double));
+    double* psm = (double*)be_->alloc(std::max<size_t>(mid.size, 1) * sizeof(double));
+    be_->memset0(phi, std::max<size_t>(phiL.size, 1) * sizeof(double));
+    be_->memset0(psm, std::max<size_t>(mid.size, 1) * sizeof(double));
+    GemmBuilder g1;
+    for (auto& b : prev_.blk) {
+      int a = b[0], bb = b[1];
+      int l = U.map[a];
+      if (l < 0) continue;
+      int pi = phiL.find(l, bb);
+      if (pi < 0) continue;
+      g1.add(phi + phiL.blk[pi].off, U.kept[a], b[3], b[3],
+             GemmSeg{U.ut(a), prev_.psi + b[4], b[2], b[2], b[3], 0, 0, 1.0});
+    }
+    g1.run(be_, Precision::FP64);
+    // recouple the site between the blocks
+    PlaceBuilder pb;
+    for (auto& pbk : phiL.blk) {
+      int l = pbk.a, bb = pbk.b;
+      for (auto& c : prev_.Rc) {
+        if (c.esec != bb) continue;
+        int sg = c.site, r = c.bsec;
+        for (auto& cp : Le.comps) {
+          if (cp.bsec != l || cp.site != sg) continue;
+          int ap = cp.esec;
+          int mi = mid.find(ap, r);
+          if (mi < 0) continue;
+          double co = recouple(Lnew.sec[l].j, kSiteJ[sg], Rmid.sec[r].j, LB.sec[ap].j,
+                               prev_.Rb.sec[bb].j, S);
+          if (co == 0.0) continue;
+          double* d = psm + mid.blk[mi].off + (size_t)cp.eoff * mid.blk[mi].cols;
+          const double* src = phi + pbk.off + c.eoff;
+          pb.add(d, Lnew.sec[l].dim, Rmid.sec[r].dim, mid.blk[mi].cols,
+                 PlaceSeg{src, pbk.cols, 0, co});
+        }
+      }
+    }
+    pb.run(be_);
+    // expand the right block: psi(a', e) = psm(a', r(e)) Ut_e
+    GemmBuilder g2;
+    for (size_t e = 0; e < V.enl.sec.size(); ++e) {
+      int r = V.map[e];
+      if (r < 0) continue;
+      int eb = RB.find(V.enl.sec[e].n, V.enl.sec[e].j);
+      if (eb < 0) continue;
+      for (auto& mb : mid.blk) {
+        if (mb.b != r) continue;
+        int pi = P.find(mb.a, eb);
+        if (pi < 0) continue;
+        g2.add(psi + P.blk[pi].off, mb.rows, RB.sec[eb].dim, RB.sec[eb].dim,
+               GemmSeg{psm + mb.off, V.ut((int)e), V.kept[e], mb.cols, RB.sec[eb].dim, 0, 0, 1.0});
+      }
+    }
+    g2.run(be_, Precision::FP64);
+    be_->sync();
+    be_->free(phi);
+    be_->free(psm);
+  } else if (prev_.bond == bond + 1) {
+    const SavedU& V = *RU_[n_ - bond - 2];  // R'(bond+1) -> R_[n-bond-2]
+    const SavedU& U = *LU_[bond + 1];       // E ~ L'(bond) -> L_[bond+1]
+    const Basis& Rnew = V.next;
+    const Basis& Lmid = U.next;             // L_[bond+1] = parent of prev L'
+    // phi(a, r) = psi(a, b) Ut_b^T
+    PsiLayout phiL = make_psi(prev_.Lb, Rnew, n_elec_, S);
+    PsiLayout mid = make_psi(Lmid, RB, n_elec_, S);
+    double* phi = (double*)be_->alloc(std::max<size_t>(phiL.size, 1) * sizeof(double));
+    double* psm = (double*)be_->alloc(std::max<size_t>(mid.size, 1) * sizeof(double));
+    be_->memset0(phi, std::max<size_t>(phiL.size, 1) * sizeof(double));
+    be_->memset0(psm, std::max<size_t>(mid.size, 1) * sizeof(double));
+    GemmBuilder g1;
+    for (auto& b : prev_.blk) {
+      int a = b[0], bb = b[1];
+      int r = V.map[bb];
+      if (r < 0) continue;
+      int pi = phiL.find(a, r);
+      if (pi < 0) continue;
+      g1.add(phi + phiL.blk[pi].off, b[2], V.kept[bb], V.kept[bb],
+             GemmSeg{prev_.psi + b[4], V.ut(bb), b[3], b[3], b[3], 0, 1, 1.0});
+    }
+    g1.run(be_, Precision::FP64);
+    PlaceBuilder pb;
+    for (auto& pbk : phiL.blk) {
+      int a = pbk.a, r = pbk.b;
+      for (auto& c : prev_.Lc) {
+        if (c.esec != a) continue;
+        int l = c.bsec, sg = c.site;
+        for (auto& cp : Re.comps) {
+          if (cp.bsec != r || cp.site != sg) continue;
+          int bp = cp.esec;
+          int mi = mid.find(l, bp);
+          if (mi < 0) continue;
+          double co = recouple(Lmid.sec[l].j, kSiteJ[sg], Rnew.sec[r].j, prev_.Lb.sec[a].j,
+                               RB.sec[bp].j, S);
+          if (co == 0.0) continue;
+          double* d = psm + mid.blk[mi].off + cp.eoff;
+          const double* src = phi + pbk.off + (size_t)c.eoff * pbk.cols;
+          pb.add(d, Lmid.sec[l].dim, Rnew.sec[r].dim, mid.blk[mi].cols,
+                 PlaceSeg{src, pbk.cols, 0, co});
+        }
+      }
+    }
+    pb.run(be_);
+    // expand the left block: psi(a'', b') = Ut_{a''}^T psm(l(a''), b')
+    GemmBuilder g2;
+    for (size_t e = 0; e < U.enl.sec.size(); ++e) {
+      int l = U.map[e];
+      if (l < 0) continue;
+      int ea = LB.find(U.enl.sec[e].n, U.enl.sec[e].j);
+      if (ea < 0) continue;
+      for (auto& mb : mid.blk) {
+        if (mb.a != l) continue;
+        int pi = P.find(ea, mb.b);
+        if (pi < 0) continue;
+        g2.add(psi + P.blk[pi].off, LB.sec[ea].dim, mb.cols, mb.cols,
+               GemmSeg{U.ut((int)e), psm + mb.off, U.kept[e], LB.sec[ea].dim, mb.cols, 1, 0, 1.0});
+      }
+    }
+    g2.run(be_, Precision::FP64);
+    be_->sync();
+    be_->free(phi);
+    be_->free(psm);
+  }
 }
 
 // ============================================================ engine
@@ -1433,6 +1634,8 @@ Engine::Engine(Backend* be, int n, const double* h, const double* eri, double e_
   if (path_[0] != two_s || path_[n] != 0) throw std::invalid_argument("bad initial spin path");
   L_.resize(n + 1);
   R_.resize(n + 1);
+  LU_.resize(n + 1);
+  RU_.resize(n + 1);
   L_[0] = vacuum(true);
   L_[0]->normal = left_normal(0);
   if (!L_[0]->normal) {
@@ -1473,14 +1676,23 @@ void Engine::build_initial_right() {
     int m = eb.sec[target].dim;
     std::vector<double> row(m, 0.0);
     row[eoff] = 1.0;
-    std::vector<double*> ut(eb.sec.size(), nullptr);
-    double* u = (double*)be_->alloc(m * sizeof(double));
-    be_->copy_h2d(u, row.data(), m * sizeof(double));
-    ut[target] = u;
+    auto U = std::make_unique<SavedU>();
+    U->be = be_;
+    U->enl = eb;
+    U->comps = e->comps;
+    U->parent = R_[r - 1]->ops->basis;
+    U->kept = kept;
+    U->map.assign(eb.sec.size(), -1);
+    U->map[target] = 0;
+    U->off.assign(eb.sec.size(), 0);
+    U->next.sec.push_back({eb.sec[target].n, eb.sec[target].j, 1, 0});
+    U->next.total = 1;
+    U->buf = (double*)be_->alloc(m * sizeof(double));
+    be_->copy_h2d(U->buf, row.data(), m * sizeof(double));
     bool sw = e->normal && !right_normal(r);
-    R_[r] = renormalize(*e, kept, ut, sw);
+    R_[r] = renormalize(*e, *U, sw);
+    RU_[r] = std::move(U);
     be_->sync();
-    be_->free(u);
   }
 }
 
@@ -1494,29 +1706,29 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   plan.in = (double*)be_->alloc(len * sizeof(double));
   plan.out = (double*)be_->alloc(len * sizeof(double));
   double* psi = (double*)be_->alloc(len * sizeof(double));
-  be_->memset0(psi, len * sizeof(double));
+  guess(i, l2r, *Le, *Re, plan, psi);
   plan_hpsi(*Le, *Re, plan);
   int its = 0;
   double e = davidson(plan, psi, &its) + e_core_;
   stats_.davidson_iters += its;
-  std::vector<int> kept;
-  std::vector<double*> ut;
-  void* store = nullptr;
   if (l2r) {
-    *trunc = decimate(*Le, plan, psi, true, kept, ut, &store);
+    auto U = decimate(*Le, plan, psi, true, trunc);
     bool sw = Le->normal && !left_normal(i + 1);
-    L_[i + 1] = renormalize(*Le, kept, ut, sw);
+    L_[i + 1] = renormalize(*Le, *U, sw);
+    LU_[i + 1] = std::move(U);
   } else {
-    *trunc = decimate(*Re, plan, psi, false, kept, ut, &store);
+    auto U = decimate(*Re, plan, psi, false, trunc);
     bool sw = Re->normal && !right_normal(n_ - i - 1);
-    R_[n_ - i - 1] = renormalize(*Re, kept, ut, sw);
+    R_[n_ - i - 1] = renormalize(*Re, *U, sw);
+    RU_[n_ - i - 1] = std::move(U);
   }
+  save_prev(i, *Le, *Re, plan, psi);
   be_->sync();
-  be_->free(store);
   be_->free(psi);
   be_->free(plan.in);
   be_->free(plan.out);
-  if (plan.X) be_->free(plan.X);
+  if (plan.dev) be_->free(plan.dev);
+  if (plan.diag) be_->free(plan.diag);
   last_bond_ = i;
   bond_e_.push_back(e);
   if (opt_.verbose)

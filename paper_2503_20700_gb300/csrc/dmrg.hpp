@@ -112,11 +112,30 @@ struct Block {
   const Basis* parent = nullptr;
 };
 
+// Transformation from an enlarged block to its renormalised block (the MPS
+// tensor of that bond in the block-sparse SU(2) form): for every enlarged
+// sector s the kept eigenvectors are the rows of a kept[s] x dim(s) matrix.
+struct SavedU {
+  Basis enl;                   // enlarged basis (block (x) site or site (x) block)
+  std::vector<EnlComp> comps;  // its components
+  Basis parent;                // basis of the block that was enlarged
+  Basis next;                  // basis of the renormalised block
+  std::vector<int> kept, map;  // per enlarged sector: kept count, new sector (-1)
+  std::vector<size_t> off;     // offset of each sector's rows in buf
+  double* buf = nullptr;
+  Backend* be = nullptr;
+  ~SavedU() {
+    if (be && buf) be->free(buf);
+  }
+  const double* ut(int s) const { return buf + off[s]; }
+};
+
 struct Options {
   int D = 64;
   int max_davidson_iter = 200;
   double davidson_tol = 1e-10;
-  Precision prec = Precision::FP64;
+  Precision prec = Precision::FP64;         // H_eff psi GEMMs
+  Precision prec_renorm = Precision::FP64;  // renormalisation / complementary GEMMs
   int max_space = 24;
   int verbose = 0;
 };
@@ -142,7 +161,10 @@ class Engine {
   double energy() const { return energy_; }
   int n() const { return n_; }
   void set_D(int D) { opt_.D = D; }
-  void set_precision(Precision p) { opt_.prec = p; }
+  void set_precision(Precision p, Precision pr) {
+    opt_.prec = p;
+    opt_.prec_renorm = pr;
+  }
   const std::vector<double>& bond_energies() const { return bond_e_; }
   // Multiplet count of the left block L(m) / right block R(m) (sites counted)
   int left_dim(int m) const;
@@ -165,6 +187,19 @@ class Engine {
   std::vector<double> bond_e_;
   int last_bond_ = -1;
   std::vector<int> occ_, path_;
+  std::vector<std::unique_ptr<SavedU>> LU_, RU_;
+  double* ones_ = nullptr;  // vector of ones (identity diagonals)
+  size_t ones_len_ = 0;  // LU_[m]: -> L_[m], RU_[m]: -> R_[m]
+  // two-site wavefunction of the last optimised bond (Davidson guess of the next one)
+  struct Prev {
+    bool valid = false;
+    int bond = -1;
+    Basis Lb, Rb;
+    std::vector<EnlComp> Lc, Rc;
+    std::vector<std::array<int, 5>> blk;  // (a, b, rows, cols, off)
+    double* psi = nullptr;
+    size_t len = 0;
+  } prev_;
 
   double hh(int p, int q) const { return h_[(size_t)p * n_ + q]; }
   double g(int p, int q, int r, int s) const {
@@ -179,16 +214,19 @@ class Engine {
   void place_terms(const Block& b, const OpSet* tmp, Block& e,
                    const std::vector<std::pair<OpKey, struct Term>>& terms);
   void build_comp_from_normal(const Block& b, OpSet& dst, const std::vector<OpKey>& keys);
-  std::unique_ptr<Block> renormalize(Block& enl, const std::vector<int>& kept,
-                                     const std::vector<double*>& ut, bool switch_to_comp);
+  std::unique_ptr<Block> renormalize(Block& enl, const SavedU& U, bool switch_to_comp);
   void build_initial_right();
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);
   size_t x_budget_elems() const;
   double davidson(struct HPsiPlan& plan, double* psi, int* iters);
-  double decimate(Block& enl, const struct HPsiPlan& plan, const double* psi, bool left,
-                  std::vector<int>& kept, std::vector<double*>& ut, void** storage);
+  std::unique_ptr<SavedU> decimate(Block& enl, const struct HPsiPlan& plan, const double* psi,
+                                   bool left, double* trunc);
   double optimize_bond(int i, bool left_to_right, double* trunc);
+  void guess(int bond, bool l2r, const Block& Le, const Block& Re, const struct HPsiPlan& plan,
+             double* psi);
+  void save_prev(int bond, const Block& Le, const Block& Re, const struct HPsiPlan& plan,
+                 const double* psi);
 
  public:
   // ---- accounting

@@ -34,6 +34,7 @@ def bind(lib):
     lib.dmrg_eigh_batched.argtypes = [dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, dp, dp,
                                       ctypes.c_int]
     lib.dmrg_eigh_batched.restype = ctypes.c_int
+    _bind_casscf(lib)
     _lib = lib
     return lib
 
@@ -82,3 +83,74 @@ def eigh_batched(mats, device=0):
         o += n * n
         ow += n
     return out
+
+
+# ---------------------------------------------------------------- CAS-SCF
+def _bind_casscf(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.c_int
+    lib.casscf_rotation.argtypes = [dp, I, dp, I]
+    lib.casscf_rotation_backward.argtypes = [dp, dp, I, dp, I]
+    lib.casscf_transform.argtypes = [dp, dp, dp, I, I, dp, dp, I]
+    lib.casscf_active_space.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, I]
+    lib.casscf_orbital_gradient.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, dp, I]
+    for f in ("casscf_rotation", "casscf_rotation_backward", "casscf_transform",
+              "casscf_active_space", "casscf_orbital_gradient"):
+        getattr(lib, f).restype = I
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _call(name, *args):
+    from . import load, DmrgError
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        raise DmrgError(st, lib.dmrg_last_error(None).decode())
+
+
+def rotation(K, device=0):
+    """R = expm(-K) on the device (U = exp(-kappa))."""
+    K = _c(K)
+    R = np.zeros_like(K)
+    _call("casscf_rotation", _dp(K), K.shape[0], _dp(R), device)
+    return R
+
+
+def rotation_backward(K, G, device=0):
+    """dE/dkappa (antisymmetric) for R = expm(-K), given G = dE/dR."""
+    K, G = _c(K), _c(G)
+    dK = np.zeros_like(K)
+    _call("casscf_rotation_backward", _dp(K), _dp(G), K.shape[0], _dp(dK), device)
+    return dK
+
+
+def transform(R, h, L, device=0):
+    """(R^T h R, R^T L^k R) on the device."""
+    R, h, L = _c(R), _c(h), _c(L)
+    ho, Lo = np.zeros_like(h), np.zeros_like(L)
+    _call("casscf_transform", _dp(R), _dp(h), _dp(L), L.shape[0], h.shape[0], _dp(ho), _dp(Lo), device)
+    return ho, Lo
+
+
+def active_space(h, L, ncore, ncas, device=0):
+    """(e_core, h_act, eri_act) of the active space."""
+    h, L = _c(h), _c(L)
+    e = np.zeros(1)
+    ha = np.zeros((ncas, ncas))
+    ea = np.zeros((ncas,) * 4)
+    _call("casscf_active_space", _dp(h), _dp(L), L.shape[0], h.shape[0], ncore, ncas, _dp(e),
+          _dp(ha), _dp(ea), device)
+    return float(e[0]), ha, ea
+
+
+def orbital_gradient(h, L, ncore, ncas, gamma, Gamma, device=0, with_fock=False):
+    """grad = 2 (F - F^T) (active-active zero) from the spin-free RDMs."""
+    h, L, gamma, Gamma = _c(h), _c(L), _c(gamma), _c(Gamma)
+    g = np.zeros_like(h)
+    F = np.zeros_like(h)
+    _call("casscf_orbital_gradient", _dp(h), _dp(L), L.shape[0], h.shape[0], ncore, ncas,
+          _dp(gamma), _dp(Gamma), _dp(g), _dp(F), device)
+    return (g, F) if with_fock else g
