@@ -212,7 +212,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cas40")
     ap.add_argument("--D", type=int, default=2048)
-    ap.add_argument("--precision", default="split", choices=["split", "fp64"])
+    ap.add_argument("--precision", default="split", choices=["split", "split-all", "fp64"],
+                    help="split: 3xTF32 in H_eff psi, renormalisation in FP64; "
+                         "split-all: 3xTF32 also in renormalisation; fp64: all FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-7)
@@ -225,7 +227,7 @@ def main():
     rank, world, dist = dist_init(args.gpus)
     device = int(os.environ.get("LOCAL_RANK", "0"))
     wl = workload(args.workload)
-    prec = pkg.SPLIT_TF32 if args.precision == "split" else pkg.FP64
+    prec = {"split": pkg.SPLIT_HPSI, "split-all": pkg.SPLIT_TF32, "fp64": pkg.FP64}[args.precision]
     W, K = max(3, args.warmup), max(1, args.steps)
     ds = ramp(args.D, W)
     g = pkg.DMRG(wl["h"], eri=wl["eri"], chol=wl["chol"], n_elec=wl["n_elec"], two_s=wl["two_s"],
@@ -240,9 +242,12 @@ def main():
     flops, dev_ms, energies = 0.0, 0.0, []
     with Clocks(device) as clk:
         t0 = time.perf_counter()
+        phases = None
         for _ in range(K):
             e, _ = g.sweep(1)
             st = g.stats()
+            ph = g.phases()
+            phases = ph if phases is None else {k: phases[k] + ph[k] for k in ph}
             flops += st["hpsi_flops"]
             dev_ms += g.sweep_device_ms()
             energies.append(e)
@@ -257,7 +262,7 @@ def main():
 
     # ---- roofline of the dominant kernel (the H_eff psi GEMM)
     pk, src = peaks()
-    if prec == pkg.SPLIT_TF32:
+    if prec != pkg.FP64:
         # 3xTF32: three TF32 tensor products per algorithmic product; TF32 peak =
         # measured dense bf16 peak x the nominal TF32/BF16 ratio (1.1/2.25)
         peak_tf = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
@@ -267,9 +272,9 @@ def main():
         peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
     avg_ms = k_ms / max(1, k_launch)
     achieved = (k_flops / max(1, k_launch)) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
-    roof = {"bound": "tensor" if prec == pkg.SPLIT_TF32 else "alu", "achieved": achieved,
+    roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf if peak_tf else None,
-            "traffic": None, "kernel": "gemm_tf32x3_mma" if prec == pkg.SPLIT_TF32 else "gemm_f64_kernel",
+            "traffic": None, "kernel": "hpsi_tf32x3_kernel" if prec != pkg.FP64 else "hpsi_f64_kernel",
             "launches": k_launch, "avg_launch_ms": avg_ms, "peak_source": peak_note}
 
     # ---- end to end through the public API with host buffers: dmrg_init
@@ -299,7 +304,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
                 "warmup": W, "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "tf32x3" if prec == pkg.SPLIT_TF32 else "f64", "data": "synthetic",
+                "dtype": "tf32x3" if prec != pkg.FP64 else "f64", "data": "synthetic",
                 "config": {"workload": wl["desc"], "D": args.D, "warmup_D": ds,
                            "precision": args.precision, "davidson_tol": args.tol,
                            "parallelism": "replicas" if world > 1 else "single",
@@ -308,6 +313,7 @@ def main():
                 "sweep_energy": energies[-1], "sweep_energies": energies,
                 "sweep_seconds": t_max / K, "wall_seconds": wall,
                 "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
+                "phase_seconds": phases, "davidson_iters": st["davidson_iters"],
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line))

@@ -134,6 +134,11 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
 dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
                               int64_t* launches);
 
+/* Wall time (s) of the phases of the last sweep: [0] blocking (enlarged
+ * operators), [1] H_eff psi task planning, [2] Davidson, [3] decimation,
+ * [4] renormalisation, [5] wavefunction prediction.  t must hold 6 values. */
+dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* ctx, double* t);
+
 /* Device time of the last sweep in milliseconds, measured with CUDA events
  * recorded on the library's stream at the start and the end of the sweep. */
 dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* ctx, double* ms);
@@ -185,6 +190,38 @@ dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, i
                               double* C, int64_t c_len, const dmrg_gemm_group* groups,
                               int n_groups, const dmrg_gemm_seg* segs, int n_segs, int precision,
                               int device);
+
+/* One item of the fused H_eff psi contraction: alpha * op(A) * P * op(B)^T
+ * with op(A) m x ka (trans_a: A stored ka x m), P ka x kb (row length ldp) and
+ * op(B)^T kb x n (trans_b = 0: B stored n x kb; trans_b = 1: B stored kb x n).
+ * a_identity / b_identity replace A / B by the identity (offsets ignored). */
+typedef struct {
+  int64_t a_off, p_off, b_off;
+  int lda, ldp, ldb, trans_a, trans_b, ka, kb, a_identity, b_identity;
+  double alpha;
+} dmrg_hpsi_item;
+
+/* Output block: rows m, cols n at c_off (row length ldc); its items are
+ * item[item_begin .. item_begin + item_count). */
+typedef struct {
+  int64_t c_off;
+  int m, n, ldc, item_begin, item_count;
+} dmrg_hpsi_block;
+
+/*
+ * dmrg_hpsi_contract -- one launch of the fused H_eff psi kernel:
+ *   C_block += sum_items alpha op(A) P op(B)^T   (Sec. II.B: the two-block
+ * effective Hamiltonian sigma = sum_t c_t A_t psi B_t^T over sector blocks),
+ * with the intermediate A P kept on chip and item chunks reduced in a fixed
+ * order.  Host buffers in/out (C updated in place); all offsets are checked
+ * against the buffer lengths before any launch.  precision: DMRG_FP64 or
+ * DMRG_SPLIT_TF32.
+ */
+dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, int64_t p_len,
+                               const double* B, int64_t b_len, double* C, int64_t c_len,
+                               const dmrg_hpsi_block* blocks, int n_blocks,
+                               const dmrg_hpsi_item* items, int n_items, int precision,
+                               int device);
 
 /*
  * dmrg_eigh_batched -- symmetric eigendecompositions in float64 on the device

@@ -78,6 +78,8 @@ def load(path=None):
     lib.dmrg_profile.restype = I
     lib.dmrg_kernel_stats.argtypes = [P, I, dp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.dmrg_kernel_stats.restype = I
+    lib.dmrg_last_sweep_phases.argtypes = [P, dp]
+    lib.dmrg_last_sweep_phases.restype = I
     lib.dmrg_last_sweep_device_ms.argtypes = [P, dp]
     lib.dmrg_last_sweep_device_ms.restype = I
     lib.dmrg_memory.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -188,6 +190,12 @@ class DMRG:
         _check(self._lib, self._ctx, self._lib.dmrg_kernel_stats(
             self._ctx, which, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
         return ms.value, fl.value, n.value
+
+    def phases(self):
+        """Wall seconds of (enlarge, plan, davidson, decimate, renormalize, guess)."""
+        t = np.zeros(6)
+        _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_phases(self._ctx, _dp(t)))
+        return dict(zip(["enlarge", "plan", "davidson", "decimate", "renormalize", "guess"], t.tolist()))
 
     def sweep_device_ms(self):
         ms = ctypes.c_double()

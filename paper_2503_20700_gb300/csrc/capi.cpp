@@ -10,6 +10,7 @@
 
 #include "../../include/dmrgscf.h"
 #include "casscf.hpp"
+#include "hpsi_fused.cuh"
 #include "dmrg.hpp"
 
 struct dmrg_ctx {
@@ -242,6 +243,19 @@ dmrg_status dmrg_kernel_stats(dmrg_ctx* c, int which, double* ms, double* flops,
   return DMRG_OK;
 }
 
+dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* c, double* t) {
+  if (!c || !c->eng || !t) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
+  if (c->sweeps_done == 0) return fail(const_cast<dmrg_ctx*>(c), DMRG_ESTATE, "no sweep has run");
+  const auto& s = c->last;
+  t[0] = s.t_enlarge;
+  t[1] = s.t_plan;
+  t[2] = s.t_davidson;
+  t[3] = s.t_decimate;
+  t[4] = s.t_renorm;
+  t[5] = s.t_guess;
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* c, double* ms) {
   if (!c || !c->eng || !ms) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
   if (c->sweeps_done == 0) return fail(const_cast<dmrg_ctx*>(c), DMRG_ESTATE, "no sweep has run");
@@ -324,6 +338,115 @@ dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, i
     be->free(dA);
     be->free(dB);
     be->free(dC);
+    be->sync();
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
+  }
+  return DMRG_OK;
+}
+
+namespace {
+// host-side validation of an H_eff psi item list against buffer lengths
+const char* check_hpsi(int64_t a_len, int64_t p_len, int64_t b_len, int64_t c_len,
+                       const dmrg_hpsi_block* blocks, int nb, const dmrg_hpsi_item* items, int ni) {
+  auto span_ok = [](int64_t off, int64_t rows, int64_t cols, int64_t ld, int64_t len) {
+    if (rows <= 0 || cols <= 0) return true;
+    return off >= 0 && ld >= cols && off + (rows - 1) * ld + cols <= len;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const auto& B = blocks[b];
+    if (B.m < 0 || B.n < 0 || B.item_begin < 0 || B.item_count < 0 || B.item_begin + B.item_count > ni)
+      return "bad block";
+    if (!span_ok(B.c_off, B.m, B.n, B.ldc, c_len)) return "C block out of range";
+    for (int i = B.item_begin; i < B.item_begin + B.item_count; ++i) {
+      const auto& I = items[i];
+      if (I.ka < 0 || I.kb < 0) return "bad item sizes";
+      if (I.a_identity && I.ka != B.m) return "identity A needs ka == m";
+      if (I.b_identity && I.kb != B.n) return "identity B needs kb == n";
+      if (!I.a_identity) {
+        int64_t r = I.trans_a ? I.ka : B.m, c = I.trans_a ? B.m : I.ka;
+        if (!span_ok(I.a_off, r, c, I.lda, a_len)) return "A block out of range";
+      }
+      if (!span_ok(I.p_off, I.ka, I.kb, I.ldp, p_len)) return "P block out of range";
+      if (!I.b_identity) {
+        int64_t r = I.trans_b ? I.kb : B.n, c = I.trans_b ? B.n : I.kb;
+        if (!span_ok(I.b_off, r, c, I.ldb, b_len)) return "B block out of range";
+      }
+    }
+  }
+  return nullptr;
+}
+
+void to_device_lists(const dmrg_hpsi_block* blocks, int nb, const dmrg_hpsi_item* items, int ni,
+                     const double* dA, const double* dP, const double* dB, double* dC,
+                     std::vector<dmrg::HpsiBlock>& hb, std::vector<dmrg::HpsiItem>& hi, double* flops) {
+  hb.resize(nb);
+  hi.resize(ni);
+  double fl = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    hb[b] = {dC + blocks[b].c_off, blocks[b].m, blocks[b].n, blocks[b].ldc, blocks[b].item_begin,
+             blocks[b].item_count};
+    for (int i = blocks[b].item_begin; i < blocks[b].item_begin + blocks[b].item_count; ++i) {
+      const auto& I = items[i];
+      hi[i] = {I.a_identity ? nullptr : dA + I.a_off, dP + I.p_off, I.b_identity ? nullptr : dB + I.b_off,
+               I.lda, I.ldp, I.ldb, I.trans_a, I.trans_b, I.ka, I.kb, I.alpha};
+      if (!I.a_identity) fl += 2.0 * blocks[b].m * I.ka * I.kb;
+      if (!I.b_identity) fl += 2.0 * blocks[b].m * blocks[b].n * I.kb;
+    }
+  }
+  if (flops) *flops = fl;
+}
+}  // namespace
+
+dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, int64_t p_len,
+                               const double* B, int64_t b_len, double* C, int64_t c_len,
+                               const dmrg_hpsi_block* blocks, int n_blocks, const dmrg_hpsi_item* items,
+                               int n_items, int precision, int device) {
+  if (!A || !P || !B || !C || (!blocks && n_blocks) || (!items && n_items) || n_blocks < 0 || n_items < 0)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  if (precision < 0 || precision > 1) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
+  if (const char* m = check_hpsi(a_len, p_len, b_len, c_len, blocks, n_blocks, items, n_items))
+    return fail(nullptr, DMRG_EINVAL, m);
+  std::string err;
+  std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  try {
+    auto up = [&](const double* h, int64_t n) {
+      double* d = (double*)be->alloc(std::max<int64_t>(n, 1) * sizeof(double));
+      be->copy_h2d(d, h, n * sizeof(double));
+      return d;
+    };
+    double* dA = up(A, a_len);
+    double* dP = up(P, p_len);
+    double* dB = up(B, b_len);
+    double* dC = up(C, c_len);
+    std::vector<dmrg::HpsiBlock> hb;
+    std::vector<dmrg::HpsiItem> hi;
+    double fl = 0.0;
+    to_device_lists(blocks, n_blocks, items, n_items, dA, dP, dB, dC, hb, hi, &fl);
+    long long tile_items = 0;
+    for (auto& b : hb) tile_items += (long long)b.item_count * ((b.m + 63) / 64) * ((b.n + 63) / 64);
+    int max_items = (int)std::max<long long>(4, tile_items / (8 * 152) + 1);
+    std::vector<dmrg::HpsiTask> tasks;
+    std::vector<dmrg::HpsiReduce> reds;
+    size_t scr = dmrg::hpsi_plan_tasks(hb, max_items, tasks, reds);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t ob = 0, oi = al(hb.size() * sizeof(dmrg::HpsiBlock));
+    size_t ot = al(oi + hi.size() * sizeof(dmrg::HpsiItem));
+    size_t orr = al(ot + tasks.size() * sizeof(dmrg::HpsiTask));
+    size_t os = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
+    char* d = (char*)be->alloc(os + scr * sizeof(double) + 256);
+    if (!hb.empty()) be->copy_h2d(d + ob, hb.data(), hb.size() * sizeof(dmrg::HpsiBlock));
+    if (!hi.empty()) be->copy_h2d(d + oi, hi.data(), hi.size() * sizeof(dmrg::HpsiItem));
+    if (!tasks.empty()) be->copy_h2d(d + ot, tasks.data(), tasks.size() * sizeof(dmrg::HpsiTask));
+    if (!reds.empty()) be->copy_h2d(d + orr, reds.data(), reds.size() * sizeof(dmrg::HpsiReduce));
+    be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
+             (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
+             (int)reds.size(), (double*)(d + os),
+             precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32, fl);
+    be->copy_d2h(C, dC, c_len * sizeof(double));
+    be->sync();
+    for (void* q : {(void*)dA, (void*)dP, (void*)dB, (void*)dC, (void*)d}) be->free(q);
     be->sync();
   } catch (const std::exception& e) {
     return translate(nullptr, e);

@@ -147,6 +147,9 @@ struct SweepStats {
   double hpsi_flops = 0.0;
   double hpsi_seconds = 0.0;
   int hpsi_calls = 0;
+  // wall time per phase of the sweep (seconds, host clock around device-synchronised steps)
+  double t_enlarge = 0.0, t_plan = 0.0, t_davidson = 0.0, t_decimate = 0.0, t_renorm = 0.0,
+         t_guess = 0.0;
 };
 
 class Engine {

@@ -20,6 +20,19 @@ class GemmGroup(ctypes.Structure):
                 ("ldc", ctypes.c_int), ("seg_begin", ctypes.c_int), ("seg_count", ctypes.c_int)]
 
 
+class HpsiItem(ctypes.Structure):
+    _fields_ = [("a_off", ctypes.c_int64), ("p_off", ctypes.c_int64), ("b_off", ctypes.c_int64),
+                ("lda", ctypes.c_int), ("ldp", ctypes.c_int), ("ldb", ctypes.c_int),
+                ("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int), ("ka", ctypes.c_int),
+                ("kb", ctypes.c_int), ("a_identity", ctypes.c_int), ("b_identity", ctypes.c_int),
+                ("alpha", ctypes.c_double)]
+
+
+class HpsiBlock(ctypes.Structure):
+    _fields_ = [("c_off", ctypes.c_int64), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("ldc", ctypes.c_int), ("item_begin", ctypes.c_int), ("item_count", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -34,6 +47,11 @@ def bind(lib):
     lib.dmrg_eigh_batched.argtypes = [dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, dp, dp,
                                       ctypes.c_int]
     lib.dmrg_eigh_batched.restype = ctypes.c_int
+    lib.dmrg_hpsi_contract.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int64, dp, ctypes.c_int64,
+                                       dp, ctypes.c_int64, ctypes.POINTER(HpsiBlock), ctypes.c_int,
+                                       ctypes.POINTER(HpsiItem), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int]
+    lib.dmrg_hpsi_contract.restype = ctypes.c_int
     _bind_casscf(lib)
     _lib = lib
     return lib
@@ -58,6 +76,28 @@ def grouped_gemm(A, B, C, groups, segs, precision=0, device=0):
     sa = (GemmSeg * max(1, len(segs)))(*[GemmSeg(*s) for s in segs])
     st = lib.dmrg_grouped_gemm(_dp(A), A.size, _dp(B), B.size, _dp(C), C.size, ga, len(groups),
                                sa, len(segs), precision, device)
+    if st != 0:
+        raise DmrgError(st, lib.dmrg_last_error(None).decode())
+    return C
+
+
+def hpsi_contract(A, P, B, C, blocks, items, precision=0, device=0):
+    """C (float64, in place) += fused H_eff psi items; see dmrgscf.h.
+
+    blocks: list of (c_off, m, n, ldc, item_begin, item_count)
+    items:  list of (a_off, p_off, b_off, lda, ldp, ldb, trans_a, trans_b, ka, kb,
+                     a_identity, b_identity, alpha)
+    """
+    from . import load, DmrgError
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    assert C.dtype == np.float64 and C.flags.c_contiguous
+    ba = (HpsiBlock * max(1, len(blocks)))(*[HpsiBlock(*b) for b in blocks])
+    ia = (HpsiItem * max(1, len(items)))(*[HpsiItem(*i) for i in items])
+    st = lib.dmrg_hpsi_contract(_dp(A), A.size, _dp(P), P.size, _dp(B), B.size, _dp(C), C.size,
+                                ba, len(blocks), ia, len(items), precision, device)
     if st != 0:
         raise DmrgError(st, lib.dmrg_last_error(None).decode())
     return C

@@ -177,3 +177,79 @@ def test_eigh_against_numpy(pkg):
         assert np.abs(w - ref).max() < 1e-11 * max(1.0, np.abs(ref).max())
         assert np.abs(V @ M - w[:, None] * V).max() < 1e-10 * max(1.0, np.abs(ref).max())
         assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-12
+
+
+def random_hpsi_problem(rng, n_blocks, max_dim, max_items, big=False):
+    """Sector-block contraction sigma += alpha op(A) P op(B)^T with ragged
+    sizes (several 64-wide tiles and tails), both transposes, identities."""
+    A_parts, P_parts, B_parts = [], [], []
+    ao = po = bo = co = 0
+    blocks, items, refs = [], [], []
+    for _ in range(n_blocks):
+        m = int(rng.integers(1, max_dim))
+        n = int(rng.integers(1, max_dim))
+        ib = len(items)
+        ref = np.zeros((m, n))
+        for _ in range(int(rng.integers(1, max_items + 1))):
+            a_id = int(rng.random() < 0.15)
+            b_id = int(rng.random() < 0.15) if not a_id else 0
+            ka = m if a_id else int(rng.integers(1, max_dim))
+            kb = n if b_id else int(rng.integers(1, max_dim))
+            ta, tb = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+            alpha = float(rng.standard_normal())
+            Pm = rng.standard_normal((ka, kb))
+            if a_id:
+                Am = np.eye(m)
+                a_entry = (0, 1, 0)
+            else:
+                a = rng.standard_normal((ka, m) if ta else (m, ka))
+                Am = a.T if ta else a
+                a_entry = (ao, a.shape[1], ta)
+                A_parts.append(a.ravel())
+                ao += a.size
+            if b_id:
+                Bt = np.eye(n)
+                b_entry = (0, 1, 0)
+            else:
+                b = rng.standard_normal((kb, n) if tb else (n, kb))
+                Bt = b if tb else b.T          # op(B)^T, kb x n
+                b_entry = (bo, b.shape[1], tb)
+                B_parts.append(b.ravel())
+                bo += b.size
+            ref += alpha * Am @ Pm @ Bt
+            items.append((a_entry[0], po, b_entry[0], a_entry[1], kb, b_entry[1], a_entry[2],
+                          b_entry[2], ka, kb, a_id, b_id, alpha))
+            P_parts.append(Pm.ravel())
+            po += Pm.size
+        blocks.append((co, m, n, n, ib, len(items) - ib))
+        refs.append((co, m, n, ref))
+        co += m * n
+    cat = lambda v: np.concatenate(v) if v else np.zeros(1)
+    return cat(A_parts), cat(P_parts), cat(B_parts), co, blocks, items, refs
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-6)])
+def test_fused_hpsi_against_numpy(pkg, prec, tol):
+    rng = np.random.default_rng(11)
+    A, P, B, clen, blocks, items, refs = random_hpsi_problem(rng, 12, 150, 6)
+    C0 = rng.standard_normal(clen)
+    C = C0.copy()
+    pkg.ops.hpsi_contract(A, P, B, C, blocks, items, precision=prec)
+    for off, m, n, ref in refs:
+        got = (C - C0)[off:off + m * n].reshape(m, n)
+        assert np.abs(got - ref).max() <= tol * (np.abs(ref).max() + 1e-300) * 10
+
+
+def test_fused_hpsi_many_items_split_into_chunks(pkg):
+    """Blocks with hundreds of items: the launch splits them into chunks whose
+    partial tiles are reduced in a fixed order; results are bitwise
+    reproducible between two launches."""
+    rng = np.random.default_rng(5)
+    A, P, B, clen, blocks, items, refs = random_hpsi_problem(rng, 3, 70, 400)
+    C1 = np.zeros(clen)
+    C2 = np.zeros(clen)
+    pkg.ops.hpsi_contract(A, P, B, C1, blocks, items, precision=0)
+    pkg.ops.hpsi_contract(A, P, B, C2, blocks, items, precision=0)
+    assert np.array_equal(C1, C2)
+    for off, m, n, ref in refs:
+        assert np.abs(C1[off:off + m * n].reshape(m, n) - ref).max() < 1e-11 * np.abs(ref).max()
