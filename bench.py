@@ -212,12 +212,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cas40")
     ap.add_argument("--D", type=int, default=2048)
-    ap.add_argument("--precision", default="split", choices=["split", "split-all", "fp64"],
+    ap.add_argument("--precision", default="split", choices=["split", "split-tc", "split-all", "fp64"],
                     help="split: 3xTF32 in H_eff psi, renormalisation in FP64; "
                          "split-all: 3xTF32 also in renormalisation; fp64: all FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--verbose", type=int, default=0, help="library diagnostics on stderr (2: H_eff psi shapes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -227,11 +228,13 @@ def main():
     rank, world, dist = dist_init(args.gpus)
     device = int(os.environ.get("LOCAL_RANK", "0"))
     wl = workload(args.workload)
-    prec = {"split": pkg.SPLIT_HPSI, "split-all": pkg.SPLIT_TF32, "fp64": pkg.FP64}[args.precision]
+    prec = {"split": pkg.SPLIT_HPSI, "split-tc": pkg.SPLIT_HPSI_TC, "split-all": pkg.SPLIT_TF32,
+            "fp64": pkg.FP64}[args.precision]
     W, K = max(3, args.warmup), max(1, args.steps)
     ds = ramp(args.D, W)
     g = pkg.DMRG(wl["h"], eri=wl["eri"], chol=wl["chol"], n_elec=wl["n_elec"], two_s=wl["two_s"],
-                 D=ds[0], e_core=wl["e_core"], precision=prec, tol=args.tol, device=device)
+                 D=ds[0], e_core=wl["e_core"], precision=prec, tol=args.tol, device=device,
+                 verbose=args.verbose)
     for d in ds:
         g.set_bond_dim(d)
         g.sweep(1)
@@ -274,7 +277,7 @@ def main():
     achieved = (k_flops / max(1, k_launch)) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf if peak_tf else None,
-            "traffic": None, "kernel": "hpsi_tf32x3_kernel" if prec != pkg.FP64 else "hpsi_f64_kernel",
+            "traffic": None, "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
             "launches": k_launch, "avg_launch_ms": avg_ms, "peak_source": peak_note}
 
     # ---- end to end through the public API with host buffers: dmrg_init

@@ -51,8 +51,12 @@ typedef enum {
                            FP32 accumulation; Davidson, eigensolver and the
                            final reductions stay float64                      */
   DMRG_BF16X9 = 2,      /* reserved: BF16x9 split products (not available)   */
-  DMRG_SPLIT_HPSI = 3   /* 3xTF32 in the H_eff psi GEMMs only; renormalisation
+  DMRG_SPLIT_HPSI = 3,  /* 3xTF32 in the H_eff psi GEMMs only; renormalisation
                            and complementary-operator GEMMs in float64          */
+  DMRG_SPLIT_HPSI_TC = 4 /* as DMRG_SPLIT_HPSI, with the H_eff psi split products
+                           issued on the tcgen05 tensor cores (TMEM
+                           accumulators, 128 x 64 sigma tiles); a bounded wait
+                           that runs out returns DMRG_ETIMEOUT              */
 } dmrg_precision;
 
 typedef struct {
@@ -107,6 +111,21 @@ dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int precision);
 
 /* Energy of the last sweep (incl. e_core).  DMRG_ESTATE before any sweep. */
 dmrg_status dmrg_energy(const dmrg_ctx* ctx, double* energy);
+
+/*
+ * dmrg_rdm12 -- spin-free one- and two-particle reduced density matrices of
+ * the state left by the last sweep (Sec. II.C, Eqs. onerdm, twordm):
+ *   gamma[p*n + q]               = <sum_s a+_{p s} a_{q s}>
+ *   Gamma[((p*n + q)*n + r)*n + s] = <sum_{s,t} a+_{p s} a+_{q t} a_{r t} a_{s s}>
+ * (row-major n x n and n^4, caller-allocated host buffers).  The state is
+ * the two-site wavefunction of the final bond (bond 1 after a full sweep),
+ * evaluated exactly in float64 by a measurement pass over all bonds (the
+ * SU(2) channels Gamma^(0), Gamma^(1) of the paper are recoupled into the
+ * spin-free form internally; Gamma~ = sqrt(3) Gamma^(1) - Gamma^(0) in the
+ * Clebsch-Gordan convention used here).  DMRG_ESTATE before any sweep or if
+ * the last sweep did not end at bond 1; DMRG_EINVAL for NULL buffers.
+ */
+dmrg_status dmrg_rdm12(dmrg_ctx* ctx, double* gamma, double* Gamma);
 
 /*
  * Statistics of the last sweep: total H_eff psi FLOPs (algorithmic, 2mnk per
@@ -214,8 +233,10 @@ typedef struct {
  * effective Hamiltonian sigma = sum_t c_t A_t psi B_t^T over sector blocks),
  * with the intermediate A P kept on chip and item chunks reduced in a fixed
  * order.  Host buffers in/out (C updated in place); all offsets are checked
- * against the buffer lengths before any launch.  precision: DMRG_FP64 or
- * DMRG_SPLIT_TF32.
+ * against the buffer lengths before any launch.  precision: DMRG_FP64,
+ * DMRG_SPLIT_TF32 (3xTF32 on mma.sync, 64 x 64 tiles) or DMRG_SPLIT_HPSI_TC
+ * (3xTF32 on tcgen05, 128 x 64 tiles; DMRG_ETIMEOUT if a bounded wait ran
+ * out).
  */
 dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, int64_t p_len,
                                const double* B, int64_t b_len, double* C, int64_t c_len,

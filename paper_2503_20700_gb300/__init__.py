@@ -17,7 +17,7 @@ LIB_NAME = "libdmrgscf.so"
 
 DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA = 0, -1, -2, -3
 DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE, DMRG_EINTERNAL = -4, -5, -6, -7
-FP64, SPLIT_TF32, SPLIT_HPSI = 0, 1, 3
+FP64, SPLIT_TF32, SPLIT_HPSI, SPLIT_HPSI_TC = 0, 1, 3, 4
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
            -5: "ETIMEOUT", -6: "ESTATE", -7: "EINTERNAL"}
@@ -68,6 +68,8 @@ def load(path=None):
     lib.dmrg_set_precision.restype = I
     lib.dmrg_energy.argtypes = [P, dp]
     lib.dmrg_energy.restype = I
+    lib.dmrg_rdm12.argtypes = [P, dp, dp]
+    lib.dmrg_rdm12.restype = I
     lib.dmrg_last_sweep_stats.argtypes = [P, dp, dp, ip, ip, dp]
     lib.dmrg_last_sweep_stats.restype = I
     lib.dmrg_bond_energies.argtypes = [P, dp, I, ip]
@@ -156,6 +158,17 @@ class DMRG:
         e = ctypes.c_double()
         _check(self._lib, self._ctx, self._lib.dmrg_energy(self._ctx, ctypes.byref(e)))
         return e.value
+
+    def rdm12(self):
+        """Spin-free (gamma~, Gamma~) of the state left by the last sweep:
+        gamma~[p,q] = <sum_s a+_ps a_qs>, Gamma~[p,q,r,s] = <sum_st a+_ps a+_qt a_rt a_ss>."""
+        n = self.n
+        g1 = np.zeros((n, n))
+        g2 = np.zeros((n, n, n, n))
+        _check(self._lib, self._ctx, self._lib.dmrg_rdm12(
+            self._ctx, g1.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            g2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return g1, g2
 
     def stats(self):
         f, s, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

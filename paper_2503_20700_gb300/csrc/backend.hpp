@@ -17,7 +17,9 @@
 
 namespace dmrg {
 
-enum class Precision : int { FP64 = 0, SPLIT_TF32 = 1, BF16X9 = 2 };
+// TC_TF32X3: the 3xTF32 split products of SPLIT_TF32 issued on the tcgen05
+// tensor cores (H_eff psi only; elsewhere it acts as SPLIT_TF32).
+enum class Precision : int { FP64 = 0, SPLIT_TF32 = 1, BF16X9 = 2, TC_TF32X3 = 3 };
 
 struct PlaceSeg {
   const double* src;
@@ -69,6 +71,9 @@ class Backend {
   virtual void copy_h2d(void* dst, const void* src, size_t bytes) = 0;
   virtual void copy_d2h(void* dst, const void* src, size_t bytes) = 0;
   virtual void sync() = 0;
+  // Reads and clears the device error flag that bounded waits in kernels set;
+  // throws "timeout: ..." when it was set.  Synchronises the stream.
+  virtual void check_device_flag() = 0;
   // the stream every primitive is issued on (cudaStream_t)
   virtual void* stream() = 0;
 

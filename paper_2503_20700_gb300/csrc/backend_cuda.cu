@@ -201,29 +201,31 @@ __global__ void precond_kernel(double* __restrict__ y, const double* __restrict_
 // ------------------------------------------------------------------ Jacobi
 // Parallel cyclic Jacobi (round-robin pairing) on a symmetric n x n matrix
 // held in global memory (destroyed).  Eigenvalues descending in w, the
-// eigenvectors as rows of V.  Bounded: at most kMaxSweeps sweeps.
+// eigenvectors as rows of V.  One round rotates n/2 disjoint pairs; each
+// 2x2 block (pair i rows, pair j columns) of A is updated in one pass as
+// R_i X R_j^T, and the eigenvector rows p, q of V are rotated together.
+// A pair is skipped when its off-diagonal entry is negligible next to both
+// diagonal entries, or below 1e-20 ||A||_F; the iteration stops after a
+// sweep without rotations, or after kMaxSweeps sweeps.
 constexpr int kMaxSweeps = 40;
 
-__global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict__ tasks, double* __restrict__ work) {
+__global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict__ tasks) {
   const EighTask tk = tasks[blockIdx.x];
   const int n = tk.n;
   double* a = const_cast<double*>(tk.A);
-  double* W = work + (size_t)blockIdx.x * 0;  // unused
-  (void)W;
-  double* v = tk.V;  // V[k*n + j]: column j = eigenvector j during the iteration
+  double* v = tk.V;  // v[p*n + k]: row p = eigenvector p during the iteration
   extern __shared__ double sm[];
   const int np = (n + 1) & ~1;  // even count, with a dummy index when n is odd
-  double* cs = sm;              // np/2 cosines
-  double* sn = sm + np / 2;     // np/2 sines
+  const int h = np / 2;
+  double* cs = sm;              // h cosines
+  double* sn = sm + h;          // h sines
   int* pp = (int*)(sm + np);    // pairs
-  int* qq = pp + np / 2;
-  int* perm = qq + np / 2;      // round-robin order (np entries)
+  int* qq = pp + h;
+  int* perm = qq + h;           // round-robin order (np entries)
   __shared__ double red[256];
-  __shared__ int done;
+  __shared__ int nrot;
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) v[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
-  __syncthreads();
-  // Frobenius norm for the stopping rule
   double fro = 0.0;
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) fro += a[e] * a[e];
   red[threadIdx.x] = fro;
@@ -232,26 +234,13 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  const double fro2 = red[0];
+  const double floor_abs = 1e-20 * sqrt(red[0]);
   __syncthreads();
   for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
-    double off = 0.0;
-    for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
-      int r = (int)(e / n), c = (int)(e % n);
-      if (r != c) off += a[e] * a[e];
-    }
-    red[threadIdx.x] = off;
+    if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) done = (red[0] <= 1e-30 * fro2 || red[0] < 1e-300);
-    __syncthreads();
-    if (done) break;
     for (int round = 0; round < np - 1; ++round) {
-      // pairs of this round: perm[i] with perm[np-1-i]
-      for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
+      for (int i = threadIdx.x; i < h; i += blockDim.x) {
         int p = perm[i], q = perm[np - 1 - i];
         if (p > q) { int t = p; p = q; q = t; }
         pp[i] = p;
@@ -259,44 +248,53 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
         double c = 1.0, s = 0.0;
         if (q < n) {
           double apq = a[(size_t)p * n + q];
-          if (apq != 0.0) {
-            double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+          double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+          double g = 100.0 * fabs(apq);
+          bool negligible = fabs(apq) <= floor_abs || (fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq));
+          if (!negligible) {
             double theta = (aqq - app) / (2.0 * apq);
             double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             c = 1.0 / sqrt(t * t + 1.0);
             s = t * c;
+            atomicAdd(&nrot, 1);
           }
         }
         cs[i] = c;
         sn[i] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (size_t e = threadIdx.x; e < (size_t)(np / 2) * n; e += blockDim.x) {
+      // A <- J^T A J, one 2x2 block per (i, j)
+      for (size_t e = threadIdx.x; e < (size_t)h * h; e += blockDim.x) {
+        int i = (int)(e / h), j = (int)(e % h);
+        double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (si == 0.0 && sj == 0.0) continue;
+        int p = pp[i], q = qq[i], r = pp[j], t = qq[j];
+        bool qv = q < n, tv = t < n;
+        double x00 = a[(size_t)p * n + r];
+        double x01 = tv ? a[(size_t)p * n + t] : 0.0;
+        double x10 = qv ? a[(size_t)q * n + r] : 0.0;
+        double x11 = (qv && tv) ? a[(size_t)q * n + t] : 0.0;
+        // rows: [p; q] <- [c -s; s c] [p; q]
+        double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+        double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+        // columns: [r t] <- [r t] [c s; -s c]
+        a[(size_t)p * n + r] = cj * y00 - sj * y01;
+        if (tv) a[(size_t)p * n + t] = sj * y00 + cj * y01;
+        if (qv) a[(size_t)q * n + r] = cj * y10 - sj * y11;
+        if (qv && tv) a[(size_t)q * n + t] = sj * y10 + cj * y11;
+      }
+      // V rows
+      for (size_t e = threadIdx.x; e < (size_t)h * n; e += blockDim.x) {
         int i = (int)(e / n), k = (int)(e % n);
+        double s = sn[i];
+        if (s == 0.0) continue;
+        double c = cs[i];
         int p = pp[i], q = qq[i];
-        if (q >= n || sn[i] == 0.0) continue;
-        double c = cs[i], s = sn[i];
-        double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
-        a[(size_t)p * n + k] = c * apk - s * aqk;
-        a[(size_t)q * n + k] = s * apk + c * aqk;
+        double vp = v[(size_t)p * n + k], vq = v[(size_t)q * n + k];
+        v[(size_t)p * n + k] = c * vp - s * vq;
+        v[(size_t)q * n + k] = s * vp + c * vq;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (size_t e = threadIdx.x; e < (size_t)(np / 2) * n; e += blockDim.x) {
-        int i = (int)(e / n), k = (int)(e % n);
-        int p = pp[i], q = qq[i];
-        if (q >= n || sn[i] == 0.0) continue;
-        double c = cs[i], s = sn[i];
-        double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
-        a[(size_t)k * n + p] = c * akp - s * akq;
-        a[(size_t)k * n + q] = s * akp + c * akq;
-        double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
-        v[(size_t)k * n + p] = c * vkp - s * vkq;
-        v[(size_t)k * n + q] = s * vkp + c * vkq;
-      }
-      __syncthreads();
-      // rotate the round-robin order (perm[0] fixed)
       if (threadIdx.x == 0) {
         int last = perm[np - 1];
         for (int i = np - 1; i > 1; --i) perm[i] = perm[i - 1];
@@ -304,25 +302,29 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
       }
       __syncthreads();
     }
+    if (nrot == 0) break;
+    __syncthreads();
   }
-  // sort eigenvalues descending (selection, one thread) and write rows of V
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    for (int i = 0; i < n; ++i) {
-      int best = i;
-      for (int j = i + 1; j < n; ++j)
-        if (a[(size_t)perm[j] * n + perm[j]] > a[(size_t)perm[best] * n + perm[best]]) best = j;
-      int t = perm[i]; perm[i] = perm[best]; perm[best] = t;
+  // sort eigenvalues descending (rank by counting, ties by index) and write rows of V
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double di = a[(size_t)i * n + i];
+    if (!(di == di)) di = -INFINITY;  // a NaN sorts last, so ranks stay a permutation
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double dj = a[(size_t)j * n + j];
+      if (!(dj == dj)) dj = -INFINITY;
+      rank += (dj > di) || (dj == di && j < i);
     }
-    for (int i = 0; i < n; ++i) tk.w[i] = a[(size_t)perm[i] * n + perm[i]];
+    perm[rank] = i;
   }
   __syncthreads();
-  // transpose columns of v into rows of the output (in place via the a buffer)
+  for (int r = threadIdx.x; r < n; r += blockDim.x) tk.w[r] = a[(size_t)perm[r] * n + perm[r]];
+  __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) a[e] = v[e];
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
     int r = (int)(e / n), k = (int)(e % n);
-    v[e] = a[(size_t)k * n + perm[r]];
+    v[e] = a[(size_t)perm[r] * n + k];
   }
   __syncthreads();
   // sign convention: largest-magnitude component of each eigenvector positive
@@ -426,6 +428,7 @@ class CudaBackend : public Backend {
     for (auto e : pool) cudaEventDestroy(e);
     if (dtask) cudaFreeAsync(dtask, st);
     if (part) cudaFreeAsync(part, st);
+    if (dflag) cudaFreeAsync(dflag, st);
     if (htask) cudaFreeHost(htask);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
@@ -473,6 +476,24 @@ class CudaBackend : public Backend {
     }
   }
   void sync() override { CK(cudaStreamSynchronize(st)); }
+  int* dflag = nullptr;  // device error flag of the bounded waits
+  int* flag() {
+    if (!dflag) {
+      CK(cudaMallocAsync((void**)&dflag, sizeof(int), st));
+      CK(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+    }
+    return dflag;
+  }
+  void check_device_flag() override {
+    if (!dflag) return;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h != 0) {
+      CK(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+      throw std::runtime_error("timeout: a bounded wait in the tcgen05 H_eff psi kernel ran out");
+    }
+  }
   void* stream() override { return (void*)st; }
 
   // upload a packed task buffer; returns the device base pointer
@@ -586,7 +607,7 @@ class CudaBackend : public Backend {
       rec = &recs.back();
       CK(cudaEventRecord(rec->a, st));
     }
-    hpsi_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, prec, st);
+    hpsi_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, prec, flag(), st);
     launches += (ntasks > 0) + (nreds > 0);
     if (rec) CK(cudaEventRecord(rec->b, st));
     if (recs.size() > 4096) drain();
@@ -642,7 +663,7 @@ class CudaBackend : public Backend {
       CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     std::vector<size_t> off;
     char* d = upload({{tasks.data(), tasks.size() * sizeof(EighTask)}}, off);
-    jacobi_kernel<<<(unsigned)tasks.size(), 256, smem, st>>>((const EighTask*)(d + off[0]), nullptr);
+    jacobi_kernel<<<(unsigned)tasks.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
     ++launches;
     CK(cudaGetLastError());
   }

@@ -40,7 +40,20 @@ dmrg_status translate(dmrg_ctx* c, const std::exception& e) {
   if (m.rfind("out of device memory", 0) == 0) return fail(c, DMRG_ENOMEM, m);
   if (m.rfind("timeout", 0) == 0) return fail(c, DMRG_ETIMEOUT, m);
   if (m.rfind("davidson", 0) == 0) return fail(c, DMRG_ENOCONV, m);
+  if (m.rfind("state", 0) == 0) return fail(c, DMRG_ESTATE, m);
   return fail(c, DMRG_EINTERNAL, m);
+}
+
+bool sweep_precision_ok(int p) {
+  return p == DMRG_FP64 || p == DMRG_SPLIT_TF32 || p == DMRG_SPLIT_HPSI || p == DMRG_SPLIT_HPSI_TC;
+}
+
+// dmrg_precision -> (H_eff psi kernel precision, renormalisation GEMM precision)
+void map_precision(int p, dmrg::Precision* hpsi, dmrg::Precision* renorm) {
+  *hpsi = p == DMRG_FP64           ? dmrg::Precision::FP64
+          : p == DMRG_SPLIT_HPSI_TC ? dmrg::Precision::TC_TF32X3
+                                    : dmrg::Precision::SPLIT_TF32;
+  *renorm = p == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64;
 }
 
 // Default initial product state: electrons spread evenly, spins coupled from
@@ -100,8 +113,7 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
   if (opts) o = *opts;
   if (o.D < 1 || o.max_space < 4 || o.davidson_tol <= 0 || o.max_davidson_iter < 1)
     return fail(nullptr, DMRG_EINVAL, "bad options");
-  if (o.precision < 0 || o.precision > 3 || o.precision == 2)
-    return fail(nullptr, DMRG_EINVAL, "unsupported precision");
+  if (!sweep_precision_ok(o.precision)) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
   auto ctx = std::make_unique<dmrg_ctx>();
   ctx->n = n;
   try {
@@ -137,8 +149,7 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     eo.D = o.D;
     eo.max_davidson_iter = o.max_davidson_iter;
     eo.davidson_tol = o.davidson_tol;
-    eo.prec = o.precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32;
-    eo.prec_renorm = o.precision == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64;
+    map_precision(o.precision, &eo.prec, &eo.prec_renorm);
     eo.max_space = o.max_space;
     eo.verbose = o.verbose;
     ctx->eng = std::make_unique<dmrg::Engine>(ctx->be.get(), n, h, g, e_core, n_elec, two_s, eo,
@@ -176,11 +187,21 @@ dmrg_status dmrg_set_bond_dim(dmrg_ctx* c, int D) {
 
 dmrg_status dmrg_set_precision(dmrg_ctx* c, int precision) {
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
-  if (precision < 0 || precision > 3 || precision == 2)
-    return fail(c, DMRG_EINVAL, "unsupported precision");
-  c->eng->set_precision(
-      precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32,
-      precision == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64);
+  if (!sweep_precision_ok(precision)) return fail(c, DMRG_EINVAL, "unsupported precision");
+  dmrg::Precision ph, pr;
+  map_precision(precision, &ph, &pr);
+  c->eng->set_precision(ph, pr);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_rdm12(dmrg_ctx* c, double* gamma, double* Gamma) {
+  if (!c || !c->eng || !gamma || !Gamma) return fail(c, DMRG_EINVAL, "invalid argument");
+  if (c->sweeps_done == 0) return fail(c, DMRG_ESTATE, "no sweep has run");
+  try {
+    c->eng->rdm12(gamma, Gamma);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
   return DMRG_OK;
 }
 
@@ -404,7 +425,8 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                                int n_items, int precision, int device) {
   if (!A || !P || !B || !C || (!blocks && n_blocks) || (!items && n_items) || n_blocks < 0 || n_items < 0)
     return fail(nullptr, DMRG_EINVAL, "invalid argument");
-  if (precision < 0 || precision > 1) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
+  if (precision != DMRG_FP64 && precision != DMRG_SPLIT_TF32 && precision != DMRG_SPLIT_HPSI_TC)
+    return fail(nullptr, DMRG_EINVAL, "unsupported precision");
   if (const char* m = check_hpsi(a_len, p_len, b_len, c_len, blocks, n_blocks, items, n_items))
     return fail(nullptr, DMRG_EINVAL, m);
   std::string err;
@@ -424,12 +446,12 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     std::vector<dmrg::HpsiItem> hi;
     double fl = 0.0;
     to_device_lists(blocks, n_blocks, items, n_items, dA, dP, dB, dC, hb, hi, &fl);
-    long long tile_items = 0;
-    for (auto& b : hb) tile_items += (long long)b.item_count * ((b.m + 63) / 64) * ((b.n + 63) / 64);
-    int max_items = (int)std::max<long long>(4, tile_items / (8 * 152) + 1);
+    const dmrg::Precision pr = precision == DMRG_FP64           ? dmrg::Precision::FP64
+                               : precision == DMRG_SPLIT_HPSI_TC ? dmrg::Precision::TC_TF32X3
+                                                                 : dmrg::Precision::SPLIT_TF32;
     std::vector<dmrg::HpsiTask> tasks;
     std::vector<dmrg::HpsiReduce> reds;
-    size_t scr = dmrg::hpsi_plan_tasks(hb, max_items, tasks, reds);
+    size_t scr = dmrg::hpsi_plan_tasks(hb, pr, tasks, reds);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t ob = 0, oi = al(hb.size() * sizeof(dmrg::HpsiBlock));
     size_t ot = al(oi + hi.size() * sizeof(dmrg::HpsiItem));
@@ -442,8 +464,8 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     if (!reds.empty()) be->copy_h2d(d + orr, reds.data(), reds.size() * sizeof(dmrg::HpsiReduce));
     be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
              (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
-             (int)reds.size(), (double*)(d + os),
-             precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32, fl);
+             (int)reds.size(), (double*)(d + os), pr, fl);
+    be->check_device_flag();
     be->copy_d2h(C, dC, c_len * sizeof(double));
     be->sync();
     for (void* q : {(void*)dA, (void*)dP, (void*)dB, (void*)dC, (void*)d}) be->free(q);

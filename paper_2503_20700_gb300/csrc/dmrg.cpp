@@ -467,7 +467,14 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   std::vector<int> esites = bsites;
   if (b.left) esites.push_back(site);
   else esites.insert(esites.begin(), site);
-  auto keys = op_keys(esites, n_, e->normal);
+  std::vector<OpKey> keys;
+  if (rdm_mode_) {
+    // measurement blocks: the single spinors and, on normal blocks, the pairs
+    for (const OpKey& k : op_keys(esites, n_, e->normal))
+      if (k.kind == K_C || (e->normal && (k.kind == K_A || k.kind == K_B))) keys.push_back(k);
+  } else {
+    keys = op_keys(esites, n_, e->normal);
+  }
   e->ops->allocate(keys);
 
   // ---- blocking terms, target by target
@@ -498,7 +505,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
     if (!in_sites(esites, p)) outs.push_back(p);
 
   // H
-  {
+  if (!rdm_mode_) {
     OpKey tk{K_H, 0, 0, 0};
     T(tk, op_blk(K_H, 0, 0, 0), op_site(sa.I), 1.0);
     SiteOp hs = site_add(sa.N.scaled(hh(s, s)), sa.Hu, g(s, s, s, s));
@@ -527,7 +534,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
     }
     return op_blk(kind, p, q, k2);  // looked up in tmp
   };
-  if (b.normal && b.nsites > 0) {
+  if (b.normal && b.nsites > 0 && !rdm_mode_) {
     tmp = std::make_unique<OpSet>();
     tmp->be = be_;
     tmp->basis = bb;
@@ -543,7 +550,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
     build_comp_from_normal(b, *tmp, tk);
   }
   // S_p, p outside the enlarged block
-  for (int p : outs) {
+  for (int p : rdm_mode_ ? std::vector<int>() : outs) {
     OpKey tk{K_S, p, 0, 1};
     T(tk, op_blk(K_S, p, 0, 1), op_site(sa.I), 1.0);
     SiteOp so = site_add(sa.D.scaled(0.5 * hh(p, s)), sa.NnD, g(p, s, s, s));
@@ -609,7 +616,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
           }
         }
       }
-  } else {
+  } else if (!rdm_mode_) {
     for (size_t a = 0; a < outs.size(); ++a)
       for (size_t c = a; c < outs.size(); ++c) {
         int p = outs[a], q = outs[c];
@@ -968,7 +975,6 @@ std::unique_ptr<Block> Engine::renormalize(Block& enl, const SavedU& U, bool swi
 }
 
 // ============================================================ bond: psi, H psi
-namespace {
 struct PsiLayout {
   struct Blk {
     int a, b, rows, cols;
@@ -1011,7 +1017,6 @@ std::vector<std::pair<int, SrcBlock>> reach(OpSet& set, const Operand& x, int ke
   }
   return out;
 }
-}  // namespace
 
 // H_eff psi as one fused launch: per sigma block, the list of items
 // alpha op(A) P op(B)^T (left operator block, psi block, right operator block).
@@ -1026,6 +1031,7 @@ struct HPsiPlan {
   HpsiTask* d_tasks = nullptr;
   HpsiReduce* d_reds = nullptr;
   double* scratch = nullptr;
+  Precision prec = Precision::FP64;  // kernel the task list was planned for
   int ntasks = 0, nreds = 0;
   size_t nitems = 0;
   double flops = 0.0;
@@ -1089,9 +1095,30 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
         }
     }
   }
+  if (opt_.verbose >= 2) {
+    // shape statistics of the contraction, weighted by flops: the smallest
+    // GEMM dimension bounds the tensor-core tile efficiency
+    const double edges[] = {16, 32, 64, 128, 256, 512, 1e30};
+    double hist[7] = {0}, tot = 0.0;
+    size_t nit = 0;
+    for (size_t b = 0; b < P.blk.size(); ++b)
+      for (auto& it : per[b]) {
+        ++nit;
+        int m = P.blk[b].rows, n = P.blk[b].cols;
+        double f = (it.A ? 2.0 * m * it.ka * it.kb : 0.0) + (it.B ? 2.0 * m * n * it.kb : 0.0);
+        int d = std::min({m, n, it.ka, it.kb});
+        int k = 0;
+        while (d > edges[k]) ++k;
+        hist[k] += f;
+        tot += f;
+      }
+    std::fprintf(stderr, "hpsi shapes: terms %zu blocks %zu items %zu flops %.3e | min-dim<=16 %.2f <=32 %.2f "
+                 "<=64 %.2f <=128 %.2f <=256 %.2f <=512 %.2f >512 %.2f\n",
+                 terms.size(), P.blk.size(), nit, tot, hist[0] / tot, hist[1] / tot, hist[2] / tot,
+                 hist[3] / tot, hist[4] / tot, hist[5] / tot, hist[6] / tot);
+  }
   std::vector<HpsiBlock> blocks;
   std::vector<HpsiItem> items;
-  long long tile_items = 0;
   for (size_t b = 0; b < P.blk.size(); ++b) {
     HpsiBlock hb;
     hb.C = plan.out + P.blk[b].off;
@@ -1102,13 +1129,11 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
     hb.item_count = (int)per[b].size();
     items.insert(items.end(), per[b].begin(), per[b].end());
     blocks.push_back(hb);
-    tile_items += (long long)per[b].size() * ((hb.m + 63) / 64) * ((hb.n + 63) / 64);
   }
-  // chunk the items of a tile so the launch has several waves of CTAs
-  int max_items = (int)std::max<long long>(4, tile_items / (8 * 152) + 1);
   std::vector<HpsiTask> tasks;
   std::vector<HpsiReduce> reds;
-  size_t scr = hpsi_plan_tasks(blocks, max_items, tasks, reds);
+  plan.prec = opt_.prec;
+  size_t scr = hpsi_plan_tasks(blocks, plan.prec, tasks, reds);
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t ob = 0, oi = al(ob + blocks.size() * sizeof(HpsiBlock));
   size_t ot = al(oi + items.size() * sizeof(HpsiItem));
@@ -1161,7 +1186,7 @@ size_t Engine::x_budget_elems() const { return 0; }
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
   be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
-            plan.scratch, opt_.prec, plan.flops);
+            plan.scratch, plan.prec, plan.flops);
 }
 
 // ============================================================ Davidson
@@ -1213,6 +1238,7 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     auto t0 = std::chrono::steady_clock::now();
     apply_hpsi(plan);
     be_->sync();
+    if (plan.prec == Precision::TC_TF32X3) be_->check_device_flag();
     auto t1 = std::chrono::steady_clock::now();
     stats_.hpsi_seconds += std::chrono::duration<double>(t1 - t0).count();
     stats_.hpsi_flops += plan.flops;
@@ -1460,6 +1486,81 @@ void Engine::save_prev(int bond, const Block& Le, const Block& Re, const HPsiPla
   be_->copy_d2d(prev_.psi, psi, prev_.len * sizeof(double));
 }
 
+// Moves the two-site wavefunction of bond b (from) to bond b+1: project the
+// old enlarged left block onto its kept multiplets (U: L'(b) -> L(b+1)),
+// recouple the site that changes side (6j), and expand the old right block
+// R(b+2) into site (x) R(b+3) with its stored MPS tensor (V).  Exact when U
+// keeps the whole support of the state.
+void Engine::move_lr(const Prev& from, const SavedU& U, const SavedU& V, const Block& Le,
+                     const Block& Re, const PsiLayout& P, double* psi) {
+  const Basis& LB = Le.ops->basis;
+  const Basis& RB = Re.ops->basis;
+  const int S = two_s_;
+  be_->memset0(psi, P.size * sizeof(double));
+  const Basis& Lnew = U.next;            // L_[bond]
+  const Basis& Rmid = V.next;            // R_[n-bond-1] = parent of prev R'
+  // phi(l, b) = Ut_a psi(a, b)
+  PsiLayout phiL = make_psi(Lnew, from.Rb, n_elec_, S);
+  PsiLayout mid = make_psi(LB, Rmid, n_elec_, S);
+  double* phi = (double*)be_->alloc(std::max<size_t>(phiL.size, 1) * sizeof(double));
+  double* psm = (double*)be_->alloc(std::max<size_t>(mid.size, 1) * sizeof(double));
+  be_->memset0(phi, std::max<size_t>(phiL.size, 1) * sizeof(double));
+  be_->memset0(psm, std::max<size_t>(mid.size, 1) * sizeof(double));
+  GemmBuilder g1;
+  for (auto& b : from.blk) {
+    int a = b[0], bb = b[1];
+    int l = U.map[a];
+    if (l < 0) continue;
+    int pi = phiL.find(l, bb);
+    if (pi < 0) continue;
+    g1.add(phi + phiL.blk[pi].off, U.kept[a], b[3], b[3],
+           GemmSeg{U.ut(a), from.psi + b[4], b[2], b[2], b[3], 0, 0, 1.0});
+  }
+  g1.run(be_, Precision::FP64);
+  // recouple the site between the blocks
+  PlaceBuilder pb;
+  for (auto& pbk : phiL.blk) {
+    int l = pbk.a, bb = pbk.b;
+    for (auto& c : from.Rc) {
+      if (c.esec != bb) continue;
+      int sg = c.site, r = c.bsec;
+      for (auto& cp : Le.comps) {
+        if (cp.bsec != l || cp.site != sg) continue;
+        int ap = cp.esec;
+        int mi = mid.find(ap, r);
+        if (mi < 0) continue;
+        double co = recouple(Lnew.sec[l].j, kSiteJ[sg], Rmid.sec[r].j, LB.sec[ap].j,
+                             from.Rb.sec[bb].j, S);
+        if (co == 0.0) continue;
+        double* d = psm + mid.blk[mi].off + (size_t)cp.eoff * mid.blk[mi].cols;
+        const double* src = phi + pbk.off + c.eoff;
+        pb.add(d, Lnew.sec[l].dim, Rmid.sec[r].dim, mid.blk[mi].cols,
+               PlaceSeg{src, pbk.cols, 0, co});
+      }
+    }
+  }
+  pb.run(be_);
+  // expand the right block: psi(a', e) = psm(a', r(e)) Ut_e
+  GemmBuilder g2;
+  for (size_t e = 0; e < V.enl.sec.size(); ++e) {
+    int r = V.map[e];
+    if (r < 0) continue;
+    int eb = RB.find(V.enl.sec[e].n, V.enl.sec[e].j);
+    if (eb < 0) continue;
+    for (auto& mb : mid.blk) {
+      if (mb.b != r) continue;
+      int pi = P.find(mb.a, eb);
+      if (pi < 0) continue;
+      g2.add(psi + P.blk[pi].off, mb.rows, RB.sec[eb].dim, RB.sec[eb].dim,
+             GemmSeg{psm + mb.off, V.ut((int)e), V.kept[e], mb.cols, RB.sec[eb].dim, 0, 0, 1.0});
+    }
+  }
+  g2.run(be_, Precision::FP64);
+  be_->sync();
+  be_->free(phi);
+  be_->free(psm);
+}
+
 // Predicted two-site wavefunction of bond `bond` from the state of the
 // previous bond (one step of the sweep): project with the new block's kept
 // eigenvectors, recouple the site that changes side (6j), expand the other
@@ -1494,70 +1595,7 @@ void Engine::guess(int bond, bool l2r, const Block& Le, const Block& Re, const H
   const int S = two_s_;
   (void)l2r;  // the move follows the position of the previous bond (turns included)
   if (prev_.bond == bond - 1) {
-    const SavedU& U = *LU_[bond];          // L'(bond-1) -> L_[bond]
-    const SavedU& V = *RU_[n_ - bond - 1]; // E ~ R'(bond) -> R_[n-bond-1]
-    const Basis& Lnew = U.next;            // L_[bond]
-    const Basis& Rmid = V.next;            // R_[n-bond-1] = parent of prev R'
-    // phi(l, b) = Ut_a psi(a, b)
-    PsiLayout phiL = make_psi(Lnew, prev_.Rb, n_elec_, S);
-    PsiLayout mid = make_psi(LB, Rmid, n_elec_, S);
-    double* phi = (double*)be_->alloc(std::max<size_t>(phiL.size, 1) * sizeof(double));
-    double* psm = (double*)be_->alloc(std::max<size_t>(mid.size, 1) * sizeof(double));
-    be_->memset0(phi, std::max<size_t>(phiL.size, 1) * sizeof(double));
-    be_->memset0(psm, std::max<size_t>(mid.size, 1) * sizeof(double));
-    GemmBuilder g1;
-    for (auto& b : prev_.blk) {
-      int a = b[0], bb = b[1];
-      int l = U.map[a];
-      if (l < 0) continue;
-      int pi = phiL.find(l, bb);
-      if (pi < 0) continue;
-      g1.add(phi + phiL.blk[pi].off, U.kept[a], b[3], b[3],
-             GemmSeg{U.ut(a), prev_.psi + b[4], b[2], b[2], b[3], 0, 0, 1.0});
-    }
-    g1.run(be_, Precision::FP64);
-    // recouple the site between the blocks
-    PlaceBuilder pb;
-    for (auto& pbk : phiL.blk) {
-      int l = pbk.a, bb = pbk.b;
-      for (auto& c : prev_.Rc) {
-        if (c.esec != bb) continue;
-        int sg = c.site, r = c.bsec;
-        for (auto& cp : Le.comps) {
-          if (cp.bsec != l || cp.site != sg) continue;
-          int ap = cp.esec;
-          int mi = mid.find(ap, r);
-          if (mi < 0) continue;
-          double co = recouple(Lnew.sec[l].j, kSiteJ[sg], Rmid.sec[r].j, LB.sec[ap].j,
-                               prev_.Rb.sec[bb].j, S);
-          if (co == 0.0) continue;
-          double* d = psm + mid.blk[mi].off + (size_t)cp.eoff * mid.blk[mi].cols;
-          const double* src = phi + pbk.off + c.eoff;
-          pb.add(d, Lnew.sec[l].dim, Rmid.sec[r].dim, mid.blk[mi].cols,
-                 PlaceSeg{src, pbk.cols, 0, co});
-        }
-      }
-    }
-    pb.run(be_);
-    // expand the right block: psi(a', e) = psm(a', r(e)) Ut_e
-    GemmBuilder g2;
-    for (size_t e = 0; e < V.enl.sec.size(); ++e) {
-      int r = V.map[e];
-      if (r < 0) continue;
-      int eb = RB.find(V.enl.sec[e].n, V.enl.sec[e].j);
-      if (eb < 0) continue;
-      for (auto& mb : mid.blk) {
-        if (mb.b != r) continue;
-        int pi = P.find(mb.a, eb);
-        if (pi < 0) continue;
-        g2.add(psi + P.blk[pi].off, mb.rows, RB.sec[eb].dim, RB.sec[eb].dim,
-               GemmSeg{psm + mb.off, V.ut((int)e), V.kept[e], mb.cols, RB.sec[eb].dim, 0, 0, 1.0});
-      }
-    }
-    g2.run(be_, Precision::FP64);
-    be_->sync();
-    be_->free(phi);
-    be_->free(psm);
+    move_lr(prev_, *LU_[bond], *RU_[n_ - bond - 1], Le, Re, P, psi);
   } else if (prev_.bond == bond + 1) {
     const SavedU& V = *RU_[n_ - bond - 2];  // R'(bond+1) -> R_[n-bond-2]
     const SavedU& U = *LU_[bond + 1];       // E ~ L'(bond) -> L_[bond+1]
@@ -1739,6 +1777,7 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   stats_.t_plan += t3 - t2;
   int its = 0;
   double e = davidson(plan, psi, &its) + e_core_;
+  be_->check_device_flag();
   stats_.davidson_iters += its;
   double t4 = now_s();
   stats_.t_davidson += t4 - t3;
@@ -1795,6 +1834,681 @@ SweepStats Engine::sweep() {
   stats_.max_trunc = tmax;
   sweep_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return stats_;
+}
+
+// ============================================================ reduced density matrices
+// Spin-free RDMs of the final two-site state (Eqs. onerdm, twordm; the SU(2)
+// channels of Sec. II.C are recoupled on the host).  A measurement pass walks
+// the bonds left to right starting at bond 1: at every bond i the state is
+// psi(L'(i), R'(i)) with L'(i) = L(i) (x) site i and R'(i) = site i+1 (x) R(i+2),
+// where L(i) is an exact left basis of the state built in a measurement mode
+// (single spinors and all normal pair operators) and R(i+2) the right block of
+// the last sweep.  Moving to the next bond keeps every multiplet of nonzero
+// weight (rho eigenvalue >= 1e-12), so the moved state is the same state.
+//
+// An element with operators at positions x1 <= x2 <= x3 (<= x4) is evaluated
+// at bond i = min(n-2, x3) (2-RDM) or min(n-2, x2) (1-RDM): at most two of its
+// operators lie in L(i), at most one to the right of site i (several on the
+// last site at the last bond).  Its position-ordered operator string is
+// a product  x_L . s . Y  of a normal operator of L(i) (identity, spinor or
+// pair), a string on site i and an operator of R'(i), and the spin-free sum
+// over the spins is expanded in the invariant couplings
+//   [[x_L^{kx} (x) s^{ks}]^{kX} (x) Y^{kX}]^0
+// that the pass can evaluate.  Their expectation values follow from
+//   N_Y(a',a) = sum_{b',b} c(a',b',a,b) psi(a',b') Y(b',b) psi(a,b)^T
+// (an operator-shaped object on L'), taken back to L(i) through the adjoint
+// of the blocking placement (W), and one GEMM of all stored L(i) operators
+// against all W.
+
+struct Engine::RdmAcc {
+  std::vector<double> g1, g2;
+};
+
+namespace {
+
+struct SortedOps {
+  int n = 0;
+  int pos[4] = {0, 0, 0, 0}, dag[4] = {0, 0, 0, 0};
+  std::vector<std::pair<int, int>> pairs;
+  double sign = 1.0;
+};
+
+// position order (stable: operators on one site keep their order); each
+// exchange of operators on different orbitals gives a factor -1
+SortedOps sort_ops(const int* pos, const int* dag, int n, const std::vector<std::pair<int, int>>& pairs) {
+  SortedOps r;
+  r.n = n;
+  int ord[4] = {0, 1, 2, 3};
+  int inv = 0;
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && pos[ord[j - 1]] > pos[ord[j]]; --j) {
+      std::swap(ord[j - 1], ord[j]);
+      ++inv;
+    }
+  int where[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    r.pos[i] = pos[ord[i]];
+    r.dag[i] = dag[ord[i]];
+    where[ord[i]] = i;
+  }
+  for (auto& pr : pairs) r.pairs.push_back({where[pr.first], where[pr.second]});
+  r.sign = (inv & 1) ? -1.0 : 1.0;
+  return r;
+}
+
+// sequences of doubled intermediate ranks of a sequential coupling of m spinors
+void seq_ranks(int m, std::vector<std::vector<int>>& out) {
+  out.clear();
+  if (m == 0) { out.push_back({}); return; }
+  std::vector<std::vector<int>> cur{{1}};  // rank after the first spinor
+  for (int i = 1; i < m; ++i) {
+    std::vector<std::vector<int>> nxt;
+    for (auto& v : cur)
+      for (int k : {v.back() - 1, v.back() + 1})
+        if (k >= 0) {
+          auto w = v;
+          w.push_back(k);
+          nxt.push_back(w);
+        }
+    cur = nxt;
+  }
+  for (auto& v : cur) out.push_back(std::vector<int>(v.begin() + 1, v.end()));  // drop the leading 1
+}
+int seq_rank(int m, const std::vector<int>& k) { return m == 0 ? 0 : (m == 1 ? 1 : k.back()); }
+
+// One evaluable coupling of a split string (l ops | s ops | y ops).
+struct Variant {
+  int kx = 0;                 // rank of the L(i) part
+  std::vector<int> kl;        // its sequential intermediates (pair: {kx})
+  std::vector<int> ks, ky;    // sequential intermediates of the site / right parts
+  int kX = 0;                 // rank of [x (x) s] (= rank of Y)
+  double c = 0.0;             // coefficient in the spin-free sum
+};
+
+// builds the coupling tree of a variant over slots 0..n-1
+std::vector<TreeNode> variant_tree(int l, int s, int y, const Variant& v) {
+  std::vector<TreeNode> t;
+  auto leaf = [&](int slot) { t.push_back(TreeNode{slot, -1, -1, 1}); return (int)t.size() - 1; };
+  auto join = [&](int a, int b, int k) { t.push_back(TreeNode{-1, a, b, k}); return (int)t.size() - 1; };
+  int xl = -1, xs = -1, xy = -1;
+  for (int i = 0; i < l; ++i) {
+    int f = leaf(i);
+    xl = (i == 0) ? f : join(xl, f, v.kl[i - 1]);
+  }
+  for (int i = 0; i < s; ++i) {
+    int f = leaf(l + i);
+    xs = (i == 0) ? f : join(xs, f, v.ks[i - 1]);
+  }
+  for (int i = 0; i < y; ++i) {
+    int f = leaf(l + s + i);
+    xy = (i == 0) ? f : join(xy, f, v.ky[i - 1]);
+  }
+  int X = -1;
+  if (xl >= 0 && xs >= 0) X = join(xl, xs, v.kX);
+  else X = xl >= 0 ? xl : xs;
+  if (X >= 0 && xy >= 0) join(X, xy, 0);
+  return t;
+}
+
+// coefficients of the spin-free pairing in an independent set of variants
+std::vector<Variant> expand_split(int l, int s, int y, const std::vector<int>& dag,
+                                  const std::vector<std::pair<int, int>>& pairs) {
+  const int n = l + s + y;
+  std::vector<std::vector<int>> KL, KS, KY;
+  seq_ranks(l, KL);
+  seq_ranks(s, KS);
+  seq_ranks(y, KY);
+  std::vector<Variant> all;
+  for (auto& kl : KL)
+    for (auto& ks : KS)
+      for (auto& ky : KY) {
+        int kx = seq_rank(l, kl), rs = seq_rank(s, ks), ry = seq_rank(y, ky);
+        for (int kX = 0; kX <= 4; ++kX) {
+          if (l > 0 && s > 0) {
+            if (!triangle(kx, rs, kX)) continue;
+          } else if (kX != (l > 0 ? kx : rs)) {
+            continue;
+          }
+          if (y > 0 ? kX != ry : kX != 0) continue;
+          Variant v;
+          v.kx = kx;
+          v.kl = kl;
+          v.ks = ks;
+          v.ky = ky;
+          v.kX = kX;
+          all.push_back(v);
+        }
+      }
+  // greedy independent subset
+  std::vector<std::vector<double>> basis, ortho;
+  std::vector<Variant> pick;
+  for (auto& v : all) {
+    auto T = tree_tensor(variant_tree(l, s, y, v), n);
+    auto u = T;
+    for (auto& o : ortho) {
+      double d = 0.0, nn = 0.0;
+      for (size_t e = 0; e < u.size(); ++e) { d += o[e] * u[e]; nn += o[e] * o[e]; }
+      for (size_t e = 0; e < u.size(); ++e) u[e] -= d / nn * o[e];
+    }
+    double nrm = 0.0;
+    for (double x : u) nrm += x * x;
+    if (nrm < 1e-20) continue;
+    ortho.push_back(u);
+    basis.push_back(T);
+    pick.push_back(v);
+  }
+  auto target = pairing_tensor(dag, pairs, n);
+  double res = 0.0;
+  auto c = expand_invariant(target, basis, &res);
+  if (res > 1e-10) throw std::runtime_error("internal: spin-free pairing outside the coupling span");
+  std::vector<Variant> out;
+  for (size_t i = 0; i < pick.size(); ++i)
+    if (std::abs(c[i]) > 1e-14) {
+      pick[i].c = c[i];
+      out.push_back(pick[i]);
+    }
+  return out;
+}
+
+// stored L(i) operator realising a position-ordered normal string (0-2 spinors)
+struct XTerm {
+  OpKey key;
+  int adj = 0;
+  double f = 1.0;
+};
+const OpKey kIdentityKey{K_T0, -1, -1, 0};
+// key of an on-site string temporary (operators of L(1) for strings of three
+// or four operators on site 0)
+OpKey string_key(const std::vector<int>& dag, const std::vector<int>& k2, int k2tot) {
+  int code = 0;
+  for (int d : dag) code = code * 2 + d;
+  for (int k : k2) code = code * 5 + k;
+  int dn = 0;
+  for (int d : dag) dn += d ? 1 : -1;
+  return OpKey{K_T0 + dn, 1000 + (int)dag.size(), code, k2tot};
+}
+void x_terms(int l, const int* pos, const int* dag, const std::vector<int>& kl, std::vector<XTerm>& out) {
+  out.clear();
+  if (l == 0) { out.push_back({kIdentityKey, 0, 1.0}); return; }
+  if (l >= 3) {
+    std::vector<int> d(dag, dag + l);
+    out.push_back({string_key(d, kl, kl.back()), 0, 1.0});
+    return;
+  }
+  const int kx = l == 2 ? kl[0] : 1;
+  if (l == 1) { out.push_back({OpKey{K_C, pos[0], 0, 1}, dag[0] ? 0 : 1, 1.0}); return; }
+  int u = pos[0], v = pos[1];
+  if (dag[0] && dag[1]) {
+    if (!(u == v && kx == 2)) out.push_back({OpKey{K_A, u, v, kx}, 0, 1.0});
+  } else if (!dag[0] && !dag[1]) {
+    // [a~_u a~_v]^k = -adj(A^k_uv)
+    if (!(u == v && kx == 2)) out.push_back({OpKey{K_A, u, v, kx}, 1, -1.0});
+  } else if (dag[0]) {
+    out.push_back({OpKey{K_B, u, v, kx}, 0, 1.0});
+  } else if (u < v) {
+    // [a~_u a+_v]^k = (-1)^k B^k_vu = adj(B^k_uv)
+    out.push_back({OpKey{K_B, u, v, kx}, 1, 1.0});
+  } else {
+    // same orbital: [a~_u a+_u]^k = (-1)^k B^k_uu + sqrt2 delta_k0
+    out.push_back({OpKey{K_B, u, u, kx}, 0, kx ? -1.0 : 1.0});
+    if (kx == 0) out.push_back({kIdentityKey, 0, kSqrt2});
+  }
+}
+
+}  // namespace
+
+void Engine::rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rparent, const PsiLayout& P,
+                      const double* psi, const std::vector<size_t>& elems, RdmAcc& acc) {
+  const int n = n_;
+  const size_t nn = (size_t)n * n;
+  // ---------------------------------------------------------------- requests
+  struct VKey {
+    int y, s, kX;
+    OpKey x;
+    int adj;
+    bool operator<(const VKey& o) const {
+      if (y != o.y) return y < o.y;
+      if (s != o.s) return s < o.s;
+      if (kX != o.kX) return kX < o.kX;
+      if (adj != o.adj) return adj < o.adj;
+      return x < o.x;
+    }
+  };
+  struct Contrib {
+    size_t target;
+    int order;
+    double c;
+    int v;
+  };
+  std::map<std::pair<std::vector<int>, std::vector<int>>, int> s_index;
+  std::vector<SiteOp> s_ops;
+  std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, int> y_index;
+  std::vector<Operand> y_ops;
+  std::vector<std::pair<OpKey, SiteOp>> y_temps;  // site strings on the last site
+  std::map<VKey, int> v_index;
+  std::vector<VKey> vkeys;
+  std::vector<Contrib> contribs;
+  std::map<std::tuple<int, int, int, int, std::vector<std::pair<int, int>>>, std::vector<Variant>> vcache;
+  const bool last = (i == n - 2);
+  std::vector<XTerm> xt;
+  for (size_t e : elems) {
+    int order, pos[4], dag[4];
+    std::vector<std::pair<int, int>> pairs;
+    size_t target;
+    if (e < nn) {
+      order = 1;
+      pos[0] = (int)(e / n);
+      pos[1] = (int)(e % n);
+      dag[0] = 1;
+      dag[1] = 0;
+      pairs = {{0, 1}};
+      target = e;
+    } else {
+      order = 2;
+      size_t t = e - nn;
+      target = t;
+      pos[3] = (int)(t % n); t /= n;
+      pos[2] = (int)(t % n); t /= n;
+      pos[1] = (int)(t % n); t /= n;
+      pos[0] = (int)t;
+      dag[0] = dag[1] = 1;
+      dag[2] = dag[3] = 0;
+      pairs = {{0, 3}, {1, 2}};
+    }
+    const int m = order == 1 ? 2 : 4;
+    SortedOps so = sort_ops(pos, dag, m, pairs);
+    int l = 0, s = 0, y = 0;
+    for (int k = 0; k < m; ++k) {
+      if (so.pos[k] < i) ++l;
+      else if (so.pos[k] == i) ++s;
+      else ++y;
+    }
+    if ((l > 2 && (i != 1 || so.pos[l - 1] != 0)) || (!last && y > 1))
+      throw std::runtime_error("internal: RDM element assigned to the wrong bond");
+    int dmask = 0;
+    for (int k = 0; k < m; ++k) dmask |= so.dag[k] << k;
+    auto ck = std::make_tuple(l, s, y, dmask, so.pairs);
+    auto it = vcache.find(ck);
+    if (it == vcache.end())
+      it = vcache.emplace(ck, expand_split(l, s, y, std::vector<int>(so.dag, so.dag + m), so.pairs)).first;
+    for (const Variant& v : it->second) {
+      x_terms(l, so.pos, so.dag, v.kl, xt);
+      // site string
+      std::vector<int> sd(so.dag + l, so.dag + l + s);
+      auto sk = std::make_pair(sd, v.ks);
+      auto si = s_index.find(sk);
+      if (si == s_index.end()) {
+        si = s_index.emplace(sk, (int)s_ops.size()).first;
+        s_ops.push_back(site_string(sd, v.ks));
+      }
+      // right operand
+      std::vector<int> yd(so.dag + l + s, so.dag + m);
+      int ypos = y > 0 ? so.pos[l + s] : -1;
+      auto yk = std::make_tuple(y, y == 1 ? ypos : -1, yd, v.ky);
+      auto yi = y_index.find(yk);
+      if (yi == y_index.end()) {
+        yi = y_index.emplace(yk, (int)y_ops.size()).first;
+        if (y == 0) {
+          y_ops.push_back(op_id());
+        } else if (y == 1) {
+          y_ops.push_back(op_blk(K_C, ypos, 0, 1, yd[0] ? 0 : 1));
+        } else {
+          SiteOp so2 = site_string(yd, v.ky);
+          OpKey key{K_T0 + so2.dn, (int)y_temps.size(), 0, so2.k2};
+          y_temps.push_back({key, so2});
+          y_ops.push_back(op_blk(key.kind, key.i, 0, key.k2));
+        }
+      }
+      for (const XTerm& x : xt) {
+        VKey vk{yi->second, si->second, v.kX, x.key, x.adj};
+        auto vi = v_index.find(vk);
+        if (vi == v_index.end()) {
+          vi = v_index.emplace(vk, (int)vkeys.size()).first;
+          vkeys.push_back(vk);
+        }
+        contribs.push_back({target, order, so.sign * v.c * x.f, vi->second});
+      }
+    }
+  }
+  if (vkeys.empty()) return;
+  // site strings of the last site as operators of R'
+  if (!y_temps.empty()) {
+    std::vector<OpKey> keys;
+    std::vector<std::pair<OpKey, Term>> terms;
+    for (auto& [k, so2] : y_temps) {
+      keys.push_back(k);
+      Term t;
+      t.x = op_site(so2);
+      t.y = op_id();
+      t.k2 = so2.k2;
+      t.coef = 1.0;
+      terms.push_back({k, t});
+    }
+    Re.ops->allocate(keys);
+    place_terms(Rparent, nullptr, Re, terms);
+  }
+  // ---------------------------------------------------------------- N_Y on L'
+  const Basis& LB = Le.ops->basis;
+  const Basis& RB = Re.ops->basis;
+  OpSet& ro = *Re.ops;
+  std::vector<double*> Nbuf(y_ops.size(), nullptr);
+  std::vector<int> Ndn(y_ops.size()), Nk(y_ops.size());
+  std::vector<void*> scratch;
+  for (size_t yi = 0; yi < y_ops.size(); ++yi) {
+    const Operand& Y = y_ops[yi];
+    const int dnX = -Y.dn, kY = Y.k2;
+    Ndn[yi] = dnX;
+    Nk[yi] = kY;
+    const Layout& NL = Le.ops->layout(dnX, kY);
+    if (NL.size == 0) continue;
+    double* N = (double*)be_->alloc(NL.size * sizeof(double));
+    be_->memset0(N, NL.size * sizeof(double));
+    Nbuf[yi] = N;
+    // T(a', b', b) = psi(a', b') op(Y)(b', b)
+    struct TB { const double* ptr; int rows, cols, ld; int ap, bp, b; };
+    std::vector<TB> tbs;
+    size_t tsz = 0;
+    std::vector<std::pair<size_t, int>> tdef;  // (offset, index into pending GEMMs)
+    GemmBuilder g1;
+    double* T = nullptr;
+    std::vector<std::tuple<int, int, int, SrcBlock, int, size_t>> pend;  // ap, bp, b, Yblk, psi blk, toff
+    for (auto& pb : P.blk) {
+      int ap = pb.a, bp = pb.b;
+      for (size_t b = 0; b < RB.sec.size(); ++b) {
+        if (RB.sec[bp].n != RB.sec[b].n + Y.dn || !triangle(RB.sec[b].j, Y.k2, RB.sec[bp].j)) continue;
+        SrcBlock yb = find_block(ro, nullptr, Y, bp, (int)b);
+        if (!yb.ok) continue;
+        pend.push_back({ap, bp, (int)b, yb, 0, tsz});
+        if (Y.t != Operand::ID) tsz += (size_t)pb.rows * RB.sec[b].dim;
+      }
+    }
+    if (tsz > 0) {
+      T = (double*)be_->alloc(tsz * sizeof(double));
+      be_->memset0(T, tsz * sizeof(double));
+      scratch.push_back(T);
+    }
+    GemmBuilder g2;
+    for (auto& [ap, bp, b, yb, unused, toff] : pend) {
+      (void)unused;
+      int pi = P.find(ap, bp);
+      const auto& pbk = P.blk[pi];
+      const double* Tp;
+      int ldT;
+      if (Y.t == Operand::ID) {
+        Tp = psi + pbk.off;
+        ldT = pbk.cols;
+      } else {
+        g1.add(T + toff, pbk.rows, RB.sec[b].dim, RB.sec[b].dim,
+               GemmSeg{psi + pbk.off, yb.ptr, pbk.cols, pbk.cols, yb.ld, 0, yb.trans, yb.coef});
+        Tp = T + toff;
+        ldT = RB.sec[b].dim;
+      }
+      // N(a', a) += c * T psi(a, b)^T
+      for (size_t a = 0; a < LB.sec.size(); ++a) {
+        int ki = P.find((int)a, b);
+        if (ki < 0) continue;
+        int ni = NL.find(ap, (int)a);
+        if (ni < 0) continue;
+        double c = hpsi_coef(LB.sec[ap].j, RB.sec[bp].j, LB.sec[a].j, RB.sec[b].j, kY, two_s_);
+        if (c == 0.0) continue;
+        if ((Y.par & LB.sec[a].n) & 1) c = -c;
+        if (Y.t == Operand::ID) c *= yb.coef;
+        const auto& kb = P.blk[ki];
+        g2.add(N + NL.blk[ni].off, pbk.rows, kb.rows, NL.blk[ni].cols,
+               GemmSeg{Tp, psi + kb.off, kb.cols, ldT, kb.cols, 0, 1, c});
+      }
+    }
+    g1.run(be_, Precision::FP64);
+    g2.run(be_, Precision::FP64);
+  }
+  // ---------------------------------------------------------------- W = adjoint placement of N
+  // group requests by (y, s, kX, adj, stored layout of x)
+  struct WKey {
+    int y, s, kX, adj, dn, k2;
+    bool operator<(const WKey& o) const {
+      return std::tie(dn, k2, y, s, kX, adj) < std::tie(o.dn, o.k2, o.y, o.s, o.kX, o.adj);
+    }
+  };
+  std::map<WKey, int> w_col;                     // column within its layout's W stack
+  std::map<std::pair<int, int>, int> w_count;    // per stored layout
+  std::vector<int> v_col(vkeys.size());
+  for (size_t v = 0; v < vkeys.size(); ++v) {
+    const VKey& k = vkeys[v];
+    WKey wk{k.y, k.s, k.kX, k.adj, kind_dn(k.x.kind), k.x.k2};
+    auto it = w_col.find(wk);
+    if (it == w_col.end()) it = w_col.emplace(wk, w_count[{wk.dn, wk.k2}]++).first;
+    v_col[v] = it->second;
+  }
+  std::vector<std::vector<const EnlComp*>> by(LB.sec.size());
+  for (auto& c : Le.comps) by[c.esec].push_back(&c);
+  const Basis& bb = Lb.ops->basis;
+  std::map<std::pair<int, int>, double*> wstack;
+  for (auto& [lk, cnt] : w_count) {
+    const Layout& XL = Lb.ops->layout(lk.first, lk.second);
+    double* Wb = (double*)be_->alloc(std::max<size_t>(1, XL.size * cnt) * sizeof(double));
+    be_->memset0(Wb, std::max<size_t>(1, XL.size * cnt) * sizeof(double));
+    wstack[lk] = Wb;
+    scratch.push_back(Wb);
+  }
+  PlaceBuilder pb;
+  for (auto& [wk, col] : w_col) {
+    double* N = Nbuf[wk.y];
+    if (!N) continue;
+    const Layout& NL = Le.ops->layout(Ndn[wk.y], Nk[wk.y]);
+    const Layout& XL = Lb.ops->layout(wk.dn, wk.k2);
+    if (XL.size == 0) continue;
+    double* W = wstack[{wk.dn, wk.k2}] + (size_t)col * XL.size;
+    const SiteOp& so = s_ops[wk.s];
+    for (auto& blk : NL.blk) {
+      int Jp = LB.sec[blk.bra].j, J = LB.sec[blk.ket].j;
+      for (const EnlComp* cp : by[blk.bra])
+        for (const EnlComp* c : by[blk.ket]) {
+          double sv = so.m[cp->site][c->site];
+          if (sv == 0.0) continue;
+          int lp = cp->bsec, l = c->bsec;
+          int xb;
+          double ac = 1.0;
+          if (!wk.adj) {
+            if (bb.sec[lp].n != bb.sec[l].n + wk.dn) continue;
+            xb = XL.find(lp, l);
+          } else {
+            if (bb.sec[l].n != bb.sec[lp].n + wk.dn) continue;
+            xb = XL.find(l, lp);
+            ac = adjoint_coef(bb.sec[lp].j, bb.sec[l].j, wk.k2);
+          }
+          if (xb < 0) continue;
+          double tp = tensor_product_coef(bb.sec[lp].j, bb.sec[l].j, wk.k2, kSiteJ[cp->site], kSiteJ[c->site],
+                                          so.k2, Jp, J, wk.kX);
+          if (tp == 0.0) continue;
+          double sign = ((so.parity & bb.sec[l].n) & 1) ? -1.0 : 1.0;
+          double alpha = tp * sv * sign * ac;
+          const auto& xbk = XL.blk[xb];
+          const double* src = N + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
+          pb.add(W + xbk.off, xbk.rows, xbk.cols, xbk.cols, PlaceSeg{src, blk.cols, wk.adj, alpha});
+        }
+    }
+  }
+  pb.run(be_);
+  // ---------------------------------------------------------------- V = <x, W> for all stored x
+  std::map<OpKey, std::pair<double*, int>> xrow;  // op -> (V run, row)
+  std::vector<std::pair<double*, size_t>> vruns;  // host copies
+  std::vector<std::tuple<double*, int, int>> runs_dev;  // (device V, rows, cols)
+  GemmBuilder gv;
+  std::vector<std::pair<std::vector<double>, std::tuple<double*, int, int>>> host_v;
+  for (auto& [lk, cnt] : w_count) {
+    const Layout& XL = Lb.ops->layout(lk.first, lk.second);
+    if (XL.size == 0) continue;
+    std::vector<std::pair<double*, OpKey>> ops;
+    for (auto& [k, p] : Lb.ops->ops)
+      if (kind_dn(k.kind) == lk.first && k.k2 == lk.second) ops.push_back({p, k});
+    std::sort(ops.begin(), ops.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    size_t r0 = 0;
+    while (r0 < ops.size()) {
+      size_t r1 = r0 + 1;
+      while (r1 < ops.size() && ops[r1].first == ops[r1 - 1].first + XL.size) ++r1;
+      int rows = (int)(r1 - r0);
+      double* V = (double*)be_->alloc((size_t)rows * cnt * sizeof(double));
+      be_->memset0(V, (size_t)rows * cnt * sizeof(double));
+      scratch.push_back(V);
+      for (size_t r = r0; r < r1; ++r) xrow[ops[r].second] = {V, (int)(r - r0)};
+      // V (rows x cnt) = X (rows x size) W^T, the K dimension in panels
+      const size_t panel = 1 << 22;
+      for (size_t c0 = 0; c0 < XL.size; c0 += panel) {
+        int kc = (int)std::min(panel, XL.size - c0);
+        gv.add(V, rows, cnt, cnt,
+               GemmSeg{ops[r0].first + c0, wstack[lk] + c0, kc, (int)XL.size, (int)XL.size, 0, 1, 1.0});
+      }
+      runs_dev.push_back({V, rows, cnt});
+      r0 = r1;
+    }
+  }
+  gv.run(be_, Precision::FP64);
+  std::map<double*, std::vector<double>> vhost;
+  for (auto& [V, rows, cols] : runs_dev) {
+    auto& h = vhost[V];
+    h.resize((size_t)rows * cols);
+    be_->copy_d2h(h.data(), V, h.size() * sizeof(double));
+  }
+  be_->sync();
+  // ---------------------------------------------------------------- assemble
+  std::vector<double> val(vkeys.size(), 0.0);
+  for (size_t v = 0; v < vkeys.size(); ++v) {
+    auto it = xrow.find(vkeys[v].x);
+    if (it == xrow.end() || !Nbuf[vkeys[v].y]) continue;  // operator absent (zero by symmetry)
+    const auto& h = vhost[it->second.first];
+    int cnt = w_count[{kind_dn(vkeys[v].x.kind), vkeys[v].x.k2}];
+    val[v] = h[(size_t)it->second.second * cnt + v_col[v]];
+  }
+  for (auto& c : contribs) {
+    if (c.order == 1) acc.g1[c.target] += c.c * val[c.v];
+    else acc.g2[c.target] += c.c * val[c.v];
+  }
+  for (double* N : Nbuf)
+    if (N) be_->free(N);
+  for (void* p : scratch) be_->free(p);
+}
+
+void Engine::rdm12(double* gamma, double* Gamma) {
+  if (!prev_.valid) throw std::runtime_error("state: no sweep has run");
+  if (n_ < 3 || prev_.bond != 1 || (int)LU_.size() < 2 || !LU_[1])
+    throw std::runtime_error("state: the RDMs are taken at bond 1, the end of a full sweep");
+  const int n = n_;
+  const size_t nn = (size_t)n * n, n4 = nn * nn;
+  // bond of every element (1-RDM: index p*n+q; 2-RDM: nn + ((p*n+q)*n+r)*n+s)
+  std::vector<std::vector<size_t>> at(n - 1);
+  // (bond 0 is folded into bond 1, whose left block is site 0 itself)
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) at[std::max(1, std::min(n - 2, std::max(p, q)))].push_back((size_t)p * n + q);
+  for (size_t t = 0; t < n4; ++t) {
+    int x[4] = {(int)(t / (nn * n)), (int)(t / nn % n), (int)(t / n % n), (int)(t % n)};
+    std::sort(x, x + 4);
+    at[std::max(1, std::min(n - 2, x[2]))].push_back(nn + t);
+  }
+  const Options saved = opt_;
+  rdm_mode_ = true;
+  opt_.prec_renorm = Precision::FP64;
+  opt_.D = 1 << 30;  // keep the whole support when moving the state
+  RdmAcc acc;
+  acc.g1.assign(nn, 0.0);
+  acc.g2.assign(n4, 0.0);
+  std::vector<void*> owned;
+  try {
+    auto vac = vacuum(true);
+    auto E0 = enlarge(*vac, 0);
+    {
+      // strings of three and four operators on site 0 (elements with x3 = 0)
+      std::vector<OpKey> keys;
+      std::vector<std::pair<OpKey, Term>> terms;
+      for (int len = 3; len <= 4; ++len) {
+        std::vector<std::vector<int>> KL;
+        seq_ranks(len, KL);
+        for (int mask = 0; mask < (1 << len); ++mask) {
+          std::vector<int> d(len);
+          for (int b = 0; b < len; ++b) d[b] = (mask >> (len - 1 - b)) & 1;
+          for (auto& kl : KL) {
+            SiteOp so = site_string(d, kl);
+            if (so.zero()) continue;
+            OpKey key = string_key(d, kl, kl.back());
+            keys.push_back(key);
+            Term t;
+            t.x = op_id();
+            t.y = op_site(so);
+            t.k2 = so.k2;
+            t.coef = 1.0;
+            terms.push_back({key, t});
+          }
+        }
+      }
+      E0->ops->allocate(keys);
+      place_terms(*vac, nullptr, *E0, terms);
+    }
+    std::unique_ptr<Block> Lb = renormalize(*E0, *LU_[1], false);
+    auto add_identity = [&](Block& B) {
+      B.ops->allocate({kIdentityKey});
+      double* I = B.ops->get(kIdentityKey);
+      const Layout& L = B.ops->layout(0, 0);
+      if (!I || L.size == 0) return;
+      std::vector<double> h(L.size, 0.0);
+      for (auto& bl : L.blk)
+        if (bl.bra == bl.ket)
+          for (int r = 0; r < bl.rows; ++r) h[bl.off + (size_t)r * bl.cols + r] = 1.0;
+      be_->copy_h2d(I, h.data(), h.size() * sizeof(double));
+    };
+    add_identity(*Lb);
+    auto Le = enlarge(*Lb, 1);
+    auto Re = enlarge(*R_[n - 3], 2);
+    PsiLayout P = make_psi(Le->ops->basis, Re->ops->basis, n_elec_, two_s_);
+    if (P.size != prev_.len) throw std::runtime_error("internal: RDM pass layout differs from the state");
+    double* psi = (double*)be_->alloc(std::max<size_t>(P.size, 1) * sizeof(double));
+    owned.push_back(psi);
+    be_->copy_d2d(psi, prev_.psi, P.size * sizeof(double));
+    for (int i = 1; i <= n - 2; ++i) {
+      rdm_bond(i, *Lb, *Le, *Re, *R_[n - i - 2], P, psi, at[i], acc);
+      if (i == n - 2) break;
+      // move the state to bond i+1, keeping its whole support
+      HPsiPlan plan;
+      plan.psi = P;
+      double tr = 0.0;
+      auto U = decimate(*Le, plan, psi, true, &tr);
+      auto Lnext = renormalize(*Le, *U, false);
+      add_identity(*Lnext);
+      auto Le2 = enlarge(*Lnext, i + 1);
+      auto Re2 = enlarge(*R_[n - i - 3], i + 2);
+      PsiLayout P2 = make_psi(Le2->ops->basis, Re2->ops->basis, n_elec_, two_s_);
+      Prev from;
+      from.valid = true;
+      from.bond = i;
+      from.Lb = Le->ops->basis;
+      from.Rb = Re->ops->basis;
+      from.Lc = Le->comps;
+      from.Rc = Re->comps;
+      for (auto& b : P.blk) from.blk.push_back({b.a, b.b, b.rows, b.cols, (int)b.off});
+      from.psi = psi;
+      from.len = P.size;
+      double* psi2 = (double*)be_->alloc(std::max<size_t>(P2.size, 1) * sizeof(double));
+      owned.push_back(psi2);
+      move_lr(from, *U, *RU_[n - i - 2], *Le2, *Re2, P2, psi2);
+      from.psi = nullptr;
+      be_->sync();
+      be_->free(psi);
+      owned.erase(std::find(owned.begin(), owned.end(), (void*)psi));
+      psi = psi2;
+      Lb = std::move(Lnext);
+      Le = std::move(Le2);
+      Re = std::move(Re2);
+      P = P2;
+    }
+  } catch (...) {
+    for (void* p : owned) be_->free(p);
+    rdm_mode_ = false;
+    opt_ = saved;
+    throw;
+  }
+  for (void* p : owned) be_->free(p);
+  rdm_mode_ = false;
+  opt_ = saved;
+  std::copy(acc.g1.begin(), acc.g1.end(), gamma);
+  std::copy(acc.g2.begin(), acc.g2.end(), Gamma);
 }
 
 }  // namespace dmrg

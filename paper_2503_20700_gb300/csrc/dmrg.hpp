@@ -61,7 +61,9 @@ struct Layout {
   int find(int bra, int ket) const { return lut[(size_t)bra * nket + ket]; }
 };
 
-enum Kind { K_H = 0, K_C, K_S, K_A, K_B, K_P, K_QJ, K_QK };
+enum Kind { K_H = 0, K_C, K_S, K_A, K_B, K_P, K_QJ, K_QK,
+            // temporaries of the RDM pass with particle change -2 .. 2
+            K_TM2, K_TM1, K_T0, K_TP1, K_TP2 };
 
 struct OpKey {
   int kind, i, j, k2;
@@ -74,6 +76,7 @@ struct OpKey {
 };
 
 inline int kind_dn(int kind) {
+  if (kind >= K_TM2) return kind - K_T0;
   switch (kind) {
     case K_C: return 1;
     case K_S: return -1;
@@ -82,7 +85,10 @@ inline int kind_dn(int kind) {
     default: return 0;
   }
 }
-inline int kind_parity(int kind) { return (kind == K_C || kind == K_S) ? 1 : 0; }
+inline int kind_parity(int kind) {
+  if (kind >= K_TM2) return (kind - K_T0) & 1;
+  return (kind == K_C || kind == K_S) ? 1 : 0;
+}
 
 // A set of operators on one basis, with one device allocation per layout.
 struct OpSet {
@@ -174,6 +180,11 @@ class Engine {
   int right_dim(int m) const;
   // Two-site wavefunction at the last optimised bond (for RDMs / checks)
   int last_bond() const { return last_bond_; }
+  // Spin-free one- and two-particle RDMs (Eqs. onerdm, twordm) of the
+  // two-site wavefunction of the last optimised bond, which must be bond 1
+  // (the end of a full sweep):  gamma[p*n+q] = <sum_s a+_ps a_qs>,
+  // Gamma[((p*n+q)*n+r)*n+s] = <sum_st a+_ps a+_qt a_rt a_ss>.
+  void rdm12(double* gamma, double* Gamma);
 
   Backend* backend() const { return be_; }
 
@@ -212,6 +223,12 @@ class Engine {
   bool right_normal(int m) const { return m < tR_; }
 
   SweepStats stats_;
+  bool rdm_mode_ = false;  // blocking builds only C and the normal pairs
+  struct RdmAcc;
+  void rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rparent, const struct PsiLayout& P,
+                const double* psi, const std::vector<size_t>& elems, RdmAcc& acc);
+  void move_lr(const Prev& from, const SavedU& U, const SavedU& V, const Block& Le, const Block& Re,
+               const struct PsiLayout& P, double* psi);
   std::unique_ptr<Block> vacuum(bool left);
   std::unique_ptr<Block> enlarge(const Block& b, int site);
   void place_terms(const Block& b, const OpSet* tmp, Block& e,

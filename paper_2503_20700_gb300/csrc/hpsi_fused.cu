@@ -366,19 +366,28 @@ __global__ void hpsi_reduce_kernel(const HpsiBlock* __restrict__ blocks, const H
 
 }  // namespace
 
-size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, int max_items, std::vector<HpsiTask>& tasks,
+void hpsi_tile(Precision prec, int* tile_m, int* tile_n) {
+  *tile_m = prec == Precision::TC_TF32X3 ? 128 : T;
+  *tile_n = T;
+}
+
+size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, Precision prec, std::vector<HpsiTask>& tasks,
                        std::vector<HpsiReduce>& reds) {
   tasks.clear();
   reds.clear();
+  int tm, tn;
+  hpsi_tile(prec, &tm, &tn);
+  long long tile_items = 0;
+  for (auto& b : blocks) tile_items += (long long)b.item_count * ((b.m + tm - 1) / tm) * ((b.n + tn - 1) / tn);
+  const int max_items = (int)std::max<long long>(4, tile_items / (8 * 152) + 1);
   long long part = 0;
-  if (max_items < 1) max_items = 1;
   for (size_t b = 0; b < blocks.size(); ++b) {
     const HpsiBlock& bk = blocks[b];
     if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
     int nch = (bk.item_count + max_items - 1) / max_items;
     int per = (bk.item_count + nch - 1) / nch;
-    for (int r0 = 0; r0 < bk.m; r0 += T)
-      for (int c0 = 0; c0 < bk.n; c0 += T) {
+    for (int r0 = 0; r0 < bk.m; r0 += tm)
+      for (int c0 = 0; c0 < bk.n; c0 += tn) {
         if (nch == 1) {
           tasks.push_back({(int)b, r0, c0, bk.item_begin, bk.item_count, -1});
         } else {
@@ -387,7 +396,7 @@ size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, int max_items, std:
             int i0 = bk.item_begin + c * per;
             int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
             tasks.push_back({(int)b, r0, c0, i0, cnt, part});
-            part += T * T;
+            part += (long long)tm * tn;
           }
         }
       }
@@ -396,7 +405,12 @@ size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, int max_items, std:
 }
 
 void hpsi_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
-                 const HpsiReduce* reds, int nreds, double* scratch, Precision prec, cudaStream_t st) {
+                 const HpsiReduce* reds, int nreds, double* scratch, Precision prec, int* err,
+                 cudaStream_t st) {
+  if (prec == Precision::TC_TF32X3) {
+    hpsi_tc_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, err, st);
+    return;
+  }
   if (ntasks > 0) {
     if (prec == Precision::FP64) {
       size_t smem = (size_t)(3 * KS * (T + 1) + T * (T + 1)) * sizeof(double);

@@ -229,3 +229,129 @@ const SiteAlgebra& site_algebra() {
 }
 
 }  // namespace dmrg
+
+namespace dmrg {
+
+SiteOp site_string(const std::vector<int>& dag, const std::vector<int>& k2) {
+  Mat4 cu = cdag(true), cd = cdag(false);
+  Mat4 au = transpose(cu), ad = transpose(cd);
+  Mat4 mau = au;
+  for (auto& r : mau) for (auto& x : r) x = -x;
+  const Tensor C{{1, cu}, {-1, cd}};
+  const Tensor D{{1, ad}, {-1, mau}};
+  if (dag.empty()) {
+    Mat4 eye = zero4();
+    for (int i = 0; i < 4; ++i) eye[i][i] = 1.0;
+    return reduce(Tensor{{0, eye}}, 0, 0, 0);
+  }
+  Tensor T = dag[0] ? C : D;
+  int kt = 1, dn = dag[0] ? 1 : -1;
+  for (size_t i = 1; i < dag.size(); ++i) {
+    int k = k2.at(i - 1);
+    T = couple(T, kt, dag[i] ? C : D, 1, k);
+    kt = k;
+    dn += dag[i] ? 1 : -1;
+  }
+  return reduce(T, kt, dn, (int)(dag.size() & 1));
+}
+
+std::vector<double> tree_tensor(const std::vector<TreeNode>& tree, int n) {
+  // per node: map (M2, mask) -> value
+  std::vector<std::map<std::pair<int, int>, double>> val(tree.size());
+  std::vector<int> rank(tree.size(), 1);
+  for (size_t i = 0; i < tree.size(); ++i) {
+    const TreeNode& t = tree[i];
+    if (t.slot >= 0) {
+      val[i][{1, 0}] = 1.0;                  // component +1/2
+      val[i][{-1, 1 << t.slot}] = 1.0;       // component -1/2
+      rank[i] = 1;
+      continue;
+    }
+    rank[i] = t.k2;
+    for (auto& [ka, va] : val[t.l])
+      for (auto& [kb, vb] : val[t.r]) {
+        int M = ka.first + kb.first;
+        if (std::abs(M) > t.k2) continue;
+        double c = clebsch(rank[t.l], ka.first, rank[t.r], kb.first, t.k2, M);
+        if (c == 0.0) continue;
+        val[i][{M, ka.second | kb.second}] += c * va * vb;
+      }
+  }
+  std::vector<double> out((size_t)1 << n, 0.0);
+  for (auto& [k, v] : val.back())
+    if (k.first == 0) out[k.second] += v;
+  return out;
+}
+
+std::vector<double> pairing_tensor(const std::vector<int>& dag,
+                                   const std::vector<std::pair<int, int>>& pairs, int n) {
+  std::vector<double> out((size_t)1 << n, 0.0);
+  const int np = (int)pairs.size();
+  for (int sp = 0; sp < (1 << np); ++sp) {  // spin of each pair: bit set = down
+    int mask = 0;
+    double f = 1.0;
+    for (int p = 0; p < np; ++p) {
+      bool down = (sp >> p) & 1;
+      int i = pairs[p].first, j = pairs[p].second;
+      for (int slot : {i, j}) {
+        if (dag[slot]) {
+          if (down) mask |= 1 << slot;      // a+_dn = o(-1/2)
+        } else {
+          if (!down) {                      // a_up = -o~(-1/2)
+            mask |= 1 << slot;
+            f = -f;
+          }                                 // a_dn = o~(+1/2)
+        }
+      }
+    }
+    out[mask] += f;
+  }
+  return out;
+}
+
+std::vector<double> expand_invariant(const std::vector<double>& target,
+                                     const std::vector<std::vector<double>>& basis, double* res) {
+  const size_t m = basis.size(), L = target.size();
+  // normal equations (m <= 4), solved by Gaussian elimination with pivoting
+  std::vector<std::vector<double>> A(m, std::vector<double>(m + 1, 0.0));
+  for (size_t a = 0; a < m; ++a) {
+    for (size_t b = 0; b < m; ++b)
+      for (size_t e = 0; e < L; ++e) A[a][b] += basis[a][e] * basis[b][e];
+    for (size_t e = 0; e < L; ++e) A[a][m] += basis[a][e] * target[e];
+  }
+  std::vector<double> c(m, 0.0);
+  std::vector<int> piv_col;
+  std::vector<size_t> rows(m);
+  for (size_t i = 0; i < m; ++i) rows[i] = i;
+  // eliminate; dependent basis tensors get coefficient 0
+  std::vector<int> pivot_of_col(m, -1);
+  size_t r = 0;
+  for (size_t col = 0; col < m && r < m; ++col) {
+    size_t best = r;
+    for (size_t i = r; i < m; ++i)
+      if (std::abs(A[i][col]) > std::abs(A[best][col])) best = i;
+    if (std::abs(A[best][col]) < 1e-12) continue;
+    std::swap(A[r], A[best]);
+    for (size_t i = 0; i < m; ++i) {
+      if (i == r) continue;
+      double f = A[i][col] / A[r][col];
+      for (size_t j = col; j <= m; ++j) A[i][j] -= f * A[r][j];
+    }
+    pivot_of_col[col] = (int)r;
+    ++r;
+  }
+  for (size_t col = 0; col < m; ++col)
+    if (pivot_of_col[col] >= 0) c[col] = A[pivot_of_col[col]][m] / A[pivot_of_col[col]][col];
+  if (res) {
+    double s = 0.0;
+    for (size_t e = 0; e < L; ++e) {
+      double v = target[e];
+      for (size_t a = 0; a < m; ++a) v -= c[a] * basis[a][e];
+      s += v * v;
+    }
+    *res = std::sqrt(s);
+  }
+  return c;
+}
+
+}  // namespace dmrg

@@ -84,3 +84,37 @@ struct SiteAlgebra {
 const SiteAlgebra& site_algebra();
 
 }  // namespace dmrg
+
+namespace dmrg {
+
+// ------------------------------------------------------------------ strings
+// Coupled tensor of a string of spinor operators on ONE site, written left to
+// right (dag[i]: a+ spinor, else a~ spinor), coupled sequentially
+// (((o0 o1)^{k2[0]} o2)^{k2[1]} ...): k2 holds the doubled intermediate ranks,
+// its last entry the rank of the whole string.  An empty string is the
+// identity.  Used for the on-site parts of the reduced density matrices.
+SiteOp site_string(const std::vector<int>& dag, const std::vector<int>& k2);
+
+// Invariant 4-index (or 2-index) tensors over the spinor components of a
+// string of rank-1/2 operators o_0 .. o_{n-1} (n = 2 or 4), entries indexed
+// by the bit mask of the components (bit i set: component -1/2 of o_i).
+//
+// A coupling tree is a list of nodes; node i is a leaf (slot >= 0) or joins
+// nodes l and r (l, r < i) to rank k2.  The last node is the root (rank 0).
+struct TreeNode {
+  int slot = -1;
+  int l = -1, r = -1, k2 = 0;
+};
+// T[mask] with  [tree]^0 = sum_mask T[mask] o_0(m_0) ... o_{n-1}(m_{n-1}).
+std::vector<double> tree_tensor(const std::vector<TreeNode>& tree, int n);
+// Spin-free pairing: sum over sigma of a+_{i sigma} ... a_{j sigma} for each
+// pair (i, j) of creator slot i and annihilator slot j, written in spinor
+// components (a+_up = o(+1/2), a+_dn = o(-1/2); a_dn = o~(+1/2), a_up = -o~(-1/2)).
+std::vector<double> pairing_tensor(const std::vector<int>& dag,
+                                   const std::vector<std::pair<int, int>>& pairs, int n);
+// Least-squares coefficients c with  target = sum_a c_a basis[a]  (exact when
+// target lies in the span; the residual is returned in *res if given).
+std::vector<double> expand_invariant(const std::vector<double>& target,
+                                     const std::vector<std::vector<double>>& basis, double* res = nullptr);
+
+}  // namespace dmrg

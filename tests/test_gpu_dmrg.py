@@ -228,7 +228,7 @@ def random_hpsi_problem(rng, n_blocks, max_dim, max_items, big=False):
     return cat(A_parts), cat(P_parts), cat(B_parts), co, blocks, items, refs
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-6), (4, 3e-6)])
 def test_fused_hpsi_against_numpy(pkg, prec, tol):
     rng = np.random.default_rng(11)
     A, P, B, clen, blocks, items, refs = random_hpsi_problem(rng, 12, 150, 6)
@@ -253,3 +253,35 @@ def test_fused_hpsi_many_items_split_into_chunks(pkg):
     assert np.array_equal(C1, C2)
     for off, m, n, ref in refs:
         assert np.abs(C1[off:off + m * n].reshape(m, n) - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_fused_hpsi_tcgen05_chunks_and_tails(pkg):
+    """tcgen05 kernel (128 x 64 sigma tiles): blocks spanning several row and
+    column tiles with ragged tails, hundreds of items split into chunks;
+    bitwise reproducible, and equal to the mma.sync kernel within the split
+    tolerance."""
+    rng = np.random.default_rng(9)
+    A, P, B, clen, blocks, items, refs = random_hpsi_problem(rng, 4, 300, 300)
+    C1 = np.zeros(clen)
+    C2 = np.zeros(clen)
+    C3 = np.zeros(clen)
+    pkg.ops.hpsi_contract(A, P, B, C1, blocks, items, precision=4)
+    pkg.ops.hpsi_contract(A, P, B, C2, blocks, items, precision=4)
+    pkg.ops.hpsi_contract(A, P, B, C3, blocks, items, precision=1)
+    assert np.array_equal(C1, C2)
+    for off, m, n, ref in refs:
+        scale = np.abs(ref).max()
+        got = C1[off:off + m * n].reshape(m, n)
+        assert np.abs(got - ref).max() < 3e-5 * scale
+        assert np.abs(got - C3[off:off + m * n].reshape(m, n)).max() < 3e-5 * scale
+
+
+@pytest.mark.parametrize("prec", ["SPLIT_HPSI", "SPLIT_HPSI_TC"])
+def test_split_hpsi_sweep_energy(pkg, prec):
+    """Whole sweeps with the split H_eff psi kernels: energy within 1e-5 Eh of
+    the FP64 path (|E| ~ 10 Eh, FP32 accumulation)."""
+    h, L = W.cholesky_random(8, 16, seed=2)
+    eri = W.eri_from_cholesky(L)
+    e64 = pkg.DMRG(h, eri=eri, n_elec=8, D=16).sweep(3)[0]
+    e32 = pkg.DMRG(h, eri=eri, n_elec=8, D=16, precision=getattr(pkg, prec)).sweep(3)[0]
+    assert abs(e32 - e64) < 1e-5
