@@ -245,6 +245,40 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                                int device);
 
 /*
+ * dmrg_hpsi_contract_noalloc -- the fused H_eff psi contraction of
+ * dmrg_hpsi_contract on caller-owned DEVICE buffers, allocating nothing.
+ * The paper has no counterpart: this entry exists for callers that cannot
+ * allocate device memory while they run -- code that records a CUDA graph by
+ * stream capture (cudaMalloc cannot be captured), latency-critical loops
+ * where an allocation would synchronise the device, and callers whose device
+ * memory is owned by another allocator (e.g. PyTorch's caching allocator).
+ *
+ * dA, dP, dB, dC: device pointers (lengths a_len .. c_len in doubles) on
+ * `device`; dC is updated in place.  blocks / items: host arrays, same meaning
+ * as for dmrg_hpsi_contract; every offset is checked against the lengths
+ * before anything is enqueued.  The call copies the task lists to a static
+ * device scratch of 32 MiB (file-scope __device__ array, one per device) and
+ * enqueues the copies and the kernels on `stream` (a cudaStream_t; NULL: the
+ * legacy default stream); it returns without synchronising.  A request whose
+ * task lists and partial tiles exceed the 32 MiB returns DMRG_EINVAL with the
+ * size it needed (use dmrg_hpsi_contract for it).  precision: DMRG_FP64 or
+ * DMRG_SPLIT_TF32.  Nothing in the scratch has to start at zero: every
+ * partial tile is written in full before the reduction reads it.
+ *
+ * The scratch is shared by all calls on a device: calls that overlap in time
+ * (two host threads, or two streams whose work is in flight together) race
+ * on it and give wrong results; serialise them.  The first call on a device
+ * looks up the scratch address (cudaGetSymbolAddress, with that device made
+ * current and then restored) and sets the kernels' shared-memory attributes;
+ * make that first call before any stream capture begins.
+ */
+dmrg_status dmrg_hpsi_contract_noalloc(const double* dA, int64_t a_len, const double* dP, int64_t p_len,
+                                       const double* dB, int64_t b_len, double* dC, int64_t c_len,
+                                       const dmrg_hpsi_block* blocks, int n_blocks,
+                                       const dmrg_hpsi_item* items, int n_items, int precision,
+                                       int device, void* stream);
+
+/*
  * dmrg_eigh_batched -- symmetric eigendecompositions in float64 on the device
  * (the sector density matrices of the decimation step, Sec. II.C).  mats holds
  * the row-major matrices back to back (sizes n[i]); w receives eigenvalues in

@@ -11,6 +11,7 @@
 #include "../../include/dmrgscf.h"
 #include "casscf.hpp"
 #include "hpsi_fused.cuh"
+#include "hpsi_noalloc.hpp"
 #include "dmrg.hpp"
 
 struct dmrg_ctx {
@@ -472,6 +473,66 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     be->sync();
   } catch (const std::exception& e) {
     return translate(nullptr, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_hpsi_contract_noalloc(const double* dA, int64_t a_len, const double* dP, int64_t p_len,
+                                       const double* dB, int64_t b_len, double* dC, int64_t c_len,
+                                       const dmrg_hpsi_block* blocks, int n_blocks,
+                                       const dmrg_hpsi_item* items, int n_items, int precision,
+                                       int device, void* stream) {
+  if (!dA || !dP || !dB || !dC || (!blocks && n_blocks) || (!items && n_items) || n_blocks < 0 ||
+      n_items < 0)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  if (precision != DMRG_FP64 && precision != DMRG_SPLIT_TF32)
+    return fail(nullptr, DMRG_EINVAL, "unsupported precision (DMRG_FP64 or DMRG_SPLIT_TF32)");
+  if (const char* m = check_hpsi(a_len, p_len, b_len, c_len, blocks, n_blocks, items, n_items))
+    return fail(nullptr, DMRG_EINVAL, m);
+  try {
+    std::vector<dmrg::HpsiBlock> hb;
+    std::vector<dmrg::HpsiItem> hi;
+    to_device_lists(blocks, n_blocks, items, n_items, dA, dP, dB, dC, hb, hi, nullptr);
+    const dmrg::Precision pr = precision == DMRG_FP64 ? dmrg::Precision::FP64 : dmrg::Precision::SPLIT_TF32;
+    std::vector<dmrg::HpsiTask> tasks;
+    std::vector<dmrg::HpsiReduce> reds;
+    size_t scr = dmrg::hpsi_plan_tasks(hb, pr, tasks, reds);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t ob = 0, oi = al(hb.size() * sizeof(dmrg::HpsiBlock));
+    size_t ot = al(oi + hi.size() * sizeof(dmrg::HpsiItem));
+    size_t orr = al(ot + tasks.size() * sizeof(dmrg::HpsiTask));
+    size_t os = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
+    size_t need = os + scr * sizeof(double);
+    if (need > dmrg::kNoAllocScratchBytes)
+      return fail(nullptr, DMRG_EINVAL,
+                  "request needs " + std::to_string(need) + " bytes of scratch; the allocation-free entry "
+                  "holds " + std::to_string(dmrg::kNoAllocScratchBytes) + " (use dmrg_hpsi_contract)");
+    void* base = nullptr;
+    cudaError_t e = dmrg::noalloc_scratch(device, &base);
+    if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
+    int prev = 0;
+    e = cudaGetDevice(&prev);
+    if (e == cudaSuccess) e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
+    cudaStream_t st = (cudaStream_t)stream;
+    char* d = (char*)base;
+    auto put = [&](size_t off, const void* h, size_t bytes) {
+      if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(d + off, h, bytes, cudaMemcpyHostToDevice, st);
+    };
+    put(ob, hb.data(), hb.size() * sizeof(dmrg::HpsiBlock));
+    put(oi, hi.data(), hi.size() * sizeof(dmrg::HpsiItem));
+    put(ot, tasks.data(), tasks.size() * sizeof(dmrg::HpsiTask));
+    put(orr, reds.data(), reds.size() * sizeof(dmrg::HpsiReduce));
+    if (e == cudaSuccess)
+      dmrg::hpsi_launch((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
+                        (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(),
+                        (const dmrg::HpsiReduce*)(d + orr), (int)reds.size(), (double*)(d + os), pr, nullptr,
+                        st);
+    cudaError_t e2 = cudaSetDevice(prev);
+    if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e2));
+  } catch (const std::exception& ex) {
+    return translate(nullptr, ex);
   }
   return DMRG_OK;
 }

@@ -52,6 +52,12 @@ def bind(lib):
                                        ctypes.POINTER(HpsiItem), ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int]
     lib.dmrg_hpsi_contract.restype = ctypes.c_int
+    vp = ctypes.c_void_p
+    lib.dmrg_hpsi_contract_noalloc.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                               vp, ctypes.c_int64, ctypes.POINTER(HpsiBlock), ctypes.c_int,
+                                               ctypes.POINTER(HpsiItem), ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, vp]
+    lib.dmrg_hpsi_contract_noalloc.restype = ctypes.c_int
     _bind_casscf(lib)
     _lib = lib
     return lib
@@ -79,6 +85,23 @@ def grouped_gemm(A, B, C, groups, segs, precision=0, device=0):
     if st != 0:
         raise DmrgError(st, lib.dmrg_last_error(None).decode())
     return C
+
+
+def hpsi_contract_noalloc(dA, a_len, dP, p_len, dB, b_len, dC, c_len, blocks, items, precision=0,
+                          device=0, stream=0):
+    """Allocation-free variant of hpsi_contract on device buffers: dA .. dC are
+    device addresses (ints, e.g. torch tensor data_ptr()) with their lengths in
+    doubles; the work is enqueued on `stream` (a cudaStream_t as int, 0: the
+    default stream) and the call returns without synchronising.  Calls on one
+    device must not overlap (they share one static scratch)."""
+    from . import load, DmrgError
+    lib = load()
+    ba = (HpsiBlock * max(1, len(blocks)))(*[HpsiBlock(*b) for b in blocks])
+    ia = (HpsiItem * max(1, len(items)))(*[HpsiItem(*i) for i in items])
+    st = lib.dmrg_hpsi_contract_noalloc(dA, a_len, dP, p_len, dB, b_len, dC, c_len, ba, len(blocks), ia,
+                                        len(items), precision, device, stream or None)
+    if st != 0:
+        raise DmrgError(st, lib.dmrg_last_error(None).decode())
 
 
 def hpsi_contract(A, P, B, C, blocks, items, precision=0, device=0):
