@@ -80,3 +80,37 @@ def orbital_transform(kappa, h, L, ncore, ncas):
     nb x nb tensor; the antisymmetric K is formed inside."""
     K = torch.tril(kappa, -1)
     return OrbitalTransform.apply(K - K.T, h, L, ncore, ncas)
+
+
+class DMRGEnergy(torch.autograd.Function):
+    """E(h, (pq|rs)) of a spin-adapted DMRG run (Sec. II.B-C) with a
+    hand-written backward from the reduced density matrices:
+
+        dE/dh_pq      = gamma~_pq
+        dE/d(pq|rs)   = 1/2 Gamma~_prsq
+
+    (Hellmann-Feynman: exact for the converged state, i.e. at stationarity of
+    the energy in the wavefunction parameters; for a truncated MPS it is the
+    derivative with the state held fixed).  Forward runs `sweeps` full sweeps
+    at bond dimension D and takes the RDMs of the final state."""
+
+    @staticmethod
+    def forward(ctx, h, eri, n_elec, two_s=0, D=64, sweeps=4, e_core=0.0, precision=0):
+        from . import DMRG
+        g = DMRG(_np(h), eri=_np(eri), n_elec=n_elec, two_s=two_s, D=D, e_core=e_core,
+                 precision=precision)
+        try:
+            e = g.sweep(sweeps)[0]
+            gamma, Gamma = g.rdm12()
+        finally:
+            g.close()
+        ctx.save_for_backward(torch.from_numpy(gamma), torch.from_numpy(Gamma))
+        ctx.dtype = h.dtype
+        return torch.tensor(e, dtype=h.dtype)
+
+    @staticmethod
+    def backward(ctx, gE):
+        gamma, Gamma = ctx.saved_tensors
+        dh = (gE.to(torch.float64) * gamma).to(ctx.dtype)
+        deri = (0.5 * gE.to(torch.float64) * Gamma.permute(0, 3, 1, 2)).to(ctx.dtype)
+        return dh, deri, None, None, None, None, None, None

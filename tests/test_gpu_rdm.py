@@ -97,3 +97,41 @@ def test_rdm_before_sweep_is_a_state_error(pkg):
     with pytest.raises(pkg.DmrgError) as ei:
         g.rdm12()
     assert ei.value.status == pkg.DMRG_ESTATE
+
+
+def test_dmrg_energy_autograd_hellmann_feynman(pkg):
+    """DMRGEnergy's backward (gamma~, 1/2 Gamma~) against central finite
+    differences of the DMRG energy at untruncated D, for perturbations of h
+    and of (pq|rs) that keep their symmetries."""
+    torch = pytest.importorskip("torch")
+    from paper_2503_20700_gb300.autograd import DMRGEnergy
+    n, N = 4, 4
+    h, L = W.cholesky_random(n, 8, seed=5)
+    eri = W.eri_from_cholesky(L)
+    ht = torch.tensor(h, requires_grad=True)
+    et = torch.tensor(eri, requires_grad=True)
+    E = DMRGEnergy.apply(ht, et, N, 0, 64, 3)
+    E.backward()
+    gh, ge = ht.grad.numpy(), et.grad.numpy()
+
+    def energy(hh, ee):
+        g = pkg.DMRG(hh, eri=ee, n_elec=N, two_s=0, D=64)
+        e = g.sweep(3)[0]
+        g.close()
+        return e
+
+    eps = 1e-4
+    for p, q in [(0, 0), (0, 1), (1, 3)]:
+        d = np.zeros((n, n))
+        d[p, q] += 1.0
+        if p != q:
+            d[q, p] += 1.0
+        fd = (energy(h + eps * d, eri) - energy(h - eps * d, eri)) / (2 * eps)
+        assert abs(fd - (gh * d).sum()) < 1e-6
+    for p, q, r, s in [(0, 0, 1, 1), (0, 1, 2, 3), (1, 2, 1, 3)]:
+        d = np.zeros((n,) * 4)
+        for a, b, c, e in {(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+                           (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)}:
+            d[a, b, c, e] = 1.0
+        fd = (energy(h, eri + eps * d) - energy(h, eri - eps * d)) / (2 * eps)
+        assert abs(fd - (ge * d).sum()) < 1e-6
