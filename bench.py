@@ -1,7 +1,8 @@
 """Benchmark of the spin-adapted DMRG sweep (H_eff psi TFLOP/s and sweep time).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cas40|pentacene|naphthalene] [--D 2048] [--precision split|fp64]
+                    [--workload cas40|casN|pentacene|naphthalene] [--D 256]
+                    [--precision split|split-tc|split-all|fp64]
 
 A step is one full two-site DMRG sweep (L->R then R->L: blocking, Davidson
 with H_eff psi, decimation, renormalisation) over the workload.  The warm-up
@@ -207,11 +208,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cas40")
-    ap.add_argument("--D", type=int, default=2048)
+    ap.add_argument("--D", type=int, default=256)
     ap.add_argument("--precision", default="split", choices=["split", "split-tc", "split-all", "fp64"],
                     help="split: 3xTF32 in H_eff psi, renormalisation in FP64; "
                          "split-all: 3xTF32 also in renormalisation; fp64: all FP64")

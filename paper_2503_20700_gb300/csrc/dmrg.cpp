@@ -1779,6 +1779,31 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   double e = davidson(plan, psi, &its) + e_core_;
   be_->check_device_flag();
   stats_.davidson_iters += its;
+  if (opt_.prec != Precision::FP64 && !l2r && i == 1) {
+    // The sweep energy (last bond) of a split-precision run: the Rayleigh
+    // quotient of the converged eigenvector with one float64 H_eff psi.  It is
+    // second order in the eigenvector's error, while the split product's own
+    // rounding (FP32 accumulation, ~1e-7 relative) would enter at first order.
+    HPsiPlan p64;
+    p64.in = plan.in;
+    p64.out = plan.out;
+    const Precision keep = opt_.prec;
+    opt_.prec = Precision::FP64;
+    plan_hpsi(*Le, *Re, p64);
+    opt_.prec = keep;
+    be_->copy_d2d(p64.in, psi, len * sizeof(double));
+    apply_hpsi(p64);
+    double* d2 = (double*)be_->alloc(2 * sizeof(double));
+    be_->dots(psi, 1, len, len, p64.out, d2);
+    be_->dots(psi, 1, len, len, psi, d2 + 1);
+    double h2[2];
+    be_->copy_d2h(h2, d2, sizeof(h2));
+    be_->sync();
+    be_->free(d2);
+    if (p64.dev) be_->free(p64.dev);
+    if (p64.diag) be_->free(p64.diag);
+    e = h2[0] / h2[1] + e_core_;
+  }
   double t4 = now_s();
   stats_.t_davidson += t4 - t3;
   std::unique_ptr<SavedU> U;

@@ -95,12 +95,18 @@ def test_naphthalene_d64_against_oracle_and_fci(pkg):
     assert eg[-1] - gold["e_fci"] < 1e-3            # D=64 is close to FCI here
 
 
-def test_split_tf32_energy_close_to_fp64(pkg):
+@pytest.mark.parametrize("prec,tol", [("SPLIT_HPSI", 1e-6), ("SPLIT_HPSI_TC", 1e-6), ("SPLIT_TF32", 3e-5)])
+def test_split_precision_sweep_energy(pkg, prec, tol):
+    """Sweep energy of the split (3xTF32) paths against the float64 path.  The
+    sweep energy is the float64 Rayleigh quotient of the split-converged
+    eigenvector, so with float64 renormalisation the difference is second
+    order (<= 1e-6 Eh); with split renormalisation (SPLIT_TF32) the operators
+    themselves carry the ~1e-7 relative rounding and the bound is first order."""
     h, L = W.cholesky_random(8, 16, seed=2)
     eri = W.eri_from_cholesky(L)
     e64 = pkg.DMRG(h, eri=eri, n_elec=8, D=16).sweep(3)[0]
-    e32 = pkg.DMRG(h, eri=eri, n_elec=8, D=16, precision=pkg.SPLIT_TF32).sweep(3)[0]
-    assert abs(e32 - e64) < 1e-6
+    e32 = pkg.DMRG(h, eri=eri, n_elec=8, D=16, precision=getattr(pkg, prec)).sweep(3)[0]
+    assert abs(e32 - e64) < tol
 
 
 def test_bad_arguments_return_einval(pkg):
@@ -274,14 +280,3 @@ def test_fused_hpsi_tcgen05_chunks_and_tails(pkg):
         got = C1[off:off + m * n].reshape(m, n)
         assert np.abs(got - ref).max() < 3e-5 * scale
         assert np.abs(got - C3[off:off + m * n].reshape(m, n)).max() < 3e-5 * scale
-
-
-@pytest.mark.parametrize("prec", ["SPLIT_HPSI", "SPLIT_HPSI_TC"])
-def test_split_hpsi_sweep_energy(pkg, prec):
-    """Whole sweeps with the split H_eff psi kernels: energy within 1e-5 Eh of
-    the FP64 path (|E| ~ 10 Eh, FP32 accumulation)."""
-    h, L = W.cholesky_random(8, 16, seed=2)
-    eri = W.eri_from_cholesky(L)
-    e64 = pkg.DMRG(h, eri=eri, n_elec=8, D=16).sweep(3)[0]
-    e32 = pkg.DMRG(h, eri=eri, n_elec=8, D=16, precision=getattr(pkg, prec)).sweep(3)[0]
-    assert abs(e32 - e64) < 1e-5
