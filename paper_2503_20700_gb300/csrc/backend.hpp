@@ -56,6 +56,8 @@ struct EighTask {
 
 struct HpsiBlock;
 struct HpsiItem;
+struct TcItem;
+struct SplitJob;
 struct HpsiTask;
 struct HpsiReduce;
 
@@ -87,6 +89,11 @@ class Backend {
   virtual void hpsi(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
                     const HpsiReduce* reds, int nreds, double* scratch, Precision prec,
                     double flops) = 0;
+  // The tcgen05 version of the contraction on pre-split operands (hpsi_tc.cuh),
+  // and the split of float64 blocks into TF32 hi/lo planes (device job list).
+  virtual void hpsi_tc(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
+                       const HpsiReduce* reds, int nreds, double* scratch, double flops) = 0;
+  virtual void split(const SplitJob* jobs, int n) = 0;
 
   // Davidson vector algebra on contiguous float64 vectors of length len.
   // out[i] = sum_t V[i*ld + t] * x[t] for i < m   (out is a device array)

@@ -20,6 +20,7 @@
 #include "backend.hpp"
 #include "gemm_split.cuh"
 #include "hpsi_fused.cuh"
+#include "hpsi_tc.cuh"
 
 namespace dmrg {
 
@@ -611,6 +612,26 @@ class CudaBackend : public Backend {
     launches += (ntasks > 0) + (nreds > 0);
     if (rec) CK(cudaEventRecord(rec->b, st));
     if (recs.size() > 4096) drain();
+  }
+
+  void hpsi_tc(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
+               const HpsiReduce* reds, int nreds, double* scratch, double flops) override {
+    gemm_flops += flops;
+    Rec* rec = nullptr;
+    if (profiling) {
+      recs.push_back(Rec{ev(), ev(), flops, 1});
+      rec = &recs.back();
+      CK(cudaEventRecord(rec->a, st));
+    }
+    hpsi_tc_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, flag(), st);
+    launches += (ntasks > 0) + (nreds > 0);
+    if (rec) CK(cudaEventRecord(rec->b, st));
+    if (recs.size() > 4096) drain();
+  }
+  void split(const SplitJob* jobs, int n) override {
+    if (n <= 0) return;
+    split_launch(jobs, n, st);
+    ++launches;
   }
 
   void ensure_part(size_t n) {

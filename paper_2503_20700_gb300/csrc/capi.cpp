@@ -12,6 +12,7 @@
 #include "casscf.hpp"
 #include "hpsi_fused.cuh"
 #include "hpsi_noalloc.hpp"
+#include "hpsi_tc.cuh"
 #include "dmrg.hpp"
 
 struct dmrg_ctx {
@@ -452,24 +453,51 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                                                                  : dmrg::Precision::SPLIT_TF32;
     std::vector<dmrg::HpsiTask> tasks;
     std::vector<dmrg::HpsiReduce> reds;
-    size_t scr = dmrg::hpsi_plan_tasks(hb, pr, tasks, reds);
+    const bool tc = pr == dmrg::Precision::TC_TF32X3;
+    dmrg::TcPlan tp;
+    void* pool = nullptr;
+    size_t scr;
+    if (tc) {
+      dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp);
+      tasks = tp.tasks;
+      reds = tp.reds;
+      scr = tp.scratch;
+    } else {
+      scr = dmrg::hpsi_plan_tasks(hb, pr, tasks, reds);
+    }
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t ob = 0, oi = al(hb.size() * sizeof(dmrg::HpsiBlock));
-    size_t ot = al(oi + hi.size() * sizeof(dmrg::HpsiItem));
+    size_t oc = al(oi + hi.size() * sizeof(dmrg::HpsiItem));
+    size_t ot = al(oc + tp.items.size() * sizeof(dmrg::TcItem));
     size_t orr = al(ot + tasks.size() * sizeof(dmrg::HpsiTask));
-    size_t os = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
+    size_t oj = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
+    size_t os = al(oj + (tp.op_jobs.size() + tp.psi_jobs.size()) * sizeof(dmrg::SplitJob));
     char* d = (char*)be->alloc(os + scr * sizeof(double) + 256);
     if (!hb.empty()) be->copy_h2d(d + ob, hb.data(), hb.size() * sizeof(dmrg::HpsiBlock));
     if (!hi.empty()) be->copy_h2d(d + oi, hi.data(), hi.size() * sizeof(dmrg::HpsiItem));
+    if (!tp.items.empty()) be->copy_h2d(d + oc, tp.items.data(), tp.items.size() * sizeof(dmrg::TcItem));
     if (!tasks.empty()) be->copy_h2d(d + ot, tasks.data(), tasks.size() * sizeof(dmrg::HpsiTask));
     if (!reds.empty()) be->copy_h2d(d + orr, reds.data(), reds.size() * sizeof(dmrg::HpsiReduce));
-    be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
-             (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
-             (int)reds.size(), (double*)(d + os), pr, fl);
+    if (tc) {
+      std::vector<dmrg::SplitJob> jobs = tp.op_jobs;
+      jobs.insert(jobs.end(), tp.psi_jobs.begin(), tp.psi_jobs.end());
+      if (!jobs.empty()) {
+        be->copy_h2d(d + oj, jobs.data(), jobs.size() * sizeof(dmrg::SplitJob));
+        be->split((const dmrg::SplitJob*)(d + oj), (int)jobs.size());
+      }
+      be->hpsi_tc((const dmrg::HpsiBlock*)(d + ob), (const dmrg::TcItem*)(d + oc),
+                  (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
+                  (int)reds.size(), (double*)(d + os), fl);
+    } else {
+      be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
+               (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
+               (int)reds.size(), (double*)(d + os), pr, fl);
+    }
     be->check_device_flag();
     be->copy_d2h(C, dC, c_len * sizeof(double));
     be->sync();
     for (void* q : {(void*)dA, (void*)dP, (void*)dB, (void*)dC, (void*)d}) be->free(q);
+    if (pool) be->free(pool);
     be->sync();
   } catch (const std::exception& e) {
     return translate(nullptr, e);

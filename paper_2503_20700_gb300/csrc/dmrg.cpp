@@ -1,6 +1,7 @@
 // Host planner of the spin-adapted two-site DMRG (see dmrg.hpp).
 #include "dmrg.hpp"
 #include "hpsi_fused.cuh"
+#include "hpsi_tc.cuh"
 
 #include <algorithm>
 #include <array>
@@ -1032,6 +1033,11 @@ struct HPsiPlan {
   HpsiReduce* d_reds = nullptr;
   double* scratch = nullptr;
   Precision prec = Precision::FP64;  // kernel the task list was planned for
+  // tcgen05 path: split planes, items on them, and the per-product psi splits
+  void* tc_pool = nullptr;
+  TcItem* d_tcitems = nullptr;
+  SplitJob* d_psi_jobs = nullptr;
+  int n_psi_jobs = 0;
   int ntasks = 0, nreds = 0;
   size_t nitems = 0;
   double flops = 0.0;
@@ -1133,25 +1139,51 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   std::vector<HpsiTask> tasks;
   std::vector<HpsiReduce> reds;
   plan.prec = opt_.prec;
-  size_t scr = hpsi_plan_tasks(blocks, plan.prec, tasks, reds);
+  const bool tc = plan.prec == Precision::TC_TF32X3;
+  TcPlan tp;
+  size_t scr;
+  if (tc) {
+    if (plan.tc_pool) be_->free(plan.tc_pool);
+    plan.tc_pool = nullptr;
+    hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp);
+    tasks = tp.tasks;
+    reds = tp.reds;
+    scr = tp.scratch;
+  } else {
+    scr = hpsi_plan_tasks(blocks, plan.prec, tasks, reds);
+  }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t ob = 0, oi = al(ob + blocks.size() * sizeof(HpsiBlock));
-  size_t ot = al(oi + items.size() * sizeof(HpsiItem));
+  size_t oc = al(oi + items.size() * sizeof(HpsiItem));
+  size_t ot = al(oc + tp.items.size() * sizeof(TcItem));
   size_t orr = al(ot + tasks.size() * sizeof(HpsiTask));
-  size_t os = al(orr + reds.size() * sizeof(HpsiReduce));
+  size_t oj = al(orr + reds.size() * sizeof(HpsiReduce));
+  size_t opj = al(oj + tp.op_jobs.size() * sizeof(SplitJob));
+  size_t os = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
   size_t total = os + scr * sizeof(double) + 256;
   if (plan.dev) be_->free(plan.dev);
   plan.dev = be_->alloc(total);
   char* d = (char*)plan.dev;
   plan.d_blocks = (HpsiBlock*)(d + ob);
   plan.d_items = (HpsiItem*)(d + oi);
+  plan.d_tcitems = (TcItem*)(d + oc);
   plan.d_tasks = (HpsiTask*)(d + ot);
   plan.d_reds = (HpsiReduce*)(d + orr);
+  plan.d_psi_jobs = (SplitJob*)(d + opj);
+  plan.n_psi_jobs = (int)tp.psi_jobs.size();
   plan.scratch = (double*)(d + os);
   if (!blocks.empty()) be_->copy_h2d(plan.d_blocks, blocks.data(), blocks.size() * sizeof(HpsiBlock));
   if (!items.empty()) be_->copy_h2d(plan.d_items, items.data(), items.size() * sizeof(HpsiItem));
+  if (!tp.items.empty()) be_->copy_h2d(plan.d_tcitems, tp.items.data(), tp.items.size() * sizeof(TcItem));
   if (!tasks.empty()) be_->copy_h2d(plan.d_tasks, tasks.data(), tasks.size() * sizeof(HpsiTask));
   if (!reds.empty()) be_->copy_h2d(plan.d_reds, reds.data(), reds.size() * sizeof(HpsiReduce));
+  if (!tp.psi_jobs.empty())
+    be_->copy_h2d(plan.d_psi_jobs, tp.psi_jobs.data(), tp.psi_jobs.size() * sizeof(SplitJob));
+  if (!tp.op_jobs.empty()) {
+    // operator blocks are constant during Davidson: split them once
+    be_->copy_h2d(d + oj, tp.op_jobs.data(), tp.op_jobs.size() * sizeof(SplitJob));
+    be_->split((const SplitJob*)(d + oj), (int)tp.op_jobs.size());
+  }
   plan.ntasks = (int)tasks.size();
   plan.nreds = (int)reds.size();
   plan.nitems = items.size();
@@ -1185,8 +1217,14 @@ size_t Engine::x_budget_elems() const { return 0; }
 
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
-  be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
-            plan.scratch, plan.prec, plan.flops);
+  if (plan.prec == Precision::TC_TF32X3) {
+    be_->split(plan.d_psi_jobs, plan.n_psi_jobs);
+    be_->hpsi_tc(plan.d_blocks, plan.d_tcitems, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
+                 plan.scratch, plan.flops);
+  } else {
+    be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
+              plan.scratch, plan.prec, plan.flops);
+  }
 }
 
 // ============================================================ Davidson
@@ -1828,6 +1866,7 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   be_->free(plan.in);
   be_->free(plan.out);
   if (plan.dev) be_->free(plan.dev);
+  if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
   last_bond_ = i;
   bond_e_.push_back(e);

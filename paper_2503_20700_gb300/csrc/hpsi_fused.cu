@@ -367,7 +367,8 @@ __global__ void hpsi_reduce_kernel(const HpsiBlock* __restrict__ blocks, const H
 }  // namespace
 
 void hpsi_tile(Precision prec, int* tile_m, int* tile_n) {
-  *tile_m = prec == Precision::TC_TF32X3 ? 128 : T;
+  (void)prec;
+  *tile_m = T;
   *tile_n = T;
 }
 
@@ -407,10 +408,9 @@ size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, Precision prec, std
 void hpsi_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
                  const HpsiReduce* reds, int nreds, double* scratch, Precision prec, int* err,
                  cudaStream_t st) {
-  if (prec == Precision::TC_TF32X3) {
-    hpsi_tc_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, err, st);
-    return;
-  }
+  (void)err;
+  if (prec == Precision::TC_TF32X3)
+    throw std::runtime_error("internal: the tcgen05 contraction runs on pre-split operands (hpsi_tc_launch)");
   if (ntasks > 0) {
     if (prec == Precision::FP64) {
       size_t smem = (size_t)(3 * KS * (T + 1) + T * (T + 1)) * sizeof(double);

@@ -48,8 +48,9 @@ struct HpsiReduce {
   long long part0;  // first partial; the others follow at +tile_m*tile_n each
 };
 
-// sigma tile owned by one CTA of the kernel used for `prec`:
-// 64 x 64 (FP64, SPLIT_TF32 on mma.sync), 128 x 64 (TC_TF32X3 on tcgen05).
+// sigma tile owned by one CTA of the kernel used for `prec`: 64 x 64 (FP64 and
+// SPLIT_TF32 on mma.sync; the tcgen05 contraction plans its own 128 x 256
+// tiles in hpsi_tc_prepare).
 void hpsi_tile(Precision prec, int* tile_m, int* tile_n);
 
 // Builds the task list (tiles x item chunks) for the given blocks; returns the
@@ -59,14 +60,10 @@ size_t hpsi_plan_tasks(const std::vector<HpsiBlock>& blocks, Precision prec, std
                        std::vector<HpsiReduce>& reds);
 
 // Launches the fused kernel and the reduction (device pointers in the lists).
-// err: device int set to 1 when a bounded wait of the tcgen05 kernel ran out
-// (the CTA then skips its remaining work); untouched by the other kernels.
+// prec: FP64 or SPLIT_TF32 (err is unused by these kernels).
 void hpsi_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
                  const HpsiReduce* reds, int nreds, double* scratch, Precision prec, int* err,
                  cudaStream_t st);
 
-// tcgen05 kernel pair (hpsi_tc.cu); tasks planned with the 128 x 64 tile.
-void hpsi_tc_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
-                    const HpsiReduce* reds, int nreds, double* scratch, int* err, cudaStream_t st);
 
 }  // namespace dmrg

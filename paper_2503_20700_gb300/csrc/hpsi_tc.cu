@@ -1,88 +1,73 @@
-// tcgen05 (5th-generation tensor core) version of the fused H_eff psi
-// contraction of hpsi_fused.cuh for sm_103a, 3xTF32 split precision:
+// tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh).
 //
-//   sigma(a', b') += sum_i alpha_i op(A_i) P_i op(B_i)^T
-//
-// One CTA (128 threads) owns a 128 x 64 tile of one sigma block and a chunk of
-// its items.  Per item and per 64-wide column chunk of P:
-//   stage 1  X (128 x 64, TMEM)  = alpha op(A) P(:, chunk)        [3 MMAs per k-step]
-//   X: TMEM -> registers -> hi/lo TF32 -> shared memory (K-major)
-//   stage 2  S (128 x 64, TMEM) += X op(B)(tile cols, chunk)^T     [3 MMAs per k-step]
-// Operands are staged from float64 into the canonical no-swizzle K-major
-// shared-memory layout (8-row x 16-byte core matrices), split into hi/lo
-// TF32 planes; one elected thread issues tcgen05.mma and commits to an
-// mbarrier.  S accumulates in FP32 in TMEM across the items of the chunk and
-// is written as a float64 partial tile (reduced by hpsi_reduce) or added into
-// sigma.  Every wait is bounded; a wait that runs out sets *err and the CTA
-// skips the rest of its work, after a second bounded wait for the MMAs still
-// in flight, and releases its TMEM columns.
+// Shared memory (bytes): X hi/lo planes (2 x 32 KB, 128 x 64, K-major) and two
+// 64 KB slots, each holding the operand tiles of one k-block of 32:
+//   stage 1: A hi | A lo (128 x 32 each, 16 KB) | P^T hi | P^T lo (64 x 32, 8 KB)
+//   stage 2: B hi | B lo (N x 32 each, N <= 256, 32 KB)
+// all in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices; 128 B between K-adjacent cores, 1 KB between 8-row groups for
+// 32-wide tiles, 2 KB for the 64-wide X).  TMEM: S in columns [0, 256), X' in
+// [256, 320).  The k-blocks of a task form one sequence; block b+1 is copied
+// into the other slot while the MMAs of block b run, each slot has its own
+// mbarrier (tcgen05.commit after the block's MMAs), and every wait is bounded
+// by 2 s of wall clock.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <map>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 
-#include "hpsi_fused.cuh"
+#include "hpsi_tc.cuh"
 
 namespace dmrg {
 
 namespace {
 
-constexpr int TM = 128, TN = 64, KS = 32, JC = 64;
-constexpr uint32_t LBO = 128;                 // bytes between K-adjacent core matrices
-constexpr uint32_t SBO_K32 = (KS / 4) * 128;  // bytes between M-adjacent cores, K = 32 tiles
-constexpr uint32_t SBO_K64 = (JC / 4) * 128;  // same for the X tile (K = 64)
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s of wall clock per wait
+constexpr int TM = kTcTileM, TNMAX = kTcTileN, KB = 32, JC = 64;
+constexpr uint32_t LBO = 128;
+constexpr uint32_t SBO32 = 1024;  // 8-row group stride of a 32-wide tile
+constexpr uint32_t SBO64 = 2048;  // of the 64-wide X tile
+constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_SLOT = 65536, SLOT = 65536;
+constexpr int SMEM_BYTES = OFF_SLOT + 2 * SLOT;  // 192 KB
+constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int roundup32(int x) { return (x + 31) & ~31; }
 
 __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // sm_100-family descriptor version; no swizzle
+  d |= (uint64_t)1 << 46;
   return d;
 }
-
 __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-
-// word offset of element (r, k) in a canonical K-major tile with K-extent kext
-__device__ __forceinline__ int koff(int r, int k, int kext) {
-  return (r >> 3) * (kext * 8) + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
-}
-
 __device__ __forceinline__ uint32_t tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ void split64(double x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32((float)x);
-  lo = tf32((float)(x - (double)__uint_as_float(hi)));
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
-
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
-
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-
-// wait for the completion of phase `parity` of the mbarrier, bounded by
-// kWaitNs of wall clock (non-blocking probes with a short sleep between them)
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   const unsigned long long t0 = global_ns();
   for (;;) {
@@ -93,10 +78,9 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity));
     if (done) return true;
     if (global_ns() - t0 > kWaitNs) return false;
-    __nanosleep(32);
+    __nanosleep(64);
   }
 }
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -108,209 +92,401 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
-
-__device__ __forceinline__ double ldA(const HpsiItem& it, int r, int c) {
-  if (it.A == nullptr) return r == c ? 1.0 : 0.0;
-  return it.transA ? it.A[(size_t)c * it.lda + r] : it.A[(size_t)r * it.lda + c];
+// 16-byte async copy; src_bytes = 0 fills the destination with zeros
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
 }
-__device__ __forceinline__ double ldB(const HpsiItem& it, int n, int k) {
-  if (it.B == nullptr) return n == k ? 1.0 : 0.0;
-  return it.transB ? it.B[(size_t)k * it.ldb + n] : it.B[(size_t)n * it.ldb + k];
+// byte offset of element (r, k) (k multiple of 4) in a K-major tile with 8-row group stride sbo
+__device__ __forceinline__ uint32_t core_off(int r, int k, uint32_t sbo) {
+  return (uint32_t)(r >> 3) * sbo + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16;
+}
+__device__ __forceinline__ uint32_t word_off(int r, int k, uint32_t sbo) {
+  return core_off(r, k & ~3, sbo) + (uint32_t)(k & 3) * 4;
 }
 
-// shared memory (bytes)
-constexpr int SZ_A = TM * KS * 4;   // 16 KB per plane
-constexpr int SZ_P = JC * KS * 4;   //  8 KB
-constexpr int SZ_X = TM * JC * 4;   // 32 KB
-constexpr int SZ_B = TN * KS * 4;   //  8 KB
-constexpr int OFF_AH = 0, OFF_AL = OFF_AH + SZ_A, OFF_PH = OFF_AL + SZ_A, OFF_PL = OFF_PH + SZ_P;
-constexpr int OFF_XH = OFF_PL + SZ_P, OFF_XL = OFF_XH + SZ_X, OFF_BH = OFF_XL + SZ_X, OFF_BL = OFF_BH + SZ_B;
-constexpr int SMEM_BYTES = OFF_BL + SZ_B;  // 128 KB
+// copies rows [row0, row0 + nrows) x cols [k0, k0 + 32) of a split matrix
+// (valid rows < rmax) into a K-major tile (both planes)
+__device__ __forceinline__ void load_tile(uint32_t dhi, uint32_t dlo, const TcMat& m, int row0, int nrows, int rmax,
+                                          int k0, int tid) {
+  const int chunks = nrows * 8;
+  for (int e = tid; e < chunks; e += 128) {
+    int r = e >> 3, kc = (e & 7) * 4;
+    int gr = row0 + r;
+    bool ok = gr < rmax;
+    size_t off = ok ? (size_t)gr * m.ld + k0 + kc : 0;
+    uint32_t o = core_off(r, kc, SBO32);
+    cp16(dhi + o, m.hi + off, ok ? 16 : 0);
+    cp16(dlo + o, m.lo + off, ok ? 16 : 0);
+  }
+}
+
+struct Cursor {
+  int ii, jc, jc_end, stage, k0;
+};
+
+__device__ __forceinline__ void cursor_item(Cursor& c, const TcItem& it, int c0, int N) {
+  c.jc = 0;
+  c.jc_end = it.kb;
+  if (it.B.hi == nullptr) {
+    c.jc = c0;
+    c.jc_end = min(it.kb, c0 + N);
+  }
+  c.stage = it.A.hi ? 1 : 2;
+  c.k0 = 0;
+}
+__device__ __forceinline__ int chunk_kspan(const Cursor& c) { return min(JC, roundup32(c.jc_end - c.jc)); }
+// advance to the next k-block; false at the end of the task
+__device__ __forceinline__ bool cursor_next(Cursor& c, const TcItem* __restrict__ items, int it_end, int c0, int N) {
+  const TcItem& it = items[c.ii];
+  if (c.stage == 1) {
+    c.k0 += KB;
+    if (c.k0 < roundup32(it.ka)) return true;
+    c.stage = 2;
+    c.k0 = 0;
+    return true;
+  }
+  c.k0 += KB;
+  if (c.k0 < chunk_kspan(c)) return true;
+  c.jc += JC;
+  if (c.jc < c.jc_end) {
+    c.stage = it.A.hi ? 1 : 2;
+    c.k0 = 0;
+    return true;
+  }
+  if (++c.ii >= it_end) return false;
+  cursor_item(c, items[c.ii], c0, N);
+  return true;
+}
 
 __global__ void __launch_bounds__(128, 1)
-    hpsi_tc_kernel(const HpsiBlock* __restrict__ blocks, const HpsiItem* __restrict__ items,
+    hpsi_tc_kernel(const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, double* __restrict__ scratch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  uint32_t* Ah = (uint32_t*)(smraw + OFF_AH);
-  uint32_t* Al = (uint32_t*)(smraw + OFF_AL);
-  uint32_t* Ph = (uint32_t*)(smraw + OFF_PH);
-  uint32_t* Pl = (uint32_t*)(smraw + OFF_PL);
-  uint32_t* Xh = (uint32_t*)(smraw + OFF_XH);
-  uint32_t* Xl = (uint32_t*)(smraw + OFF_XL);
-  uint32_t* Bh = (uint32_t*)(smraw + OFF_BH);
-  uint32_t* Bl = (uint32_t*)(smraw + OFF_BL);
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5;
   const HpsiTask tk = tasks[blockIdx.x];
   const HpsiBlock bk = blocks[tk.block];
+  const int nvalid = min(TNMAX, bk.n - tk.c0);
+  const int N = (nvalid + 15) & ~15;  // MMA N: multiple of 16
+  const int it_end = tk.it_begin + tk.it_count;
+  const uint32_t sbase = smem_u32(smraw);
+  const uint32_t xh = sbase + OFF_XH, xl = sbase + OFF_XL;
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tX = tmem_base;       // columns [0, 64): X accumulator
-  const uint32_t tS = tmem_base + 64;  // columns [64, 128): sigma accumulator
+  const uint32_t tS = tmem_base + TCOL_S, tX = tmem_base + TCOL_X;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t id1 = idesc_tf32(TM, JC);
-  const uint32_t id2 = idesc_tf32(TM, TN);
-  uint32_t phase = 0;
-  bool s_started = false;  // sigma accumulator holds data
-  // issue the MMAs of one staged k-block (32 wide) and wait for them
-  auto run_k32 = [&](uint32_t dtm, uint32_t a_h, uint32_t a_l, uint32_t a_sbo, uint32_t b_h, uint32_t b_l,
-                     uint32_t idesc, bool& started) -> bool {
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-#pragma unroll
-      for (int s = 0; s < KS / 8; ++s) {
-        uint32_t ko = (uint32_t)s * 2 * LBO;
-        uint64_t ah = desc(a_h + ko, a_sbo), al = desc(a_l + ko, a_sbo);
-        uint64_t bh = desc(b_h + s * 2 * LBO, SBO_K32), bl = desc(b_l + s * 2 * LBO, SBO_K32);
-        mma_tf32(dtm, al, bh, idesc, (started || s > 0) ? 1u : 0u);
-        mma_tf32(dtm, ah, bl, idesc, 1u);
-        mma_tf32(dtm, ah, bh, idesc, 1u);
+  const uint32_t id1 = idesc_tf32(TM, JC), id2 = idesc_tf32(TM, N);
+
+  // issue the operand copies of the block at cursor c into slot s
+  auto produce = [&](const Cursor& c, int s) {
+    const TcItem& it = items[c.ii];
+    const uint32_t sl = sbase + OFF_SLOT + s * SLOT;
+    if (c.stage == 1) {
+      load_tile(sl, sl + 16384, it.A, tk.r0, TM, bk.m, c.k0, tid);
+      load_tile(sl + 32768, sl + 40960, it.Pt, c.jc, JC, it.kb, c.k0, tid);
+    } else if (it.B.hi != nullptr) {
+      load_tile(sl, sl + 32768, it.B, tk.c0, N, bk.n, c.jc + c.k0, tid);
+    } else {
+      // identity on the right: B(n, k) = [c0 + n == jc + k0 + k]
+      float* bh = (float*)(smraw + OFF_SLOT + s * SLOT);
+      float* bl = (float*)(smraw + OFF_SLOT + s * SLOT + 32768);
+      for (int e = tid; e < N * KB; e += 128) {
+        int n = e / KB, k = e % KB;
+        bool one = (tk.c0 + n == c.jc + c.k0 + k) && (tk.c0 + n < bk.n);
+        uint32_t o = word_off(n, k, SBO32) >> 2;
+        bh[o] = one ? 1.0f : 0.0f;
+        bl[o] = 0.0f;
       }
-      commit(&bar);
     }
-    started = true;  // uniform over the CTA: the epilogue's tcgen05.ld is warp-collective
-    bool ok = wait_bar(&bar, phase & 1);
-    if (!ok) {
-      ok = false;
-      wait_bar(&bar, phase & 1);  // second bounded window for the MMAs in flight
-      abort_flag = 1;
-    }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (abort_flag != 0 && tid == 0) atomicExch(err, 1);
-    return abort_flag == 0;
+    asm volatile("cp.async.commit_group;");
   };
-  bool alive = true;
-  for (int ii = tk.it_begin; ii < tk.it_begin + tk.it_count && alive; ++ii) {
-    const HpsiItem it = items[ii];
-    int jc_begin = 0, jc_end = it.kb;
-    if (it.B == nullptr) {
-      jc_begin = tk.c0;
-      jc_end = min(it.kb, tk.c0 + TN);
+  // bounded wait on the commit of block b; failure sets the abort flag
+  auto wait_block = [&](int b) {
+    if (!wait_bar(&bar[b & 1], (uint32_t)((b >> 1) & 1))) abort_flag = 1;
+  };
+
+  Cursor cur;
+  cur.ii = tk.it_begin;
+  cursor_item(cur, items[cur.ii], tk.c0, N);
+  bool s_started = false;
+  int b = 0;
+  produce(cur, 0);
+  for (;;) {
+    // prefetch block b+1 into the other slot once the MMAs of block b-1 are done
+    Cursor nxt = cur;
+    const bool has_next = cursor_next(nxt, items, it_end, tk.c0, N);
+    if (has_next) {
+      if (b >= 1) wait_block(b - 1);
+      produce(nxt, (b + 1) & 1);
+      asm volatile("cp.async.wait_group 1;");
+    } else {
+      asm volatile("cp.async.wait_group 0;");
     }
-    for (int jc = jc_begin; jc < jc_end && alive; jc += JC) {
-      // ---- stage 1: X = alpha op(A) P(:, jc chunk)
-      bool x_started = false;
-      for (int k0 = 0; k0 < it.ka && alive; k0 += KS) {
-        for (int e = tid; e < TM * KS; e += 128) {
-          int r = e / KS, k = e % KS;
-          int gr = tk.r0 + r, gk = k0 + k;
-          double v = (gr < bk.m && gk < it.ka) ? it.alpha * ldA(it, gr, gk) : 0.0;
-          uint32_t h, l;
-          split64(v, h, l);
-          int o = koff(r, k, KS);
-          Ah[o] = h;
-          Al[o] = l;
-        }
-        for (int e = tid; e < JC * KS; e += 128) {
-          int n = e % JC, k = e / JC;  // P^T (n, k) = P(k, n)
-          int gk = k0 + k, gn = jc + n;
-          double v = (gk < it.ka && gn < jc_end) ? it.P[(size_t)gk * it.ldp + gn] : 0.0;
-          uint32_t h, l;
-          split64(v, h, l);
-          int o = koff(n, k, KS);
-          Ph[o] = h;
-          Pl[o] = l;
-        }
-        alive = run_k32(tX, smem_u32(Ah), smem_u32(Al), SBO_K32, smem_u32(Ph), smem_u32(Pl), id1, x_started);
-      }
-      if (!alive) break;
-      // ---- X: TMEM -> registers -> hi/lo K-major tile (row = thread)
-      {
-        const int r = tid;
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (abort_flag) break;
+    const TcItem& it = items[cur.ii];
+    if (cur.stage == 2 && cur.k0 == 0) {
+      // X = alpha X' (or alpha P for an identity left operand) -> hi/lo planes;
+      // the commit of block b-1 covers every earlier MMA (stage 1 of this
+      // chunk, stage 2 of the previous one that read X)
+      if (b >= 1) wait_block(b - 1);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int r = tid;
+      float* xhp = (float*)(smraw + OFF_XH);
+      float* xlp = (float*)(smraw + OFF_XL);
+      if (it.A.hi != nullptr) {
 #pragma unroll
         for (int c0 = 0; c0 < JC; c0 += 16) {
           float v[16];
           tmem_ld16(tX + lane_base + c0, v);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            uint32_t h = tf32(v[j]);
-            int o = koff(r, c0 + j, JC);
-            Xh[o] = h;
-            Xl[o] = tf32(v[j] - __uint_as_float(h));
+            float x = (float)it.alpha * v[j];
+            uint32_t h = tf32(x);
+            uint32_t o = word_off(r, c0 + j, SBO64) >> 2;
+            xhp[o] = __uint_as_float(h);
+            xlp[o] = __uint_as_float(tf32(x - __uint_as_float(h)));
           }
         }
-      }
-      // ---- stage 2: S += X op(B)(tile cols, chunk)^T
-      for (int k0 = 0; k0 < JC && jc + k0 < jc_end && alive; k0 += KS) {
-        for (int e = tid; e < TN * KS; e += 128) {
-          int n = e / KS, k = e % KS;
-          int gn = tk.c0 + n, gk = jc + k0 + k;
-          double v = (gn < bk.n && gk < jc_end) ? ldB(it, gn, gk) : 0.0;
-          uint32_t h, l;
-          split64(v, h, l);
-          int o = koff(n, k, KS);
-          Bh[o] = h;
-          Bl[o] = l;
+      } else {
+        const int gr = tk.r0 + r;
+        for (int c = 0; c < JC; ++c) {
+          int gc = cur.jc + c;
+          double x = (gr < bk.m && gc < it.kb) ? it.alpha * it.P[(size_t)gr * it.ldp + gc] : 0.0;
+          uint32_t h = tf32((float)x);
+          uint32_t o = word_off(r, c, SBO64) >> 2;
+          xhp[o] = __uint_as_float(h);
+          xlp[o] = __uint_as_float(tf32((float)(x - (double)__uint_as_float(h))));
         }
-        uint32_t xoff = (uint32_t)(k0 / 4) * LBO;
-        alive = run_k32(tS, smem_u32(Xh) + xoff, smem_u32(Xl) + xoff, SBO_K64, smem_u32(Bh), smem_u32(Bl), id2,
-                        s_started);
       }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (abort_flag) break;
     }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sl = sbase + OFF_SLOT + (b & 1) * SLOT;
+      if (cur.stage == 1) {
+#pragma unroll
+        for (int s = 0; s < KB / 8; ++s) {
+          const uint32_t ko = (uint32_t)s * 2 * LBO;
+          uint64_t ah = desc(sl + ko, SBO32), al = desc(sl + 16384 + ko, SBO32);
+          uint64_t ph = desc(sl + 32768 + ko, SBO32), pl = desc(sl + 40960 + ko, SBO32);
+          mma_tf32(tX, al, ph, id1, (cur.k0 > 0 || s > 0) ? 1u : 0u);
+          mma_tf32(tX, ah, pl, id1, 1u);
+          mma_tf32(tX, ah, ph, id1, 1u);
+        }
+      } else {
+        const uint32_t xo = (uint32_t)(cur.k0 / 4) * LBO;
+#pragma unroll
+        for (int s = 0; s < KB / 8; ++s) {
+          const uint32_t ko = (uint32_t)s * 2 * LBO;
+          uint64_t ah = desc(xh + xo + ko, SBO64), al = desc(xl + xo + ko, SBO64);
+          uint64_t bh = desc(sl + ko, SBO32), bl = desc(sl + 32768 + ko, SBO32);
+          mma_tf32(tS, al, bh, id2, (s_started || s > 0) ? 1u : 0u);
+          mma_tf32(tS, ah, bl, id2, 1u);
+          mma_tf32(tS, ah, bh, id2, 1u);
+        }
+      }
+      commit(&bar[b & 1]);
+    }
+    if (cur.stage == 2) s_started = true;  // uniform over the CTA
+    if (!has_next) break;
+    cur = nxt;
+    ++b;
   }
-  // ---- write the sigma tile (row = thread)
-  if (alive) {
+  // wait for the last block (and, after an abort, for whatever is in flight)
+  wait_block(b);
+  if (b >= 1) wait_block(b - 1);
+  asm volatile("cp.async.wait_group 0;");
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
     const int r = tid;
-    for (int c0 = 0; c0 < TN; c0 += 16) {
+    for (int c0 = 0; c0 < N; c0 += 16) {
       float v[16];
-      if (s_started) tmem_ld16(tS + lane_base + c0, v);
-      else
-        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      if (s_started) {
+        tmem_ld16(tS + lane_base + c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      }
+#pragma unroll
       for (int j = 0; j < 16; ++j) {
         int c = c0 + j;
         if (tk.part >= 0) {
-          scratch[tk.part + (long long)r * TN + c] = (double)v[j];
+          scratch[tk.part + (long long)r * TNMAX + c] = (double)v[j];
         } else {
           int gr = tk.r0 + r, gc = tk.c0 + c;
-          if (gr < bk.m && gc < bk.n) bk.C[(size_t)gr * bk.ldc + gc] += (double)v[j];
+          if (gr < bk.m && c < nvalid) bk.C[(size_t)gr * bk.ldc + gc] += (double)v[j];
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(128));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
 }
 
-// partial tiles of the tcgen05 kernel are TM x TN
+// partial tiles are TM x TNMAX (row stride TNMAX)
 __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiReduce* __restrict__ reds,
                                const double* __restrict__ scratch) {
   const HpsiReduce rd = reds[blockIdx.x];
   const HpsiBlock bk = blocks[rd.block];
-  for (int e = threadIdx.x; e < TM * TN; e += blockDim.x) {
-    int r = e / TN, c = e % TN;
-    int gr = rd.r0 + r, gc = rd.c0 + c;
-    if (gr >= bk.m || gc >= bk.n) continue;
+  const int nvalid = min(TNMAX, bk.n - rd.c0);
+  for (int e = threadIdx.x; e < TM * TNMAX; e += blockDim.x) {
+    int r = e / TNMAX, c = e % TNMAX;
+    int gr = rd.r0 + r;
+    if (gr >= bk.m || c >= nvalid) continue;
     double acc = 0.0;
-    for (int p = 0; p < rd.nparts; ++p) acc += scratch[rd.part0 + (long long)p * TM * TN + e];
-    bk.C[(size_t)gr * bk.ldc + gc] += acc;
+    for (int p = 0; p < rd.nparts; ++p) acc += scratch[rd.part0 + (long long)p * TM * TNMAX + e];
+    bk.C[(size_t)gr * bk.ldc + rd.c0 + c] += acc;
+  }
+}
+
+__global__ void split_kernel(const SplitJob* __restrict__ jobs, int n) {
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const SplitJob jb = jobs[j];
+    const size_t total = (size_t)jb.rows * jb.ldd;
+    for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+      int r = (int)(e / jb.ldd), c = (int)(e % jb.ldd);
+      double v = 0.0;
+      if (c < jb.cols) v = jb.trans ? jb.src[(size_t)c * jb.ld + r] : jb.src[(size_t)r * jb.ld + c];
+      float h = __uint_as_float(tf32((float)v));
+      jb.hi[e] = h;
+      jb.lo[e] = __uint_as_float(tf32((float)(v - (double)h)));
+    }
   }
 }
 
 }  // namespace
 
-void hpsi_tc_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask* tasks, int ntasks,
+void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
+                     const std::function<void*(size_t)>& alloc, TcPlan& plan) {
+  plan = TcPlan();
+  auto r32 = [](int x) { return (x + 31) & ~31; };
+  // distinct operands: (src, trans, rows, cols, ld) -> job; plane offsets in floats
+  std::map<std::tuple<const double*, int, int, int, int>, int> index;
+  std::vector<SplitJob> jobs;
+  std::vector<std::pair<size_t, size_t>> offs;
+  std::vector<int> is_psi;
+  size_t floats = 0;
+  auto want = [&](const double* src, int trans, int rows, int cols, int ld, bool psi) -> int {
+    auto key = std::make_tuple(src, trans, rows, cols, ld);
+    auto it = index.find(key);
+    if (it != index.end()) return it->second;
+    SplitJob j{src, rows, cols, ld, trans, nullptr, nullptr, r32(cols)};
+    size_t plane = (size_t)rows * j.ldd;
+    offs.push_back({floats, floats + plane});
+    floats += 2 * plane;
+    floats = (floats + 3) & ~size_t(3);  // 16-byte alignment of every plane
+    index.emplace(key, (int)jobs.size());
+    jobs.push_back(j);
+    is_psi.push_back(psi);
+    return (int)jobs.size() - 1;
+  };
+  struct Ref {
+    int a, p, b;
+  };
+  std::vector<Ref> refs(items.size(), Ref{-1, -1, -1});
+  for (auto& bk : blocks)
+    for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
+      const HpsiItem& it = items[i];
+      if (it.A) refs[i].a = want(it.A, it.transA, bk.m, it.ka, it.lda, false);
+      if (it.A) refs[i].p = want(it.P, 1, it.kb, it.ka, it.ldp, true);
+      if (it.B) refs[i].b = want(it.B, it.transB, bk.n, it.kb, it.ldb, false);
+    }
+  float* pool = nullptr;
+  if (floats > 0) pool = (float*)alloc(floats * sizeof(float));
+  plan.pool_bytes = floats * sizeof(float);
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    jobs[j].hi = pool + offs[j].first;
+    jobs[j].lo = pool + offs[j].second;
+    (is_psi[j] ? plan.psi_jobs : plan.op_jobs).push_back(jobs[j]);
+  }
+  auto mat = [&](int j) {
+    TcMat m;
+    if (j >= 0) {
+      m.hi = jobs[j].hi;
+      m.lo = jobs[j].lo;
+      m.ld = jobs[j].ldd;
+    }
+    return m;
+  };
+  plan.items.resize(items.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    const HpsiItem& it = items[i];
+    TcItem t;
+    t.A = mat(refs[i].a);
+    t.Pt = mat(refs[i].p);
+    t.P = it.P;
+    t.ldp = it.ldp;
+    t.B = mat(refs[i].b);
+    t.ka = it.ka;
+    t.kb = it.kb;
+    t.alpha = it.alpha;
+    plan.items[i] = t;
+  }
+  // tasks: 128 x 256 tiles, items chunked so that a launch has a few waves
+  long long tile_items = 0;
+  for (auto& b : blocks)
+    tile_items += (long long)b.item_count * ((b.m + TM - 1) / TM) * ((b.n + TNMAX - 1) / TNMAX);
+  const int max_items = (int)std::max<long long>(4, tile_items / (3 * 152) + 1);
+  long long part = 0;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const HpsiBlock& bk = blocks[b];
+    if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
+    int nch = (bk.item_count + max_items - 1) / max_items;
+    int per = (bk.item_count + nch - 1) / nch;
+    for (int r0 = 0; r0 < bk.m; r0 += TM)
+      for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
+        if (nch == 1) {
+          plan.tasks.push_back({(int)b, r0, c0, bk.item_begin, bk.item_count, -1});
+        } else {
+          plan.reds.push_back({(int)b, r0, c0, nch, part});
+          for (int c = 0; c < nch; ++c) {
+            int i0 = bk.item_begin + c * per;
+            int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
+            plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
+            part += (long long)TM * TNMAX;
+          }
+        }
+      }
+  }
+  plan.scratch = (size_t)part;
+}
+
+void split_launch(const SplitJob* jobs, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  split_kernel<<<std::min(n, 152 * 8), 256, 0, st>>>(jobs, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: split launch: ") + cudaGetErrorString(e));
+}
+
+void hpsi_tc_launch(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
                     const HpsiReduce* reds, int nreds, double* scratch, int* err, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(hpsi_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(hpsi_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc attribute: ") + cudaGetErrorString(e));
     attr = true;
   }
   if (ntasks > 0) {
