@@ -155,7 +155,9 @@ dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flop
 
 /* Wall time (s) of the phases of the last sweep: [0] blocking (enlarged
  * operators), [1] H_eff psi task planning, [2] Davidson, [3] decimation,
- * [4] renormalisation, [5] wavefunction prediction.  t must hold 6 values. */
+ * [4] renormalisation, [5] wavefunction prediction; parts of [0]: [6] host
+ * term lists, [7] host placement lists, [8] complementary-operator GEMMs.
+ * t must hold 9 values. */
 dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* ctx, double* t);
 
 /* Device time of the last sweep in milliseconds, measured with CUDA events

@@ -205,10 +205,13 @@ class DMRG:
         return ms.value, fl.value, n.value
 
     def phases(self):
-        """Wall seconds of (enlarge, plan, davidson, decimate, renormalize, guess)."""
-        t = np.zeros(6)
+        """Wall seconds of the sweep phases (enlarge, plan, davidson, decimate,
+        renormalize, guess) and of three parts of enlarge (host term lists,
+        host placement lists, complementary-operator GEMMs)."""
+        t = np.zeros(9)
         _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_phases(self._ctx, _dp(t)))
-        return dict(zip(["enlarge", "plan", "davidson", "decimate", "renormalize", "guess"], t.tolist()))
+        return dict(zip(["enlarge", "plan", "davidson", "decimate", "renormalize", "guess",
+                         "enlarge_terms_host", "enlarge_place_host", "enlarge_comp"], t.tolist()))
 
     def sweep_device_ms(self):
         ms = ctypes.c_double()

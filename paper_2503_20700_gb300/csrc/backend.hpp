@@ -48,9 +48,9 @@ struct GemmGroup {
 };
 
 struct EighTask {
-  const double* A;  // n x n symmetric, row-major (read only)
-  double* w;        // n eigenvalues, ascending
-  double* V;        // n x n eigenvectors as columns (row-major storage)
+  const double* A;  // n x n symmetric, row-major (used as work space: destroyed)
+  double* w;        // n eigenvalues, descending
+  double* V;        // n x n eigenvectors as rows (row-major storage)
   int n;
 };
 

@@ -341,6 +341,194 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
   }
 }
 
+// Cooperative variant for large matrices: a group of g CTAs shares one
+// matrix.  Every CTA of the group computes the round's rotation parameters
+// from the same diagonal and off-diagonal entries (identical values, so no
+// exchange is needed) and updates the 2x2 blocks of its own pair rows and
+// the matching eigenvector rows; one group barrier per round publishes the
+// updates.  Launched cooperatively (all CTAs co-resident); the barrier's
+// wait is bounded by 5 s of wall clock and sets the error flag on timeout.
+struct CoopEigh {
+  EighTask t;
+  int g, cta0;
+  unsigned* bar;  // (arrivals, generation), zero at launch
+};
+
+__device__ __forceinline__ unsigned long long jac_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// returns false when the wait ran out
+__device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned target = gen + 1;
+    if (atomicAdd(&bar[0], 1u) == (unsigned)g - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const unsigned long long t0 = jac_ns();
+      while ((int)(atomicAdd(&bar[1], 0u) - target) < 0) {
+        if (jac_ns() - t0 > 5000000000ull) {
+          *ok_s = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    gen = target;
+    __threadfence();
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+__global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __restrict__ tasks, int ntasks,
+                                                          int* __restrict__ err) {
+  int ti = 0;
+  while (ti + 1 < ntasks && tasks[ti + 1].cta0 <= (int)blockIdx.x) ++ti;
+  const CoopEigh ct = tasks[ti];
+  const int g = ct.g, me = (int)blockIdx.x - ct.cta0;
+  const int n = ct.t.n;
+  double* a = const_cast<double*>(ct.t.A);
+  double* v = ct.t.V;
+  extern __shared__ double sm[];
+  const int np = (n + 1) & ~1, h = np / 2;
+  double* cs = sm;
+  double* sn = sm + h;
+  int* pp = (int*)(sm + np);
+  int* qq = pp + h;
+  int* perm = qq + h;
+  __shared__ double red[256];
+  __shared__ int ok_s;
+  __shared__ int nrot;
+  unsigned gen = 0;
+  if (threadIdx.x == 0) ok_s = 1;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
+  for (int r = me; r < n; r += g)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v[(size_t)r * n + k] = (r == k) ? 1.0 : 0.0;
+  double fro = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+    double x = __ldcg(a + e);
+    fro += x * x;
+  }
+  red[threadIdx.x] = fro;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double floor_abs = 1e-20 * sqrt(red[0]);
+  if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
+  for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      for (int i = threadIdx.x; i < h; i += blockDim.x) {
+        int p = perm[i], q = perm[np - 1 - i];
+        if (p > q) { int t = p; p = q; q = t; }
+        pp[i] = p;
+        qq[i] = q;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = __ldcg(a + (size_t)p * n + q);
+          double app = __ldcg(a + (size_t)p * n + p), aqq = __ldcg(a + (size_t)q * n + q);
+          double gg = 100.0 * fabs(apq);
+          bool negligible = fabs(apq) <= floor_abs || (fabs(app) + gg == fabs(app) && fabs(aqq) + gg == fabs(aqq));
+          if (!negligible) {
+            double theta = (aqq - app) / (2.0 * apq);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // my pair rows i = me, me + g, ...: blocks (i, j) for all j
+      const int my_rows = (h - me + g - 1) / g;
+      for (size_t e = threadIdx.x; e < (size_t)my_rows * h; e += blockDim.x) {
+        int i = me + (int)(e / h) * g, j = (int)(e % h);
+        double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (si == 0.0 && sj == 0.0) continue;
+        int p = pp[i], q = qq[i], r = pp[j], t = qq[j];
+        bool qv = q < n, tv = t < n;
+        double x00 = __ldcg(a + (size_t)p * n + r);
+        double x01 = tv ? __ldcg(a + (size_t)p * n + t) : 0.0;
+        double x10 = qv ? __ldcg(a + (size_t)q * n + r) : 0.0;
+        double x11 = (qv && tv) ? __ldcg(a + (size_t)q * n + t) : 0.0;
+        double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+        double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+        a[(size_t)p * n + r] = cj * y00 - sj * y01;
+        if (tv) a[(size_t)p * n + t] = sj * y00 + cj * y01;
+        if (qv) a[(size_t)q * n + r] = cj * y10 - sj * y11;
+        if (qv && tv) a[(size_t)q * n + t] = sj * y10 + cj * y11;
+      }
+      for (size_t e = threadIdx.x; e < (size_t)my_rows * n; e += blockDim.x) {
+        int i = me + (int)(e / n) * g, k = (int)(e % n);
+        double s = sn[i];
+        if (s == 0.0) continue;
+        double c = cs[i];
+        int p = pp[i], q = qq[i];
+        double vp = __ldcg(v + (size_t)p * n + k), vq = __ldcg(v + (size_t)q * n + k);
+        v[(size_t)p * n + k] = c * vp - s * vq;
+        v[(size_t)q * n + k] = s * vp + c * vq;
+      }
+      if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
+      if (threadIdx.x == 0) {
+        int last = perm[np - 1];
+        for (int i = np - 1; i > 1; --i) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncthreads();
+    }
+    if (nrot == 0) break;
+    __syncthreads();
+  }
+  if (me != 0) return;
+  // CTA 0: eigenvalues descending (rank by counting, ties by index), rows of V
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double di = __ldcg(a + (size_t)i * n + i);
+    if (!(di == di)) di = -INFINITY;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double dj = __ldcg(a + (size_t)j * n + j);
+      if (!(dj == dj)) dj = -INFINITY;
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) ct.t.w[r] = __ldcg(a + (size_t)perm[r] * n + perm[r]);
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) a[e] = __ldcg(v + e);
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+    int r = (int)(e / n), k = (int)(e % n);
+    v[e] = a[(size_t)perm[r] * n + k];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double best = 0.0;
+    int bi = 0;
+    for (int k = 0; k < n; ++k) {
+      double x = fabs(v[(size_t)r * n + k]);
+      if (x > best + 1e-12) { best = x; bi = k; }
+    }
+    if (v[(size_t)r * n + bi] < 0)
+      for (int k = 0; k < n; ++k) v[(size_t)r * n + k] = -v[(size_t)r * n + k];
+  }
+  return;
+fail:
+  if (threadIdx.x == 0) atomicExch(err, 1);
+}
+
 // ------------------------------------------------------------------ backend
 class CudaBackend : public Backend {
  public:
@@ -673,20 +861,70 @@ class CudaBackend : public Backend {
     ++launches;
     CK(cudaGetLastError());
   }
+  // Matrices up to kCoopN use one CTA each; larger ones a cooperative group
+  // of g CTAs (g grows with n, the groups of one launch fit co-resident).
+  static constexpr int kCoopN = 96;
   void eigh(const std::vector<EighTask>& tasks) override {
     if (tasks.empty()) return;
+    std::vector<EighTask> small, large;
+    for (auto& t : tasks) (t.n <= kCoopN ? small : large).push_back(t);
+    auto smem_for = [](int nmax) {
+      int np = (nmax + 1) & ~1;
+      return (size_t)np * sizeof(double) + (size_t)(np / 2) * 2 * sizeof(int) + (size_t)np * sizeof(int);
+    };
+    if (!small.empty()) {
+      int nmax = 1;
+      for (auto& t : small) nmax = std::max(nmax, t.n);
+      size_t smem = smem_for(nmax);
+      if (smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      std::vector<size_t> off;
+      char* d = upload({{small.data(), small.size() * sizeof(EighTask)}}, off);
+      jacobi_kernel<<<(unsigned)small.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
+      ++launches;
+      CK(cudaGetLastError());
+    }
+    if (large.empty()) return;
     int nmax = 1;
-    for (auto& t : tasks) nmax = std::max(nmax, t.n);
-    int np = (nmax + 1) & ~1;
-    size_t smem = (size_t)np * sizeof(double) + (size_t)(np / 2) * 2 * sizeof(int) + (size_t)np * sizeof(int);
+    for (auto& t : large) nmax = std::max(nmax, t.n);
+    size_t smem = smem_for(nmax);
     if (smem > 200 * 1024) throw std::runtime_error("internal: eigensolver matrix too large");
-    if (smem > 48 * 1024)
-      CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    std::vector<size_t> off;
-    char* d = upload({{tasks.data(), tasks.size() * sizeof(EighTask)}}, off);
-    jacobi_kernel<<<(unsigned)tasks.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
-    ++launches;
-    CK(cudaGetLastError());
+    CK(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, 256, smem));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int capacity = std::max(1, per_sm * sms);
+    // largest matrices first; one launch per batch that fits co-resident
+    std::sort(large.begin(), large.end(), [](const EighTask& x, const EighTask& y) { return x.n > y.n; });
+    size_t i0 = 0;
+    while (i0 < large.size()) {
+      std::vector<CoopEigh> ct;
+      int ctas = 0;
+      size_t i1 = i0;
+      while (i1 < large.size()) {
+        int g = std::min(16, std::max(2, large[i1].n / 32));
+        g = std::min(g, capacity);
+        if (ctas + g > capacity && !ct.empty()) break;
+        ct.push_back({large[i1], g, ctas, nullptr});
+        ctas += g;
+        ++i1;
+      }
+      std::vector<unsigned> bars(2 * ct.size(), 0u);
+      std::vector<size_t> off;
+      char* d = upload({{ct.data(), ct.size() * sizeof(CoopEigh)}, {bars.data(), bars.size() * sizeof(unsigned)}},
+                       off);
+      unsigned* dbar = (unsigned*)(d + off[1]);
+      for (size_t k = 0; k < ct.size(); ++k) ct[k].bar = dbar + 2 * k;
+      CK(cudaMemcpyAsync(d + off[0], ct.data(), ct.size() * sizeof(CoopEigh), cudaMemcpyHostToDevice, st));
+      const CoopEigh* dt = (const CoopEigh*)(d + off[0]);
+      int nt = (int)ct.size();
+      int* fl = flag();
+      void* args[] = {(void*)&dt, (void*)&nt, (void*)&fl};
+      CK(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(ctas), dim3(256), args, smem, st));
+      ++launches;
+      i0 = i1;
+    }
   }
 };
 

@@ -276,6 +276,9 @@ dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* c, double* t) {
   t[3] = s.t_decimate;
   t[4] = s.t_renorm;
   t[5] = s.t_guess;
+  t[6] = s.t_enl_terms;
+  t[7] = s.t_enl_place_host;
+  t[8] = s.t_enl_comp;
   return DMRG_OK;
 }
 
@@ -590,6 +593,7 @@ dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, doubl
       ow += n[i];
     }
     be->eigh(t);
+    be->check_device_flag();
     be->copy_d2h(w, dw, wt * sizeof(double));
     be->copy_d2h(vecs, dV, tot * sizeof(double));
     be->free(dA);

@@ -15,6 +15,11 @@
 
 namespace dmrg {
 
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+
 namespace {
 thread_local std::string g_last_error;
 const double kSqrt2 = std::sqrt(2.0);
@@ -346,28 +351,41 @@ std::vector<OpKey> op_keys(const std::vector<int>& sites, int n, bool normal) {
 }
 
 // Collects place segments grouped by destination sub-block.
+// Collects place segments and groups them by destination sub-block (one
+// destination pointer always has the same shape): a flat list sorted by
+// destination at run time, in insertion order within a destination.
 struct PlaceBuilder {
-  std::map<std::tuple<double*, int, int, int>, std::vector<PlaceSeg>> groups;
+  struct Entry {
+    double* dst;
+    int rows, cols, ld;
+    PlaceSeg seg;
+  };
+  std::vector<Entry> entries;
   void add(double* dst, int rows, int cols, int ld, const PlaceSeg& s) {
     if (s.alpha == 0.0 || rows == 0 || cols == 0) return;
-    groups[{dst, rows, cols, ld}].push_back(s);
+    entries.push_back({dst, rows, cols, ld, s});
   }
   void run(Backend* be) {
+    std::stable_sort(entries.begin(), entries.end(),
+                     [](const Entry& a, const Entry& b) { return std::less<double*>()(a.dst, b.dst); });
     std::vector<PlaceGroup> g;
     std::vector<PlaceSeg> segs;
-    for (auto& [k, v] : groups) {
+    segs.reserve(entries.size());
+    for (size_t i = 0; i < entries.size();) {
+      size_t j = i;
       PlaceGroup pg;
-      pg.dst = std::get<0>(k);
-      pg.rows = std::get<1>(k);
-      pg.cols = std::get<2>(k);
-      pg.ld = std::get<3>(k);
+      pg.dst = entries[i].dst;
+      pg.rows = entries[i].rows;
+      pg.cols = entries[i].cols;
+      pg.ld = entries[i].ld;
       pg.seg_begin = (int)segs.size();
-      pg.seg_count = (int)v.size();
-      segs.insert(segs.end(), v.begin(), v.end());
+      while (j < entries.size() && entries[j].dst == entries[i].dst) segs.push_back(entries[j++].seg);
+      pg.seg_count = (int)(j - i);
       g.push_back(pg);
+      i = j;
     }
     if (!g.empty()) be->place(g, segs);
-    groups.clear();
+    entries.clear();
   }
 };
 
@@ -433,6 +451,7 @@ std::unique_ptr<Block> Engine::vacuum(bool left) {
 // Blocking: enlarged block = b (x) site (left) or site (x) b (right).
 std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   const SiteAlgebra& sa = site_algebra();
+  const double t_start = now_s();
   auto e = std::make_unique<Block>();
   e->left = b.left;
   e->nsites = b.nsites + 1;
@@ -548,7 +567,9 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
       tk.push_back({K_P, p, s, 2});
     }
     tmp->allocate(tk);
+    const double tc0 = now_s();
     build_comp_from_normal(b, *tmp, tk);
+    stats_.t_enl_comp += now_s() - tc0;
   }
   // S_p, p outside the enlarged block
   for (int p : rdm_mode_ ? std::vector<int>() : outs) {
@@ -658,6 +679,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
         }
       }
   }
+  stats_.t_enl_terms += now_s() - t_start;
   place_terms(b, tmp.get(), *e, terms);
   return e;
 }
@@ -707,6 +729,56 @@ SrcBlock find_block(OpSet& set, const OpSet* tmp, const Operand& x, int bra, int
   }
   return r;
 }
+// find_block with the operand's storage resolved once (base and layout of a
+// block operand; both null for the identity)
+struct ResolvedOperand {
+  const double* base = nullptr;
+  const Layout* lay = nullptr;
+  bool ok = false;
+};
+ResolvedOperand resolve(OpSet& set, const OpSet* tmp, const Operand& x) {
+  ResolvedOperand r;
+  if (x.t == Operand::ID) {
+    r.ok = true;
+    return r;
+  }
+  const double* base = set.get(x.key);
+  OpSet* owner = &set;
+  if (!base && tmp) {
+    base = tmp->get(x.key);
+    owner = const_cast<OpSet*>(tmp);
+  }
+  if (!base) return r;
+  r.base = base;
+  r.lay = &owner->layout(kind_dn(x.key.kind), x.key.k2);
+  r.ok = true;
+  return r;
+}
+SrcBlock block_of(const Basis& B, const ResolvedOperand& ro, const Operand& x, int bra, int ket) {
+  SrcBlock r;
+  if (x.t == Operand::ID) {
+    if (bra != ket) return r;
+    r.ok = true;
+    r.ld = B.sec[bra].dim;
+    return r;
+  }
+  if (!x.adj) {
+    int bi = ro.lay->find(bra, ket);
+    if (bi < 0) return r;
+    r.ptr = ro.base + ro.lay->blk[bi].off;
+    r.ld = ro.lay->blk[bi].cols;
+    r.ok = true;
+  } else {
+    int bi = ro.lay->find(ket, bra);
+    if (bi < 0) return r;
+    r.ptr = ro.base + ro.lay->blk[bi].off;
+    r.ld = ro.lay->blk[bi].cols;
+    r.trans = 1;
+    r.coef = adjoint_coef(B.sec[bra].j, B.sec[ket].j, x.key.k2);
+    r.ok = true;
+  }
+  return r;
+}
 double site_val(const Operand& y, int bra, int ket) {
   if (y.t == Operand::ID) return bra == ket ? 1.0 : 0.0;
   return y.s.m[bra][ket];
@@ -722,6 +794,7 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
   std::vector<std::vector<const EnlComp*>> by(eb.sec.size());
   for (auto& c : e.comps) by[c.esec].push_back(&c);
   const bool L = e.left;
+  const double t_host = now_s();
   PlaceBuilder pb;
   for (auto& [tk, t] : terms) {
     double* dst = eo.get(tk);
@@ -730,13 +803,15 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     const Operand& bop = L ? t.x : t.y;   // operand on the block part
     const Operand& sop = L ? t.y : t.x;   // operand on the site part
     if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
+    const ResolvedOperand rop = resolve(bo, tmp, bop);
+    if (!rop.ok) continue;
     for (auto& blk : TL.blk) {
       int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
       for (const EnlComp* cp : by[blk.bra])
         for (const EnlComp* c : by[blk.ket]) {
           double sv = site_val(sop, cp->site, c->site);
           if (sv == 0.0) continue;
-          SrcBlock src = find_block(bo, tmp, bop, cp->bsec, c->bsec);
+          SrcBlock src = block_of(bb, rop, bop, cp->bsec, c->bsec);
           if (!src.ok) continue;
           int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
           int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
@@ -760,6 +835,7 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
         }
     }
   }
+  stats_.t_enl_place_host += now_s() - t_host;
   pb.run(be_);
 }
 
@@ -1451,6 +1527,7 @@ std::unique_ptr<SavedU> Engine::decimate(Block& enl, const HPsiPlan& plan, const
     if (B.sec[s].dim > 0) tasks.push_back({rho + roff[s], wv + woff[s], vec + roff[s], B.sec[s].dim});
   }
   be_->eigh(tasks);
+  be_->check_device_flag();
   std::vector<double> w(wtot);
   be_->copy_d2h(w.data(), wv, wtot * sizeof(double));
   std::vector<Cand> cands;
@@ -1784,12 +1861,6 @@ void Engine::build_initial_right() {
     be_->sync();
   }
 }
-
-namespace {
-double now_s() {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-}  // namespace
 
 double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   double t0 = now_s();

@@ -156,6 +156,8 @@ struct SweepStats {
   // wall time per phase of the sweep (seconds, host clock around device-synchronised steps)
   double t_enlarge = 0.0, t_plan = 0.0, t_davidson = 0.0, t_decimate = 0.0, t_renorm = 0.0,
          t_guess = 0.0;
+  // inside enlarge: host term lists, host placement lists, complementary GEMMs
+  double t_enl_terms = 0.0, t_enl_place_host = 0.0, t_enl_comp = 0.0;
 };
 
 class Engine {

@@ -1,6 +1,9 @@
 // SU(2) coefficients (Racah closed forms) and the explicit one-site algebra.
 #include "su2.hpp"
 
+#include <cstdint>
+#include <unordered_map>
+
 #include <cstdlib>
 #include <mutex>
 #include <unordered_map>
@@ -102,9 +105,24 @@ double wigner9j(int a, int b, int c, int d, int e, int f, int g, int h, int i) {
 }
 
 double tensor_product_coef(int j1p, int j1, int kx, int j2p, int j2, int ky, int Jp, int J, int k) {
+  // memoised: the blocking and RDM planners ask for the same few thousand
+  // combinations millions of times; doubled spins here are far below 128
+  const int v[9] = {j1p, j1, kx, j2p, j2, ky, Jp, J, k};
+  uint64_t key = 0;
+  bool packable = true;
+  for (int x : v) {
+    if (x < 0 || x >= 128) packable = false;
+    key = (key << 7) | (uint64_t)(x & 127);
+  }
+  static thread_local std::unordered_map<uint64_t, double> cache;
+  if (packable) {
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
   double n9 = wigner9j(j1p, j1, kx, j2p, j2, ky, Jp, J, k);
-  if (n9 == 0.0) return 0.0;
-  return std::sqrt((J + 1.0) * (k + 1.0) * (j1p + 1.0) * (j2p + 1.0)) * n9;
+  double r = n9 == 0.0 ? 0.0 : std::sqrt((J + 1.0) * (k + 1.0) * (j1p + 1.0) * (j2p + 1.0)) * n9;
+  if (packable) cache.emplace(key, r);
+  return r;
 }
 
 double hpsi_coef(int jLp, int jRp, int jL, int jR, int k, int S) {

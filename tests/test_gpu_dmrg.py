@@ -185,6 +185,26 @@ def test_eigh_against_numpy(pkg):
         assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-12
 
 
+def test_eigh_cooperative_groups_density_matrices(pkg):
+    """Matrices above 96 go to the cooperative multi-CTA Jacobi: a batch of
+    density-matrix-like (PSD, rank-deficient, fast-decaying) and indefinite
+    matrices of several sizes, with small ones mixed in."""
+    rng = np.random.default_rng(8)
+    mats = []
+    for n in (97, 130, 257, 40, 400, 3):
+        x = rng.standard_normal((n, max(1, n // 2))) * np.exp(-np.arange(max(1, n // 2)) / 8.0)
+        mats.append(x @ x.T)
+    y = rng.standard_normal((211, 211))
+    mats.append(y + y.T)
+    res = pkg.ops.eigh_batched(mats)
+    for M, (w, V) in zip(mats, res):
+        ref = np.sort(np.linalg.eigvalsh(M))[::-1]
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(w - ref).max() < 1e-11 * scale
+        assert np.abs(V @ M - w[:, None] * V).max() < 1e-10 * scale
+        assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-11
+
+
 def random_hpsi_problem(rng, n_blocks, max_dim, max_items, big=False):
     """Sector-block contraction sigma += alpha op(A) P op(B)^T with ragged
     sizes (several 64-wide tiles and tails), both transposes, identities."""
