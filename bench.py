@@ -205,6 +205,77 @@ def run_reference(args):
     return 0
 
 
+def hpsi_problem(seed, n_blocks, dim_lo, dim_hi, items_per_block):
+    """Synthetic sector-block H_eff psi contraction with the shape mix of the
+    middle bonds of the Cholesky workloads (sector dimensions dim_lo..dim_hi,
+    a few percent identity factors), as flat float64 host arrays and the
+    block/item tuples of ops.hpsi_contract."""
+    rng = np.random.default_rng(seed)
+    dims = rng.integers(dim_lo, dim_hi + 1, size=n_blocks * 2)
+    A_parts, P_parts, B_parts, blocks, items = [], [], [], [], []
+    ao = po = bo = co = 0
+    flops = 0.0
+    for b in range(n_blocks):
+        m, n = int(dims[2 * b]), int(dims[2 * b + 1])
+        ib = len(items)
+        for _ in range(items_per_block):
+            ka = m if rng.random() < 0.02 else int(rng.integers(dim_lo, dim_hi + 1))
+            kb = n if rng.random() < 0.02 else int(rng.integers(dim_lo, dim_hi + 1))
+            a_id, b_id = int(ka == m and rng.random() < 0.5), 0
+            ta, tb = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+            if a_id:
+                a_entry = (0, 1, 0)
+            else:
+                a = rng.standard_normal((ka, m) if ta else (m, ka))
+                a_entry = (ao, a.shape[1], ta)
+                A_parts.append(a.ravel())
+                ao += a.size
+                flops += 2.0 * m * ka * kb
+            bm = rng.standard_normal((kb, n) if tb else (n, kb))
+            B_parts.append(bm.ravel())
+            b_entry = (bo, bm.shape[1], tb)
+            bo += bm.size
+            flops += 2.0 * m * n * kb
+            P_parts.append(rng.standard_normal(ka * kb))
+            items.append((a_entry[0], po, b_entry[0], a_entry[1], kb, b_entry[1], a_entry[2], b_entry[2],
+                          ka, kb, a_id, b_id, float(rng.standard_normal())))
+            po += ka * kb
+        blocks.append((co, m, n, n, ib, len(items) - ib))
+        co += m * n
+    return (np.concatenate(A_parts), np.concatenate(P_parts), np.concatenate(B_parts), co, blocks, items,
+            flops)
+
+
+def run_hpsi_only(args):
+    """The H_eff psi contraction alone (dmrg_hpsi_contract, one launch per
+    step) on the synthetic sector blocks; device time from CUDA events."""
+    import paper_2503_20700_gb300 as pkg
+    pkg.load()
+    prec = {"split": 1, "split-tc": 4, "split-all": 1, "fp64": 0}[args.precision]
+    A, P, B, clen, blocks, items, flops = hpsi_problem(7, 16, 100, 250, 80)
+    C = np.zeros(clen)
+    W, K = max(3, args.warmup), max(1, args.steps)
+    for _ in range(W):
+        pkg.ops.hpsi_contract(A, P, B, C, blocks, items, precision=prec)
+    ms = []
+    for _ in range(K):
+        pkg.ops.hpsi_contract(A, P, B, C, blocks, items, precision=prec)
+        ms.append(pkg.ops.last_contract_ms())
+    t = float(np.median(ms))
+    achieved = flops / (t / 1000.0) / 1e12
+    pk, src = peaks()
+    peak = pk["bf16_tflops"] * (1.1 / 2.25) / 3.0 if prec else 1.25
+    nbytes = 8.0 * (A.size + P.size + B.size + 2 * clen)
+    print(json.dumps({"mode": "hpsi-only", "precision": args.precision, "value": achieved, "unit": "TFLOP/s",
+                      "ms_per_launch": t, "steps": K, "warmup": W, "algorithmic_flops": flops,
+                      "operand_bytes": nbytes, "blocks": len(blocks), "items": len(items),
+                      "roofline": {"bound": "tensor" if prec else "alu", "achieved": achieved, "peak": peak,
+                                   "unit": "TFLOP/s", "frac": achieved / peak,
+                                   "peak_source": ("3xTF32 effective peak = burst bf16 (%s) x 1.1/2.25 / 3" % src)
+                                   if prec else "FP64 nominal 1.25 TFLOP/s"}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,9 +291,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--verbose", type=int, default=0, help="library diagnostics on stderr (2: H_eff psi shapes)")
+    ap.add_argument("--hpsi-only", action="store_true",
+                    help="time the H_eff psi contraction alone on synthetic sector blocks (kernel roofline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.hpsi_only:
+        return run_hpsi_only(args)
 
     import paper_2503_20700_gb300 as pkg
     pkg.load()

@@ -246,6 +246,12 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                                const dmrg_hpsi_item* items, int n_items, int precision,
                                int device);
 
+/* Device time (ms, CUDA events on the library's stream) of the kernels of
+ * the calling thread's last dmrg_hpsi_contract: the operand splits (tcgen05
+ * path), the contraction and the reduction of item chunks; host copies not
+ * included. */
+dmrg_status dmrg_last_contract_ms(double* ms);
+
 /*
  * dmrg_hpsi_contract_noalloc -- the fused H_eff psi contraction of
  * dmrg_hpsi_contract on caller-owned DEVICE buffers, allocating nothing.

@@ -818,8 +818,17 @@ class CudaBackend : public Backend {
   }
   void split(const SplitJob* jobs, int n) override {
     if (n <= 0) return;
+    // counted with the H_eff psi launches: the splits are part of its cost
+    Rec* rec = nullptr;
+    if (profiling) {
+      recs.push_back(Rec{ev(), ev(), 0.0, 1});
+      rec = &recs.back();
+      CK(cudaEventRecord(rec->a, st));
+    }
     split_launch(jobs, n, st);
     ++launches;
+    if (rec) CK(cudaEventRecord(rec->b, st));
+    if (recs.size() > 4096) drain();
   }
 
   void ensure_part(size_t n) {

@@ -27,6 +27,7 @@ struct dmrg_ctx {
 
 namespace {
 thread_local std::string tl_err;
+thread_local double tl_contract_ms = 0.0;
 
 dmrg_status fail(dmrg_ctx* c, dmrg_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -451,6 +452,8 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     std::vector<dmrg::HpsiItem> hi;
     double fl = 0.0;
     to_device_lists(blocks, n_blocks, items, n_items, dA, dP, dB, dC, hb, hi, &fl);
+    be->sync();
+    be->set_profile(true);
     const dmrg::Precision pr = precision == DMRG_FP64           ? dmrg::Precision::FP64
                                : precision == DMRG_SPLIT_HPSI_TC ? dmrg::Precision::TC_TF32X3
                                                                  : dmrg::Precision::SPLIT_TF32;
@@ -497,6 +500,9 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                (int)reds.size(), (double*)(d + os), pr, fl);
     }
     be->check_device_flag();
+    double kms = 0.0;
+    be->kernel_stats(1, &kms, nullptr, nullptr);
+    tl_contract_ms = kms;
     be->copy_d2h(C, dC, c_len * sizeof(double));
     be->sync();
     for (void* q : {(void*)dA, (void*)dP, (void*)dB, (void*)dC, (void*)d}) be->free(q);
@@ -505,6 +511,12 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
   } catch (const std::exception& e) {
     return translate(nullptr, e);
   }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_last_contract_ms(double* ms) {
+  if (!ms) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  *ms = tl_contract_ms;
   return DMRG_OK;
 }
 

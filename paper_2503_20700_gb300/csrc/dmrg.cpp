@@ -1077,22 +1077,22 @@ PsiLayout make_psi(const Basis& L, const Basis& R, int N, int S) {
   return P;
 }
 // bra sectors reachable from ket sector `ket` through operand x on basis B
-std::vector<std::pair<int, SrcBlock>> reach(OpSet& set, const Operand& x, int ket) {
-  std::vector<std::pair<int, SrcBlock>> out;
-  const Basis& B = set.basis;
+void reach(const Basis& B, const ResolvedOperand& ro, const Operand& x, int ket,
+           std::vector<std::pair<int, SrcBlock>>& out) {
+  out.clear();
+  if (!ro.ok) return;
   if (x.t == Operand::ID) {
     SrcBlock s;
     s.ok = true;
     s.ld = B.sec[ket].dim;
     out.push_back({ket, s});
-    return out;
+    return;
   }
   for (size_t bra = 0; bra < B.sec.size(); ++bra) {
     if (B.sec[bra].n != B.sec[ket].n + x.dn || !triangle(B.sec[ket].j, x.k2, B.sec[bra].j)) continue;
-    SrcBlock s = find_block(set, nullptr, x, (int)bra, ket);
+    SrcBlock s = block_of(B, ro, x, (int)bra, ket);
     if (s.ok) out.push_back({(int)bra, s});
   }
-  return out;
 }
 
 // H_eff psi as one fused launch: per sigma block, the list of items
@@ -1139,13 +1139,16 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   std::vector<std::vector<HpsiItem>> per(P.blk.size());
   std::vector<std::pair<int, HpsiItem>> diag_items;
   plan.flops = 0.0;
+  std::vector<std::pair<int, SrcBlock>> lr, rr;
   for (auto& t : terms) {
     // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
     int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
+    const ResolvedOperand rx = resolve(lo, nullptr, t.x), ry = resolve(ro, nullptr, t.y);
+    if (!rx.ok || !ry.ok) continue;
     for (auto& kb : P.blk) {
-      auto lr = reach(lo, t.x, kb.a);
+      reach(lo.basis, rx, t.x, kb.a, lr);
       if (lr.empty()) continue;
-      auto rr = reach(ro, t.y, kb.b);
+      reach(ro.basis, ry, t.y, kb.b, rr);
       if (rr.empty()) continue;
       const Sector& sa = lo.basis.sec[kb.a];
       const Sector& sb = ro.basis.sec[kb.b];
@@ -1389,11 +1392,12 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     be_->axpby(r, 1.0, x, -e, len);
     double rn = std::sqrt(std::max(0.0, dot_host(r, r)));
     if (opt_.verbose > 1) std::fprintf(stderr, "  davidson it %d m %d E %.12f res %.3e\n", it, m, e, rn);
-    // With split-precision H_eff psi the residual has a noise floor of a few
-    // 1e-7 |E| (TF32 pairs keep ~22 bits): converge to max(tol, floor) and
-    // stop on stagnation (no 10% improvement in 8 iterations) in any mode.
+    // With split-precision H_eff psi the residual has a noise floor of about
+    // 1e-7 |E| (TF32 pairs keep ~22 bits, FP32 accumulation): converge to
+    // max(tol, 2e-7 |E|) and stop on stagnation (no 10% improvement in 8
+    // iterations) in any mode.
     double tol_eff = opt_.davidson_tol;
-    if (opt_.prec != Precision::FP64) tol_eff = std::max(tol_eff, 1e-6 * std::max(1.0, std::abs(e)));
+    if (opt_.prec != Precision::FP64) tol_eff = std::max(tol_eff, 2e-7 * std::max(1.0, std::abs(e)));
     if (rn < tol_eff) break;
     if (rn < 0.9 * best_res) {
       best_res = rn;

@@ -52,6 +52,8 @@ def bind(lib):
                                        ctypes.POINTER(HpsiItem), ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int]
     lib.dmrg_hpsi_contract.restype = ctypes.c_int
+    lib.dmrg_last_contract_ms.argtypes = [dp]
+    lib.dmrg_last_contract_ms.restype = ctypes.c_int
     vp = ctypes.c_void_p
     lib.dmrg_hpsi_contract_noalloc.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                                vp, ctypes.c_int64, ctypes.POINTER(HpsiBlock), ctypes.c_int,
@@ -102,6 +104,15 @@ def hpsi_contract_noalloc(dA, a_len, dP, p_len, dB, b_len, dC, c_len, blocks, it
                                         len(items), precision, device, stream or None)
     if st != 0:
         raise DmrgError(st, lib.dmrg_last_error(None).decode())
+
+
+def last_contract_ms():
+    """Device milliseconds of the kernels of this thread's last hpsi_contract."""
+    from . import load
+    lib = load()
+    ms = ctypes.c_double()
+    lib.dmrg_last_contract_ms(ctypes.byref(ms))
+    return ms.value
 
 
 def hpsi_contract(A, P, B, C, blocks, items, precision=0, device=0):
