@@ -340,6 +340,7 @@ def main():
         wall = time.perf_counter() - t0
     launches = g.launch_count() - l0
     k_ms, k_flops, k_launch = g.kernel_stats(1)
+    kernel_ms = {name: g.kernel_stats(i)[0] for i, name in enumerate(["gemm", "hpsi", "place", "eigh"])}
     mem_now, mem_peak = g.memory()
     flops_job += flops
     _ = g.energy()
@@ -393,7 +394,7 @@ def main():
                 "sweep_energy": energies[-1], "sweep_energies": energies,
                 "sweep_seconds": t_max / K, "wall_seconds": wall,
                 "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
-                "phase_seconds": phases, "davidson_iters": st["davidson_iters"],
+                "phase_seconds": phases, "kernel_ms": kernel_ms, "davidson_iters": st["davidson_iters"],
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line))

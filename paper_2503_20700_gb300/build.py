@@ -55,7 +55,7 @@ def build(verbose=False):
         for (o, err), s in zip(res, srcs):
             if err.strip():
                 print(f"--- {s}\n{err}", file=sys.stderr)
-    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -552,8 +552,10 @@ class CudaBackend : public Backend {
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  double acc_ms[2] = {0, 0}, acc_flops[2] = {0, 0};
-  long acc_launch[2] = {0, 0};
+  // categories: 0 GEMMs, 1 H_eff psi (with its operand splits), 2 blocking
+  // placement, 3 eigensolver
+  double acc_ms[4] = {0, 0, 0, 0}, acc_flops[4] = {0, 0, 0, 0};
+  long acc_launch[4] = {0, 0, 0, 0};
   cudaEvent_t ev() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -569,7 +571,7 @@ class CudaBackend : public Backend {
       CK(cudaEventSynchronize(r.b));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, r.a, r.b));
-      int t = r.tag ? 1 : 0;
+      int t = std::min(3, std::max(0, r.tag));
       acc_ms[t] += ms;
       acc_flops[t] += r.flops;
       acc_launch[t] += 1;
@@ -593,11 +595,11 @@ class CudaBackend : public Backend {
   void set_profile(bool on) override {
     drain();
     profiling = on;
-    for (int t = 0; t < 2; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
+    for (int t = 0; t < 4; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
   }
   void kernel_stats(int t, double* ms, double* flops, long* launches) override {
     drain();
-    t = t ? 1 : 0;
+    t = std::min(3, std::max(0, t));
     if (ms) *ms = acc_ms[t];
     if (flops) *flops = acc_flops[t];
     if (launches) *launches = acc_launch[t];
@@ -726,9 +728,17 @@ class CudaBackend : public Backend {
                       {segs.data(), segs.size() * sizeof(PlaceSeg)},
                       {tiles.data(), tiles.size() * sizeof(PlaceTile)}},
                      off);
+    Rec* rec = nullptr;
+    if (profiling) {
+      recs.push_back(Rec{ev(), ev(), 0.0, 2});
+      rec = &recs.back();
+      CK(cudaEventRecord(rec->a, st));
+    }
     place_kernel<<<(unsigned)tiles.size(), 256, 0, st>>>((const PlaceGroup*)(d + off[0]),
                                                           (const PlaceSeg*)(d + off[1]),
                                                           (const PlaceTile*)(d + off[2]));
+    if (rec) CK(cudaEventRecord(rec->b, st));
+    if (recs.size() > 4096) drain();
     ++launches;
     CK(cudaGetLastError());
   }
@@ -889,7 +899,14 @@ class CudaBackend : public Backend {
         CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       std::vector<size_t> off;
       char* d = upload({{small.data(), small.size() * sizeof(EighTask)}}, off);
+      Rec* rec = nullptr;
+      if (profiling) {
+        recs.push_back(Rec{ev(), ev(), 0.0, 3});
+        rec = &recs.back();
+        CK(cudaEventRecord(rec->a, st));
+      }
       jacobi_kernel<<<(unsigned)small.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
+      if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       CK(cudaGetLastError());
     }
@@ -930,7 +947,14 @@ class CudaBackend : public Backend {
       int nt = (int)ct.size();
       int* fl = flag();
       void* args[] = {(void*)&dt, (void*)&nt, (void*)&fl};
+      Rec* rec = nullptr;
+      if (profiling) {
+        recs.push_back(Rec{ev(), ev(), 0.0, 3});
+        rec = &recs.back();
+        CK(cudaEventRecord(rec->a, st));
+      }
       CK(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(ctas), dim3(256), args, smem, st));
+      if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       i0 = i1;
     }

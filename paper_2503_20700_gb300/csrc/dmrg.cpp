@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -795,46 +796,83 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
   for (auto& c : e.comps) by[c.esec].push_back(&c);
   const bool L = e.left;
   const double t_host = now_s();
-  PlaceBuilder pb;
-  for (auto& [tk, t] : terms) {
-    double* dst = eo.get(tk);
-    if (!dst) continue;
-    const Layout& TL = eo.layout(kind_dn(tk.kind), tk.k2);
-    const Operand& bop = L ? t.x : t.y;   // operand on the block part
-    const Operand& sop = L ? t.y : t.x;   // operand on the site part
+  // storage of every term resolved serially (layouts are created on demand)
+  struct TermCtx {
+    double* dst = nullptr;
+    const Layout* TL = nullptr;
+    ResolvedOperand rop;
+  };
+  std::vector<TermCtx> ctx(terms.size());
+  for (size_t i = 0; i < terms.size(); ++i) {
+    const auto& [tk, t] = terms[i];
+    ctx[i].dst = eo.get(tk);
+    if (!ctx[i].dst) continue;
+    ctx[i].TL = &eo.layout(kind_dn(tk.kind), tk.k2);
+    const Operand& bop = L ? t.x : t.y;
     if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
-    const ResolvedOperand rop = resolve(bo, tmp, bop);
-    if (!rop.ok) continue;
-    for (auto& blk : TL.blk) {
-      int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
-      for (const EnlComp* cp : by[blk.bra])
-        for (const EnlComp* c : by[blk.ket]) {
-          double sv = site_val(sop, cp->site, c->site);
-          if (sv == 0.0) continue;
-          SrcBlock src = block_of(bb, rop, bop, cp->bsec, c->bsec);
-          if (!src.ok) continue;
-          int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
-          int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
-          double tp;
-          int nleft, pright;
-          if (L) {
-            tp = tensor_product_coef(jb_p, jb, bop.k2, js_p, js, sop.k2, Jp, J, t.k2);
-            nleft = bb.sec[c->bsec].n;
-            pright = sop.par;
-          } else {
-            tp = tensor_product_coef(js_p, js, sop.k2, jb_p, jb, bop.k2, Jp, J, t.k2);
-            nleft = kSiteN[c->site];
-            pright = bop.par;
-          }
-          if (tp == 0.0) continue;
-          double sign = ((pright & nleft) & 1) ? -1.0 : 1.0;
-          double alpha = t.coef * tp * sv * sign * src.coef;
-          int rows = bb.sec[cp->bsec].dim, cols = bb.sec[c->bsec].dim;
-          double* d = dst + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
-          pb.add(d, rows, cols, blk.cols, PlaceSeg{src.ptr, src.ld, src.trans, alpha});
-        }
-    }
+    ctx[i].rop = resolve(bo, tmp, bop);
   }
+  // placement segments of a range of terms (pure host arithmetic)
+  auto generate = [&](size_t t0, size_t t1, std::vector<PlaceBuilder::Entry>& out) {
+    for (size_t i = t0; i < t1; ++i) {
+      const TermCtx& cx = ctx[i];
+      if (!cx.dst || !cx.rop.ok) continue;
+      const Term& t = terms[i].second;
+      const Operand& bop = L ? t.x : t.y;   // operand on the block part
+      const Operand& sop = L ? t.y : t.x;   // operand on the site part
+      for (auto& blk : cx.TL->blk) {
+        int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
+        for (const EnlComp* cp : by[blk.bra])
+          for (const EnlComp* c : by[blk.ket]) {
+            double sv = site_val(sop, cp->site, c->site);
+            if (sv == 0.0) continue;
+            SrcBlock src = block_of(bb, cx.rop, bop, cp->bsec, c->bsec);
+            if (!src.ok) continue;
+            int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
+            int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
+            double tp;
+            int nleft, pright;
+            if (L) {
+              tp = tensor_product_coef(jb_p, jb, bop.k2, js_p, js, sop.k2, Jp, J, t.k2);
+              nleft = bb.sec[c->bsec].n;
+              pright = sop.par;
+            } else {
+              tp = tensor_product_coef(js_p, js, sop.k2, jb_p, jb, bop.k2, Jp, J, t.k2);
+              nleft = kSiteN[c->site];
+              pright = bop.par;
+            }
+            if (tp == 0.0) continue;
+            double sign = ((pright & nleft) & 1) ? -1.0 : 1.0;
+            double alpha = t.coef * tp * sv * sign * src.coef;
+            int rows = bb.sec[cp->bsec].dim, cols = bb.sec[c->bsec].dim;
+            if (alpha == 0.0 || rows == 0 || cols == 0) continue;
+            double* d = cx.dst + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
+            out.push_back({d, rows, cols, blk.cols, PlaceSeg{src.ptr, src.ld, src.trans, alpha}});
+          }
+      }
+    }
+  };
+  // host threads over contiguous term ranges, concatenated in term order so
+  // the placement (and its summation order) does not depend on the split
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (terms.size() < 256) nth = 1;
+  std::vector<std::vector<PlaceBuilder::Entry>> parts(nth);
+  if (nth == 1) {
+    generate(0, terms.size(), parts[0]);
+  } else {
+    std::vector<std::thread> th;
+    const size_t per = (terms.size() + nth - 1) / nth;
+    for (unsigned w = 0; w < nth; ++w) {
+      size_t t0 = std::min(terms.size(), w * per), t1 = std::min(terms.size(), t0 + per);
+      th.emplace_back([&, t0, t1, w] { generate(t0, t1, parts[w]); });
+    }
+    for (auto& x : th) x.join();
+  }
+  PlaceBuilder pb;
+  size_t total = 0;
+  for (auto& p : parts) total += p.size();
+  pb.entries.reserve(total);
+  for (auto& p : parts) pb.entries.insert(pb.entries.end(), p.begin(), p.end());
   stats_.t_enl_place_host += now_s() - t_host;
   pb.run(be_);
 }

@@ -1,16 +1,17 @@
 // tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh).
 //
-// Shared memory (bytes): X hi/lo planes (2 x 32 KB, 128 x 64, K-major) and two
-// 64 KB slots, each holding the operand tiles of one k-block of 32:
+// Shared memory (bytes): X hi/lo planes (2 x 32 KB, 128 x 64, K-major) and
+// three 48 KB slots, each holding the operand tiles of one k-block of 32:
 //   stage 1: A hi | A lo (128 x 32 each, 16 KB) | P^T hi | P^T lo (64 x 32, 8 KB)
-//   stage 2: B hi | B lo (N x 32 each, N <= 256, 32 KB)
+//   stage 2: B hi | B lo (up to 128 x 32 each, 16 KB): one column half of
+//            the sigma tile (columns [0, 128) or [128, N))
 // all in the canonical no-swizzle K-major layout (8-row x 16-byte core
 // matrices; 128 B between K-adjacent cores, 1 KB between 8-row groups for
 // 32-wide tiles, 2 KB for the 64-wide X).  TMEM: S in columns [0, 256), X' in
-// [256, 320).  The k-blocks of a task form one sequence; block b+1 is copied
-// into the other slot while the MMAs of block b run, each slot has its own
-// mbarrier (tcgen05.commit after the block's MMAs), and every wait is bounded
-// by 2 s of wall clock.
+// [256, 320).  The k-blocks of a task form one sequence; blocks b+1 and b+2
+// are in flight (cp.async into the other two slots) while the MMAs of block
+// b run; each slot has its own mbarrier (tcgen05.commit after the block's
+// MMAs) and every wait is bounded by 2 s of wall clock.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +20,7 @@
 #include <stdexcept>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 
 #include "hpsi_tc.cuh"
 
@@ -30,8 +32,11 @@ constexpr int TM = kTcTileM, TNMAX = kTcTileN, KB = 32, JC = 64;
 constexpr uint32_t LBO = 128;
 constexpr uint32_t SBO32 = 1024;  // 8-row group stride of a 32-wide tile
 constexpr uint32_t SBO64 = 2048;  // of the 64-wide X tile
-constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_SLOT = 65536, SLOT = 65536;
-constexpr int SMEM_BYTES = OFF_SLOT + 2 * SLOT;  // 192 KB
+constexpr int NSLOT = 3;
+constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_SLOT = 65536, SLOT = 49152;
+constexpr int SMEM_BYTES = OFF_SLOT + NSLOT * SLOT;  // 208 KB
+constexpr int HALF = 128;  // column half of the sigma tile per stage-2 block
+constexpr int kDrainItems = 4;  // items accumulated in FP32 before a float64 drain
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -121,7 +126,7 @@ __device__ __forceinline__ void load_tile(uint32_t dhi, uint32_t dlo, const TcMa
 }
 
 struct Cursor {
-  int ii, jc, jc_end, stage, k0;
+  int ii, jc, jc_end, stage, k0, half;
 };
 
 __device__ __forceinline__ void cursor_item(Cursor& c, const TcItem& it, int c0, int N) {
@@ -133,6 +138,7 @@ __device__ __forceinline__ void cursor_item(Cursor& c, const TcItem& it, int c0,
   }
   c.stage = it.A.hi ? 1 : 2;
   c.k0 = 0;
+  c.half = 0;
 }
 __device__ __forceinline__ int chunk_kspan(const Cursor& c) { return min(JC, roundup32(c.jc_end - c.jc)); }
 // advance to the next k-block; false at the end of the task
@@ -145,6 +151,11 @@ __device__ __forceinline__ bool cursor_next(Cursor& c, const TcItem* __restrict_
     c.k0 = 0;
     return true;
   }
+  if (c.half == 0 && N > HALF) {
+    c.half = 1;
+    return true;
+  }
+  c.half = 0;
   c.k0 += KB;
   if (c.k0 < chunk_kspan(c)) return true;
   c.jc += JC;
@@ -162,7 +173,7 @@ __global__ void __launch_bounds__(128, 1)
     hpsi_tc_kernel(const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, double* __restrict__ scratch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[NSLOT];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -178,8 +189,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    for (int i = 0; i < NSLOT; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -188,7 +198,8 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tS = tmem_base + TCOL_S, tX = tmem_base + TCOL_X;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t id1 = idesc_tf32(TM, JC), id2 = idesc_tf32(TM, N);
+  const int N1 = min(N, HALF), N2 = N - N1;  // MMA widths of the two column halves
+  const uint32_t id1 = idesc_tf32(TM, JC), id2a = idesc_tf32(TM, N1), id2b = idesc_tf32(TM, N2 > 0 ? N2 : 16);
 
   // issue the operand copies of the block at cursor c into slot s
   auto produce = [&](const Cursor& c, int s) {
@@ -198,14 +209,15 @@ __global__ void __launch_bounds__(128, 1)
       load_tile(sl, sl + 16384, it.A, tk.r0, TM, bk.m, c.k0, tid);
       load_tile(sl + 32768, sl + 40960, it.Pt, c.jc, JC, it.kb, c.k0, tid);
     } else if (it.B.hi != nullptr) {
-      load_tile(sl, sl + 32768, it.B, tk.c0, N, bk.n, c.jc + c.k0, tid);
+      load_tile(sl, sl + 16384, it.B, tk.c0 + c.half * HALF, c.half ? N2 : N1, bk.n, c.jc + c.k0, tid);
     } else {
       // identity on the right: B(n, k) = [c0 + n == jc + k0 + k]
       float* bh = (float*)(smraw + OFF_SLOT + s * SLOT);
-      float* bl = (float*)(smraw + OFF_SLOT + s * SLOT + 32768);
-      for (int e = tid; e < N * KB; e += 128) {
+      float* bl = (float*)(smraw + OFF_SLOT + s * SLOT + 16384);
+      const int n0 = c.half * HALF, nn = c.half ? N2 : N1;
+      for (int e = tid; e < nn * KB; e += 128) {
         int n = e / KB, k = e % KB;
-        bool one = (tk.c0 + n == c.jc + c.k0 + k) && (tk.c0 + n < bk.n);
+        bool one = (tk.c0 + n0 + n == c.jc + c.k0 + k) && (tk.c0 + n0 + n < bk.n);
         uint32_t o = word_off(n, k, SBO32) >> 2;
         bh[o] = one ? 1.0f : 0.0f;
         bl[o] = 0.0f;
@@ -215,22 +227,58 @@ __global__ void __launch_bounds__(128, 1)
   };
   // bounded wait on the commit of block b; failure sets the abort flag
   auto wait_block = [&](int b) {
-    if (!wait_bar(&bar[b & 1], (uint32_t)((b >> 1) & 1))) abort_flag = 1;
+    if (b < 0) return;
+    if (!wait_bar(&bar[b % NSLOT], (uint32_t)((b / NSLOT) & 1))) abort_flag = 1;
+  };
+
+  // S (FP32, TMEM) is added to the task's float64 output every kDrainItems
+  // items and at the end, so FP32 accumulation spans a few items only.
+  // The first drain into a private partial tile stores, later ones add.
+  bool s_started = false, s_started_b = false;  // first / second column half written since the last drain
+  bool drained = false;
+  auto drain = [&]() {
+    const int r = tid;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      if (s_started) {
+        tmem_ld16(tS + lane_base + c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        int c = c0 + j;
+        if (tk.part >= 0) {
+          double* d = scratch + tk.part + (long long)r * TNMAX + c;
+          *d = drained ? *d + (double)v[j] : (double)v[j];
+        } else {
+          int gr = tk.r0 + r, gc = tk.c0 + c;
+          if (gr < bk.m && c < nvalid) bk.C[(size_t)gr * bk.ldc + gc] += (double)v[j];
+        }
+      }
+    }
+    drained = true;
   };
 
   Cursor cur;
   cur.ii = tk.it_begin;
   cursor_item(cur, items[cur.ii], tk.c0, N);
-  bool s_started = false;
+  // blocks b+1 and b+2 (n1, n2) are prefetched ahead of block b
+  Cursor n1 = cur, n2;
+  bool has1 = cursor_next(n1, items, it_end, tk.c0, N), has2 = false;
+  n2 = n1;
+  if (has1) has2 = cursor_next(n2, items, it_end, tk.c0, N);
   int b = 0;
   produce(cur, 0);
+  if (has1) produce(n1, 1);
   for (;;) {
-    // prefetch block b+1 into the other slot once the MMAs of block b-1 are done
-    Cursor nxt = cur;
-    const bool has_next = cursor_next(nxt, items, it_end, tk.c0, N);
-    if (has_next) {
-      if (b >= 1) wait_block(b - 1);
-      produce(nxt, (b + 1) & 1);
+    // prefetch block b+2 into the slot of block b-1 once its MMAs are done
+    if (has2) {
+      wait_block(b - 1);
+      produce(n2, (b + 2) % NSLOT);
+      asm volatile("cp.async.wait_group 2;");
+    } else if (has1) {
       asm volatile("cp.async.wait_group 1;");
     } else {
       asm volatile("cp.async.wait_group 0;");
@@ -239,7 +287,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (abort_flag) break;
     const TcItem& it = items[cur.ii];
-    if (cur.stage == 2 && cur.k0 == 0) {
+    if (cur.stage == 2 && cur.k0 == 0 && cur.half == 0) {
       // X = alpha X' (or alpha P for an identity left operand) -> hi/lo planes;
       // the commit of block b-1 covers every earlier MMA (stage 1 of this
       // chunk, stage 2 of the previous one that read X)
@@ -281,7 +329,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sl = sbase + OFF_SLOT + (b & 1) * SLOT;
+      const uint32_t sl = sbase + OFF_SLOT + (b % NSLOT) * SLOT;
       if (cur.stage == 1) {
 #pragma unroll
         for (int s = 0; s < KB / 8; ++s) {
@@ -294,52 +342,61 @@ __global__ void __launch_bounds__(128, 1)
         }
       } else {
         const uint32_t xo = (uint32_t)(cur.k0 / 4) * LBO;
+        const uint32_t dS = tS + (uint32_t)(cur.half * HALF);
+        const uint32_t id2 = cur.half ? id2b : id2a;
+        // the first MMA into each column half overwrites it
+        const bool fresh = cur.half == 0 ? !s_started : !s_started_b;
 #pragma unroll
         for (int s = 0; s < KB / 8; ++s) {
           const uint32_t ko = (uint32_t)s * 2 * LBO;
           uint64_t ah = desc(xh + xo + ko, SBO64), al = desc(xl + xo + ko, SBO64);
-          uint64_t bh = desc(sl + ko, SBO32), bl = desc(sl + 32768 + ko, SBO32);
-          mma_tf32(tS, al, bh, id2, (s_started || s > 0) ? 1u : 0u);
-          mma_tf32(tS, ah, bl, id2, 1u);
-          mma_tf32(tS, ah, bh, id2, 1u);
+          uint64_t bh = desc(sl + ko, SBO32), bl = desc(sl + 16384 + ko, SBO32);
+          mma_tf32(dS, al, bh, id2, (!fresh || s > 0) ? 1u : 0u);
+          mma_tf32(dS, ah, bl, id2, 1u);
+          mma_tf32(dS, ah, bh, id2, 1u);
         }
       }
-      commit(&bar[b & 1]);
+      commit(&bar[b % NSLOT]);
     }
-    if (cur.stage == 2) s_started = true;  // uniform over the CTA
-    if (!has_next) break;
-    cur = nxt;
+    // uniform over the CTA
+    if (cur.stage == 2) {
+      if (cur.half == 0) s_started = true;
+      else s_started_b = true;
+    }
+    if (!has1) break;
+    if (n1.ii != cur.ii && ((n1.ii - tk.it_begin) % kDrainItems) == 0 && s_started) {
+      // item boundary: drain S once its MMAs are done, then let the next
+      // stage-2 MMA overwrite it
+      wait_block(b);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      __syncthreads();
+      if (abort_flag) break;
+      drain();
+      s_started = s_started_b = false;
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+    }
+    cur = n1;
+    n1 = n2;
+    has1 = has2;
+    if (has1) {
+      has2 = cursor_next(n2, items, it_end, tk.c0, N);
+    } else {
+      has2 = false;
+    }
     ++b;
   }
-  // wait for the last block (and, after an abort, for whatever is in flight)
+  // wait for the last blocks (after an abort, whatever may be in flight)
   wait_block(b);
-  if (b >= 1) wait_block(b - 1);
+  wait_block(b - 1);
+  wait_block(b - 2);
   asm volatile("cp.async.wait_group 0;");
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
   if (abort_flag) {
     if (tid == 0) atomicExch(err, 1);
-  } else {
-    const int r = tid;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      if (s_started) {
-        tmem_ld16(tS + lane_base + c0, v);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        int c = c0 + j;
-        if (tk.part >= 0) {
-          scratch[tk.part + (long long)r * TNMAX + c] = (double)v[j];
-        } else {
-          int gr = tk.r0 + r, gc = tk.c0 + c;
-          if (gr < bk.m && c < nvalid) bk.C[(size_t)gr * bk.ldc + gc] += (double)v[j];
-        }
-      }
-    }
+  } else if (s_started || !drained) {
+    drain();
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -384,13 +441,27 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
   plan = TcPlan();
   auto r32 = [](int x) { return (x + 31) & ~31; };
   // distinct operands: (src, trans, rows, cols, ld) -> job; plane offsets in floats
-  std::map<std::tuple<const double*, int, int, int, int>, int> index;
+  struct Key {
+    const double* src;
+    int trans, rows, cols, ld;
+    bool operator==(const Key& o) const {
+      return src == o.src && trans == o.trans && rows == o.rows && cols == o.cols && ld == o.ld;
+    }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      size_t h = std::hash<const void*>()(k.src);
+      for (int v : {k.trans, k.rows, k.cols, k.ld}) h = h * 1000003u ^ (size_t)v;
+      return h;
+    }
+  };
+  std::unordered_map<Key, int, KeyHash> index;
   std::vector<SplitJob> jobs;
   std::vector<std::pair<size_t, size_t>> offs;
   std::vector<int> is_psi;
   size_t floats = 0;
   auto want = [&](const double* src, int trans, int rows, int cols, int ld, bool psi) -> int {
-    auto key = std::make_tuple(src, trans, rows, cols, ld);
+    const Key key{src, trans, rows, cols, ld};
     auto it = index.find(key);
     if (it != index.end()) return it->second;
     SplitJob j{src, rows, cols, ld, trans, nullptr, nullptr, r32(cols)};
