@@ -5,7 +5,8 @@
 //   gemm_f64_kernel     C += sum_s alpha_s op(A_s) op(B_s)    (FP64 reference path, DFMA)
 //   gemm_tf32x3 (gemm_split.cu)                                (split-FP32 tensor-core path)
 //   dots/combine/axpby  Davidson vector algebra (FP64, deterministic two-stage reductions)
-//   jacobi_kernel       parallel cyclic Jacobi eigensolver, one CTA per matrix (FP64)
+//   jacobi_smem_kernel  parallel cyclic Jacobi eigensolver in shared memory, one CTA per matrix (FP64)
+//   jacobi_coop_kernel  the same on cooperative CTA groups for larger matrices
 // All kernels are bounded loops over their inputs; none waits on another CTA.
 #include <cuda_runtime.h>
 
@@ -201,34 +202,51 @@ __global__ void precond_kernel(double* __restrict__ y, const double* __restrict_
 
 // ------------------------------------------------------------------ Jacobi
 // Parallel cyclic Jacobi (round-robin pairing) on a symmetric n x n matrix
-// held in global memory (destroyed).  Eigenvalues descending in w, the
-// eigenvectors as rows of V.  One round rotates n/2 disjoint pairs; each
-// 2x2 block (pair i rows, pair j columns) of A is updated in one pass as
-// R_i X R_j^T, and the eigenvector rows p, q of V are rotated together.
-// A pair is skipped when its off-diagonal entry is negligible next to both
-// diagonal entries, or below 1e-20 ||A||_F; the iteration stops after a
-// sweep without rotations, or after kMaxSweeps sweeps.
+// (destroyed).  Eigenvalues descending in w, the eigenvectors as rows of V.
+// One round rotates n/2 disjoint pairs; each 2x2 block (pair i rows, pair j
+// columns) of A is updated in one pass as R_i X R_j^T, and the eigenvector
+// rows p, q of V are rotated together.  A pair is skipped when its
+// off-diagonal entry is negligible next to both diagonal entries, or below
+// 1e-20 ||A||_F; the iteration stops after a sweep without rotations, or
+// after kMaxSweeps sweeps.
 constexpr int kMaxSweeps = 40;
 
-__global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict__ tasks) {
+// jacobi_smem_kernel (n <= kSmemN, one CTA per matrix): A (row stride n+1)
+// and the eigenvector rows V live in shared memory for the whole iteration,
+// so every round's loads and stores stay on chip.
+constexpr int kSmemN = 112;
+__host__ __device__ constexpr size_t jacobi_smem_bytes(int n) {
+  return ((size_t)n * (n + 1) + (size_t)n * n + (size_t)((n + 1) & ~1)) * sizeof(double) +
+         (size_t)((n + 1) & ~1) * 2 * sizeof(int) + 64;
+}
+
+__global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __restrict__ tasks) {
   const EighTask tk = tasks[blockIdx.x];
   const int n = tk.n;
-  double* a = const_cast<double*>(tk.A);
-  double* v = tk.V;  // v[p*n + k]: row p = eigenvector p during the iteration
+  const int lda = n + 1;
+  const int np = (n + 1) & ~1, h = np / 2;
   extern __shared__ double sm[];
-  const int np = (n + 1) & ~1;  // even count, with a dummy index when n is odd
-  const int h = np / 2;
-  double* cs = sm;              // h cosines
-  double* sn = sm + h;          // h sines
-  int* pp = (int*)(sm + np);    // pairs
+  double* a = sm;                        // n x (n+1)
+  double* v = a + (size_t)n * lda;       // n x n, row p = eigenvector p
+  double* cs = v + (size_t)n * n;        // h
+  double* sn = cs + h;                   // h
+  int* pp = (int*)(sn + h);
   int* qq = pp + h;
-  int* perm = qq + h;           // round-robin order (np entries)
+  int* perm = qq + h;                    // np
   __shared__ double red[256];
   __shared__ int nrot;
-  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) v[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e % n;
+    a[r * lda + c] = tk.A[e];
+    v[e] = (r == c) ? 1.0 : 0.0;
+  }
   for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
+  __syncthreads();
   double fro = 0.0;
-  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) fro += a[e] * a[e];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    double x = a[(e / n) * lda + e % n];
+    fro += x * x;
+  }
   red[threadIdx.x] = fro;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -248,8 +266,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
         qq[i] = q;
         double c = 1.0, s = 0.0;
         if (q < n) {
-          double apq = a[(size_t)p * n + q];
-          double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+          double apq = a[p * lda + q], app = a[p * lda + p], aqq = a[q * lda + q];
           double g = 100.0 * fabs(apq);
           bool negligible = fabs(apq) <= floor_abs || (fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq));
           if (!negligible) {
@@ -264,36 +281,32 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
         sn[i] = s;
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block per (i, j)
-      for (size_t e = threadIdx.x; e < (size_t)h * h; e += blockDim.x) {
-        int i = (int)(e / h), j = (int)(e % h);
+      for (int e = threadIdx.x; e < h * h; e += blockDim.x) {
+        int i = e / h, j = e % h;
         double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
         if (si == 0.0 && sj == 0.0) continue;
         int p = pp[i], q = qq[i], r = pp[j], t = qq[j];
         bool qv = q < n, tv = t < n;
-        double x00 = a[(size_t)p * n + r];
-        double x01 = tv ? a[(size_t)p * n + t] : 0.0;
-        double x10 = qv ? a[(size_t)q * n + r] : 0.0;
-        double x11 = (qv && tv) ? a[(size_t)q * n + t] : 0.0;
-        // rows: [p; q] <- [c -s; s c] [p; q]
+        double x00 = a[p * lda + r];
+        double x01 = tv ? a[p * lda + t] : 0.0;
+        double x10 = qv ? a[q * lda + r] : 0.0;
+        double x11 = (qv && tv) ? a[q * lda + t] : 0.0;
         double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
         double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        // columns: [r t] <- [r t] [c s; -s c]
-        a[(size_t)p * n + r] = cj * y00 - sj * y01;
-        if (tv) a[(size_t)p * n + t] = sj * y00 + cj * y01;
-        if (qv) a[(size_t)q * n + r] = cj * y10 - sj * y11;
-        if (qv && tv) a[(size_t)q * n + t] = sj * y10 + cj * y11;
+        a[p * lda + r] = cj * y00 - sj * y01;
+        if (tv) a[p * lda + t] = sj * y00 + cj * y01;
+        if (qv) a[q * lda + r] = cj * y10 - sj * y11;
+        if (qv && tv) a[q * lda + t] = sj * y10 + cj * y11;
       }
-      // V rows
-      for (size_t e = threadIdx.x; e < (size_t)h * n; e += blockDim.x) {
-        int i = (int)(e / n), k = (int)(e % n);
+      for (int e = threadIdx.x; e < h * n; e += blockDim.x) {
+        int i = e / n, k = e % n;
         double s = sn[i];
         if (s == 0.0) continue;
         double c = cs[i];
         int p = pp[i], q = qq[i];
-        double vp = v[(size_t)p * n + k], vq = v[(size_t)q * n + k];
-        v[(size_t)p * n + k] = c * vp - s * vq;
-        v[(size_t)q * n + k] = s * vp + c * vq;
+        double vp = v[p * n + k], vq = v[q * n + k];
+        v[p * n + k] = c * vp - s * vq;
+        v[q * n + k] = s * vp + c * vq;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -306,38 +319,30 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const EighTask* __restrict_
     if (nrot == 0) break;
     __syncthreads();
   }
-  // sort eigenvalues descending (rank by counting, ties by index) and write rows of V
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double di = a[(size_t)i * n + i];
-    if (!(di == di)) di = -INFINITY;  // a NaN sorts last, so ranks stay a permutation
+    double di = a[i * lda + i];
+    if (!(di == di)) di = -INFINITY;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double dj = a[(size_t)j * n + j];
+      double dj = a[j * lda + j];
       if (!(dj == dj)) dj = -INFINITY;
       rank += (dj > di) || (dj == di && j < i);
     }
     perm[rank] = i;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += blockDim.x) tk.w[r] = a[(size_t)perm[r] * n + perm[r]];
-  __syncthreads();
-  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) a[e] = v[e];
-  __syncthreads();
-  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
-    int r = (int)(e / n), k = (int)(e % n);
-    v[e] = a[(size_t)perm[r] * n + k];
-  }
-  __syncthreads();
-  // sign convention: largest-magnitude component of each eigenvector positive
+  for (int r = threadIdx.x; r < n; r += blockDim.x) tk.w[r] = a[perm[r] * lda + perm[r]];
+  // eigenvector rows in descending order, largest-magnitude component positive
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double* src = v + (size_t)perm[r] * n;
     double best = 0.0;
     int bi = 0;
     for (int k = 0; k < n; ++k) {
-      double x = fabs(v[(size_t)r * n + k]);
+      double x = fabs(src[k]);
       if (x > best + 1e-12) { best = x; bi = k; }
     }
-    if (v[(size_t)r * n + bi] < 0)
-      for (int k = 0; k < n; ++k) v[(size_t)r * n + k] = -v[(size_t)r * n + k];
+    double sg = src[bi] < 0 ? -1.0 : 1.0;
+    for (int k = 0; k < n; ++k) tk.V[(size_t)r * n + k] = sg * src[k];
   }
 }
 
@@ -882,30 +887,31 @@ class CudaBackend : public Backend {
   }
   // Matrices up to kCoopN use one CTA each; larger ones a cooperative group
   // of g CTAs (g grows with n, the groups of one launch fit co-resident).
-  static constexpr int kCoopN = 96;
+  static constexpr int kCoopN = kSmemN;
   void eigh(const std::vector<EighTask>& tasks) override {
     if (tasks.empty()) return;
-    std::vector<EighTask> small, large;
-    for (auto& t : tasks) (t.n <= kCoopN ? small : large).push_back(t);
-    auto smem_for = [](int nmax) {
-      int np = (nmax + 1) & ~1;
-      return (size_t)np * sizeof(double) + (size_t)(np / 2) * 2 * sizeof(int) + (size_t)np * sizeof(int);
-    };
-    if (!small.empty()) {
+    std::vector<EighTask> large;
+    // matrices that fit in shared memory: one launch per size class
+    std::vector<EighTask> cls[3];
+    for (auto& t : tasks) {
+      if (t.n > kSmemN) large.push_back(t);
+      else cls[t.n <= 32 ? 0 : (t.n <= 64 ? 1 : 2)].push_back(t);
+    }
+    for (auto& c : cls) {
+      if (c.empty()) continue;
       int nmax = 1;
-      for (auto& t : small) nmax = std::max(nmax, t.n);
-      size_t smem = smem_for(nmax);
-      if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      for (auto& t : c) nmax = std::max(nmax, t.n);
+      const size_t smem = jacobi_smem_bytes(nmax);
+      CK(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       std::vector<size_t> off;
-      char* d = upload({{small.data(), small.size() * sizeof(EighTask)}}, off);
+      char* d = upload({{c.data(), c.size() * sizeof(EighTask)}}, off);
       Rec* rec = nullptr;
       if (profiling) {
         recs.push_back(Rec{ev(), ev(), 0.0, 3});
         rec = &recs.back();
         CK(cudaEventRecord(rec->a, st));
       }
-      jacobi_kernel<<<(unsigned)small.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
+      jacobi_smem_kernel<<<(unsigned)c.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
       if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       CK(cudaGetLastError());
@@ -913,7 +919,8 @@ class CudaBackend : public Backend {
     if (large.empty()) return;
     int nmax = 1;
     for (auto& t : large) nmax = std::max(nmax, t.n);
-    size_t smem = smem_for(nmax);
+    const int npm = (nmax + 1) & ~1;
+    size_t smem = (size_t)npm * sizeof(double) + (size_t)(npm / 2) * 2 * sizeof(int) + (size_t)npm * sizeof(int);
     if (smem > 200 * 1024) throw std::runtime_error("internal: eigensolver matrix too large");
     CK(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

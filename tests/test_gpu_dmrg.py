@@ -109,6 +109,24 @@ def test_split_precision_sweep_energy(pkg, prec, tol):
     assert abs(e32 - e64) < tol
 
 
+@pytest.mark.parametrize("prec", ["SPLIT_HPSI", "SPLIT_HPSI_TC"])
+def test_split_sweep_drift_from_same_state(pkg, prec):
+    """One sweep in split precision against the same sweep in float64, both
+    from the same converged float64 state (identical history in two
+    contexts): the energy drift is within 1e-6 Eh."""
+    h, L = W.cholesky_random(16, 64, seed=20250326)
+    out = []
+    for p in (pkg.FP64, getattr(pkg, prec)):
+        g = pkg.DMRG(h, chol=L, n_elec=16, D=64, precision=pkg.FP64)
+        for d in (16, 32, 64):
+            g.set_bond_dim(d)
+            g.sweep(1)
+        g.set_precision(p)
+        out.append(g.sweep(1)[0])
+        g.close()
+    assert abs(out[1] - out[0]) < 1e-6
+
+
 def test_bad_arguments_return_einval(pkg):
     h = np.zeros((4, 4))
     eri = np.zeros((4, 4, 4, 4))
