@@ -147,17 +147,19 @@ dmrg_status dmrg_block_dims(const dmrg_ctx* ctx, int* left, int* right);
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
 
 /* Device time (ms), algorithmic FLOPs and launch count of the GEMM kernels
- * since profiling was turned on.  which = 1: the H_eff psi launches,
- * which = 0: all other GEMM launches (renormalisation, complementary
- * operators, density matrices). */
+ * since profiling was turned on.  which = 1: the H_eff psi launches (with
+ * the operand splits of the tcgen05 path), 0: all other GEMM launches
+ * (renormalisation, complementary operators, density matrices), 2: the
+ * blocking placement kernel, 3: the eigensolver. */
 dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
                               int64_t* launches);
 
 /* Wall time (s) of the phases of the last sweep: [0] blocking (enlarged
  * operators), [1] H_eff psi task planning, [2] Davidson, [3] decimation,
  * [4] renormalisation, [5] wavefunction prediction; parts of [0]: [6] host
- * term lists, [7] host placement lists, [8] complementary-operator GEMMs.
- * t must hold 9 values. */
+ * term lists, [7] host placement lists, [8] complementary-operator GEMMs,
+ * [9] placement submission (grouping, upload, launch), [10] operator
+ * allocation.  t must hold 11 values. */
 dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* ctx, double* t);
 
 /* Device time of the last sweep in milliseconds, measured with CUDA events

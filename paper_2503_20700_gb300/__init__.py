@@ -206,12 +206,14 @@ class DMRG:
 
     def phases(self):
         """Wall seconds of the sweep phases (enlarge, plan, davidson, decimate,
-        renormalize, guess) and of three parts of enlarge (host term lists,
-        host placement lists, complementary-operator GEMMs)."""
-        t = np.zeros(9)
+        renormalize, guess) and of parts of enlarge (host term lists, host
+        placement lists, complementary-operator GEMMs, placement submission,
+        operator allocation)."""
+        t = np.zeros(11)
         _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_phases(self._ctx, _dp(t)))
         return dict(zip(["enlarge", "plan", "davidson", "decimate", "renormalize", "guess",
-                         "enlarge_terms_host", "enlarge_place_host", "enlarge_comp"], t.tolist()))
+                         "enlarge_terms_host", "enlarge_place_host", "enlarge_comp",
+                         "enlarge_place_run", "enlarge_alloc"], t.tolist()))
 
     def sweep_device_ms(self):
         ms = ctypes.c_double()

@@ -207,9 +207,11 @@ __global__ void precond_kernel(double* __restrict__ y, const double* __restrict_
 // columns) of A is updated in one pass as R_i X R_j^T, and the eigenvector
 // rows p, q of V are rotated together.  A pair is skipped when its
 // off-diagonal entry is negligible next to both diagonal entries, or below
-// 1e-20 ||A||_F; the iteration stops after a sweep without rotations, or
-// after kMaxSweeps sweeps.
-constexpr int kMaxSweeps = 40;
+// 1e-16 ||A||_F: the rounding noise of a GEMM-formed density matrix, whose
+// (near) null space would otherwise keep rotating noise for every sweep.
+// The iteration stops after a sweep without rotations, or after kMaxSweeps
+// sweeps.
+constexpr int kMaxSweeps = 30;
 
 // jacobi_smem_kernel (n <= kSmemN, one CTA per matrix): A (row stride n+1)
 // and the eigenvector rows V live in shared memory for the whole iteration,
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  const double floor_abs = 1e-20 * sqrt(red[0]);
+  const double floor_abs = 1e-16 * sqrt(red[0]);
   __syncthreads();
   for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __rest
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  const double floor_abs = 1e-20 * sqrt(red[0]);
+  const double floor_abs = 1e-16 * sqrt(red[0]);
   if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
   for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;

@@ -280,6 +280,8 @@ dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* c, double* t) {
   t[6] = s.t_enl_terms;
   t[7] = s.t_enl_place_host;
   t[8] = s.t_enl_comp;
+  t[9] = s.t_enl_place_run;
+  t[10] = s.t_enl_alloc;
   return DMRG_OK;
 }
 

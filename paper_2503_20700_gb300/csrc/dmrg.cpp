@@ -488,6 +488,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   std::vector<int> esites = bsites;
   if (b.left) esites.push_back(site);
   else esites.insert(esites.begin(), site);
+  const double t_alloc0 = now_s();
   std::vector<OpKey> keys;
   if (rdm_mode_) {
     // measurement blocks: the single spinors and, on normal blocks, the pairs
@@ -497,6 +498,7 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
     keys = op_keys(esites, n_, e->normal);
   }
   e->ops->allocate(keys);
+  stats_.t_enl_alloc += now_s() - t_alloc0;
 
   // ---- blocking terms, target by target
   Side bs;
@@ -874,7 +876,9 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
   pb.entries.reserve(total);
   for (auto& p : parts) pb.entries.insert(pb.entries.end(), p.begin(), p.end());
   stats_.t_enl_place_host += now_s() - t_host;
+  const double t_run = now_s();
   pb.run(be_);
+  stats_.t_enl_place_run += now_s() - t_run;
 }
 
 // ============================================================ complementary from normal

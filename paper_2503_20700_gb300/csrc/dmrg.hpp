@@ -157,7 +157,8 @@ struct SweepStats {
   double t_enlarge = 0.0, t_plan = 0.0, t_davidson = 0.0, t_decimate = 0.0, t_renorm = 0.0,
          t_guess = 0.0;
   // inside enlarge: host term lists, host placement lists, complementary GEMMs
-  double t_enl_terms = 0.0, t_enl_place_host = 0.0, t_enl_comp = 0.0;
+  double t_enl_terms = 0.0, t_enl_place_host = 0.0, t_enl_comp = 0.0, t_enl_place_run = 0.0,
+         t_enl_alloc = 0.0;
 };
 
 class Engine {
