@@ -55,7 +55,8 @@ typedef enum {
                            and complementary-operator GEMMs in float64          */
   DMRG_SPLIT_HPSI_TC = 4 /* as DMRG_SPLIT_HPSI, with the H_eff psi split products
                            issued on the tcgen05 tensor cores (TMEM
-                           accumulators, 128 x 64 sigma tiles); a bounded wait
+                           accumulators, 128 x 256 sigma tiles, operands
+                           pre-split into TF32 hi/lo planes); a bounded wait
                            that runs out returns DMRG_ETIMEOUT              */
 } dmrg_precision;
 
@@ -99,7 +100,9 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
  * dmrg_sweep -- run n_sweeps full sweeps (L->R over bonds 0..n-3, then R->L
  * over bonds n-2..1; Sec. II.B two-site DMRG).  *energy receives the Davidson
  * eigenvalue of the last bond plus e_core, *max_trunc_err the largest
- * discarded weight of the last sweep.  Either output may be NULL.
+ * discarded weight of the last sweep.  Either output may be NULL.  With a
+ * split precision the reported energy is the float64 Rayleigh quotient of
+ * the last bond's eigenvector (one float64 H_eff psi).
  */
 dmrg_status dmrg_sweep(dmrg_ctx* ctx, int n_sweeps, double* energy, double* max_trunc_err);
 

@@ -798,10 +798,18 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
   for (auto& c : e.comps) by[c.esec].push_back(&c);
   const bool L = e.left;
   const double t_host = now_s();
-  // storage of every term resolved serially (layouts are created on demand)
+  // Every destination sub-block of a target operator has a dense index
+  // (layout block, bra component, ket component); the segments of one
+  // target are grouped by it with a counting sort, in term order.
+  struct LayoutIndex {
+    std::vector<size_t> base;  // per layout block
+    size_t total = 0;
+  };
+  std::map<const Layout*, LayoutIndex> lidx;
   struct TermCtx {
     double* dst = nullptr;
     const Layout* TL = nullptr;
+    const LayoutIndex* LI = nullptr;
     ResolvedOperand rop;
   };
   std::vector<TermCtx> ctx(terms.size());
@@ -810,74 +818,140 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     ctx[i].dst = eo.get(tk);
     if (!ctx[i].dst) continue;
     ctx[i].TL = &eo.layout(kind_dn(tk.kind), tk.k2);
+    auto it = lidx.find(ctx[i].TL);
+    if (it == lidx.end()) {
+      LayoutIndex li;
+      for (auto& blk : ctx[i].TL->blk) {
+        li.base.push_back(li.total);
+        li.total += by[blk.bra].size() * by[blk.ket].size();
+      }
+      it = lidx.emplace(ctx[i].TL, std::move(li)).first;
+    }
+    ctx[i].LI = &it->second;
     const Operand& bop = L ? t.x : t.y;
     if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
     ctx[i].rop = resolve(bo, tmp, bop);
   }
+  struct Entry {
+    uint32_t li;
+    double* d;
+    int rows, cols, ld;
+    PlaceSeg seg;
+  };
   // placement segments of a range of terms (pure host arithmetic)
-  auto generate = [&](size_t t0, size_t t1, std::vector<PlaceBuilder::Entry>& out) {
+  auto generate = [&](size_t t0, size_t t1, std::vector<Entry>& out, std::vector<size_t>& ends) {
     for (size_t i = t0; i < t1; ++i) {
       const TermCtx& cx = ctx[i];
-      if (!cx.dst || !cx.rop.ok) continue;
-      const Term& t = terms[i].second;
-      const Operand& bop = L ? t.x : t.y;   // operand on the block part
-      const Operand& sop = L ? t.y : t.x;   // operand on the site part
-      for (auto& blk : cx.TL->blk) {
-        int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
-        for (const EnlComp* cp : by[blk.bra])
-          for (const EnlComp* c : by[blk.ket]) {
-            double sv = site_val(sop, cp->site, c->site);
-            if (sv == 0.0) continue;
-            SrcBlock src = block_of(bb, cx.rop, bop, cp->bsec, c->bsec);
-            if (!src.ok) continue;
-            int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
-            int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
-            double tp;
-            int nleft, pright;
-            if (L) {
-              tp = tensor_product_coef(jb_p, jb, bop.k2, js_p, js, sop.k2, Jp, J, t.k2);
-              nleft = bb.sec[c->bsec].n;
-              pright = sop.par;
-            } else {
-              tp = tensor_product_coef(js_p, js, sop.k2, jb_p, jb, bop.k2, Jp, J, t.k2);
-              nleft = kSiteN[c->site];
-              pright = bop.par;
+      if (cx.dst && cx.rop.ok) {
+        const Term& t = terms[i].second;
+        const Operand& bop = L ? t.x : t.y;   // operand on the block part
+        const Operand& sop = L ? t.y : t.x;   // operand on the site part
+        for (size_t bi = 0; bi < cx.TL->blk.size(); ++bi) {
+          const auto& blk = cx.TL->blk[bi];
+          int Jp = eb.sec[blk.bra].j, J = eb.sec[blk.ket].j;
+          const auto& cps = by[blk.bra];
+          const auto& cs = by[blk.ket];
+          for (size_t ia = 0; ia < cps.size(); ++ia)
+            for (size_t ic = 0; ic < cs.size(); ++ic) {
+              const EnlComp* cp = cps[ia];
+              const EnlComp* c = cs[ic];
+              double sv = site_val(sop, cp->site, c->site);
+              if (sv == 0.0) continue;
+              SrcBlock src = block_of(bb, cx.rop, bop, cp->bsec, c->bsec);
+              if (!src.ok) continue;
+              int jb_p = bb.sec[cp->bsec].j, jb = bb.sec[c->bsec].j;
+              int js_p = kSiteJ[cp->site], js = kSiteJ[c->site];
+              double tp;
+              int nleft, pright;
+              if (L) {
+                tp = tensor_product_coef(jb_p, jb, bop.k2, js_p, js, sop.k2, Jp, J, t.k2);
+                nleft = bb.sec[c->bsec].n;
+                pright = sop.par;
+              } else {
+                tp = tensor_product_coef(js_p, js, sop.k2, jb_p, jb, bop.k2, Jp, J, t.k2);
+                nleft = kSiteN[c->site];
+                pright = bop.par;
+              }
+              if (tp == 0.0) continue;
+              double sign = ((pright & nleft) & 1) ? -1.0 : 1.0;
+              double alpha = t.coef * tp * sv * sign * src.coef;
+              int rows = bb.sec[cp->bsec].dim, cols = bb.sec[c->bsec].dim;
+              if (alpha == 0.0 || rows == 0 || cols == 0) continue;
+              double* d = cx.dst + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
+              out.push_back({(uint32_t)(cx.LI->base[bi] + ia * cs.size() + ic), d, rows, cols, blk.cols,
+                             PlaceSeg{src.ptr, src.ld, src.trans, alpha}});
             }
-            if (tp == 0.0) continue;
-            double sign = ((pright & nleft) & 1) ? -1.0 : 1.0;
-            double alpha = t.coef * tp * sv * sign * src.coef;
-            int rows = bb.sec[cp->bsec].dim, cols = bb.sec[c->bsec].dim;
-            if (alpha == 0.0 || rows == 0 || cols == 0) continue;
-            double* d = cx.dst + blk.off + (size_t)cp->eoff * blk.cols + c->eoff;
-            out.push_back({d, rows, cols, blk.cols, PlaceSeg{src.ptr, src.ld, src.trans, alpha}});
-          }
+        }
       }
+      ends.push_back(out.size());
     }
   };
-  // host threads over contiguous term ranges, concatenated in term order so
-  // the placement (and its summation order) does not depend on the split
+  // host threads over contiguous term ranges
   unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   if (terms.size() < 256) nth = 1;
-  std::vector<std::vector<PlaceBuilder::Entry>> parts(nth);
-  if (nth == 1) {
-    generate(0, terms.size(), parts[0]);
-  } else {
-    std::vector<std::thread> th;
+  std::vector<std::vector<Entry>> parts(nth);
+  std::vector<std::vector<size_t>> part_ends(nth);
+  std::vector<size_t> t_begin(nth + 1, terms.size());
+  {
     const size_t per = (terms.size() + nth - 1) / nth;
-    for (unsigned w = 0; w < nth; ++w) {
-      size_t t0 = std::min(terms.size(), w * per), t1 = std::min(terms.size(), t0 + per);
-      th.emplace_back([&, t0, t1, w] { generate(t0, t1, parts[w]); });
+    for (unsigned w = 0; w < nth; ++w) t_begin[w] = std::min(terms.size(), w * per);
+    if (nth == 1) {
+      generate(0, terms.size(), parts[0], part_ends[0]);
+    } else {
+      std::vector<std::thread> th;
+      for (unsigned w = 0; w < nth; ++w)
+        th.emplace_back([&, w] { generate(t_begin[w], t_begin[w + 1], parts[w], part_ends[w]); });
+      for (auto& x : th) x.join();
     }
-    for (auto& x : th) x.join();
   }
-  PlaceBuilder pb;
-  size_t total = 0;
-  for (auto& p : parts) total += p.size();
-  pb.entries.reserve(total);
-  for (auto& p : parts) pb.entries.insert(pb.entries.end(), p.begin(), p.end());
+  // entry range of every term
+  std::vector<std::pair<const Entry*, const Entry*>> range(terms.size(), {nullptr, nullptr});
+  for (unsigned w = 0; w < nth; ++w) {
+    size_t prev = 0;
+    for (size_t k = 0; k < part_ends[w].size(); ++k) {
+      const Entry* base = parts[w].data();
+      range[t_begin[w] + k] = {base + prev, base + part_ends[w][k]};
+      prev = part_ends[w][k];
+    }
+  }
+  // terms of each target, in term order
+  std::map<OpKey, std::vector<size_t>> by_target;
+  for (size_t i = 0; i < terms.size(); ++i)
+    if (ctx[i].dst && range[i].first != range[i].second) by_target[terms[i].first].push_back(i);
+  std::vector<PlaceGroup> groups;
+  std::vector<PlaceSeg> segs;
+  std::vector<uint32_t> count;
+  std::vector<const Entry*> order;
+  for (auto& [tk, tlist] : by_target) {
+    const LayoutIndex& LI = *ctx[tlist.front()].LI;
+    count.assign(LI.total + 1, 0);
+    size_t ne = 0;
+    for (size_t i : tlist)
+      for (const Entry* x = range[i].first; x != range[i].second; ++x) {
+        ++count[x->li + 1];
+        ++ne;
+      }
+    for (size_t k = 1; k <= LI.total; ++k) count[k] += count[k - 1];
+    order.assign(ne, nullptr);
+    for (size_t i : tlist)
+      for (const Entry* x = range[i].first; x != range[i].second; ++x) order[count[x->li]++] = x;
+    for (size_t k = 0; k < ne;) {
+      size_t j = k;
+      PlaceGroup pg;
+      pg.dst = order[k]->d;
+      pg.rows = order[k]->rows;
+      pg.cols = order[k]->cols;
+      pg.ld = order[k]->ld;
+      pg.seg_begin = (int)segs.size();
+      while (j < ne && order[j]->li == order[k]->li) segs.push_back(order[j++]->seg);
+      pg.seg_count = (int)(j - k);
+      groups.push_back(pg);
+      k = j;
+    }
+  }
   stats_.t_enl_place_host += now_s() - t_host;
   const double t_run = now_s();
-  pb.run(be_);
+  if (!groups.empty()) be_->place(groups, segs);
   stats_.t_enl_place_run += now_s() - t_run;
 }
 

@@ -142,8 +142,10 @@ __device__ __forceinline__ void cursor_item(Cursor& c, const TcItem& it, int c0,
 }
 __device__ __forceinline__ int chunk_kspan(const Cursor& c) { return min(JC, roundup32(c.jc_end - c.jc)); }
 // advance to the next k-block; false at the end of the task
-__device__ __forceinline__ bool cursor_next(Cursor& c, const TcItem* __restrict__ items, int it_end, int c0, int N) {
-  const TcItem& it = items[c.ii];
+// `it` is the cursor's current item (kept in registers): reloaded from the
+// item list only when the cursor moves to the next item
+__device__ __forceinline__ bool cursor_next(Cursor& c, TcItem& it, const TcItem* __restrict__ items, int it_end,
+                                            int c0, int N) {
   if (c.stage == 1) {
     c.k0 += KB;
     if (c.k0 < roundup32(it.ka)) return true;
@@ -165,7 +167,8 @@ __device__ __forceinline__ bool cursor_next(Cursor& c, const TcItem* __restrict_
     return true;
   }
   if (++c.ii >= it_end) return false;
-  cursor_item(c, items[c.ii], c0, N);
+  it = items[c.ii];
+  cursor_item(c, it, c0, N);
   return true;
 }
 
@@ -201,9 +204,8 @@ __global__ void __launch_bounds__(128, 1)
   const int N1 = min(N, HALF), N2 = N - N1;  // MMA widths of the two column halves
   const uint32_t id1 = idesc_tf32(TM, JC), id2a = idesc_tf32(TM, N1), id2b = idesc_tf32(TM, N2 > 0 ? N2 : 16);
 
-  // issue the operand copies of the block at cursor c into slot s
-  auto produce = [&](const Cursor& c, int s) {
-    const TcItem& it = items[c.ii];
+  // issue the operand copies of the block at cursor c (item it) into slot s
+  auto produce = [&](const Cursor& c, const TcItem& it, int s) {
     const uint32_t sl = sbase + OFF_SLOT + s * SLOT;
     if (c.stage == 1) {
       load_tile(sl, sl + 16384, it.A, tk.r0, TM, bk.m, c.k0, tid);
@@ -263,20 +265,23 @@ __global__ void __launch_bounds__(128, 1)
 
   Cursor cur;
   cur.ii = tk.it_begin;
-  cursor_item(cur, items[cur.ii], tk.c0, N);
+  TcItem it_cur = items[cur.ii];
+  cursor_item(cur, it_cur, tk.c0, N);
   // blocks b+1 and b+2 (n1, n2) are prefetched ahead of block b
   Cursor n1 = cur, n2;
-  bool has1 = cursor_next(n1, items, it_end, tk.c0, N), has2 = false;
+  TcItem it_n1 = it_cur, it_n2;
+  bool has1 = cursor_next(n1, it_n1, items, it_end, tk.c0, N), has2 = false;
   n2 = n1;
-  if (has1) has2 = cursor_next(n2, items, it_end, tk.c0, N);
+  it_n2 = it_n1;
+  if (has1) has2 = cursor_next(n2, it_n2, items, it_end, tk.c0, N);
   int b = 0;
-  produce(cur, 0);
-  if (has1) produce(n1, 1);
+  produce(cur, it_cur, 0);
+  if (has1) produce(n1, it_n1, 1);
   for (;;) {
     // prefetch block b+2 into the slot of block b-1 once its MMAs are done
     if (has2) {
       wait_block(b - 1);
-      produce(n2, (b + 2) % NSLOT);
+      produce(n2, it_n2, (b + 2) % NSLOT);
       asm volatile("cp.async.wait_group 2;");
     } else if (has1) {
       asm volatile("cp.async.wait_group 1;");
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (abort_flag) break;
-    const TcItem& it = items[cur.ii];
+    const TcItem& it = it_cur;
     if (cur.stage == 2 && cur.k0 == 0 && cur.half == 0) {
       // X = alpha X' (or alpha P for an identity left operand) -> hi/lo planes;
       // the commit of block b-1 covers every earlier MMA (stage 1 of this
@@ -377,10 +382,12 @@ __global__ void __launch_bounds__(128, 1)
       __syncthreads();
     }
     cur = n1;
+    it_cur = it_n1;
     n1 = n2;
+    it_n1 = it_n2;
     has1 = has2;
     if (has1) {
-      has2 = cursor_next(n2, items, it_end, tk.c0, N);
+      has2 = cursor_next(n2, it_n2, items, it_end, tk.c0, N);
     } else {
       has2 = false;
     }
