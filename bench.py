@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload cas40|casN|pentacene|naphthalene] [--D 256]
-                    [--precision split|split-tc|split-all|fp64]
+                    [--precision split-tc|split|split-all|fp64]
 
 A step is one full two-site DMRG sweep (L->R then R->L: blocking, Davidson
 with H_eff psi, decimation, renormalisation) over the workload.  The warm-up
@@ -284,9 +284,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cas40")
     ap.add_argument("--D", type=int, default=256)
-    ap.add_argument("--precision", default="split", choices=["split", "split-tc", "split-all", "fp64"],
-                    help="split: 3xTF32 in H_eff psi, renormalisation in FP64; "
-                         "split-all: 3xTF32 also in renormalisation; fp64: all FP64")
+    ap.add_argument("--precision", default="split-tc", choices=["split", "split-tc", "split-all", "fp64"],
+                    help="split-tc: 3xTF32 H_eff psi on tcgen05, renormalisation in FP64; "
+                         "split: the same products on mma.sync; split-all: mma.sync 3xTF32 also in "
+                         "renormalisation; fp64: all FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-7)

@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
       for (int i = threadIdx.x; i < h; i += blockDim.x) {
-        int p = perm[i], q = perm[np - 1 - i];
+        // round-robin pairs in closed form: (round, M) and (round +- i) mod M
+        const int M = np - 1;
+        int p = i == 0 ? round : (round + i) % M, q = i == 0 ? M : (round - i + M) % M;
         if (p > q) { int t = p; p = q; q = t; }
         pp[i] = p;
         qq[i] = q;
@@ -309,12 +311,6 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
         double vp = v[p * n + k], vq = v[q * n + k];
         v[p * n + k] = c * vp - s * vq;
         v[q * n + k] = s * vp + c * vq;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int last = perm[np - 1];
-        for (int i = np - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
       }
       __syncthreads();
     }
@@ -436,7 +432,9 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __rest
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
       for (int i = threadIdx.x; i < h; i += blockDim.x) {
-        int p = perm[i], q = perm[np - 1 - i];
+        // round-robin pairs in closed form: (round, M) and (round +- i) mod M
+        const int M = np - 1;
+        int p = i == 0 ? round : (round + i) % M, q = i == 0 ? M : (round - i + M) % M;
         if (p > q) { int t = p; p = q; q = t; }
         pp[i] = p;
         qq[i] = q;
@@ -488,12 +486,6 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __rest
         v[(size_t)q * n + k] = s * vp + c * vq;
       }
       if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
-      if (threadIdx.x == 0) {
-        int last = perm[np - 1];
-        for (int i = np - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
-      }
-      __syncthreads();
     }
     if (nrot == 0) break;
     __syncthreads();
