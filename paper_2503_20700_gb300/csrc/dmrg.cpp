@@ -1255,46 +1255,81 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   std::vector<std::vector<HpsiItem>> per(P.blk.size());
   std::vector<std::pair<int, HpsiItem>> diag_items;
   plan.flops = 0.0;
-  std::vector<std::pair<int, SrcBlock>> lr, rr;
-  for (auto& t : terms) {
-    // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
-    int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
-    const ResolvedOperand rx = resolve(lo, nullptr, t.x), ry = resolve(ro, nullptr, t.y);
-    if (!rx.ok || !ry.ok) continue;
-    for (auto& kb : P.blk) {
-      reach(lo.basis, rx, t.x, kb.a, lr);
-      if (lr.empty()) continue;
-      reach(ro.basis, ry, t.y, kb.b, rr);
-      if (rr.empty()) continue;
-      const Sector& sa = lo.basis.sec[kb.a];
-      const Sector& sb = ro.basis.sec[kb.b];
-      double sign = ((t.y.par & sa.n) & 1) ? -1.0 : 1.0;
-      for (auto& [ap, xs] : lr)
-        for (auto& [bp, ys] : rr) {
-          int pi = P.find(ap, bp);
-          if (pi < 0) continue;
-          const Sector& sap = lo.basis.sec[ap];
-          const Sector& sbp = ro.basis.sec[bp];
-          double hc = hpsi_coef(sap.j, sbp.j, sa.j, sb.j, kop, two_s_);
-          if (hc == 0.0) continue;
-          HpsiItem it;
-          it.A = (t.x.t == Operand::ID) ? nullptr : xs.ptr;
-          it.lda = xs.ld;
-          it.transA = xs.trans;
-          it.P = plan.in + kb.off;
-          it.ldp = sb.dim;
-          it.B = (t.y.t == Operand::ID) ? nullptr : ys.ptr;
-          it.ldb = ys.ld;
-          it.transB = ys.trans;
-          it.ka = sa.dim;
-          it.kb = sb.dim;
-          it.alpha = t.coef * hc * sign * xs.coef * ys.coef;
-          per[pi].push_back(it);
-          if (it.A) plan.flops += 2.0 * sap.dim * sa.dim * sb.dim;
-          if (it.B) plan.flops += 2.0 * sap.dim * sbp.dim * sb.dim;
-          if (ap == kb.a && bp == kb.b) diag_items.push_back({pi, it});
-        }
+  // operands resolved serially (layouts are created on demand), items of
+  // contiguous term ranges generated by host threads and merged in term
+  // order, so the item order (and the summation order) does not depend on
+  // the number of threads
+  std::vector<std::pair<ResolvedOperand, ResolvedOperand>> rop(terms.size());
+  for (size_t i = 0; i < terms.size(); ++i)
+    rop[i] = {resolve(lo, nullptr, terms[i].x), resolve(ro, nullptr, terms[i].y)};
+  struct Gen {
+    std::vector<std::pair<int, HpsiItem>> items;  // (sigma block, item) in term order
+    std::vector<std::pair<int, HpsiItem>> diag;
+    double flops = 0.0;
+  };
+  auto generate = [&](size_t t0, size_t t1, Gen& out) {
+    std::vector<std::pair<int, SrcBlock>> lr, rr;
+    for (size_t ti = t0; ti < t1; ++ti) {
+      const Term& t = terms[ti];
+      // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
+      int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
+      const ResolvedOperand& rx = rop[ti].first;
+      const ResolvedOperand& ry = rop[ti].second;
+      if (!rx.ok || !ry.ok) continue;
+      for (auto& kb : P.blk) {
+        reach(lo.basis, rx, t.x, kb.a, lr);
+        if (lr.empty()) continue;
+        reach(ro.basis, ry, t.y, kb.b, rr);
+        if (rr.empty()) continue;
+        const Sector& sa = lo.basis.sec[kb.a];
+        const Sector& sb = ro.basis.sec[kb.b];
+        double sign = ((t.y.par & sa.n) & 1) ? -1.0 : 1.0;
+        for (auto& [ap, xs] : lr)
+          for (auto& [bp, ys] : rr) {
+            int pi = P.find(ap, bp);
+            if (pi < 0) continue;
+            const Sector& sap = lo.basis.sec[ap];
+            const Sector& sbp = ro.basis.sec[bp];
+            double hc = hpsi_coef(sap.j, sbp.j, sa.j, sb.j, kop, two_s_);
+            if (hc == 0.0) continue;
+            HpsiItem it;
+            it.A = (t.x.t == Operand::ID) ? nullptr : xs.ptr;
+            it.lda = xs.ld;
+            it.transA = xs.trans;
+            it.P = plan.in + kb.off;
+            it.ldp = sb.dim;
+            it.B = (t.y.t == Operand::ID) ? nullptr : ys.ptr;
+            it.ldb = ys.ld;
+            it.transB = ys.trans;
+            it.ka = sa.dim;
+            it.kb = sb.dim;
+            it.alpha = t.coef * hc * sign * xs.coef * ys.coef;
+            out.items.push_back({pi, it});
+            if (it.A) out.flops += 2.0 * sap.dim * sa.dim * sb.dim;
+            if (it.B) out.flops += 2.0 * sap.dim * sbp.dim * sb.dim;
+            if (ap == kb.a && bp == kb.b) out.diag.push_back({pi, it});
+          }
+      }
     }
+  };
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (terms.size() < 64) nth = 1;
+  std::vector<Gen> gens(nth);
+  if (nth == 1) {
+    generate(0, terms.size(), gens[0]);
+  } else {
+    std::vector<std::thread> th;
+    const size_t per_t = (terms.size() + nth - 1) / nth;
+    for (unsigned w = 0; w < nth; ++w) {
+      size_t t0 = std::min(terms.size(), w * per_t), t1 = std::min(terms.size(), t0 + per_t);
+      th.emplace_back([&, t0, t1, w] { generate(t0, t1, gens[w]); });
+    }
+    for (auto& x : th) x.join();
+  }
+  for (auto& g : gens) {
+    for (auto& [pi, it] : g.items) per[pi].push_back(it);
+    diag_items.insert(diag_items.end(), g.diag.begin(), g.diag.end());
+    plan.flops += g.flops;
   }
   if (opt_.verbose >= 2) {
     // shape statistics of the contraction, weighted by flops: the smallest
