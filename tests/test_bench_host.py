@@ -1,0 +1,71 @@
+"""Host logic of bench.py on the CPU: the warm-up ramp, the synthetic sector-
+block problem of the kernel-only mode, and the N > 1 replica path (max of
+the device times and sum of the FLOPs over ranks) on two gloo ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_ramp_ends_at_target_and_doubles():
+    assert bench.ramp(256, 3) == [64, 128, 256]
+    assert bench.ramp(2048, 4) == [512, 1024, 2048, 2048]
+    assert bench.ramp(16, 3) == [16, 16, 16]
+
+
+def test_hpsi_problem_offsets_and_flops():
+    A, P, B, clen, blocks, items, flops = bench.hpsi_problem(3, 4, 10, 30, 5)
+    fl = 0.0
+    for (c_off, m, n, ldc, ib, cnt) in blocks:
+        assert ldc == n and c_off + m * n <= clen
+        for it in items[ib:ib + cnt]:
+            a_off, p_off, b_off, lda, ldp, ldb, ta, tb, ka, kb, a_id, b_id, alpha = it
+            assert p_off + ka * kb <= P.size and ldp == kb
+            if a_id:
+                assert ka == m
+            else:
+                assert a_off + m * ka <= A.size and lda == (m if ta else ka)
+                fl += 2.0 * m * ka * kb
+            assert not b_id and b_off + n * kb <= B.size and ldb == (n if tb else kb)
+            fl += 2.0 * m * n * kb
+    assert fl == flops
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _replica(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    r, w, dist = bench.dist_init(world)
+    assert (r, w) == (rank, world)
+    # rank r "took" 1 + r seconds and did 10 * (r + 1) FLOPs
+    t = bench.allmax(dist, 1.0 + rank)
+    f = bench.allsum(dist, 10.0 * (rank + 1))
+    bench.barrier(dist)
+    out.put((rank, t, f))
+    dist.destroy_process_group()
+
+
+def test_replicas_take_max_time_and_sum_flops_over_two_gloo_ranks():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_replica, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 2.0, 30.0), (1, 2.0, 30.0)]
