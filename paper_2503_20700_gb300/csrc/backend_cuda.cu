@@ -216,23 +216,21 @@ constexpr int kMaxSweeps = 30;
 // jacobi_smem_kernel (n <= kSmemN, one CTA per matrix): A (row stride n+1)
 // and the eigenvector rows V live in shared memory for the whole iteration,
 // so every round's loads and stores stay on chip.
-constexpr int kSmemN = 112;   // A and V in shared memory
-constexpr int kSmemAN = 160;  // A in shared memory, V rows in global memory
-__host__ __device__ constexpr size_t jacobi_smem_bytes(int n, bool v_shared) {
-  return ((size_t)n * (n + 1) + (v_shared ? (size_t)n * n : 0) + (size_t)((n + 1) & ~1)) * sizeof(double) +
+constexpr int kSmemN = 112;  // A and V in shared memory (larger: cooperative groups, which measured faster)
+__host__ __device__ constexpr size_t jacobi_smem_bytes(int n) {
+  return ((size_t)n * (n + 1) + (size_t)n * n + (size_t)((n + 1) & ~1)) * sizeof(double) +
          (size_t)((n + 1) & ~1) * 2 * sizeof(int) + 64;
 }
 
-template <bool VShared>
 __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __restrict__ tasks) {
   const EighTask tk = tasks[blockIdx.x];
   const int n = tk.n;
   const int lda = n + 1;
   const int np = (n + 1) & ~1, h = np / 2;
   extern __shared__ double sm[];
-  double* a = sm;                                            // n x (n+1)
-  double* v = VShared ? a + (size_t)n * lda : tk.V;          // n x n, row p = eigenvector p
-  double* cs = (VShared ? a + (size_t)n * lda + (size_t)n * n : a + (size_t)n * lda);  // h
+  double* a = sm;                        // n x (n+1)
+  double* v = a + (size_t)n * lda;       // n x n, row p = eigenvector p
+  double* cs = v + (size_t)n * n;        // h
   double* sn = cs + h;                   // h
   int* pp = (int*)(sn + h);
   int* qq = pp + h;
@@ -332,13 +330,6 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
   }
   __syncthreads();
   for (int r = threadIdx.x; r < n; r += blockDim.x) tk.w[r] = a[perm[r] * lda + perm[r]];
-  if (!VShared) {
-    // the working rows live in V itself: move them through the (now free) input matrix
-    double* tmp = const_cast<double*>(tk.A);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) tmp[e] = v[e];
-    __syncthreads();
-    v = tmp;
-  }
   // eigenvector rows in descending order, largest-magnitude component positive
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const double* src = v + (size_t)perm[r] * n;
@@ -890,27 +881,22 @@ class CudaBackend : public Backend {
   }
   // Matrices up to kCoopN use one CTA each; larger ones a cooperative group
   // of g CTAs (g grows with n, the groups of one launch fit co-resident).
-  static constexpr int kCoopN = kSmemAN;
+  static constexpr int kCoopN = kSmemN;
   void eigh(const std::vector<EighTask>& tasks) override {
     if (tasks.empty()) return;
     std::vector<EighTask> large;
     // matrices that fit in shared memory: one launch per size class
-    std::vector<EighTask> cls[4];
+    std::vector<EighTask> cls[3];
     for (auto& t : tasks) {
-      if (t.n > kSmemAN) large.push_back(t);
-      else cls[t.n <= 32 ? 0 : (t.n <= 64 ? 1 : (t.n <= kSmemN ? 2 : 3))].push_back(t);
+      if (t.n > kSmemN) large.push_back(t);
+      else cls[t.n <= 32 ? 0 : (t.n <= 64 ? 1 : 2)].push_back(t);
     }
-    for (int ci = 0; ci < 4; ++ci) {
-      auto& c = cls[ci];
+    for (auto& c : cls) {
       if (c.empty()) continue;
       int nmax = 1;
       for (auto& t : c) nmax = std::max(nmax, t.n);
-      const bool vs = ci < 3;
-      const size_t smem = jacobi_smem_bytes(nmax, vs);
-      if (vs)
-        CK(cudaFuncSetAttribute(jacobi_smem_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      else
-        CK(cudaFuncSetAttribute(jacobi_smem_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const size_t smem = jacobi_smem_bytes(nmax);
+      CK(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       std::vector<size_t> off;
       char* d = upload({{c.data(), c.size() * sizeof(EighTask)}}, off);
       Rec* rec = nullptr;
@@ -919,10 +905,7 @@ class CudaBackend : public Backend {
         rec = &recs.back();
         CK(cudaEventRecord(rec->a, st));
       }
-      if (vs)
-        jacobi_smem_kernel<true><<<(unsigned)c.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
-      else
-        jacobi_smem_kernel<false><<<(unsigned)c.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
+      jacobi_smem_kernel<<<(unsigned)c.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
       if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       CK(cudaGetLastError());
