@@ -74,6 +74,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+  // a short spin first (the MMAs of a k-block take about a microsecond), then
+  // probes with a sleep between them, bounded by kWaitNs of wall clock
+  for (int i = 0; i < 128; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+    if (done) return true;
+  }
   const unsigned long long t0 = global_ns();
   for (;;) {
     uint32_t done;
@@ -302,18 +312,26 @@ __global__ void __launch_bounds__(128, 1)
       float* xhp = (float*)(smraw + OFF_XH);
       float* xlp = (float*)(smraw + OFF_XL);
       if (it.A.hi != nullptr) {
+        // the four 16-column loads of the row are issued before one wait
+        uint32_t q[64];
 #pragma unroll
-        for (int c0 = 0; c0 < JC; c0 += 16) {
-          float v[16];
-          tmem_ld16(tX + lane_base + c0, v);
+        for (int c4 = 0; c4 < 4; ++c4)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(q[16 * c4 + 0]), "=r"(q[16 * c4 + 1]), "=r"(q[16 * c4 + 2]), "=r"(q[16 * c4 + 3]),
+                "=r"(q[16 * c4 + 4]), "=r"(q[16 * c4 + 5]), "=r"(q[16 * c4 + 6]), "=r"(q[16 * c4 + 7]),
+                "=r"(q[16 * c4 + 8]), "=r"(q[16 * c4 + 9]), "=r"(q[16 * c4 + 10]), "=r"(q[16 * c4 + 11]),
+                "=r"(q[16 * c4 + 12]), "=r"(q[16 * c4 + 13]), "=r"(q[16 * c4 + 14]), "=r"(q[16 * c4 + 15])
+              : "r"(tX + lane_base + 16 * c4));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const float al = (float)it.alpha;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float x = (float)it.alpha * v[j];
-            uint32_t h = tf32(x);
-            uint32_t o = word_off(r, c0 + j, SBO64) >> 2;
-            xhp[o] = __uint_as_float(h);
-            xlp[o] = __uint_as_float(tf32(x - __uint_as_float(h)));
-          }
+        for (int j = 0; j < JC; ++j) {
+          float x = al * __uint_as_float(q[j]);
+          uint32_t h = tf32(x);
+          uint32_t o = word_off(r, j, SBO64) >> 2;
+          xhp[o] = __uint_as_float(h);
+          xlp[o] = __uint_as_float(tf32(x - __uint_as_float(h)));
         }
       } else {
         const int gr = tk.r0 + r;
