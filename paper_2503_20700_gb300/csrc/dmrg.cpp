@@ -1443,7 +1443,6 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   gd.run(be_, Precision::FP64);
 }
 
-size_t Engine::x_budget_elems() const { return 0; }
 
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));

@@ -241,7 +241,6 @@ class Engine {
   void build_initial_right();
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);
-  size_t x_budget_elems() const;
   double davidson(struct HPsiPlan& plan, double* psi, int* iters);
   std::unique_ptr<SavedU> decimate(Block& enl, const struct HPsiPlan& plan, const double* psi,
                                    bool left, double* trunc);
