@@ -153,7 +153,8 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
  * since profiling was turned on.  which = 1: the H_eff psi launches (with
  * the operand splits of the tcgen05 path), 0: all other GEMM launches
  * (renormalisation, complementary operators, density matrices), 2: the
- * blocking placement kernel, 3: the eigensolver. */
+ * blocking placement kernel, 3: the shared-memory eigensolver, 4: the
+ * cooperative eigensolver (sectors above 112). */
 dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
                               int64_t* launches);
 
@@ -162,7 +163,9 @@ dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flop
  * [4] renormalisation, [5] wavefunction prediction; parts of [0]: [6] host
  * term lists, [7] host placement lists, [8] complementary-operator GEMMs,
  * [9] placement submission (grouping, upload, launch), [10] operator
- * allocation.  t must hold 11 values. */
+ * allocation; parts of [1]: [11] host item lists, [12] task lists,
+ * [13] uploads and operand splits, [14] preconditioner diagonal.
+ * t must hold 15 values. */
 dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* ctx, double* t);
 
 /* Device time of the last sweep in milliseconds, measured with CUDA events

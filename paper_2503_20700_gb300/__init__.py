@@ -209,11 +209,12 @@ class DMRG:
         renormalize, guess) and of parts of enlarge (host term lists, host
         placement lists, complementary-operator GEMMs, placement submission,
         operator allocation)."""
-        t = np.zeros(11)
+        t = np.zeros(15)
         _check(self._lib, self._ctx, self._lib.dmrg_last_sweep_phases(self._ctx, _dp(t)))
         return dict(zip(["enlarge", "plan", "davidson", "decimate", "renormalize", "guess",
                          "enlarge_terms_host", "enlarge_place_host", "enlarge_comp",
-                         "enlarge_place_run", "enlarge_alloc"], t.tolist()))
+                         "enlarge_place_run", "enlarge_alloc", "plan_items", "plan_tasks",
+                         "plan_upload", "plan_diag"], t.tolist()))
 
     def sweep_device_ms(self):
         ms = ctypes.c_double()

@@ -552,9 +552,10 @@ class CudaBackend : public Backend {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   // categories: 0 GEMMs, 1 H_eff psi (with its operand splits), 2 blocking
-  // placement, 3 eigensolver
-  double acc_ms[4] = {0, 0, 0, 0}, acc_flops[4] = {0, 0, 0, 0};
-  long acc_launch[4] = {0, 0, 0, 0};
+  // placement, 3 eigensolver (shared-memory kernel), 4 eigensolver
+  // (cooperative kernel)
+  double acc_ms[5] = {0, 0, 0, 0, 0}, acc_flops[5] = {0, 0, 0, 0, 0};
+  long acc_launch[5] = {0, 0, 0, 0, 0};
   cudaEvent_t ev() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -570,7 +571,7 @@ class CudaBackend : public Backend {
       CK(cudaEventSynchronize(r.b));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, r.a, r.b));
-      int t = std::min(3, std::max(0, r.tag));
+      int t = std::min(4, std::max(0, r.tag));
       acc_ms[t] += ms;
       acc_flops[t] += r.flops;
       acc_launch[t] += 1;
@@ -594,11 +595,11 @@ class CudaBackend : public Backend {
   void set_profile(bool on) override {
     drain();
     profiling = on;
-    for (int t = 0; t < 4; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
+    for (int t = 0; t < 5; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
   }
   void kernel_stats(int t, double* ms, double* flops, long* launches) override {
     drain();
-    t = std::min(3, std::max(0, t));
+    t = std::min(4, std::max(0, t));
     if (ms) *ms = acc_ms[t];
     if (flops) *flops = acc_flops[t];
     if (launches) *launches = acc_launch[t];
@@ -950,7 +951,7 @@ class CudaBackend : public Backend {
       void* args[] = {(void*)&dt, (void*)&nt, (void*)&fl};
       Rec* rec = nullptr;
       if (profiling) {
-        recs.push_back(Rec{ev(), ev(), 0.0, 3});
+        recs.push_back(Rec{ev(), ev(), 0.0, 4});
         rec = &recs.back();
         CK(cudaEventRecord(rec->a, st));
       }

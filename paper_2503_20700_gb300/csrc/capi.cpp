@@ -257,6 +257,7 @@ dmrg_status dmrg_profile(dmrg_ctx* c, int on) {
 
 dmrg_status dmrg_kernel_stats(dmrg_ctx* c, int which, double* ms, double* flops, int64_t* launches) {
   if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
+  if (which < 0 || which > 4) return fail(c, DMRG_EINVAL, "which must be 0..4");
   try {
     long l = 0;
     c->be->kernel_stats(which, ms, flops, &l);
@@ -282,6 +283,10 @@ dmrg_status dmrg_last_sweep_phases(const dmrg_ctx* c, double* t) {
   t[8] = s.t_enl_comp;
   t[9] = s.t_enl_place_run;
   t[10] = s.t_enl_alloc;
+  t[11] = s.t_plan_items;
+  t[12] = s.t_plan_tasks;
+  t[13] = s.t_plan_upload;
+  t[14] = s.t_plan_diag;
   return DMRG_OK;
 }
 

@@ -1237,6 +1237,7 @@ struct HPsiPlan {
 };
 
 void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
+  const double tp0 = now_s();
   OpSet& lo = *Le.ops;
   OpSet& ro = *Re.ops;
   plan.psi = make_psi(lo.basis, ro.basis, n_elec_, two_s_);
@@ -1353,6 +1354,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
                  terms.size(), P.blk.size(), nit, tot, hist[0] / tot, hist[1] / tot, hist[2] / tot,
                  hist[3] / tot, hist[4] / tot, hist[5] / tot, hist[6] / tot);
   }
+  const double tp1 = now_s();
+  stats_.t_plan_items += tp1 - tp0;
   std::vector<HpsiBlock> blocks;
   std::vector<HpsiItem> items;
   for (size_t b = 0; b < P.blk.size(); ++b) {
@@ -1382,6 +1385,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   } else {
     scr = hpsi_plan_tasks(blocks, plan.prec, tasks, reds);
   }
+  const double tp2 = now_s();
+  stats_.t_plan_tasks += tp2 - tp1;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t ob = 0, oi = al(ob + blocks.size() * sizeof(HpsiBlock));
   size_t oc = al(oi + items.size() * sizeof(HpsiItem));
@@ -1417,6 +1422,9 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   plan.ntasks = (int)tasks.size();
   plan.nreds = (int)reds.size();
   plan.nitems = items.size();
+  be_->sync();
+  const double tp3 = now_s();
+  stats_.t_plan_upload += tp3 - tp2;
   // diagonal: sigma_diag(a,b)[i,j] = sum alpha A(a,a)[i,i] B(b,b)[j,j] over the
   // items whose ket block equals their sigma block (outer products, k = 1)
   if (plan.diag) be_->free(plan.diag);
@@ -1441,6 +1449,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
     gd.add(plan.diag + bl.off, bl.rows, bl.cols, bl.cols, GemmSeg{a, b, 1, lda, ldb, 0, 1, it.alpha});
   }
   gd.run(be_, Precision::FP64);
+  be_->sync();
+  stats_.t_plan_diag += now_s() - tp3;
 }
 
 

@@ -159,6 +159,9 @@ struct SweepStats {
   // inside enlarge: host term lists, host placement lists, complementary GEMMs
   double t_enl_terms = 0.0, t_enl_place_host = 0.0, t_enl_comp = 0.0, t_enl_place_run = 0.0,
          t_enl_alloc = 0.0;
+  // inside plan: host item lists, task lists (tcgen05 preparation included),
+  // uploads and operator splits (device-synchronised), diagonal (synchronised)
+  double t_plan_items = 0.0, t_plan_tasks = 0.0, t_plan_upload = 0.0, t_plan_diag = 0.0;
 };
 
 class Engine {
