@@ -5,9 +5,10 @@
 //   gemm_f64_kernel     C += sum_s alpha_s op(A_s) op(B_s)    (FP64 reference path, DFMA)
 //   gemm_tf32x3 (gemm_split.cu)                                (split-FP32 tensor-core path)
 //   dots/combine/axpby  Davidson vector algebra (FP64, deterministic two-stage reductions)
-//   jacobi_smem_kernel  parallel cyclic Jacobi eigensolver in shared memory, one CTA per matrix (FP64)
-//   jacobi_coop_kernel  the same on cooperative CTA groups for larger matrices
-// All kernels are bounded loops over their inputs; none waits on another CTA.
+//   jacobi_smem_kernel  parallel cyclic Jacobi eigensolver (FP64) of one matrix in shared memory, one CTA
+//   jacobi_coop_kernel  a batch of matrices on one CTA per SM, each on a group of CTAs sized to its work
+// All kernels are bounded loops over their inputs; the one wait on other CTAs,
+// the group barrier of jacobi_coop_kernel, gives up after 5 s and sets the error flag.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,6 +75,19 @@ struct GemmTile {
 
 constexpr int kTM = 64, kTN = 64, kTK = 16;
 
+__device__ __forceinline__ void gemm_f64_step(const double (*As)[kTM + 1], const double (*Bs)[kTN + 1], int kk,
+                                              int tx, int ty, double (&acc)[4][4]) {
+  double a[4], b[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+}
+
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmGroup* __restrict__ groups,
                                                        const GemmSeg* __restrict__ segs,
                                                        const GemmTile* __restrict__ tiles) {
@@ -112,17 +126,13 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmGroup* __restri
         Bs[kk][j] = v;
       }
       __syncthreads();
+      // a ragged last step (k = 1 outer products, k tails) runs only its valid kk
+      const int kn = min(kTK, sg.k - k0);
+      if (kn == kTK) {
 #pragma unroll
-      for (int kk = 0; kk < kTK; ++kk) {
-        double a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int kk = 0; kk < kTK; ++kk) gemm_f64_step(As, Bs, kk, tx, ty, acc);
+      } else {
+        for (int kk = 0; kk < kn; ++kk) gemm_f64_step(As, Bs, kk, tx, ty, acc);
       }
       __syncthreads();
     }
@@ -203,131 +213,225 @@ __global__ void precond_kernel(double* __restrict__ y, const double* __restrict_
 // ------------------------------------------------------------------ Jacobi
 // Parallel cyclic Jacobi (round-robin pairing) on a symmetric n x n matrix
 // (destroyed).  Eigenvalues descending in w, the eigenvectors as rows of V.
-// One round rotates n/2 disjoint pairs; each 2x2 block (pair i rows, pair j
-// columns) of A is updated in one pass as R_i X R_j^T, and the eigenvector
-// rows p, q of V are rotated together.  A pair is skipped when its
-// off-diagonal entry is negligible next to both diagonal entries, or below
-// 1e-16 ||A||_F: the rounding noise of a GEMM-formed density matrix, whose
-// (near) null space would otherwise keep rotating noise for every sweep.
-// The iteration stops after a sweep without rotations, or after kMaxSweeps
-// sweeps.
+// One round rotates n/2 disjoint pairs.  The matrix is updated as 2x2 blocks
+// (rows of pair i, columns of pair j) R_i X R_j^T for i <= j only, each
+// result stored at both symmetric positions: 2n^2 FP64 operations a round on
+// A instead of 4n^2, plus 2n^2 on the eigenvector rows p, q of V.  A pair is
+// skipped when its off-diagonal entry is negligible next to both diagonal
+// entries, or below 1e-16 ||A||_F: the rounding noise of a GEMM-formed
+// density matrix, whose (near) null space would otherwise keep rotating noise
+// for every sweep.  The iteration stops after a sweep without rotations, or
+// after kMaxSweeps sweeps.
+//
+// The work is FP64-bound (GB300 has few FP64 units per SM), so a batch of
+// matrices is spread over the SMs: one cooperative launch with one CTA per
+// SM, each matrix on a group of g CTAs sized to its share of the work (g = 1:
+// A and V in shared memory; g > 1: A and V in global memory, one group
+// barrier per round).
 constexpr int kMaxSweeps = 30;
+constexpr int kSmemN = 112;       // largest matrix of the shared-memory path
+constexpr int kJacThreads = 512;  // threads of a batched-launch CTA
 
-// jacobi_smem_kernel (n <= kSmemN, one CTA per matrix): A (row stride n+1)
-// and the eigenvector rows V live in shared memory for the whole iteration,
-// so every round's loads and stores stay on chip.
-constexpr int kSmemN = 112;  // A and V in shared memory (larger: cooperative groups, which measured faster)
 __host__ __device__ constexpr size_t jacobi_smem_bytes(int n) {
   return ((size_t)n * (n + 1) + (size_t)n * n + (size_t)((n + 1) & ~1)) * sizeof(double) +
          (size_t)((n + 1) & ~1) * 2 * sizeof(int) + 64;
 }
 
-__global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __restrict__ tasks) {
-  const EighTask tk = tasks[blockIdx.x];
-  const int n = tk.n;
-  const int lda = n + 1;
-  const int np = (n + 1) & ~1, h = np / 2;
-  extern __shared__ double sm[];
-  double* a = sm;                        // n x (n+1)
-  double* v = a + (size_t)n * lda;       // n x n, row p = eigenvector p
-  double* cs = v + (size_t)n * n;        // h
-  double* sn = cs + h;                   // h
-  int* pp = (int*)(sn + h);
-  int* qq = pp + h;
-  int* perm = qq + h;                    // np
-  __shared__ double red[256];
-  __shared__ int nrot;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int r = e / n, c = e % n;
-    a[r * lda + c] = tk.A[e];
-    v[e] = (r == c) ? 1.0 : 0.0;
+// pair i of a round, closed form of the round-robin schedule: (round, M) and
+// (round + i, round - i) mod M, M = np - 1
+__device__ __forceinline__ void jac_pair(int round, int i, int np, int& p, int& q) {
+  const int M = np - 1;
+  p = i == 0 ? round : (round + i) % M;
+  q = i == 0 ? M : (round - i + M) % M;
+  if (p > q) {
+    int t = p;
+    p = q;
+    q = t;
   }
-  for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
-  __syncthreads();
-  double fro = 0.0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    double x = a[(e / n) * lda + e % n];
-    fro += x * x;
+}
+
+// (c, s) of the rotation that annihilates a_pq; false when the pair is skipped
+__device__ __forceinline__ bool jac_rotation(double apq, double app, double aqq, double floor_abs, double& c,
+                                             double& s) {
+  c = 1.0;
+  s = 0.0;
+  const double g = 100.0 * fabs(apq);
+  if (fabs(apq) <= floor_abs || (fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) return false;
+  const double theta = (aqq - app) / (2.0 * apq);
+  const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  c = 1.0 / sqrt(t * t + 1.0);
+  s = t * c;
+  return true;
+}
+
+// block (i, j), i <= j < h, of linear index e in the row-major upper triangle;
+// row i starts at i h - i (i - 1) / 2
+__device__ __forceinline__ void tri_index(int e, int h, int& i, int& j) {
+  const float b = 2.0f * (float)h + 1.0f;
+  int r = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))) * 0.5f);
+  r = max(0, min(r, h - 1));
+  while (r > 0 && r * h - r * (r - 1) / 2 > e) --r;
+  while (r + 1 < h && (r + 1) * h - (r + 1) * r / 2 <= e) ++r;
+  i = r;
+  j = r + (e - (r * h - r * (r - 1) / 2));
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ double jac_ld(const double* p) {
+  if constexpr (kGlobal) return __ldcg(p);
+  else return *p;
+}
+
+struct JacRound {
+  const double* cs;
+  const double* sn;
+  const int* pp;
+  const int* qq;
+};
+
+// R_i X R_j^T on block (i, j), i <= j, stored at both symmetric positions
+template <bool kGlobal>
+__device__ __forceinline__ void jac_block(double* a, int lda, int n, int i, int j, const JacRound& R) {
+  const double ci = R.cs[i], si = R.sn[i], cj = R.cs[j], sj = R.sn[j];
+  if (si == 0.0 && sj == 0.0) return;
+  const int p = R.pp[i], q = R.qq[i], r = R.pp[j], t = R.qq[j];
+  const bool qv = q < n, tv = t < n;
+  const double x00 = jac_ld<kGlobal>(a + (size_t)p * lda + r);
+  const double x01 = tv ? jac_ld<kGlobal>(a + (size_t)p * lda + t) : 0.0;
+  const double x10 = qv ? jac_ld<kGlobal>(a + (size_t)q * lda + r) : 0.0;
+  const double x11 = (qv && tv) ? jac_ld<kGlobal>(a + (size_t)q * lda + t) : 0.0;
+  const double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+  const double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+  const double n00 = cj * y00 - sj * y01, n01 = sj * y00 + cj * y01;
+  if (i == j) {  // r = p, t = q: the diagonal block, (p, q) and (q, p) from one value
+    a[(size_t)p * lda + p] = n00;
+    if (qv) {
+      a[(size_t)p * lda + q] = n01;
+      a[(size_t)q * lda + p] = n01;
+      a[(size_t)q * lda + q] = sj * y10 + cj * y11;
+    }
+    return;
   }
-  red[threadIdx.x] = fro;
+  const double n10 = cj * y10 - sj * y11, n11 = sj * y10 + cj * y11;
+  a[(size_t)p * lda + r] = n00;
+  a[(size_t)r * lda + p] = n00;
+  if (tv) {
+    a[(size_t)p * lda + t] = n01;
+    a[(size_t)t * lda + p] = n01;
+  }
+  if (qv) {
+    a[(size_t)q * lda + r] = n10;
+    a[(size_t)r * lda + q] = n10;
+  }
+  if (qv && tv) {
+    a[(size_t)q * lda + t] = n11;
+    a[(size_t)t * lda + q] = n11;
+  }
+}
+
+// element k of the eigenvector rows p, q of pair i
+template <bool kGlobal>
+__device__ __forceinline__ void jac_vrot(double* v, int n, int i, int k, const JacRound& R) {
+  const double s = R.sn[i];
+  if (s == 0.0) return;
+  const double c = R.cs[i];
+  const int p = R.pp[i], q = R.qq[i];
+  const double vp = jac_ld<kGlobal>(v + (size_t)p * n + k), vq = jac_ld<kGlobal>(v + (size_t)q * n + k);
+  v[(size_t)p * n + k] = c * vp - s * vq;
+  v[(size_t)q * n + k] = s * vp + c * vq;
+}
+
+// rotation parameters of every pair of the round (threads < h); nrot counts
+// the rotations of the sweep
+template <bool kGlobal>
+__device__ __forceinline__ void jac_params(const double* a, int lda, int n, int np, int round, double floor_abs,
+                                           double* cs, double* sn, int* pp, int* qq, int* nrot) {
+  const int h = np / 2;
+  for (int i = threadIdx.x; i < h; i += blockDim.x) {
+    int p, q;
+    jac_pair(round, i, np, p, q);
+    pp[i] = p;
+    qq[i] = q;
+    double c = 1.0, s = 0.0;
+    if (q < n &&
+        jac_rotation(jac_ld<kGlobal>(a + (size_t)p * lda + q), jac_ld<kGlobal>(a + (size_t)p * lda + p),
+                     jac_ld<kGlobal>(a + (size_t)q * lda + q), floor_abs, c, s))
+      atomicAdd(nrot, 1);
+    cs[i] = c;
+    sn[i] = s;
+  }
+}
+
+// sum over the CTA (blockDim a power of two, red holds blockDim values)
+__device__ double jac_block_sum(double x, double* red) {
+  red[threadIdx.x] = x;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  const double floor_abs = 1e-16 * sqrt(red[0]);
+  const double r = red[0];
   __syncthreads();
-  for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
-    if (threadIdx.x == 0) nrot = 0;
-    __syncthreads();
-    for (int round = 0; round < np - 1; ++round) {
-      for (int i = threadIdx.x; i < h; i += blockDim.x) {
-        // round-robin pairs in closed form: (round, M) and (round +- i) mod M
-        const int M = np - 1;
-        int p = i == 0 ? round : (round + i) % M, q = i == 0 ? M : (round - i + M) % M;
-        if (p > q) { int t = p; p = q; q = t; }
-        pp[i] = p;
-        qq[i] = q;
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = a[p * lda + q], app = a[p * lda + p], aqq = a[q * lda + q];
-          double g = 100.0 * fabs(apq);
-          bool negligible = fabs(apq) <= floor_abs || (fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq));
-          if (!negligible) {
-            double theta = (aqq - app) / (2.0 * apq);
-            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
-            atomicAdd(&nrot, 1);
-          }
-        }
-        cs[i] = c;
-        sn[i] = s;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < h * h; e += blockDim.x) {
-        int i = e / h, j = e % h;
-        double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-        if (si == 0.0 && sj == 0.0) continue;
-        int p = pp[i], q = qq[i], r = pp[j], t = qq[j];
-        bool qv = q < n, tv = t < n;
-        double x00 = a[p * lda + r];
-        double x01 = tv ? a[p * lda + t] : 0.0;
-        double x10 = qv ? a[q * lda + r] : 0.0;
-        double x11 = (qv && tv) ? a[q * lda + t] : 0.0;
-        double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
-        double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        a[p * lda + r] = cj * y00 - sj * y01;
-        if (tv) a[p * lda + t] = sj * y00 + cj * y01;
-        if (qv) a[q * lda + r] = cj * y10 - sj * y11;
-        if (qv && tv) a[q * lda + t] = sj * y10 + cj * y11;
-      }
-      for (int e = threadIdx.x; e < h * n; e += blockDim.x) {
-        int i = e / n, k = e % n;
-        double s = sn[i];
-        if (s == 0.0) continue;
-        double c = cs[i];
-        int p = pp[i], q = qq[i];
-        double vp = v[p * n + k], vq = v[q * n + k];
-        v[p * n + k] = c * vp - s * vq;
-        v[q * n + k] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-    if (nrot == 0) break;
-    __syncthreads();
-  }
+  return r;
+}
+
+// rank of the diagonal entries, descending (NaN last, ties by index): perm[rank] = i
+template <bool kGlobal>
+__device__ void jac_order(const double* a, int lda, int n, int* perm) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double di = a[i * lda + i];
+    double di = jac_ld<kGlobal>(a + (size_t)i * lda + i);
     if (!(di == di)) di = -INFINITY;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double dj = a[j * lda + j];
+      double dj = jac_ld<kGlobal>(a + (size_t)j * lda + j);
       if (!(dj == dj)) dj = -INFINITY;
       rank += (dj > di) || (dj == di && j < i);
     }
     perm[rank] = i;
   }
+}
+
+// one matrix on one CTA, A (row stride n+1) and V in shared memory
+__device__ void jacobi_one(const EighTask& tk, double* sm, double* red, int* nrot) {
+  const int n = tk.n;
+  const int lda = n + 1;
+  const int np = (n + 1) & ~1, h = np / 2;
+  double* a = sm;                   // n x (n+1)
+  double* v = a + (size_t)n * lda;  // n x n, row p = eigenvector p
+  double* cs = v + (size_t)n * n;   // h
+  double* sn = cs + h;              // h
+  int* pp = (int*)(sn + h);
+  int* qq = pp + h;
+  int* perm = qq + h;  // np
+  const JacRound R{cs, sn, pp, qq};
+  double fro = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e % n;
+    const double x = tk.A[e];
+    a[r * lda + c] = x;
+    v[e] = (r == c) ? 1.0 : 0.0;
+    fro += x * x;
+  }
+  const double floor_abs = 1e-16 * sqrt(jac_block_sum(fro, red));
+  const int nb = h * (h + 1) / 2;
+  for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
+    if (threadIdx.x == 0) *nrot = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      jac_params<false>(a, lda, n, np, round, floor_abs, cs, sn, pp, qq, nrot);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+        int i, j;
+        tri_index(e, h, i, j);
+        jac_block<false>(a, lda, n, i, j, R);
+      }
+      for (int e = threadIdx.x; e < h * n; e += blockDim.x) jac_vrot<false>(v, n, e / n, e % n, R);
+      __syncthreads();
+    }
+    if (*nrot == 0) break;
+    __syncthreads();
+  }
+  jac_order<false>(a, lda, n, perm);
   __syncthreads();
   for (int r = threadIdx.x; r < n; r += blockDim.x) tk.w[r] = a[perm[r] * lda + perm[r]];
   // eigenvector rows in descending order, largest-magnitude component positive
@@ -337,20 +441,29 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
     int bi = 0;
     for (int k = 0; k < n; ++k) {
       double x = fabs(src[k]);
-      if (x > best + 1e-12) { best = x; bi = k; }
+      if (x > best + 1e-12) {
+        best = x;
+        bi = k;
+      }
     }
-    double sg = src[bi] < 0 ? -1.0 : 1.0;
+    const double sg = src[bi] < 0 ? -1.0 : 1.0;
     for (int k = 0; k < n; ++k) tk.V[(size_t)r * n + k] = sg * src[k];
   }
 }
 
-// Cooperative variant for large matrices: a group of g CTAs shares one
-// matrix.  Every CTA of the group computes the round's rotation parameters
-// from the same diagonal and off-diagonal entries (identical values, so no
-// exchange is needed) and updates the 2x2 blocks of its own pair rows and
-// the matching eigenvector rows; one group barrier per round publishes the
-// updates.  Launched cooperatively (all CTAs co-resident); the barrier's
-// wait is bounded by 5 s of wall clock and sets the error flag on timeout.
+__global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __restrict__ tasks) {
+  extern __shared__ double sm[];
+  __shared__ double red[256];
+  __shared__ int nrot;
+  jacobi_one(tasks[blockIdx.x], sm, red, &nrot);
+}
+
+// A matrix on a group of g CTAs: every CTA of the group computes the round's
+// rotation parameters from the same entries (identical values, so no
+// exchange is needed) and updates its own contiguous share of the triangle
+// blocks and of the eigenvector elements; one group barrier per round
+// publishes the updates.  The barrier's wait is bounded by 5 s of wall clock
+// and sets the error flag on timeout.
 struct CoopEigh {
   EighTask t;
   int g, cta0;
@@ -361,6 +474,12 @@ __device__ __forceinline__ unsigned long long jac_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned x;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+  return x;
 }
 
 // returns false when the wait ran out
@@ -375,12 +494,14 @@ __device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
       atomicExch(&bar[1], target);
     } else {
       const unsigned long long t0 = jac_ns();
-      while ((int)(atomicAdd(&bar[1], 0u) - target) < 0) {
-        if (jac_ns() - t0 > 5000000000ull) {
-          *ok_s = 0;
-          break;
+      for (int probe = 0; (int)(ld_acquire(&bar[1]) - target) < 0; ++probe) {
+        if (probe >= 256) {
+          if (jac_ns() - t0 > 5000000000ull) {
+            *ok_s = 0;
+            break;
+          }
+          __nanosleep(32);
         }
-        __nanosleep(32);
       }
     }
     gen = target;
@@ -390,126 +511,61 @@ __device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
   return *ok_s != 0;
 }
 
-__global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __restrict__ tasks, int ntasks,
-                                                          int* __restrict__ err) {
-  int ti = 0;
-  while (ti + 1 < ntasks && tasks[ti + 1].cta0 <= (int)blockIdx.x) ++ti;
-  const CoopEigh ct = tasks[ti];
-  const int g = ct.g, me = (int)blockIdx.x - ct.cta0;
+__device__ void jacobi_group(const CoopEigh& ct, int me, double* sm, double* red, int* nrot, int* ok_s,
+                             int* err) {
+  const int g = ct.g;
   const int n = ct.t.n;
   double* a = const_cast<double*>(ct.t.A);
   double* v = ct.t.V;
-  extern __shared__ double sm[];
   const int np = (n + 1) & ~1, h = np / 2;
   double* cs = sm;
   double* sn = sm + h;
   int* pp = (int*)(sm + np);
   int* qq = pp + h;
   int* perm = qq + h;
-  __shared__ double red[256];
-  __shared__ int ok_s;
-  __shared__ int nrot;
+  const JacRound R{cs, sn, pp, qq};
   unsigned gen = 0;
-  if (threadIdx.x == 0) ok_s = 1;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) perm[i] = i;
+  if (threadIdx.x == 0) *ok_s = 1;
   for (int r = me; r < n; r += g)
     for (int k = threadIdx.x; k < n; k += blockDim.x) v[(size_t)r * n + k] = (r == k) ? 1.0 : 0.0;
   double fro = 0.0;
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
-    double x = __ldcg(a + e);
+    const double x = __ldcg(a + e);
     fro += x * x;
   }
-  red[threadIdx.x] = fro;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double floor_abs = 1e-16 * sqrt(red[0]);
-  if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
+  const double floor_abs = 1e-16 * sqrt(jac_block_sum(fro, red));
+  // this CTA's shares: triangle blocks [b0, b1), eigenvector elements [v0, v1)
+  const long long nb = (long long)h * (h + 1) / 2, nv = (long long)h * n;
+  const int b0 = (int)(nb * me / g), b1 = (int)(nb * (me + 1) / g);
+  const int v0 = (int)(nv * me / g), v1 = (int)(nv * (me + 1) / g);
+  if (!group_sync(ct.bar, g, gen, ok_s)) goto fail;
   for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
-    if (threadIdx.x == 0) nrot = 0;
+    if (threadIdx.x == 0) *nrot = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
-      for (int i = threadIdx.x; i < h; i += blockDim.x) {
-        // round-robin pairs in closed form: (round, M) and (round +- i) mod M
-        const int M = np - 1;
-        int p = i == 0 ? round : (round + i) % M, q = i == 0 ? M : (round - i + M) % M;
-        if (p > q) { int t = p; p = q; q = t; }
-        pp[i] = p;
-        qq[i] = q;
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = __ldcg(a + (size_t)p * n + q);
-          double app = __ldcg(a + (size_t)p * n + p), aqq = __ldcg(a + (size_t)q * n + q);
-          double gg = 100.0 * fabs(apq);
-          bool negligible = fabs(apq) <= floor_abs || (fabs(app) + gg == fabs(app) && fabs(aqq) + gg == fabs(aqq));
-          if (!negligible) {
-            double theta = (aqq - app) / (2.0 * apq);
-            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
-            atomicAdd(&nrot, 1);
-          }
-        }
-        cs[i] = c;
-        sn[i] = s;
-      }
+      jac_params<true>(a, n, n, np, round, floor_abs, cs, sn, pp, qq, nrot);
       __syncthreads();
-      // my pair rows i = me, me + g, ...: blocks (i, j) for all j
-      const int my_rows = (h - me + g - 1) / g;
-      for (size_t e = threadIdx.x; e < (size_t)my_rows * h; e += blockDim.x) {
-        int i = me + (int)(e / h) * g, j = (int)(e % h);
-        double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-        if (si == 0.0 && sj == 0.0) continue;
-        int p = pp[i], q = qq[i], r = pp[j], t = qq[j];
-        bool qv = q < n, tv = t < n;
-        double x00 = __ldcg(a + (size_t)p * n + r);
-        double x01 = tv ? __ldcg(a + (size_t)p * n + t) : 0.0;
-        double x10 = qv ? __ldcg(a + (size_t)q * n + r) : 0.0;
-        double x11 = (qv && tv) ? __ldcg(a + (size_t)q * n + t) : 0.0;
-        double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
-        double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        a[(size_t)p * n + r] = cj * y00 - sj * y01;
-        if (tv) a[(size_t)p * n + t] = sj * y00 + cj * y01;
-        if (qv) a[(size_t)q * n + r] = cj * y10 - sj * y11;
-        if (qv && tv) a[(size_t)q * n + t] = sj * y10 + cj * y11;
+      for (int e = b0 + (int)threadIdx.x; e < b1; e += blockDim.x) {
+        int i, j;
+        tri_index(e, h, i, j);
+        jac_block<true>(a, n, n, i, j, R);
       }
-      for (size_t e = threadIdx.x; e < (size_t)my_rows * n; e += blockDim.x) {
-        int i = me + (int)(e / n) * g, k = (int)(e % n);
-        double s = sn[i];
-        if (s == 0.0) continue;
-        double c = cs[i];
-        int p = pp[i], q = qq[i];
-        double vp = __ldcg(v + (size_t)p * n + k), vq = __ldcg(v + (size_t)q * n + k);
-        v[(size_t)p * n + k] = c * vp - s * vq;
-        v[(size_t)q * n + k] = s * vp + c * vq;
-      }
-      if (!group_sync(ct.bar, g, gen, &ok_s)) goto fail;
+      for (int e = v0 + (int)threadIdx.x; e < v1; e += blockDim.x) jac_vrot<true>(v, n, e / n, e % n, R);
+      if (!group_sync(ct.bar, g, gen, ok_s)) goto fail;
     }
-    if (nrot == 0) break;
+    if (*nrot == 0) break;
     __syncthreads();
   }
   if (me != 0) return;
-  // CTA 0: eigenvalues descending (rank by counting, ties by index), rows of V
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double di = __ldcg(a + (size_t)i * n + i);
-    if (!(di == di)) di = -INFINITY;
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double dj = __ldcg(a + (size_t)j * n + j);
-      if (!(dj == dj)) dj = -INFINITY;
-      rank += (dj > di) || (dj == di && j < i);
-    }
-    perm[rank] = i;
-  }
+  // CTA 0: eigenvalues descending, rows of V permuted, largest component positive
+  jac_order<true>(a, n, n, perm);
   __syncthreads();
   for (int r = threadIdx.x; r < n; r += blockDim.x) ct.t.w[r] = __ldcg(a + (size_t)perm[r] * n + perm[r]);
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) a[e] = __ldcg(v + e);
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
-    int r = (int)(e / n), k = (int)(e % n);
+    const int r = (int)(e / n), k = (int)(e % n);
     v[e] = a[(size_t)perm[r] * n + k];
   }
   __syncthreads();
@@ -518,7 +574,10 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __rest
     int bi = 0;
     for (int k = 0; k < n; ++k) {
       double x = fabs(v[(size_t)r * n + k]);
-      if (x > best + 1e-12) { best = x; bi = k; }
+      if (x > best + 1e-12) {
+        best = x;
+        bi = k;
+      }
     }
     if (v[(size_t)r * n + bi] < 0)
       for (int k = 0; k < n; ++k) v[(size_t)r * n + k] = -v[(size_t)r * n + k];
@@ -526,6 +585,48 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(const CoopEigh* __rest
   return;
 fail:
   if (threadIdx.x == 0) atomicExch(err, 1);
+}
+
+// The batched launch: CTA b belongs to the last task whose cta0 <= b.
+__global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(const CoopEigh* __restrict__ tasks, int ntasks,
+                                                                  int* __restrict__ err) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tasks[mid].cta0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const CoopEigh ct = tasks[lo];
+  extern __shared__ double sm[];
+  __shared__ double red[kJacThreads];
+  __shared__ int nrot, ok_s;
+  if (ct.g == 1) jacobi_one(ct.t, sm, red, &nrot);
+  else jacobi_group(ct, (int)blockIdx.x - ct.cta0, sm, red, &nrot, &ok_s, err);
+}
+
+// Modelled time of an n x n matrix on g CTAs, in SM clocks (FP64 rate of 2
+// operations a clock; a group barrier about 6000 clocks): the group sizes of
+// a batch minimise the slowest matrix.
+inline double jac_cost(int n, int g) {
+  const double rounds = std::max(1, ((n + 1) & ~1) - 1);
+  const double ops = 2.0 * (double)n * n;  // clocks of the FP64 work of a round on one SM
+  return rounds * (g == 1 ? ops + 1000.0 : 1.15 * ops / g + 6000.0);
+}
+
+// g[k] of batch tasks (descending n) start at their minimum; spare CTAs go to
+// the slowest matrix while that shortens it
+inline void jac_assign_groups(const std::vector<int>& n, std::vector<int>& g, int spare) {
+  while (spare > 0) {
+    size_t k = 0;
+    for (size_t i = 1; i < n.size(); ++i)
+      if (jac_cost(n[i], g[i]) > jac_cost(n[k], g[k])) k = i;
+    const int gmax = std::max(2, std::min(32, ((n[k] + 1) & ~1) / 2));
+    int ng = g[k] + 1;
+    while (ng <= gmax && ng - g[k] <= spare && jac_cost(n[k], ng) >= jac_cost(n[k], g[k])) ++ng;
+    if (ng > gmax || ng - g[k] > spare) break;
+    spare -= ng - g[k];
+    g[k] = ng;
+  }
 }
 
 // ------------------------------------------------------------------ backend
@@ -880,63 +981,61 @@ class CudaBackend : public Backend {
     ++launches;
     CK(cudaGetLastError());
   }
-  // Matrices up to kCoopN use one CTA each; larger ones a cooperative group
-  // of g CTAs (g grows with n, the groups of one launch fit co-resident).
-  static constexpr int kCoopN = kSmemN;
+  // One small matrix (the Davidson subspace problem): one CTA.  A batch (the
+  // density-matrix sectors of a decimation): cooperative launches of one CTA
+  // per SM (the shared memory of the n <= kSmemN path admits one CTA per SM),
+  // largest matrices first, group sizes from jac_assign_groups.
+  bool jac_init = false;
+  int jac_cap = 0;
   void eigh(const std::vector<EighTask>& tasks) override {
     if (tasks.empty()) return;
-    std::vector<EighTask> large;
-    // matrices that fit in shared memory: one launch per size class
-    std::vector<EighTask> cls[3];
-    for (auto& t : tasks) {
-      if (t.n > kSmemN) large.push_back(t);
-      else cls[t.n <= 32 ? 0 : (t.n <= 64 ? 1 : 2)].push_back(t);
-    }
-    for (auto& c : cls) {
-      if (c.empty()) continue;
-      int nmax = 1;
-      for (auto& t : c) nmax = std::max(nmax, t.n);
-      const size_t smem = jacobi_smem_bytes(nmax);
+    const size_t smem = jacobi_smem_bytes(kSmemN);
+    if (!jac_init) {
       CK(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      CK(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0, sms = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, kJacThreads, smem));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      jac_cap = per_sm * sms;
+      if (jac_cap < 2) throw std::runtime_error("cuda: eigensolver needs two co-resident CTAs");
+      jac_init = true;
+    }
+    if (tasks.size() == 1 && tasks[0].n <= kSmemN) {
       std::vector<size_t> off;
-      char* d = upload({{c.data(), c.size() * sizeof(EighTask)}}, off);
+      char* d = upload({{tasks.data(), sizeof(EighTask)}}, off);
       Rec* rec = nullptr;
       if (profiling) {
         recs.push_back(Rec{ev(), ev(), 0.0, 3});
         rec = &recs.back();
         CK(cudaEventRecord(rec->a, st));
       }
-      jacobi_smem_kernel<<<(unsigned)c.size(), 256, smem, st>>>((const EighTask*)(d + off[0]));
+      jacobi_smem_kernel<<<1, 256, jacobi_smem_bytes(tasks[0].n), st>>>((const EighTask*)(d + off[0]));
       if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       CK(cudaGetLastError());
+      return;
     }
-    if (large.empty()) return;
-    int nmax = 1;
-    for (auto& t : large) nmax = std::max(nmax, t.n);
-    const int npm = (nmax + 1) & ~1;
-    size_t smem = (size_t)npm * sizeof(double) + (size_t)(npm / 2) * 2 * sizeof(int) + (size_t)npm * sizeof(int);
-    if (smem > 200 * 1024) throw std::runtime_error("internal: eigensolver matrix too large");
-    CK(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, 256, smem));
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int capacity = std::max(1, per_sm * sms);
-    // largest matrices first; one launch per batch that fits co-resident
-    std::sort(large.begin(), large.end(), [](const EighTask& x, const EighTask& y) { return x.n > y.n; });
+    std::vector<EighTask> order(tasks);
+    std::stable_sort(order.begin(), order.end(), [](const EighTask& x, const EighTask& y) { return x.n > y.n; });
     size_t i0 = 0;
-    while (i0 < large.size()) {
+    while (i0 < order.size()) {
+      std::vector<int> ns, g;
+      int used = 0;
+      size_t i1 = i0;
+      while (i1 < order.size()) {
+        const int gmin = order[i1].n > kSmemN ? 2 : 1;
+        if (used + gmin > jac_cap) break;
+        ns.push_back(order[i1].n);
+        g.push_back(gmin);
+        used += gmin;
+        ++i1;
+      }
+      jac_assign_groups(ns, g, jac_cap - used);
       std::vector<CoopEigh> ct;
       int ctas = 0;
-      size_t i1 = i0;
-      while (i1 < large.size()) {
-        int g = std::min(16, std::max(2, large[i1].n / 32));
-        g = std::min(g, capacity);
-        if (ctas + g > capacity && !ct.empty()) break;
-        ct.push_back({large[i1], g, ctas, nullptr});
-        ctas += g;
-        ++i1;
+      for (size_t k = 0; k < ns.size(); ++k) {
+        ct.push_back({order[i0 + k], g[k], ctas, nullptr});
+        ctas += g[k];
       }
       std::vector<unsigned> bars(2 * ct.size(), 0u);
       std::vector<size_t> off;
@@ -955,7 +1054,7 @@ class CudaBackend : public Backend {
         rec = &recs.back();
         CK(cudaEventRecord(rec->a, st));
       }
-      CK(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(ctas), dim3(256), args, smem, st));
+      CK(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(ctas), dim3(kJacThreads), args, smem, st));
       if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
       i0 = i1;

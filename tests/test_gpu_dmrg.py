@@ -204,7 +204,7 @@ def test_eigh_against_numpy(pkg):
 
 
 def test_eigh_cooperative_groups_density_matrices(pkg):
-    """Matrices above 96 go to the cooperative multi-CTA Jacobi: a batch of
+    """Matrices above 112 go to the cooperative multi-CTA Jacobi: a batch of
     density-matrix-like (PSD, rank-deficient, fast-decaying) and indefinite
     matrices of several sizes, with small ones mixed in."""
     rng = np.random.default_rng(8)
@@ -214,6 +214,29 @@ def test_eigh_cooperative_groups_density_matrices(pkg):
         mats.append(x @ x.T)
     y = rng.standard_normal((211, 211))
     mats.append(y + y.T)
+    res = pkg.ops.eigh_batched(mats)
+    for M, (w, V) in zip(mats, res):
+        ref = np.sort(np.linalg.eigvalsh(M))[::-1]
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(w - ref).max() < 1e-11 * scale
+        assert np.abs(V @ M - w[:, None] * V).max() < 1e-10 * scale
+        assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-11
+
+
+def test_eigh_batches_larger_than_one_launch(pkg):
+    """More matrices than one CTA per SM: several cooperative launches, group
+    sizes from the cost model (mid-size matrices split over CTA groups, small
+    ones on one CTA), density-matrix-like and indefinite, sizes 1..160."""
+    rng = np.random.default_rng(12)
+    mats = []
+    for k in range(190):
+        n = int(rng.integers(1, 161))
+        if k % 3:
+            x = rng.standard_normal((n, max(1, n // 3))) * np.exp(-np.arange(max(1, n // 3)) / 6.0)
+            mats.append(x @ x.T)
+        else:
+            y = rng.standard_normal((n, n))
+            mats.append(y + y.T)
     res = pkg.ops.eigh_batched(mats)
     for M, (w, V) in zip(mats, res):
         ref = np.sort(np.linalg.eigvalsh(M))[::-1]
