@@ -342,7 +342,7 @@ def main():
     launches = g.launch_count() - l0
     k_ms, k_flops, k_launch = g.kernel_stats(1)
     kernel_ms = {name: g.kernel_stats(i)[0]
-                 for i, name in enumerate(["gemm", "hpsi", "place", "eigh_smem", "eigh_coop"])}
+                 for i, name in enumerate(["gemm", "hpsi", "place", "eigh_subspace", "eigh_batched"])}
     mem_now, mem_peak = g.memory()
     flops_job += flops
     _ = g.energy()

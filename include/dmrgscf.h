@@ -153,8 +153,9 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
  * since profiling was turned on.  which = 1: the H_eff psi launches (with
  * the operand splits of the tcgen05 path), 0: all other GEMM launches
  * (renormalisation, complementary operators, density matrices), 2: the
- * blocking placement kernel, 3: the shared-memory eigensolver, 4: the
- * cooperative eigensolver (sectors above 112). */
+ * blocking placement kernel, 3: the eigensolver of a single small matrix
+ * (the Davidson subspace problem), 4: the batched eigensolver (the
+ * density-matrix sectors of a decimation, one cooperative launch per batch). */
 dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
                               int64_t* launches);
 
