@@ -2,6 +2,7 @@
 #include "dmrg.hpp"
 #include "hpsi_fused.cuh"
 #include "hpsi_tc.cuh"
+#include "host_pool.hpp"
 
 #include <algorithm>
 #include <array>
@@ -12,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <set>
 #include <stdexcept>
 
 namespace dmrg {
@@ -805,7 +807,30 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     std::vector<size_t> base;  // per layout block
     size_t total = 0;
   };
+  // The layouts of the targets and operands are created first, so that the
+  // threaded passes below only read the layout maps.
+  {
+    std::set<std::pair<int, int>> used;
+    for (const auto& [tk, t] : terms) {
+      used.insert({kind_dn(tk.kind), tk.k2});
+      const Operand& bop = L ? t.x : t.y;
+      if (bop.t != Operand::ID) used.insert({kind_dn(bop.key.kind), bop.key.k2});
+    }
+    for (auto& [dn, k2] : used) {
+      eo.layout(dn, k2);
+      bo.layout(dn, k2);
+      if (tmp) const_cast<OpSet*>(tmp)->layout(dn, k2);
+    }
+  }
   std::map<const Layout*, LayoutIndex> lidx;
+  for (auto& [key, lay] : eo.layouts) {
+    LayoutIndex li;
+    for (auto& blk : lay.blk) {
+      li.base.push_back(li.total);
+      li.total += by[blk.bra].size() * by[blk.ket].size();
+    }
+    lidx.emplace(&lay, std::move(li));
+  }
   struct TermCtx {
     double* dst = nullptr;
     const Layout* TL = nullptr;
@@ -813,37 +838,34 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     ResolvedOperand rop;
   };
   std::vector<TermCtx> ctx(terms.size());
-  for (size_t i = 0; i < terms.size(); ++i) {
-    const auto& [tk, t] = terms[i];
-    ctx[i].dst = eo.get(tk);
-    if (!ctx[i].dst) continue;
-    ctx[i].TL = &eo.layout(kind_dn(tk.kind), tk.k2);
-    auto it = lidx.find(ctx[i].TL);
-    if (it == lidx.end()) {
-      LayoutIndex li;
-      for (auto& blk : ctx[i].TL->blk) {
-        li.base.push_back(li.total);
-        li.total += by[blk.bra].size() * by[blk.ket].size();
-      }
-      it = lidx.emplace(ctx[i].TL, std::move(li)).first;
-    }
-    ctx[i].LI = &it->second;
-    const Operand& bop = L ? t.x : t.y;
-    if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
-    ctx[i].rop = resolve(bo, tmp, bop);
-  }
   struct Entry {
     uint32_t li;
     double* d;
     int rows, cols, ld;
     PlaceSeg seg;
   };
-  // placement segments of a range of terms (pure host arithmetic)
-  auto generate = [&](size_t t0, size_t t1, std::vector<Entry>& out, std::vector<size_t>& ends) {
+  // term chunks: context, then placement segments (pure host arithmetic)
+  const size_t nterm = terms.size();
+  const size_t chunk = std::max<size_t>(16, nterm / (8 * host_threads()) + 1);
+  const size_t nchunk = (nterm + chunk - 1) / chunk;
+  std::vector<std::vector<Entry>> parts(nchunk);
+  std::vector<std::pair<const Entry*, const Entry*>> range(nterm, {nullptr, nullptr});
+  host_parallel_for(nchunk, [&](size_t c) {
+    const size_t t0 = c * chunk, t1 = std::min(nterm, t0 + chunk);
+    std::vector<size_t> ends;
+    std::vector<Entry>& out = parts[c];
     for (size_t i = t0; i < t1; ++i) {
-      const TermCtx& cx = ctx[i];
+      TermCtx& cx = ctx[i];
+      const auto& [tk, t] = terms[i];
+      cx.dst = eo.get(tk);
+      if (cx.dst) {
+        cx.TL = &eo.layout(kind_dn(tk.kind), tk.k2);
+        cx.LI = &lidx.at(cx.TL);
+        const Operand& bop = L ? t.x : t.y;
+        if (bop.t == Operand::SITE) throw std::runtime_error("site operand on block part");
+        cx.rop = resolve(bo, tmp, bop);
+      }
       if (cx.dst && cx.rop.ok) {
-        const Term& t = terms[i].second;
         const Operand& bop = L ? t.x : t.y;   // operand on the block part
         const Operand& sop = L ? t.y : t.x;   // operand on the site part
         for (size_t bi = 0; bi < cx.TL->blk.size(); ++bi) {
@@ -885,69 +907,76 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
       }
       ends.push_back(out.size());
     }
-  };
-  // host threads over contiguous term ranges
-  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (terms.size() < 256) nth = 1;
-  std::vector<std::vector<Entry>> parts(nth);
-  std::vector<std::vector<size_t>> part_ends(nth);
-  std::vector<size_t> t_begin(nth + 1, terms.size());
-  {
-    const size_t per = (terms.size() + nth - 1) / nth;
-    for (unsigned w = 0; w < nth; ++w) t_begin[w] = std::min(terms.size(), w * per);
-    if (nth == 1) {
-      generate(0, terms.size(), parts[0], part_ends[0]);
-    } else {
-      std::vector<std::thread> th;
-      for (unsigned w = 0; w < nth; ++w)
-        th.emplace_back([&, w] { generate(t_begin[w], t_begin[w + 1], parts[w], part_ends[w]); });
-      for (auto& x : th) x.join();
-    }
-  }
-  // entry range of every term
-  std::vector<std::pair<const Entry*, const Entry*>> range(terms.size(), {nullptr, nullptr});
-  for (unsigned w = 0; w < nth; ++w) {
+    // entry range of every term of the chunk (out no longer grows)
     size_t prev = 0;
-    for (size_t k = 0; k < part_ends[w].size(); ++k) {
-      const Entry* base = parts[w].data();
-      range[t_begin[w] + k] = {base + prev, base + part_ends[w][k]};
-      prev = part_ends[w][k];
+    for (size_t k = 0; k < ends.size(); ++k) {
+      range[t0 + k] = {out.data() + prev, out.data() + ends[k]};
+      prev = ends[k];
     }
+  });
+  // terms with segments grouped by target (targets in key order, terms in
+  // term order within a target)
+  std::vector<uint32_t> tord;
+  for (size_t i = 0; i < nterm; ++i)
+    if (ctx[i].dst && range[i].first != range[i].second) tord.push_back((uint32_t)i);
+  std::stable_sort(tord.begin(), tord.end(),
+                   [&](uint32_t a, uint32_t b) { return terms[a].first < terms[b].first; });
+  std::vector<std::pair<size_t, size_t>> tgt;  // [begin, end) of a target's terms in tord
+  for (size_t k = 0; k < tord.size();) {
+    size_t j = k + 1;
+    while (j < tord.size() && !(terms[tord[k]].first < terms[tord[j]].first)) ++j;
+    tgt.push_back({k, j});
+    k = j;
   }
-  // terms of each target, in term order
-  std::map<OpKey, std::vector<size_t>> by_target;
-  for (size_t i = 0; i < terms.size(); ++i)
-    if (ctx[i].dst && range[i].first != range[i].second) by_target[terms[i].first].push_back(i);
+  // the segments of one target ordered by destination sub-block with a
+  // counting sort (stable: term order within a sub-block); target chunks in
+  // parallel, concatenated in target order
+  const size_t tchunk = std::max<size_t>(1, tgt.size() / (4 * host_threads()) + 1);
+  const size_t ntchunk = (tgt.size() + tchunk - 1) / tchunk;
+  std::vector<std::vector<PlaceGroup>> cgroups(ntchunk);
+  std::vector<std::vector<PlaceSeg>> csegs(ntchunk);
+  host_parallel_for(ntchunk, [&](size_t c) {
+    std::vector<uint32_t> count;
+    std::vector<const Entry*> order;
+    auto& groups = cgroups[c];
+    auto& segs = csegs[c];
+    for (size_t g = c * tchunk; g < std::min(tgt.size(), (c + 1) * tchunk); ++g) {
+      const LayoutIndex& LI = *ctx[tord[tgt[g].first]].LI;
+      count.assign(LI.total + 1, 0);
+      size_t ne = 0;
+      for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
+        for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) {
+          ++count[x->li + 1];
+          ++ne;
+        }
+      for (size_t k = 1; k <= LI.total; ++k) count[k] += count[k - 1];
+      order.assign(ne, nullptr);
+      for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
+        for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) order[count[x->li]++] = x;
+      for (size_t k = 0; k < ne;) {
+        size_t j = k;
+        PlaceGroup pg;
+        pg.dst = order[k]->d;
+        pg.rows = order[k]->rows;
+        pg.cols = order[k]->cols;
+        pg.ld = order[k]->ld;
+        pg.seg_begin = (int)segs.size();
+        while (j < ne && order[j]->li == order[k]->li) segs.push_back(order[j++]->seg);
+        pg.seg_count = (int)(j - k);
+        groups.push_back(pg);
+        k = j;
+      }
+    }
+  });
   std::vector<PlaceGroup> groups;
   std::vector<PlaceSeg> segs;
-  std::vector<uint32_t> count;
-  std::vector<const Entry*> order;
-  for (auto& [tk, tlist] : by_target) {
-    const LayoutIndex& LI = *ctx[tlist.front()].LI;
-    count.assign(LI.total + 1, 0);
-    size_t ne = 0;
-    for (size_t i : tlist)
-      for (const Entry* x = range[i].first; x != range[i].second; ++x) {
-        ++count[x->li + 1];
-        ++ne;
-      }
-    for (size_t k = 1; k <= LI.total; ++k) count[k] += count[k - 1];
-    order.assign(ne, nullptr);
-    for (size_t i : tlist)
-      for (const Entry* x = range[i].first; x != range[i].second; ++x) order[count[x->li]++] = x;
-    for (size_t k = 0; k < ne;) {
-      size_t j = k;
-      PlaceGroup pg;
-      pg.dst = order[k]->d;
-      pg.rows = order[k]->rows;
-      pg.cols = order[k]->cols;
-      pg.ld = order[k]->ld;
-      pg.seg_begin = (int)segs.size();
-      while (j < ne && order[j]->li == order[k]->li) segs.push_back(order[j++]->seg);
-      pg.seg_count = (int)(j - k);
+  for (size_t c = 0; c < ntchunk; ++c) {
+    const int base = (int)segs.size();
+    for (PlaceGroup pg : cgroups[c]) {
+      pg.seg_begin += base;
       groups.push_back(pg);
-      k = j;
     }
+    segs.insert(segs.end(), csegs[c].begin(), csegs[c].end());
   }
   stats_.t_enl_place_host += now_s() - t_host;
   const double t_run = now_s();
@@ -1256,13 +1285,22 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   std::vector<std::vector<HpsiItem>> per(P.blk.size());
   std::vector<std::pair<int, HpsiItem>> diag_items;
   plan.flops = 0.0;
-  // operands resolved serially (layouts are created on demand), items of
-  // contiguous term ranges generated by host threads and merged in term
+  // operand layouts created first (the threaded pass only reads the layout
+  // maps); items of term chunks generated on the host pool and merged in term
   // order, so the item order (and the summation order) does not depend on
   // the number of threads
+  {
+    std::set<std::pair<int, int>> used;
+    for (const Term& t : terms) {
+      if (t.x.t != Operand::ID) used.insert({kind_dn(t.x.key.kind), t.x.key.k2});
+      if (t.y.t != Operand::ID) used.insert({kind_dn(t.y.key.kind), t.y.key.k2});
+    }
+    for (auto& [dn, k2] : used) {
+      lo.layout(dn, k2);
+      ro.layout(dn, k2);
+    }
+  }
   std::vector<std::pair<ResolvedOperand, ResolvedOperand>> rop(terms.size());
-  for (size_t i = 0; i < terms.size(); ++i)
-    rop[i] = {resolve(lo, nullptr, terms[i].x), resolve(ro, nullptr, terms[i].y)};
   struct Gen {
     std::vector<std::pair<int, HpsiItem>> items;  // (sigma block, item) in term order
     std::vector<std::pair<int, HpsiItem>> diag;
@@ -1274,6 +1312,7 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
       const Term& t = terms[ti];
       // rank k of the two factors of the scalar coupling [x^k (x) y^k]^0
       int kop = (t.x.t != Operand::ID) ? t.x.k2 : t.y.k2;
+      rop[ti] = {resolve(lo, nullptr, t.x), resolve(ro, nullptr, t.y)};
       const ResolvedOperand& rx = rop[ti].first;
       const ResolvedOperand& ry = rop[ti].second;
       if (!rx.ok || !ry.ok) continue;
@@ -1313,20 +1352,11 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
       }
     }
   };
-  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (terms.size() < 64) nth = 1;
-  std::vector<Gen> gens(nth);
-  if (nth == 1) {
-    generate(0, terms.size(), gens[0]);
-  } else {
-    std::vector<std::thread> th;
-    const size_t per_t = (terms.size() + nth - 1) / nth;
-    for (unsigned w = 0; w < nth; ++w) {
-      size_t t0 = std::min(terms.size(), w * per_t), t1 = std::min(terms.size(), t0 + per_t);
-      th.emplace_back([&, t0, t1, w] { generate(t0, t1, gens[w]); });
-    }
-    for (auto& x : th) x.join();
-  }
+  const size_t nterm = terms.size();
+  const size_t chunk = std::max<size_t>(4, nterm / (8 * host_threads()) + 1);
+  const size_t nchunk = (nterm + chunk - 1) / chunk;
+  std::vector<Gen> gens(nchunk);
+  host_parallel_for(nchunk, [&](size_t c) { generate(c * chunk, std::min(nterm, (c + 1) * chunk), gens[c]); });
   for (auto& g : gens) {
     for (auto& [pi, it] : g.items) per[pi].push_back(it);
     diag_items.insert(diag_items.end(), g.diag.begin(), g.diag.end());

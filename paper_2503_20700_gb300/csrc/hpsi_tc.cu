@@ -461,115 +461,6 @@ __global__ void split_kernel(const SplitJob* __restrict__ jobs, int n) {
 
 }  // namespace
 
-void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
-                     const std::function<void*(size_t)>& alloc, TcPlan& plan) {
-  plan = TcPlan();
-  auto r32 = [](int x) { return (x + 31) & ~31; };
-  // distinct operands: (src, trans, rows, cols, ld) -> job; plane offsets in floats
-  struct Key {
-    const double* src;
-    int trans, rows, cols, ld;
-    bool operator==(const Key& o) const {
-      return src == o.src && trans == o.trans && rows == o.rows && cols == o.cols && ld == o.ld;
-    }
-  };
-  struct KeyHash {
-    size_t operator()(const Key& k) const {
-      size_t h = std::hash<const void*>()(k.src);
-      for (int v : {k.trans, k.rows, k.cols, k.ld}) h = h * 1000003u ^ (size_t)v;
-      return h;
-    }
-  };
-  std::unordered_map<Key, int, KeyHash> index;
-  std::vector<SplitJob> jobs;
-  std::vector<std::pair<size_t, size_t>> offs;
-  std::vector<int> is_psi;
-  size_t floats = 0;
-  auto want = [&](const double* src, int trans, int rows, int cols, int ld, bool psi) -> int {
-    const Key key{src, trans, rows, cols, ld};
-    auto it = index.find(key);
-    if (it != index.end()) return it->second;
-    SplitJob j{src, rows, cols, ld, trans, nullptr, nullptr, r32(cols)};
-    size_t plane = (size_t)rows * j.ldd;
-    offs.push_back({floats, floats + plane});
-    floats += 2 * plane;
-    floats = (floats + 3) & ~size_t(3);  // 16-byte alignment of every plane
-    index.emplace(key, (int)jobs.size());
-    jobs.push_back(j);
-    is_psi.push_back(psi);
-    return (int)jobs.size() - 1;
-  };
-  struct Ref {
-    int a, p, b;
-  };
-  std::vector<Ref> refs(items.size(), Ref{-1, -1, -1});
-  for (auto& bk : blocks)
-    for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
-      const HpsiItem& it = items[i];
-      if (it.A) refs[i].a = want(it.A, it.transA, bk.m, it.ka, it.lda, false);
-      if (it.A) refs[i].p = want(it.P, 1, it.kb, it.ka, it.ldp, true);
-      if (it.B) refs[i].b = want(it.B, it.transB, bk.n, it.kb, it.ldb, false);
-    }
-  float* pool = nullptr;
-  if (floats > 0) pool = (float*)alloc(floats * sizeof(float));
-  plan.pool_bytes = floats * sizeof(float);
-  for (size_t j = 0; j < jobs.size(); ++j) {
-    jobs[j].hi = pool + offs[j].first;
-    jobs[j].lo = pool + offs[j].second;
-    (is_psi[j] ? plan.psi_jobs : plan.op_jobs).push_back(jobs[j]);
-  }
-  auto mat = [&](int j) {
-    TcMat m;
-    if (j >= 0) {
-      m.hi = jobs[j].hi;
-      m.lo = jobs[j].lo;
-      m.ld = jobs[j].ldd;
-    }
-    return m;
-  };
-  plan.items.resize(items.size());
-  for (size_t i = 0; i < items.size(); ++i) {
-    const HpsiItem& it = items[i];
-    TcItem t;
-    t.A = mat(refs[i].a);
-    t.Pt = mat(refs[i].p);
-    t.P = it.P;
-    t.ldp = it.ldp;
-    t.B = mat(refs[i].b);
-    t.ka = it.ka;
-    t.kb = it.kb;
-    t.alpha = it.alpha;
-    plan.items[i] = t;
-  }
-  // tasks: 128 x 256 tiles, items chunked so that a launch has a few waves
-  long long tile_items = 0;
-  for (auto& b : blocks)
-    tile_items += (long long)b.item_count * ((b.m + TM - 1) / TM) * ((b.n + TNMAX - 1) / TNMAX);
-  const int max_items = (int)std::max<long long>(4, tile_items / (3 * 152) + 1);
-  long long part = 0;
-  for (size_t b = 0; b < blocks.size(); ++b) {
-    const HpsiBlock& bk = blocks[b];
-    if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
-    int nch = (bk.item_count + max_items - 1) / max_items;
-    int per = (bk.item_count + nch - 1) / nch;
-    for (int r0 = 0; r0 < bk.m; r0 += TM)
-      for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
-        if (nch == 1) {
-          plan.tasks.push_back({(int)b, r0, c0, bk.item_begin, bk.item_count, -1});
-        } else {
-          plan.reds.push_back({(int)b, r0, c0, nch, part});
-          for (int c = 0; c < nch; ++c) {
-            int i0 = bk.item_begin + c * per;
-            int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
-            plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
-            part += (long long)TM * TNMAX;
-          }
-        }
-      }
-  }
-  plan.scratch = (size_t)part;
-}
-
 void split_launch(const SplitJob* jobs, int n, cudaStream_t st) {
   if (n <= 0) return;
   split_kernel<<<std::min(n, 152 * 8), 256, 0, st>>>(jobs, n);
