@@ -288,12 +288,8 @@ __global__ void __launch_bounds__(128, 1)
   produce(cur, it_cur, 0);
   if (has1) produce(n1, it_n1, 1);
   for (;;) {
-    // prefetch block b+2 into the slot of block b-1 once its MMAs are done
-    if (has2) {
-      wait_block(b - 1);
-      produce(n2, it_n2, (b + 2) % NSLOT);
-      asm volatile("cp.async.wait_group 2;");
-    } else if (has1) {
+    // copies in flight: blocks b and b+1 (b+2 is issued after the MMAs of b)
+    if (has1) {
       asm volatile("cp.async.wait_group 1;");
     } else {
       asm volatile("cp.async.wait_group 0;");
@@ -385,6 +381,12 @@ __global__ void __launch_bounds__(128, 1)
     if (cur.stage == 2) {
       if (cur.half == 0) s_started = true;
       else s_started_b = true;
+    }
+    // prefetch block b+2 into the slot of block b-1 once its MMAs are done;
+    // the MMAs of b are already queued behind them
+    if (has2) {
+      wait_block(b - 1);
+      produce(n2, it_n2, (b + 2) % NSLOT);
     }
     if (!has1) break;
     if (n1.ii != cur.ii && ((n1.ii - tk.it_begin) % kDrainItems) == 0 && s_started) {

@@ -12,7 +12,9 @@
 //   stage 1:  X' = op(A)(tile rows, :) P(:, j)           (TMEM, 128 x 64)
 //   X = alpha X'  ->  hi/lo TF32 planes in shared memory
 //   stage 2:  S += X op(B)(tile cols, j)^T               (TMEM, 128 x N)
-// with 16-byte cp.async copies double-buffered against the MMAs.
+// with 16-byte cp.async copies in three slots: the MMAs of a k-block are
+// issued once its copies land, then the copies two blocks ahead refill the
+// slot whose MMAs precede them.
 #pragma once
 #include <cuda_runtime.h>
 
