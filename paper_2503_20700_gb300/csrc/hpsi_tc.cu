@@ -119,19 +119,28 @@ __device__ __forceinline__ uint32_t word_off(int r, int k, uint32_t sbo) {
   return core_off(r, k & ~3, sbo) + (uint32_t)(k & 3) * 4;
 }
 
-// copies rows [row0, row0 + nrows) x cols [k0, k0 + 32) of a split matrix
-// (valid rows < rmax) into a K-major tile (both planes)
+// copies rows [row0, min(row0 + nrows, rmax)) x cols [k0, k0 + 32) of a
+// split matrix into a K-major tile (both planes).  A thread keeps one 16-byte
+// column chunk and steps 16 rows at a time.  Tile rows at or beyond rmax are
+// not copied and keep earlier slot contents (zero at kernel start, later
+// finite operand values): rows of A or B there only reach output rows or
+// columns outside the block, which are never stored, and rows of P^T beyond
+// kb only reach columns of X that meet the zero padding of B's planes (or
+// zeros of a generated identity tile).
 __device__ __forceinline__ void load_tile(uint32_t dhi, uint32_t dlo, const TcMat& m, int row0, int nrows, int rmax,
                                           int k0, int tid) {
-  const int chunks = nrows * 8;
-  for (int e = tid; e < chunks; e += 128) {
-    int r = e >> 3, kc = (e & 7) * 4;
-    int gr = row0 + r;
-    bool ok = gr < rmax;
-    size_t off = ok ? (size_t)gr * m.ld + k0 + kc : 0;
-    uint32_t o = core_off(r, kc, SBO32);
-    cp16(dhi + o, m.hi + off, ok ? 16 : 0);
-    cp16(dlo + o, m.lo + off, ok ? 16 : 0);
+  const int rows = min(nrows, rmax - row0);
+  const int kc = (tid & 7) * 4;
+  int r = tid >> 3;
+  if (r >= rows) return;
+  const size_t step = (size_t)16 * m.ld;
+  size_t off = (size_t)(row0 + r) * m.ld + k0 + kc;
+  uint32_t o = core_off(r, kc, SBO32);
+  for (; r < rows; r += 16) {  // 16 rows = two 8-row core-matrix groups
+    cp16(dhi + o, m.hi + off, 16);
+    cp16(dlo + o, m.lo + off, 16);
+    off += step;
+    o += 2 * SBO32;
   }
 }
 
@@ -201,6 +210,9 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  // slots start at zero: tile rows that are never copied hold finite values
+  for (int e = tid; e < NSLOT * SLOT / 16; e += 128)
+    reinterpret_cast<uint4*>(smraw + OFF_SLOT)[e] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int i = 0; i < NSLOT; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
