@@ -255,13 +255,17 @@ __global__ void __launch_bounds__(128, 1)
     if (!wait_bar(&bar[b % NSLOT], (uint32_t)((b / NSLOT) & 1))) abort_flag = 1;
   };
 
-  // S (FP32, TMEM) is added to the task's float64 output every kDrainItems
+  // S (FP32, TMEM) is added to the task's partial tile every kDrainItems
   // items and at the end, so FP32 accumulation spans a few items only.
-  // The first drain into a private partial tile stores, later ones add.
+  // The first drain stores, later ones add.
   bool s_started = false, s_started_b = false;  // first / second column half written since the last drain
   bool drained = false;
   auto drain = [&]() {
+    // the task's partial tile holds float pairs (hi, lo): a TwoSum (Knuth)
+    // adds each FP32 value of S with its rounding error kept in lo, on the
+    // FP32 pipe (the float64 conversion happens once, in the reduction)
     const int r = tid;
+    float2* d = reinterpret_cast<float2*>(scratch + tk.part) + (size_t)r * TNMAX;
     for (int c0 = 0; c0 < N; c0 += 16) {
       float v[16];
       if (s_started) {
@@ -270,15 +274,17 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = 0.0f;
       }
+      if (!drained) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        int c = c0 + j;
-        if (tk.part >= 0) {
-          double* d = scratch + tk.part + (long long)r * TNMAX + c;
-          *d = drained ? *d + (double)v[j] : (double)v[j];
-        } else {
-          int gr = tk.r0 + r, gc = tk.c0 + c;
-          if (gr < bk.m && c < nvalid) bk.C[(size_t)gr * bk.ldc + gc] += (double)v[j];
+        for (int j = 0; j < 16; ++j) d[c0 + j] = make_float2(v[j], 0.0f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float2 a = d[c0 + j];
+          const float sum = __fadd_rn(a.x, v[j]);
+          const float bv = __fsub_rn(sum, a.x);
+          const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(v[j], bv));
+          d[c0 + j] = make_float2(sum, __fadd_rn(a.y, err));
         }
       }
     }
@@ -452,8 +458,12 @@ __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiR
     int r = e / TNMAX, c = e % TNMAX;
     int gr = rd.r0 + r;
     if (gr >= bk.m || c >= nvalid) continue;
+    const float2* part = reinterpret_cast<const float2*>(scratch + rd.part0) + e;
     double acc = 0.0;
-    for (int p = 0; p < rd.nparts; ++p) acc += scratch[rd.part0 + (long long)p * TM * TNMAX + e];
+    for (int p = 0; p < rd.nparts; ++p) {
+      const float2 v = part[(long long)p * TM * TNMAX];
+      acc += (double)v.x + (double)v.y;
+    }
     bk.C[(size_t)gr * bk.ldc + rd.c0 + c] += acc;
   }
 }

@@ -61,8 +61,8 @@ struct TcPlan {
   std::vector<SplitJob> psi_jobs;  // psi blocks (run before every product)
   std::vector<TcItem> items;
   std::vector<HpsiTask> tasks;     // (block, r0, c0, items, partial offset)
-  std::vector<HpsiReduce> reds;    // partial tiles are kTcTileM x kTcTileN
-  size_t scratch = 0;              // doubles of partial tiles
+  std::vector<HpsiReduce> reds;    // one per tile: its chunks' partial tiles into sigma
+  size_t scratch = 0;              // 8-byte words of partial tiles (kTcTileM x kTcTileN float pairs per task)
   size_t pool_bytes = 0;           // split planes
 };
 

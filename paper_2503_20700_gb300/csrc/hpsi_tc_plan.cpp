@@ -181,18 +181,16 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
     int nch = (bk.item_count + max_items - 1) / max_items;
     int per = (bk.item_count + nch - 1) / nch;
+    // every chunk owns a partial tile (float pairs); the reduction adds the
+    // chunks of a tile into sigma in float64
     for (int r0 = 0; r0 < bk.m; r0 += TM)
       for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
-        if (nch == 1) {
-          plan.tasks.push_back({(int)b, r0, c0, bk.item_begin, bk.item_count, -1});
-        } else {
-          plan.reds.push_back({(int)b, r0, c0, nch, part});
-          for (int c = 0; c < nch; ++c) {
-            int i0 = bk.item_begin + c * per;
-            int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
-            plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
-            part += (long long)TM * TNMAX;
-          }
+        plan.reds.push_back({(int)b, r0, c0, nch, part});
+        for (int c = 0; c < nch; ++c) {
+          int i0 = bk.item_begin + c * per;
+          int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
+          plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
+          part += (long long)TM * TNMAX;
         }
       }
   }
