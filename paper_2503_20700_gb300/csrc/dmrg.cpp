@@ -928,9 +928,10 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     tgt.push_back({k, j});
     k = j;
   }
-  // the segments of one target ordered by destination sub-block with a
-  // counting sort (stable: term order within a sub-block); target chunks in
-  // parallel, concatenated in target order
+  // the segments of one target ordered by destination sub-block, stably
+  // (term order within a sub-block): a counting sort when the target has
+  // many segments for its layout, else a comparison sort of its few
+  // segments; target chunks in parallel, concatenated in target order
   const size_t tchunk = std::max<size_t>(1, tgt.size() / (4 * host_threads()) + 1);
   const size_t ntchunk = (tgt.size() + tchunk - 1) / tchunk;
   std::vector<std::vector<PlaceGroup>> cgroups(ntchunk);
@@ -942,17 +943,22 @@ void Engine::place_terms(const Block& b, const OpSet* tmp, Block& e,
     auto& segs = csegs[c];
     for (size_t g = c * tchunk; g < std::min(tgt.size(), (c + 1) * tchunk); ++g) {
       const LayoutIndex& LI = *ctx[tord[tgt[g].first]].LI;
-      count.assign(LI.total + 1, 0);
       size_t ne = 0;
-      for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
-        for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) {
-          ++count[x->li + 1];
-          ++ne;
-        }
-      for (size_t k = 1; k <= LI.total; ++k) count[k] += count[k - 1];
-      order.assign(ne, nullptr);
-      for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
-        for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) order[count[x->li]++] = x;
+      for (size_t k = tgt[g].first; k < tgt[g].second; ++k) ne += range[tord[k]].second - range[tord[k]].first;
+      order.clear();
+      if (4 * ne >= LI.total) {
+        count.assign(LI.total + 1, 0);
+        for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
+          for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) ++count[x->li + 1];
+        for (size_t k = 1; k <= LI.total; ++k) count[k] += count[k - 1];
+        order.assign(ne, nullptr);
+        for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
+          for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) order[count[x->li]++] = x;
+      } else {
+        for (size_t k = tgt[g].first; k < tgt[g].second; ++k)
+          for (const Entry* x = range[tord[k]].first; x != range[tord[k]].second; ++x) order.push_back(x);
+        std::stable_sort(order.begin(), order.end(), [](const Entry* a, const Entry* b) { return a->li < b->li; });
+      }
       for (size_t k = 0; k < ne;) {
         size_t j = k;
         PlaceGroup pg;

@@ -1,12 +1,11 @@
 // SU(2) coefficients (Racah closed forms) and the explicit one-site algebra.
 #include "su2.hpp"
 
+#include <algorithm>
 #include <cstdint>
-#include <unordered_map>
-
 #include <cstdlib>
 #include <mutex>
-#include <unordered_map>
+#include <vector>
 
 namespace dmrg {
 
@@ -48,30 +47,78 @@ double log_delta(int a, int b, int c) {
   return 0.5 * (log_factorial((a + b - c) / 2) + log_factorial((a - b + c) / 2) +
                 log_factorial((-a + b + c) / 2) - log_factorial((a + b + c) / 2 + 1));
 }
-struct Key6 {
-  int v[6];
-  bool operator==(const Key6& o) const {
-    for (int i = 0; i < 6; ++i) if (v[i] != o.v[i]) return false;
-    return true;
+// Memo of coefficients under a packed integer key: open addressing with
+// linear probing, at most half full, one table per thread.  The planners ask
+// for the same few thousand coefficients millions of times.
+class FlatMemo {
+ public:
+  bool find(uint64_t key, double& v) const {
+    if (n_ == 0) return false;
+    for (size_t h = mix(key) & mask_;; h = (h + 1) & mask_) {
+      if (!used_[h]) return false;
+      if (keys_[h] == key) {
+        v = vals_[h];
+        return true;
+      }
+    }
   }
-};
-struct Hash6 {
-  size_t operator()(const Key6& k) const {
-    size_t h = 0;
-    for (int i = 0; i < 6; ++i) h = h * 131 + (size_t)(k.v[i] + 7);
-    return h;
+  void put(uint64_t key, double v) {
+    if (2 * (n_ + 1) > keys_.size()) grow();
+    size_t h = mix(key) & mask_;
+    while (used_[h] && keys_[h] != key) h = (h + 1) & mask_;
+    if (!used_[h]) ++n_;
+    used_[h] = 1;
+    keys_[h] = key;
+    vals_[h] = v;
   }
+
+ private:
+  static uint64_t mix(uint64_t x) {
+    x ^= x >> 31;
+    x *= 0x9e3779b97f4a7c15ull;
+    return x ^ (x >> 29);
+  }
+  void grow() {
+    std::vector<uint64_t> k = std::move(keys_);
+    std::vector<double> v = std::move(vals_);
+    std::vector<uint8_t> u = std::move(used_);
+    const size_t cap = std::max<size_t>(1024, 2 * k.size());
+    keys_.assign(cap, 0);
+    vals_.assign(cap, 0.0);
+    used_.assign(cap, 0);
+    mask_ = cap - 1;
+    n_ = 0;
+    for (size_t i = 0; i < k.size(); ++i)
+      if (u[i]) put(k[i], v[i]);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<double> vals_;
+  std::vector<uint8_t> used_;
+  size_t n_ = 0, mask_ = 0;
 };
+
+// packs small non-negative arguments (doubled spins below 128), 7 bits each
+template <size_t K>
+bool pack7(const int (&v)[K], uint64_t& key) {
+  key = 0;
+  for (int x : v) {
+    if (x < 0 || x >= 128) return false;
+    key = (key << 7) | (uint64_t)x;
+  }
+  return true;
+}
 }  // namespace
 
 // Racah's closed form for {a b c; d e f} (doubled arguments).
 double wigner6j(int a, int b, int c, int d, int e, int f) {
   if (!triangle(a, b, c) || !triangle(a, e, f) || !triangle(d, b, f) || !triangle(d, e, c))
     return 0.0;
-  static thread_local std::unordered_map<Key6, double, Hash6> cache;
-  Key6 key{{a, b, c, d, e, f}};
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
+  static thread_local FlatMemo cache;
+  const int args[6] = {a, b, c, d, e, f};
+  uint64_t key;
+  const bool packed = pack7(args, key);
+  double hit;
+  if (packed && cache.find(key, hit)) return hit;
   double ld = log_delta(a, b, c) + log_delta(a, e, f) + log_delta(d, b, f) + log_delta(d, e, c);
   int t1 = (a + b + c) / 2, t2 = (a + e + f) / 2, t3 = (d + b + f) / 2, t4 = (d + e + c) / 2;
   int u1 = (a + b + d + e) / 2, u2 = (b + c + e + f) / 2, u3 = (c + a + f + d) / 2;
@@ -85,7 +132,7 @@ double wigner6j(int a, int b, int c, int d, int e, int f) {
     double term = std::exp(lt + ld);
     s += (t & 1) ? -term : term;
   }
-  cache.emplace(key, s);
+  if (packed) cache.put(key, s);
   return s;
 }
 
@@ -108,20 +155,14 @@ double tensor_product_coef(int j1p, int j1, int kx, int j2p, int j2, int ky, int
   // memoised: the blocking and RDM planners ask for the same few thousand
   // combinations millions of times; doubled spins here are far below 128
   const int v[9] = {j1p, j1, kx, j2p, j2, ky, Jp, J, k};
-  uint64_t key = 0;
-  bool packable = true;
-  for (int x : v) {
-    if (x < 0 || x >= 128) packable = false;
-    key = (key << 7) | (uint64_t)(x & 127);
-  }
-  static thread_local std::unordered_map<uint64_t, double> cache;
-  if (packable) {
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-  }
+  uint64_t key;
+  const bool packed = pack7(v, key);
+  static thread_local FlatMemo cache;
+  double hit;
+  if (packed && cache.find(key, hit)) return hit;
   double n9 = wigner9j(j1p, j1, kx, j2p, j2, ky, Jp, J, k);
   double r = n9 == 0.0 ? 0.0 : std::sqrt((J + 1.0) * (k + 1.0) * (j1p + 1.0) * (j2p + 1.0)) * n9;
-  if (packable) cache.emplace(key, r);
+  if (packed) cache.put(key, r);
   return r;
 }
 
