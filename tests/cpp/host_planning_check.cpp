@@ -1,0 +1,220 @@
+// Checks of the host planning code on the CPU (no device calls):
+//  - host_parallel_for runs every index exactly once, also when nested and
+//    after an exception, and rethrows the first exception;
+//  - hpsi_tc_prepare (tcgen05 H_eff psi planning) against properties any
+//    correct plan has: each operand of each item refers to a split job with
+//    exactly that operand's (src, trans, rows, cols, ld); jobs are distinct
+//    and numbered in first-occurrence order over (items in block order;
+//    roles A, P (non-identity A), B); planes are disjoint, 16-byte aligned,
+//    rows x round32(cols) floats; the chunks of every 128 x 256 tile cover
+//    its items once, in order, each chunk with its own partial tile, and one
+//    reduction per tile names all of its chunks.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <random>
+#include <set>
+#include <stdexcept>
+#include <tuple>
+#include <vector>
+
+#include "host_pool.hpp"
+#include "hpsi_tc.cuh"
+
+using namespace dmrg;
+
+static int fails = 0;
+#define CHECK(c)                                                   \
+  do {                                                             \
+    if (!(c)) {                                                    \
+      std::printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c);     \
+      ++fails;                                                     \
+    }                                                              \
+  } while (0)
+
+static void check_pool() {
+  for (int rep = 0; rep < 300; ++rep) {
+    const size_t n = 1 + rep % 131;
+    std::vector<int> hit(n, 0);
+    host_parallel_for(n, [&](size_t i) {
+      hit[i]++;
+      host_parallel_for(2, [](size_t) {});  // nested: runs serially
+    });
+    for (size_t i = 0; i < n; ++i) CHECK(hit[i] == 1);
+  }
+  bool threw = false;
+  try {
+    host_parallel_for(64, [](size_t i) {
+      if (i == 7) throw std::runtime_error("planned");
+    });
+  } catch (const std::runtime_error&) {
+    threw = true;
+  }
+  CHECK(threw);
+  std::vector<int> hit(500, 0);
+  host_parallel_for(hit.size(), [&](size_t i) { hit[i]++; });
+  for (int x : hit) CHECK(x == 1);
+  CHECK(host_threads() >= 1);
+}
+
+using Key = std::tuple<const double*, int, int, int, int>;
+
+static void check_plan(unsigned seed) {
+  std::mt19937 rng(seed);
+  const int nblk = 3 + rng() % 12;
+  std::vector<int> dims(nblk);
+  for (auto& d : dims) d = 1 + rng() % 300;
+  std::vector<HpsiBlock> blocks;
+  std::vector<HpsiItem> items;
+  const double* op = reinterpret_cast<const double*>(uintptr_t(1) << 32);
+  const double* ps = reinterpret_cast<const double*>(uintptr_t(9) << 32);
+  for (int b = 0; b < nblk; ++b) {
+    HpsiBlock hb{};
+    hb.m = dims[b];
+    hb.n = dims[(b * 5 + 1) % nblk];
+    hb.ldc = hb.n;
+    hb.item_begin = (int)items.size();
+    const int cnt = (b % 4 == 3) ? 0 : (int)(rng() % 700);
+    for (int k = 0; k < cnt; ++k) {
+      HpsiItem it{};
+      const int q = rng() % nblk;
+      const int ka = dims[q], kb = dims[(q * 3) % nblk];
+      const int oa = rng() % 40, ob = rng() % 40;
+      const bool ida = rng() % 6 == 0, idb = !ida && rng() % 6 == 0;
+      it.A = ida ? nullptr : op + ((size_t)oa * 64 + q) * 4096 + b % 3;
+      it.lda = ka;
+      it.transA = oa % 2;
+      it.P = ps + (size_t)q * 4096;
+      it.ldp = kb;
+      it.B = idb ? nullptr : op + ((size_t)ob * 64 + q) * 4096 + 7;
+      it.ldb = kb;
+      it.transB = ob % 2;
+      it.ka = ida ? hb.m : ka;
+      it.kb = idb ? hb.n : kb;
+      it.alpha = 0.25 * (k + 1);
+      items.push_back(it);
+    }
+    hb.item_count = cnt;
+    blocks.push_back(hb);
+  }
+  char* const pool = reinterpret_cast<char*>(uintptr_t(0x40) << 32);
+  size_t pool_bytes = 0;
+  TcPlan plan;
+  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { pool_bytes = bytes; return (void*)pool; }, plan);
+  CHECK(plan.pool_bytes == pool_bytes);
+  // expected jobs: first occurrences in reference order
+  std::map<Key, int> first;
+  std::vector<Key> order;
+  std::vector<int> is_psi;
+  auto note = [&](const Key& k, bool psi) {
+    if (first.emplace(k, (int)order.size()).second) {
+      order.push_back(k);
+      is_psi.push_back(psi);
+    }
+  };
+  for (auto& bk : blocks)
+    for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
+      const HpsiItem& it = items[i];
+      if (it.A) note(Key{it.A, it.transA, bk.m, it.ka, it.lda}, false);
+      if (it.A) note(Key{it.P, 1, it.kb, it.ka, it.ldp}, true);
+      if (it.B) note(Key{it.B, it.transB, bk.n, it.kb, it.ldb}, false);
+    }
+  std::vector<SplitJob> jobs_op, jobs_psi;
+  for (size_t j = 0; j < order.size(); ++j) {
+    SplitJob sj{};
+    std::tie(sj.src, sj.trans, sj.rows, sj.cols, sj.ld) = order[j];
+    (is_psi[j] ? jobs_psi : jobs_op).push_back(sj);
+  }
+  CHECK(plan.op_jobs.size() == jobs_op.size());
+  CHECK(plan.psi_jobs.size() == jobs_psi.size());
+  std::map<const float*, Key> by_plane;
+  std::vector<std::pair<size_t, size_t>> spans;
+  auto check_jobs = [&](const std::vector<SplitJob>& got, const std::vector<SplitJob>& want) {
+    for (size_t j = 0; j < std::min(got.size(), want.size()); ++j) {
+      const SplitJob& g = got[j];
+      CHECK(g.src == want[j].src && g.trans == want[j].trans && g.rows == want[j].rows &&
+            g.cols == want[j].cols && g.ld == want[j].ld);
+      CHECK(g.ldd == ((g.cols + 31) & ~31));
+      const size_t bytes = (size_t)g.rows * g.ldd * sizeof(float);
+      for (const float* p : {g.hi, g.lo}) {
+        const size_t off = (size_t)((const char*)p - pool);
+        CHECK(((uintptr_t)p & 15) == 0);
+        CHECK(off + bytes <= pool_bytes);
+        spans.push_back({off, off + bytes});
+      }
+      by_plane[g.hi] = Key{g.src, g.trans, g.rows, g.cols, g.ld};
+    }
+  };
+  check_jobs(plan.op_jobs, jobs_op);
+  check_jobs(plan.psi_jobs, jobs_psi);
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); ++i) CHECK(spans[i].first >= spans[i - 1].second);
+  // items
+  CHECK(plan.items.size() == items.size());
+  for (auto& bk : blocks)
+    for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
+      const HpsiItem& it = items[i];
+      const TcItem& t = plan.items[i];
+      CHECK(t.P == it.P && t.ldp == it.ldp && t.ka == it.ka && t.kb == it.kb && t.alpha == it.alpha);
+      auto refers = [&](const TcMat& m, const Key& k) {
+        auto f = by_plane.find(m.hi);
+        return f != by_plane.end() && f->second == k && m.ld == ((std::get<3>(k) + 31) & ~31);
+      };
+      if (it.A) {
+        CHECK(refers(t.A, Key{it.A, it.transA, bk.m, it.ka, it.lda}));
+        CHECK(refers(t.Pt, Key{it.P, 1, it.kb, it.ka, it.ldp}));
+      } else {
+        CHECK(t.A.hi == nullptr && t.Pt.hi == nullptr);
+      }
+      if (it.B) CHECK(refers(t.B, Key{it.B, it.transB, bk.n, it.kb, it.ldb}));
+      else CHECK(t.B.hi == nullptr);
+    }
+  // tiles, chunks, partial tiles, reductions
+  std::map<std::tuple<int, int, int>, std::vector<const HpsiTask*>> chunks;
+  std::set<long long> parts;
+  for (const HpsiTask& t : plan.tasks) {
+    chunks[{t.block, t.r0, t.c0}].push_back(&t);
+    CHECK(t.part >= 0 && t.part % ((long long)kTcTileM * kTcTileN) == 0);
+    CHECK(parts.insert(t.part).second);
+    CHECK((size_t)t.part + (size_t)kTcTileM * kTcTileN <= plan.scratch);
+  }
+  size_t tiles = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const HpsiBlock& bk = blocks[b];
+    if (bk.item_count == 0) continue;
+    for (int r0 = 0; r0 < bk.m; r0 += kTcTileM)
+      for (int c0 = 0; c0 < bk.n; c0 += kTcTileN) {
+        ++tiles;
+        auto& v = chunks[{b, r0, c0}];
+        int next = bk.item_begin;
+        for (const HpsiTask* t : v) {
+          CHECK(t->it_begin == next && t->it_count > 0);
+          next += t->it_count;
+        }
+        CHECK(next == bk.item_begin + bk.item_count);
+        int nred = 0;
+        for (const HpsiReduce& rd : plan.reds)
+          if (rd.block == b && rd.r0 == r0 && rd.c0 == c0) {
+            ++nred;
+            CHECK(rd.nparts == (int)v.size());
+            CHECK(!v.empty() && rd.part0 == v.front()->part);
+            for (size_t k = 0; k < v.size(); ++k)
+              CHECK(v[k]->part == rd.part0 + (long long)k * kTcTileM * kTcTileN);
+          }
+        CHECK(nred == 1);
+      }
+  }
+  CHECK(chunks.size() == tiles && plan.reds.size() == tiles);
+}
+
+int main() {
+  check_pool();
+  for (unsigned s = 1; s <= 12; ++s) check_plan(s);
+  if (fails) {
+    std::printf("%d checks failed\n", fails);
+    return 1;
+  }
+  std::printf("host planning checks passed\n");
+  return 0;
+}
