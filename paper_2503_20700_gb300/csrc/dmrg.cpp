@@ -1425,7 +1425,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   stats_.t_plan_tasks += tp2 - tp1;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t ob = 0, oi = al(ob + blocks.size() * sizeof(HpsiBlock));
-  size_t oc = al(oi + items.size() * sizeof(HpsiItem));
+  // the tcgen05 path reads its own item descriptors only
+  size_t oc = al(oi + (tc ? 0 : items.size()) * sizeof(HpsiItem));
   size_t ot = al(oc + tp.items.size() * sizeof(TcItem));
   size_t orr = al(ot + tasks.size() * sizeof(HpsiTask));
   size_t oj = al(orr + reds.size() * sizeof(HpsiReduce));
@@ -1444,7 +1445,7 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   plan.n_psi_jobs = (int)tp.psi_jobs.size();
   plan.scratch = (double*)(d + os);
   if (!blocks.empty()) be_->copy_h2d(plan.d_blocks, blocks.data(), blocks.size() * sizeof(HpsiBlock));
-  if (!items.empty()) be_->copy_h2d(plan.d_items, items.data(), items.size() * sizeof(HpsiItem));
+  if (!tc && !items.empty()) be_->copy_h2d(plan.d_items, items.data(), items.size() * sizeof(HpsiItem));
   if (!tp.items.empty()) be_->copy_h2d(plan.d_tcitems, tp.items.data(), tp.items.size() * sizeof(TcItem));
   if (!tasks.empty()) be_->copy_h2d(plan.d_tasks, tasks.data(), tasks.size() * sizeof(HpsiTask));
   if (!reds.empty()) be_->copy_h2d(plan.d_reds, reds.data(), reds.size() * sizeof(HpsiReduce));
