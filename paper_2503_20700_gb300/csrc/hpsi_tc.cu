@@ -8,19 +8,18 @@
 // all in the canonical no-swizzle K-major layout (8-row x 16-byte core
 // matrices; 128 B between K-adjacent cores, 1 KB between 8-row groups for
 // 32-wide tiles, 2 KB for the 64-wide X).  TMEM: S in columns [0, 256), X' in
-// [256, 320).  The k-blocks of a task form one sequence; blocks b+1 and b+2
-// are in flight (cp.async into the other two slots) while the MMAs of block
-// b run; each slot has its own mbarrier (tcgen05.commit after the block's
-// MMAs) and every wait is bounded by 2 s of wall clock.
+// [256, 320).  The k-blocks of a task form one sequence: the MMAs of block b
+// are issued once its copies have landed (blocks b and b+1 are in flight),
+// then the copies of block b+2 refill the slot of block b-1 after its MMAs
+// completed.  Each slot has its own mbarrier (tcgen05.commit after the
+// block's MMAs) and every wait is bounded by 2 s of wall clock.  The FP32
+// accumulator S is drained into the task's partial tile of float pairs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
-#include <map>
 #include <stdexcept>
 #include <string>
-#include <tuple>
-#include <unordered_map>
 
 #include "hpsi_tc.cuh"
 
