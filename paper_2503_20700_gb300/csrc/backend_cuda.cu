@@ -23,6 +23,7 @@
 #include "gemm_split.cuh"
 #include "hpsi_fused.cuh"
 #include "hpsi_tc.cuh"
+#include "jacobi_plan.hpp"
 
 namespace dmrg {
 
@@ -229,7 +230,7 @@ __global__ void precond_kernel(double* __restrict__ y, const double* __restrict_
 // A and V in shared memory; g > 1: A and V in global memory, one group
 // barrier per round).
 constexpr int kMaxSweeps = 30;
-constexpr int kSmemN = 112;       // largest matrix of the shared-memory path
+constexpr int kSmemN = kJacSmemN;  // largest matrix of the shared-memory path
 constexpr int kJacThreads = 512;  // threads of a batched-launch CTA
 
 __host__ __device__ constexpr size_t jacobi_smem_bytes(int n) {
@@ -602,31 +603,6 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(const CoopEigh
   __shared__ int nrot, ok_s;
   if (ct.g == 1) jacobi_one(ct.t, sm, red, &nrot);
   else jacobi_group(ct, (int)blockIdx.x - ct.cta0, sm, red, &nrot, &ok_s, err);
-}
-
-// Modelled time of an n x n matrix on g CTAs, in SM clocks (FP64 rate of 2
-// operations a clock; a group barrier about 6000 clocks): the group sizes of
-// a batch minimise the slowest matrix.
-inline double jac_cost(int n, int g) {
-  const double rounds = std::max(1, ((n + 1) & ~1) - 1);
-  const double ops = 2.0 * (double)n * n;  // clocks of the FP64 work of a round on one SM
-  return rounds * (g == 1 ? ops + 1000.0 : 1.15 * ops / g + 6000.0);
-}
-
-// g[k] of batch tasks (descending n) start at their minimum; spare CTAs go to
-// the slowest matrix while that shortens it
-inline void jac_assign_groups(const std::vector<int>& n, std::vector<int>& g, int spare) {
-  while (spare > 0) {
-    size_t k = 0;
-    for (size_t i = 1; i < n.size(); ++i)
-      if (jac_cost(n[i], g[i]) > jac_cost(n[k], g[k])) k = i;
-    const int gmax = std::max(2, std::min(32, ((n[k] + 1) & ~1) / 2));
-    int ng = g[k] + 1;
-    while (ng <= gmax && ng - g[k] <= spare && jac_cost(n[k], ng) >= jac_cost(n[k], g[k])) ++ng;
-    if (ng > gmax || ng - g[k] > spare) break;
-    spare -= ng - g[k];
-    g[k] = ng;
-  }
 }
 
 // ------------------------------------------------------------------ backend
@@ -1017,25 +993,14 @@ class CudaBackend : public Backend {
     }
     std::vector<EighTask> order(tasks);
     std::stable_sort(order.begin(), order.end(), [](const EighTask& x, const EighTask& y) { return x.n > y.n; });
-    size_t i0 = 0;
-    while (i0 < order.size()) {
-      std::vector<int> ns, g;
-      int used = 0;
-      size_t i1 = i0;
-      while (i1 < order.size()) {
-        const int gmin = order[i1].n > kSmemN ? 2 : 1;
-        if (used + gmin > jac_cap) break;
-        ns.push_back(order[i1].n);
-        g.push_back(gmin);
-        used += gmin;
-        ++i1;
-      }
-      jac_assign_groups(ns, g, jac_cap - used);
+    std::vector<int> n_desc;
+    for (auto& t : order) n_desc.push_back(t.n);
+    for (const JacBatch& jb : jac_plan_batches(n_desc, jac_cap)) {
       std::vector<CoopEigh> ct;
       int ctas = 0;
-      for (size_t k = 0; k < ns.size(); ++k) {
-        ct.push_back({order[i0 + k], g[k], ctas, nullptr});
-        ctas += g[k];
+      for (size_t k = jb.begin; k < jb.end; ++k) {
+        ct.push_back({order[k], jb.g[k - jb.begin], ctas, nullptr});
+        ctas += jb.g[k - jb.begin];
       }
       std::vector<unsigned> bars(2 * ct.size(), 0u);
       std::vector<size_t> off;
@@ -1057,7 +1022,6 @@ class CudaBackend : public Backend {
       CK(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(ctas), dim3(kJacThreads), args, smem, st));
       if (rec) CK(cudaEventRecord(rec->b, st));
       ++launches;
-      i0 = i1;
     }
   }
 };

@@ -8,7 +8,11 @@
 //    roles A, P (non-identity A), B); planes are disjoint, 16-byte aligned,
 //    rows x round32(cols) floats; the chunks of every 128 x 256 tile cover
 //    its items once, in order, each chunk with its own partial tile, and one
-//    reduction per tile names all of its chunks.
+//    reduction per tile names all of its chunks;
+//  - jac_plan_batches (batched Jacobi eigensolver launches): every matrix in
+//    exactly one launch, in order; at most `cap` CTAs per launch; group sizes
+//    between the minimum (two above the shared-memory size) and the cap of
+//    the cost model; extra CTAs never make the slowest matrix slower.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
@@ -21,6 +25,7 @@
 
 #include "host_pool.hpp"
 #include "hpsi_tc.cuh"
+#include "jacobi_plan.hpp"
 
 using namespace dmrg;
 
@@ -208,8 +213,39 @@ static void check_plan(unsigned seed) {
   CHECK(chunks.size() == tiles && plan.reds.size() == tiles);
 }
 
+static void check_jacobi_batches(unsigned seed, int cap) {
+  std::mt19937 rng(seed);
+  const int count = 1 + rng() % 400;
+  std::vector<int> n(count);
+  for (auto& x : n) x = 1 + rng() % (seed % 2 ? 160 : 420);
+  std::sort(n.begin(), n.end(), [](int a, int b) { return a > b; });
+  const std::vector<JacBatch> batches = jac_plan_batches(n, cap);
+  size_t next = 0;
+  for (const JacBatch& b : batches) {
+    CHECK(b.begin == next && b.end > b.begin && b.g.size() == b.end - b.begin);
+    next = b.end;
+    int sum = 0;
+    double worst_min = 0.0, worst = 0.0;
+    for (size_t k = b.begin; k < b.end; ++k) {
+      const int g = b.g[k - b.begin];
+      const int gmin = n[k] > kJacSmemN ? 2 : 1;
+      const int gmax = std::max(2, std::min(32, ((n[k] + 1) & ~1) / 2));
+      CHECK(g >= gmin && g <= std::max(gmin, gmax));
+      sum += g;
+      worst_min = std::max(worst_min, jac_cost(n[k], gmin));
+      worst = std::max(worst, jac_cost(n[k], g));
+    }
+    CHECK(sum <= cap);
+    CHECK(worst <= worst_min);
+  }
+  CHECK(next == n.size());
+  for (int m = 2; m < 500; m += 7)
+    for (int g = 2; g < 32; ++g) CHECK(jac_cost(m, g + 1) < jac_cost(m, g));
+}
+
 int main() {
   check_pool();
+  for (unsigned s = 1; s <= 40; ++s) check_jacobi_batches(s, s % 3 ? 152 : 40);
   for (unsigned s = 1; s <= 12; ++s) check_plan(s);
   if (fails) {
     std::printf("%d checks failed\n", fails);

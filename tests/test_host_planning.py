@@ -1,7 +1,8 @@
-"""CPU checks of the host planning code: the persistent thread pool and the
+"""CPU checks of the host planning code: the persistent thread pool, the
 tcgen05 H_eff psi planner (operand deduplication, split-plane layout, tiles,
-item chunks and reductions), through a small C++ program compiled against
-the package sources (tests/cpp/host_planning_check.cpp).  No device calls."""
+item chunks and reductions) and the launch plan of the batched Jacobi
+eigensolver, through a small C++ program compiled against the package
+sources (tests/cpp/host_planning_check.cpp).  No device calls."""
 import os
 import shutil
 import subprocess
@@ -12,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2503_20700_gb300", "csrc")
 
 
-def test_host_pool_and_tcgen05_planner(tmp_path):
+def test_host_pool_planners(tmp_path):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no C++ compiler")
