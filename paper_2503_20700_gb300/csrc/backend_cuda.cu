@@ -689,6 +689,8 @@ class CudaBackend : public Backend {
     CK(cudaDeviceGetDefaultMemPool(&pool, dev));
     uint64_t thr = UINT64_MAX;
     CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    size_t fr = 0;
+    CK(cudaMemGetInfo(&fr, &total_mem));
   }
   ~CudaBackend() override {
     cudaStreamSynchronize(st);
@@ -727,6 +729,8 @@ class CudaBackend : public Backend {
     CK(cudaFreeAsync(p, st));
   }
   size_t bytes_in_use() const override { return used; }
+  size_t total_mem = 0;
+  size_t capacity() const override { return total_mem; }
   void memset0(void* p, size_t b) override { if (b) CK(cudaMemsetAsync(p, 0, b, st)); }
   void copy_d2d(void* d, const void* s, size_t b) override {
     if (b) CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToDevice, st));

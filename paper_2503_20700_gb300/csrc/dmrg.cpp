@@ -2065,8 +2065,16 @@ void Engine::build_initial_right() {
 
 double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   double t0 = now_s();
-  auto Le = enlarge(*L_[i], i);
-  auto Re = enlarge(*R_[n_ - i - 2], i + 1);
+  // the environment side may have been enlarged at this bond on the way here
+  auto take = [](std::vector<std::unique_ptr<Block>>& keep, int b) {
+    std::unique_ptr<Block> e;
+    if (b < (int)keep.size() && keep[b]) e = std::move(keep[b]);
+    return e;
+  };
+  std::unique_ptr<Block> Le = l2r ? nullptr : take(keep_L_, i);
+  std::unique_ptr<Block> Re = l2r ? take(keep_R_, i) : nullptr;
+  if (!Le) Le = enlarge(*L_[i], i);
+  if (!Re) Re = enlarge(*R_[n_ - i - 2], i + 1);
   be_->sync();
   double t1 = now_s();
   stats_.t_enlarge += t1 - t0;
@@ -2140,6 +2148,12 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   if (plan.dev) be_->free(plan.dev);
   if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
+  // keep this bond's system-side enlarged block for the way back
+  if ((double)be_->bytes_in_use() <= kKeepFraction * (double)be_->capacity()) {
+    auto& keep = l2r ? keep_L_ : keep_R_;
+    if ((int)keep.size() < n_) keep.resize(n_);
+    keep[i] = l2r ? std::move(Le) : std::move(Re);
+  }
   last_bond_ = i;
   bond_e_.push_back(e);
   if (opt_.verbose)
@@ -2726,6 +2740,7 @@ void Engine::rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rpare
 
 void Engine::rdm12(double* gamma, double* Gamma) {
   if (!prev_.valid) throw std::runtime_error("state: no sweep has run");
+  drop_kept();  // the measurement pass needs the memory more than the next sweep
   if (n_ < 3 || prev_.bond != 1 || (int)LU_.size() < 2 || !LU_[1])
     throw std::runtime_error("state: the RDMs are taken at bond 1, the end of a full sweep");
   const int n = n_;

@@ -179,6 +179,7 @@ class Engine {
   void set_precision(Precision p, Precision pr) {
     opt_.prec = p;
     opt_.prec_renorm = pr;
+    drop_kept();  // complementary operators of enlarged blocks follow the precision
   }
   const std::vector<double>& bond_energies() const { return bond_e_; }
   // Multiplet count of the left block L(m) / right block R(m) (sites counted)
@@ -202,6 +203,17 @@ class Engine {
   Options opt_;
   std::vector<double> h_, g_;  // h_pq and g_pqrs = (ps|qr)
   std::vector<std::unique_ptr<Block>> L_, R_;  // L_[m]: sites 0..m-1, R_[m]: last m sites
+  // Enlarged blocks kept for the opposite half-sweep: the enlarged L(i) (x)
+  // site i built at bond i going right is the left block of bond i again on
+  // the way back, and L(i) does not change in between (likewise for the
+  // right side).  Kept while the device holds at most kKeepFraction of its
+  // capacity; dropped when the precision changes and before the RDM pass.
+  std::vector<std::unique_ptr<Block>> keep_L_, keep_R_;
+  static constexpr double kKeepFraction = 0.4;
+  void drop_kept() {
+    keep_L_.clear();
+    keep_R_.clear();
+  }
   int tL_, tR_;
   double energy_ = 0.0;
   std::vector<double> bond_e_;
