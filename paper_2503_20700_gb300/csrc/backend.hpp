@@ -68,8 +68,10 @@ class Backend {
   virtual void* alloc(size_t bytes) = 0;
   virtual void free(void* p) = 0;
   virtual size_t bytes_in_use() const = 0;
-  // device memory the backend can hold in all (bytes)
+  // device memory the backend can hold in all (bytes), and what the whole
+  // device has free now (other contexts included)
   virtual size_t capacity() const { return ~size_t(0); }
+  virtual size_t device_free() const { return ~size_t(0); }
   virtual void memset0(void* p, size_t bytes) = 0;
   virtual void copy_d2d(void* dst, const void* src, size_t bytes) = 0;
   virtual void copy_h2d(void* dst, const void* src, size_t bytes) = 0;

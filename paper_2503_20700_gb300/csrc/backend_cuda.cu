@@ -731,6 +731,14 @@ class CudaBackend : public Backend {
   size_t bytes_in_use() const override { return used; }
   size_t total_mem = 0;
   size_t capacity() const override { return total_mem; }
+  size_t device_free() const override {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return fr;
+  }
   void memset0(void* p, size_t b) override { if (b) CK(cudaMemsetAsync(p, 0, b, st)); }
   void copy_d2d(void* d, const void* s, size_t b) override {
     if (b) CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToDevice, st));

@@ -2149,7 +2149,8 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
   // keep this bond's system-side enlarged block for the way back
-  if ((double)be_->bytes_in_use() <= kKeepFraction * (double)be_->capacity()) {
+  if ((double)be_->bytes_in_use() <= kKeepFraction * (double)be_->capacity() &&
+      (double)be_->device_free() >= kKeepFreeFraction * (double)be_->capacity()) {
     auto& keep = l2r ? keep_L_ : keep_R_;
     if ((int)keep.size() < n_) keep.resize(n_);
     keep[i] = l2r ? std::move(Le) : std::move(Re);

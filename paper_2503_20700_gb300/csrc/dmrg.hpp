@@ -206,10 +206,11 @@ class Engine {
   // Enlarged blocks kept for the opposite half-sweep: the enlarged L(i) (x)
   // site i built at bond i going right is the left block of bond i again on
   // the way back, and L(i) does not change in between (likewise for the
-  // right side).  Kept while the device holds at most kKeepFraction of its
-  // capacity; dropped when the precision changes and before the RDM pass.
+  // right side).  Kept while this context holds at most kKeepFraction of the
+  // device and the device still has kKeepFreeFraction free; dropped when the
+  // precision changes and before the RDM pass.
   std::vector<std::unique_ptr<Block>> keep_L_, keep_R_;
-  static constexpr double kKeepFraction = 0.4;
+  static constexpr double kKeepFraction = 0.4, kKeepFreeFraction = 0.2;
   void drop_kept() {
     keep_L_.clear();
     keep_R_.clear();
