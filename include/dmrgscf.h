@@ -103,6 +103,12 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
  * discarded weight of the last sweep.  Either output may be NULL.  With a
  * split precision the reported energy is the float64 Rayleigh quotient of
  * the last bond's eigenvector (one float64 H_eff psi).
+ *
+ * Device memory: besides the stored blocks of every bond, the context keeps
+ * each bond's enlarged block (block plus site) for the opposite half-sweep,
+ * which needs it again.  A block is kept only while the context holds at most 40%
+ * of the device's memory and at least 20% of it is still free.  Kept blocks
+ * are released by dmrg_set_precision, dmrg_rdm12 and dmrg_free.
  */
 dmrg_status dmrg_sweep(dmrg_ctx* ctx, int n_sweeps, double* energy, double* max_trunc_err);
 
