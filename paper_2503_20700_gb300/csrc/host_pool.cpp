@@ -105,9 +105,12 @@ class Pool {
   std::exception_ptr err_;
 };
 
+// Created on first use and never destroyed: idle workers end with the
+// process, and a forked child (whose copy of the pool has no threads, see
+// run) never joins threads it does not have.
 Pool& pool() {
-  static Pool p;
-  return p;
+  static Pool* p = new Pool();
+  return *p;
 }
 
 }  // namespace
