@@ -271,10 +271,11 @@ dmrg_status dmrg_last_contract_ms(double* ms);
  * dmrg_hpsi_contract_noalloc -- the fused H_eff psi contraction of
  * dmrg_hpsi_contract on caller-owned DEVICE buffers, allocating nothing.
  * The paper has no counterpart: this entry exists for callers that cannot
- * allocate device memory while they run -- code that records a CUDA graph by
- * stream capture (cudaMalloc cannot be captured), latency-critical loops
- * where an allocation would synchronise the device, and callers whose device
- * memory is owned by another allocator (e.g. PyTorch's caching allocator).
+ * allocate device memory while they run -- latency-critical loops where a
+ * cudaMalloc or cudaFree would synchronise the device, and callers whose
+ * device memory is owned by another allocator (e.g. PyTorch's caching
+ * allocator, or a fixed arena set aside by a serving process), where a
+ * private allocation would fragment or overcommit that memory.
  *
  * dA, dP, dB, dC: device pointers (lengths a_len .. c_len in doubles) on
  * `device`; dC is updated in place.  blocks / items: host arrays, same meaning
@@ -292,8 +293,10 @@ dmrg_status dmrg_last_contract_ms(double* ms);
  * (two host threads, or two streams whose work is in flight together) race
  * on it and give wrong results; serialise them.  The first call on a device
  * looks up the scratch address (cudaGetSymbolAddress, with that device made
- * current and then restored) and sets the kernels' shared-memory attributes;
- * make that first call before any stream capture begins.
+ * current and then restored) and sets the kernels' shared-memory attributes
+ * for that device.  The task lists are copied from host memory that lives
+ * only for the duration of the call, so the entry is for eager calls:
+ * recording it into a CUDA graph by stream capture is not supported.
  */
 dmrg_status dmrg_hpsi_contract_noalloc(const double* dA, int64_t a_len, const double* dP, int64_t p_len,
                                        const double* dB, int64_t b_len, double* dC, int64_t c_len,

@@ -23,6 +23,8 @@ The oracle is plain, slow, float64 numpy/scipy code written from the paper:
   their spin-coupled forms (Eq. rdm1_su2 and the two-channel 2-RDM).
 * ``casscf`` -- orbital rotation U = exp(-kappa), integral transformation,
   the CAS-SCF energy functional and its orbital gradient (Sec. II.A).
-* ``contract`` -- plain definition of the grouped sector contraction
-  sigma = sum_t c_t A_t psi B_t^T used to pin the GEMM kernels.
+
+The kernel-level tests (grouped GEMM, fused sector contraction, eigensolver)
+compare against the plain definition written inline in the test (a numpy
+matrix product or ``numpy.linalg.eigh``).
 """

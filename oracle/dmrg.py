@@ -23,7 +23,8 @@ operators:
   their components with S-.
 
 Readings fixed here (the paper is silent on them):
-* Initial state: the product state of ``workloads.initial_product_state``,
+* Initial state: the product state of ``workloads.initial_product_state``
+  (or a given occupation and spin path, e.g. ``workloads.aufbau_state``),
   coupled from the right; every right block starts as one multiplet.
 * Sweep: L->R over bonds 0..n-3 (truncating the left enlarged block after
   each), then R->L over bonds n-2..1 (truncating the right enlarged block).
@@ -129,7 +130,7 @@ class SweepRecord:
 class OracleDMRG:
     """Two-site SU(2) DMRG on explicit full-space block bases."""
 
-    def __init__(self, h, eri, n_elec, two_s, D, e_core=0.0, tol=1e-10):
+    def __init__(self, h, eri, n_elec, two_s, D, e_core=0.0, tol=1e-10, occ=None, two_s_right=None):
         from workloads import initial_product_state
         self.h = np.asarray(h, float)
         self.eri = np.asarray(eri, float)
@@ -143,8 +144,11 @@ class OracleDMRG:
                     for tm in range(-two_s, two_s + 1, 2)}
         self.H = self.ham[two_s]
         self.states = self.H.ops.states
-        occ, path = initial_product_state(self.n, n_elec, two_s)
-        self.right = initial_right_bases(self.n, occ, path)
+        if occ is None:
+            occ, path = initial_product_state(self.n, n_elec, two_s)
+        else:
+            path = two_s_right
+        self.right = initial_right_bases(self.n, list(occ), list(path))
         self.left = [None] * (self.n + 1)
         self.left[0] = vacuum_basis()
         full0 = self.right[0]

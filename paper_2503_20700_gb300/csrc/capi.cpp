@@ -47,6 +47,29 @@ dmrg_status translate(dmrg_ctx* c, const std::exception& e) {
   return fail(c, DMRG_EINTERNAL, m);
 }
 
+// Makes `device` current for its lifetime and puts the caller's device back
+// on every exit path (a thrown launch error included).
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard(int device, cudaError_t* e) {
+    *e = cudaGetDevice(&prev);
+    if (*e != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    *e = cudaSetDevice(device);
+  }
+  cudaError_t restore() {
+    cudaError_t e = cudaSuccess;
+    if (prev >= 0) e = cudaSetDevice(prev);
+    prev = -1;
+    return e;
+  }
+  ~DeviceGuard() { restore(); }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 bool sweep_precision_ok(int p) {
   return p == DMRG_FP64 || p == DMRG_SPLIT_TF32 || p == DMRG_SPLIT_HPSI || p == DMRG_SPLIT_HPSI_TC;
 }
@@ -560,9 +583,7 @@ dmrg_status dmrg_hpsi_contract_noalloc(const double* dA, int64_t a_len, const do
     void* base = nullptr;
     cudaError_t e = dmrg::noalloc_scratch(device, &base);
     if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
-    int prev = 0;
-    e = cudaGetDevice(&prev);
-    if (e == cudaSuccess) e = cudaSetDevice(device);
+    DeviceGuard guard(device, &e);
     if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
     char* d = (char*)base;
@@ -578,9 +599,9 @@ dmrg_status dmrg_hpsi_contract_noalloc(const double* dA, int64_t a_len, const do
                         (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(),
                         (const dmrg::HpsiReduce*)(d + orr), (int)reds.size(), (double*)(d + os), pr, nullptr,
                         st);
-    cudaError_t e2 = cudaSetDevice(prev);
     if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
-    if (e2 != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e2));
+    e = guard.restore();
+    if (e != cudaSuccess) return fail(nullptr, DMRG_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
   } catch (const std::exception& ex) {
     return translate(nullptr, ex);
   }

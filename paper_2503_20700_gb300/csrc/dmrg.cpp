@@ -2139,7 +2139,8 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
     RU_[n_ - i - 1] = std::move(U);
   }
   be_->sync();
-  stats_.t_renorm += now_s() - t5;
+  const double t6 = now_s();
+  stats_.t_renorm += t6 - t5;
   save_prev(i, *Le, *Re, plan, psi);
   be_->sync();
   be_->free(psi);
@@ -2148,6 +2149,15 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   if (plan.dev) be_->free(plan.dev);
   if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
+  size_t enl_bytes = 0;
+  int enl_maxsec = 0;
+  if (opt_.verbose) {
+    for (const Block* b : {Le.get(), Re.get()})
+      if (b && b->ops) enl_bytes += b->ops->bytes();
+    const Block* tb = l2r ? Le.get() : Re.get();
+    if (tb && tb->ops)
+      for (auto& sc : tb->ops->basis.sec) enl_maxsec = std::max(enl_maxsec, sc.dim);
+  }
   // keep this bond's system-side enlarged block for the way back
   if ((double)be_->bytes_in_use() <= kKeepFraction * (double)be_->capacity() &&
       (double)be_->device_free() >= kKeepFreeFraction * (double)be_->capacity()) {
@@ -2157,9 +2167,21 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   }
   last_bond_ = i;
   bond_e_.push_back(e);
-  if (opt_.verbose)
-    std::fprintf(stderr, "bond %d %s E %.12f trunc %.3e it %d len %zu flops %.3e\n", i,
-                 l2r ? "LR" : "RL", e, *trunc, its, len, plan.flops);
+  if (opt_.verbose) {
+    // stored blocks of every bond, the two enlarged blocks of this one, and
+    // the largest sector of the truncated enlarged basis (the eigensolver's
+    // largest matrix)
+    size_t stored = 0;
+    for (auto& b : L_)
+      if (b && b->ops) stored += b->ops->bytes();
+    for (auto& b : R_)
+      if (b && b->ops) stored += b->ops->bytes();
+    std::fprintf(stderr,
+                 "bond %d %s E %.12f trunc %.3e it %d len %zu flops %.3e | mem %.2f GB stored %.2f GB "
+                 "enl %.2f GB maxsec %d | t enl %.3f plan %.3f dav %.3f dec %.3f ren %.3f\n",
+                 i, l2r ? "LR" : "RL", e, *trunc, its, len, plan.flops, be_->bytes_in_use() / 1e9,
+                 stored / 1e9, enl_bytes / 1e9, enl_maxsec, t1 - t0, t3 - t2, t4 - t3, t5 - t4, t6 - t5);
+  }
   return e;
 }
 

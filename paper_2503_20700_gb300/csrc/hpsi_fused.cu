@@ -3,6 +3,7 @@
 #include <string>
 
 #include "hpsi_fused.cuh"
+#include "kattr.hpp"
 
 namespace dmrg {
 
@@ -414,19 +415,15 @@ void hpsi_launch(const HpsiBlock* blocks, const HpsiItem* items, const HpsiTask*
   if (ntasks > 0) {
     if (prec == Precision::FP64) {
       size_t smem = (size_t)(3 * KS * (T + 1) + T * (T + 1)) * sizeof(double);
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(hpsi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-      }
+      cudaError_t ea = ensure_smem_attr((const void*)hpsi_f64_kernel, (int)smem);
+      if (ea != cudaSuccess)
+        throw std::runtime_error(std::string("cuda: hpsi f64 attribute: ") + cudaGetErrorString(ea));
       hpsi_f64_kernel<<<ntasks, 256, smem, st>>>(blocks, items, tasks, scratch);
     } else {
       size_t smem = (size_t)SM_WORDS * sizeof(uint32_t);
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(hpsi_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-      }
+      cudaError_t ea = ensure_smem_attr((const void*)hpsi_tf32x3_kernel, (int)smem);
+      if (ea != cudaSuccess)
+        throw std::runtime_error(std::string("cuda: hpsi tf32x3 attribute: ") + cudaGetErrorString(ea));
       hpsi_tf32x3_kernel<<<ntasks, 256, smem, st>>>(blocks, items, tasks, scratch);
     }
     cudaError_t e = cudaGetLastError();

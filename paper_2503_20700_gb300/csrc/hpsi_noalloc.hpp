@@ -6,9 +6,9 @@
 
 namespace dmrg {
 
-// Capacity of the static scratch: task lists, reduction list, the timeout
-// flag and the partial tiles of one call (about one thousand 64 x 64 float64
-// partial tiles).
+// Capacity of the static scratch: block, item, task and reduction lists and
+// the partial tiles of one call (about one thousand 64 x 64 float64 partial
+// tiles).
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 
 // Device address of the static scratch on `device`, looked up once (with that

@@ -22,6 +22,7 @@
 #include <string>
 
 #include "hpsi_tc.cuh"
+#include "kattr.hpp"
 
 namespace dmrg {
 
@@ -493,11 +494,9 @@ void split_launch(const SplitJob* jobs, int n, cudaStream_t st) {
 
 void hpsi_tc_launch(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
                     const HpsiReduce* reds, int nreds, double* scratch, int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hpsi_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  {
+    cudaError_t e = ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES);
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc attribute: ") + cudaGetErrorString(e));
-    attr = true;
   }
   if (ntasks > 0) {
     hpsi_tc_kernel<<<ntasks, 128, SMEM_BYTES, st>>>(blocks, items, tasks, scratch, err);

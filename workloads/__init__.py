@@ -18,7 +18,8 @@ Workloads (all energies returned in Hartree, integrals in chemists' notation
   (pq|rs) = sum_k L^k_pq L^k_rs, 8-fold symmetric and positive semidefinite.
 * ``initial_product_state(n, n_elec, two_s)`` -- occupations and the
   intermediate-spin path of the deterministic product state that starts the
-  sweeps.
+  sweeps; ``aufbau_state(h, n_elec, two_s)`` the same for an occupation by
+  orbital energy.
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ DEFAULT_SEED = 20250326
 __all__ = [
     "HARTREE_EV", "DEFAULT_SEED", "acene_geometry", "ppp_integrals", "ppp_acene",
     "cholesky_random", "eri_from_cholesky", "initial_product_state",
-    "hubbard_chain",
+    "aufbau_state", "spin_path", "hubbard_chain",
 ]
 
 
@@ -164,9 +165,47 @@ def initial_product_state(n: int, n_elec: int, two_s: int):
         occ = [1] * n_elec + [0] * (n - n_elec)
     else:
         occ = [2] * (n_elec - n) + [1] * (2 * n - n_elec)
-    n_single = sum(1 for o in occ if o == 1)
-    if two_s > n_single:
+    return occ, spin_path(occ, two_s)
+
+
+def aufbau_state(h, n_elec: int, two_s: int):
+    """Closed-shell-like product state by orbital energy (``occ``, ``two_s_right``).
+
+    The orbitals with the lowest diagonal one-electron integrals h_pp take the
+    electrons: (n_elec - two_s)/2 of them doubly occupied, the next two_s
+    singly occupied (ties by orbital index).  Sites keep their chain order;
+    only the occupation pattern follows h_pp.  For the random Cholesky active
+    spaces, whose h_pp grow along the chain on average, this start is near the
+    ground state's charge distribution, where the even-spread state puts one
+    electron on every orbital and leaves the sweeps to move charge between the
+    halves of the chain one bond at a time.
+    """
+    d = np.asarray(np.diag(h), dtype=np.float64)
+    n = d.size
+    if not (0 <= n_elec <= 2 * n) or two_s < 0 or (n_elec - two_s) % 2 != 0:
+        raise ValueError("bad n_elec / two_s")
+    n_double = (n_elec - two_s) // 2
+    if n_double + two_s > n:
         raise ValueError("two_s too large for this filling")
+    order = sorted(range(n), key=lambda p: (d[p], p))
+    occ = [0] * n
+    for p in order[:n_double]:
+        occ[p] = 2
+    for p in order[n_double:n_double + two_s]:
+        occ[p] = 1
+    return occ, spin_path(occ, two_s)
+
+
+def spin_path(occ, two_s: int):
+    """Doubled spins of the right blocks of a product state (length n+1).
+
+    Scanning from the right end, the singly occupied sites first couple up to
+    the target spin, then alternate (S+1/2, S, S+1/2, ...), so every
+    intermediate spin is as small as the path allows."""
+    n = len(occ)
+    n_single = sum(1 for o in occ if o == 1)
+    if two_s > n_single or (n_single - two_s) % 2 != 0:
+        raise ValueError("two_s not reachable from this occupation")
     path = [0] * (n + 1)
     seen = 0
     cur = 0
@@ -179,4 +218,4 @@ def initial_product_state(n: int, n_elec: int, two_s: int):
                 cur = cur + 1 if cur == two_s else cur - 1
         path[i] = cur
     assert path[0] == two_s, (path, two_s)
-    return occ, path
+    return path
