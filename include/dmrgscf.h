@@ -112,6 +112,54 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
  */
 dmrg_status dmrg_sweep(dmrg_ctx* ctx, int n_sweeps, double* energy, double* max_trunc_err);
 
+/*
+ * dmrg_sweep_part -- part of a sweep (Sec. II.B two-site DMRG): direction 0
+ * runs L->R over bonds 0..last_bond (starting a sweep), direction 1 runs
+ * R->L over bonds n-2..last_bond (after a completed L->R half-sweep).
+ * Afterwards the context holds the blocks of the next bond in that
+ * direction (last_bond+1, or last_bond-1), where dmrg_bond_solve can run.
+ * Outputs as for dmrg_sweep (energy of bond last_bond).  DMRG_EINVAL for a
+ * bond out of range, DMRG_ESTATE for an R->L part without its left blocks.
+ * dmrg_rdm12 needs a sweep that ended at bond 1 (a full sweep).
+ */
+dmrg_status dmrg_sweep_part(dmrg_ctx* ctx, int direction, int last_bond, double* energy,
+                            double* max_trunc_err);
+
+/* Result of dmrg_bond_solve (energies include e_core). */
+typedef struct {
+  double energy;          /* Davidson eigenvalue in the product's precision   */
+  double energy_rq64;     /* float64 Rayleigh quotient of the returned vector */
+  double residual64;      /* float64 ||H_eff psi - E_rq psi||, ||psi|| = 1    */
+  double gap;             /* second minus lowest Ritz value at exit           */
+  int iterations;         /* Davidson iterations                              */
+  int calls;              /* H_eff psi products (timed)                       */
+  double flops_per_call;  /* algorithmic FLOPs of one product (2mnk, once)    */
+  double ms_total;        /* CUDA-event milliseconds of all products          */
+  int64_t dim;            /* length of the two-site wavefunction              */
+} dmrg_bond_result;
+
+/*
+ * dmrg_bond_solve -- Davidson (Sec. II.D) for the two-site wavefunction of
+ * `bond` on the blocks the context holds, from the wavefunction predicted
+ * from the neighbouring bond, with the H_eff psi product in `precision`
+ * (DMRG_FP64, DMRG_SPLIT_HPSI or DMRG_SPLIT_HPSI_TC), at most max_iter
+ * iterations to residual tol.  Nothing of the stored state changes (no
+ * decimation), so calls with different precisions start from the same
+ * vector.  Every product is timed with CUDA events on the library's stream;
+ * when Davidson stops before min_calls products, H_eff psi is applied to its
+ * vector until min_calls have run.  call_ms (cap values, may be NULL with
+ * cap 0) receives the time of each product.  direction: the direction of
+ * the partial sweep that stopped next to `bond` (0 L->R, 1 R->L).
+ * DMRG_ESTATE when the blocks of `bond` are not held.
+ */
+dmrg_status dmrg_bond_solve(dmrg_ctx* ctx, int bond, int direction, int precision, int max_iter,
+                            double tol, int min_calls, dmrg_bond_result* out, double* call_ms, int cap);
+
+/* Change the Davidson iteration cap (per bond) and residual tolerance used
+ * by subsequent sweeps (Sec. II.D).  A bond that reaches the cap keeps its
+ * last Ritz vector. */
+dmrg_status dmrg_set_davidson(dmrg_ctx* ctx, int max_iter, double tol);
+
 /* Change the bond dimension used by subsequent sweeps. */
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* ctx, int D);
 
@@ -156,12 +204,13 @@ dmrg_status dmrg_block_dims(const dmrg_ctx* ctx, int* left, int* right);
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);
 
 /* Device time (ms), algorithmic FLOPs and launch count of the GEMM kernels
- * since profiling was turned on.  which = 1: the H_eff psi launches (with
- * the operand splits of the tcgen05 path), 0: all other GEMM launches
- * (renormalisation, complementary operators, density matrices), 2: the
- * blocking placement kernel, 3: the eigensolver of a single small matrix
- * (the Davidson subspace problem), 4: the batched eigensolver (the
- * density-matrix sectors of a decimation, one cooperative launch per batch). */
+ * since profiling was turned on.  which = 1: the H_eff psi contraction
+ * launches (the kernel and the reduction of its item chunks), 0: all other
+ * GEMM launches (renormalisation, complementary operators, density
+ * matrices), 2: the blocking placement kernel, 3: the eigensolver of a single
+ * small matrix (the Davidson subspace problem), 4: the batched eigensolver
+ * (the density-matrix sectors of a decimation, one cooperative launch per
+ * batch), 5: the TF32 hi/lo splits of the tcgen05 path's operands. */
 dmrg_status dmrg_kernel_stats(dmrg_ctx* ctx, int which, double* ms, double* flops,
                               int64_t* launches);
 
@@ -262,9 +311,9 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
                                int device);
 
 /* Device time (ms, CUDA events on the library's stream) of the kernels of
- * the calling thread's last dmrg_hpsi_contract: the operand splits (tcgen05
- * path), the contraction and the reduction of item chunks; host copies not
- * included. */
+ * the calling thread's last dmrg_hpsi_contract: the contraction and the
+ * reduction of item chunks (the operand splits of the tcgen05 path and the
+ * host copies are not included). */
 dmrg_status dmrg_last_contract_ms(double* ms);
 
 /*

@@ -36,6 +36,14 @@ class Opts(ctypes.Structure):
                 ("device", ctypes.c_int)]
 
 
+class BondResult(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("energy_rq64", ctypes.c_double),
+                ("residual64", ctypes.c_double), ("gap", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("calls", ctypes.c_int),
+                ("flops_per_call", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("dim", ctypes.c_int64)]
+
+
 _lib = None
 _lib_path = None
 
@@ -62,6 +70,12 @@ def load(path=None):
     lib.dmrg_init.restype = I
     lib.dmrg_sweep.argtypes = [P, I, dp, dp]
     lib.dmrg_sweep.restype = I
+    lib.dmrg_sweep_part.argtypes = [P, I, I, dp, dp]
+    lib.dmrg_sweep_part.restype = I
+    lib.dmrg_bond_solve.argtypes = [P, I, I, I, I, D, I, ctypes.POINTER(BondResult), dp, I]
+    lib.dmrg_bond_solve.restype = I
+    lib.dmrg_set_davidson.argtypes = [P, I, D]
+    lib.dmrg_set_davidson.restype = I
     lib.dmrg_set_bond_dim.argtypes = [P, I]
     lib.dmrg_set_bond_dim.restype = I
     lib.dmrg_set_precision.argtypes = [P, I]
@@ -147,6 +161,31 @@ class DMRG:
         _check(self._lib, self._ctx, self._lib.dmrg_sweep(self._ctx, n_sweeps, ctypes.byref(e),
                                                          ctypes.byref(t)))
         return e.value, t.value
+
+    def sweep_part(self, direction, last_bond):
+        """Part of a sweep (direction 0: L->R over bonds 0..last_bond, 1: R->L
+        over bonds n-2..last_bond); returns (energy, max discarded weight)."""
+        e = ctypes.c_double()
+        t = ctypes.c_double()
+        _check(self._lib, self._ctx, self._lib.dmrg_sweep_part(self._ctx, int(direction), int(last_bond),
+                                                              ctypes.byref(e), ctypes.byref(t)))
+        return e.value, t.value
+
+    def bond_solve(self, bond, direction, precision, max_iter=200, tol=1e-7, min_calls=0):
+        """Davidson at `bond` on the held blocks (dmrg_bond_solve); returns a
+        dict of the result and the CUDA-event time of every product."""
+        r = BondResult()
+        cap = max(int(min_calls), int(max_iter) + 2)
+        ms = np.zeros(cap)
+        _check(self._lib, self._ctx, self._lib.dmrg_bond_solve(
+            self._ctx, int(bond), int(direction), int(precision), int(max_iter), float(tol), int(min_calls),
+            ctypes.byref(r), _dp(ms), cap))
+        out = {k: getattr(r, k) for k, _ in BondResult._fields_}
+        out["call_ms"] = ms[:min(cap, r.calls)].tolist()
+        return out
+
+    def set_davidson(self, max_iter, tol):
+        _check(self._lib, self._ctx, self._lib.dmrg_set_davidson(self._ctx, int(max_iter), float(tol)))
 
     def set_bond_dim(self, D):
         _check(self._lib, self._ctx, self._lib.dmrg_set_bond_dim(self._ctx, D))

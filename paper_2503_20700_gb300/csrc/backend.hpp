@@ -60,6 +60,7 @@ struct TcItem;
 struct SplitJob;
 struct HpsiTask;
 struct HpsiReduce;
+struct TcLaunch;
 
 class Backend {
  public:
@@ -71,6 +72,8 @@ class Backend {
   // device memory the backend can hold in all (bytes), and what the whole
   // device has free now (other contexts included)
   virtual size_t capacity() const { return ~size_t(0); }
+  // streaming multiprocessors of the device (the persistent launches' grid)
+  virtual int sm_count() const { return 152; }
   virtual size_t device_free() const { return ~size_t(0); }
   virtual void memset0(void* p, size_t bytes) = 0;
   virtual void copy_d2d(void* dst, const void* src, size_t bytes) = 0;
@@ -95,9 +98,8 @@ class Backend {
                     double flops) = 0;
   // The tcgen05 version of the contraction on pre-split operands (hpsi_tc.cuh),
   // and the split of float64 blocks into TF32 hi/lo planes (device job list).
-  virtual void hpsi_tc(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
-                       const HpsiReduce* reds, int nreds, double* scratch, double flops) = 0;
-  virtual void split(const SplitJob* jobs, int n) = 0;
+  virtual void hpsi_tc(const TcLaunch& launch, double flops) = 0;
+  virtual void split(const SplitJob* jobs, int n, float* pool) = 0;
 
   // Davidson vector algebra on contiguous float64 vectors of length len.
   // out[i] = sum_t V[i*ld + t] * x[t] for i < m   (out is a device array)

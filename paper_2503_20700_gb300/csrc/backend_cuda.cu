@@ -631,8 +631,9 @@ class CudaBackend : public Backend {
   // categories: 0 GEMMs, 1 H_eff psi (with its operand splits), 2 blocking
   // placement, 3 eigensolver (shared-memory kernel), 4 eigensolver
   // (cooperative kernel)
-  double acc_ms[5] = {0, 0, 0, 0, 0}, acc_flops[5] = {0, 0, 0, 0, 0};
-  long acc_launch[5] = {0, 0, 0, 0, 0};
+  static constexpr int kTags = 6;
+  double acc_ms[kTags] = {0, 0, 0, 0, 0, 0}, acc_flops[kTags] = {0, 0, 0, 0, 0, 0};
+  long acc_launch[kTags] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t ev() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -648,7 +649,7 @@ class CudaBackend : public Backend {
       CK(cudaEventSynchronize(r.b));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, r.a, r.b));
-      int t = std::min(4, std::max(0, r.tag));
+      int t = std::min(kTags - 1, std::max(0, r.tag));
       acc_ms[t] += ms;
       acc_flops[t] += r.flops;
       acc_launch[t] += 1;
@@ -672,11 +673,11 @@ class CudaBackend : public Backend {
   void set_profile(bool on) override {
     drain();
     profiling = on;
-    for (int t = 0; t < 5; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
+    for (int t = 0; t < kTags; ++t) acc_ms[t] = acc_flops[t] = 0, acc_launch[t] = 0;
   }
   void kernel_stats(int t, double* ms, double* flops, long* launches) override {
     drain();
-    t = std::min(4, std::max(0, t));
+    t = std::min(kTags - 1, std::max(0, t));
     if (ms) *ms = acc_ms[t];
     if (flops) *flops = acc_flops[t];
     if (launches) *launches = acc_launch[t];
@@ -691,7 +692,10 @@ class CudaBackend : public Backend {
     CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     size_t fr = 0;
     CK(cudaMemGetInfo(&fr, &total_mem));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
+  int sms = 152;
+  int sm_count() const override { return sms; }
   ~CudaBackend() override {
     cudaStreamSynchronize(st);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -901,8 +905,7 @@ class CudaBackend : public Backend {
     if (recs.size() > 4096) drain();
   }
 
-  void hpsi_tc(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
-               const HpsiReduce* reds, int nreds, double* scratch, double flops) override {
+  void hpsi_tc(const TcLaunch& L, double flops) override {
     gemm_flops += flops;
     Rec* rec = nullptr;
     if (profiling) {
@@ -910,21 +913,21 @@ class CudaBackend : public Backend {
       rec = &recs.back();
       CK(cudaEventRecord(rec->a, st));
     }
-    hpsi_tc_launch(blocks, items, tasks, ntasks, reds, nreds, scratch, flag(), st);
-    launches += (ntasks > 0) + (nreds > 0);
+    hpsi_tc_launch(L, flag(), st);
+    launches += (L.ncta > 0) + (L.nreds > 0);
     if (rec) CK(cudaEventRecord(rec->b, st));
     if (recs.size() > 4096) drain();
   }
-  void split(const SplitJob* jobs, int n) override {
+  void split(const SplitJob* jobs, int n, float* pool) override {
     if (n <= 0) return;
-    // counted with the H_eff psi launches: the splits are part of its cost
+    // the operand splits of the tcgen05 path (tag 5)
     Rec* rec = nullptr;
     if (profiling) {
-      recs.push_back(Rec{ev(), ev(), 0.0, 1});
+      recs.push_back(Rec{ev(), ev(), 0.0, 5});
       rec = &recs.back();
       CK(cudaEventRecord(rec->a, st));
     }
-    split_launch(jobs, n, st);
+    split_launch(jobs, n, pool, st);
     ++launches;
     if (rec) CK(cudaEventRecord(rec->b, st));
     if (recs.size() > 4096) drain();

@@ -204,6 +204,57 @@ dmrg_status dmrg_sweep(dmrg_ctx* c, int n_sweeps, double* energy, double* max_tr
   return DMRG_OK;
 }
 
+dmrg_status dmrg_sweep_part(dmrg_ctx* c, int direction, int last_bond, double* energy, double* max_trunc) {
+  if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
+  if (direction != 0 && direction != 1) return fail(c, DMRG_EINVAL, "direction must be 0 (L->R) or 1 (R->L)");
+  try {
+    c->last = c->eng->sweep_part(direction == 0, last_bond);
+    c->sweep_seconds = c->eng->sweep_seconds;
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  if (energy) *energy = c->last.energy;
+  if (max_trunc) *max_trunc = c->last.max_trunc;
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision, int max_iter, double tol,
+                            int min_calls, dmrg_bond_result* out, double* call_ms, int cap) {
+  if (!c || !c->eng || !out) return fail(c, DMRG_EINVAL, "invalid argument");
+  if (direction != 0 && direction != 1) return fail(c, DMRG_EINVAL, "direction must be 0 (L->R) or 1 (R->L)");
+  if (!sweep_precision_ok(precision) || precision == DMRG_SPLIT_TF32)
+    return fail(c, DMRG_EINVAL, "precision must be DMRG_FP64, DMRG_SPLIT_HPSI or DMRG_SPLIT_HPSI_TC");
+  if (max_iter < 1 || !(tol > 0) || min_calls < 0 || cap < 0 || (cap > 0 && !call_ms))
+    return fail(c, DMRG_EINVAL, "invalid argument");
+  try {
+    dmrg::Precision ph, pr;
+    map_precision(precision, &ph, &pr);
+    dmrg::Engine::BondSolve r = c->eng->solve_bond(bond, direction == 0, ph, max_iter, tol, min_calls);
+    out->energy = r.energy;
+    out->energy_rq64 = r.energy_rq64;
+    out->residual64 = r.residual64;
+    out->gap = r.gap;
+    out->iterations = r.iterations;
+    out->calls = r.calls;
+    out->flops_per_call = r.flops_per_call;
+    out->dim = (int64_t)r.dim;
+    double tot = 0.0;
+    for (double x : r.call_ms) tot += x;
+    out->ms_total = tot;
+    for (int i = 0; i < std::min(cap, (int)r.call_ms.size()); ++i) call_ms[i] = r.call_ms[i];
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_davidson(dmrg_ctx* c, int max_iter, double tol) {
+  if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
+  if (max_iter < 1 || !(tol > 0)) return fail(c, DMRG_EINVAL, "max_iter < 1 or tol <= 0");
+  c->eng->set_davidson(max_iter, tol);
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* c, int D) {
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
   if (D < 1) return fail(c, DMRG_EINVAL, "D < 1");
@@ -280,7 +331,7 @@ dmrg_status dmrg_profile(dmrg_ctx* c, int on) {
 
 dmrg_status dmrg_kernel_stats(dmrg_ctx* c, int which, double* ms, double* flops, int64_t* launches) {
   if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
-  if (which < 0 || which > 4) return fail(c, DMRG_EINVAL, "which must be 0..4");
+  if (which < 0 || which > 5) return fail(c, DMRG_EINVAL, "which must be 0..5");
   try {
     long l = 0;
     c->be->kernel_stats(which, ms, flops, &l);
@@ -494,7 +545,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     void* pool = nullptr;
     size_t scr;
     if (tc) {
-      dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp);
+      dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp, be->sm_count());
       tasks = tp.tasks;
       reds = tp.reds;
       scr = tp.scratch;
@@ -507,7 +558,9 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     size_t ot = al(oc + tp.items.size() * sizeof(dmrg::TcItem));
     size_t orr = al(ot + tasks.size() * sizeof(dmrg::HpsiTask));
     size_t oj = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
-    size_t os = al(oj + (tp.op_jobs.size() + tp.psi_jobs.size()) * sizeof(dmrg::SplitJob));
+    size_t oco = al(oj + (tp.op_jobs.size() + tp.psi_jobs.size()) * sizeof(dmrg::SplitJob));
+    size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
+    size_t os = al(oct + tp.cta_task.size() * sizeof(int));
     char* d = (char*)be->alloc(os + scr * sizeof(double) + 256);
     if (!hb.empty()) be->copy_h2d(d + ob, hb.data(), hb.size() * sizeof(dmrg::HpsiBlock));
     if (!hi.empty()) be->copy_h2d(d + oi, hi.data(), hi.size() * sizeof(dmrg::HpsiItem));
@@ -519,11 +572,23 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
       jobs.insert(jobs.end(), tp.psi_jobs.begin(), tp.psi_jobs.end());
       if (!jobs.empty()) {
         be->copy_h2d(d + oj, jobs.data(), jobs.size() * sizeof(dmrg::SplitJob));
-        be->split((const dmrg::SplitJob*)(d + oj), (int)jobs.size());
+        be->split((const dmrg::SplitJob*)(d + oj), (int)jobs.size(), (float*)pool);
       }
-      be->hpsi_tc((const dmrg::HpsiBlock*)(d + ob), (const dmrg::TcItem*)(d + oc),
-                  (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),
-                  (int)reds.size(), (double*)(d + os), fl);
+      if (!tp.cta_off.empty()) be->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
+      if (!tp.cta_task.empty()) be->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(int));
+      dmrg::TcLaunch L;
+      L.blocks = (const dmrg::HpsiBlock*)(d + ob);
+      L.items = (const dmrg::TcItem*)(d + oc);
+      L.tasks = (const dmrg::HpsiTask*)(d + ot);
+      L.cta_off = (const int*)(d + oco);
+      L.cta_task = (const int*)(d + oct);
+      L.ncta = (int)tp.cta_off.size() - 1;
+      L.reds = (const dmrg::HpsiReduce*)(d + orr);
+      L.nreds = (int)reds.size();
+      L.scratch = (double*)(d + os);
+      L.pool = pool;
+      L.units = tp.units;
+      be->hpsi_tc(L, fl);
     } else {
       be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),
                (const dmrg::HpsiTask*)(d + ot), (int)tasks.size(), (const dmrg::HpsiReduce*)(d + orr),

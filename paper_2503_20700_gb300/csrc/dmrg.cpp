@@ -1265,6 +1265,7 @@ struct HPsiPlan {
   TcItem* d_tcitems = nullptr;
   SplitJob* d_psi_jobs = nullptr;
   int n_psi_jobs = 0;
+  TcLaunch tc;  // device lists of the persistent contraction
   int ntasks = 0, nreds = 0;
   size_t nitems = 0;
   double flops = 0.0;
@@ -1414,7 +1415,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   if (tc) {
     if (plan.tc_pool) be_->free(plan.tc_pool);
     plan.tc_pool = nullptr;
-    hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp);
+    hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp,
+                    be_->sm_count());
     tasks = tp.tasks;
     reds = tp.reds;
     scr = tp.scratch;
@@ -1431,7 +1433,9 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   size_t orr = al(ot + tasks.size() * sizeof(HpsiTask));
   size_t oj = al(orr + reds.size() * sizeof(HpsiReduce));
   size_t opj = al(oj + tp.op_jobs.size() * sizeof(SplitJob));
-  size_t os = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
+  size_t oco = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
+  size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
+  size_t os = al(oct + tp.cta_task.size() * sizeof(int));
   size_t total = os + scr * sizeof(double) + 256;
   if (plan.dev) be_->free(plan.dev);
   plan.dev = be_->alloc(total);
@@ -1451,10 +1455,26 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   if (!reds.empty()) be_->copy_h2d(plan.d_reds, reds.data(), reds.size() * sizeof(HpsiReduce));
   if (!tp.psi_jobs.empty())
     be_->copy_h2d(plan.d_psi_jobs, tp.psi_jobs.data(), tp.psi_jobs.size() * sizeof(SplitJob));
+  if (tc) {
+    if (!tp.cta_off.empty()) be_->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
+    if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(int));
+    plan.tc = TcLaunch();
+    plan.tc.blocks = plan.d_blocks;
+    plan.tc.items = plan.d_tcitems;
+    plan.tc.tasks = plan.d_tasks;
+    plan.tc.cta_off = (const int*)(d + oco);
+    plan.tc.cta_task = (const int*)(d + oct);
+    plan.tc.ncta = (int)tp.cta_off.size() - 1;
+    plan.tc.reds = plan.d_reds;
+    plan.tc.nreds = (int)reds.size();
+    plan.tc.scratch = (double*)(d + os);
+    plan.tc.pool = plan.tc_pool;
+    plan.tc.units = tp.units;
+  }
   if (!tp.op_jobs.empty()) {
-    // operator blocks are constant during Davidson: split them once
+    // operator blocks (and identities) are constant during Davidson: split them once
     be_->copy_h2d(d + oj, tp.op_jobs.data(), tp.op_jobs.size() * sizeof(SplitJob));
-    be_->split((const SplitJob*)(d + oj), (int)tp.op_jobs.size());
+    be_->split((const SplitJob*)(d + oj), (int)tp.op_jobs.size(), (float*)plan.tc_pool);
   }
   plan.ntasks = (int)tasks.size();
   plan.nreds = (int)reds.size();
@@ -1494,9 +1514,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
   if (plan.prec == Precision::TC_TF32X3) {
-    be_->split(plan.d_psi_jobs, plan.n_psi_jobs);
-    be_->hpsi_tc(plan.d_blocks, plan.d_tcitems, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
-                 plan.scratch, plan.flops);
+    be_->split(plan.d_psi_jobs, plan.n_psi_jobs, (float*)plan.tc_pool);
+    be_->hpsi_tc(plan.tc, plan.flops);
   } else {
     be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
               plan.scratch, plan.prec, plan.flops);
@@ -1550,7 +1569,9 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
   auto apply = [&](int i) {
     be_->copy_d2d(plan.in, V + (size_t)i * len, len * sizeof(double));
     auto t0 = std::chrono::steady_clock::now();
+    if (call_ms_) be_->mark_begin();
     apply_hpsi(plan);
+    if (call_ms_) call_ms_->push_back(be_->mark_end());
     be_->sync();
     if (plan.prec == Precision::TC_TF32X3) be_->check_device_flag();
     auto t1 = std::chrono::steady_clock::now();
@@ -1582,6 +1603,7 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     be_->copy_d2h(Z.data(), dEv, (size_t)m * m * sizeof(double));
     // lowest eigenpair = last row (eigenvalues descending)
     e = w[m - 1];
+    last_gap_ = m >= 2 ? w[m - 2] - w[m - 1] : 0.0;
     for (int i = 0; i < m; ++i) c[i] = Z[(size_t)(m - 1) * m + i];
     be_->copy_h2d(dZ, c.data(), m * sizeof(double));
     be_->combine(x, 0.0, V, m, len, len, dZ);
@@ -2183,6 +2205,131 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
                  stored / 1e9, enl_bytes / 1e9, enl_maxsec, t1 - t0, t3 - t2, t4 - t3, t5 - t4, t6 - t5);
   }
   return e;
+}
+
+SweepStats Engine::sweep_part(bool l2r, int last) {
+  stats_ = SweepStats();
+  auto t0 = std::chrono::steady_clock::now();
+  be_->mark_begin();
+  double e = 0.0, tr = 0.0, tmax = 0.0;
+  if (l2r) {
+    if (last < 0 || last > n_ - 3) throw std::invalid_argument("sweep part: last bond out of range");
+    for (int i = 0; i <= last; ++i) {
+      e = optimize_bond(i, true, &tr);
+      tmax = std::max(tmax, tr);
+      if (n_ - i - 2 > 0) R_[n_ - i - 2].reset();
+    }
+  } else {
+    if (last < 1 || last > n_ - 2) throw std::invalid_argument("sweep part: last bond out of range");
+    if (!L_[n_ - 2]) throw std::runtime_error("state: an R->L part needs a completed L->R half-sweep");
+    for (int i = n_ - 2; i >= last; --i) {
+      e = optimize_bond(i, false, &tr);
+      tmax = std::max(tmax, tr);
+      if (i > 0) L_[i].reset();
+    }
+  }
+  sweep_device_ms = be_->mark_end();
+  be_->sync();
+  energy_ = e;
+  stats_.energy = e;
+  stats_.max_trunc = tmax;
+  sweep_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return stats_;
+}
+
+Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls) {
+  if (bond < 0 || bond > n_ - 2) throw std::invalid_argument("bond out of range");
+  if (!L_[bond] || !R_[n_ - bond - 2]) throw std::runtime_error("state: the blocks of this bond are not held");
+  BondSolve out;
+  // the side that was enlarged on the way here may be kept
+  std::unique_ptr<Block> Le, Re;
+  if (!l2r && bond < (int)keep_L_.size() && keep_L_[bond]) Le = std::move(keep_L_[bond]);
+  if (l2r && bond < (int)keep_R_.size() && keep_R_[bond]) Re = std::move(keep_R_[bond]);
+  if (!Le) Le = enlarge(*L_[bond], bond);
+  if (!Re) Re = enlarge(*R_[n_ - bond - 2], bond + 1);
+  HPsiPlan plan;
+  plan.psi = make_psi(Le->ops->basis, Re->ops->basis, n_elec_, two_s_);
+  const size_t len = plan.psi.size;
+  if (len == 0) throw std::runtime_error("empty two-site space at bond " + std::to_string(bond));
+  plan.in = (double*)be_->alloc(len * sizeof(double));
+  plan.out = (double*)be_->alloc(len * sizeof(double));
+  double* psi = (double*)be_->alloc(len * sizeof(double));
+  guess(bond, l2r, *Le, *Re, plan, psi);
+  const Options keep = opt_;
+  opt_.prec = p;
+  opt_.max_davidson_iter = std::max(1, max_iter);
+  opt_.davidson_tol = tol;
+  plan_hpsi(*Le, *Re, plan);
+  std::vector<double> ms;
+  call_ms_ = &ms;
+  int its = 0;
+  double e = 0.0;
+  try {
+    e = davidson(plan, psi, &its);
+    // pad with products on the result vector up to min_calls
+    while ((int)ms.size() < min_calls) {
+      be_->copy_d2d(plan.in, psi, len * sizeof(double));
+      be_->mark_begin();
+      apply_hpsi(plan);
+      ms.push_back(be_->mark_end());
+      if (plan.prec == Precision::TC_TF32X3) be_->check_device_flag();
+    }
+  } catch (...) {
+    call_ms_ = nullptr;
+    opt_ = keep;
+    throw;
+  }
+  call_ms_ = nullptr;
+  out.gap = last_gap_;
+  out.flops_per_call = plan.flops;
+  opt_ = keep;
+  // float64 Rayleigh quotient and residual of the vector
+  HPsiPlan p64;
+  p64.in = plan.in;
+  p64.out = plan.out;
+  const Precision kp = opt_.prec;
+  opt_.prec = Precision::FP64;
+  plan_hpsi(*Le, *Re, p64);
+  opt_.prec = kp;
+  be_->copy_d2d(p64.in, psi, len * sizeof(double));
+  apply_hpsi(p64);
+  double* d3 = (double*)be_->alloc(3 * sizeof(double));
+  be_->dots(psi, 1, len, len, p64.out, d3);
+  be_->dots(psi, 1, len, len, psi, d3 + 1);
+  double h2[2];
+  be_->copy_d2h(h2, d3, 2 * sizeof(double));
+  const double erq = h2[0] / h2[1];
+  // r = H psi / |psi| - E_rq psi / |psi|
+  be_->axpby(p64.out, 1.0 / std::sqrt(h2[1]), psi, -erq / std::sqrt(h2[1]), len);
+  be_->dots(p64.out, 1, len, len, p64.out, d3 + 2);
+  double r2;
+  be_->copy_d2h(&r2, d3 + 2, sizeof(double));
+  be_->sync();
+  be_->free(d3);
+  if (p64.dev) be_->free(p64.dev);
+  if (p64.diag) be_->free(p64.diag);
+  out.energy = e + e_core_;
+  out.energy_rq64 = erq + e_core_;
+  out.residual64 = std::sqrt(std::max(0.0, r2));
+  out.iterations = its;
+  out.calls = (int)ms.size();
+  out.call_ms = std::move(ms);
+  out.dim = len;
+  be_->free(psi);
+  be_->free(plan.in);
+  be_->free(plan.out);
+  if (plan.dev) be_->free(plan.dev);
+  if (plan.tc_pool) be_->free(plan.tc_pool);
+  if (plan.diag) be_->free(plan.diag);
+  // the enlarged side stays available for the next call at this bond
+  if (!l2r) {
+    if ((int)keep_L_.size() < n_) keep_L_.resize(n_);
+    keep_L_[bond] = std::move(Le);
+  } else {
+    if ((int)keep_R_.size() < n_) keep_R_.resize(n_);
+    keep_R_[bond] = std::move(Re);
+  }
+  return out;
 }
 
 SweepStats Engine::sweep() {

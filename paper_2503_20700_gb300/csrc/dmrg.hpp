@@ -173,9 +173,34 @@ class Engine {
   // One full sweep (L->R then R->L).  Returns the Davidson energy of the last
   // bond (including e_core).
   SweepStats sweep();
+  // Part of a sweep: L->R over bonds 0..last (l2r), or R->L over bonds
+  // n-2..last.  An L->R part starts a sweep; an R->L part needs the left
+  // blocks of a completed L->R half-sweep.  Afterwards the blocks of the next
+  // bond in that direction are held: bond last+1 after an L->R part, bond
+  // last-1 after an R->L part.
+  SweepStats sweep_part(bool l2r, int last);
+  // Davidson at `bond` on the blocks the context holds (after a partial
+  // sweep that stopped next to it), without decimation or any change of the
+  // stored state.  Each H_eff psi is timed with CUDA events; after Davidson
+  // stops, H_eff psi is applied to its vector until min_calls products ran.
+  struct BondSolve {
+    double energy = 0.0;       // Davidson eigenvalue (+ e_core)
+    double energy_rq64 = 0.0;  // float64 Rayleigh quotient of its vector (+ e_core)
+    double residual64 = 0.0;   // ||H psi - E_rq psi|| in float64, ||psi|| = 1
+    double gap = 0.0;          // second minus lowest Ritz value at exit
+    int iterations = 0, calls = 0;
+    double flops_per_call = 0.0;
+    std::vector<double> call_ms;  // CUDA-event time of every product
+    size_t dim = 0;
+  };
+  BondSolve solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls);
   double energy() const { return energy_; }
   int n() const { return n_; }
   void set_D(int D) { opt_.D = D; }
+  void set_davidson(int max_iter, double tol) {
+    opt_.max_davidson_iter = max_iter;
+    opt_.davidson_tol = tol;
+  }
   void set_precision(Precision p, Precision pr) {
     opt_.prec = p;
     opt_.prec_renorm = pr;
@@ -258,6 +283,9 @@ class Engine {
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);
   double davidson(struct HPsiPlan& plan, double* psi, int* iters);
+  std::vector<double>* call_ms_ = nullptr;  // when set: CUDA-event ms of every H_eff psi
+  double last_gap_ = 0.0;                   // Ritz gap at the last Davidson exit
+  int cur_i_ = -1;                          // bond the blocks are held for
   std::unique_ptr<SavedU> decimate(Block& enl, const struct HPsiPlan& plan, const double* psi,
                                    bool left, double* trunc);
   double optimize_bond(int i, bool left_to_right, double* trunc);

@@ -1,23 +1,32 @@
-// tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh).
+// tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh), persistent and
+// warp-specialised, with operand tiles brought in by TMA.
 //
-// Shared memory (bytes): X hi/lo planes (2 x 32 KB, 128 x 64, K-major) and
-// three 48 KB slots, each holding the operand tiles of one k-block of 32:
-//   stage 1: A hi | A lo (128 x 32 each, 16 KB) | P^T hi | P^T lo (64 x 32, 8 KB)
-//   stage 2: B hi | B lo (up to 128 x 32 each, 16 KB): one column half of
-//            the sigma tile (columns [0, 128) or [128, N))
-// all in the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices; 128 B between K-adjacent cores, 1 KB between 8-row groups for
-// 32-wide tiles, 2 KB for the 64-wide X).  TMEM: S in columns [0, 256), X' in
-// [256, 320).  The k-blocks of a task form one sequence: the MMAs of block b
-// are issued once its copies have landed (blocks b and b+1 are in flight),
-// then the copies of block b+2 refill the slot of block b-1 after its MMAs
-// completed.  Each slot has its own mbarrier (tcgen05.commit after the
-// block's MMAs) and every wait is bounded by 2 s of wall clock.  The FP32
-// accumulator S is drained into the task's partial tile of float pairs.
+// Shared memory (bytes): X hi | X lo planes (2 x 32 KB, 128 x 64, K-major,
+// 2 KB between 8-row groups) and three 48 KB stages, each holding the TMA
+// tiles of one k-block of 32:
+//   stage 1: A (128 rows: 32 KB, units interleaved hi/lo) | P^T (64 rows: 16 KB)
+//   stage 2: B (one 128-row column half of the sigma tile: 32 KB)
+// Inside a TMA tile, row group g occupies 2 KB: hi core matrices at 2048 g,
+// lo at 2048 g + 1024, k-cores 128 B apart.  TMEM: S in columns [0, 256),
+// X' double-buffered in [256, 320) and [320, 384).
+//
+// Warps: 0 producer (one lane issues cp.async.bulk.tensor into the stages;
+// full/empty mbarriers), 1 MMA issuer (one lane; owns the TMEM allocation),
+// 2..5 converters (TMEM lanes 32 (w % 4) .. +31: X' -> alpha X' as TF32
+// hi/lo planes in shared memory, and the drains of S into the task's partial
+// tile of float pairs).  The MMA order over the chunks c of the CTA's task
+// list is  S1(0), S1(1), S2(0), S1(2), S2(1), ...: the tensor pipe runs
+// stage 1 of the next chunk while the converters turn the last X' into X.
+// S is drained every kDrainItems items of a task and at its end.  Every wait
+// gives up after 2 s of wall clock: the CTA then sets the error flag, waits
+// (bounded) for its copies and MMAs in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 
@@ -28,29 +37,36 @@ namespace dmrg {
 
 namespace {
 
-constexpr int TM = kTcTileM, TNMAX = kTcTileN, KB = 32, JC = 64;
-constexpr uint32_t LBO = 128;
-constexpr uint32_t SBO32 = 1024;  // 8-row group stride of a 32-wide tile
-constexpr uint32_t SBO64 = 2048;  // of the 64-wide X tile
-constexpr int NSLOT = 3;
-constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_SLOT = 65536, SLOT = 49152;
-constexpr int SMEM_BYTES = OFF_SLOT + NSLOT * SLOT;  // 208 KB
-constexpr int HALF = 128;  // column half of the sigma tile per stage-2 block
-constexpr int kDrainItems = 4;  // items accumulated in FP32 before a float64 drain
+constexpr int TM = kTcTileM, TNMAX = kTcTileN, JC = 64, HALF = 128;
+constexpr uint32_t LBO = 128;        // between K-adjacent core matrices
+constexpr uint32_t SBO_OP = 2048;    // between 8-row groups of a TMA tile (hi and lo interleaved)
+constexpr uint32_t SBO_X = 2048;     // between 8-row groups of the 64-wide X planes
+constexpr int NSTAGE = 3;
+constexpr int STAGE = 49152;
+constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_STAGE = 65536;
+constexpr int SMEM_USED = OFF_STAGE + NSTAGE * STAGE;  // 208 KB
+constexpr int SMEM_BYTES = SMEM_USED + 1024;            // slack for 1 KB alignment of the base
+constexpr int A_BYTES = 32768, P_BYTES = 16384, B_BYTES = 32768;
+constexpr int kDrainItems = 4;
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
+constexpr int NTHREADS = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
+// barriers
+enum { B_FULL = 0, B_EMPTY = B_FULL + NSTAGE, B_XPF = B_EMPTY + NSTAGE, B_XPE = B_XPF + 2, B_XF = B_XPE + 2,
+       B_XE, B_SF, B_SE, B_DONE, B_COUNT };
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ int roundup32(int x) { return (x + 31) & ~31; }
 
 __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture; no swizzle
   return d;
 }
+// kind::tf32, FP32 accumulator, both operands K-major
 __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -66,399 +82,481 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
-  // a short spin first (the MMAs of a k-block take about a microsecond), then
-  // probes with a sleep between them, bounded by kWaitNs of wall clock
-  for (int i = 0; i < 128; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity));
-    if (done) return true;
-  }
+__device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait on the phase with the given parity; false after kWaitNs, or
+// at once when another role has aborted (abort != 0)
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (int i = 0; i < 256; ++i)
+    if (test_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity));
-    if (done) return true;
+    if (test_wait(bar, parity)) return true;
+    if (*abort) return false;
     if (global_ns() - t0 > kWaitNs) return false;
-    __nanosleep(64);
+    __nanosleep(32);
   }
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+// the same, with one outcome for the whole warp (the converter warps issue
+// .sync.aligned TMEM loads right after their waits)
+__device__ __forceinline__ bool wait_bar_warp(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const bool ok = wait_bar(bar, parity, abort);
+  return __all_sync(0xffffffffu, ok);
 }
-// 16-byte async copy; src_bytes = 0 fills the destination with zeros
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-// byte offset of element (r, k) (k multiple of 4) in a K-major tile with 8-row group stride sbo
-__device__ __forceinline__ uint32_t core_off(int r, int k, uint32_t sbo) {
-  return (uint32_t)(r >> 3) * sbo + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16;
-}
-__device__ __forceinline__ uint32_t word_off(int r, int k, uint32_t sbo) {
-  return core_off(r, k & ~3, sbo) + (uint32_t)(k & 3) * 4;
+// byte offset of element (r, k) (k multiple of 4) in the 64-wide X planes
+__device__ __forceinline__ uint32_t x_off(int r, int k) {
+  return (uint32_t)(r >> 3) * SBO_X + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16;
 }
 
-// copies rows [row0, min(row0 + nrows, rmax)) x cols [k0, k0 + 32) of a
-// split matrix into a K-major tile (both planes).  A thread keeps one 16-byte
-// column chunk and steps 16 rows at a time.  Tile rows at or beyond rmax are
-// not copied and keep earlier slot contents (zero at kernel start, later
-// finite operand values): rows of A or B there only reach output rows or
-// columns outside the block, which are never stored, and rows of P^T beyond
-// kb only reach columns of X that meet the zero padding of B's planes (or
-// zeros of a generated identity tile).
-__device__ __forceinline__ void load_tile(uint32_t dhi, uint32_t dlo, const TcMat& m, int row0, int nrows, int rmax,
-                                          int k0, int tid) {
-  const int rows = min(nrows, rmax - row0);
-  const int kc = (tid & 7) * 4;
-  int r = tid >> 3;
-  if (r >= rows) return;
-  const size_t step = (size_t)16 * m.ld;
-  size_t off = (size_t)(row0 + r) * m.ld + k0 + kc;
-  uint32_t o = core_off(r, kc, SBO32);
-  for (; r < rows; r += 16) {  // 16 rows = two 8-row core-matrix groups
-    cp16(dhi + o, m.hi + off, 16);
-    cp16(dlo + o, m.lo + off, 16);
-    off += step;
-    o += 2 * SBO32;
-  }
-}
-
-struct Cursor {
-  int ii, jc, jc_end, stage, k0, half;
+// The chunk sequence of one CTA: its tasks in list order, their items, and
+// the 64-wide chunks of psi's columns of every item.
+struct Walk {
+  const HpsiBlock* blocks;
+  const TcItem* items;
+  const HpsiTask* tasks;
+  const int* list;
+  int t, t_end;
+  HpsiTask tk;
+  int N;   // MMA width of the tile (multiple of 16)
+  int ii;  // item (global index)
+  int k;   // item position within the task
+  int jc;
+  TcItem it;
+  bool valid;
 };
-
-__device__ __forceinline__ void cursor_item(Cursor& c, const TcItem& it, int c0, int N) {
-  c.jc = 0;
-  c.jc_end = it.kb;
-  if (it.B.hi == nullptr) {
-    c.jc = c0;
-    c.jc_end = min(it.kb, c0 + N);
-  }
-  c.stage = it.A.hi ? 1 : 2;
-  c.k0 = 0;
-  c.half = 0;
+__device__ __forceinline__ void walk_task(Walk& w) {
+  w.tk = w.tasks[w.list[w.t]];
+  const HpsiBlock bk = w.blocks[w.tk.block];
+  const int nvalid = min(TNMAX, bk.n - w.tk.c0);
+  w.N = (nvalid + 15) & ~15;
+  w.ii = w.tk.it_begin;
+  w.k = 0;
+  w.jc = 0;
+  w.it = w.items[w.ii];
 }
-__device__ __forceinline__ int chunk_kspan(const Cursor& c) { return min(JC, roundup32(c.jc_end - c.jc)); }
-// advance to the next k-block; false at the end of the task
-// `it` is the cursor's current item (kept in registers): reloaded from the
-// item list only when the cursor moves to the next item
-__device__ __forceinline__ bool cursor_next(Cursor& c, TcItem& it, const TcItem* __restrict__ items, int it_end,
-                                            int c0, int N) {
-  if (c.stage == 1) {
-    c.k0 += KB;
-    if (c.k0 < roundup32(it.ka)) return true;
-    c.stage = 2;
-    c.k0 = 0;
-    return true;
-  }
-  if (c.half == 0 && N > HALF) {
-    c.half = 1;
-    return true;
-  }
-  c.half = 0;
-  c.k0 += KB;
-  if (c.k0 < chunk_kspan(c)) return true;
-  c.jc += JC;
-  if (c.jc < c.jc_end) {
-    c.stage = it.A.hi ? 1 : 2;
-    c.k0 = 0;
-    return true;
-  }
-  if (++c.ii >= it_end) return false;
-  it = items[c.ii];
-  cursor_item(c, it, c0, N);
-  return true;
+__device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, const TcItem* items,
+                                           const HpsiTask* tasks, const int* list, int t0, int t1) {
+  w.blocks = blocks;
+  w.items = items;
+  w.tasks = tasks;
+  w.list = list;
+  w.t = t0;
+  w.t_end = t1;
+  w.valid = t0 < t1;
+  if (w.valid) walk_task(w);
 }
+__device__ __forceinline__ void walk_next(Walk& w) {
+  w.jc += JC;
+  if (w.jc < w.it.kb) return;
+  ++w.ii;
+  ++w.k;
+  w.jc = 0;
+  if (w.k < w.tk.it_count) {
+    w.it = w.items[w.ii];
+    return;
+  }
+  if (++w.t >= w.t_end) {
+    w.valid = false;
+    return;
+  }
+  walk_task(w);
+}
+__device__ __forceinline__ bool last_chunk_of_item(const Walk& w) { return w.jc + JC >= w.it.kb; }
+__device__ __forceinline__ bool drain_point(const Walk& w) {
+  return last_chunk_of_item(w) && (((w.k + 1) % kDrainItems) == 0 || w.k + 1 == w.tk.it_count);
+}
+__device__ __forceinline__ int s1_blocks(const Walk& w) { return (w.it.ka + 31) >> 5; }
+__device__ __forceinline__ int s2_kblocks(const Walk& w) { return min(2, (w.it.kb - w.jc + 31) >> 5); }
+__device__ __forceinline__ int s2_halves(const Walk& w) { return w.N > HALF ? 2 : 1; }
 
-__global__ void __launch_bounds__(128, 1)
-    hpsi_tc_kernel(const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
-                   const HpsiTask* __restrict__ tasks, double* __restrict__ scratch, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bar[NSLOT];
+__global__ void __launch_bounds__(NTHREADS, 1)
+    hpsi_tc_kernel(const __grid_constant__ CUtensorMap map32, const __grid_constant__ CUtensorMap map16,
+                   const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
+                   const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
+                   const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar[B_COUNT];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const HpsiTask tk = tasks[blockIdx.x];
-  const HpsiBlock bk = blocks[tk.block];
-  const int nvalid = min(TNMAX, bk.n - tk.c0);
-  const int N = (nvalid + 15) & ~15;  // MMA N: multiple of 16
-  const int it_end = tk.it_begin + tk.it_count;
-  const uint32_t sbase = smem_u32(smraw);
-  const uint32_t xh = sbase + OFF_XH, xl = sbase + OFF_XL;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(512));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  // slots start at zero: tile rows that are never copied hold finite values
-  for (int e = tid; e < NSLOT * SLOT / 16; e += 128)
-    reinterpret_cast<uint4*>(smraw + OFF_SLOT)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __shared__ int consumed;  // stage fills the MMA warp has waited for
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sraw = smem_u32(smraw);
+  const uint32_t sbase = (sraw + 1023u) & ~1023u;
+  unsigned char* sgen = smraw + (sbase - sraw);
+  const int t0 = cta_off[blockIdx.x], t1 = cta_off[blockIdx.x + 1];
+  volatile int* abort = &abort_flag;
+
   if (tid == 0) {
-    for (int i = 0; i < NSLOT; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])));
+    for (int i = 0; i < NSTAGE; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_FULL + i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_EMPTY + i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XPF + i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XPE + i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XF])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XE])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_SF])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_SE])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_DONE])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
+    consumed = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tS = tmem_base + TCOL_S, tX = tmem_base + TCOL_X;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const int N1 = min(N, HALF), N2 = N - N1;  // MMA widths of the two column halves
-  const uint32_t id1 = idesc_tf32(TM, JC), id2a = idesc_tf32(TM, N1), id2b = idesc_tf32(TM, N2 > 0 ? N2 : 16);
+  const uint32_t tS = tmem_base + TCOL_S;
+  int produced = 0;  // stage fills issued (producer lane)
 
-  // issue the operand copies of the block at cursor c (item it) into slot s
-  auto produce = [&](const Cursor& c, const TcItem& it, int s) {
-    const uint32_t sl = sbase + OFF_SLOT + s * SLOT;
-    if (c.stage == 1) {
-      load_tile(sl, sl + 16384, it.A, tk.r0, TM, bk.m, c.k0, tid);
-      load_tile(sl + 32768, sl + 40960, it.Pt, c.jc, JC, it.kb, c.k0, tid);
-    } else if (it.B.hi != nullptr) {
-      load_tile(sl, sl + 16384, it.B, tk.c0 + c.half * HALF, c.half ? N2 : N1, bk.n, c.jc + c.k0, tid);
-    } else {
-      // identity on the right: B(n, k) = [c0 + n == jc + k0 + k]
-      float* bh = (float*)(smraw + OFF_SLOT + s * SLOT);
-      float* bl = (float*)(smraw + OFF_SLOT + s * SLOT + 16384);
-      const int n0 = c.half * HALF, nn = c.half ? N2 : N1;
-      for (int e = tid; e < nn * KB; e += 128) {
-        int n = e / KB, k = e % KB;
-        bool one = (tk.c0 + n0 + n == c.jc + c.k0 + k) && (tk.c0 + n0 + n < bk.n);
-        uint32_t o = word_off(n, k, SBO32) >> 2;
-        bh[o] = one ? 1.0f : 0.0f;
-        bl[o] = 0.0f;
-      }
-    }
-    asm volatile("cp.async.commit_group;");
-  };
-  // bounded wait on the commit of block b; failure sets the abort flag
-  auto wait_block = [&](int b) {
-    if (b < 0) return;
-    if (!wait_bar(&bar[b % NSLOT], (uint32_t)((b / NSLOT) & 1))) abort_flag = 1;
-  };
-
-  // S (FP32, TMEM) is added to the task's partial tile every kDrainItems
-  // items and at the end, so FP32 accumulation spans a few items only.
-  // The first drain stores, later ones add.
-  bool s_started = false, s_started_b = false;  // first / second column half written since the last drain
-  bool drained = false;
-  auto drain = [&]() {
-    // the task's partial tile holds float pairs (hi, lo): a TwoSum (Knuth)
-    // adds each FP32 value of S with its rounding error kept in lo, on the
-    // FP32 pipe (the float64 conversion happens once, in the reduction)
-    const int r = tid;
-    float2* d = reinterpret_cast<float2*>(scratch + tk.part) + (size_t)r * TNMAX;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      if (s_started) {
-        tmem_ld16(tS + lane_base + c0, v);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
-      }
-      if (!drained) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) d[c0 + j] = make_float2(v[j], 0.0f);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float2 a = d[c0 + j];
-          const float sum = __fadd_rn(a.x, v[j]);
-          const float bv = __fsub_rn(sum, a.x);
-          const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(v[j], bv));
-          d[c0 + j] = make_float2(sum, __fadd_rn(a.y, err));
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map32)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map16)) : "memory");
+      int q = 0;
+      bool ok = true;
+      auto acquire = [&](int& s) -> bool {
+        s = q % NSTAGE;
+        const uint32_t par = (uint32_t)(((q / NSTAGE) & 1) ^ 1);
+        if (!wait_bar(&bar[B_EMPTY + s], par, abort)) return false;
+        return true;
+      };
+      auto s1 = [&](const Walk& w) -> bool {
+        const int nb = s1_blocks(w);
+        for (int kk = 0; kk < nb; ++kk) {
+          int s;
+          if (!acquire(s)) return false;
+          const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+          arrive_expect(&bar[B_FULL + s], A_BYTES + P_BYTES);
+          tma_load(st, &map32, w.it.A.unit + (kk * w.it.A.groups + (w.tk.r0 >> 3)) * 2, &bar[B_FULL + s]);
+          tma_load(st + A_BYTES, &map16, w.it.Pt.unit + (kk * w.it.Pt.groups + (w.jc >> 3)) * 2, &bar[B_FULL + s]);
+          ++q;
+        }
+        return true;
+      };
+      auto s2 = [&](const Walk& w) -> bool {
+        const int nh = s2_halves(w), nk = s2_kblocks(w);
+        for (int h = 0; h < nh; ++h)
+          for (int kk = 0; kk < nk; ++kk) {
+            int s;
+            if (!acquire(s)) return false;
+            const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+            arrive_expect(&bar[B_FULL + s], B_BYTES);
+            tma_load(st, &map32,
+                     w.it.B.unit + (((w.jc >> 5) + kk) * w.it.B.groups + ((w.tk.c0 + h * HALF) >> 3)) * 2,
+                     &bar[B_FULL + s]);
+            ++q;
+          }
+        return true;
+      };
+      Walk cur;
+      walk_start(cur, blocks, items, tasks, cta_task, t0, t1);
+      if (cur.valid) {
+        ok = s1(cur);
+        while (ok) {
+          Walk nxt = cur;
+          walk_next(nxt);
+          if (nxt.valid && !(ok = s1(nxt))) break;
+          if (!(ok = s2(cur))) break;
+          if (!nxt.valid) break;
+          cur = nxt;
         }
       }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(err, 1);
+      }
+      produced = q;
     }
-    drained = true;
-  };
-
-  Cursor cur;
-  cur.ii = tk.it_begin;
-  TcItem it_cur = items[cur.ii];
-  cursor_item(cur, it_cur, tk.c0, N);
-  // blocks b+1 and b+2 (n1, n2) are prefetched ahead of block b
-  Cursor n1 = cur, n2;
-  TcItem it_n1 = it_cur, it_n2;
-  bool has1 = cursor_next(n1, it_n1, items, it_end, tk.c0, N), has2 = false;
-  n2 = n1;
-  it_n2 = it_n1;
-  if (has1) has2 = cursor_next(n2, it_n2, items, it_end, tk.c0, N);
-  int b = 0;
-  produce(cur, it_cur, 0);
-  if (has1) produce(n1, it_n1, 1);
-  for (;;) {
-    // copies in flight: blocks b and b+1 (b+2 is issued after the MMAs of b)
-    if (has1) {
-      asm volatile("cp.async.wait_group 1;");
-    } else {
-      asm volatile("cp.async.wait_group 0;");
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (abort_flag) break;
-    const TcItem& it = it_cur;
-    if (cur.stage == 2 && cur.k0 == 0 && cur.half == 0) {
-      // X = alpha X' (or alpha P for an identity left operand) -> hi/lo planes;
-      // the commit of block b-1 covers every earlier MMA (stage 1 of this
-      // chunk, stage 2 of the previous one that read X)
-      if (b >= 1) wait_block(b - 1);
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int r = tid;
-      float* xhp = (float*)(smraw + OFF_XH);
-      float* xlp = (float*)(smraw + OFF_XL);
-      if (it.A.hi != nullptr) {
-        // the four 16-column loads of the row are issued before one wait
-        uint32_t q[64];
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int q = 0, nd = 0, c = 0;  // stage fills consumed, drains requested, chunks issued in S1
+      bool need_se = false, fresh0 = true, fresh1 = true, ok = true;
+      const uint32_t xh = sbase + OFF_XH, xl = sbase + OFF_XL;
+      auto take = [&](int& s) -> bool {
+        s = q % NSTAGE;
+        if (!wait_bar(&bar[B_FULL + s], (uint32_t)((q / NSTAGE) & 1), abort)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        return true;
+      };
+      auto s1 = [&](const Walk& w, int chunk) -> bool {
+        const int b = chunk & 1;
+        if (chunk >= 2 && !wait_bar(&bar[B_XPE + b], (uint32_t)(((chunk >> 1) - 1) & 1), abort)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t tX = tmem_base + TCOL_X + 64 * b;
+        const uint32_t id = idesc_tf32(TM, JC);
+        const int nb = s1_blocks(w);
+        for (int kk = 0; kk < nb; ++kk) {
+          int s;
+          if (!take(s)) return false;
+          const uint32_t st = sbase + OFF_STAGE + s * STAGE;
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(q[16 * c4 + 0]), "=r"(q[16 * c4 + 1]), "=r"(q[16 * c4 + 2]), "=r"(q[16 * c4 + 3]),
-                "=r"(q[16 * c4 + 4]), "=r"(q[16 * c4 + 5]), "=r"(q[16 * c4 + 6]), "=r"(q[16 * c4 + 7]),
-                "=r"(q[16 * c4 + 8]), "=r"(q[16 * c4 + 9]), "=r"(q[16 * c4 + 10]), "=r"(q[16 * c4 + 11]),
-                "=r"(q[16 * c4 + 12]), "=r"(q[16 * c4 + 13]), "=r"(q[16 * c4 + 14]), "=r"(q[16 * c4 + 15])
-              : "r"(tX + lane_base + 16 * c4));
+          for (int k8 = 0; k8 < 4; ++k8) {
+            const uint32_t ko = (uint32_t)k8 * 2 * LBO;
+            const uint64_t ah = desc(st + ko, SBO_OP), al = desc(st + 1024 + ko, SBO_OP);
+            const uint64_t ph = desc(st + A_BYTES + ko, SBO_OP), pl = desc(st + A_BYTES + 1024 + ko, SBO_OP);
+            mma_tf32(tX, al, ph, id, (kk > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32(tX, ah, pl, id, 1u);
+            mma_tf32(tX, ah, ph, id, 1u);
+          }
+          commit(&bar[B_EMPTY + s]);
+          ++q;
+        }
+        commit(&bar[B_XPF + b]);
+        return true;
+      };
+      auto s2 = [&](const Walk& w, int chunk) -> bool {
+        if (!wait_bar(&bar[B_XF], (uint32_t)(chunk & 1), abort)) return false;
+        if (need_se) {
+          if (!wait_bar(&bar[B_SE], (uint32_t)((nd - 1) & 1), abort)) return false;
+          need_se = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int nh = s2_halves(w), nk = s2_kblocks(w);
+        const int N1 = min(w.N, HALF), N2 = w.N - N1;
+        for (int h = 0; h < nh; ++h) {
+          const uint32_t id = idesc_tf32(TM, h ? N2 : N1);
+          const uint32_t dS = tS + (uint32_t)(h * HALF);
+          bool& fresh = h ? fresh1 : fresh0;
+          for (int kk = 0; kk < nk; ++kk) {
+            int s;
+            if (!take(s)) return false;
+            const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+#pragma unroll
+            for (int k8 = 0; k8 < 4; ++k8) {
+              const uint32_t ko = (uint32_t)k8 * 2 * LBO;
+              const uint32_t xo = (uint32_t)kk * 8 * LBO + ko;
+              const uint64_t xhd = desc(xh + xo, SBO_X), xld = desc(xl + xo, SBO_X);
+              const uint64_t bh = desc(st + ko, SBO_OP), bl = desc(st + 1024 + ko, SBO_OP);
+              mma_tf32(dS, xld, bh, id, fresh ? 0u : 1u);
+              fresh = false;
+              mma_tf32(dS, xhd, bl, id, 1u);
+              mma_tf32(dS, xhd, bh, id, 1u);
+            }
+            commit(&bar[B_EMPTY + s]);
+            ++q;
+          }
+        }
+        commit(&bar[B_XE]);
+        if (drain_point(w)) {
+          commit(&bar[B_SF]);
+          ++nd;
+          need_se = true;
+          fresh0 = fresh1 = true;
+        }
+        return true;
+      };
+      Walk cur;
+      walk_start(cur, blocks, items, tasks, cta_task, t0, t1);
+      if (cur.valid) {
+        ok = s1(cur, c++);
+        int c2 = 0;
+        while (ok) {
+          Walk nxt = cur;
+          walk_next(nxt);
+          if (nxt.valid && !(ok = s1(nxt, c++))) break;
+          if (!(ok = s2(cur, c2++))) break;
+          if (!nxt.valid) break;
+          cur = nxt;
+        }
+      }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(err, 1);
+      }
+      consumed = q;
+      // every MMA issued by this thread has completed once B_DONE fires
+      // (waited for also after an abort, bounded)
+      commit(&bar[B_DONE]);
+      const unsigned long long t0w = global_ns();
+      while (!test_wait(&bar[B_DONE], 0u) && global_ns() - t0w < kWaitNs) __nanosleep(64);
+    }
+  } else {
+    // ------------------------------------------------------------ converters
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;  // TMEM lane = tile row
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    float2* const part_base = reinterpret_cast<float2*>(scratch);
+    int nd = 0;  // drains done
+    bool ok = true;
+    auto convert = [&](const Walk& w, int chunk) -> bool {
+      const int b = chunk & 1;
+      if (!wait_bar_warp(&bar[B_XPF + b], (uint32_t)((chunk >> 1) & 1), abort)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t tX = tmem_base + TCOL_X + 64 * b + lane_base;
+      uint32_t q[64];
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(q[16 * c4 + 0]), "=r"(q[16 * c4 + 1]), "=r"(q[16 * c4 + 2]), "=r"(q[16 * c4 + 3]),
+              "=r"(q[16 * c4 + 4]), "=r"(q[16 * c4 + 5]), "=r"(q[16 * c4 + 6]), "=r"(q[16 * c4 + 7]),
+              "=r"(q[16 * c4 + 8]), "=r"(q[16 * c4 + 9]), "=r"(q[16 * c4 + 10]), "=r"(q[16 * c4 + 11]),
+              "=r"(q[16 * c4 + 12]), "=r"(q[16 * c4 + 13]), "=r"(q[16 * c4 + 14]), "=r"(q[16 * c4 + 15])
+            : "r"(tX + 16 * c4));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      arrive(&bar[B_XPE + b]);
+      // X of the previous chunk must have been read by its stage-2 MMAs
+      if (chunk >= 1 && !wait_bar_warp(&bar[B_XE], (uint32_t)((chunk - 1) & 1), abort)) return false;
+      const float al = (float)w.it.alpha;
+#pragma unroll
+      for (int j = 0; j < JC; j += 4) {
+        float4 hv, lv;
+        float x0 = al * __uint_as_float(q[j]), x1 = al * __uint_as_float(q[j + 1]);
+        float x2 = al * __uint_as_float(q[j + 2]), x3 = al * __uint_as_float(q[j + 3]);
+        hv.x = __uint_as_float(tf32(x0));
+        hv.y = __uint_as_float(tf32(x1));
+        hv.z = __uint_as_float(tf32(x2));
+        hv.w = __uint_as_float(tf32(x3));
+        lv.x = __uint_as_float(tf32(x0 - hv.x));
+        lv.y = __uint_as_float(tf32(x1 - hv.y));
+        lv.z = __uint_as_float(tf32(x2 - hv.z));
+        lv.w = __uint_as_float(tf32(x3 - hv.w));
+        const uint32_t o = x_off(r, j);
+        *reinterpret_cast<float4*>(sgen + OFF_XH + o) = hv;
+        *reinterpret_cast<float4*>(sgen + OFF_XL + o) = lv;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      arrive(&bar[B_XF]);
+      return true;
+    };
+    // S (FP32, TMEM) is added to the task's partial tile of float pairs (hi,
+    // lo) by a TwoSum (Knuth) on the FP32 pipe; the first drain of a task
+    // stores.  N columns of every row are written; the reduction reads the
+    // valid ones only.
+    auto drain = [&](long long part, int N, bool first) -> bool {
+      if (!wait_bar_warp(&bar[B_SF], (uint32_t)(nd & 1), abort)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float2* d = part_base + part + (size_t)r * TNMAX;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tS + lane_base + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const float al = (float)it.alpha;
+        const int nc = min(32, N - c0);
+        if (first) {
 #pragma unroll
-        for (int j = 0; j < JC; ++j) {
-          float x = al * __uint_as_float(q[j]);
-          uint32_t h = tf32(x);
-          uint32_t o = word_off(r, j, SBO64) >> 2;
-          xhp[o] = __uint_as_float(h);
-          xlp[o] = __uint_as_float(tf32(x - __uint_as_float(h)));
-        }
-      } else {
-        const int gr = tk.r0 + r;
-        for (int c = 0; c < JC; ++c) {
-          int gc = cur.jc + c;
-          double x = (gr < bk.m && gc < it.kb) ? it.alpha * it.P[(size_t)gr * it.ldp + gc] : 0.0;
-          uint32_t h = tf32((float)x);
-          uint32_t o = word_off(r, c, SBO64) >> 2;
-          xhp[o] = __uint_as_float(h);
-          xlp[o] = __uint_as_float(tf32((float)(x - (double)__uint_as_float(h))));
+          for (int j = 0; j < 32; ++j)
+            if (j < nc) d[c0 + j] = make_float2(__uint_as_float(v[j]), 0.0f);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j >= nc) break;
+            const float x = __uint_as_float(v[j]);
+            const float2 a = d[c0 + j];
+            const float sum = __fadd_rn(a.x, x);
+            const float bv = __fsub_rn(sum, a.x);
+            const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
+            d[c0 + j] = make_float2(sum, __fadd_rn(a.y, e));
+          }
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;");
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (abort_flag) break;
-    }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sl = sbase + OFF_SLOT + (b % NSLOT) * SLOT;
-      if (cur.stage == 1) {
-#pragma unroll
-        for (int s = 0; s < KB / 8; ++s) {
-          const uint32_t ko = (uint32_t)s * 2 * LBO;
-          uint64_t ah = desc(sl + ko, SBO32), al = desc(sl + 16384 + ko, SBO32);
-          uint64_t ph = desc(sl + 32768 + ko, SBO32), pl = desc(sl + 40960 + ko, SBO32);
-          mma_tf32(tX, al, ph, id1, (cur.k0 > 0 || s > 0) ? 1u : 0u);
-          mma_tf32(tX, ah, pl, id1, 1u);
-          mma_tf32(tX, ah, ph, id1, 1u);
-        }
-      } else {
-        const uint32_t xo = (uint32_t)(cur.k0 / 4) * LBO;
-        const uint32_t dS = tS + (uint32_t)(cur.half * HALF);
-        const uint32_t id2 = cur.half ? id2b : id2a;
-        // the first MMA into each column half overwrites it
-        const bool fresh = cur.half == 0 ? !s_started : !s_started_b;
-#pragma unroll
-        for (int s = 0; s < KB / 8; ++s) {
-          const uint32_t ko = (uint32_t)s * 2 * LBO;
-          uint64_t ah = desc(xh + xo + ko, SBO64), al = desc(xl + xo + ko, SBO64);
-          uint64_t bh = desc(sl + ko, SBO32), bl = desc(sl + 16384 + ko, SBO32);
-          mma_tf32(dS, al, bh, id2, (!fresh || s > 0) ? 1u : 0u);
-          mma_tf32(dS, ah, bl, id2, 1u);
-          mma_tf32(dS, ah, bh, id2, 1u);
-        }
+      arrive(&bar[B_SE]);
+      ++nd;
+      return true;
+    };
+    Walk w;
+    walk_start(w, blocks, items, tasks, cta_task, t0, t1);
+    int chunk = 0, drains_in_task = 0, last_t = -1;
+    bool pend = false, pend_first = false;
+    long long pend_part = 0;
+    int pend_N = 0;
+    while (ok && w.valid) {
+      if (w.t != last_t) {
+        last_t = w.t;
+        drains_in_task = 0;
       }
-      commit(&bar[b % NSLOT]);
+      if (!(ok = convert(w, chunk++))) break;
+      if (pend && !(ok = drain(pend_part, pend_N, pend_first))) break;
+      pend = drain_point(w);
+      if (pend) {
+        pend_part = w.tk.part;
+        pend_N = w.N;
+        pend_first = drains_in_task == 0;
+        ++drains_in_task;
+      }
+      walk_next(w);
     }
-    // uniform over the CTA
-    if (cur.stage == 2) {
-      if (cur.half == 0) s_started = true;
-      else s_started_b = true;
+    if (ok && pend) ok = drain(pend_part, pend_N, pend_first);
+    if (!ok) {
+      *abort = 1;
+      if (lane == 0) atomicExch(err, 1);
     }
-    // prefetch block b+2 into the slot of block b-1 once its MMAs are done;
-    // the MMAs of b are already queued behind them
-    if (has2) {
-      wait_block(b - 1);
-      produce(n2, it_n2, (b + 2) % NSLOT);
-    }
-    if (!has1) break;
-    if (n1.ii != cur.ii && ((n1.ii - tk.it_begin) % kDrainItems) == 0 && s_started) {
-      // item boundary: drain S once its MMAs are done, then let the next
-      // stage-2 MMA overwrite it
-      wait_block(b);
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      __syncthreads();
-      if (abort_flag) break;
-      drain();
-      s_started = s_started_b = false;
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-    }
-    cur = n1;
-    it_cur = it_n1;
-    n1 = n2;
-    it_n1 = it_n2;
-    has1 = has2;
-    if (has1) {
-      has2 = cursor_next(n2, it_n2, items, it_end, tk.c0, N);
-    } else {
-      has2 = false;
-    }
-    ++b;
   }
-  // wait for the last blocks (after an abort, whatever may be in flight)
-  wait_block(b);
-  wait_block(b - 1);
-  wait_block(b - 2);
-  asm volatile("cp.async.wait_group 0;");
-  asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
-  if (abort_flag) {
-    if (tid == 0) atomicExch(err, 1);
-  } else if (s_started || !drained) {
-    drain();
+  if (warp == 0 && lane == 0 && *abort) {
+    // copies still in flight land before the CTA exits
+    for (int q = consumed; q < produced; ++q) {
+      uint32_t par = (uint32_t)((q / NSTAGE) & 1);
+      const unsigned long long t0w = global_ns();
+      while (!test_wait(&bar[B_FULL + q % NSTAGE], par) && global_ns() - t0w < kWaitNs) __nanosleep(64);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
 }
 
-// partial tiles are TM x TNMAX (row stride TNMAX)
+// partial tiles are TM x TNMAX (row stride TNMAX); CTA (tile, y) sums rows
+// [16 y, 16 y + 16) of a tile over its chunks in fixed order
 __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiReduce* __restrict__ reds,
                                const double* __restrict__ scratch) {
   const HpsiReduce rd = reds[blockIdx.x];
   const HpsiBlock bk = blocks[rd.block];
   const int nvalid = min(TNMAX, bk.n - rd.c0);
-  for (int e = threadIdx.x; e < TM * TNMAX; e += blockDim.x) {
-    int r = e / TNMAX, c = e % TNMAX;
-    int gr = rd.r0 + r;
-    if (gr >= bk.m || c >= nvalid) continue;
-    const float2* part = reinterpret_cast<const float2*>(scratch + rd.part0) + e;
+  const int c = threadIdx.x;
+  if (c >= nvalid) return;
+  for (int r = blockIdx.y * 16; r < blockIdx.y * 16 + 16; ++r) {
+    const int gr = rd.r0 + r;
+    if (gr >= bk.m) break;
+    const float2* part = reinterpret_cast<const float2*>(scratch + rd.part0) + (size_t)r * TNMAX + c;
     double acc = 0.0;
     for (int p = 0; p < rd.nparts; ++p) {
       const float2 v = part[(long long)p * TM * TNMAX];
@@ -468,43 +566,88 @@ __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiR
   }
 }
 
-__global__ void split_kernel(const SplitJob* __restrict__ jobs, int n) {
+// unit pairs of job j: pair p = kblock * G + g holds hi (unit 2p) and lo
+// (unit 2p + 1) of rows [8g, 8g + 8) x cols [32 kblock, 32 kblock + 32)
+__global__ void split_kernel(const SplitJob* __restrict__ jobs, int n, float* __restrict__ pool) {
   for (int j = blockIdx.x; j < n; j += gridDim.x) {
     const SplitJob jb = jobs[j];
-    const size_t total = (size_t)jb.rows * jb.ldd;
-    for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
-      int r = (int)(e / jb.ldd), c = (int)(e % jb.ldd);
+    const int G = (jb.rows + 7) >> 3;
+    const size_t pairs = (size_t)G * ((jb.cols + 31) >> 5);
+    float* const base = pool + (size_t)jb.unit * kTcUnitFloats;
+    for (size_t e = threadIdx.x; e < pairs * kTcUnitFloats; e += blockDim.x) {
+      const size_t pr = e / kTcUnitFloats;
+      const int w = (int)(e % kTcUnitFloats);
+      const int kbk = (int)(pr / G), g = (int)(pr % G);
+      const int r = 8 * g + ((w >> 2) & 7);
+      const int k = 32 * kbk + 4 * (w >> 5) + (w & 3);
       double v = 0.0;
-      if (c < jb.cols) v = jb.trans ? jb.src[(size_t)c * jb.ld + r] : jb.src[(size_t)r * jb.ld + c];
-      float h = __uint_as_float(tf32((float)v));
-      jb.hi[e] = h;
-      jb.lo[e] = __uint_as_float(tf32((float)(v - (double)h)));
+      if (r < jb.rows && k < jb.cols) {
+        if (jb.src == nullptr) v = (r == k) ? 1.0 : 0.0;
+        else v = jb.trans ? jb.src[(size_t)k * jb.ld + r] : jb.src[(size_t)r * jb.ld + k];
+      }
+      const float h = __uint_as_float(tf32((float)v));
+      float* u = base + pr * 2 * kTcUnitFloats;
+      u[w] = h;
+      u[kTcUnitFloats + w] = __uint_as_float(tf32((float)(v - (double)h)));
     }
   }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D map over the pool: 256 floats (one unit) per row, `rows` rows per box
+void make_map(CUtensorMap* m, const void* pool, size_t units, int rows) {
+  auto fn = encode_fn();
+  if (!fn) throw std::runtime_error("cuda: cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {(cuuint64_t)kTcUnitFloats, (cuuint64_t)units};
+  cuuint64_t strides[1] = {(cuuint64_t)kTcUnitFloats * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kTcUnitFloats, (cuuint32_t)rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(pool), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuda: tensor map encoding failed (" + std::to_string((int)r) + ")");
+}
+
 }  // namespace
 
-void split_launch(const SplitJob* jobs, int n, cudaStream_t st) {
+void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st) {
   if (n <= 0) return;
-  split_kernel<<<std::min(n, 152 * 8), 256, 0, st>>>(jobs, n);
+  split_kernel<<<std::min(n, 152 * 8), 256, 0, st>>>(jobs, n, pool);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: split launch: ") + cudaGetErrorString(e));
 }
 
-void hpsi_tc_launch(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
-                    const HpsiReduce* reds, int nreds, double* scratch, int* err, cudaStream_t st) {
+void hpsi_tc_launch(const TcLaunch& L, int* err, cudaStream_t st) {
   {
     cudaError_t e = ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES);
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc attribute: ") + cudaGetErrorString(e));
   }
-  if (ntasks > 0) {
-    hpsi_tc_kernel<<<ntasks, 128, SMEM_BYTES, st>>>(blocks, items, tasks, scratch, err);
+  if (L.ncta > 0) {
+    if (!L.pool || L.units == 0) throw std::runtime_error("internal: tcgen05 contraction without a split pool");
+    if (((uintptr_t)L.pool & 15) != 0) throw std::runtime_error("internal: split pool not 16-byte aligned");
+    CUtensorMap m32, m16;
+    make_map(&m32, L.pool, L.units, 32);
+    make_map(&m16, L.pool, L.units, 16);
+    hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m16, L.blocks, L.items, L.tasks, L.cta_off,
+                                                          L.cta_task, L.scratch, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }
-  if (nreds > 0) {
-    hpsi_tc_reduce<<<nreds, 256, 0, st>>>(blocks, reds, scratch);
+  if (L.nreds > 0) {
+    hpsi_tc_reduce<<<dim3(L.nreds, TM / 16), TNMAX, 0, st>>>(L.blocks, L.reds, L.scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc reduce: ") + cudaGetErrorString(e));
   }

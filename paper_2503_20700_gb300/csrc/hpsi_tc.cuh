@@ -3,18 +3,33 @@
 //
 //   sigma(a', b') += sum_i alpha_i op(A_i) P_i op(B_i)^T
 //
-// Operands are split once into TF32 hi/lo planes (float32 storage,
-// row-major, row length padded to a multiple of 32 with zeros): the operator
-// blocks once per bond (they are constant during Davidson), the psi blocks
-// once per product (transposed, so that both products are K-major).  One CTA
-// owns a 128 x N (N <= 256) tile of a sigma block and a chunk of its items;
-// per item and per 64-wide chunk j of psi's columns
+// Operands are split into TF32 hi/lo planes once: the operator blocks once
+// per bond (they are constant during Davidson), the psi blocks before every
+// product (transposed, so that both products are K-major).  Identity factors
+// become explicit identity planes, so every item has the same three operands.
+//
+// Plane layout in the pool (1 KB units, 256 floats each).  A matrix of R rows
+// and K columns has G = ceil(R/8) row groups and ceil(K/32) k-blocks; unit
+// 2 (kb G + g) holds the hi plane and unit 2 (kb G + g) + 1 the lo plane of
+// rows [8g, 8g+8) x columns [32kb, 32kb+32), each as eight 8-row x 16-byte
+// core matrices (k-core c at byte 128 c, row r at byte 16 r within it), the
+// canonical no-swizzle K-major layout of the tensor core.  A 128-row tile of
+// one k-block is therefore 32 consecutive units and a 64-row tile 16: one TMA
+// box each (a 2D tensor map over the pool with 1 KB rows).  Rows and columns
+// beyond the matrix are zero inside a plane; a box that runs past a plane
+// reads other planes' finite values, which only reach unstored output rows
+// and columns or meet zero padding.
+//
+// One CTA of the persistent kernel walks its list of tasks (a 128 x N, N <=
+// 256, tile of a sigma block and a chunk of its items).  Per item and per
+// 64-wide chunk j of psi's columns:
 //   stage 1:  X' = op(A)(tile rows, :) P(:, j)           (TMEM, 128 x 64)
-//   X = alpha X'  ->  hi/lo TF32 planes in shared memory
+//   X = alpha X'  ->  hi/lo TF32 planes in shared memory  (converter warps)
 //   stage 2:  S += X op(B)(tile cols, j)^T               (TMEM, 128 x N)
-// with 16-byte cp.async copies in three slots: the MMAs of a k-block are
-// issued once its copies land, then the copies two blocks ahead refill the
-// slot whose MMAs precede them.
+// Warp roles: one producer warp issues the TMA copies into a ring of stages,
+// one warp issues the MMAs (stage 1 of chunk j+1 before stage 2 of chunk j),
+// four warps convert X' and drain S into the task's partial tile of float
+// pairs.  Every wait is bounded.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -26,59 +41,72 @@
 
 namespace dmrg {
 
-// hi/lo TF32 planes of a matrix; rows = output index of the product, columns
-// = contraction index; ld = padded row length (multiple of 32 floats)
+// split plane pair of a matrix in the pool: first unit and row groups
 struct TcMat {
-  const float* hi = nullptr;
-  const float* lo = nullptr;
-  int ld = 0;
+  int unit = 0;
+  int groups = 0;
 };
 
 struct TcItem {
-  TcMat A;             // op(A): m' x ka; A.hi == nullptr: identity (ka == m')
-  TcMat Pt;            // P^T: kb x ka
-  const double* P;     // P (ka x kb, float64, row length ldp) for identity-A items
-  int ldp;
-  TcMat B;             // op(B): n' x kb; B.hi == nullptr: identity (kb == n')
+  TcMat A;   // op(A): m' x ka
+  TcMat Pt;  // P^T: kb x ka
+  TcMat B;   // op(B): n' x kb
   int ka, kb;
   double alpha;
 };
 
-// dst (rows x ldd, float32 hi/lo) = split(op(src)) with op(src)(r, c) =
-// trans ? src[c*ld + r] : src[r*ld + c] for c < cols, zero for cols <= c < ldd
+// Split of one matrix into its plane pair: op(src)(r, c) =
+// trans ? src[c*ld + r] : src[r*ld + c] for r < rows, c < cols (src ==
+// nullptr: the identity), zero elsewhere in the plane.
 struct SplitJob {
   const double* src;
   int rows, cols, ld, trans;
-  float* hi;
-  float* lo;
-  int ldd;
+  int unit;  // first unit of the plane pair
 };
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
+constexpr int kTcUnitFloats = 256;  // one 1 KB unit
 
 struct TcPlan {
-  std::vector<SplitJob> op_jobs;   // operator blocks (run once per plan)
+  std::vector<SplitJob> op_jobs;   // operator blocks and identities (run once per plan)
   std::vector<SplitJob> psi_jobs;  // psi blocks (run before every product)
   std::vector<TcItem> items;
   std::vector<HpsiTask> tasks;     // (block, r0, c0, items, partial offset)
   std::vector<HpsiReduce> reds;    // one per tile: its chunks' partial tiles into sigma
+  std::vector<int> cta_off;        // tasks of CTA c: cta_task[cta_off[c] .. cta_off[c+1])
+  std::vector<int> cta_task;       // task indices, each CTA's list in decreasing cost
   size_t scratch = 0;              // 8-byte words of partial tiles (kTcTileM x kTcTileN float pairs per task)
-  size_t pool_bytes = 0;           // split planes
+  size_t units = 0;                // pool size in 1 KB units
+  size_t pool_bytes = 0;
 };
 
-// Split planes, items and tasks for the fused contraction of `blocks`/`items`
-// (device pointers inside).  alloc(bytes) returns the device memory of the
-// split planes; the caller owns it.
+// Split planes, items, tasks and the per-CTA task lists of the fused
+// contraction of `blocks`/`items` (device pointers inside).  alloc(bytes)
+// returns the device memory of the pool; the caller owns it.  ncta: CTAs of
+// the persistent launch (0: one per SM of a 152-SM device).
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
-                     const std::function<void*(size_t)>& alloc, TcPlan& plan);
+                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta = 0);
 
-// Runs the split jobs (device list of n jobs).
-void split_launch(const SplitJob* jobs, int n, cudaStream_t st);
+// Device-side lists and the pool of one planned contraction.
+struct TcLaunch {
+  const HpsiBlock* blocks = nullptr;
+  const TcItem* items = nullptr;
+  const HpsiTask* tasks = nullptr;
+  const int* cta_off = nullptr;
+  const int* cta_task = nullptr;
+  int ncta = 0;
+  const HpsiReduce* reds = nullptr;
+  int nreds = 0;
+  double* scratch = nullptr;
+  const void* pool = nullptr;
+  size_t units = 0;
+};
 
-// The fused kernel and the reduction of item chunks (device lists).  err: a
-// device int set to 1 when a bounded wait ran out (the CTA then skips the
-// rest of its work).
-void hpsi_tc_launch(const HpsiBlock* blocks, const TcItem* items, const HpsiTask* tasks, int ntasks,
-                    const HpsiReduce* reds, int nreds, double* scratch, int* err, cudaStream_t st);
+// Runs the split jobs (device list of n jobs) into the pool.
+void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st);
+
+// The persistent contraction and the reduction of item chunks.  err: a
+// device int set to 1 when a bounded wait ran out (the CTA then stops).
+void hpsi_tc_launch(const TcLaunch& L, int* err, cudaStream_t st);
 
 }  // namespace dmrg

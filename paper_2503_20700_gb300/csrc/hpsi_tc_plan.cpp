@@ -1,9 +1,13 @@
 // Host planning of the tcgen05 H_eff psi contraction: distinct operands and
-// their TF32 hi/lo planes, the kernel's item descriptors, and the 128 x 256
-// sigma tiles with their item chunks (Sec. II.B two-site effective
-// Hamiltonian; the kernel is in hpsi_tc.cu).
+// their TF32 hi/lo plane pairs in the pool, the kernel's item descriptors,
+// the 128 x 256 sigma tiles with their item chunks, and the task lists of the
+// persistent launch (Sec. II.B two-site effective Hamiltonian; the kernel is
+// in hpsi_tc.cu).
 #include <algorithm>
 #include <cstdint>
+#include <numeric>
+#include <queue>
+#include <stdexcept>
 #include <vector>
 
 #include "hpsi_tc.cuh"
@@ -12,16 +16,31 @@
 namespace dmrg {
 namespace {
 constexpr int TM = kTcTileM, TNMAX = kTcTileN;
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// tensor-pipe work of one item on a tile of width N, in units of one
+// stage-1 k-block (128 x 64 x 32 in three TF32 products), plus a fixed
+// per-chunk overhead
+double item_cost(int ka, int kb, int N) {
+  double c = 0.0;
+  for (int jc = 0; jc < kb; jc += 64) {
+    const int kbl = std::min(2, ceil_div(kb - jc, 32));
+    c += ceil_div(ka, 32) + kbl * (N / 64.0) + 0.5;
+  }
+  return c;
+}
 }  // namespace
 
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
-                     const std::function<void*(size_t)>& alloc, TcPlan& plan) {
+                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta) {
   plan = TcPlan();
-  auto r32 = [](int x) { return (x + 31) & ~31; };
+  if (ncta <= 0) ncta = 152;
   // Distinct operands (src, trans, rows, cols, ld) become split jobs, numbered
   // in first-occurrence order over the references (items in block order;
-  // roles A, P (for a non-identity A), B).  The references are hashed into
-  // kShards tables processed in parallel; one ordered scan numbers the jobs.
+  // roles A, P^T, B).  An identity factor is the operand (nullptr, 0, d, d, -1).
+  // The references are hashed into kShards tables processed in parallel; one
+  // ordered scan numbers the jobs.
   struct Key {
     const double* src = nullptr;
     int trans = 0, rows = 0, cols = 0, ld = 0;
@@ -45,53 +64,42 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
       iorder.push_back((uint32_t)i);
     }
   const size_t nref = 3 * iorder.size();
-  auto key_of = [&](size_t r, Key& k) -> bool {
+  auto key_of = [&](size_t r) -> Key {
     const HpsiItem& it = items[iorder[r / 3]];
     const HpsiBlock& bk = blocks[item_blk[iorder[r / 3]]];
     switch (r % 3) {
       case 0:
-        if (!it.A) return false;
-        k = Key{it.A, it.transA, bk.m, it.ka, it.lda};
-        return true;
+        return it.A ? Key{it.A, it.transA, bk.m, it.ka, it.lda} : Key{nullptr, 0, bk.m, bk.m, -1};
       case 1:
-        if (!it.A) return false;
-        k = Key{it.P, 1, it.kb, it.ka, it.ldp};
-        return true;
+        return Key{it.P, 1, it.kb, it.ka, it.ldp};
       default:
-        if (!it.B) return false;
-        k = Key{it.B, it.transB, bk.n, it.kb, it.ldb};
-        return true;
+        return it.B ? Key{it.B, it.transB, bk.n, it.kb, it.ldb} : Key{nullptr, 0, bk.n, bk.n, -1};
     }
   };
   constexpr size_t kShards = 32;
-  constexpr uint64_t kNone = ~0ull;
-  std::vector<uint64_t> rhash(nref);  // hash of reference r, kNone: no operand
+  std::vector<uint64_t> rhash(nref);
   const size_t rchunk = 4096;
   host_parallel_for((nref + rchunk - 1) / rchunk, [&](size_t c) {
     for (size_t r = c * rchunk; r < std::min(nref, (c + 1) * rchunk); ++r) {
-      Key k;
-      rhash[r] = key_of(r, k) ? (mix((uint64_t)(uintptr_t)k.src ^ ((uint64_t)(uint32_t)k.rows << 32) ^
-                                     ((uint64_t)(uint32_t)k.cols << 12) ^ ((uint64_t)(uint32_t)k.ld << 44) ^
-                                     (uint64_t)k.trans) &
-                                 (kNone >> 1))
-                              : kNone;
+      const Key k = key_of(r);
+      rhash[r] = mix((uint64_t)(uintptr_t)k.src ^ ((uint64_t)(uint32_t)k.rows << 32) ^
+                     ((uint64_t)(uint32_t)k.cols << 12) ^ ((uint64_t)(uint32_t)k.ld << 44) ^ (uint64_t)k.trans);
     }
   });
-  std::vector<int> lid(nref, -1);        // shard-local operand of reference r
-  std::vector<uint8_t> first(nref, 0);   // r is the first reference of its operand
+  std::vector<int> lid(nref, -1);       // shard-local operand of reference r
+  std::vector<uint8_t> first(nref, 0);  // r is the first reference of its operand
   std::vector<std::vector<Key>> skeys(kShards);
   host_parallel_for(kShards, [&](size_t sh) {
     size_t mine = 0;
-    for (size_t r = 0; r < nref; ++r) mine += rhash[r] != kNone && rhash[r] % kShards == sh;
+    for (size_t r = 0; r < nref; ++r) mine += rhash[r] % kShards == sh;
     size_t cap = 64;
     while (cap < 2 * mine + 64) cap <<= 1;
     const size_t mask = cap - 1;
     std::vector<int> slot(cap, -1);
     auto& keys = skeys[sh];
     for (size_t r = 0; r < nref; ++r) {
-      if (rhash[r] == kNone || rhash[r] % kShards != sh) continue;
-      Key k;
-      key_of(r, k);
+      if (rhash[r] % kShards != sh) continue;
+      const Key k = key_of(r);
       size_t h = (rhash[r] / kShards) & mask;
       while (slot[h] >= 0 && !(keys[slot[h]] == k)) h = (h + 1) & mask;
       if (slot[h] < 0) {
@@ -104,45 +112,27 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
   });
   std::vector<std::vector<int>> gid(kShards);
   for (size_t sh = 0; sh < kShards; ++sh) gid[sh].assign(skeys[sh].size(), -1);
-  size_t njobs = 0;
-  for (auto& k : skeys) njobs += k.size();
   std::vector<SplitJob> jobs;
-  std::vector<std::pair<size_t, size_t>> offs;
   std::vector<uint8_t> is_psi;
-  jobs.reserve(njobs);
-  offs.reserve(njobs);
-  is_psi.reserve(njobs);
-  size_t floats = 0;
+  size_t units = 0;
   for (size_t r = 0; r < nref; ++r) {
     if (!first[r]) continue;
     const size_t sh = rhash[r] % kShards;
     const Key& k = skeys[sh][lid[r]];
     gid[sh][lid[r]] = (int)jobs.size();
-    SplitJob j{k.src, k.rows, k.cols, k.ld, k.trans, nullptr, nullptr, r32(k.cols)};
-    const size_t plane = (size_t)k.rows * j.ldd;
-    offs.push_back({floats, floats + plane});
-    floats += 2 * plane;
-    floats = (floats + 3) & ~size_t(3);  // 16-byte alignment of every plane
-    jobs.push_back(j);
+    if (units > (size_t)INT32_MAX) throw std::runtime_error("tcgen05 plan: split pool beyond 2^31 units");
+    jobs.push_back(SplitJob{k.src, k.rows, k.cols, k.ld, k.trans, (int)units});
+    units += 2 * (size_t)ceil_div(k.rows, 8) * (size_t)ceil_div(k.cols, 32);
     is_psi.push_back(r % 3 == 1);
   }
-  float* pool = nullptr;
-  if (floats > 0) pool = (float*)alloc(floats * sizeof(float));
-  plan.pool_bytes = floats * sizeof(float);
-  for (size_t j = 0; j < jobs.size(); ++j) {
-    jobs[j].hi = pool + offs[j].first;
-    jobs[j].lo = pool + offs[j].second;
-    (is_psi[j] ? plan.psi_jobs : plan.op_jobs).push_back(jobs[j]);
-  }
+  if (units > (size_t)INT32_MAX) throw std::runtime_error("tcgen05 plan: split pool beyond 2^31 units");
+  plan.units = units;
+  plan.pool_bytes = units * kTcUnitFloats * sizeof(float);
+  if (units > 0) alloc(plan.pool_bytes);
+  for (size_t j = 0; j < jobs.size(); ++j) (is_psi[j] ? plan.psi_jobs : plan.op_jobs).push_back(jobs[j]);
   auto mat = [&](size_t r) {
-    TcMat m;
-    if (rhash[r] != kNone) {
-      const SplitJob& j = jobs[gid[rhash[r] % kShards][lid[r]]];
-      m.hi = j.hi;
-      m.lo = j.lo;
-      m.ld = j.ldd;
-    }
-    return m;
+    const SplitJob& j = jobs[gid[rhash[r] % kShards][lid[r]]];
+    return TcMat{j.unit, ceil_div(j.rows, 8)};
   };
   plan.items.resize(items.size());
   const size_t ichunk = 2048;
@@ -150,51 +140,96 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     for (size_t q = c * ichunk; q < std::min(iorder.size(), (c + 1) * ichunk); ++q) {
       const size_t i = iorder[q];
       const HpsiItem& it = items[i];
+      const HpsiBlock& bk = blocks[item_blk[i]];
       TcItem t;
       t.A = mat(3 * q);
       t.Pt = mat(3 * q + 1);
-      t.P = it.P;
-      t.ldp = it.ldp;
       t.B = mat(3 * q + 2);
-      t.ka = it.ka;
-      t.kb = it.kb;
+      t.ka = it.A ? it.ka : bk.m;
+      t.kb = it.B ? it.kb : bk.n;
       t.alpha = it.alpha;
       plan.items[i] = t;
     }
   });
   for (size_t i = 0; i < items.size(); ++i)
-    if (item_blk[i] < 0) {  // an item of no block: no operands
-      plan.items[i].P = items[i].P;
-      plan.items[i].ldp = items[i].ldp;
-      plan.items[i].ka = items[i].ka;
-      plan.items[i].kb = items[i].kb;
-      plan.items[i].alpha = items[i].alpha;
+    if (item_blk[i] < 0) {  // an item of no block: never referenced by a task
+      plan.items[i] = TcItem{TcMat{}, TcMat{}, TcMat{}, items[i].ka, items[i].kb, items[i].alpha};
     }
-  // tasks: 128 x 256 tiles, items chunked so that a launch has a few waves
-  long long tile_items = 0;
-  for (auto& b : blocks)
-    tile_items += (long long)b.item_count * ((b.m + TM - 1) / TM) * ((b.n + TNMAX - 1) / TNMAX);
-  const int max_items = (int)std::max<long long>(4, tile_items / (3 * 152) + 1);
+  // Tasks: 128 x 256 tiles, the items of a tile cut into contiguous chunks of
+  // about equal tensor work, so that the launch has a few tasks per CTA.
+  double total = 0.0;
+  std::vector<std::vector<double>> icost(blocks.size());
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const HpsiBlock& bk = blocks[b];
+    if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
+    icost[b].resize(bk.item_count);
+    for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
+      const int N = std::min(TNMAX, (std::min(TNMAX, bk.n - c0) + 15) & ~15);
+      for (int k = 0; k < bk.item_count; ++k) {
+        const TcItem& t = plan.items[bk.item_begin + k];
+        const double c = item_cost(t.ka, t.kb, N);
+        if (c0 == 0) icost[b][k] = c;
+        total += c * ceil_div(bk.m, TM);
+      }
+    }
+  }
+  const double target = std::max(1.0, total / (4.0 * ncta));
+  std::vector<double> tcost;
   long long part = 0;
   for (size_t b = 0; b < blocks.size(); ++b) {
     const HpsiBlock& bk = blocks[b];
     if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
-    int nch = (bk.item_count + max_items - 1) / max_items;
-    int per = (bk.item_count + nch - 1) / nch;
-    // every chunk owns a partial tile (float pairs); the reduction adds the
-    // chunks of a tile into sigma in float64
+    // chunk boundaries from the first column tile's costs (the same for all
+    // tiles of the block, so every tile of a block has the same chunks)
+    std::vector<int> cuts{0};
+    double acc = 0.0;
+    for (int k = 0; k < bk.item_count; ++k) {
+      acc += icost[b][k];
+      if (acc >= target && k + 1 < bk.item_count) {
+        cuts.push_back(k + 1);
+        acc = 0.0;
+      }
+    }
+    cuts.push_back(bk.item_count);
+    const int nch = (int)cuts.size() - 1;
     for (int r0 = 0; r0 < bk.m; r0 += TM)
       for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
+        const int N = std::min(TNMAX, (std::min(TNMAX, bk.n - c0) + 15) & ~15);
         plan.reds.push_back({(int)b, r0, c0, nch, part});
         for (int c = 0; c < nch; ++c) {
-          int i0 = bk.item_begin + c * per;
-          int cnt = std::min(per, bk.item_begin + bk.item_count - i0);
+          const int i0 = bk.item_begin + cuts[c], cnt = cuts[c + 1] - cuts[c];
           plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
+          double tc = 2.0;  // drain
+          for (int k = i0; k < i0 + cnt; ++k) tc += item_cost(plan.items[k].ka, plan.items[k].kb, N);
+          tcost.push_back(tc);
           part += (long long)TM * TNMAX;
         }
       }
   }
   plan.scratch = (size_t)part;
+  // Persistent launch: longest task first onto the least-loaded CTA; each
+  // CTA runs its tasks in decreasing cost.
+  const int nt = (int)plan.tasks.size();
+  const int G = std::max(1, std::min(ncta, nt));
+  std::vector<int> order(nt);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
+  using Load = std::pair<double, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int c = 0; c < G; ++c) pq.push({0.0, c});
+  std::vector<std::vector<int>> lists(G);
+  for (int t : order) {
+    Load l = pq.top();
+    pq.pop();
+    lists[l.second].push_back(t);
+    pq.push({l.first + tcost[t], l.second});
+  }
+  plan.cta_off.assign(G + 1, 0);
+  for (int c = 0; c < G; ++c) {
+    plan.cta_off[c + 1] = plan.cta_off[c] + (int)lists[c].size();
+    plan.cta_task.insert(plan.cta_task.end(), lists[c].begin(), lists[c].end());
+  }
+  if (nt == 0) plan.cta_off.assign(1, 0);
 }
 
 }  // namespace dmrg

@@ -3,12 +3,14 @@
 //    after an exception, and rethrows the first exception;
 //  - hpsi_tc_prepare (tcgen05 H_eff psi planning) against properties any
 //    correct plan has: each operand of each item refers to a split job with
-//    exactly that operand's (src, trans, rows, cols, ld); jobs are distinct
-//    and numbered in first-occurrence order over (items in block order;
-//    roles A, P (non-identity A), B); planes are disjoint, 16-byte aligned,
-//    rows x round32(cols) floats; the chunks of every 128 x 256 tile cover
-//    its items once, in order, each chunk with its own partial tile, and one
-//    reduction per tile names all of its chunks;
+//    exactly that operand's (src, trans, rows, cols, ld), identity factors to
+//    one identity job per dimension; jobs are distinct and numbered in
+//    first-occurrence order over (items in block order; roles A, P^T, B);
+//    plane pairs are disjoint runs of 2 ceil(rows/8) ceil(cols/32) units
+//    inside the pool; the chunks of every 128 x 256 tile cover its items
+//    once, in order, each chunk with its own partial tile, one reduction per
+//    tile names all of its chunks, and every task is in exactly one CTA list
+//    of the persistent launch;
 //  - jac_plan_batches (batched Jacobi eigensolver launches): every matrix in
 //    exactly one launch, in order; at most `cap` CTAs per launch; group sizes
 //    between the minimum (two above the shared-memory size) and the cap of
@@ -106,9 +108,12 @@ static void check_plan(unsigned seed) {
   char* const pool = reinterpret_cast<char*>(uintptr_t(0x40) << 32);
   size_t pool_bytes = 0;
   TcPlan plan;
-  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { pool_bytes = bytes; return (void*)pool; }, plan);
+  const int ncta = 5 + (int)(seed % 7) * 23;
+  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { pool_bytes = bytes; return (void*)pool; }, plan, ncta);
   CHECK(plan.pool_bytes == pool_bytes);
-  // expected jobs: first occurrences in reference order
+  CHECK(plan.pool_bytes == plan.units * kTcUnitFloats * sizeof(float));
+  // expected jobs: first occurrences in reference order; an identity factor
+  // is the operand (nullptr, 0, d, d, -1)
   std::map<Key, int> first;
   std::vector<Key> order;
   std::vector<int> is_psi;
@@ -118,12 +123,18 @@ static void check_plan(unsigned seed) {
       is_psi.push_back(psi);
     }
   };
+  auto key_a = [&](const HpsiBlock& bk, const HpsiItem& it) {
+    return it.A ? Key{it.A, it.transA, bk.m, it.ka, it.lda} : Key{nullptr, 0, bk.m, bk.m, -1};
+  };
+  auto key_b = [&](const HpsiBlock& bk, const HpsiItem& it) {
+    return it.B ? Key{it.B, it.transB, bk.n, it.kb, it.ldb} : Key{nullptr, 0, bk.n, bk.n, -1};
+  };
   for (auto& bk : blocks)
     for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
       const HpsiItem& it = items[i];
-      if (it.A) note(Key{it.A, it.transA, bk.m, it.ka, it.lda}, false);
-      if (it.A) note(Key{it.P, 1, it.kb, it.ka, it.ldp}, true);
-      if (it.B) note(Key{it.B, it.transB, bk.n, it.kb, it.ldb}, false);
+      note(key_a(bk, it), false);
+      note(Key{it.P, 1, it.kb, it.ka, it.ldp}, true);
+      note(key_b(bk, it), false);
     }
   std::vector<SplitJob> jobs_op, jobs_psi;
   for (size_t j = 0; j < order.size(); ++j) {
@@ -133,22 +144,18 @@ static void check_plan(unsigned seed) {
   }
   CHECK(plan.op_jobs.size() == jobs_op.size());
   CHECK(plan.psi_jobs.size() == jobs_psi.size());
-  std::map<const float*, Key> by_plane;
+  // plane pairs: 2 ceil(rows/8) ceil(cols/32) units each, disjoint, inside the pool
+  std::map<int, Key> by_unit;
   std::vector<std::pair<size_t, size_t>> spans;
   auto check_jobs = [&](const std::vector<SplitJob>& got, const std::vector<SplitJob>& want) {
     for (size_t j = 0; j < std::min(got.size(), want.size()); ++j) {
       const SplitJob& g = got[j];
       CHECK(g.src == want[j].src && g.trans == want[j].trans && g.rows == want[j].rows &&
             g.cols == want[j].cols && g.ld == want[j].ld);
-      CHECK(g.ldd == ((g.cols + 31) & ~31));
-      const size_t bytes = (size_t)g.rows * g.ldd * sizeof(float);
-      for (const float* p : {g.hi, g.lo}) {
-        const size_t off = (size_t)((const char*)p - pool);
-        CHECK(((uintptr_t)p & 15) == 0);
-        CHECK(off + bytes <= pool_bytes);
-        spans.push_back({off, off + bytes});
-      }
-      by_plane[g.hi] = Key{g.src, g.trans, g.rows, g.cols, g.ld};
+      const size_t units = 2 * (size_t)((g.rows + 7) / 8) * ((g.cols + 31) / 32);
+      CHECK(g.unit >= 0 && (size_t)g.unit + units <= plan.units);
+      spans.push_back({(size_t)g.unit, (size_t)g.unit + units});
+      by_unit[g.unit] = Key{g.src, g.trans, g.rows, g.cols, g.ld};
     }
   };
   check_jobs(plan.op_jobs, jobs_op);
@@ -161,20 +168,25 @@ static void check_plan(unsigned seed) {
     for (int i = bk.item_begin; i < bk.item_begin + bk.item_count; ++i) {
       const HpsiItem& it = items[i];
       const TcItem& t = plan.items[i];
-      CHECK(t.P == it.P && t.ldp == it.ldp && t.ka == it.ka && t.kb == it.kb && t.alpha == it.alpha);
+      CHECK(t.ka == (it.A ? it.ka : bk.m) && t.kb == (it.B ? it.kb : bk.n) && t.alpha == it.alpha);
       auto refers = [&](const TcMat& m, const Key& k) {
-        auto f = by_plane.find(m.hi);
-        return f != by_plane.end() && f->second == k && m.ld == ((std::get<3>(k) + 31) & ~31);
+        auto f = by_unit.find(m.unit);
+        return f != by_unit.end() && f->second == k && m.groups == (std::get<2>(k) + 7) / 8;
       };
-      if (it.A) {
-        CHECK(refers(t.A, Key{it.A, it.transA, bk.m, it.ka, it.lda}));
-        CHECK(refers(t.Pt, Key{it.P, 1, it.kb, it.ka, it.ldp}));
-      } else {
-        CHECK(t.A.hi == nullptr && t.Pt.hi == nullptr);
-      }
-      if (it.B) CHECK(refers(t.B, Key{it.B, it.transB, bk.n, it.kb, it.ldb}));
-      else CHECK(t.B.hi == nullptr);
+      CHECK(refers(t.A, key_a(bk, it)));
+      CHECK(refers(t.Pt, Key{it.P, 1, it.kb, it.ka, it.ldp}));
+      CHECK(refers(t.B, key_b(bk, it)));
     }
+  // persistent launch: every task in exactly one CTA list, no empty CTA
+  const int G = (int)plan.cta_off.size() - 1;
+  CHECK(G == std::min<int>(ncta, (int)plan.tasks.size()) || (plan.tasks.empty() && G == 0));
+  std::vector<int> seen(plan.tasks.size(), 0);
+  for (int c = 0; c < G; ++c) {
+    CHECK(plan.cta_off[c + 1] > plan.cta_off[c]);
+    for (int q = plan.cta_off[c]; q < plan.cta_off[c + 1]; ++q) seen[plan.cta_task[q]]++;
+  }
+  CHECK(plan.cta_task.size() == plan.tasks.size());
+  for (int x : seen) CHECK(x == 1);
   // tiles, chunks, partial tiles, reductions
   std::map<std::tuple<int, int, int>, std::vector<const HpsiTask*>> chunks;
   std::set<long long> parts;
