@@ -1,21 +1,26 @@
-"""Benchmark of the spin-adapted DMRG sweep (H_eff psi TFLOP/s and sweep time).
+"""Benchmark of the spin-adapted DMRG hot path (H_eff psi TFLOP/s at D, sweep time).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cas40|casN|pentacene|naphthalene] [--D 256]
-                    [--precision split-tc|split|split-all|fp64]
+                    [--mode bond|sweep] [--workload cas40|casN|pentacene|naphthalene]
+                    [--D 2048] [--precision split-tc|split|split-all|fp64]
 
-A step is one full two-site DMRG sweep (L->R then R->L: blocking, Davidson
-with H_eff psi, decimation, renormalisation) over the workload.  The warm-up
-steps ramp the bond dimension (D/4, D/2, D, ...) so the timed sweeps run at
-the target D on a converged-size MPS.  The library's work stays in HBM; the
-timed sweeps are bracketed by a barrier and a device synchronisation and
-their device time comes from CUDA events the library records on its stream.
+--mode bond (default): a step is one H_eff psi product at the middle bond of
+the workload at bond dimension D, inside the Davidson solve of that bond.
+The state is brought there by a ramp of sweeps (D 256 then 1024, Davidson
+capped), one L->R half-sweep at D and an R->L part down to the bond next to
+the middle one; the W warm-up products and the K timed products then run at
+the middle bond on the same blocks (dmrg_bond_solve).  The FP64 arm times
+float64 products at the same bond on the same vector, and the precision of
+the split result is reported as its float64 residual.
 
-Metric: algorithmic H_eff psi FLOPs of the timed sweeps divided by their
-device time (TFLOP/s, whole-sweep throughput), with the sweep time per step.
-With N > 1 GPUs every rank runs an independent replica of the workload
-(replicas only: the sweep has no data-parallel split on one node here) and
-``value`` is the sum over ranks.
+--mode sweep: a step is one full two-site sweep (L->R then R->L: blocking,
+Davidson with H_eff psi, decimation, renormalisation) at D, after W warm-up
+sweeps that ramp D.
+
+The library's work stays in HBM; the timed region is bracketed by a barrier
+and a device synchronisation, and its device time comes from CUDA events
+the library records on its stream.  With N > 1 GPUs every rank runs an
+independent replica (replicas only) and ``value`` is the sum over ranks.
 """
 from __future__ import annotations
 
@@ -184,11 +189,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     res = []
+    # each step a bounded sample, so that the whole run stays within minutes
+    per_step = max(1.0, min(10.0, 90.0 / max(1, args.steps)))
     for _ in range(args.warmup):
-        oracle_sample(3.0)
+        oracle_sample(min(3.0, per_step))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        res.append(oracle_sample(10.0))
+        res.append(oracle_sample(per_step))
     wall = time.perf_counter() - t0
     v = float(np.mean([r["value"] for r in res]))
     cb = dict(res[-1])
@@ -252,7 +259,11 @@ def run_hpsi_only(args):
     import paper_2503_20700_gb300 as pkg
     pkg.load()
     prec = {"split": 1, "split-tc": 4, "split-all": 1, "fp64": 0}[args.precision]
-    A, P, B, clen, blocks, items, flops = hpsi_problem(7, 16, 100, 250, 80)
+    if args.hpsi_shape == "large":
+        # sector dimensions of the middle bonds at D = 1024 .. 2048 (300 .. 600)
+        A, P, B, clen, blocks, items, flops = hpsi_problem(7, 8, 300, 600, 30)
+    else:
+        A, P, B, clen, blocks, items, flops = hpsi_problem(7, 16, 100, 250, 80)
     C = np.zeros(clen)
     W, K = max(3, args.warmup), max(1, args.steps)
     for _ in range(W):
@@ -266,7 +277,8 @@ def run_hpsi_only(args):
     pk, src = peaks()
     peak = pk["bf16_tflops"] * (1.1 / 2.25) / 3.0 if prec else 1.25
     nbytes = 8.0 * (A.size + P.size + B.size + 2 * clen)
-    print(json.dumps({"mode": "hpsi-only", "precision": args.precision, "value": achieved, "unit": "TFLOP/s",
+    print(json.dumps({"mode": "hpsi-only", "shape": args.hpsi_shape, "precision": args.precision,
+                      "value": achieved, "unit": "TFLOP/s",
                       "ms_per_launch": t, "steps": K, "warmup": W, "algorithmic_flops": flops,
                       "operand_bytes": nbytes, "blocks": len(blocks), "items": len(items),
                       "roofline": {"bound": "tensor" if prec else "alu", "achieved": achieved, "peak": peak,
@@ -276,39 +288,165 @@ def run_hpsi_only(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cas40")
-    ap.add_argument("--D", type=int, default=256)
-    ap.add_argument("--precision", default="split-tc", choices=["split", "split-tc", "split-all", "fp64"],
-                    help="split-tc: 3xTF32 H_eff psi on tcgen05, renormalisation in FP64; "
-                         "split: the same products on mma.sync; split-all: mma.sync 3xTF32 also in "
-                         "renormalisation; fp64: all FP64")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--tol", type=float, default=1e-7)
-    ap.add_argument("--verbose", type=int, default=0, help="library diagnostics on stderr (2: H_eff psi shapes)")
-    ap.add_argument("--hpsi-only", action="store_true",
-                    help="time the H_eff psi contraction alone on synthetic sector blocks (kernel roofline)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.hpsi_only:
-        return run_hpsi_only(args)
+def initial_state(wl):
+    """Aufbau occupation for the Cholesky workloads (their h_pp grow along the
+    chain), the even-spread default state for the half-filled PPP models."""
+    import workloads as W
+    if wl["chol"] is not None:
+        return W.aufbau_state(wl["h"], wl["n_elec"], wl["two_s"])
+    return None, None
 
-    import paper_2503_20700_gb300 as pkg
-    pkg.load()
-    rank, world, dist = dist_init(args.gpus)
-    device = int(os.environ.get("LOCAL_RANK", "0"))
+
+def tc_peak(prec, pk, src, pkg):
+    if prec != pkg.FP64:
+        # 3xTF32: three TF32 tensor products per algorithmic product; TF32 peak =
+        # measured dense bf16 peak x the nominal TF32/BF16 ratio (1.1/2.25)
+        return (pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0,
+                f"3xTF32 effective peak = sustained bf16 ({src}) x 1.1/2.25 / 3")
+    return 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+
+
+def parse_ramp(text):
+    out = []
+    for part in text.split(","):
+        if part.strip():
+            d, it = part.split(":")
+            out.append((int(d), int(it)))
+    return out
+
+
+def run_bond(args, pkg, prec, rank, world, dist, device):
     wl = workload(args.workload)
-    prec = {"split": pkg.SPLIT_HPSI, "split-tc": pkg.SPLIT_HPSI_TC, "split-all": pkg.SPLIT_TF32,
-            "fp64": pkg.FP64}[args.precision]
+    n = wl["h"].shape[0]
+    mid = n // 2 - 1 if args.bond < 0 else args.bond
+    W, K = max(3, args.warmup), max(1, args.steps)
+    ramp_list = parse_ramp(args.ramp)
+    occ, path = initial_state(wl)
+    barrier(dist)
+    t_job0 = time.perf_counter()
+    g = pkg.DMRG(wl["h"], eri=wl["eri"], chol=wl["chol"], n_elec=wl["n_elec"], two_s=wl["two_s"],
+                 D=ramp_list[0][0] if ramp_list else args.D, e_core=wl["e_core"], precision=prec,
+                 tol=args.tol, device=device, verbose=args.verbose, occ=occ, two_s_right=path)
+    flops_job = 0.0
+    t_ramp0 = time.perf_counter()
+    ramp_energies = []
+    for d, it in ramp_list:
+        g.set_bond_dim(d)
+        g.set_davidson(it, args.tol)
+        ramp_energies.append(g.sweep(1)[0])
+        flops_job += g.stats()["hpsi_flops"]
+    t_ramp = time.perf_counter() - t_ramp0
+    # at the target D: one L->R half-sweep, then R->L down to the bond next to
+    # the middle one, with the Davidson cap of the approach
+    g.set_bond_dim(args.D)
+    g.set_davidson(args.approach_iters, args.tol)
+    t_app0 = time.perf_counter()
+    g.sweep_part(0, n - 3)
+    flops_job += g.stats()["hpsi_flops"]
+    app_ms = g.sweep_device_ms()
+    g.sweep_part(1, mid + 1)
+    flops_job += g.stats()["hpsi_flops"]
+    app_ms += g.sweep_device_ms()
+    t_app = time.perf_counter() - t_app0
+    left, right = g.block_dims()
+    # warm-up products at the middle bond
+    g.bond_solve(mid, 1, prec, max_iter=max(1, W - 1), tol=args.tol, min_calls=W)
+    # ---- timed region: K products inside the Davidson solve of the middle bond
+    barrier(dist)
+    g.profile(True)
+    l0 = g.launch_count()
+    with Clocks(device) as clk:
+        t0 = time.perf_counter()
+        res = g.bond_solve(mid, 1, prec, max_iter=max(1, K - 1), tol=args.tol, min_calls=K)
+        wall = time.perf_counter() - t0
+    launches = g.launch_count() - l0
+    k_ms, k_launch = res["contraction_ms"], res["contraction_launches"]
+    k_flops = res["calls"] * res["flops_per_call"]
+    s_ms, s_launch = res["split_ms"], res["calls"]
+    flops_job += res["calls"] * res["flops_per_call"]
+    kernel_ms = {name: g.kernel_stats(i)[0]
+                 for i, name in enumerate(["gemm", "hpsi", "place", "eigh_subspace", "eigh_batched",
+                                           "split"])}
+    dev_s = res["ms_total"] / 1000.0
+    t_max = allmax(dist, dev_s)
+    flops_all = allsum(dist, res["calls"] * res["flops_per_call"])
+    value = flops_all / t_max / 1e12
+    # ---- FP64 arm: float64 products at the same bond from the same vector
+    fp64 = None
+    if args.fp64_calls > 0 and prec != pkg.FP64:
+        r64 = g.bond_solve(mid, 1, pkg.FP64, max_iter=max(1, args.fp64_calls - 1), tol=args.tol,
+                           min_calls=args.fp64_calls)
+        v64 = r64["calls"] * r64["flops_per_call"] / (r64["ms_total"] / 1000.0) / 1e12
+        fp64 = {"value": v64, "unit": "TFLOP/s", "calls": r64["calls"],
+                "ms_per_call": r64["ms_total"] / max(1, r64["calls"]), "speedup_split_over_fp64": value / v64}
+        if args.fp64_converge:
+            rc = g.bond_solve(mid, 1, pkg.FP64, max_iter=200, tol=args.tol, min_calls=0)
+            fp64["converged"] = {"energy": rc["energy_rq64"], "residual64": rc["residual64"],
+                                 "iterations": rc["iterations"],
+                                 "delta_e_split_minus_fp64": res["energy_rq64"] - rc["energy_rq64"]}
+    mem_now, mem_peak = g.memory()
+    _ = g.energy()
+    t_job = allmax(dist, time.perf_counter() - t_job0)
+    barrier(dist)
+
+    pk, src = peaks()
+    peak_tf, peak_note = tc_peak(prec, pk, src, pkg)
+    achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
+    roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved, "peak": peak_tf,
+            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
+            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
+            "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,
+            "what": "algorithmic FLOPs of the contraction launches (kernel and chunk reduction) / their "
+                    "CUDA-event time; the psi splits are timed apart (split_ms)",
+            "split_ms": s_ms, "split_launches": s_launch}
+    e2e = None
+    if not args.no_e2e:
+        h2d = wl["h"].nbytes + (wl["eri"].nbytes if wl["eri"] is not None else wl["chol"].nbytes)
+        e2e = {"value": allsum(dist, flops_job) / t_job / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8, "seconds": t_job,
+               "what": ("whole job through the public API: dmrg_init from host integrals (h2d once), "
+                        f"ramp sweeps {ramp_list}, the approach to bond {mid} at D={args.D}, W={W} warm-up "
+                        f"and K={K} timed products, the FP64 arm, energy read back (d2h); all H_eff psi "
+                        "FLOPs / wall time")}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(15.0)
+    if rank == 0:
+        ms_sorted = sorted(res["call_ms"])
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "tf32x3" if prec != pkg.FP64 else "f64", "data": "synthetic",
+                "config": {"workload": f"{wl['desc']}: H_eff psi at the middle bond {mid} at D={args.D}",
+                           "D": args.D, "bond": mid, "ramp": ramp_list, "approach_davidson_iters": args.approach_iters,
+                           "precision": args.precision, "davidson_tol": args.tol,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": ("operators larger than L2" if mem_peak > 4 * L2_BYTES
+                                  else "working set below L2 size")},
+                "step": "one H_eff psi product inside the Davidson solve of the bond",
+                "flops_per_step": res["flops_per_call"], "psi_dim": res["dim"],
+                "ms_median": ms_sorted[len(ms_sorted) // 2] if ms_sorted else None,
+                "davidson_iters": res["iterations"],
+                "precision_check": {"energy_split": res["energy"], "energy_rq64": res["energy_rq64"],
+                                    "delta_e_eval": res["energy"] - res["energy_rq64"],
+                                    "residual64": res["residual64"], "ritz_gap": res["gap"],
+                                    "delta_e_bound": (res["residual64"] ** 2 / res["gap"]) if res["gap"] > 0 else None},
+                "fp64": fp64, "ramp_energies": ramp_energies, "ramp_seconds": t_ramp,
+                "approach_seconds": t_app, "approach_device_ms": app_ms,
+                "block_dims_left": left.tolist(), "block_dims_right": right.tolist(),
+                "wall_seconds": wall, "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
+                "kernel_ms": kernel_ms, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    g.close()
+    return 0
+
+
+def run_sweep(args, pkg, prec, rank, world, dist, device):
+    wl = workload(args.workload)
     W, K = max(3, args.warmup), max(1, args.steps)
     ds = ramp(args.D, W)
+    occ, path = initial_state(wl)
     # the whole job runs through the public API from host integrals: its wall
     # time (dmrg_init with the host->device copy of the integrals, every sweep,
     # the final energy read back) is the end-to-end figure
@@ -316,7 +454,7 @@ def main():
     t_job0 = time.perf_counter()
     g = pkg.DMRG(wl["h"], eri=wl["eri"], chol=wl["chol"], n_elec=wl["n_elec"], two_s=wl["two_s"],
                  D=ds[0], e_core=wl["e_core"], precision=prec, tol=args.tol, device=device,
-                 verbose=args.verbose)
+                 verbose=args.verbose, occ=occ, two_s_right=path)
     flops_job = 0.0
     for d in ds:
         g.set_bond_dim(d)
@@ -341,8 +479,10 @@ def main():
         wall = time.perf_counter() - t0
     launches = g.launch_count() - l0
     k_ms, k_flops, k_launch = g.kernel_stats(1)
+    s_ms, _, s_launch = g.kernel_stats(5)
     kernel_ms = {name: g.kernel_stats(i)[0]
-                 for i, name in enumerate(["gemm", "hpsi", "place", "eigh_subspace", "eigh_batched"])}
+                 for i, name in enumerate(["gemm", "hpsi", "place", "eigh_subspace", "eigh_batched",
+                                           "split"])}
     mem_now, mem_peak = g.memory()
     flops_job += flops
     _ = g.energy()
@@ -351,26 +491,14 @@ def main():
     t_max = allmax(dist, dev_ms / 1000.0)
     flops_all = allsum(dist, flops)
     value = flops_all / t_max / 1e12
-
-    # ---- roofline of the dominant kernel (the H_eff psi GEMM)
     pk, src = peaks()
-    if prec != pkg.FP64:
-        # 3xTF32: three TF32 tensor products per algorithmic product; TF32 peak =
-        # measured dense bf16 peak x the nominal TF32/BF16 ratio (1.1/2.25)
-        peak_tf = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
-        peak_note = f"3xTF32 effective peak = sustained bf16 ({src}) x 1.1/2.25 / 3"
-    else:
-        peak_tf = 1.25
-        peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
-    avg_ms = k_ms / max(1, k_launch)
-    achieved = (k_flops / max(1, k_launch)) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
+    peak_tf, peak_note = tc_peak(prec, pk, src, pkg)
+    achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved,
-            "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf if peak_tf else None,
-            "traffic": None, "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
-            "launches": k_launch, "avg_launch_ms": avg_ms, "peak_source": peak_note}
-
-    # ---- end to end: the whole job above (init from host integrals, the
-    # warm-up ramp and the timed sweeps, energy read back), all sweeps' flops
+            "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
+            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
+            "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,
+            "split_ms": s_ms, "split_launches": s_launch}
     e2e = None
     if not args.no_e2e:
         h2d = wl["h"].nbytes + (wl["eri"].nbytes if wl["eri"] is not None else wl["chol"].nbytes)
@@ -378,22 +506,20 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8, "seconds": t_job,
                "what": ("whole job through the public API: dmrg_init from host integrals (h2d once), "
                         f"{len(ds)} warm-up sweeps at D={ds} and {K} timed sweep(s), energy read back (d2h)")}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(15.0)
-
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
                 "warmup": W, "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "tf32x3" if prec != pkg.FP64 else "f64", "data": "synthetic",
-                "config": {"workload": wl["desc"], "D": args.D, "warmup_D": ds,
+                "config": {"workload": f"{wl['desc']}: full sweeps at D={args.D}", "D": args.D, "warmup_D": ds,
                            "precision": args.precision, "davidson_tol": args.tol,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": ("operators larger than L2" if mem_peak > 4 * L2_BYTES
                                   else "working set below L2 size")},
-                "sweep_energy": energies[-1], "sweep_energies": energies,
+                "step": "one full sweep", "sweep_energy": energies[-1], "sweep_energies": energies,
                 "sweep_seconds": t_max / K, "wall_seconds": wall,
                 "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
                 "phase_seconds": phases, "kernel_ms": kernel_ms, "davidson_iters": st["davidson_iters"],
@@ -401,9 +527,56 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line))
     g.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="bond", choices=["bond", "sweep"])
+    ap.add_argument("--workload", default="cas40")
+    ap.add_argument("--D", type=int, default=2048)
+    ap.add_argument("--bond", type=int, default=-1, help="bond of --mode bond (default: the middle one)")
+    ap.add_argument("--ramp", default="64:4,256:4,1024:4",
+                    help="--mode bond: sweeps before the target D, as D:davidson_iters,...")
+    ap.add_argument("--approach-iters", type=int, default=2,
+                    help="--mode bond: Davidson cap of the half-sweeps at the target D")
+    ap.add_argument("--fp64-calls", type=int, default=2, help="--mode bond: float64 products timed (0: none)")
+    ap.add_argument("--fp64-converge", action="store_true",
+                    help="--mode bond: also converge the float64 Davidson at the bond (slow at large D)")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per contraction launch from an ncu capture of the same kernel")
+    ap.add_argument("--precision", default="split-tc", choices=["split", "split-tc", "split-all", "fp64"],
+                    help="split-tc: 3xTF32 H_eff psi on tcgen05, renormalisation in FP64; "
+                         "split: the same products on mma.sync; split-all: mma.sync 3xTF32 also in "
+                         "renormalisation; fp64: all FP64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--verbose", type=int, default=0, help="library diagnostics on stderr (2: H_eff psi shapes)")
+    ap.add_argument("--hpsi-only", action="store_true",
+                    help="time the H_eff psi contraction alone on synthetic sector blocks (kernel roofline)")
+    ap.add_argument("--hpsi-shape", default="small", choices=["small", "large"],
+                    help="--hpsi-only: sector dimensions 100-250 (small) or 300-600 (large)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.hpsi_only:
+        return run_hpsi_only(args)
+
+    import paper_2503_20700_gb300 as pkg
+    pkg.load()
+    rank, world, dist = dist_init(args.gpus)
+    device = int(os.environ.get("LOCAL_RANK", "0"))
+    prec = {"split": pkg.SPLIT_HPSI, "split-tc": pkg.SPLIT_HPSI_TC, "split-all": pkg.SPLIT_TF32,
+            "fp64": pkg.FP64}[args.precision]
+    rc = (run_bond if args.mode == "bond" else run_sweep)(args, pkg, prec, rank, world, dist, device)
     if dist is not None:
         dist.destroy_process_group()
-    return 0
+    return rc
 
 
 if __name__ == "__main__":

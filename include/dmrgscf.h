@@ -68,9 +68,35 @@ typedef struct {
   int max_space;          /* Davidson subspace size before restart           */
   int verbose;            /* 0 quiet, 1 per bond, 2 per Davidson step        */
   int device;             /* CUDA device ordinal                             */
+  int strict_convergence; /* 1: dmrg_sweep / dmrg_sweep_part return
+                             DMRG_ENOCONV (after completing the sweep, state
+                             intact) when a bond's Davidson stopped at
+                             max_davidson_iter above davidson_tol             */
+  int debug_bounds;       /* 1: every tcgen05 task list is checked on the host
+                             against its pool, scratch and item ranges before
+                             its first launch (DMRG_EINTERNAL on a violation) */
+  uint64_t seed;          /* seed of the Davidson start vector where no
+                             predicted wavefunction exists (0: fixed default) */
+  size_t hbm_budget_bytes;/* 0: no cap.  Otherwise the device memory the
+                             context may hold: an allocation beyond it fails
+                             with DMRG_ENOMEM unless stored blocks can be moved
+                             to pinned host memory (see dmrg_sweep)            */
+  double wait_timeout_s;  /* bound of every device-side wait (default 2 s; 0:
+                             a wait not complete at its first probe gives up)
+                             -- a wait that runs out returns DMRG_ETIMEOUT     */
+  double trunc_target;    /* 0: keep D multiplets at every bond.  > 0: dynamic
+                             bond dimension (Sec. II.D): keep the fewest
+                             multiplets whose discarded weight is at most
+                             trunc_target, between D_min and D                */
+  int D_min;              /* lower bound of the dynamic bond dimension        */
+  int rq64_every_bond;    /* 1: with a split precision, every bond energy (not
+                             only the sweep energy) is the float64 Rayleigh
+                             quotient of its eigenvector (one float64 H_eff psi
+                             per bond)                                        */
 } dmrg_opts;
 
-/* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24. */
+/* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24,
+ * no budget, wait bound 2 s, fixed D (trunc_target 0, D_min 1). */
 void dmrg_default_opts(dmrg_opts* o);
 
 /*
@@ -136,6 +162,10 @@ typedef struct {
   double flops_per_call;  /* algorithmic FLOPs of one product (2mnk, once)    */
   double ms_total;        /* CUDA-event milliseconds of all products          */
   int64_t dim;            /* length of the two-site wavefunction              */
+  double contraction_ms;  /* with dmrg_profile on: the contraction launches of
+                             the products (kernel and chunk reduction)        */
+  double split_ms;        /* with dmrg_profile on: their psi splits (tcgen05)  */
+  int64_t contraction_launches;
 } dmrg_bond_result;
 
 /*
@@ -159,6 +189,17 @@ dmrg_status dmrg_bond_solve(dmrg_ctx* ctx, int bond, int direction, int precisio
  * by subsequent sweeps (Sec. II.D).  A bond that reaches the cap keeps its
  * last Ritz vector. */
 dmrg_status dmrg_set_davidson(dmrg_ctx* ctx, int max_iter, double tol);
+
+/* Bound (seconds) of the device-side waits of the context's kernels for
+ * subsequent calls (the wait_timeout_s option): 0 makes a wait that is not
+ * complete at its first probe give up, so the call returns DMRG_ETIMEOUT and
+ * the context stays usable.  DMRG_EINVAL outside [0, 3600]. */
+dmrg_status dmrg_set_wait_timeout(dmrg_ctx* ctx, double seconds);
+
+/* The same bound, process-wide, for the kernel-level entry points
+ * (dmrg_hpsi_contract, dmrg_eigh_batched and the CAS-SCF routines) called
+ * after it; default 2 s. */
+dmrg_status dmrg_set_kernel_wait_timeout(double seconds);
 
 /* Change the bond dimension used by subsequent sweeps. */
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* ctx, int D);

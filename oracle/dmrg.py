@@ -31,6 +31,9 @@ Readings fixed here (the paper is silent on them):
   The sweep energy is the Davidson eigenvalue of the last bond.
 * Selection: multiplets ranked by lambda (descending); lambda < 1e-12 dropped;
   exact ties (relative 1e-9) at the cut broken by (N asc, 2j asc, index asc).
+  With a truncation-error target (dynamic block-state selection) the number
+  kept is the fewest whose discarded weight is at most the target, clamped
+  to [D_min, D].
 """
 from __future__ import annotations
 
@@ -130,7 +133,8 @@ class SweepRecord:
 class OracleDMRG:
     """Two-site SU(2) DMRG on explicit full-space block bases."""
 
-    def __init__(self, h, eri, n_elec, two_s, D, e_core=0.0, tol=1e-10, occ=None, two_s_right=None):
+    def __init__(self, h, eri, n_elec, two_s, D, e_core=0.0, tol=1e-10, occ=None, two_s_right=None,
+                 trunc_target=0.0, D_min=1):
         from workloads import initial_product_state
         self.h = np.asarray(h, float)
         self.eri = np.asarray(eri, float)
@@ -138,6 +142,8 @@ class OracleDMRG:
         if self.n < 2:
             raise ValueError("need at least two sites")
         self.n_elec, self.two_s, self.D = n_elec, two_s, D
+        self.trunc_target, self.D_min = float(trunc_target), int(D_min)
+        self.kept = []  # multiplets kept at each decimation, in sweep order
         self.e_core, self.tol = float(e_core), tol
         # one Hamiltonian per Sz component of the target multiplet
         self.ham = {tm: Hamiltonian(self.h, self.eri, n_elec, tm, e_core)
@@ -298,7 +304,10 @@ class OracleDMRG:
                     hw[cols] = W @ vec[:, k]
                     cands.append((lam, int(ne), int(tm), rank_in, hw))
         total = sum(c[0] for c in cands)
+        if self.trunc_target > 0.0:
+            D = dbss_dimension([c[0] for c in cands], D, self.D_min, self.trunc_target)
         kept = select_multiplets([(c[0], c[1], c[2], c[3]) for c in cands], D)
+        self.kept.append(len(kept))
         disc = total - sum(cands[k][0] for k in kept)
         vecs, nn, mm, jj, mid = [], [], [], [], []
         for mid_k, k in enumerate(kept):
@@ -372,6 +381,19 @@ class OracleDMRG:
         """Multiplet counts of the current left (0..n-2) and right bases."""
         return ([b.n_multiplets() if b is not None else None for b in self.left],
                 [b.n_multiplets() if b is not None else None for b in self.right])
+
+
+def dbss_dimension(lams, D_max, D_min, target):
+    """Dynamic block-state selection (Sec. II.D, fixed truncation error): the
+    fewest multiplets, taken in decreasing weight, whose discarded weight
+    sum(lams) - sum(kept) is at most `target`, clamped to [D_min, D_max]."""
+    lams = sorted(lams, reverse=True)
+    total = sum(lams)
+    kept, k = 0.0, 0
+    while k < len(lams) and total - kept > target:
+        kept += lams[k]
+        k += 1
+    return max(D_min, min(D_max, k))
 
 
 def select_multiplets(cands, D):

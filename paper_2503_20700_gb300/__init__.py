@@ -33,7 +33,11 @@ class Opts(ctypes.Structure):
     _fields_ = [("D", ctypes.c_int), ("max_davidson_iter", ctypes.c_int),
                 ("davidson_tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_space", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("strict_convergence", ctypes.c_int),
+                ("debug_bounds", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("wait_timeout_s", ctypes.c_double),
+                ("trunc_target", ctypes.c_double), ("D_min", ctypes.c_int),
+                ("rq64_every_bond", ctypes.c_int)]
 
 
 class BondResult(ctypes.Structure):
@@ -41,7 +45,8 @@ class BondResult(ctypes.Structure):
                 ("residual64", ctypes.c_double), ("gap", ctypes.c_double),
                 ("iterations", ctypes.c_int), ("calls", ctypes.c_int),
                 ("flops_per_call", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("dim", ctypes.c_int64)]
+                ("dim", ctypes.c_int64), ("contraction_ms", ctypes.c_double),
+                ("split_ms", ctypes.c_double), ("contraction_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -74,6 +79,10 @@ def load(path=None):
     lib.dmrg_sweep_part.restype = I
     lib.dmrg_bond_solve.argtypes = [P, I, I, I, I, D, I, ctypes.POINTER(BondResult), dp, I]
     lib.dmrg_bond_solve.restype = I
+    lib.dmrg_set_wait_timeout.argtypes = [P, D]
+    lib.dmrg_set_wait_timeout.restype = I
+    lib.dmrg_set_kernel_wait_timeout.argtypes = [D]
+    lib.dmrg_set_kernel_wait_timeout.restype = I
     lib.dmrg_set_davidson.argtypes = [P, I, D]
     lib.dmrg_set_davidson.restype = I
     lib.dmrg_set_bond_dim.argtypes = [P, I]
@@ -116,6 +125,13 @@ def _dp(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def set_kernel_wait_timeout(seconds):
+    """Bound of the device waits of the kernel-level entry points (process-wide)."""
+    lib = load()
+    st = lib.dmrg_set_kernel_wait_timeout(float(seconds))
+    _check(lib, None, st)
+
+
 def _ip(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 
@@ -131,7 +147,9 @@ class DMRG:
 
     def __init__(self, h, eri=None, chol=None, n_elec=None, two_s=0, D=64, e_core=0.0,
                  tol=1e-10, precision=FP64, max_iter=200, max_space=24, verbose=0,
-                 device=0, occ=None, two_s_right=None):
+                 device=0, occ=None, two_s_right=None, strict_convergence=False,
+                 debug_bounds=False, seed=0, hbm_budget_bytes=0, wait_timeout_s=None,
+                 trunc_target=0.0, D_min=1, rq64_every_bond=False):
         lib = load()
         self._lib = lib
         h = np.ascontiguousarray(h, dtype=np.float64)
@@ -145,6 +163,12 @@ class DMRG:
         lib.dmrg_default_opts(ctypes.byref(o))
         o.D, o.davidson_tol, o.precision = D, tol, precision
         o.max_davidson_iter, o.max_space, o.verbose, o.device = max_iter, max_space, verbose, device
+        o.strict_convergence, o.debug_bounds, o.seed = int(bool(strict_convergence)), int(bool(debug_bounds)), seed
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if wait_timeout_s is not None:
+            o.wait_timeout_s = float(wait_timeout_s)
+        o.trunc_target, o.D_min = float(trunc_target), int(D_min)
+        o.rq64_every_bond = int(bool(rq64_every_bond))
         occ_a = None if occ is None else np.ascontiguousarray(occ, dtype=np.int32)
         path_a = None if two_s_right is None else np.ascontiguousarray(two_s_right, dtype=np.int32)
         ctx = ctypes.c_void_p()
@@ -183,6 +207,9 @@ class DMRG:
         out = {k: getattr(r, k) for k, _ in BondResult._fields_}
         out["call_ms"] = ms[:min(cap, r.calls)].tolist()
         return out
+
+    def set_wait_timeout(self, seconds):
+        _check(self._lib, self._ctx, self._lib.dmrg_set_wait_timeout(self._ctx, float(seconds)))
 
     def set_davidson(self, max_iter, tol):
         _check(self._lib, self._ctx, self._lib.dmrg_set_davidson(self._ctx, int(max_iter), float(tol)))

@@ -74,6 +74,14 @@ class Backend {
   virtual size_t capacity() const { return ~size_t(0); }
   // streaming multiprocessors of the device (the persistent launches' grid)
   virtual int sm_count() const { return 152; }
+  // device memory the backend may hold (0: no cap); an allocation beyond it
+  // throws "out of device memory"
+  virtual void set_budget(size_t bytes) { budget_ = bytes; }
+  size_t budget() const { return budget_; }
+  // bound of every device-side wait of the kernels (nanoseconds; 0: a wait
+  // that is not complete at its first probe gives up)
+  void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
+  unsigned long long wait_ns() const { return wait_ns_; }
   virtual size_t device_free() const { return ~size_t(0); }
   virtual void memset0(void* p, size_t bytes) = 0;
   virtual void copy_d2d(void* dst, const void* src, size_t bytes) = 0;
@@ -127,6 +135,12 @@ class Backend {
   virtual void mark_begin() = 0;
   virtual double mark_end() = 0;
   virtual void set_profile(bool on) = 0;
+
+ protected:
+  size_t budget_ = 0;
+  unsigned long long wait_ns_ = 2000000000ull;
+
+ public:
   // total device time (ms), algorithmic flops and launches of one tag
   virtual void kernel_stats(int tag, double* ms, double* flops, long* launches) = 0;
 };

@@ -8,7 +8,8 @@
 //   jacobi_smem_kernel  parallel cyclic Jacobi eigensolver (FP64) of one matrix in shared memory, one CTA
 //   jacobi_coop_kernel  a batch of matrices on one CTA per SM, each on a group of CTAs sized to its work
 // All kernels are bounded loops over their inputs; the one wait on other CTAs,
-// the group barrier of jacobi_coop_kernel, gives up after 5 s and sets the error flag.
+// the group barrier of jacobi_coop_kernel, gives up after the backend's wait
+// bound (2 s by default) and sets the error flag.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -463,8 +464,9 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(const EighTask* __rest
 // rotation parameters from the same entries (identical values, so no
 // exchange is needed) and updates its own contiguous share of the triangle
 // blocks and of the eigenvector elements; one group barrier per round
-// publishes the updates.  The barrier's wait is bounded by 5 s of wall clock
-// and sets the error flag on timeout.
+// publishes the updates.  The barrier's wait is bounded by the backend's
+// wait bound (wall clock) and sets the error flag on timeout; with a bound of
+// 0 a barrier not complete at its first probe gives up.
 struct CoopEigh {
   EighTask t;
   int g, cta0;
@@ -484,7 +486,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // returns false when the wait ran out
-__device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
+__device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -495,9 +497,10 @@ __device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
       atomicExch(&bar[1], target);
     } else {
       const unsigned long long t0 = jac_ns();
+      const int spin = wait_ns > 0 ? 256 : 1;
       for (int probe = 0; (int)(ld_acquire(&bar[1]) - target) < 0; ++probe) {
-        if (probe >= 256) {
-          if (jac_ns() - t0 > 5000000000ull) {
+        if (probe >= spin) {
+          if (jac_ns() - t0 >= wait_ns) {
             *ok_s = 0;
             break;
           }
@@ -513,7 +516,7 @@ __device__ bool group_sync(unsigned* bar, int g, unsigned& gen, int* ok_s) {
 }
 
 __device__ void jacobi_group(const CoopEigh& ct, int me, double* sm, double* red, int* nrot, int* ok_s,
-                             int* err) {
+                             int* err, unsigned long long wait_ns) {
   const int g = ct.g;
   const int n = ct.t.n;
   double* a = const_cast<double*>(ct.t.A);
@@ -539,7 +542,7 @@ __device__ void jacobi_group(const CoopEigh& ct, int me, double* sm, double* red
   const long long nb = (long long)h * (h + 1) / 2, nv = (long long)h * n;
   const int b0 = (int)(nb * me / g), b1 = (int)(nb * (me + 1) / g);
   const int v0 = (int)(nv * me / g), v1 = (int)(nv * (me + 1) / g);
-  if (!group_sync(ct.bar, g, gen, ok_s)) goto fail;
+  if (!group_sync(ct.bar, g, gen, ok_s, wait_ns)) goto fail;
   for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
     if (threadIdx.x == 0) *nrot = 0;
     __syncthreads();
@@ -552,7 +555,7 @@ __device__ void jacobi_group(const CoopEigh& ct, int me, double* sm, double* red
         jac_block<true>(a, n, n, i, j, R);
       }
       for (int e = v0 + (int)threadIdx.x; e < v1; e += blockDim.x) jac_vrot<true>(v, n, e / n, e % n, R);
-      if (!group_sync(ct.bar, g, gen, ok_s)) goto fail;
+      if (!group_sync(ct.bar, g, gen, ok_s, wait_ns)) goto fail;
     }
     if (*nrot == 0) break;
     __syncthreads();
@@ -590,7 +593,8 @@ fail:
 
 // The batched launch: CTA b belongs to the last task whose cta0 <= b.
 __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(const CoopEigh* __restrict__ tasks, int ntasks,
-                                                                  int* __restrict__ err) {
+                                                                  int* __restrict__ err,
+                                                                  unsigned long long wait_ns) {
   int lo = 0, hi = ntasks - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(const CoopEigh
   __shared__ double red[kJacThreads];
   __shared__ int nrot, ok_s;
   if (ct.g == 1) jacobi_one(ct.t, sm, red, &nrot);
-  else jacobi_group(ct, (int)blockIdx.x - ct.cta0, sm, red, &nrot, &ok_s, err);
+  else jacobi_group(ct, (int)blockIdx.x - ct.cta0, sm, red, &nrot, &ok_s, err, wait_ns);
 }
 
 // ------------------------------------------------------------------ backend
@@ -711,6 +715,9 @@ class CudaBackend : public Backend {
   void* alloc(size_t b) override {
     void* p = nullptr;
     if (b == 0) b = 8;
+    if (budget_ && used + b > budget_)
+      throw std::runtime_error("out of device memory (budget of " + std::to_string(budget_) + " bytes: " +
+                               std::to_string(used) + " held, " + std::to_string(b) + " requested)");
     cudaError_t e = cudaMallocAsync(&p, b, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -913,7 +920,7 @@ class CudaBackend : public Backend {
       rec = &recs.back();
       CK(cudaEventRecord(rec->a, st));
     }
-    hpsi_tc_launch(L, flag(), st);
+    hpsi_tc_launch(L, flag(), wait_ns_, st);
     launches += (L.ncta > 0) + (L.nreds > 0);
     if (rec) CK(cudaEventRecord(rec->b, st));
     if (recs.size() > 4096) drain();
@@ -1027,7 +1034,8 @@ class CudaBackend : public Backend {
       const CoopEigh* dt = (const CoopEigh*)(d + off[0]);
       int nt = (int)ct.size();
       int* fl = flag();
-      void* args[] = {(void*)&dt, (void*)&nt, (void*)&fl};
+      unsigned long long wns = wait_ns_;
+      void* args[] = {(void*)&dt, (void*)&nt, (void*)&fl, (void*)&wns};
       Rec* rec = nullptr;
       if (profiling) {
         recs.push_back(Rec{ev(), ev(), 0.0, 4});

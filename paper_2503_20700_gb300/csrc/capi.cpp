@@ -1,5 +1,6 @@
 // extern "C" entry points (include/dmrgscf.h).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <exception>
 #include <memory>
@@ -23,9 +24,12 @@ struct dmrg_ctx {
   int sweeps_done = 0;
   dmrg::SweepStats last;
   double sweep_seconds = 0.0;
+  bool strict = false;
 };
 
 namespace {
+// wait bound of the kernel-level entry points (dmrg_set_kernel_wait_timeout)
+std::atomic<unsigned long long> g_kernel_wait_ns{2000000000ull};
 thread_local std::string tl_err;
 thread_local double tl_contract_ms = 0.0;
 
@@ -120,6 +124,14 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->max_space = 24;
   o->verbose = 0;
   o->device = 0;
+  o->strict_convergence = 0;
+  o->debug_bounds = 0;
+  o->seed = 0;
+  o->hbm_budget_bytes = 0;
+  o->wait_timeout_s = 2.0;
+  o->trunc_target = 0.0;
+  o->D_min = 1;
+  o->rq64_every_bond = 0;
 }
 
 dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const double* chol,
@@ -139,6 +151,10 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
   if (opts) o = *opts;
   if (o.D < 1 || o.max_space < 4 || o.davidson_tol <= 0 || o.max_davidson_iter < 1)
     return fail(nullptr, DMRG_EINVAL, "bad options");
+  if (!(o.wait_timeout_s >= 0.0) || o.wait_timeout_s > 3600.0)
+    return fail(nullptr, DMRG_EINVAL, "wait_timeout_s must be in [0, 3600]");
+  if (!(o.trunc_target >= 0.0) || o.trunc_target >= 1.0 || o.D_min < 1 || o.D_min > o.D)
+    return fail(nullptr, DMRG_EINVAL, "trunc_target must be in [0, 1) and 1 <= D_min <= D");
   if (!sweep_precision_ok(o.precision)) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
   auto ctx = std::make_unique<dmrg_ctx>();
   ctx->n = n;
@@ -156,21 +172,31 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     } else if (!default_state(n, n_elec, two_s, oc, path)) {
       return fail(nullptr, DMRG_EINVAL, "two_s too large for this filling");
     }
-    std::vector<double> e4;
-    const double* g = eri;
-    if (!g) {
-      size_t nn = (size_t)n * n;
-      e4.assign(nn * nn, 0.0);
-      for (int k = 0; k < rank; ++k) {
-        const double* L = chol + (size_t)k * nn;
-        for (size_t a = 0; a < nn; ++a)
-          for (size_t b = 0; b < nn; ++b) e4[a * nn + b] += L[a] * L[b];
-      }
-      g = e4.data();
-    }
     std::string err;
     ctx->be.reset(dmrg::make_cuda_backend(o.device, &err));
     if (!ctx->be) return fail(nullptr, DMRG_ECUDA, err.empty() ? "cuda: no device" : err);
+    ctx->be->set_budget(o.hbm_budget_bytes);
+    ctx->be->set_wait_ns((unsigned long long)(o.wait_timeout_s * 1e9));
+    std::vector<double> e4;
+    const double* g = eri;
+    if (!g) {
+      // (pq|rs) = sum_k L^k_pq L^k_rs: one (n^2 x rank)(rank x n^2) float64
+      // GEMM on the device; the result enters the host task coefficients
+      const size_t nn = (size_t)n * n;
+      e4.assign(nn * nn, 0.0);
+      double* dL = (double*)ctx->be->alloc((size_t)rank * nn * sizeof(double));
+      double* dE = (double*)ctx->be->alloc(nn * nn * sizeof(double));
+      ctx->be->copy_h2d(dL, chol, (size_t)rank * nn * sizeof(double));
+      ctx->be->memset0(dE, nn * nn * sizeof(double));
+      std::vector<dmrg::GemmGroup> gg{{dE, (int)nn, (int)nn, (int)nn, 0, 1}};
+      std::vector<dmrg::GemmSeg> gs{{dL, dL, rank, (int)nn, (int)nn, 1, 0, 1.0}};
+      ctx->be->gemm(gg, gs, dmrg::Precision::FP64);
+      ctx->be->copy_d2h(e4.data(), dE, nn * nn * sizeof(double));
+      ctx->be->sync();
+      ctx->be->free(dL);
+      ctx->be->free(dE);
+      g = e4.data();
+    }
     dmrg::Options eo;
     eo.D = o.D;
     eo.max_davidson_iter = o.max_davidson_iter;
@@ -178,6 +204,12 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     map_precision(o.precision, &eo.prec, &eo.prec_renorm);
     eo.max_space = o.max_space;
     eo.verbose = o.verbose;
+    eo.seed = o.seed;
+    eo.debug_bounds = o.debug_bounds != 0;
+    eo.trunc_target = o.trunc_target;
+    eo.D_min = o.D_min;
+    eo.rq64_every_bond = o.rq64_every_bond != 0;
+    ctx->strict = o.strict_convergence != 0;
     ctx->eng = std::make_unique<dmrg::Engine>(ctx->be.get(), n, h, g, e_core, n_elec, two_s, eo,
                                               oc.data(), path.data());
   } catch (const std::exception& e) {
@@ -191,16 +223,21 @@ dmrg_status dmrg_sweep(dmrg_ctx* c, int n_sweeps, double* energy, double* max_tr
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
   if (n_sweeps < 0) return fail(c, DMRG_EINVAL, "n_sweeps < 0");
   try {
+    int noconv = 0;
     for (int s = 0; s < n_sweeps; ++s) {
       c->last = c->eng->sweep();
       c->sweep_seconds = c->eng->sweep_seconds;
       ++c->sweeps_done;
+      noconv += c->last.noconv_bonds;
     }
+    if (energy) *energy = c->last.energy;
+    if (max_trunc) *max_trunc = c->last.max_trunc;
+    if (c->strict && noconv > 0)
+      return fail(c, DMRG_ENOCONV, "davidson: " + std::to_string(noconv) +
+                                       " bond solve(s) stopped at max_davidson_iter above davidson_tol");
   } catch (const std::exception& e) {
     return translate(c, e);
   }
-  if (energy) *energy = c->last.energy;
-  if (max_trunc) *max_trunc = c->last.max_trunc;
   return DMRG_OK;
 }
 
@@ -210,11 +247,14 @@ dmrg_status dmrg_sweep_part(dmrg_ctx* c, int direction, int last_bond, double* e
   try {
     c->last = c->eng->sweep_part(direction == 0, last_bond);
     c->sweep_seconds = c->eng->sweep_seconds;
+    if (energy) *energy = c->last.energy;
+    if (max_trunc) *max_trunc = c->last.max_trunc;
+    if (c->strict && c->last.noconv_bonds > 0)
+      return fail(c, DMRG_ENOCONV, "davidson: " + std::to_string(c->last.noconv_bonds) +
+                                       " bond solve(s) stopped at max_davidson_iter above davidson_tol");
   } catch (const std::exception& e) {
     return translate(c, e);
   }
-  if (energy) *energy = c->last.energy;
-  if (max_trunc) *max_trunc = c->last.max_trunc;
   return DMRG_OK;
 }
 
@@ -238,6 +278,9 @@ dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision,
     out->calls = r.calls;
     out->flops_per_call = r.flops_per_call;
     out->dim = (int64_t)r.dim;
+    out->contraction_ms = r.contraction_ms;
+    out->split_ms = r.split_ms;
+    out->contraction_launches = r.contraction_launches;
     double tot = 0.0;
     for (double x : r.call_ms) tot += x;
     out->ms_total = tot;
@@ -252,6 +295,19 @@ dmrg_status dmrg_set_davidson(dmrg_ctx* c, int max_iter, double tol) {
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
   if (max_iter < 1 || !(tol > 0)) return fail(c, DMRG_EINVAL, "max_iter < 1 or tol <= 0");
   c->eng->set_davidson(max_iter, tol);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_wait_timeout(dmrg_ctx* c, double seconds) {
+  if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
+  if (!(seconds >= 0.0) || seconds > 3600.0) return fail(c, DMRG_EINVAL, "seconds must be in [0, 3600]");
+  c->be->set_wait_ns((unsigned long long)(seconds * 1e9));
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_kernel_wait_timeout(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 3600.0) return fail(nullptr, DMRG_EINVAL, "seconds must be in [0, 3600]");
+  g_kernel_wait_ns.store((unsigned long long)(seconds * 1e9));
   return DMRG_OK;
 }
 
@@ -425,6 +481,7 @@ dmrg_status dmrg_grouped_gemm(const double* A, int64_t a_len, const double* B, i
   }
   std::string err;
   std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (be) be->set_wait_ns(g_kernel_wait_ns.load());
   if (!be) return fail(nullptr, DMRG_ECUDA, err);
   try {
     double* dA = (double*)be->alloc(std::max<int64_t>(a_len, 1) * sizeof(double));
@@ -518,6 +575,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     return fail(nullptr, DMRG_EINVAL, m);
   std::string err;
   std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (be) be->set_wait_ns(g_kernel_wait_ns.load());
   if (!be) return fail(nullptr, DMRG_ECUDA, err);
   try {
     auto up = [&](const double* h, int64_t n) {
@@ -684,6 +742,7 @@ dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, doubl
   }
   std::string err;
   std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (be) be->set_wait_ns(g_kernel_wait_ns.load());
   if (!be) return fail(nullptr, DMRG_ECUDA, err);
   try {
     double* dA = (double*)be->alloc(std::max<size_t>(tot, 1) * sizeof(double));
@@ -719,6 +778,7 @@ template <class F>
 dmrg_status with_casscf(int device, F&& f) {
   std::string err;
   std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
+  if (be) be->set_wait_ns(g_kernel_wait_ns.load());
   if (!be) return fail(nullptr, DMRG_ECUDA, err);
   try {
     dmrg::Casscf c(be.get());

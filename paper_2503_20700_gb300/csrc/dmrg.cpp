@@ -5,6 +5,7 @@
 #include "host_pool.hpp"
 
 #include <algorithm>
+#include <functional>
 #include <array>
 #include <chrono>
 #include <thread>
@@ -1417,6 +1418,10 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
     plan.tc_pool = nullptr;
     hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp,
                     be_->sm_count());
+    if (opt_.debug_bounds) {
+      const std::string bad = tc_plan_check(tp, blocks);
+      if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
+    }
     tasks = tp.tasks;
     reds = tp.reds;
     scr = tp.scratch;
@@ -1552,7 +1557,8 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     for (double x : h) nrm += x * x;
     if (!(nrm > 1e-20)) {
       for (size_t i = 0; i < len; ++i)
-        h[i] = ((splitmix64(i + 12345) >> 11) * (1.0 / 9007199254740992.0)) - 0.5;
+        h[i] = ((splitmix64(i + 12345 + opt_.seed * 0x9E3779B97F4A7C15ull) >> 11) * (1.0 / 9007199254740992.0)) -
+               0.5;
       nrm = 0.0;
       for (double x : h) nrm += x * x;
     }
@@ -1588,6 +1594,7 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
   int it = 0;
   double best_res = 1e300;
   int best_it = 0;
+  double last_res = 1e300, last_tol = 0.0;
   for (it = 1; it <= opt_.max_davidson_iter; ++it) {
     // projected matrix: row/col m-1
     be_->dots(V, m, len, len, HV + (size_t)(m - 1) * len, dc);
@@ -1617,6 +1624,8 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     // iterations) in any mode.
     double tol_eff = opt_.davidson_tol;
     if (opt_.prec != Precision::FP64) tol_eff = std::max(tol_eff, 2e-7 * std::max(1.0, std::abs(e)));
+    last_res = rn;
+    last_tol = tol_eff;
     if (rn < tol_eff) break;
     if (rn < 0.9 * best_res) {
       best_res = rn;
@@ -1665,6 +1674,7 @@ double Engine::davidson(HPsiPlan& plan, double* psi, int* iters) {
     ++m;
   }
   if (iters) *iters = it;
+  if (!(last_res < last_tol)) stats_.noconv_bonds += 1;
   be_->sync();
   be_->free(V);
   be_->free(HV);
@@ -1761,7 +1771,21 @@ std::unique_ptr<SavedU> Engine::decimate(Block& enl, const HPsiPlan& plan, const
       total += lam;
       cands.push_back({lam, B.sec[s].n, B.sec[s].j, r, (int)s});
     }
-  auto keep = select(cands, opt_.D);
+  int Dk = opt_.D;
+  if (opt_.trunc_target > 0.0) {
+    // dynamic bond dimension: the fewest multiplets whose discarded weight is
+    // at most trunc_target, between D_min and D
+    std::vector<double> lams;
+    lams.reserve(cands.size());
+    for (auto& c : cands) lams.push_back(c.lam);
+    std::sort(lams.begin(), lams.end(), std::greater<double>());
+    double kept_w = 0.0;
+    size_t k = 0;
+    while (k < lams.size() && total - kept_w > opt_.trunc_target) kept_w += lams[k++];
+    Dk = std::max(opt_.D_min, std::min(opt_.D, (int)k));
+  }
+  auto keep = select(cands, Dk);
+  stats_.kept.push_back((int)keep.size());
   auto U = std::make_unique<SavedU>();
   U->be = be_;
   U->enl = B;
@@ -2119,7 +2143,7 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   double e = davidson(plan, psi, &its) + e_core_;
   be_->check_device_flag();
   stats_.davidson_iters += its;
-  if (opt_.prec != Precision::FP64 && !l2r && i == 1) {
+  if (opt_.prec != Precision::FP64 && ((!l2r && i == 1) || opt_.rq64_every_bond)) {
     // The sweep energy (last bond) of a split-precision run: the Rayleigh
     // quotient of the converged eigenvector with one float64 H_eff psi.  It is
     // second order in the eigenvector's error, while the split product's own
@@ -2264,6 +2288,12 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
   call_ms_ = &ms;
   int its = 0;
   double e = 0.0;
+  // kernel-class times of the products alone (the float64 evaluation below
+  // is not counted)
+  double c0 = 0.0, s0 = 0.0;
+  long l0 = 0, ls = 0;
+  be_->kernel_stats(1, &c0, nullptr, &l0);
+  be_->kernel_stats(5, &s0, nullptr, &ls);
   try {
     e = davidson(plan, psi, &its);
     // pad with products on the result vector up to min_calls
@@ -2280,6 +2310,15 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
     throw;
   }
   call_ms_ = nullptr;
+  {
+    double c1 = 0.0, s1 = 0.0;
+    long l1 = 0;
+    be_->kernel_stats(1, &c1, nullptr, &l1);
+    be_->kernel_stats(5, &s1, nullptr, &ls);
+    out.contraction_ms = c1 - c0;
+    out.split_ms = s1 - s0;
+    out.contraction_launches = l1 - l0;
+  }
   out.gap = last_gap_;
   out.flops_per_call = plan.flops;
   opt_ = keep;

@@ -18,6 +18,7 @@
 //   A^k_pq, B^k_pq   normal pair operators [a+a+]^k, [a+a~]^k, p<=q in block
 //   P^k_pq, QJ_pq, QK^k_pq   complementary pair operators, p<=q outside
 #pragma once
+#include <cstdint>
 #include <map>
 #include <memory>
 #include <string>
@@ -144,6 +145,11 @@ struct Options {
   Precision prec_renorm = Precision::FP64;  // renormalisation / complementary GEMMs
   int max_space = 24;
   int verbose = 0;
+  uint64_t seed = 0;          // Davidson start vector where no prediction exists
+  bool debug_bounds = false;  // host check of every tcgen05 plan before launch
+  double trunc_target = 0.0;  // > 0: dynamic bond dimension (discarded weight bound)
+  int D_min = 1;              // lower bound of the dynamic bond dimension
+  bool rq64_every_bond = false;  // split runs: float64 Rayleigh quotient at every bond
 };
 
 struct SweepStats {
@@ -153,6 +159,8 @@ struct SweepStats {
   double hpsi_flops = 0.0;
   double hpsi_seconds = 0.0;
   int hpsi_calls = 0;
+  int noconv_bonds = 0;  // Davidson solves that stopped above the tolerance
+  std::vector<int> kept;  // multiplets kept at each decimation, in sweep order
   // wall time per phase of the sweep (seconds, host clock around device-synchronised steps)
   double t_enlarge = 0.0, t_plan = 0.0, t_davidson = 0.0, t_decimate = 0.0, t_renorm = 0.0,
          t_guess = 0.0;
@@ -191,6 +199,9 @@ class Engine {
     int iterations = 0, calls = 0;
     double flops_per_call = 0.0;
     std::vector<double> call_ms;  // CUDA-event time of every product
+    double contraction_ms = 0.0;  // of which the contraction launches (kernel and chunk reduction)
+    double split_ms = 0.0;        // and the psi splits of the tcgen05 path
+    long contraction_launches = 0;
     size_t dim = 0;
   };
   BondSolve solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls);

@@ -18,8 +18,9 @@
 // list is  S1(0), S1(1), S2(0), S1(2), S2(1), ...: the tensor pipe runs
 // stage 1 of the next chunk while the converters turn the last X' into X.
 // S is drained every kDrainItems items of a task and at its end.  Every wait
-// gives up after 2 s of wall clock: the CTA then sets the error flag, waits
-// (bounded) for its copies and MMAs in flight, frees TMEM and returns.
+// gives up after the launch's wait bound (2 s of wall clock by default): the
+// CTA then sets the error flag, waits (bounded by 2 s) for its copies and
+// MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -113,23 +114,28 @@ __device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// bounded wait on the phase with the given parity; false after kWaitNs, or
-// at once when another role has aborted (abort != 0)
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (int i = 0; i < 256; ++i)
+// bounded wait on the phase with the given parity; false after wait_ns of
+// wall clock (0: after the first probe), or at once when another role has
+// aborted (abort != 0)
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                         unsigned long long wait_ns) {
+  const int spin = wait_ns > 0 ? 256 : 1;
+  for (int i = 0; i < spin; ++i)
     if (test_wait(bar, parity)) return true;
+  if (wait_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (test_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > wait_ns) return false;
     __nanosleep(32);
   }
 }
 // the same, with one outcome for the whole warp (the converter warps issue
 // .sync.aligned TMEM loads right after their waits)
-__device__ __forceinline__ bool wait_bar_warp(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  const bool ok = wait_bar(bar, parity, abort);
+__device__ __forceinline__ bool wait_bar_warp(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                              unsigned long long wait_ns) {
+  const bool ok = wait_bar(bar, parity, abort, wait_ns);
   return __all_sync(0xffffffffu, ok);
 }
 // byte offset of element (r, k) (k multiple of 4) in the 64-wide X planes
@@ -202,7 +208,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     hpsi_tc_kernel(const __grid_constant__ CUtensorMap map32, const __grid_constant__ CUtensorMap map16,
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
-                   const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err) {
+                   const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
+                   unsigned long long wait_ns) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[B_COUNT];
   __shared__ uint32_t tmem_base;
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       auto acquire = [&](int& s) -> bool {
         s = q % NSTAGE;
         const uint32_t par = (uint32_t)(((q / NSTAGE) & 1) ^ 1);
-        if (!wait_bar(&bar[B_EMPTY + s], par, abort)) return false;
+        if (!wait_bar(&bar[B_EMPTY + s], par, abort, wait_ns)) return false;
         return true;
       };
       auto s1 = [&](const Walk& w) -> bool {
@@ -312,13 +319,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t xh = sbase + OFF_XH, xl = sbase + OFF_XL;
       auto take = [&](int& s) -> bool {
         s = q % NSTAGE;
-        if (!wait_bar(&bar[B_FULL + s], (uint32_t)((q / NSTAGE) & 1), abort)) return false;
+        if (!wait_bar(&bar[B_FULL + s], (uint32_t)((q / NSTAGE) & 1), abort, wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
         return true;
       };
       auto s1 = [&](const Walk& w, int chunk) -> bool {
         const int b = chunk & 1;
-        if (chunk >= 2 && !wait_bar(&bar[B_XPE + b], (uint32_t)(((chunk >> 1) - 1) & 1), abort)) return false;
+        if (chunk >= 2 && !wait_bar(&bar[B_XPE + b], (uint32_t)(((chunk >> 1) - 1) & 1), abort, wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t tX = tmem_base + TCOL_X + 64 * b;
         const uint32_t id = idesc_tf32(TM, JC);
@@ -343,9 +350,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         return true;
       };
       auto s2 = [&](const Walk& w, int chunk) -> bool {
-        if (!wait_bar(&bar[B_XF], (uint32_t)(chunk & 1), abort)) return false;
+        if (!wait_bar(&bar[B_XF], (uint32_t)(chunk & 1), abort, wait_ns)) return false;
         if (need_se) {
-          if (!wait_bar(&bar[B_SE], (uint32_t)((nd - 1) & 1), abort)) return false;
+          if (!wait_bar(&bar[B_SE], (uint32_t)((nd - 1) & 1), abort, wait_ns)) return false;
           need_se = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     auto convert = [&](const Walk& w, int chunk) -> bool {
       const int b = chunk & 1;
-      if (!wait_bar_warp(&bar[B_XPF + b], (uint32_t)((chunk >> 1) & 1), abort)) return false;
+      if (!wait_bar_warp(&bar[B_XPF + b], (uint32_t)((chunk >> 1) & 1), abort, wait_ns)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t tX = tmem_base + TCOL_X + 64 * b + lane_base;
       uint32_t q[64];
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("tcgen05.fence::before_thread_sync;");
       arrive(&bar[B_XPE + b]);
       // X of the previous chunk must have been read by its stage-2 MMAs
-      if (chunk >= 1 && !wait_bar_warp(&bar[B_XE], (uint32_t)((chunk - 1) & 1), abort)) return false;
+      if (chunk >= 1 && !wait_bar_warp(&bar[B_XE], (uint32_t)((chunk - 1) & 1), abort, wait_ns)) return false;
       const float al = (float)w.it.alpha;
 #pragma unroll
       for (int j = 0; j < JC; j += 4) {
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // stores.  N columns of every row are written; the reduction reads the
     // valid ones only.
     auto drain = [&](long long part, int N, bool first) -> bool {
-      if (!wait_bar_warp(&bar[B_SF], (uint32_t)(nd & 1), abort)) return false;
+      if (!wait_bar_warp(&bar[B_SF], (uint32_t)(nd & 1), abort, wait_ns)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;");
       float2* d = part_base + part + (size_t)r * TNMAX;
       for (int c0 = 0; c0 < N; c0 += 32) {
@@ -630,7 +637,7 @@ void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st) {
   if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: split launch: ") + cudaGetErrorString(e));
 }
 
-void hpsi_tc_launch(const TcLaunch& L, int* err, cudaStream_t st) {
+void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st) {
   {
     cudaError_t e = ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES);
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc attribute: ") + cudaGetErrorString(e));
@@ -642,7 +649,7 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, cudaStream_t st) {
     make_map(&m32, L.pool, L.units, 32);
     make_map(&m16, L.pool, L.units, 16);
     hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m16, L.blocks, L.items, L.tasks, L.cta_off,
-                                                          L.cta_task, L.scratch, err);
+                                                          L.cta_task, L.scratch, err, wait_ns);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }

@@ -35,6 +35,7 @@
 
 #include <cstdint>
 #include <functional>
+#include <string>
 #include <vector>
 
 #include "hpsi_fused.cuh"
@@ -106,7 +107,15 @@ struct TcLaunch {
 void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st);
 
 // The persistent contraction and the reduction of item chunks.  err: a
-// device int set to 1 when a bounded wait ran out (the CTA then stops).
-void hpsi_tc_launch(const TcLaunch& L, int* err, cudaStream_t st);
+// device int set to 1 when a bounded wait ran out (the CTA then stops);
+// wait_ns bounds every wait (0: a wait not complete at its first probe
+// gives up).
+void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st);
+
+// Host-side check of a plan against its own ranges (debug_bounds): every
+// TMA box of every item inside the pool's units or its zero-filled tail,
+// every task's items and partial tile inside their lists, every CTA list a
+// permutation of the tasks.  Returns an empty string or the first violation.
+std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& blocks);
 
 }  // namespace dmrg

@@ -8,6 +8,7 @@
 #include <numeric>
 #include <queue>
 #include <stdexcept>
+#include <string>
 #include <vector>
 
 #include "hpsi_tc.cuh"
@@ -230,6 +231,52 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     plan.cta_task.insert(plan.cta_task.end(), lists[c].begin(), lists[c].end());
   }
   if (nt == 0) plan.cta_off.assign(1, 0);
+}
+
+std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& blocks) {
+  auto fits = [&](const TcMat& m, int rows, int cols) {
+    if (m.unit < 0 || m.groups != ceil_div(rows, 8)) return false;
+    return (size_t)m.unit + 2 * (size_t)m.groups * (size_t)ceil_div(cols, 32) <= plan.units;
+  };
+  const long long tile = (long long)TM * TNMAX;
+  for (size_t t = 0; t < plan.tasks.size(); ++t) {
+    const HpsiTask& tk = plan.tasks[t];
+    const std::string at = "task " + std::to_string(t) + ": ";
+    if (tk.block < 0 || tk.block >= (int)blocks.size()) return at + "block out of range";
+    const HpsiBlock& bk = blocks[tk.block];
+    if (tk.r0 < 0 || tk.r0 >= bk.m || tk.r0 % TM || tk.c0 < 0 || tk.c0 >= bk.n || tk.c0 % TNMAX)
+      return at + "tile origin out of range";
+    if (tk.it_count < 1 || tk.it_begin < bk.item_begin || tk.it_begin + tk.it_count > bk.item_begin + bk.item_count ||
+        tk.it_begin + tk.it_count > (int)plan.items.size())
+      return at + "items out of range";
+    if (tk.part < 0 || (size_t)(tk.part + tile) > plan.scratch) return at + "partial tile out of range";
+    for (int i = tk.it_begin; i < tk.it_begin + tk.it_count; ++i) {
+      const TcItem& it = plan.items[i];
+      if (it.ka < 1 || it.kb < 1) return at + "empty item " + std::to_string(i);
+      if (!fits(it.A, bk.m, it.ka) || !fits(it.Pt, it.kb, it.ka) || !fits(it.B, bk.n, it.kb))
+        return at + "operand planes of item " + std::to_string(i) + " outside the pool";
+    }
+  }
+  for (const HpsiReduce& rd : plan.reds) {
+    if (rd.block < 0 || rd.block >= (int)blocks.size() || rd.nparts < 1 || rd.part0 < 0 ||
+        (size_t)(rd.part0 + rd.nparts * tile) > plan.scratch)
+      return "reduction out of range";
+  }
+  if (plan.cta_off.empty() || plan.cta_off.front() != 0 || plan.cta_off.back() != (int)plan.cta_task.size() ||
+      plan.cta_task.size() != plan.tasks.size())
+    return "CTA lists do not cover the tasks";
+  std::vector<int> seen(plan.tasks.size(), 0);
+  for (size_t c = 0; c + 1 < plan.cta_off.size(); ++c) {
+    if (plan.cta_off[c + 1] <= plan.cta_off[c]) return "empty CTA list " + std::to_string(c);
+    for (int q = plan.cta_off[c]; q < plan.cta_off[c + 1]; ++q) {
+      const int t = plan.cta_task[q];
+      if (t < 0 || t >= (int)seen.size() || seen[t]++) return "CTA lists are not a permutation of the tasks";
+    }
+  }
+  if ((plan.units ? (size_t)plan.units * kTcUnitFloats * sizeof(float) : 0) != plan.pool_bytes)
+    return "pool size mismatch";
+  if (plan.units > (size_t)INT32_MAX) return "pool beyond 2^31 units";
+  return std::string();
 }
 
 }  // namespace dmrg

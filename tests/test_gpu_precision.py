@@ -1,0 +1,91 @@
+"""GPU parity of the split-precision (3xTF32) paths and of the dynamic bond
+dimension against the CPU oracle, through the C-ABI.
+
+Tolerance 1e-6 Eh for split precision (the precision target of the split
+H_eff psi path against the float64 oracle): with rq64_every_bond every bond
+energy is the float64 Rayleigh quotient of the split-converged eigenvector,
+second order in the eigenvector's error, and the truncations of the sweep
+follow the split eigenvectors.  The dynamic bond dimension in float64 is held
+to the float64 bar, 1e-8 Eh, with identical kept dimensions.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dmrg import OracleDMRG
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2503_20700_gb300 as p
+    p.load()
+    return p
+
+
+def _oracle_bonds(o):
+    return np.array([e for (_, _, _, e) in o.record.bond_energies])
+
+
+@pytest.mark.parametrize("prec", ["SPLIT_HPSI_TC", "SPLIT_HPSI"])
+@pytest.mark.parametrize("D", [12, 16])
+def test_split_sweep_and_bond_energies_match_oracle(pkg, prec, D):
+    h, L = W.cholesky_random(8, 32, seed=20250326)
+    eri = W.eri_from_cholesky(L)
+    o = OracleDMRG(h, eri, 8, 0, D=D)
+    eo = o.sweep(3)
+    g = pkg.DMRG(h, eri=eri, n_elec=8, two_s=0, D=D, precision=getattr(pkg, prec), tol=1e-10,
+                 rq64_every_bond=True)
+    eg = [g.sweep()[0] for _ in range(3)]
+    bg = g.bond_energies()
+    g.close()
+    assert np.abs(np.array(eg) - np.array(eo)).max() < 1e-6
+    bo = _oracle_bonds(o)
+    assert bg.shape == bo.shape
+    assert np.abs(bg - bo).max() < 1e-6
+
+
+def test_split_tc_doublet_and_aufbau_start_match_oracle(pkg):
+    """An odd electron count (doublet) from the aufbau product state."""
+    h, L = W.cholesky_random(8, 32, seed=7)
+    eri = W.eri_from_cholesky(L)
+    occ, path = W.aufbau_state(h, 7, 1)
+    o = OracleDMRG(h, eri, 7, 1, D=14, occ=occ, two_s_right=path)
+    eo = o.sweep(3)
+    g = pkg.DMRG(h, eri=eri, n_elec=7, two_s=1, D=14, precision=pkg.SPLIT_HPSI_TC, tol=1e-10,
+                 occ=occ, two_s_right=path, rq64_every_bond=True)
+    eg = [g.sweep()[0] for _ in range(3)]
+    bg = g.bond_energies()
+    g.close()
+    assert np.abs(np.array(eg) - np.array(eo)).max() < 1e-6
+    assert np.abs(bg - _oracle_bonds(o)).max() < 1e-6
+
+
+@pytest.mark.parametrize("target,dmin", [(1e-3, 2), (1e-5, 4)])
+def test_dynamic_bond_dimension_matches_oracle(pkg, target, dmin):
+    """Dynamic block-state selection: fewest multiplets with discarded weight
+    at most the target, between D_min and D; same energies and kept
+    dimensions as the oracle."""
+    h, L = W.cholesky_random(8, 32, seed=11)
+    eri = W.eri_from_cholesky(L)
+    o = OracleDMRG(h, eri, 8, 0, D=40, D_min=dmin, trunc_target=target)
+    eo = o.sweep(3)
+    g = pkg.DMRG(h, eri=eri, n_elec=8, two_s=0, D=40, D_min=dmin, trunc_target=target, tol=1e-10)
+    eg = []
+    for _ in range(3):
+        e, tr = g.sweep()
+        eg.append(e)
+    left, right = g.block_dims()
+    g.close()
+    assert np.abs(np.array(eg) - np.array(eo)).max() < 1e-8
+    # right blocks R(m) (the last m sites) of the last R->L half-sweep; the
+    # oracle indexes them by their first site n - m
+    _, orr = o.bond_dims()
+    compared = 0
+    for m in range(1, 8):
+        if right[m] >= 0 and orr[8 - m] is not None:
+            assert right[m] == orr[8 - m], (m, right[m], orr[8 - m])
+            compared += 1
+    assert compared >= 5
+    assert max(tr for tr in o.record.trunc[1:]) <= target + 1e-12

@@ -12,7 +12,7 @@ import scipy.linalg
 
 import workloads as W
 from oracle import casscf as C
-from oracle.dmrg import OracleDMRG, select_multiplets
+from oracle.dmrg import OracleDMRG, dbss_dimension, select_multiplets
 from oracle.fci import Hamiltonian, fci
 from oracle.rdm import Gamma_su2, energy_from_rdms, gamma_su2, rdm12
 from oracle.su2 import cg, wigner6j_bruteforce
@@ -216,6 +216,39 @@ def test_selection_rule_ties_and_threshold():
     cands = [(0.5, 2, 0, 0), (0.2, 3, 1, 0), (0.2, 1, 1, 0), (0.1, 2, 2, 0), (1e-13, 2, 0, 1)]
     assert select_multiplets(cands, 2) == [0, 2]         # tie broken by N asc
     assert select_multiplets(cands, 10) == [0, 2, 1, 3]  # below 1e-12 dropped
+
+
+def test_dbss_dimension_rule_by_hand():
+    """Fewest multiplets with discarded weight <= target, clamped to [D_min, D]."""
+    lam = [0.6, 0.3, 0.09, 0.009, 0.001]
+    assert dbss_dimension(lam, 10, 1, 0.0101) == 3      # discards 0.009 + 0.001
+    assert dbss_dimension(lam, 10, 1, 0.0099) == 4      # 0.01 is above the target
+    assert dbss_dimension(lam, 10, 1, 0.5) == 1
+    assert dbss_dimension(lam, 2, 1, 0.0099) == 2       # D_max caps
+    assert dbss_dimension(lam, 10, 4, 0.5) == 4         # D_min floors
+    assert dbss_dimension(list(reversed(lam)), 10, 1, 0.0101) == 3  # order-free
+    assert dbss_dimension(lam, 10, 1, 0.0) == 5
+
+
+def test_dbss_sweeps_bound_discarded_weight_and_reach_fci():
+    h, L = W.cholesky_random(6, 12, seed=1)
+    eri = W.eri_from_cholesky(L)
+    e_fci, _, _ = fci(h, eri, 6, 0)
+    fixed = OracleDMRG(h, eri, 6, 0, D=6)
+    e_fixed = fixed.sweep(3)
+    same = OracleDMRG(h, eri, 6, 0, D=6, trunc_target=0.0)
+    assert same.sweep(3) == e_fixed                    # target 0: fixed D
+    d = OracleDMRG(h, eri, 6, 0, D=400, D_min=2, trunc_target=1e-3)
+    es = d.sweep(3)
+    assert max(d.record.trunc[1:]) <= 1e-3 + 1e-15      # the bound, after the first sweep
+    assert es[-1] >= e_fci - 1e-10
+    assert min(d.kept) >= 2 and max(d.kept) < 400
+    finer = OracleDMRG(h, eri, 6, 0, D=400, D_min=2, trunc_target=1e-6)
+    e_finer = finer.sweep(3)[-1]
+    assert e_fci - 1e-10 <= e_finer < es[-1]             # a smaller target is closer to FCI
+    assert max(finer.kept) > max(d.kept)
+    tight = OracleDMRG(h, eri, 6, 0, D=400, D_min=1, trunc_target=1e-14)
+    assert tight.sweep(3)[-1] == pytest.approx(e_fci, abs=1e-9)
 
 
 # ---------------------------------------------------------------- CAS-SCF
