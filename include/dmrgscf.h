@@ -443,6 +443,25 @@ dmrg_status casscf_orbital_gradient(const double* h, const double* chol, int ran
                                     int ncore, int ncas, const double* gamma, const double* Gamma,
                                     double* grad, double* fock, int device);
 
+/*
+ * casscf_transform_backward -- backward of the map kappa -> (e_core, h_act,
+ * eri_act) = casscf_active_space(casscf_transform(expm(-K), h, chol)) of
+ * Sec. II.A, for upstream weights g_core (scalar), g_h (ncas^2) and g_eri
+ * (ncas^4): the weighted sum is a CAS-SCF energy functional with RDMs
+ * gamma = sym(g_h) / g_core and Gamma_tvwu = 2 sym8(g_eri)_tuvw / g_core, its
+ * derivative with respect to the rotated orbitals is dE/dR = 2 R F^T (F the
+ * generalised Fock matrix of casscf_orbital_gradient in the rotated basis;
+ * with g_core = 0 the core part of F is subtracted), and the adjoint Frechet
+ * derivative of expm carries it to K.  K: the antisymmetric nb x nb input,
+ * R = expm(-K), h_rot / chol_rot: the rotated integrals of the forward call.
+ * dK receives dE/dK, the gradient with respect to the full antisymmetric
+ * matrix (half of dE/dkappa_pq on both (p,q) and (q,p) with opposite signs).
+ */
+dmrg_status casscf_transform_backward(const double* K, const double* R, const double* h_rot,
+                                      const double* chol_rot, int rank, int nb, int ncore, int ncas,
+                                      double g_core, const double* g_h, const double* g_eri, double* dK,
+                                      int device);
+
 #ifdef __cplusplus
 }
 #endif

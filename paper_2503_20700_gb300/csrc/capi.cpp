@@ -831,4 +831,16 @@ dmrg_status casscf_orbital_gradient(const double* h, const double* chol, int ran
   });
 }
 
+dmrg_status casscf_transform_backward(const double* K, const double* R, const double* h_rot,
+                                      const double* chol_rot, int rank, int nb, int ncore, int ncas,
+                                      double g_core, const double* g_h, const double* g_eri, double* dK,
+                                      int device) {
+  if (!K || !R || !h_rot || !chol_rot || !g_h || !g_eri || !dK || rank < 1 || nb < 1 || nb > 4096 ||
+      ncore < 0 || ncas < 1 || ncore + ncas > nb)
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  return with_casscf(device, [&](dmrg::Casscf& c) {
+    c.transform_backward(K, R, h_rot, chol_rot, rank, nb, ncore, ncas, g_core, g_h, g_eri, dK);
+  });
+}
+
 }  // extern "C"

@@ -156,6 +156,67 @@ __global__ void k_add_diag(double* A, int n, double s) {
     A[(size_t)i * n + i] += s;
 }
 
+// out[0] = max_c sum_r |A[r, c]| (1-norm; single block)
+__global__ void k_norm1(const double* __restrict__ A, int n, double* __restrict__ out) {
+  __shared__ double s[256];
+  double m = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double a = 0.0;
+    for (int r = 0; r < n; ++r) a += fabs(A[(size_t)r * n + c]);
+    m = fmax(m, a);
+  }
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + st]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// B (2n x 2n) = [[K, G], [0, K]]
+__global__ void k_block_upper(const double* __restrict__ K, const double* __restrict__ G, int n,
+                              double* __restrict__ B) {
+  const size_t m = 2 * (size_t)n, tot = m * m;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / m), c = (int)(e % m);
+    double v = 0.0;
+    if (r < n && c < n) v = K[(size_t)r * n + c];
+    else if (r >= n && c >= n) v = K[(size_t)(r - n) * n + (c - n)];
+    else if (r < n && c >= n) v = G[(size_t)r * n + (c - n)];
+    B[e] = v;
+  }
+}
+
+// dK[r, c] = scale * (L[c, r] - L[r, c]) with L the upper-right block of E (2n x 2n)
+__global__ void k_antisym_from_upper(const double* __restrict__ E, int n, double scale, double* __restrict__ dK) {
+  const size_t tot = (size_t)n * n, m = 2 * (size_t)n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    dK[e] = scale * (E[(size_t)c * m + r + n] - E[(size_t)r * m + c + n]);
+  }
+}
+
+// Upstream weights of the active-space functional to RDM-shaped inputs of the
+// generalised Fock matrix: gamma = sym(g_h) / c, and Gamma[t,v,w,u] =
+// (2 / c) * (8-fold average of g_eri)[t,u,v,w] (E holds 1/2 (tu|vw) Gamma_tvwu)
+__global__ void k_weights_to_rdms(const double* __restrict__ gh, const double* __restrict__ ge, int n, double c,
+                                  double* __restrict__ gamma, double* __restrict__ Gamma) {
+  const size_t n2 = (size_t)n * n, tot = n2 * n2;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    size_t q = e;
+    const int w = (int)(q % n); q /= n;
+    const int v = (int)(q % n); q /= n;
+    const int u = (int)(q % n); q /= n;
+    const int t = (int)q;
+    auto at = [&](int a, int b, int cc, int d) { return ge[(((size_t)a * n + b) * n + cc) * n + d]; };
+    const double sym = (at(t, u, v, w) + at(u, t, v, w) + at(t, u, w, v) + at(u, t, w, v) + at(v, w, t, u) +
+                        at(w, v, t, u) + at(v, w, u, t) + at(w, v, u, t)) / 8.0;
+    Gamma[(((size_t)t * n + v) * n + w) * n + u] = (2.0 / c) * sym;
+    if (v == 0 && w == 0) gamma[(size_t)t * n + u] = 0.5 * (gh[(size_t)t * n + u] + gh[(size_t)u * n + t]) / c;
+  }
+}
+
 #define ST ((cudaStream_t)be_->stream())
 int grid_for(size_t n) { return (int)std::min<size_t>(152 * 16, std::max<size_t>(1, (n + 255) / 256)); }
 
@@ -195,14 +256,15 @@ Casscf::Casscf(Backend* be) : be_(be) {}
 // R = expm(-K): scaling and squaring with a degree-18 Taylor polynomial
 // (Horner form) of the scaled matrix.
 void Casscf::expm_neg(const double* dK, int n, double* dR, double sign) {
-  // host copy for the norm (1-norm of the scaled argument <= 1/4)
-  std::vector<double> K((size_t)n * n);
-  be_->copy_d2h(K.data(), dK, K.size() * sizeof(double));
+  // 1-norm on the device; the number of squarings makes the scaled
+  // argument's norm at most 1/4
   double nrm = 0.0;
-  for (int c = 0; c < n; ++c) {
-    double s = 0.0;
-    for (int r = 0; r < n; ++r) s += std::abs(K[(size_t)r * n + c]);
-    nrm = std::max(nrm, s);
+  {
+    Dev d0(be_);
+    double* dn = d0.alloc(1);
+    k_norm1<<<1, 256, 0, ST>>>(dK, n, dn);
+    be_->copy_d2h(&nrm, dn, sizeof(double));
+    be_->sync();
   }
   int sq = 0;
   while (nrm / std::ldexp(1.0, sq) > 0.25 && sq < 60) ++sq;
@@ -240,26 +302,26 @@ void Casscf::rotation(const double* K, int nb, double* R) {
 // dE/dK for R = expm(-K) given G = dE/dR: with X = -K, dE/dX = L_exp(X^T, G)
 // = upper-right block of expm([[K, G], [0, K]]) (X^T = K for antisymmetric K),
 // so dE/dK = -L and the parameter gradient is antisymmetrised.
-void Casscf::rotation_backward(const double* K, const double* G, int nb, double* dK) {
-  int n2 = 2 * nb;
-  std::vector<double> B((size_t)n2 * n2, 0.0);
-  for (int r = 0; r < nb; ++r)
-    for (int c = 0; c < nb; ++c) {
-      B[(size_t)r * n2 + c] = K[(size_t)r * nb + c];
-      B[(size_t)(r + nb) * n2 + c + nb] = K[(size_t)r * nb + c];
-      B[(size_t)r * n2 + c + nb] = G[(size_t)r * nb + c];
-    }
+void Casscf::rotation_backward_dev(const double* dKin, const double* dG, int nb, double scale, double* ddK) {
+  const size_t n2 = 2 * (size_t)nb;
   Dev d(be_);
-  double* dB = d.upload(B.data(), B.size());
-  double* dE = d.alloc(B.size());
-  expm_neg(dB, n2, dE, 1.0);
-  std::vector<double> E(B.size());
-  be_->copy_d2h(E.data(), dE, E.size() * sizeof(double));
-  for (int r = 0; r < nb; ++r)
-    for (int c = 0; c < nb; ++c) {
-      double a = -E[(size_t)r * n2 + c + nb], b = -E[(size_t)c * n2 + r + nb];
-      dK[(size_t)r * nb + c] = a - b;
-    }
+  double* dB = d.alloc(n2 * n2);
+  double* dE = d.alloc(n2 * n2);
+  k_block_upper<<<grid_for(n2 * n2), 256, 0, ST>>>(dKin, dG, nb, dB);
+  expm_neg(dB, (int)n2, dE, 1.0);
+  // dK = -(L - L^T) with L = dE/dX = upper-right block (X = -K, X^T = K)
+  k_antisym_from_upper<<<grid_for((size_t)nb * nb), 256, 0, ST>>>(dE, nb, scale, ddK);
+  be_->sync();
+}
+
+void Casscf::rotation_backward(const double* K, const double* G, int nb, double* dK) {
+  Dev d(be_);
+  const size_t nn = (size_t)nb * nb;
+  double* dKin = d.upload(K, nn);
+  double* dG = d.upload(G, nn);
+  double* dout = d.alloc(nn);
+  rotation_backward_dev(dKin, dG, nb, 1.0, dout);
+  be_->copy_d2h(dK, dout, nn * sizeof(double));
 }
 
 // h' = R^T h R and L'^k = R^T L^k R (batched over the Cholesky index)
@@ -369,6 +431,64 @@ void Casscf::gradient(const double* h, const double* L, int rank, int nb, int nc
   double* dL = d.upload(L, nn * rank);
   double* dg = d.upload(gamma, (size_t)a2);
   double* dG = d.upload(Gamma, (size_t)a2 * a2);
+  double* F = d.alloc(nn);
+  fock_dev(dh, dL, rank, nb, ncore, ncas, dg, dG, F);
+  double* dgr = d.alloc(nn);
+  k_gradient<<<grid_for(nn), 256, 0, ST>>>(F, nb, ncore, ncas, dgr);
+  be_->copy_d2h(grad, dgr, nn * sizeof(double));
+  if (fock) be_->copy_d2h(fock, F, nn * sizeof(double));
+}
+
+// Backward of (e_core, h_act, eri_act) = active_space(transform(expm(-K), h, L))
+// for upstream weights (c, g_h, g_eri): the weighted sum is a CAS-SCF energy
+// functional with RDMs (g_h / c, 2 g_eri / c), whose derivative with respect
+// to the rotated orbitals is 2 R F^T (F its generalised Fock matrix); the
+// core part of F scales with c, so for c = 0 the functional is evaluated with
+// c = 1 and the pure-core F(0, 0) subtracted.  The adjoint Frechet derivative
+// of expm carries dE/dR to K; half of it is the gradient with respect to the
+// full antisymmetric input matrix.
+void Casscf::transform_backward(const double* K, const double* R, const double* h, const double* L, int rank,
+                                int nb, int ncore, int ncas, double g_core, const double* g_h,
+                                const double* g_eri, double* dK) {
+  Dev d(be_);
+  const size_t nn = (size_t)nb * nb;
+  const int a2 = ncas * ncas;
+  double* dKin = d.upload(K, nn);
+  double* dR = d.upload(R, nn);
+  double* dh = d.upload(h, nn);
+  double* dL = d.upload(L, nn * rank);
+  double* dgh = d.upload(g_h, (size_t)a2);
+  double* dge = d.upload(g_eri, (size_t)a2 * a2);
+  const double c_eff = g_core != 0.0 ? g_core : 1.0;
+  double* dgam = d.alloc((size_t)a2);
+  double* dGam = d.alloc((size_t)a2 * a2);
+  k_weights_to_rdms<<<grid_for((size_t)a2 * a2), 256, 0, ST>>>(dgh, dge, ncas, c_eff, dgam, dGam);
+  double* F = d.alloc(nn);
+  fock_dev(dh, dL, rank, nb, ncore, ncas, dgam, dGam, F);
+  double* Ft = d.alloc(nn);
+  if (g_core != 0.0) {
+    k_axpbypcz<<<grid_for(nn), 256, 0, ST>>>(Ft, nn, g_core, F, 0.0, nullptr, 0.0, nullptr);
+  } else {
+    double* z1 = d.alloc((size_t)a2);
+    double* z2 = d.alloc((size_t)a2 * a2);
+    double* F0 = d.alloc(nn);
+    fock_dev(dh, dL, rank, nb, ncore, ncas, z1, z2, F0);
+    k_axpbypcz<<<grid_for(nn), 256, 0, ST>>>(Ft, nn, 1.0, F, -1.0, F0, 0.0, nullptr);
+  }
+  // G = dE/dR = 2 R Ft^T
+  double* G = d.alloc(nn);
+  gemm1(be_, G, nb, nb, nb, dR, nb, 0, Ft, nb, 1, nb, 2.0);
+  double* out = d.alloc(nn);
+  rotation_backward_dev(dKin, G, nb, 0.5, out);
+  be_->copy_d2h(dK, out, nn * sizeof(double));
+}
+
+// generalised Fock matrix F (device, nb x nb) from device integrals and RDMs
+void Casscf::fock_dev(const double* dh, const double* dL, int rank, int nb, int ncore, int ncas,
+                      const double* dg, const double* dG, double* F) {
+  Dev d(be_);
+  size_t nn = (size_t)nb * nb;
+  int a2 = ncas * ncas;
   FockParts f = fock_parts(be_, d, dh, dL, rank, nb, ncore, ncas, dg);
   // d[t,u,v,w] = Gamma[t,v,w,u];  W (rank x a2) = La (rank x a2) d^T (a2 x a2)
   double* dd = d.alloc((size_t)a2 * a2);
@@ -382,12 +502,8 @@ void Casscf::gradient(const double* h, const double* L, int rank, int nb, int nc
   for (int k = 0; k < rank; ++k)
     s.push_back({W + (size_t)k * a2, dL + nn * k + ncore, ncas, ncas, nb, 0, 1, 1.0});
   be_->gemm(g, s, Precision::FP64);
-  double* F = d.alloc(nn);
   k_assemble_fock<<<grid_for(nn), 256, 0, ST>>>(f.FI, f.FA, dg, F2, nb, ncore, ncas, F);
-  double* dgr = d.alloc(nn);
-  k_gradient<<<grid_for(nn), 256, 0, ST>>>(F, nb, ncore, ncas, dgr);
-  be_->copy_d2h(grad, dgr, nn * sizeof(double));
-  if (fock) be_->copy_d2h(fock, F, nn * sizeof(double));
+  be_->sync();
 }
 
 }  // namespace dmrg

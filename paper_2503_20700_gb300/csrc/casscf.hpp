@@ -22,8 +22,22 @@ class Casscf {
   // grad = 2 (F - F^T) (active-active zero); fock (optional) = F
   void gradient(const double* h, const double* L, int rank, int nb, int ncore, int ncas,
                 const double* gamma, const double* Gamma, double* grad, double* fock);
+  // backward of the whole forward map (rotation, transform, active space)
+  // for upstream weights (g_core, g_h, g_eri): the gradient with respect to
+  // the full antisymmetric K (nb x nb)
+  void transform_backward(const double* K, const double* R, const double* h, const double* L, int rank,
+                          int nb, int ncore, int ncas, double g_core, const double* g_h,
+                          const double* g_eri, double* dK);
   // device scaling-and-squaring exponential: dR = expm(sign * dK)
   void expm_neg(const double* dK, int n, double* dR, double sign);
+
+ private:
+  // device-pointer forms
+  void rotation_backward_dev(const double* dK, const double* dG, int nb, double scale, double* ddK);
+  void fock_dev(const double* dh, const double* dL, int rank, int nb, int ncore, int ncas, const double* dg,
+                const double* dG, double* F);
+
+ public:
 
  private:
   Backend* be_;

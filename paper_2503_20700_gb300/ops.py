@@ -168,8 +168,9 @@ def _bind_casscf(lib):
     lib.casscf_transform.argtypes = [dp, dp, dp, I, I, dp, dp, I]
     lib.casscf_active_space.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, I]
     lib.casscf_orbital_gradient.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, dp, I]
+    lib.casscf_transform_backward.argtypes = [dp, dp, dp, dp, I, I, I, I, ctypes.c_double, dp, dp, dp, I]
     for f in ("casscf_rotation", "casscf_rotation_backward", "casscf_transform",
-              "casscf_active_space", "casscf_orbital_gradient"):
+              "casscf_active_space", "casscf_orbital_gradient", "casscf_transform_backward"):
         getattr(lib, f).restype = I
 
 
@@ -228,3 +229,12 @@ def orbital_gradient(h, L, ncore, ncas, gamma, Gamma, device=0, with_fock=False)
     _call("casscf_orbital_gradient", _dp(h), _dp(L), L.shape[0], h.shape[0], ncore, ncas,
           _dp(gamma), _dp(Gamma), _dp(g), _dp(F), device)
     return (g, F) if with_fock else g
+
+
+def transform_backward(K, R, h_rot, L_rot, ncore, ncas, g_core, g_h, g_eri, device=0):
+    """dE/dK of the weighted active-space outputs (casscf_transform_backward)."""
+    K, R, h_rot, L_rot, g_h, g_eri = (_c(x) for x in (K, R, h_rot, L_rot, g_h, g_eri))
+    dK = np.zeros_like(K)
+    _call("casscf_transform_backward", _dp(K), _dp(R), _dp(h_rot), _dp(L_rot), L_rot.shape[0], K.shape[0],
+          ncore, ncas, float(g_core), _dp(g_h), _dp(g_eri), _dp(dK), device)
+    return dK
