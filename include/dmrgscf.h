@@ -272,6 +272,16 @@ dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* ctx, double* ms);
 /* Device memory held by the context now and at its high-water mark (bytes). */
 dmrg_status dmrg_memory(const dmrg_ctx* ctx, int64_t* in_use, int64_t* peak);
 
+/* Staging detail (bytes), out[6]: [0] stored blocks on the device, [1] stored
+ * blocks staged out to pinned host memory, [2] total moved out and [3] total
+ * moved back in so far, [4] the largest working memory of a bond beyond the
+ * stored blocks so far, [5] the largest stored block.  With hbm_budget_bytes
+ * set, stored blocks whose next use in the sweep is farthest away are copied
+ * to pinned host memory on a side stream whenever the stored blocks plus the
+ * last bond's working memory would exceed the budget, and are copied back
+ * one bond ahead of their use; the values are bit-identical either way. */
+dmrg_status dmrg_memory_detail(const dmrg_ctx* ctx, int64_t* out);
+
 /* Number of device kernel launches issued by the context so far. */
 dmrg_status dmrg_launch_count(const dmrg_ctx* ctx, int64_t* launches);
 
@@ -461,6 +471,40 @@ dmrg_status casscf_transform_backward(const double* K, const double* R, const do
                                       const double* chol_rot, int rank, int nb, int ncore, int ncas,
                                       double g_core, const double* g_h, const double* g_eri, double* dK,
                                       int device);
+
+/* Options of the DMRG-SCF macro iterations. */
+typedef struct {
+  int max_iter;     /* macro iterations (60)                                 */
+  double e_tol;     /* energy change of the last iteration (1e-7 Eh)         */
+  double g_tol;     /* largest orbital-gradient entry (1e-3)                 */
+  int memory;       /* L-BFGS pairs kept (8)                                 */
+  double max_step;  /* cap of the largest rotation entry of a step (0.5)     */
+  int sweeps;       /* DMRG sweeps per macro iteration (4)                   */
+} casscf_scf_opts;
+
+void casscf_default_scf_opts(casscf_scf_opts* o);
+
+/*
+ * casscf_dmrg_scf -- the DMRG-SCF macro loop of Sec. II.A (the paper's
+ * thresholds: 1e-7 in the energy, 1e-3 in the orbital gradient).  Per
+ * iteration: the integrals rotated by the accumulated orbital rotation U
+ * (casscf_transform), the active-space problem (casscf_active_space), a
+ * DMRG-CI solve of it (dmrg_opts; `sweeps` sweeps from the default product
+ * state) and its spin-free RDMs (dmrg_rdm12), the orbital gradient
+ * (casscf_orbital_gradient) and a step: limited-memory BFGS over the
+ * non-redundant rotations (core-active, core-virtual, active-virtual) with
+ * an approximate diagonal Hessian (virtual-core 4 (f_a - f_i), virtual-active
+ * 2 n_t f_a - 2 F_tt, active-core 4 (f_t - f_i) + 2 n_t f_i - 2 F_tt, f =
+ * F^I + F^A, floored at 0.05) as the initial inverse and the largest entry
+ * capped at max_step; U <- U expm(-(x - x^T)).  Stops after an iteration
+ * whose energy changed by less than e_tol with max |g| below g_tol.
+ * Outputs: U (nb x nb), energies and gmax (max_iter values, the first
+ * *n_iter written), *converged (1 or 0).  ORCA's SuperCI(PT) optimiser of
+ * the paper is not part of this library.
+ */
+dmrg_status casscf_dmrg_scf(const double* h, const double* chol, int rank, int nb, int ncore, int ncas,
+                            int n_elec, int two_s, const dmrg_opts* dopts, const casscf_scf_opts* sopts,
+                            double* U, double* energies, double* gmax, int* n_iter, int* converged);
 
 #ifdef __cplusplus
 }

@@ -106,3 +106,118 @@ def orbital_gradient(h, L, ncore, ncas, gamma, Gamma):
     a = slice(ncore, ncore + ncas)
     G[a, a] = 0.0
     return G
+
+
+# ---------------------------------------------------------------- DMRG-SCF
+def fock_diagonals(h, L, ncore, ncas, gamma, Gamma):
+    """Diagonals of F^I, F^A and of the generalised Fock matrix F."""
+    a = slice(ncore, ncore + ncas)
+    fi = inactive_fock(h, L, ncore)
+    w = np.einsum("ktu,tu->k", L[:, a, a], gamma)
+    fa = np.einsum("k,kpq->pq", w, L)
+    fa -= 0.5 * np.einsum("kpt,tu,kuq->pq", L[:, :, a], gamma, L[:, a, :], optimize=True)
+    F = generalized_fock(h, L, ncore, ncas, gamma, Gamma)
+    return np.diag(fi).copy(), np.diag(fa).copy(), np.diag(F).copy()
+
+
+def diagonal_hessian(h, L, ncore, ncas, gamma, Gamma, floor=0.05):
+    """Approximate diagonal orbital Hessian H[p, q] (p > q) of the
+    closed-shell-core CAS-SCF energy, one value per non-redundant rotation,
+    floored at `floor` (the step of a quasi-Newton update):
+      core i - virtual a:   4 (f_aa - f_ii)
+      active t - virtual a: 2 n_t f_aa - 2 F_tt
+      core i - active t:    4 (f_tt - f_ii) + 2 n_t f_ii - 2 F_tt
+    with f = F^I + F^A, n_t = gamma~_tt and F the generalised Fock matrix.
+    Active-active pairs and the rest are 0 (no step)."""
+    nb = h.shape[0]
+    fi, fa, Fd = fock_diagonals(h, L, ncore, ncas, gamma, Gamma)
+    f = fi + fa
+    H = np.zeros((nb, nb))
+    for p in range(nb):
+        for q in range(p):
+            pc, pa = p < ncore, ncore <= p < ncore + ncas
+            qc, qa = q < ncore, ncore <= q < ncore + ncas
+            if pc or (pa and qa):
+                continue          # p > q: p core implies q core; active-active redundant
+            if not pa and qc:      # virtual - core
+                v = 4.0 * (f[p] - f[q])
+            elif not pa and qa:    # virtual - active
+                t = q - ncore
+                v = 2.0 * gamma[t, t] * f[p] - 2.0 * Fd[q]
+            elif pa and qc:        # active - core
+                t = p - ncore
+                v = 4.0 * (f[p] - f[q]) + 2.0 * gamma[t, t] * f[q] - 2.0 * Fd[p]
+            else:
+                continue
+            H[p, q] = max(v, floor)
+    return H
+
+
+def rotation_mask(nb, ncore, ncas):
+    """Non-redundant rotations: p > q in different classes (core, active,
+    virtual); core-core, active-active and virtual-virtual rotations are left
+    out (the last two do not change a CAS energy; active-active rotations are
+    not used, Sec. II.C)."""
+    cls = np.array([0 if p < ncore else (1 if p < ncore + ncas else 2) for p in range(nb)])
+    m = (cls[:, None] != cls[None, :]) & np.tril(np.ones((nb, nb), bool), -1)
+    return m.astype(float)
+
+
+def dmrg_scf(h, L, ncore, ncas, solver, max_iter=60, e_tol=1e-7, g_tol=1e-3, memory=8, max_step=0.5):
+    """DMRG-SCF macro iterations (Sec. II.A; thresholds of the paper: energy
+    change 1e-7, gradient 1e-3).  The active-space problem of the current
+    orbitals is solved by `solver(h_act, eri_act, e_core)` -> (E, gamma~,
+    Gamma~); the orbital gradient g = dE/dkappa (non-redundant p > q) comes
+    from the RDMs; the step x = -H^-1 g is a limited-memory BFGS step (the
+    last `memory` pairs of steps and gradient changes, two-loop recursion)
+    with the diagonal Hessian above as the initial inverse, its largest
+    entry capped at max_step; the orbitals rotate as U <- U expm(-(x - x^T)).
+    Stops after an iteration whose energy change is below e_tol with
+    max |g| below g_tol.
+
+    Returns (energies, max |g| per iteration, U)."""
+    nb = h.shape[0]
+    mask = rotation_mask(nb, ncore, ncas)
+    U = np.eye(nb)
+    energies, gmax = [], []
+    S, Y = [], []
+    x_prev = g_prev = None
+    a = slice(ncore, ncore + ncas)
+    for it in range(max_iter):
+        h2, L2 = transform(h, L, U)
+        fi = inactive_fock(h2, L2, ncore)
+        e_core = float(np.trace(h2[:ncore, :ncore]) + np.trace(fi[:ncore, :ncore]))
+        eri_a = np.einsum("ktu,kvw->tuvw", L2[:, a, a], L2[:, a, a])
+        E, gamma, Gamma = solver(fi[a, a], eri_a, e_core)
+        g = mask * orbital_gradient(h2, L2, ncore, ncas, gamma, Gamma)
+        energies.append(float(E))
+        gmax.append(float(np.abs(g).max()))
+        if it > 0 and abs(energies[-1] - energies[-2]) < e_tol and gmax[-1] < g_tol:
+            break
+        if x_prev is not None:
+            y = g - g_prev
+            if float(np.sum(x_prev * y)) > 1e-12:
+                S.append(x_prev)
+                Y.append(y)
+                if len(S) > memory:
+                    S.pop(0)
+                    Y.pop(0)
+        Hd = diagonal_hessian(h2, L2, ncore, ncas, gamma, Gamma)
+        q = g.copy()
+        alpha = []
+        for s_i, y_i in zip(reversed(S), reversed(Y)):
+            rho = 1.0 / float(np.sum(y_i * s_i))
+            al = rho * float(np.sum(s_i * q))
+            q = q - al * y_i
+            alpha.append((rho, al))
+        r = np.where(mask > 0, q / np.where(Hd > 0, Hd, 1.0), 0.0)
+        for (s_i, y_i), (rho, al) in zip(zip(S, Y), reversed(alpha)):
+            be = rho * float(np.sum(y_i * r))
+            r = r + (al - be) * s_i
+        x = -r
+        big = float(np.abs(x).max())
+        if big > max_step:
+            x = x * (max_step / big)
+        U = U @ rotation_matrix(x - x.T)
+        x_prev, g_prev = x, g
+    return energies, gmax, U

@@ -109,6 +109,8 @@ def load(path=None):
     lib.dmrg_last_sweep_device_ms.restype = I
     lib.dmrg_memory.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.dmrg_memory.restype = I
+    lib.dmrg_memory_detail.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.dmrg_memory_detail.restype = I
     lib.dmrg_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.dmrg_launch_count.restype = I
     lib.dmrg_free.argtypes = [P]
@@ -291,6 +293,15 @@ class DMRG:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(self._lib, self._ctx, self._lib.dmrg_memory(self._ctx, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def memory_detail(self):
+        """Staging detail: stored bytes on the device and in pinned host memory,
+        bytes moved out / in so far, the largest bond working memory and the
+        largest stored block."""
+        out = (ctypes.c_int64 * 6)()
+        _check(self._lib, self._ctx, self._lib.dmrg_memory_detail(self._ctx, out))
+        keys = ["stored_device", "stored_host", "staged_out", "staged_in", "max_bond_extra", "max_block"]
+        return dict(zip(keys, list(out)))
 
     def launch_count(self):
         n = ctypes.c_int64()

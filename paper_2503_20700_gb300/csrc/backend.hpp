@@ -78,6 +78,22 @@ class Backend {
   // throws "out of device memory"
   virtual void set_budget(size_t bytes) { budget_ = bytes; }
   size_t budget() const { return budget_; }
+  // Staging of device buffers to pinned host memory on a side stream.
+  //   stage_out(dev, bytes): returns a pinned host copy of dev; the copy runs
+  //     on the side stream after all work queued so far on the main stream,
+  //     and dev is freed there (stream-ordered) once the copy is done.
+  //   stage_in(host, bytes): allocates device memory and copies host into it
+  //     on the side stream; returns the device pointer.  The main stream waits
+  //     for the copy at the next stage_join() (or at release of the host copy).
+  //   stage_join(): the main stream waits for every side-stream copy issued.
+  //   host_release(host): frees a pinned copy after its copies completed.
+  virtual void* stage_out(void* dev, size_t bytes) = 0;
+  virtual void* stage_in(const void* host, size_t bytes) = 0;
+  virtual void stage_join() = 0;
+  virtual void host_release(void* host) = 0;
+  size_t staged_bytes = 0;       // pinned host bytes currently held
+  size_t staged_out_bytes = 0;   // counters of bytes moved (for the accounting)
+  size_t staged_in_bytes = 0;
   // bound of every device-side wait of the kernels (nanoseconds; 0: a wait
   // that is not complete at its first probe gives up)
   void set_wait_ns(unsigned long long ns) { wait_ns_ = ns; }
@@ -130,6 +146,7 @@ class Backend {
   int tag = 0;
   long launches = 0;     // kernel launches issued by this backend
   size_t peak_bytes = 0; // high-water mark of bytes_in_use()
+  size_t window_peak = 0;  // high-water mark since the caller last reset it
   // Device-side interval on the backend stream (CUDA events): mark_begin()
   // then mark_end() returns the elapsed milliseconds.
   virtual void mark_begin() = 0;

@@ -702,6 +702,10 @@ class CudaBackend : public Backend {
   int sm_count() const override { return sms; }
   ~CudaBackend() override {
     cudaStreamSynchronize(st);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
     if (dtask) cudaFreeAsync(dtask, st);
@@ -725,6 +729,7 @@ class CudaBackend : public Backend {
     }
     used += b;
     peak_bytes = std::max(peak_bytes, used);
+    window_peak = std::max(window_peak, used);
     live.push_back({p, b});
     return p;
   }
@@ -740,6 +745,67 @@ class CudaBackend : public Backend {
     CK(cudaFreeAsync(p, st));
   }
   size_t bytes_in_use() const override { return used; }
+  // ---- staging to pinned host memory on the side stream
+  cudaStream_t side = nullptr;
+  cudaStream_t side_stream() {
+    if (!side) CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    return side;
+  }
+  void* stage_out(void* dev, size_t bytes) override {
+    if (!dev || bytes == 0) return nullptr;
+    cudaStream_t sd = side_stream();
+    void* h = nullptr;
+    if (cudaMallocHost(&h, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::runtime_error("out of pinned host memory (" + std::to_string(bytes) + " bytes)");
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, st));
+    CK(cudaStreamWaitEvent(sd, e, 0));
+    CK(cudaEventDestroy(e));
+    CK(cudaMemcpyAsync(h, dev, bytes, cudaMemcpyDeviceToHost, sd));
+    // the device buffer goes back to the pool after the copy (side-stream order)
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i].first == dev) {
+        used -= live[i].second;
+        live[i] = live.back();
+        live.pop_back();
+        break;
+      }
+    CK(cudaFreeAsync(dev, sd));
+    staged_bytes += bytes;
+    staged_out_bytes += bytes;
+    ++launches;
+    return h;
+  }
+  void* stage_in(const void* host, size_t bytes) override {
+    if (!host || bytes == 0) return nullptr;
+    cudaStream_t sd = side_stream();
+    void* d = alloc(bytes);  // main-stream ordered allocation
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, st));
+    CK(cudaStreamWaitEvent(sd, e, 0));
+    CK(cudaEventDestroy(e));
+    CK(cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, sd));
+    staged_in_bytes += bytes;
+    ++launches;
+    return d;
+  }
+  void stage_join() override {
+    if (!side) return;
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, side));
+    CK(cudaStreamWaitEvent(st, e, 0));
+    CK(cudaEventDestroy(e));
+  }
+  void host_release(void* host) override {
+    if (!host) return;
+    if (side) CK(cudaStreamSynchronize(side));
+    CK(cudaFreeHost(host));
+  }
   size_t total_mem = 0;
   size_t capacity() const override { return total_mem; }
   size_t device_free() const override {

@@ -311,6 +311,19 @@ dmrg_status dmrg_set_kernel_wait_timeout(double seconds) {
   return DMRG_OK;
 }
 
+dmrg_status dmrg_memory_detail(const dmrg_ctx* c, int64_t* out) {
+  if (!c || !c->eng || !out) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
+  size_t d = 0, h = 0, mb = 0, mx = 0;
+  c->eng->memory_detail(&d, &h, &mb, &mx);
+  out[0] = (int64_t)d;
+  out[1] = (int64_t)h;
+  out[2] = (int64_t)c->be->staged_out_bytes;
+  out[3] = (int64_t)c->be->staged_in_bytes;
+  out[4] = (int64_t)mx;
+  out[5] = (int64_t)mb;
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* c, int D) {
   if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
   if (D < 1) return fail(c, DMRG_EINVAL, "D < 1");
@@ -841,6 +854,90 @@ dmrg_status casscf_transform_backward(const double* K, const double* R, const do
   return with_casscf(device, [&](dmrg::Casscf& c) {
     c.transform_backward(K, R, h_rot, chol_rot, rank, nb, ncore, ncas, g_core, g_h, g_eri, dK);
   });
+}
+
+void casscf_default_scf_opts(casscf_scf_opts* o) {
+  if (!o) return;
+  o->max_iter = 60;
+  o->e_tol = 1e-7;
+  o->g_tol = 1e-3;
+  o->memory = 8;
+  o->max_step = 0.5;
+  o->sweeps = 4;
+}
+
+dmrg_status casscf_dmrg_scf(const double* h, const double* chol, int rank, int nb, int ncore, int ncas,
+                            int n_elec, int two_s, const dmrg_opts* dopts, const casscf_scf_opts* sopts,
+                            double* U, double* energies, double* gmax, int* n_iter, int* converged) {
+  if (!h || !chol || !U || !energies || !gmax || rank < 1 || nb < 2 || nb > 4096 || ncore < 0 || ncas < 2 ||
+      ncore + ncas > nb || n_elec < 0 || n_elec > 2 * ncas || two_s < 0 || ((n_elec - two_s) & 1))
+    return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  dmrg_opts o;
+  dmrg_default_opts(&o);
+  if (dopts) o = *dopts;
+  casscf_scf_opts so;
+  casscf_default_scf_opts(&so);
+  if (sopts) so = *sopts;
+  if (so.max_iter < 1 || so.sweeps < 1 || so.memory < 0 || !(so.max_step > 0) || !(so.e_tol > 0) || !(so.g_tol > 0))
+    return fail(nullptr, DMRG_EINVAL, "bad SCF options");
+  if (o.D < 1 || o.max_space < 4 || o.davidson_tol <= 0 || o.max_davidson_iter < 1 || !sweep_precision_ok(o.precision))
+    return fail(nullptr, DMRG_EINVAL, "bad DMRG options");
+  std::vector<int> occ, path;
+  if (!default_state(ncas, n_elec, two_s, occ, path)) return fail(nullptr, DMRG_EINVAL, "two_s too large");
+  std::string err;
+  std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(o.device, &err));
+  if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  be->set_wait_ns((unsigned long long)(o.wait_timeout_s * 1e9));
+  try {
+    dmrg::Casscf cas(be.get());
+    dmrg::ScfStepper stepper(be.get(), nb, ncore, ncas, so.memory, so.max_step);
+    const size_t nn = (size_t)nb * nb, a2 = (size_t)ncas * ncas;
+    std::vector<double> Ucur(nn, 0.0), h2(nn), L2(nn * rank), hact(a2), eact(a2 * a2), gam(a2), Gam(a2 * a2),
+        g(nn), K(nn), R(nn), Un(nn);
+    for (int p = 0; p < nb; ++p) Ucur[(size_t)p * nb + p] = 1.0;
+    dmrg::Options eo;
+    eo.D = o.D;
+    eo.max_davidson_iter = o.max_davidson_iter;
+    eo.davidson_tol = o.davidson_tol;
+    map_precision(o.precision, &eo.prec, &eo.prec_renorm);
+    eo.max_space = o.max_space;
+    eo.seed = o.seed;
+    eo.trunc_target = o.trunc_target;
+    eo.D_min = o.D_min;
+    int it = 0;
+    bool conv = false;
+    for (; it < so.max_iter; ++it) {
+      cas.transform(Ucur.data(), h, chol, rank, nb, h2.data(), L2.data());
+      double e_core = 0.0;
+      cas.active_space(h2.data(), L2.data(), rank, nb, ncore, ncas, &e_core, hact.data(), eact.data());
+      double E = 0.0;
+      {
+        dmrg::Engine eng(be.get(), ncas, hact.data(), eact.data(), e_core, n_elec, two_s, eo, occ.data(),
+                         path.data());
+        for (int sw = 0; sw < so.sweeps; ++sw) E = eng.sweep().energy;
+        eng.rdm12(gam.data(), Gam.data());
+      }
+      cas.gradient(h2.data(), L2.data(), rank, nb, ncore, ncas, gam.data(), Gam.data(), g.data(), nullptr);
+      const double gm = stepper.gradient_max(g.data());
+      energies[it] = E;
+      gmax[it] = gm;
+      if (it > 0 && std::abs(E - energies[it - 1]) < so.e_tol && gm < so.g_tol) {
+        conv = true;
+        ++it;
+        break;
+      }
+      stepper.step(cas, h2.data(), L2.data(), rank, gam.data(), Gam.data(), K.data());
+      cas.rotation(K.data(), nb, R.data());
+      cas.matmul(Ucur.data(), R.data(), nb, Un.data());
+      Ucur.swap(Un);
+    }
+    std::copy(Ucur.begin(), Ucur.end(), U);
+    if (n_iter) *n_iter = it;
+    if (converged) *converged = conv ? 1 : 0;
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
+  }
+  return DMRG_OK;
 }
 
 }  // extern "C"

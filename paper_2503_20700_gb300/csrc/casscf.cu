@@ -217,6 +217,90 @@ __global__ void k_weights_to_rdms(const double* __restrict__ gh, const double* _
   }
 }
 
+// mask[p, q] = 1 for the non-redundant rotations p > q between different
+// orbital classes (core, active, virtual), else 0
+__global__ void k_rotation_mask(int nb, int ncore, int ncas, double* __restrict__ m) {
+  const size_t tot = (size_t)nb * nb;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / nb), q = (int)(e % nb);
+    const int cp = p < ncore ? 0 : (p < ncore + ncas ? 1 : 2), cq = q < ncore ? 0 : (q < ncore + ncas ? 1 : 2);
+    m[e] = (p > q && cp != cq) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b, size_t n, double* __restrict__ out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = a[e] * b[e];
+}
+
+// out[0] = max |a| (single block)
+__global__ void k_maxabs(const double* __restrict__ a, size_t n, double* __restrict__ out) {
+  __shared__ double s[256];
+  double m = 0.0;
+  for (size_t e = threadIdx.x; e < n; e += blockDim.x) m = fmax(m, fabs(a[e]));
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + st]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// r = mask ? q / h : 0  (h > 0 by the floor)
+__global__ void k_div_mask(const double* __restrict__ q, const double* __restrict__ h, const double* __restrict__ m,
+                           size_t n, double* __restrict__ r) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    r[e] = (m[e] != 0.0 && h[e] > 0.0) ? q[e] / h[e] : 0.0;
+}
+
+// K = x - x^T
+__global__ void k_antisym(const double* __restrict__ x, int nb, double* __restrict__ K) {
+  const size_t tot = (size_t)nb * nb;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / nb), q = (int)(e % nb);
+    K[e] = x[e] - x[(size_t)q * nb + p];
+  }
+}
+
+// fd[p] = F^I_pp + F^A_pp (FA may be null)
+__global__ void k_fock_diag(const double* __restrict__ FI, const double* __restrict__ FA, int nb, double* __restrict__ fd) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nb; p += gridDim.x * blockDim.x)
+    fd[p] = FI[(size_t)p * nb + p] + (FA ? FA[(size_t)p * nb + p] : 0.0);
+}
+
+// Approximate diagonal orbital Hessian of the closed-shell-core CAS-SCF
+// energy for the rotations p > q, floored: virtual-core 4 (f_p - f_q),
+// virtual-active 2 n_t f_p - 2 F_tt, active-core 4 (f_p - f_q) + 2 n_t f_q -
+// 2 F_tt (f = F^I + F^A, n_t = gamma~_tt, F the generalised Fock matrix)
+__global__ void k_diag_hessian(const double* __restrict__ f, const double* __restrict__ F,
+                               const double* __restrict__ gamma, int nb, int ncore, int ncas, double floor_v,
+                               double* __restrict__ H) {
+  const size_t tot = (size_t)nb * nb;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / nb), q = (int)(e % nb);
+    const bool pc = p < ncore, pa = p >= ncore && p < ncore + ncas;
+    const bool qc = q < ncore, qa = q >= ncore && q < ncore + ncas;
+    double v = 0.0;
+    bool set = false;
+    if (p > q && !pc && !(pa && qa)) {
+      if (!pa && qc) {
+        v = 4.0 * (f[p] - f[q]);
+        set = true;
+      } else if (!pa && qa) {
+        const int t = q - ncore;
+        v = 2.0 * gamma[(size_t)t * ncas + t] * f[p] - 2.0 * F[(size_t)q * nb + q];
+        set = true;
+      } else if (pa && qc) {
+        const int t = p - ncore;
+        v = 4.0 * (f[p] - f[q]) + 2.0 * gamma[(size_t)t * ncas + t] * f[q] - 2.0 * F[(size_t)p * nb + p];
+        set = true;
+      }
+    }
+    H[e] = set ? fmax(v, floor_v) : 0.0;
+  }
+}
+
 #define ST ((cudaStream_t)be_->stream())
 int grid_for(size_t n) { return (int)std::min<size_t>(152 * 16, std::max<size_t>(1, (n + 255) / 256)); }
 
@@ -289,6 +373,16 @@ void Casscf::expm_neg(const double* dK, int n, double* dR, double sign) {
     be_->copy_d2d(dR, T, (size_t)n * n * sizeof(double));
   }
   be_->sync();
+}
+
+void Casscf::matmul(const double* A, const double* B, int n, double* C) {
+  Dev d(be_);
+  const size_t nn = (size_t)n * n;
+  double* dA = d.upload(A, nn);
+  double* dB = d.upload(B, nn);
+  double* dC = d.alloc(nn);
+  gemm1(be_, dC, n, n, n, dA, n, 0, dB, n, 0, n, 1.0);
+  be_->copy_d2h(C, dC, nn * sizeof(double));
 }
 
 void Casscf::rotation(const double* K, int nb, double* R) {
@@ -485,7 +579,7 @@ void Casscf::transform_backward(const double* K, const double* R, const double* 
 
 // generalised Fock matrix F (device, nb x nb) from device integrals and RDMs
 void Casscf::fock_dev(const double* dh, const double* dL, int rank, int nb, int ncore, int ncas,
-                      const double* dg, const double* dG, double* F) {
+                      const double* dg, const double* dG, double* F, double* fdiag) {
   Dev d(be_);
   size_t nn = (size_t)nb * nb;
   int a2 = ncas * ncas;
@@ -503,7 +597,117 @@ void Casscf::fock_dev(const double* dh, const double* dL, int rank, int nb, int 
     s.push_back({W + (size_t)k * a2, dL + nn * k + ncore, ncas, ncas, nb, 0, 1, 1.0});
   be_->gemm(g, s, Precision::FP64);
   k_assemble_fock<<<grid_for(nn), 256, 0, ST>>>(f.FI, f.FA, dg, F2, nb, ncore, ncas, F);
+  if (fdiag) k_fock_diag<<<grid_for(nb), 256, 0, ST>>>(f.FI, f.FA, nb, fdiag);
   be_->sync();
+}
+
+// ---------------------------------------------------------------- DMRG-SCF step
+ScfStepper::ScfStepper(Backend* be, int nb, int ncore, int ncas, int memory, double max_step)
+    : be_(be), nb_(nb), ncore_(ncore), ncas_(ncas), memory_(std::max(0, memory)), max_step_(max_step) {
+  const size_t nn = (size_t)nb * nb;
+  auto al = [&](size_t n) {
+    double* p = (double*)be_->alloc(std::max<size_t>(n, 1) * sizeof(double));
+    be_->memset0(p, std::max<size_t>(n, 1) * sizeof(double));
+    mem_.push_back(p);
+    return p;
+  };
+  mask_ = al(nn);
+  g_ = al(nn);
+  gprev_ = al(nn);
+  xprev_ = al(nn);
+  q_ = al(nn);
+  r_ = al(nn);
+  hd_ = al(nn);
+  scal_ = al(4);
+  S_.resize(memory_);
+  Y_.resize(memory_);
+  for (int i = 0; i < memory_; ++i) {
+    S_[i] = al(nn);
+    Y_[i] = al(nn);
+  }
+  k_rotation_mask<<<grid_for(nn), 256, 0, (cudaStream_t)be_->stream()>>>(nb, ncore, ncas, mask_);
+}
+
+ScfStepper::~ScfStepper() {
+  be_->sync();
+  for (double* p : mem_) be_->free(p);
+}
+
+double ScfStepper::dot(const double* a, const double* b) {
+  be_->dots(a, 1, (size_t)nb_ * nb_, (size_t)nb_ * nb_, b, scal_);
+  double v;
+  be_->copy_d2h(&v, scal_, sizeof(double));
+  return v;
+}
+
+double ScfStepper::gradient_max(const double* g_host) {
+  const size_t nn = (size_t)nb_ * nb_;
+  be_->copy_h2d(q_, g_host, nn * sizeof(double));
+  cudaStream_t st = (cudaStream_t)be_->stream();
+  k_mul<<<grid_for(nn), 256, 0, st>>>(q_, mask_, nn, g_);
+  k_maxabs<<<1, 256, 0, st>>>(g_, nn, scal_ + 1);
+  double v;
+  be_->copy_d2h(&v, scal_ + 1, sizeof(double));
+  return v;
+}
+
+void ScfStepper::step(Casscf& cas, const double* h, const double* L, int rank, const double* gamma,
+                      const double* Gamma, double* K_host) {
+  const size_t nn = (size_t)nb_ * nb_;
+  cudaStream_t st = (cudaStream_t)be_->stream();
+  // curvature pair of the last step
+  if (have_prev_) {
+    double* y = q_;
+    be_->copy_d2d(y, g_, nn * sizeof(double));
+    be_->axpby(y, 1.0, gprev_, -1.0, nn);
+    if (dot(xprev_, y) > 1e-12 && memory_ > 0) {
+      const int slot = pairs_ % memory_;
+      be_->copy_d2d(S_[slot], xprev_, nn * sizeof(double));
+      be_->copy_d2d(Y_[slot], y, nn * sizeof(double));
+      ++pairs_;
+    }
+  }
+  // diagonal Hessian of the current orbitals
+  {
+    Casscf::Dev d(be_);
+    const int a2 = ncas_ * ncas_;
+    double* dh = d.upload(h, nn);
+    double* dL = d.upload(L, nn * rank);
+    double* dg = d.upload(gamma, (size_t)a2);
+    double* dG = d.upload(Gamma, (size_t)a2 * a2);
+    double* F = d.alloc(nn);
+    double* fd = d.alloc(nb_);
+    cas.fock_dev(dh, dL, rank, nb_, ncore_, ncas_, dg, dG, F, fd);
+    k_diag_hessian<<<grid_for(nn), 256, 0, st>>>(fd, F, dg, nb_, ncore_, ncas_, 0.05, hd_);
+    be_->sync();
+  }
+  // two-loop recursion, newest pair first
+  const int np = std::min(pairs_, memory_);
+  std::vector<double> rho(np), alpha(np);
+  be_->copy_d2d(q_, g_, nn * sizeof(double));
+  for (int k = 0; k < np; ++k) {
+    const int slot = (pairs_ - 1 - k) % memory_;
+    rho[k] = 1.0 / dot(Y_[slot], S_[slot]);
+    alpha[k] = rho[k] * dot(S_[slot], q_);
+    be_->axpby(q_, 1.0, Y_[slot], -alpha[k], nn);
+  }
+  k_div_mask<<<grid_for(nn), 256, 0, st>>>(q_, hd_, mask_, nn, r_);
+  for (int k = np - 1; k >= 0; --k) {
+    const int slot = (pairs_ - 1 - k) % memory_;
+    const double beta = rho[k] * dot(Y_[slot], r_);
+    be_->axpby(r_, 1.0, S_[slot], alpha[k] - beta, nn);
+  }
+  // x = -r, largest entry capped
+  k_maxabs<<<1, 256, 0, st>>>(r_, nn, scal_ + 2);
+  double big;
+  be_->copy_d2h(&big, scal_ + 2, sizeof(double));
+  const double sc = big > max_step_ ? -max_step_ / big : -1.0;
+  be_->axpby(r_, sc, r_, 0.0, nn);
+  be_->copy_d2d(xprev_, r_, nn * sizeof(double));
+  be_->copy_d2d(gprev_, g_, nn * sizeof(double));
+  have_prev_ = true;
+  k_antisym<<<grid_for(nn), 256, 0, st>>>(r_, nb_, q_);
+  be_->copy_d2h(K_host, q_, nn * sizeof(double));
 }
 
 }  // namespace dmrg

@@ -1,6 +1,8 @@
 // CAS-SCF device routines (orbital rotation, integral transform, active space,
 // orbital gradient).  Host arrays in and out; all arithmetic on the device.
 #pragma once
+#include <vector>
+
 #include "backend.hpp"
 
 namespace dmrg {
@@ -9,6 +11,8 @@ class Casscf {
  public:
   struct Dev;
   explicit Casscf(Backend* be);
+  // C = A B (n x n, host arrays)
+  void matmul(const double* A, const double* B, int n, double* C);
   // R = expm(-K) (U = exp(-kappa) of Sec. II.A)
   void rotation(const double* K, int nb, double* R);
   // dE/dkappa (antisymmetric) for R = expm(-K) given G = dE/dR
@@ -34,13 +38,42 @@ class Casscf {
  private:
   // device-pointer forms
   void rotation_backward_dev(const double* dK, const double* dG, int nb, double scale, double* ddK);
-  void fock_dev(const double* dh, const double* dL, int rank, int nb, int ncore, int ncas, const double* dg,
-                const double* dG, double* F);
 
  public:
+  // generalised Fock matrix F of device integrals and RDMs (device), and
+  // optionally the diagonal of F^I + F^A (fdiag, nb)
+  void fock_dev(const double* dh, const double* dL, int rank, int nb, int ncore, int ncas, const double* dg,
+                const double* dG, double* F, double* fdiag = nullptr);
 
  private:
   Backend* be_;
+};
+
+// One DMRG-SCF orbital step per macro iteration (Sec. II.A): limited-memory
+// BFGS over the non-redundant rotations with the approximate diagonal
+// Hessian as the initial inverse, largest entry capped; history on the
+// device.
+class ScfStepper {
+ public:
+  ScfStepper(Backend* be, int nb, int ncore, int ncas, int memory, double max_step);
+  ~ScfStepper();
+  // masks the gradient matrix (host, nb x nb) to the non-redundant rotations
+  // and returns its largest magnitude
+  double gradient_max(const double* g_host);
+  // the step from the gradient of the last gradient_max call: K (host, nb x nb,
+  // antisymmetric) with U <- U expm(-K)
+  void step(Casscf& cas, const double* h, const double* L, int rank, const double* gamma, const double* Gamma,
+            double* K_host);
+
+ private:
+  double dot(const double* a, const double* b);
+  Backend* be_;
+  int nb_, ncore_, ncas_, memory_;
+  double max_step_;
+  std::vector<double*> mem_, S_, Y_;
+  double *mask_, *g_, *gprev_, *xprev_, *q_, *r_, *hd_, *scal_;
+  int pairs_ = 0;
+  bool have_prev_ = false;
 };
 
 }  // namespace dmrg

@@ -55,8 +55,61 @@ void set_last_error(const std::string& e) { g_last_error = e; }
 
 // ============================================================ op sets
 OpSet::~OpSet() {
-  if (be)
+  if (!be) return;
+  if (!pending.empty()) {
+    be->stage_join();
+    release_pending();
+  }
+  if (on_host) {
+    for (void* h : host) be->host_release(h);
+    be->staged_bytes -= device_bytes();
+  } else {
     for (void* p : mem) be->free(p);
+  }
+}
+
+size_t OpSet::device_bytes() const {
+  size_t b = 0;
+  for (size_t x : mem_bytes) b += x;
+  return b;
+}
+
+void OpSet::stage_out() {
+  if (on_host || mem.empty()) return;
+  host.assign(mem.size(), nullptr);
+  for (size_t i = 0; i < mem.size(); ++i) host[i] = be->stage_out(mem[i], mem_bytes[i]);
+  on_host = true;
+}
+
+void OpSet::stage_in() {
+  if (!on_host) return;
+  // operator pointers are offsets into the allocations: rebase them
+  std::vector<double*> old(mem.size());
+  for (size_t i = 0; i < mem.size(); ++i) old[i] = (double*)mem[i];
+  std::vector<double*> fresh(mem.size());
+  for (size_t i = 0; i < mem.size(); ++i) fresh[i] = (double*)be->stage_in(host[i], mem_bytes[i]);
+  for (auto& [k, p] : ops) {
+    for (size_t i = 0; i < mem.size(); ++i) {
+      const size_t n = mem_bytes[i] / sizeof(double);
+      if (p >= old[i] && p < old[i] + n) {
+        p = fresh[i] + (p - old[i]);
+        break;
+      }
+    }
+  }
+  for (size_t i = 0; i < mem.size(); ++i) mem[i] = fresh[i];
+  // the copies are in flight on the side stream: the main stream waits for
+  // them at the next join, and the pinned copies are released after it
+  pending.insert(pending.end(), host.begin(), host.end());
+  be->staged_bytes -= device_bytes();
+  host.clear();
+  on_host = false;
+  arriving = true;
+}
+
+void OpSet::release_pending() {
+  for (void* h : pending) be->host_release(h);
+  pending.clear();
 }
 
 static Layout make_layout(const Basis& bra, const Basis& ket, int dn, int k2) {
@@ -96,6 +149,7 @@ void OpSet::allocate(const std::vector<OpKey>& keys) {
     double* p = (double*)be->alloc(bytes);
     be->memset0(p, bytes);
     mem.push_back(p);
+    mem_bytes.push_back(bytes);
     for (size_t i = 0; i < ks.size(); ++i) ops[ks[i]] = p + i * L.size;
   }
 }
@@ -2109,7 +2163,105 @@ void Engine::build_initial_right() {
   }
 }
 
+// ---- staging of stored blocks to pinned host memory (device budget)
+// Bond b uses L(b) and R(n-b-2) in both directions; in sweep steps, L->R
+// bond i is step i and R->L bond i is step (n-2) + (n-2-i), period 2n-4.
+void Engine::memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra) const {
+  size_t d = 0, h = 0, mb = 0;
+  for (auto* v : {&L_, &R_})
+    for (auto& b : *v) {
+      if (!b || !b->ops) continue;
+      const size_t x = b->ops->device_bytes();
+      (b->ops->on_host ? h : d) += x;
+      mb = std::max(mb, x);
+    }
+  if (dev) *dev = d;
+  if (host) *host = h;
+  if (max_block) *max_block = mb;
+  if (max_extra) *max_extra = max_bond_extra_;
+}
+
+int Engine::next_use(bool left, int m, int step) const {
+  const int b = left ? m : n_ - m - 2;
+  const int P = 2 * n_ - 4;
+  int best = INT32_MAX;
+  for (int s : {b <= n_ - 3 ? b : -1, (b >= 1 && b <= n_ - 2) ? (n_ - 2) + (n_ - 2 - b) : -1}) {
+    if (s < 0) continue;
+    int t = s;
+    while (t < step) t += P;
+    best = std::min(best, t);
+  }
+  return best;
+}
+
+void Engine::resident(Block* b) {
+  if (!b || !b->ops) return;
+  if (b->ops->on_host) b->ops->stage_in();
+  if (b->ops->arriving) {
+    be_->stage_join();
+    b->ops->arriving = false;
+  }
+}
+
+// Before the bond of `step`: its two blocks on the device; when the stored
+// blocks plus the bond's own working memory (measured at the previous bond)
+// would exceed the budget, the blocks whose next use is farthest away are
+// staged out; the blocks of the next step are brought back ahead of time.
+void Engine::stage_for_step(int step) {
+  const size_t budget = be_->budget();
+  auto bond_of = [&](int s) {
+    const int P = 2 * n_ - 4;
+    s %= P;
+    return s <= n_ - 3 ? s : (n_ - 2) - (s - (n_ - 2));
+  };
+  auto blocks_of = [&](int s, Block** lb, Block** rb) {
+    const int b = bond_of(s);
+    *lb = (b >= 0 && b < (int)L_.size()) ? L_[b].get() : nullptr;
+    *rb = (n_ - b - 2 >= 0 && n_ - b - 2 < (int)R_.size()) ? R_[n_ - b - 2].get() : nullptr;
+  };
+  Block *l0, *r0, *l1, *r1;
+  blocks_of(step, &l0, &r0);
+  blocks_of(step + 1, &l1, &r1);
+  resident(l0);
+  resident(r0);
+  for (auto* v : {&L_, &R_})
+    for (auto& b : *v)
+      if (b && b->ops && !b->ops->pending.empty() && !b->ops->arriving) b->ops->release_pending();
+  if (budget == 0) return;
+  const size_t need = bond_extra_ + bond_extra_ / 10;
+  if (be_->bytes_in_use() + need > budget) {
+    struct Cand {
+      int next;
+      Block* b;
+    };
+    std::vector<Cand> c;
+    for (int side = 0; side < 2; ++side) {
+      auto& v = side == 0 ? L_ : R_;
+      for (int m = 0; m < (int)v.size(); ++m) {
+        Block* b = v[m].get();
+        if (!b || !b->ops || b->ops->on_host || b == l0 || b == r0 || b == l1 || b == r1) continue;
+        if (b->ops->mem.empty()) continue;
+        c.push_back({next_use(side == 0, m, step), b});
+      }
+    }
+    std::stable_sort(c.begin(), c.end(), [](const Cand& a, const Cand& b) { return a.next > b.next; });
+    for (const Cand& x : c) {
+      if (be_->bytes_in_use() + need <= budget) break;
+      x.b->ops->stage_out();
+    }
+    // kept enlarged blocks are a cache: dropped (rebuilt when needed) rather
+    // than staged
+    if (be_->bytes_in_use() + need > budget) drop_kept();
+  }
+  // prefetch the next step's blocks
+  for (Block* b : {l1, r1})
+    if (b && b->ops && b->ops->on_host) b->ops->stage_in();
+}
+
 double Engine::optimize_bond(int i, bool l2r, double* trunc) {
+  stage_for_step(step_of(i, l2r));
+  const size_t bond_start = be_->bytes_in_use();
+  be_->window_peak = bond_start;
   double t0 = now_s();
   // the environment side may have been enlarged at this bond on the way here
   auto take = [](std::vector<std::unique_ptr<Block>>& keep, int b) {
@@ -2195,6 +2347,8 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   if (plan.dev) be_->free(plan.dev);
   if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
+  bond_extra_ = be_->window_peak > bond_start ? be_->window_peak - bond_start : 0;
+  max_bond_extra_ = std::max(max_bond_extra_, bond_extra_);
   size_t enl_bytes = 0;
   int enl_maxsec = 0;
   if (opt_.verbose) {
@@ -2205,7 +2359,8 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
       for (auto& sc : tb->ops->basis.sec) enl_maxsec = std::max(enl_maxsec, sc.dim);
   }
   // keep this bond's system-side enlarged block for the way back
-  if ((double)be_->bytes_in_use() <= kKeepFraction * (double)be_->capacity() &&
+  const double cap = be_->budget() ? (double)std::min(be_->budget(), be_->capacity()) : (double)be_->capacity();
+  if ((double)be_->bytes_in_use() <= kKeepFraction * cap &&
       (double)be_->device_free() >= kKeepFreeFraction * (double)be_->capacity()) {
     auto& keep = l2r ? keep_L_ : keep_R_;
     if ((int)keep.size() < n_) keep.resize(n_);
@@ -2264,6 +2419,8 @@ SweepStats Engine::sweep_part(bool l2r, int last) {
 Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls) {
   if (bond < 0 || bond > n_ - 2) throw std::invalid_argument("bond out of range");
   if (!L_[bond] || !R_[n_ - bond - 2]) throw std::runtime_error("state: the blocks of this bond are not held");
+  resident(L_[bond].get());
+  resident(R_[n_ - bond - 2].get());
   BondSolve out;
   // the side that was enlarged on the way here may be kept
   std::unique_ptr<Block> Le, Re;
@@ -3016,6 +3173,7 @@ void Engine::rdm12(double* gamma, double* Gamma) {
     };
     add_identity(*Lb);
     auto Le = enlarge(*Lb, 1);
+    resident(R_[n - 3].get());
     auto Re = enlarge(*R_[n - 3], 2);
     PsiLayout P = make_psi(Le->ops->basis, Re->ops->basis, n_elec_, two_s_);
     if (P.size != prev_.len) throw std::runtime_error("internal: RDM pass layout differs from the state");
@@ -3023,6 +3181,7 @@ void Engine::rdm12(double* gamma, double* Gamma) {
     owned.push_back(psi);
     be_->copy_d2d(psi, prev_.psi, P.size * sizeof(double));
     for (int i = 1; i <= n - 2; ++i) {
+      resident(R_[n - i - 2].get());
       rdm_bond(i, *Lb, *Le, *Re, *R_[n - i - 2], P, psi, at[i], acc);
       if (i == n - 2) break;
       // move the state to bond i+1, keeping its whole support
@@ -3033,6 +3192,7 @@ void Engine::rdm12(double* gamma, double* Gamma) {
       auto Lnext = renormalize(*Le, *U, false);
       add_identity(*Lnext);
       auto Le2 = enlarge(*Lnext, i + 1);
+      resident(R_[n - i - 3].get());
       auto Re2 = enlarge(*R_[n - i - 3], i + 2);
       PsiLayout P2 = make_psi(Le2->ops->basis, Re2->ops->basis, n_elec_, two_s_);
       Prev from;

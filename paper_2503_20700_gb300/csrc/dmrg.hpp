@@ -107,6 +107,19 @@ struct OpSet {
   // allocate (zeroed) storage for the given keys
   void allocate(const std::vector<OpKey>& keys);
   size_t bytes() const;
+  // Staging of the operator storage to pinned host memory (renormalised
+  // blocks that the sweep does not need for a while, when the device budget
+  // is tight): every allocation is copied out on the backend's side stream
+  // and freed; stage_in brings it back and rebases the operator pointers.
+  std::vector<size_t> mem_bytes;  // size of each allocation of mem
+  std::vector<void*> host;        // pinned copies while staged out
+  std::vector<void*> pending;     // pinned copies whose copy back may still run
+  bool on_host = false;
+  bool arriving = false;          // staged in; the main stream has not joined yet
+  size_t device_bytes() const;
+  void stage_out();
+  void stage_in();
+  void release_pending();
 };
 
 struct Block {
@@ -230,6 +243,9 @@ class Engine {
   void rdm12(double* gamma, double* Gamma);
 
   Backend* backend() const { return be_; }
+  // device and pinned-host bytes of the stored blocks, the largest one, and
+  // the largest working memory of a bond beyond the stored blocks so far
+  void memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra) const;
 
  private:
   friend struct EngineAccess;
@@ -252,6 +268,12 @@ class Engine {
     keep_R_.clear();
   }
   int tL_, tR_;
+  // staging policy (hbm budget): the sweep step of each block's next use and
+  // the memory a bond needs beyond the stored blocks (from the last bond)
+  size_t bond_extra_ = 0, max_bond_extra_ = 0;
+  void stage_for_step(int step);
+  int next_use(bool left, int m, int step) const;
+  void resident(Block* b);  // operators on the device and joined
   double energy_ = 0.0;
   std::vector<double> bond_e_;
   int last_bond_ = -1;
@@ -300,6 +322,7 @@ class Engine {
   std::unique_ptr<SavedU> decimate(Block& enl, const struct HPsiPlan& plan, const double* psi,
                                    bool left, double* trunc);
   double optimize_bond(int i, bool left_to_right, double* trunc);
+  int step_of(int i, bool l2r) const { return l2r ? i : (n_ - 2) + (n_ - 2 - i); }
   void guess(int bond, bool l2r, const Block& Le, const Block& Re, const struct HPsiPlan& plan,
              double* psi);
   void save_prev(int bond, const Block& Le, const Block& Re, const struct HPsiPlan& plan,

@@ -160,6 +160,11 @@ def eigh_batched(mats, device=0):
 
 
 # ---------------------------------------------------------------- CAS-SCF
+class ScfOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("e_tol", ctypes.c_double), ("g_tol", ctypes.c_double),
+                ("memory", ctypes.c_int), ("max_step", ctypes.c_double), ("sweeps", ctypes.c_int)]
+
+
 def _bind_casscf(lib):
     dp = ctypes.POINTER(ctypes.c_double)
     I = ctypes.c_int
@@ -169,6 +174,12 @@ def _bind_casscf(lib):
     lib.casscf_active_space.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, I]
     lib.casscf_orbital_gradient.argtypes = [dp, dp, I, I, I, I, dp, dp, dp, dp, I]
     lib.casscf_transform_backward.argtypes = [dp, dp, dp, dp, I, I, I, I, ctypes.c_double, dp, dp, dp, I]
+    from . import Opts
+    lib.casscf_default_scf_opts.argtypes = [ctypes.POINTER(ScfOpts)]
+    lib.casscf_default_scf_opts.restype = None
+    lib.casscf_dmrg_scf.argtypes = [dp, dp, I, I, I, I, I, I, ctypes.POINTER(Opts), ctypes.POINTER(ScfOpts),
+                                    dp, dp, dp, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.casscf_dmrg_scf.restype = I
     for f in ("casscf_rotation", "casscf_rotation_backward", "casscf_transform",
               "casscf_active_space", "casscf_orbital_gradient", "casscf_transform_backward"):
         getattr(lib, f).restype = I
@@ -238,3 +249,29 @@ def transform_backward(K, R, h_rot, L_rot, ncore, ncas, g_core, g_h, g_eri, devi
     _call("casscf_transform_backward", _dp(K), _dp(R), _dp(h_rot), _dp(L_rot), L_rot.shape[0], K.shape[0],
           ncore, ncas, float(g_core), _dp(g_h), _dp(g_eri), _dp(dK), device)
     return dK
+
+
+def dmrg_scf(h, L, ncore, ncas, n_elec, two_s=0, D=64, tol=1e-10, precision=0, sweeps=4, max_iter=60,
+             e_tol=1e-7, g_tol=1e-3, memory=8, max_step=0.5, device=0):
+    """DMRG-SCF macro iterations (casscf_dmrg_scf); returns (energies, max |g|
+    per iteration, U, converged)."""
+    from . import load, Opts, DmrgError
+    lib = load()
+    h, L = _c(h), _c(L)
+    nb = h.shape[0]
+    o = Opts()
+    lib.dmrg_default_opts(ctypes.byref(o))
+    o.D, o.davidson_tol, o.precision, o.device = D, tol, precision, device
+    so = ScfOpts()
+    lib.casscf_default_scf_opts(ctypes.byref(so))
+    so.max_iter, so.e_tol, so.g_tol, so.memory, so.max_step, so.sweeps = (max_iter, e_tol, g_tol, memory,
+                                                                          max_step, sweeps)
+    U = np.zeros((nb, nb))
+    es = np.zeros(max_iter)
+    gs = np.zeros(max_iter)
+    nit, conv = ctypes.c_int(), ctypes.c_int()
+    st = lib.casscf_dmrg_scf(_dp(h), _dp(L), L.shape[0], nb, ncore, ncas, n_elec, two_s, ctypes.byref(o),
+                             ctypes.byref(so), _dp(U), _dp(es), _dp(gs), ctypes.byref(nit), ctypes.byref(conv))
+    if st != 0:
+        raise DmrgError(st, lib.dmrg_last_error(None).decode())
+    return es[:nit.value].tolist(), gs[:nit.value].tolist(), U, bool(conv.value)

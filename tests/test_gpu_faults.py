@@ -124,3 +124,25 @@ def test_debug_bounds_checks_plans_without_changing_results(pkg):
     a.close()
     b.close()
     assert ea == eb
+
+
+def test_budget_stages_blocks_to_pinned_host_memory_bit_identically(pkg):
+    """A device budget below the unbudgeted high-water mark: stored blocks go
+    to pinned host memory on the side stream and come back ahead of their
+    bond; the energies are bit-identical to the unbudgeted run."""
+    h, eri, ec = W.ppp_acene(5)
+    ref = pkg.DMRG(h, eri=eri, n_elec=22, D=96, e_core=ec)
+    e_ref = [ref.sweep()[0] for _ in range(2)]
+    md = ref.memory_detail()
+    _, peak = ref.memory()
+    ref.close()
+    budget = md["max_bond_extra"] + 5 * md["max_block"] + (64 << 20)
+    assert budget < peak
+    g = pkg.DMRG(h, eri=eri, n_elec=22, D=96, e_core=ec, hbm_budget_bytes=budget)
+    e = [g.sweep()[0] for _ in range(2)]
+    st = g.memory_detail()
+    _, peak_b = g.memory()
+    g.close()
+    assert e == e_ref
+    assert st["staged_out"] > 0 and st["staged_in"] > 0
+    assert peak_b <= budget

@@ -327,3 +327,43 @@ def test_transform_preserves_energy_under_active_rotation():
     e0 = C.casscf_energy(h, L, nc, na, g, G)
     e1 = C.casscf_energy(h, L, nc, na, g2, G2, K=K)
     assert e1 == pytest.approx(e0, abs=1e-10)
+
+
+# ---------------------------------------------------------------- DMRG-SCF
+def _fci_solver(n_elec, two_s=0):
+    def solve(h_act, eri_act, e_core):
+        e, x, H = fci(h_act, eri_act, n_elec, two_s, e_core=e_core)
+        g, G = rdm12(H.ops, x)
+        return e, g, G
+    return solve
+
+
+def test_dmrg_scf_converges_to_a_minimum_of_the_cas_energy():
+    """The macro loop (exact CI in the active space) reaches the paper's
+    thresholds, lowers the energy, and ends at a local minimum: a direct
+    minimisation of the CAS-CI energy over the non-redundant rotations from
+    the final orbitals finds nothing lower."""
+    import scipy.optimize
+    h, L = W.cholesky_random(7, 14, seed=5, sigma_h=0.2)
+    nc, na, ne = 1, 4, 4
+    es, gs, U = C.dmrg_scf(h, L, nc, na, _fci_solver(ne))
+    assert gs[-1] < 1e-3 and abs(es[-1] - es[-2]) < 1e-7
+    assert es[-1] < es[0]
+    assert np.allclose(U.T @ U, np.eye(7), atol=1e-12)
+    h2, L2 = C.transform(h, L, U)
+    mask = C.rotation_mask(7, nc, na)
+    idx = np.argwhere(mask > 0)
+
+    def cas_energy(x):
+        K = np.zeros((7, 7))
+        K[idx[:, 0], idx[:, 1]] = x
+        h3, L3 = C.transform(h2, L2, C.rotation_matrix(K - K.T))
+        fi = C.inactive_fock(h3, L3, nc)
+        a = slice(nc, nc + na)
+        e_core = float(np.trace(h3[:nc, :nc]) + np.trace(fi[:nc, :nc]))
+        eri = np.einsum("ktu,kvw->tuvw", L3[:, a, a], L3[:, a, a])
+        return fci(fi[a, a], eri, ne, 0, e_core=e_core)[0]
+
+    assert cas_energy(np.zeros(len(idx))) == pytest.approx(es[-1], abs=1e-9)
+    res = scipy.optimize.minimize(cas_energy, np.zeros(len(idx)), method="BFGS", options={"gtol": 1e-6})
+    assert res.fun > es[-1] - 1e-6
