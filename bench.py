@@ -350,14 +350,14 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     t_app = time.perf_counter() - t_app0
     left, right = g.block_dims()
     # warm-up products at the middle bond
-    g.bond_solve(mid, 1, prec, max_iter=max(1, W - 1), tol=args.tol, min_calls=W)
+    g.bond_solve(mid, 1, prec, max_iter=max(1, W - 1), tol=args.tol, min_calls=W, check64=False)
     # ---- timed region: K products inside the Davidson solve of the middle bond
     barrier(dist)
     g.profile(True)
     l0 = g.launch_count()
     with Clocks(device) as clk:
         t0 = time.perf_counter()
-        res = g.bond_solve(mid, 1, prec, max_iter=max(1, K - 1), tol=args.tol, min_calls=K)
+        res = g.bond_solve(mid, 1, prec, max_iter=max(1, K - 1), tol=args.tol, min_calls=K, check64=False)
         wall = time.perf_counter() - t0
     launches = g.launch_count() - l0
     k_ms, k_launch = res["contraction_ms"], res["contraction_launches"]
@@ -371,19 +371,21 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     t_max = allmax(dist, dev_s)
     flops_all = allsum(dist, res["calls"] * res["flops_per_call"])
     value = flops_all / t_max / 1e12
-    # ---- FP64 arm: float64 products at the same bond from the same vector
+    # ---- FP64 arm: one float64 product at the same bond on the split
+    # result's vector; it also gives the float64 Rayleigh quotient and residual
     fp64 = None
-    if args.fp64_calls > 0 and prec != pkg.FP64:
-        r64 = g.bond_solve(mid, 1, pkg.FP64, max_iter=max(1, args.fp64_calls - 1), tol=args.tol,
-                           min_calls=args.fp64_calls)
-        v64 = r64["calls"] * r64["flops_per_call"] / (r64["ms_total"] / 1000.0) / 1e12
-        fp64 = {"value": v64, "unit": "TFLOP/s", "calls": r64["calls"],
-                "ms_per_call": r64["ms_total"] / max(1, r64["calls"]), "speedup_split_over_fp64": value / v64}
+    chk = g.bond_check64()
+    res["energy_rq64"], res["residual64"] = chk["energy_rq64"], chk["residual64"]
+    if prec != pkg.FP64:
+        v64 = chk["flops"] / (chk["ms"] / 1000.0) / 1e12
+        fp64 = {"value": v64, "unit": "TFLOP/s", "calls": 1, "ms_per_call": chk["ms"],
+                "speedup_split_over_fp64": value / v64, "kernel": "hpsi_f64_kernel"}
         if args.fp64_converge:
+            e_split_rq = res["energy_rq64"]
             rc = g.bond_solve(mid, 1, pkg.FP64, max_iter=200, tol=args.tol, min_calls=0)
             fp64["converged"] = {"energy": rc["energy_rq64"], "residual64": rc["residual64"],
                                  "iterations": rc["iterations"],
-                                 "delta_e_split_minus_fp64": res["energy_rq64"] - rc["energy_rq64"]}
+                                 "delta_e_split_minus_fp64": e_split_rq - rc["energy_rq64"]}
     mem_now, mem_peak = g.memory()
     _ = g.energy()
     t_job = allmax(dist, time.perf_counter() - t_job0)
@@ -544,7 +546,6 @@ def main():
                     help="--mode bond: sweeps before the target D, as D:davidson_iters,...")
     ap.add_argument("--approach-iters", type=int, default=2,
                     help="--mode bond: Davidson cap of the half-sweeps at the target D")
-    ap.add_argument("--fp64-calls", type=int, default=2, help="--mode bond: float64 products timed (0: none)")
     ap.add_argument("--fp64-converge", action="store_true",
                     help="--mode bond: also converge the float64 Davidson at the bond (slow at large D)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -93,6 +93,12 @@ typedef struct {
                              only the sweep energy) is the float64 Rayleigh
                              quotient of its eigenvector (one float64 H_eff psi
                              per bond)                                        */
+  int tc_drain_terms;     /* DMRG_SPLIT_HPSI_TC: FP32 accumulation length of the
+                             tcgen05 contraction's sigma tile between drains
+                             into its float-pair partial tile, in terms of
+                             psi's column index (sum of kb over items; 0:
+                             after every item; default 256) -- shorter is more
+                             accurate and slower                              */
 } dmrg_opts;
 
 /* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24,
@@ -183,7 +189,20 @@ typedef struct {
  * DMRG_ESTATE when the blocks of `bond` are not held.
  */
 dmrg_status dmrg_bond_solve(dmrg_ctx* ctx, int bond, int direction, int precision, int max_iter,
-                            double tol, int min_calls, dmrg_bond_result* out, double* call_ms, int cap);
+                            double tol, int min_calls, int check64, dmrg_bond_result* out,
+                            double* call_ms, int cap);
+
+/*
+ * dmrg_bond_check64 -- the float64 Rayleigh quotient (+ e_core) and
+ * residual ||H_eff psi - E psi|| (||psi|| = 1) of the vector of the last
+ * dmrg_bond_solve, from one float64 H_eff psi on the same blocks; *ms its
+ * CUDA-event time and *flops its algorithmic FLOPs.  dmrg_bond_solve with
+ * check64 = 1 runs it and fills energy_rq64 / residual64 (0 otherwise).
+ * DMRG_ESTATE without a bond solve since the last sweep.  Any NULL output is
+ * skipped.
+ */
+dmrg_status dmrg_bond_check64(dmrg_ctx* ctx, double* energy_rq64, double* residual64, double* ms,
+                              double* flops);
 
 /* Change the Davidson iteration cap (per bond) and residual tolerance used
  * by subsequent sweeps (Sec. II.D).  A bond that reaches the cap keeps its
@@ -200,6 +219,10 @@ dmrg_status dmrg_set_wait_timeout(dmrg_ctx* ctx, double seconds);
  * (dmrg_hpsi_contract, dmrg_eigh_batched and the CAS-SCF routines) called
  * after it; default 2 s. */
 dmrg_status dmrg_set_kernel_wait_timeout(double seconds);
+
+/* tc_drain_terms (see dmrg_opts) of the kernel-level dmrg_hpsi_contract,
+ * process-wide; default 256. */
+dmrg_status dmrg_set_kernel_tc_drain_terms(int terms);
 
 /* Change the bond dimension used by subsequent sweeps. */
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* ctx, int D);

@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("debug_bounds", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("wait_timeout_s", ctypes.c_double),
                 ("trunc_target", ctypes.c_double), ("D_min", ctypes.c_int),
-                ("rq64_every_bond", ctypes.c_int)]
+                ("rq64_every_bond", ctypes.c_int), ("tc_drain_terms", ctypes.c_int)]
 
 
 class BondResult(ctypes.Structure):
@@ -77,10 +77,14 @@ def load(path=None):
     lib.dmrg_sweep.restype = I
     lib.dmrg_sweep_part.argtypes = [P, I, I, dp, dp]
     lib.dmrg_sweep_part.restype = I
-    lib.dmrg_bond_solve.argtypes = [P, I, I, I, I, D, I, ctypes.POINTER(BondResult), dp, I]
+    lib.dmrg_bond_solve.argtypes = [P, I, I, I, I, D, I, I, ctypes.POINTER(BondResult), dp, I]
     lib.dmrg_bond_solve.restype = I
+    lib.dmrg_bond_check64.argtypes = [P, dp, dp, dp, dp]
+    lib.dmrg_bond_check64.restype = I
     lib.dmrg_set_wait_timeout.argtypes = [P, D]
     lib.dmrg_set_wait_timeout.restype = I
+    lib.dmrg_set_kernel_tc_drain_terms.argtypes = [I]
+    lib.dmrg_set_kernel_tc_drain_terms.restype = I
     lib.dmrg_set_kernel_wait_timeout.argtypes = [D]
     lib.dmrg_set_kernel_wait_timeout.restype = I
     lib.dmrg_set_davidson.argtypes = [P, I, D]
@@ -127,6 +131,12 @@ def _dp(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def set_kernel_tc_drain_terms(terms):
+    """FP32 accumulation length of the kernel-level tcgen05 contraction (process-wide)."""
+    lib = load()
+    _check(lib, None, lib.dmrg_set_kernel_tc_drain_terms(int(terms)))
+
+
 def set_kernel_wait_timeout(seconds):
     """Bound of the device waits of the kernel-level entry points (process-wide)."""
     lib = load()
@@ -151,7 +161,7 @@ class DMRG:
                  tol=1e-10, precision=FP64, max_iter=200, max_space=24, verbose=0,
                  device=0, occ=None, two_s_right=None, strict_convergence=False,
                  debug_bounds=False, seed=0, hbm_budget_bytes=0, wait_timeout_s=None,
-                 trunc_target=0.0, D_min=1, rq64_every_bond=False):
+                 trunc_target=0.0, D_min=1, rq64_every_bond=False, tc_drain_terms=None):
         lib = load()
         self._lib = lib
         h = np.ascontiguousarray(h, dtype=np.float64)
@@ -171,6 +181,8 @@ class DMRG:
             o.wait_timeout_s = float(wait_timeout_s)
         o.trunc_target, o.D_min = float(trunc_target), int(D_min)
         o.rq64_every_bond = int(bool(rq64_every_bond))
+        if tc_drain_terms is not None:
+            o.tc_drain_terms = int(tc_drain_terms)
         occ_a = None if occ is None else np.ascontiguousarray(occ, dtype=np.int32)
         path_a = None if two_s_right is None else np.ascontiguousarray(two_s_right, dtype=np.int32)
         ctx = ctypes.c_void_p()
@@ -197,7 +209,7 @@ class DMRG:
                                                               ctypes.byref(e), ctypes.byref(t)))
         return e.value, t.value
 
-    def bond_solve(self, bond, direction, precision, max_iter=200, tol=1e-7, min_calls=0):
+    def bond_solve(self, bond, direction, precision, max_iter=200, tol=1e-7, min_calls=0, check64=True):
         """Davidson at `bond` on the held blocks (dmrg_bond_solve); returns a
         dict of the result and the CUDA-event time of every product."""
         r = BondResult()
@@ -205,10 +217,18 @@ class DMRG:
         ms = np.zeros(cap)
         _check(self._lib, self._ctx, self._lib.dmrg_bond_solve(
             self._ctx, int(bond), int(direction), int(precision), int(max_iter), float(tol), int(min_calls),
-            ctypes.byref(r), _dp(ms), cap))
+            int(bool(check64)), ctypes.byref(r), _dp(ms), cap))
         out = {k: getattr(r, k) for k, _ in BondResult._fields_}
         out["call_ms"] = ms[:min(cap, r.calls)].tolist()
         return out
+
+    def bond_check64(self):
+        """float64 Rayleigh quotient, residual, time (ms) and FLOPs of one
+        float64 H_eff psi on the vector of the last bond_solve."""
+        e, r, ms, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib, self._ctx, self._lib.dmrg_bond_check64(self._ctx, ctypes.byref(e), ctypes.byref(r),
+                                                                ctypes.byref(ms), ctypes.byref(fl)))
+        return {"energy_rq64": e.value, "residual64": r.value, "ms": ms.value, "flops": fl.value}
 
     def set_wait_timeout(self, seconds):
         _check(self._lib, self._ctx, self._lib.dmrg_set_wait_timeout(self._ctx, float(seconds)))

@@ -30,6 +30,7 @@ struct dmrg_ctx {
 namespace {
 // wait bound of the kernel-level entry points (dmrg_set_kernel_wait_timeout)
 std::atomic<unsigned long long> g_kernel_wait_ns{2000000000ull};
+std::atomic<int> g_kernel_drain_terms{dmrg::kTcDrainTerms};
 thread_local std::string tl_err;
 thread_local double tl_contract_ms = 0.0;
 
@@ -132,6 +133,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->trunc_target = 0.0;
   o->D_min = 1;
   o->rq64_every_bond = 0;
+  o->tc_drain_terms = dmrg::kTcDrainTerms;
 }
 
 dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const double* chol,
@@ -153,6 +155,7 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     return fail(nullptr, DMRG_EINVAL, "bad options");
   if (!(o.wait_timeout_s >= 0.0) || o.wait_timeout_s > 3600.0)
     return fail(nullptr, DMRG_EINVAL, "wait_timeout_s must be in [0, 3600]");
+  if (o.tc_drain_terms < 0) return fail(nullptr, DMRG_EINVAL, "tc_drain_terms < 0");
   if (!(o.trunc_target >= 0.0) || o.trunc_target >= 1.0 || o.D_min < 1 || o.D_min > o.D)
     return fail(nullptr, DMRG_EINVAL, "trunc_target must be in [0, 1) and 1 <= D_min <= D");
   if (!sweep_precision_ok(o.precision)) return fail(nullptr, DMRG_EINVAL, "unsupported precision");
@@ -209,6 +212,7 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     eo.trunc_target = o.trunc_target;
     eo.D_min = o.D_min;
     eo.rq64_every_bond = o.rq64_every_bond != 0;
+    eo.tc_drain_terms = o.tc_drain_terms;
     ctx->strict = o.strict_convergence != 0;
     ctx->eng = std::make_unique<dmrg::Engine>(ctx->be.get(), n, h, g, e_core, n_elec, two_s, eo,
                                               oc.data(), path.data());
@@ -258,8 +262,19 @@ dmrg_status dmrg_sweep_part(dmrg_ctx* c, int direction, int last_bond, double* e
   return DMRG_OK;
 }
 
+dmrg_status dmrg_bond_check64(dmrg_ctx* c, double* energy_rq64, double* residual64, double* ms,
+                              double* flops) {
+  if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
+  try {
+    c->eng->check_bond64(energy_rq64, residual64, ms, flops);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision, int max_iter, double tol,
-                            int min_calls, dmrg_bond_result* out, double* call_ms, int cap) {
+                            int min_calls, int check64, dmrg_bond_result* out, double* call_ms, int cap) {
   if (!c || !c->eng || !out) return fail(c, DMRG_EINVAL, "invalid argument");
   if (direction != 0 && direction != 1) return fail(c, DMRG_EINVAL, "direction must be 0 (L->R) or 1 (R->L)");
   if (!sweep_precision_ok(precision) || precision == DMRG_SPLIT_TF32)
@@ -269,7 +284,8 @@ dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision,
   try {
     dmrg::Precision ph, pr;
     map_precision(precision, &ph, &pr);
-    dmrg::Engine::BondSolve r = c->eng->solve_bond(bond, direction == 0, ph, max_iter, tol, min_calls);
+    dmrg::Engine::BondSolve r = c->eng->solve_bond(bond, direction == 0, ph, max_iter, tol, min_calls,
+                                                   check64 != 0);
     out->energy = r.energy;
     out->energy_rq64 = r.energy_rq64;
     out->residual64 = r.residual64;
@@ -302,6 +318,12 @@ dmrg_status dmrg_set_wait_timeout(dmrg_ctx* c, double seconds) {
   if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
   if (!(seconds >= 0.0) || seconds > 3600.0) return fail(c, DMRG_EINVAL, "seconds must be in [0, 3600]");
   c->be->set_wait_ns((unsigned long long)(seconds * 1e9));
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_kernel_tc_drain_terms(int terms) {
+  if (terms < 0) return fail(nullptr, DMRG_EINVAL, "terms < 0");
+  g_kernel_drain_terms.store(terms);
   return DMRG_OK;
 }
 
@@ -659,6 +681,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
       L.scratch = (double*)(d + os);
       L.pool = pool;
       L.units = tp.units;
+      L.drain_terms = g_kernel_drain_terms.load();
       be->hpsi_tc(L, fl);
     } else {
       be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),

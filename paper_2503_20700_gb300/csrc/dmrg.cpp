@@ -476,6 +476,7 @@ struct GemmBuilder {
 }  // namespace
 
 Engine::~Engine() {
+  if (solve_psi_ && be_) be_->free(solve_psi_);
   if (prev_.psi && be_) be_->free(prev_.psi);
   if (ones_ && be_) be_->free(ones_);
 }
@@ -1529,6 +1530,7 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
     plan.tc.scratch = (double*)(d + os);
     plan.tc.pool = plan.tc_pool;
     plan.tc.units = tp.units;
+    plan.tc.drain_terms = opt_.tc_drain_terms;
   }
   if (!tp.op_jobs.empty()) {
     // operator blocks (and identities) are constant during Davidson: split them once
@@ -2386,7 +2388,17 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   return e;
 }
 
+void Engine::end_bond_solves() {
+  if (solve_bond_ < 0) return;
+  // the enlarged blocks kept by bond solves are not those a sweep keeps
+  drop_kept();
+  if (solve_psi_) be_->free(solve_psi_);
+  solve_psi_ = nullptr;
+  solve_bond_ = -1;
+}
+
 SweepStats Engine::sweep_part(bool l2r, int last) {
+  end_bond_solves();
   stats_ = SweepStats();
   auto t0 = std::chrono::steady_clock::now();
   be_->mark_begin();
@@ -2416,16 +2428,25 @@ SweepStats Engine::sweep_part(bool l2r, int last) {
   return stats_;
 }
 
-Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls) {
+Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls,
+                                     bool check64) {
   if (bond < 0 || bond > n_ - 2) throw std::invalid_argument("bond out of range");
   if (!L_[bond] || !R_[n_ - bond - 2]) throw std::runtime_error("state: the blocks of this bond are not held");
   resident(L_[bond].get());
   resident(R_[n_ - bond - 2].get());
   BondSolve out;
-  // the side that was enlarged on the way here may be kept
+  // the side that was enlarged on the way here may be kept; other kept
+  // enlarged blocks are released
   std::unique_ptr<Block> Le, Re;
   if (!l2r && bond < (int)keep_L_.size() && keep_L_[bond]) Le = std::move(keep_L_[bond]);
   if (l2r && bond < (int)keep_R_.size() && keep_R_[bond]) Re = std::move(keep_R_[bond]);
+  if (l2r && bond < (int)keep_L_.size() && keep_L_[bond]) Le = std::move(keep_L_[bond]);
+  if (!l2r && bond < (int)keep_R_.size() && keep_R_[bond]) Re = std::move(keep_R_[bond]);
+  drop_kept();
+  if (solve_psi_) {
+    be_->free(solve_psi_);
+    solve_psi_ = nullptr;
+  }
   if (!Le) Le = enlarge(*L_[bond], bond);
   if (!Re) Re = enlarge(*R_[n_ - bond - 2], bond + 1);
   HPsiPlan plan;
@@ -2467,6 +2488,11 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
     throw;
   }
   call_ms_ = nullptr;
+  // the tcgen05 operand pool is not needed past the products
+  if (plan.tc_pool) {
+    be_->free(plan.tc_pool);
+    plan.tc_pool = nullptr;
+  }
   {
     double c1 = 0.0, s1 = 0.0;
     long l1 = 0;
@@ -2479,16 +2505,52 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
   out.gap = last_gap_;
   out.flops_per_call = plan.flops;
   opt_ = keep;
-  // float64 Rayleigh quotient and residual of the vector
+  out.energy = e + e_core_;
+  out.iterations = its;
+  out.calls = (int)ms.size();
+  out.call_ms = std::move(ms);
+  out.dim = len;
+  be_->free(plan.in);
+  be_->free(plan.out);
+  if (plan.dev) be_->free(plan.dev);
+  if (plan.diag) be_->free(plan.diag);
+  // both enlarged blocks stay for the next call at this bond, and the vector
+  // for check_bond64
+  if ((int)keep_L_.size() < n_) keep_L_.resize(n_);
+  if ((int)keep_R_.size() < n_) keep_R_.resize(n_);
+  keep_L_[bond] = std::move(Le);
+  keep_R_[bond] = std::move(Re);
+  solve_psi_ = psi;
+  solve_bond_ = bond;
+  solve_l2r_ = l2r;
+  if (check64) {
+    double ms64 = 0.0, fl = 0.0;
+    check_bond64(&out.energy_rq64, &out.residual64, &ms64, &fl);
+  }
+  return out;
+}
+
+void Engine::check_bond64(double* energy_rq64, double* residual64, double* ms, double* flops) {
+  const int bond = solve_bond_;
+  if (!solve_psi_ || bond < 0 || bond >= (int)keep_L_.size() || !keep_L_[bond] || bond >= (int)keep_R_.size() ||
+      !keep_R_[bond])
+    throw std::runtime_error("state: no bond solve to check");
+  Block& Le = *keep_L_[bond];
+  Block& Re = *keep_R_[bond];
   HPsiPlan p64;
-  p64.in = plan.in;
-  p64.out = plan.out;
+  p64.psi = make_psi(Le.ops->basis, Re.ops->basis, n_elec_, two_s_);
+  const size_t len = p64.psi.size;
+  p64.in = (double*)be_->alloc(len * sizeof(double));
+  p64.out = (double*)be_->alloc(len * sizeof(double));
   const Precision kp = opt_.prec;
   opt_.prec = Precision::FP64;
-  plan_hpsi(*Le, *Re, p64);
+  plan_hpsi(Le, Re, p64);
   opt_.prec = kp;
+  const double* psi = solve_psi_;
   be_->copy_d2d(p64.in, psi, len * sizeof(double));
+  be_->mark_begin();
   apply_hpsi(p64);
+  const double t = be_->mark_end();
   double* d3 = (double*)be_->alloc(3 * sizeof(double));
   be_->dots(psi, 1, len, len, p64.out, d3);
   be_->dots(psi, 1, len, len, psi, d3 + 1);
@@ -2502,33 +2564,18 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
   be_->copy_d2h(&r2, d3 + 2, sizeof(double));
   be_->sync();
   be_->free(d3);
+  be_->free(p64.in);
+  be_->free(p64.out);
   if (p64.dev) be_->free(p64.dev);
   if (p64.diag) be_->free(p64.diag);
-  out.energy = e + e_core_;
-  out.energy_rq64 = erq + e_core_;
-  out.residual64 = std::sqrt(std::max(0.0, r2));
-  out.iterations = its;
-  out.calls = (int)ms.size();
-  out.call_ms = std::move(ms);
-  out.dim = len;
-  be_->free(psi);
-  be_->free(plan.in);
-  be_->free(plan.out);
-  if (plan.dev) be_->free(plan.dev);
-  if (plan.tc_pool) be_->free(plan.tc_pool);
-  if (plan.diag) be_->free(plan.diag);
-  // the enlarged side stays available for the next call at this bond
-  if (!l2r) {
-    if ((int)keep_L_.size() < n_) keep_L_.resize(n_);
-    keep_L_[bond] = std::move(Le);
-  } else {
-    if ((int)keep_R_.size() < n_) keep_R_.resize(n_);
-    keep_R_[bond] = std::move(Re);
-  }
-  return out;
+  if (energy_rq64) *energy_rq64 = erq + e_core_;
+  if (residual64) *residual64 = std::sqrt(std::max(0.0, r2));
+  if (ms) *ms = t;
+  if (flops) *flops = p64.flops;
 }
 
 SweepStats Engine::sweep() {
+  end_bond_solves();
   stats_ = SweepStats();
   auto t0 = std::chrono::steady_clock::now();
   be_->mark_begin();

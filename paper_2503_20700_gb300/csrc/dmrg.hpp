@@ -163,6 +163,7 @@ struct Options {
   double trunc_target = 0.0;  // > 0: dynamic bond dimension (discarded weight bound)
   int D_min = 1;              // lower bound of the dynamic bond dimension
   bool rq64_every_bond = false;  // split runs: float64 Rayleigh quotient at every bond
+  int tc_drain_terms = 256;       // FP32 accumulation length of the tcgen05 contraction
 };
 
 struct SweepStats {
@@ -217,7 +218,11 @@ class Engine {
     long contraction_launches = 0;
     size_t dim = 0;
   };
-  BondSolve solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls);
+  BondSolve solve_bond(int bond, bool l2r, Precision p, int max_iter, double tol, int min_calls,
+                       bool check64 = true);
+  // float64 Rayleigh quotient and residual of the vector of the last
+  // solve_bond (one float64 H_eff psi, timed with CUDA events: *ms)
+  void check_bond64(double* energy_rq64, double* residual64, double* ms, double* flops);
   double energy() const { return energy_; }
   int n() const { return n_; }
   void set_D(int D) { opt_.D = D; }
@@ -317,6 +322,11 @@ class Engine {
   void apply_hpsi(struct HPsiPlan& plan);
   double davidson(struct HPsiPlan& plan, double* psi, int* iters);
   std::vector<double>* call_ms_ = nullptr;  // when set: CUDA-event ms of every H_eff psi
+  // vector of the last solve_bond and where it lives
+  void end_bond_solves();
+  double* solve_psi_ = nullptr;
+  int solve_bond_ = -1;
+  bool solve_l2r_ = false;
   double last_gap_ = 0.0;                   // Ritz gap at the last Davidson exit
   int cur_i_ = -1;                          // bond the blocks are held for
   std::unique_ptr<SavedU> decimate(Block& enl, const struct HPsiPlan& plan, const double* psi,

@@ -17,7 +17,9 @@
 // tile of float pairs).  The MMA order over the chunks c of the CTA's task
 // list is  S1(0), S1(1), S2(0), S1(2), S2(1), ...: the tensor pipe runs
 // stage 1 of the next chunk while the converters turn the last X' into X.
-// S is drained every kDrainItems items of a task and at its end.  Every wait
+// S is drained into the partial tile once the items accumulated in FP32
+// since the last drain reach drain_terms terms of psi's column index (sum of
+// kb; 0: after every item), and at the end of every task.  Every wait
 // gives up after the launch's wait bound (2 s of wall clock by default): the
 // CTA then sets the error flag, waits (bounded by 2 s) for its copies and
 // MMAs in flight, frees TMEM and returns.
@@ -48,7 +50,6 @@ constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_STAGE = 65536;
 constexpr int SMEM_USED = OFF_STAGE + NSTAGE * STAGE;  // 208 KB
 constexpr int SMEM_BYTES = SMEM_USED + 1024;            // slack for 1 KB alignment of the base
 constexpr int A_BYTES = 32768, P_BYTES = 16384, B_BYTES = 32768;
-constexpr int kDrainItems = 4;
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
 constexpr int NTHREADS = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -156,6 +157,8 @@ struct Walk {
   int ii;  // item (global index)
   int k;   // item position within the task
   int jc;
+  int acc;          // sum of kb over the items since the last drain, this one included
+  int drain_terms;  // drain once acc reaches it
   TcItem it;
   bool valid;
 };
@@ -168,9 +171,13 @@ __device__ __forceinline__ void walk_task(Walk& w) {
   w.k = 0;
   w.jc = 0;
   w.it = w.items[w.ii];
+  w.acc = w.it.kb;
 }
+__device__ __forceinline__ bool drain_point(const Walk& w);
 __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, const TcItem* items,
-                                           const HpsiTask* tasks, const int* list, int t0, int t1) {
+                                           const HpsiTask* tasks, const int* list, int t0, int t1,
+                                           int drain_terms) {
+  w.drain_terms = drain_terms;
   w.blocks = blocks;
   w.items = items;
   w.tasks = tasks;
@@ -181,13 +188,15 @@ __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, con
   if (w.valid) walk_task(w);
 }
 __device__ __forceinline__ void walk_next(Walk& w) {
+  const bool drained = drain_point(w);  // only true at an item's last chunk
   w.jc += JC;
   if (w.jc < w.it.kb) return;
+  w.jc = 0;
   ++w.ii;
   ++w.k;
-  w.jc = 0;
   if (w.k < w.tk.it_count) {
     w.it = w.items[w.ii];
+    w.acc = drained ? w.it.kb : w.acc + w.it.kb;
     return;
   }
   if (++w.t >= w.t_end) {
@@ -198,7 +207,7 @@ __device__ __forceinline__ void walk_next(Walk& w) {
 }
 __device__ __forceinline__ bool last_chunk_of_item(const Walk& w) { return w.jc + JC >= w.it.kb; }
 __device__ __forceinline__ bool drain_point(const Walk& w) {
-  return last_chunk_of_item(w) && (((w.k + 1) % kDrainItems) == 0 || w.k + 1 == w.tk.it_count);
+  return last_chunk_of_item(w) && (w.acc >= w.drain_terms || w.k + 1 == w.tk.it_count);
 }
 __device__ __forceinline__ int s1_blocks(const Walk& w) { return (w.it.ka + 31) >> 5; }
 __device__ __forceinline__ int s2_kblocks(const Walk& w) { return min(2, (w.it.kb - w.jc + 31) >> 5); }
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
                    const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
-                   unsigned long long wait_ns) {
+                   unsigned long long wait_ns, int drain_terms) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[B_COUNT];
   __shared__ uint32_t tmem_base;
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         return true;
       };
       Walk cur;
-      walk_start(cur, blocks, items, tasks, cta_task, t0, t1);
+      walk_start(cur, blocks, items, tasks, cta_task, t0, t1, drain_terms);
       if (cur.valid) {
         ok = s1(cur);
         while (ok) {
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         return true;
       };
       Walk cur;
-      walk_start(cur, blocks, items, tasks, cta_task, t0, t1);
+      walk_start(cur, blocks, items, tasks, cta_task, t0, t1, drain_terms);
       if (cur.valid) {
         ok = s1(cur, c++);
         int c2 = 0;
@@ -509,7 +518,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       return true;
     };
     Walk w;
-    walk_start(w, blocks, items, tasks, cta_task, t0, t1);
+    walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
     int chunk = 0, drains_in_task = 0, last_t = -1;
     bool pend = false, pend_first = false;
     long long pend_part = 0;
@@ -649,7 +658,8 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
     make_map(&m32, L.pool, L.units, 32);
     make_map(&m16, L.pool, L.units, 16);
     hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m16, L.blocks, L.items, L.tasks, L.cta_off,
-                                                          L.cta_task, L.scratch, err, wait_ns);
+                                                          L.cta_task, L.scratch, err, wait_ns,
+                                                          L.drain_terms);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }

@@ -67,6 +67,7 @@ struct SplitJob {
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
 constexpr int kTcUnitFloats = 256;  // one 1 KB unit
+constexpr int kTcDrainTerms = 256;  // default FP32 accumulation length (terms) between drains
 
 struct TcPlan {
   std::vector<SplitJob> op_jobs;   // operator blocks and identities (run once per plan)
@@ -101,6 +102,10 @@ struct TcLaunch {
   double* scratch = nullptr;
   const void* pool = nullptr;
   size_t units = 0;
+  // FP32 accumulation length of S between drains into the float-pair partial
+  // tile: once the items since the last drain reach this many terms of psi's
+  // column index (sum of kb), after the item (0: after every item)
+  int drain_terms = kTcDrainTerms;
 };
 
 // Runs the split jobs (device list of n jobs) into the pool.
