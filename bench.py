@@ -438,6 +438,7 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
                 "block_dims_left": left.tolist(), "block_dims_right": right.tolist(),
                 "wall_seconds": wall, "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
                 "kernel_ms": kernel_ms, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+                "launches_before_timed": l0,
                 "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line))
     g.close()

@@ -97,8 +97,8 @@ typedef struct {
                              tcgen05 contraction's sigma tile between drains
                              into its float-pair partial tile, in terms of
                              psi's column index (sum of kb over items; 0:
-                             after every item; default 256) -- shorter is more
-                             accurate and slower                              */
+                             after every item; default 1024) -- shorter is
+                             slightly more accurate and slower                */
 } dmrg_opts;
 
 /* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24,
@@ -221,7 +221,7 @@ dmrg_status dmrg_set_wait_timeout(dmrg_ctx* ctx, double seconds);
 dmrg_status dmrg_set_kernel_wait_timeout(double seconds);
 
 /* tc_drain_terms (see dmrg_opts) of the kernel-level dmrg_hpsi_contract,
- * process-wide; default 256. */
+ * process-wide; default 1024. */
 dmrg_status dmrg_set_kernel_tc_drain_terms(int terms);
 
 /* Change the bond dimension used by subsequent sweeps. */

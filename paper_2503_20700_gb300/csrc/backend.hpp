@@ -12,6 +12,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -87,6 +88,9 @@ class Backend {
   //     for the copy at the next stage_join() (or at release of the host copy).
   //   stage_join(): the main stream waits for every side-stream copy issued.
   //   host_release(host): frees a pinned copy after its copies completed.
+  // called by alloc when an allocation would exceed the budget: frees device
+  // memory (e.g. by staging a block out) and returns false when it cannot
+  std::function<bool()> make_room;
   virtual void* stage_out(void* dev, size_t bytes) = 0;
   virtual void* stage_in(const void* host, size_t bytes) = 0;
   virtual void stage_join() = 0;

@@ -719,6 +719,8 @@ class CudaBackend : public Backend {
   void* alloc(size_t b) override {
     void* p = nullptr;
     if (b == 0) b = 8;
+    while (budget_ && used + b > budget_ && make_room && make_room()) {
+    }
     if (budget_ && used + b > budget_)
       throw std::runtime_error("out of device memory (budget of " + std::to_string(budget_) + " bytes: " +
                                std::to_string(used) + " held, " + std::to_string(b) + " requested)");
@@ -776,7 +778,6 @@ class CudaBackend : public Backend {
     CK(cudaFreeAsync(dev, sd));
     staged_bytes += bytes;
     staged_out_bytes += bytes;
-    ++launches;
     return h;
   }
   void* stage_in(const void* host, size_t bytes) override {
@@ -790,7 +791,6 @@ class CudaBackend : public Backend {
     CK(cudaEventDestroy(e));
     CK(cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, sd));
     staged_in_bytes += bytes;
-    ++launches;
     return d;
   }
   void stage_join() override {

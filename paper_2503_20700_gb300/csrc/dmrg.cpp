@@ -476,6 +476,7 @@ struct GemmBuilder {
 }  // namespace
 
 Engine::~Engine() {
+  if (be_) be_->make_room = nullptr;
   if (solve_psi_ && be_) be_->free(solve_psi_);
   if (prev_.psi && be_) be_->free(prev_.psi);
   if (ones_ && be_) be_->free(ones_);
@@ -2209,8 +2210,52 @@ void Engine::resident(Block* b) {
 // blocks plus the bond's own working memory (measured at the previous bond)
 // would exceed the budget, the blocks whose next use is farthest away are
 // staged out; the blocks of the next step are brought back ahead of time.
+bool Engine::stage_out_one() {
+  const int step = cur_step_;
+  auto bond_of = [&](int s) {
+    const int P = 2 * n_ - 4;
+    s %= P;
+    return s <= n_ - 3 ? s : (n_ - 2) - (s - (n_ - 2));
+  };
+  std::vector<const Block*> busy;
+  for (int s : {step, step + 1}) {
+    const int b = bond_of(s);
+    if (b >= 0 && b < (int)L_.size()) busy.push_back(L_[b].get());
+    if (n_ - b - 2 >= 0 && n_ - b - 2 < (int)R_.size()) busy.push_back(R_[n_ - b - 2].get());
+  }
+  Block* best = nullptr;
+  int best_next = -1;
+  for (int side = 0; side < 2; ++side) {
+    auto& v = side == 0 ? L_ : R_;
+    for (int m = 0; m < (int)v.size(); ++m) {
+      Block* b = v[m].get();
+      if (!b || !b->ops || b->ops->on_host || b->ops->mem.empty() || b->ops->arriving) continue;
+      if (std::find(busy.begin(), busy.end(), b) != busy.end()) continue;
+      const int nu = next_use(side == 0, m, step);
+      if (nu > best_next) {
+        best_next = nu;
+        best = b;
+      }
+    }
+  }
+  if (best) {
+    best->ops->stage_out();
+    return true;
+  }
+  if (!keep_L_.empty() || !keep_R_.empty()) {
+    bool any = false;
+    for (auto& b : keep_L_) any = any || b != nullptr;
+    for (auto& b : keep_R_) any = any || b != nullptr;
+    drop_kept();
+    return any;
+  }
+  return false;
+}
+
 void Engine::stage_for_step(int step) {
+  cur_step_ = step;
   const size_t budget = be_->budget();
+  if (budget && !be_->make_room) be_->make_room = [this]() { return stage_out_one(); };
   auto bond_of = [&](int s) {
     const int P = 2 * n_ - 4;
     s %= P;
@@ -2230,7 +2275,7 @@ void Engine::stage_for_step(int step) {
     for (auto& b : *v)
       if (b && b->ops && !b->ops->pending.empty() && !b->ops->arriving) b->ops->release_pending();
   if (budget == 0) return;
-  const size_t need = bond_extra_ + bond_extra_ / 10;
+  const size_t need = bond_extra_ + bond_extra_ * 3 / 10;
   if (be_->bytes_in_use() + need > budget) {
     struct Cand {
       int next;

@@ -163,7 +163,7 @@ struct Options {
   double trunc_target = 0.0;  // > 0: dynamic bond dimension (discarded weight bound)
   int D_min = 1;              // lower bound of the dynamic bond dimension
   bool rq64_every_bond = false;  // split runs: float64 Rayleigh quotient at every bond
-  int tc_drain_terms = 256;       // FP32 accumulation length of the tcgen05 contraction
+  int tc_drain_terms = 1024;      // FP32 accumulation length of the tcgen05 contraction
 };
 
 struct SweepStats {
@@ -279,6 +279,8 @@ class Engine {
   void stage_for_step(int step);
   int next_use(bool left, int m, int step) const;
   void resident(Block* b);  // operators on the device and joined
+  bool stage_out_one();     // the stored block used farthest ahead (not by the current step)
+  int cur_step_ = 0;
   double energy_ = 0.0;
   std::vector<double> bond_e_;
   int last_bond_ = -1;

@@ -67,7 +67,7 @@ struct SplitJob {
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
 constexpr int kTcUnitFloats = 256;  // one 1 KB unit
-constexpr int kTcDrainTerms = 256;  // default FP32 accumulation length (terms) between drains
+constexpr int kTcDrainTerms = 1024;  // default FP32 accumulation length (terms) between drains
 
 struct TcPlan {
   std::vector<SplitJob> op_jobs;   // operator blocks and identities (run once per plan)
