@@ -295,10 +295,11 @@ dmrg_status dmrg_last_sweep_device_ms(const dmrg_ctx* ctx, double* ms);
 /* Device memory held by the context now and at its high-water mark (bytes). */
 dmrg_status dmrg_memory(const dmrg_ctx* ctx, int64_t* in_use, int64_t* peak);
 
-/* Staging detail (bytes), out[6]: [0] stored blocks on the device, [1] stored
+/* Staging detail (bytes), out[7]: [0] stored blocks on the device, [1] stored
  * blocks staged out to pinned host memory, [2] total moved out and [3] total
  * moved back in so far, [4] the largest working memory of a bond beyond the
- * stored blocks so far, [5] the largest stored block.  With hbm_budget_bytes
+ * stored blocks so far, [5] the largest stored block, [6] the MPS tensors
+ * (kept eigenvectors of every bond, always on the device).  With hbm_budget_bytes
  * set, stored blocks whose next use in the sweep is farthest away are copied
  * to pinned host memory on a side stream whenever the stored blocks plus the
  * last bond's working memory would exceed the budget, and are copied back

@@ -318,9 +318,10 @@ class DMRG:
         """Staging detail: stored bytes on the device and in pinned host memory,
         bytes moved out / in so far, the largest bond working memory and the
         largest stored block."""
-        out = (ctypes.c_int64 * 6)()
+        out = (ctypes.c_int64 * 7)()
         _check(self._lib, self._ctx, self._lib.dmrg_memory_detail(self._ctx, out))
-        keys = ["stored_device", "stored_host", "staged_out", "staged_in", "max_bond_extra", "max_block"]
+        keys = ["stored_device", "stored_host", "staged_out", "staged_in", "max_bond_extra", "max_block",
+                "mps"]
         return dict(zip(keys, list(out)))
 
     def launch_count(self):

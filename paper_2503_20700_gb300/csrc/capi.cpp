@@ -335,14 +335,15 @@ dmrg_status dmrg_set_kernel_wait_timeout(double seconds) {
 
 dmrg_status dmrg_memory_detail(const dmrg_ctx* c, int64_t* out) {
   if (!c || !c->eng || !out) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid argument");
-  size_t d = 0, h = 0, mb = 0, mx = 0;
-  c->eng->memory_detail(&d, &h, &mb, &mx);
+  size_t d = 0, h = 0, mb = 0, mx = 0, mu = 0;
+  c->eng->memory_detail(&d, &h, &mb, &mx, &mu);
   out[0] = (int64_t)d;
   out[1] = (int64_t)h;
   out[2] = (int64_t)c->be->staged_out_bytes;
   out[3] = (int64_t)c->be->staged_in_bytes;
   out[4] = (int64_t)mx;
   out[5] = (int64_t)mb;
+  out[6] = (int64_t)mu;
   return DMRG_OK;
 }
 

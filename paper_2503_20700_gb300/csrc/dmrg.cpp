@@ -2169,7 +2169,17 @@ void Engine::build_initial_right() {
 // ---- staging of stored blocks to pinned host memory (device budget)
 // Bond b uses L(b) and R(n-b-2) in both directions; in sweep steps, L->R
 // bond i is step i and R->L bond i is step (n-2) + (n-2-i), period 2n-4.
-void Engine::memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra) const {
+void Engine::memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra,
+                           size_t* mps_bytes) const {
+  size_t u = 0;
+  for (auto* v : {&LU_, &RU_})
+    for (auto& x : *v)
+      if (x) {
+        size_t n = 0;
+        for (size_t s = 0; s < x->kept.size(); ++s) n += (size_t)x->kept[s] * x->enl.sec[s].dim;
+        u += n * sizeof(double);
+      }
+  if (mps_bytes) *mps_bytes = u;
   size_t d = 0, h = 0, mb = 0;
   for (auto* v : {&L_, &R_})
     for (auto& b : *v) {
@@ -2407,7 +2417,9 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   }
   // keep this bond's system-side enlarged block for the way back
   const double cap = be_->budget() ? (double)std::min(be_->budget(), be_->capacity()) : (double)be_->capacity();
+  // ... and only while the next bond's working memory still fits next to it
   if ((double)be_->bytes_in_use() <= kKeepFraction * cap &&
+      (double)be_->bytes_in_use() + 1.3 * (double)bond_extra_ <= 0.85 * cap &&
       (double)be_->device_free() >= kKeepFreeFraction * (double)be_->capacity()) {
     auto& keep = l2r ? keep_L_ : keep_R_;
     if ((int)keep.size() < n_) keep.resize(n_);

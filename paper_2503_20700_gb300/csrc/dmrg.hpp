@@ -250,7 +250,8 @@ class Engine {
   Backend* backend() const { return be_; }
   // device and pinned-host bytes of the stored blocks, the largest one, and
   // the largest working memory of a bond beyond the stored blocks so far
-  void memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra) const;
+  void memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra,
+                     size_t* mps_bytes = nullptr) const;
 
  private:
   friend struct EngineAccess;

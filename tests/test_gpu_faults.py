@@ -127,20 +127,21 @@ def test_debug_bounds_checks_plans_without_changing_results(pkg):
 
 
 def test_budget_stages_blocks_to_pinned_host_memory_bit_identically(pkg):
-    """A device budget below the unbudgeted high-water mark: stored blocks go
-    to pinned host memory on the side stream and come back ahead of their
-    bond; the energies are bit-identical to the unbudgeted run."""
-    h, eri, ec = W.ppp_acene(5)
-    ref = pkg.DMRG(h, eri=eri, n_elec=22, D=128, e_core=ec)
+    """A device budget below what the stored blocks of a sweep need (PPP
+    octacene, 34 sites, D=64): stored blocks go to pinned host memory on the
+    side stream and come back ahead of their bond; the energies are
+    bit-identical to the unbudgeted run."""
+    h, eri, ec = W.ppp_acene(8)
+    ref = pkg.DMRG(h, eri=eri, n_elec=34, D=64, e_core=ec)
     e_ref = [ref.sweep()[0] for _ in range(2)]
     md = ref.memory_detail()
     _, peak = ref.memory()
     ref.close()
-    # room for a bond's working memory and the four blocks of this bond and
-    # the next, not for all stored blocks at once
-    budget = md["max_bond_extra"] + int(4.5 * md["max_block"]) + (32 << 20)
-    assert budget < md["max_bond_extra"] + md["stored_device"] + md["stored_host"]
-    g = pkg.DMRG(h, eri=eri, n_elec=22, D=128, e_core=ec, hbm_budget_bytes=budget)
+    # room for a bond's working memory, the MPS tensors and the four blocks of
+    # this bond and the next, not for all stored blocks at once
+    budget = md["max_bond_extra"] + md["mps"] + int(4.5 * md["max_block"]) + (4 << 20)
+    assert budget < md["max_bond_extra"] + md["mps"] + md["stored_device"] + md["stored_host"]
+    g = pkg.DMRG(h, eri=eri, n_elec=34, D=64, e_core=ec, hbm_budget_bytes=budget)
     e = [g.sweep()[0] for _ in range(2)]
     st = g.memory_detail()
     _, peak_b = g.memory()
