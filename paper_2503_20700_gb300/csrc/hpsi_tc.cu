@@ -115,21 +115,29 @@ __device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
+// a probe that may suspend the thread for up to ~1 us while the phase is
+// incomplete (frees the issue slot for the warps that share the scheduler)
+__device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+      : "memory");
+  return done != 0;
+}
 // bounded wait on the phase with the given parity; false after wait_ns of
 // wall clock (0: after the first probe), or at once when another role has
 // aborted (abort != 0)
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort,
                                          unsigned long long wait_ns) {
-  const int spin = wait_ns > 0 ? 256 : 1;
-  for (int i = 0; i < spin; ++i)
-    if (test_wait(bar, parity)) return true;
+  if (test_wait(bar, parity)) return true;
   if (wait_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    if (test_wait(bar, parity)) return true;
+    if (try_wait(bar, parity)) return true;
     if (*abort) return false;
     if (global_ns() - t0 > wait_ns) return false;
-    __nanosleep(32);
   }
 }
 // the same, with one outcome for the whole warp (the converter warps issue
@@ -343,14 +351,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           int s;
           if (!take(s)) return false;
           const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+          // descriptors of the stage; a k-step of 8 moves the start address by
+          // 256 B (16 in the address field, which stays inside its 14 bits)
+          const uint64_t ah0 = desc(st, SBO_OP), al0 = desc(st + 1024, SBO_OP);
+          const uint64_t ph0 = desc(st + A_BYTES, SBO_OP), pl0 = desc(st + A_BYTES + 1024, SBO_OP);
 #pragma unroll
           for (int k8 = 0; k8 < 4; ++k8) {
-            const uint32_t ko = (uint32_t)k8 * 2 * LBO;
-            const uint64_t ah = desc(st + ko, SBO_OP), al = desc(st + 1024 + ko, SBO_OP);
-            const uint64_t ph = desc(st + A_BYTES + ko, SBO_OP), pl = desc(st + A_BYTES + 1024 + ko, SBO_OP);
-            mma_tf32(tX, al, ph, id, (kk > 0 || k8 > 0) ? 1u : 0u);
-            mma_tf32(tX, ah, pl, id, 1u);
-            mma_tf32(tX, ah, ph, id, 1u);
+            const uint64_t ko = (uint64_t)(k8 * 2 * LBO) >> 4;
+            mma_tf32(tX, al0 + ko, ph0 + ko, id, (kk > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32(tX, ah0 + ko, pl0 + ko, id, 1u);
+            mma_tf32(tX, ah0 + ko, ph0 + ko, id, 1u);
           }
           commit(&bar[B_EMPTY + s]);
           ++q;
@@ -375,16 +385,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int s;
             if (!take(s)) return false;
             const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+            const uint32_t xo = (uint32_t)kk * 8 * LBO;
+            const uint64_t xh0 = desc(xh + xo, SBO_X), xl0 = desc(xl + xo, SBO_X);
+            const uint64_t bh0 = desc(st, SBO_OP), bl0 = desc(st + 1024, SBO_OP);
 #pragma unroll
             for (int k8 = 0; k8 < 4; ++k8) {
-              const uint32_t ko = (uint32_t)k8 * 2 * LBO;
-              const uint32_t xo = (uint32_t)kk * 8 * LBO + ko;
-              const uint64_t xhd = desc(xh + xo, SBO_X), xld = desc(xl + xo, SBO_X);
-              const uint64_t bh = desc(st + ko, SBO_OP), bl = desc(st + 1024 + ko, SBO_OP);
-              mma_tf32(dS, xld, bh, id, fresh ? 0u : 1u);
+              const uint64_t ko = (uint64_t)(k8 * 2 * LBO) >> 4;
+              mma_tf32(dS, xl0 + ko, bh0 + ko, id, fresh ? 0u : 1u);
               fresh = false;
-              mma_tf32(dS, xhd, bl, id, 1u);
-              mma_tf32(dS, xhd, bh, id, 1u);
+              mma_tf32(dS, xh0 + ko, bl0 + ko, id, 1u);
+              mma_tf32(dS, xh0 + ko, bh0 + ko, id, 1u);
             }
             commit(&bar[B_EMPTY + s]);
             ++q;

@@ -69,3 +69,21 @@ def test_replicas_take_max_time_and_sum_flops_over_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(0, 2.0, 30.0), (1, 2.0, 30.0)]
+
+
+def test_parse_ramp_and_bond_defaults():
+    assert bench.parse_ramp("64:4,256:4,1024:4") == [(64, 4), (256, 4), (1024, 4)]
+    assert bench.parse_ramp("") == []
+    # the default step is the middle-bond product at D = 2048
+    src = open(os.path.join(os.path.dirname(bench.__file__), "bench.py")).read()
+    assert 'ap.add_argument("--mode", default="bond"' in src
+    assert 'ap.add_argument("--D", type=int, default=2048)' in src
+
+
+def test_initial_state_is_aufbau_for_cholesky_workloads():
+    import workloads as W
+    wl = bench.workload("cas8")
+    occ, path = bench.initial_state(wl)
+    assert sum(occ) == 8 and path[0] == 0 and occ == W.aufbau_state(wl["h"], 8, 0)[0]
+    wl = bench.workload("naphthalene")
+    assert bench.initial_state(wl) == (None, None)

@@ -137,10 +137,12 @@ def test_budget_stages_blocks_to_pinned_host_memory_bit_identically(pkg):
     md = ref.memory_detail()
     _, peak = ref.memory()
     ref.close()
-    # room for a bond's working memory, the MPS tensors and the four blocks of
-    # this bond and the next, not for all stored blocks at once
-    budget = md["max_bond_extra"] + md["mps"] + int(4.5 * md["max_block"]) + (4 << 20)
-    assert budget < md["max_bond_extra"] + md["mps"] + md["stored_device"] + md["stored_host"]
+    # room for a bond's working memory, the MPS tensors and three quarters of
+    # the right blocks a sweep ends with: in the middle of a sweep the left
+    # blocks built so far come on top, so blocks have to be staged out
+    stored = md["stored_device"] + md["stored_host"]
+    assert stored > 6 * md["max_block"]
+    budget = md["max_bond_extra"] + md["mps"] + int(0.75 * stored) + (8 << 20)
     g = pkg.DMRG(h, eri=eri, n_elec=34, D=64, e_core=ec, hbm_budget_bytes=budget)
     e = [g.sweep()[0] for _ in range(2)]
     st = g.memory_detail()
