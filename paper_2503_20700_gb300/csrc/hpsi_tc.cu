@@ -1,28 +1,36 @@
 // tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh), persistent and
 // warp-specialised, with operand tiles brought in by TMA.
 //
-// Shared memory (bytes): X hi | X lo planes (2 x 32 KB, 128 x 64, K-major,
-// 2 KB between 8-row groups) and three 48 KB stages, each holding the TMA
-// tiles of one k-block of 32:
-//   stage 1: A (128 rows: 32 KB, units interleaved hi/lo) | P^T (64 rows: 16 KB)
-//   stage 2: B (one 128-row column half of the sigma tile: 32 KB)
-// Inside a TMA tile, row group g occupies 2 KB: hi core matrices at 2048 g,
-// lo at 2048 g + 1024, k-cores 128 B apart.  TMEM: S in columns [0, 256),
-// X' double-buffered in [256, 320) and [320, 384).
+// Per item of a task (a 128 x N, N <= 256, sigma tile) and per super-chunk
+// of up to 256 columns of psi (columns [c, c+256) of P):
+//   stage 1:  X' = op(A)(tile rows, :) P(:, c..c+256)          (TMEM, 128 x 256)
+// then per 32-column piece p of the super-chunk:
+//   X = alpha X'(:, p)  ->  TF32 hi/lo planes in shared memory (converters)
+//   stage 2:  S += X op(B)(tile cols, p)^T                      (TMEM, 128 x N)
+// Stage 1 uses N = 256 (one A panel fetch per 256 columns of psi) and stage 2
+// the full tile width, so the MMAs are as wide as the tile allows.
+//
+// Shared memory (bytes): two X piece buffers (each hi | lo, 128 x 32, 16 KB
+// per plane, 1 KB between 8-row groups) and three 48 KB stages, each holding
+// the TMA tiles of one k-block of 16:
+//   stage 1: A (128 rows: 16 KB) | P^T (256 rows: 32 KB)
+//   stage 2: B (256 rows, the tile's columns: 32 KB)
+// A TMA tile of a k-block of 16 takes half of each 1 KB pool unit: row group
+// g holds its hi core matrices at 1024 g and its lo ones at 1024 g + 512,
+// k-cores 128 B apart.  TMEM: S in columns [0, 256), X' in [256, 512).
 //
 // Warps: 0 producer (one lane issues cp.async.bulk.tensor into the stages;
 // full/empty mbarriers), 1 MMA issuer (one lane; owns the TMEM allocation),
-// 2..5 converters (TMEM lanes 32 (w % 4) .. +31: X' -> alpha X' as TF32
-// hi/lo planes in shared memory, and the drains of S into the task's partial
-// tile of float pairs).  The MMA order over the chunks c of the CTA's task
-// list is  S1(0), S1(1), S2(0), S1(2), S2(1), ...: the tensor pipe runs
-// stage 1 of the next chunk while the converters turn the last X' into X.
-// S is drained into the partial tile once the items accumulated in FP32
-// since the last drain reach drain_terms terms of psi's column index (sum of
-// kb; 0: after every item), and at the end of every task.  Every wait
-// gives up after the launch's wait bound (2 s of wall clock by default): the
-// CTA then sets the error flag, waits (bounded by 2 s) for its copies and
-// MMAs in flight, frees TMEM and returns.
+// 2..5 converters (TMEM lanes 32 (w % 4) .. +31: X' pieces -> alpha X' as
+// TF32 hi/lo planes, double-buffered, and the drains of S into the task's
+// partial tile of float pairs).  The MMA order issues stage 1 of the next
+// super-chunk before stage 2 of the last piece of the current one, so the
+// tensor pipe runs it while the last piece is converted.  S is drained once
+// the items accumulated in FP32 since the last drain reach drain_terms terms
+// of psi's column index (sum of kb; 0: after every item) and at the end of
+// every task.  Every wait gives up after the launch's wait bound (2 s of wall
+// clock by default): the CTA then sets the error flag, waits (bounded by
+// 2 s) for its copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -40,23 +48,27 @@ namespace dmrg {
 
 namespace {
 
-constexpr int TM = kTcTileM, TNMAX = kTcTileN, JC = 64, HALF = 128;
-constexpr uint32_t LBO = 128;        // between K-adjacent core matrices
-constexpr uint32_t SBO_OP = 2048;    // between 8-row groups of a TMA tile (hi and lo interleaved)
-constexpr uint32_t SBO_X = 2048;     // between 8-row groups of the 64-wide X planes
+constexpr int TM = kTcTileM, TNMAX = kTcTileN;
+constexpr int W1 = 256;               // stage-1 super-chunk width (columns of psi)
+constexpr int PW = 32;                // piece width (X planes, stage-2 K per piece)
+constexpr uint32_t LBO = 128;         // between K-adjacent core matrices
+constexpr uint32_t SBO_OP = 1024;     // between 8-row groups of a TMA tile (hi and lo interleaved)
+constexpr uint32_t LO_OP = 512;       // lo plane of a row group in a TMA tile
+constexpr uint32_t SBO_X = 1024;      // between 8-row groups of a 32-wide X plane
 constexpr int NSTAGE = 3;
 constexpr int STAGE = 49152;
-constexpr int OFF_XH = 0, OFF_XL = 32768, OFF_STAGE = 65536;
+constexpr int XBUF = 32768, XLO = 16384;  // X piece buffer (hi | lo)
+constexpr int OFF_X = 0, OFF_STAGE = 2 * XBUF;
 constexpr int SMEM_USED = OFF_STAGE + NSTAGE * STAGE;  // 208 KB
 constexpr int SMEM_BYTES = SMEM_USED + 1024;            // slack for 1 KB alignment of the base
-constexpr int A_BYTES = 32768, P_BYTES = 16384, B_BYTES = 32768;
+constexpr int A_BYTES = 16384, P_BYTES = 32768, B_BYTES = 32768;
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
 constexpr int NTHREADS = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // barriers
-enum { B_FULL = 0, B_EMPTY = B_FULL + NSTAGE, B_XPF = B_EMPTY + NSTAGE, B_XPE = B_XPF + 2, B_XF = B_XPE + 2,
-       B_XE, B_SF, B_SE, B_DONE, B_COUNT };
+enum { B_FULL = 0, B_EMPTY = B_FULL + NSTAGE, B_XPF = B_EMPTY + NSTAGE, B_XPE, B_XF, B_XE = B_XF + 2,
+       B_SF = B_XE + 2, B_SE, B_DONE, B_COUNT };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,11 +106,12 @@ __device__ __forceinline__ void arrive_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int y, uint64_t* bar) {
+// TMA copy of the box at (x floats, y units) of `map` into shared memory
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(smem_u32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -147,13 +160,13 @@ __device__ __forceinline__ bool wait_bar_warp(uint64_t* bar, uint32_t parity, vo
   const bool ok = wait_bar(bar, parity, abort, wait_ns);
   return __all_sync(0xffffffffu, ok);
 }
-// byte offset of element (r, k) (k multiple of 4) in the 64-wide X planes
+// byte offset of element (r, k) (k multiple of 4) in a 32-wide X plane
 __device__ __forceinline__ uint32_t x_off(int r, int k) {
   return (uint32_t)(r >> 3) * SBO_X + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16;
 }
 
-// The chunk sequence of one CTA: its tasks in list order, their items, and
-// the 64-wide chunks of psi's columns of every item.
+// The piece sequence of one CTA: its tasks in list order, their items, the
+// super-chunks of 256 columns of psi of every item and their 32-column pieces.
 struct Walk {
   const HpsiBlock* blocks;
   const TcItem* items;
@@ -161,10 +174,11 @@ struct Walk {
   const int* list;
   int t, t_end;
   HpsiTask tk;
-  int N;   // MMA width of the tile (multiple of 16)
-  int ii;  // item (global index)
-  int k;   // item position within the task
-  int jc;
+  int N;    // MMA width of the tile (multiple of 16)
+  int ii;   // item (global index)
+  int k;    // item position within the task
+  int jc;   // first column of the super-chunk
+  int p;    // piece within the super-chunk
   int acc;          // sum of kb over the items since the last drain, this one included
   int drain_terms;  // drain once acc reaches it
   TcItem it;
@@ -178,10 +192,10 @@ __device__ __forceinline__ void walk_task(Walk& w) {
   w.ii = w.tk.it_begin;
   w.k = 0;
   w.jc = 0;
+  w.p = 0;
   w.it = w.items[w.ii];
   w.acc = w.it.kb;
 }
-__device__ __forceinline__ bool drain_point(const Walk& w);
 __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, const TcItem* items,
                                            const HpsiTask* tasks, const int* list, int t0, int t1,
                                            int drain_terms) {
@@ -195,11 +209,19 @@ __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, con
   w.valid = t0 < t1;
   if (w.valid) walk_task(w);
 }
-__device__ __forceinline__ void walk_next(Walk& w) {
-  const bool drained = drain_point(w);  // only true at an item's last chunk
-  w.jc += JC;
-  if (w.jc < w.it.kb) return;
+__device__ __forceinline__ int sc_width(const Walk& w) { return min(W1, w.it.kb - w.jc); }
+__device__ __forceinline__ int sc_pieces(const Walk& w) { return (sc_width(w) + PW - 1) / PW; }
+__device__ __forceinline__ bool last_piece(const Walk& w) { return w.p + 1 >= sc_pieces(w); }
+__device__ __forceinline__ bool last_piece_of_item(const Walk& w) {
+  return last_piece(w) && w.jc + W1 >= w.it.kb;
+}
+__device__ __forceinline__ bool drain_point(const Walk& w) {
+  return last_piece_of_item(w) && (w.acc >= w.drain_terms || w.k + 1 == w.tk.it_count);
+}
+// to the next item (after its last piece)
+__device__ __forceinline__ void walk_next_item(Walk& w, bool drained) {
   w.jc = 0;
+  w.p = 0;
   ++w.ii;
   ++w.k;
   if (w.k < w.tk.it_count) {
@@ -213,16 +235,28 @@ __device__ __forceinline__ void walk_next(Walk& w) {
   }
   walk_task(w);
 }
-__device__ __forceinline__ bool last_chunk_of_item(const Walk& w) { return w.jc + JC >= w.it.kb; }
-__device__ __forceinline__ bool drain_point(const Walk& w) {
-  return last_chunk_of_item(w) && (w.acc >= w.drain_terms || w.k + 1 == w.tk.it_count);
+// to the next piece
+__device__ __forceinline__ void walk_next(Walk& w) {
+  const bool drained = drain_point(w);  // only true at an item's last piece
+  if (!last_piece(w)) {
+    ++w.p;
+    return;
+  }
+  w.p = 0;
+  w.jc += W1;
+  if (w.jc < w.it.kb) return;
+  walk_next_item(w, drained);
 }
-__device__ __forceinline__ int s1_blocks(const Walk& w) { return (w.it.ka + 31) >> 5; }
-__device__ __forceinline__ int s2_kblocks(const Walk& w) { return min(2, (w.it.kb - w.jc + 31) >> 5); }
-__device__ __forceinline__ int s2_halves(const Walk& w) { return w.N > HALF ? 2 : 1; }
+// to the start of the next super-chunk (from any of its pieces)
+__device__ __forceinline__ void walk_next_sc(Walk& w) {
+  w.p = sc_pieces(w) - 1;
+  walk_next(w);
+}
+__device__ __forceinline__ int s1_blocks(const Walk& w) { return (w.it.ka + 15) >> 4; }
+__device__ __forceinline__ int s2_kblocks(const Walk& w) { return min(2, (w.it.kb - w.jc - PW * w.p + 15) >> 4); }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    hpsi_tc_kernel(const __grid_constant__ CUtensorMap map32, const __grid_constant__ CUtensorMap map16,
+    hpsi_tc_kernel(const __grid_constant__ CUtensorMap map32, const __grid_constant__ CUtensorMap map64,
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
                    const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
@@ -244,12 +278,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_FULL + i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_EMPTY + i])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XPF])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XPE])));
     for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XPF + i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XPE + i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XF + i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XE + i])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XF])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XE])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_SF])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_SE])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_DONE])));
@@ -265,62 +299,68 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tS = tmem_base + TCOL_S;
+  const uint32_t tS = tmem_base + TCOL_S, tX = tmem_base + TCOL_X;
   int produced = 0;  // stage fills issued (producer lane)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map32)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map16)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map64)) : "memory");
       int q = 0;
       bool ok = true;
       auto acquire = [&](int& s) -> bool {
         s = q % NSTAGE;
-        const uint32_t par = (uint32_t)(((q / NSTAGE) & 1) ^ 1);
-        if (!wait_bar(&bar[B_EMPTY + s], par, abort, wait_ns)) return false;
-        return true;
+        return wait_bar(&bar[B_EMPTY + s], (uint32_t)(((q / NSTAGE) & 1) ^ 1), abort, wait_ns);
       };
+      // stage 1 of the super-chunk at w: per k-block of 16 of ka, the A tile
+      // (the tile's rows) and the P^T tile (256 rows from the super-chunk's first)
       auto s1 = [&](const Walk& w) -> bool {
         const int nb = s1_blocks(w);
         for (int kk = 0; kk < nb; ++kk) {
           int s;
           if (!acquire(s)) return false;
           const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+          const int x = (kk & 1) * 128, kb32 = kk >> 1;
           arrive_expect(&bar[B_FULL + s], A_BYTES + P_BYTES);
-          tma_load(st, &map32, w.it.A.unit + (kk * w.it.A.groups + (w.tk.r0 >> 3)) * 2, &bar[B_FULL + s]);
-          tma_load(st + A_BYTES, &map16, w.it.Pt.unit + (kk * w.it.Pt.groups + (w.jc >> 3)) * 2, &bar[B_FULL + s]);
+          tma_load(st, &map32, x, w.it.A.unit + (kb32 * w.it.A.groups + (w.tk.r0 >> 3)) * 2, &bar[B_FULL + s]);
+          tma_load(st + A_BYTES, &map64, x, w.it.Pt.unit + (kb32 * w.it.Pt.groups + (w.jc >> 3)) * 2,
+                   &bar[B_FULL + s]);
           ++q;
         }
         return true;
       };
+      // stage 2 of the piece at w: per k-block of 16 of the piece, the B tile
+      // (the tile's columns, 256 rows)
       auto s2 = [&](const Walk& w) -> bool {
-        const int nh = s2_halves(w), nk = s2_kblocks(w);
-        for (int h = 0; h < nh; ++h)
-          for (int kk = 0; kk < nk; ++kk) {
-            int s;
-            if (!acquire(s)) return false;
-            const uint32_t st = sbase + OFF_STAGE + s * STAGE;
-            arrive_expect(&bar[B_FULL + s], B_BYTES);
-            tma_load(st, &map32,
-                     w.it.B.unit + (((w.jc >> 5) + kk) * w.it.B.groups + ((w.tk.c0 + h * HALF) >> 3)) * 2,
-                     &bar[B_FULL + s]);
-            ++q;
-          }
+        const int nk = s2_kblocks(w);
+        const int k16 = (w.jc + PW * w.p) >> 4;
+        for (int kk = 0; kk < nk; ++kk) {
+          int s;
+          if (!acquire(s)) return false;
+          const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+          const int kq = k16 + kk;
+          arrive_expect(&bar[B_FULL + s], B_BYTES);
+          tma_load(st, &map64, (kq & 1) * 128, w.it.B.unit + ((kq >> 1) * w.it.B.groups + (w.tk.c0 >> 3)) * 2,
+                   &bar[B_FULL + s]);
+          ++q;
+        }
         return true;
       };
-      Walk cur;
-      walk_start(cur, blocks, items, tasks, cta_task, t0, t1, drain_terms);
-      if (cur.valid) {
-        ok = s1(cur);
-        while (ok) {
-          Walk nxt = cur;
-          walk_next(nxt);
-          if (nxt.valid && !(ok = s1(nxt))) break;
-          if (!(ok = s2(cur))) break;
-          if (!nxt.valid) break;
-          cur = nxt;
+      Walk s1w, s2w;
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
+      s1w = s2w;
+      if (s1w.valid) {
+        ok = s1(s1w);
+        walk_next_sc(s1w);
+      }
+      while (ok && s2w.valid) {
+        if (last_piece(s2w) && s1w.valid) {
+          if (!(ok = s1(s1w))) break;
+          walk_next_sc(s1w);
         }
+        if (!(ok = s2(s2w))) break;
+        walk_next(s2w);
       }
       if (!ok) {
         *abort = 1;
@@ -331,21 +371,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int q = 0, nd = 0, c = 0;  // stage fills consumed, drains requested, chunks issued in S1
-      bool need_se = false, fresh0 = true, fresh1 = true, ok = true;
-      const uint32_t xh = sbase + OFF_XH, xl = sbase + OFF_XL;
+      int q = 0, nd = 0, nsc = 0, g = 0;  // stage fills consumed, drains, super-chunks issued, pieces issued
+      bool need_se = false, fresh = true, ok = true;
       auto take = [&](int& s) -> bool {
         s = q % NSTAGE;
         if (!wait_bar(&bar[B_FULL + s], (uint32_t)((q / NSTAGE) & 1), abort, wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
         return true;
       };
-      auto s1 = [&](const Walk& w, int chunk) -> bool {
-        const int b = chunk & 1;
-        if (chunk >= 2 && !wait_bar(&bar[B_XPE + b], (uint32_t)(((chunk >> 1) - 1) & 1), abort, wait_ns)) return false;
+      auto s1 = [&](const Walk& w) -> bool {
+        // X' must have been read by the converters (every piece of the last super-chunk)
+        if (nsc >= 1 && !wait_bar(&bar[B_XPE], (uint32_t)((nsc - 1) & 1), abort, wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t tX = tmem_base + TCOL_X + 64 * b;
-        const uint32_t id = idesc_tf32(TM, JC);
+        const uint32_t id = idesc_tf32(TM, (sc_width(w) + 15) & ~15);
         const int nb = s1_blocks(w);
         for (int kk = 0; kk < nb; ++kk) {
           int s;
@@ -353,10 +391,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t st = sbase + OFF_STAGE + s * STAGE;
           // descriptors of the stage; a k-step of 8 moves the start address by
           // 256 B (16 in the address field, which stays inside its 14 bits)
-          const uint64_t ah0 = desc(st, SBO_OP), al0 = desc(st + 1024, SBO_OP);
-          const uint64_t ph0 = desc(st + A_BYTES, SBO_OP), pl0 = desc(st + A_BYTES + 1024, SBO_OP);
+          const uint64_t ah0 = desc(st, SBO_OP), al0 = desc(st + LO_OP, SBO_OP);
+          const uint64_t ph0 = desc(st + A_BYTES, SBO_OP), pl0 = desc(st + A_BYTES + LO_OP, SBO_OP);
 #pragma unroll
-          for (int k8 = 0; k8 < 4; ++k8) {
+          for (int k8 = 0; k8 < 2; ++k8) {
             const uint64_t ko = (uint64_t)(k8 * 2 * LBO) >> 4;
             mma_tf32(tX, al0 + ko, ph0 + ko, id, (kk > 0 || k8 > 0) ? 1u : 0u);
             mma_tf32(tX, ah0 + ko, pl0 + ko, id, 1u);
@@ -365,63 +403,63 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           commit(&bar[B_EMPTY + s]);
           ++q;
         }
-        commit(&bar[B_XPF + b]);
+        commit(&bar[B_XPF]);
+        ++nsc;
         return true;
       };
-      auto s2 = [&](const Walk& w, int chunk) -> bool {
-        if (!wait_bar(&bar[B_XF], (uint32_t)(chunk & 1), abort, wait_ns)) return false;
+      auto s2 = [&](const Walk& w) -> bool {
+        const int b = g & 1;
+        if (!wait_bar(&bar[B_XF + b], (uint32_t)((g >> 1) & 1), abort, wait_ns)) return false;
         if (need_se) {
           if (!wait_bar(&bar[B_SE], (uint32_t)((nd - 1) & 1), abort, wait_ns)) return false;
           need_se = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int nh = s2_halves(w), nk = s2_kblocks(w);
-        const int N1 = min(w.N, HALF), N2 = w.N - N1;
-        for (int h = 0; h < nh; ++h) {
-          const uint32_t id = idesc_tf32(TM, h ? N2 : N1);
-          const uint32_t dS = tS + (uint32_t)(h * HALF);
-          bool& fresh = h ? fresh1 : fresh0;
-          for (int kk = 0; kk < nk; ++kk) {
-            int s;
-            if (!take(s)) return false;
-            const uint32_t st = sbase + OFF_STAGE + s * STAGE;
-            const uint32_t xo = (uint32_t)kk * 8 * LBO;
-            const uint64_t xh0 = desc(xh + xo, SBO_X), xl0 = desc(xl + xo, SBO_X);
-            const uint64_t bh0 = desc(st, SBO_OP), bl0 = desc(st + 1024, SBO_OP);
+        const uint32_t id = idesc_tf32(TM, w.N);
+        const uint32_t xh = sbase + OFF_X + b * XBUF, xl = xh + XLO;
+        const int nk = s2_kblocks(w);
+        for (int kk = 0; kk < nk; ++kk) {
+          int s;
+          if (!take(s)) return false;
+          const uint32_t st = sbase + OFF_STAGE + s * STAGE;
+          const uint32_t xo = (uint32_t)kk * 4 * LBO;
+          const uint64_t xh0 = desc(xh + xo, SBO_X), xl0 = desc(xl + xo, SBO_X);
+          const uint64_t bh0 = desc(st, SBO_OP), bl0 = desc(st + LO_OP, SBO_OP);
 #pragma unroll
-            for (int k8 = 0; k8 < 4; ++k8) {
-              const uint64_t ko = (uint64_t)(k8 * 2 * LBO) >> 4;
-              mma_tf32(dS, xl0 + ko, bh0 + ko, id, fresh ? 0u : 1u);
-              fresh = false;
-              mma_tf32(dS, xh0 + ko, bl0 + ko, id, 1u);
-              mma_tf32(dS, xh0 + ko, bh0 + ko, id, 1u);
-            }
-            commit(&bar[B_EMPTY + s]);
-            ++q;
+          for (int k8 = 0; k8 < 2; ++k8) {
+            const uint64_t ko = (uint64_t)(k8 * 2 * LBO) >> 4;
+            mma_tf32(tS, xl0 + ko, bh0 + ko, id, fresh ? 0u : 1u);
+            fresh = false;
+            mma_tf32(tS, xh0 + ko, bl0 + ko, id, 1u);
+            mma_tf32(tS, xh0 + ko, bh0 + ko, id, 1u);
           }
+          commit(&bar[B_EMPTY + s]);
+          ++q;
         }
-        commit(&bar[B_XE]);
+        commit(&bar[B_XE + b]);
+        ++g;
         if (drain_point(w)) {
           commit(&bar[B_SF]);
           ++nd;
           need_se = true;
-          fresh0 = fresh1 = true;
+          fresh = true;
         }
         return true;
       };
-      Walk cur;
-      walk_start(cur, blocks, items, tasks, cta_task, t0, t1, drain_terms);
-      if (cur.valid) {
-        ok = s1(cur, c++);
-        int c2 = 0;
-        while (ok) {
-          Walk nxt = cur;
-          walk_next(nxt);
-          if (nxt.valid && !(ok = s1(nxt, c++))) break;
-          if (!(ok = s2(cur, c2++))) break;
-          if (!nxt.valid) break;
-          cur = nxt;
+      Walk s1w, s2w;
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
+      s1w = s2w;
+      if (s1w.valid) {
+        ok = s1(s1w);
+        walk_next_sc(s1w);
+      }
+      while (ok && s2w.valid) {
+        if (last_piece(s2w) && s1w.valid) {
+          if (!(ok = s1(s1w))) break;
+          walk_next_sc(s1w);
         }
+        if (!(ok = s2(s2w))) break;
+        walk_next(s2w);
       }
       if (!ok) {
         *abort = 1;
@@ -440,34 +478,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r = quarter * 32 + lane;  // TMEM lane = tile row
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     float2* const part_base = reinterpret_cast<float2*>(scratch);
-    int nd = 0;  // drains done
+    int nd = 0, nsc = 0, g = 0;  // drains done, super-chunks and pieces converted
     bool ok = true;
-    auto convert = [&](const Walk& w, int chunk) -> bool {
-      const int b = chunk & 1;
-      if (!wait_bar_warp(&bar[B_XPF + b], (uint32_t)((chunk >> 1) & 1), abort, wait_ns)) return false;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t tX = tmem_base + TCOL_X + 64 * b + lane_base;
-      uint32_t q[64];
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(q[16 * c4 + 0]), "=r"(q[16 * c4 + 1]), "=r"(q[16 * c4 + 2]), "=r"(q[16 * c4 + 3]),
-              "=r"(q[16 * c4 + 4]), "=r"(q[16 * c4 + 5]), "=r"(q[16 * c4 + 6]), "=r"(q[16 * c4 + 7]),
-              "=r"(q[16 * c4 + 8]), "=r"(q[16 * c4 + 9]), "=r"(q[16 * c4 + 10]), "=r"(q[16 * c4 + 11]),
-              "=r"(q[16 * c4 + 12]), "=r"(q[16 * c4 + 13]), "=r"(q[16 * c4 + 14]), "=r"(q[16 * c4 + 15])
-            : "r"(tX + 16 * c4));
+    auto convert = [&](const Walk& w) -> bool {
+      if (w.p == 0) {
+        // X' of this super-chunk complete
+        if (!wait_bar_warp(&bar[B_XPF], (uint32_t)(nsc & 1), abort, wait_ns)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
+      uint32_t q[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+            "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]),
+            "=r"(q[16]), "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]),
+            "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+          : "r"(tX + lane_base + (uint32_t)(PW * w.p)));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      arrive(&bar[B_XPE + b]);
-      // X of the previous chunk must have been read by its stage-2 MMAs
-      if (chunk >= 1 && !wait_bar_warp(&bar[B_XE], (uint32_t)((chunk - 1) & 1), abort, wait_ns)) return false;
+      if (last_piece(w)) {
+        // every piece of the super-chunk is read: X' may be overwritten
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        arrive(&bar[B_XPE]);
+        ++nsc;
+      }
+      // the piece buffer of two pieces back must have been read by its MMAs
+      const int b = g & 1;
+      if (g >= 2 && !wait_bar_warp(&bar[B_XE + b], (uint32_t)(((g >> 1) - 1) & 1), abort, wait_ns)) return false;
       const float al = (float)w.it.alpha;
+      unsigned char* xb = sgen + OFF_X + b * XBUF;
 #pragma unroll
-      for (int j = 0; j < JC; j += 4) {
+      for (int j = 0; j < PW; j += 4) {
         float4 hv, lv;
-        float x0 = al * __uint_as_float(q[j]), x1 = al * __uint_as_float(q[j + 1]);
-        float x2 = al * __uint_as_float(q[j + 2]), x3 = al * __uint_as_float(q[j + 3]);
+        const float x0 = al * __uint_as_float(q[j]), x1 = al * __uint_as_float(q[j + 1]);
+        const float x2 = al * __uint_as_float(q[j + 2]), x3 = al * __uint_as_float(q[j + 3]);
         hv.x = __uint_as_float(tf32(x0));
         hv.y = __uint_as_float(tf32(x1));
         hv.z = __uint_as_float(tf32(x2));
@@ -477,21 +521,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         lv.z = __uint_as_float(tf32(x2 - hv.z));
         lv.w = __uint_as_float(tf32(x3 - hv.w));
         const uint32_t o = x_off(r, j);
-        *reinterpret_cast<float4*>(sgen + OFF_XH + o) = hv;
-        *reinterpret_cast<float4*>(sgen + OFF_XL + o) = lv;
+        *reinterpret_cast<float4*>(xb + o) = hv;
+        *reinterpret_cast<float4*>(xb + XLO + o) = lv;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      arrive(&bar[B_XF]);
+      arrive(&bar[B_XF + b]);
+      ++g;
       return true;
     };
     // S (FP32, TMEM) is added to the task's partial tile of float pairs (hi,
-    // lo) by a TwoSum (Knuth) on the FP32 pipe; the first drain of a task
-    // stores.  N columns of every row are written; the reduction reads the
-    // valid ones only.
+    // lo), stored column by column (element (r, c) at c * 128 + r, so a warp's
+    // lanes touch consecutive pairs), by a TwoSum (Knuth) on the FP32 pipe;
+    // the first drain of a task stores.  N columns are written; the reduction
+    // reads the valid rows and columns only.
     auto drain = [&](long long part, int N, bool first) -> bool {
       if (!wait_bar_warp(&bar[B_SF], (uint32_t)(nd & 1), abort, wait_ns)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      float2* d = part_base + part + (size_t)r * TNMAX;
+      float2* d = part_base + part + r;
       for (int c0 = 0; c0 < N; c0 += 32) {
         uint32_t v[32];
         asm volatile(
@@ -508,17 +554,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (first) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (j < nc) d[c0 + j] = make_float2(__uint_as_float(v[j]), 0.0f);
+            if (j < nc) d[(size_t)(c0 + j) * TM] = make_float2(__uint_as_float(v[j]), 0.0f);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             if (j >= nc) break;
             const float x = __uint_as_float(v[j]);
-            const float2 a = d[c0 + j];
+            const float2 a = d[(size_t)(c0 + j) * TM];
             const float sum = __fadd_rn(a.x, x);
             const float bv = __fsub_rn(sum, a.x);
             const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
-            d[c0 + j] = make_float2(sum, __fadd_rn(a.y, e));
+            d[(size_t)(c0 + j) * TM] = make_float2(sum, __fadd_rn(a.y, e));
           }
         }
       }
@@ -529,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     };
     Walk w;
     walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
-    int chunk = 0, drains_in_task = 0, last_t = -1;
+    int drains_in_task = 0, last_t = -1;
     bool pend = false, pend_first = false;
     long long pend_part = 0;
     int pend_N = 0;
@@ -538,7 +584,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         last_t = w.t;
         drains_in_task = 0;
       }
-      if (!(ok = convert(w, chunk++))) break;
+      if (!(ok = convert(w))) break;
       if (pend && !(ok = drain(pend_part, pend_N, pend_first))) break;
       pend = drain_point(w);
       if (pend) {
@@ -570,19 +616,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
 }
 
-// partial tiles are TM x TNMAX (row stride TNMAX); CTA (tile, y) sums rows
-// [16 y, 16 y + 16) of a tile over its chunks in fixed order
+// partial tiles are TM x TNMAX float pairs stored column by column (element
+// (r, c) at c * TM + r); CTA (tile, y) sums columns [32 y, 32 y + 32) of a
+// tile over its chunks in fixed order, thread t taking row t % 128 of every
+// second column
 __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiReduce* __restrict__ reds,
                                const double* __restrict__ scratch) {
   const HpsiReduce rd = reds[blockIdx.x];
   const HpsiBlock bk = blocks[rd.block];
   const int nvalid = min(TNMAX, bk.n - rd.c0);
-  const int c = threadIdx.x;
-  if (c >= nvalid) return;
-  for (int r = blockIdx.y * 16; r < blockIdx.y * 16 + 16; ++r) {
-    const int gr = rd.r0 + r;
-    if (gr >= bk.m) break;
-    const float2* part = reinterpret_cast<const float2*>(scratch + rd.part0) + (size_t)r * TNMAX + c;
+  const int r = threadIdx.x & (TM - 1), gr = rd.r0 + r;
+  if (gr >= bk.m) return;
+  const int cend = min(nvalid, (int)blockIdx.y * 32 + 32);
+  for (int c = blockIdx.y * 32 + (int)(threadIdx.x >> 7); c < cend; c += 2) {
+    const float2* part = reinterpret_cast<const float2*>(scratch + rd.part0) + (size_t)c * TM + r;
     double acc = 0.0;
     for (int p = 0; p < rd.nparts; ++p) {
       const float2 v = part[(long long)p * TM * TNMAX];
@@ -633,13 +680,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over the pool: 256 floats (one unit) per row, `rows` rows per box
+// 2D map over the pool: 256 floats (one unit) per row; a box is 128 floats
+// (half a unit: one k-block of 16) by `rows` units
 void make_map(CUtensorMap* m, const void* pool, size_t units, int rows) {
   auto fn = encode_fn();
   if (!fn) throw std::runtime_error("cuda: cuTensorMapEncodeTiled is not available");
   cuuint64_t dims[2] = {(cuuint64_t)kTcUnitFloats, (cuuint64_t)units};
   cuuint64_t strides[1] = {(cuuint64_t)kTcUnitFloats * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)kTcUnitFloats, (cuuint32_t)rows};
+  cuuint32_t box[2] = {(cuuint32_t)(kTcUnitFloats / 2), (cuuint32_t)rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(pool), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -664,17 +712,17 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
   if (L.ncta > 0) {
     if (!L.pool || L.units == 0) throw std::runtime_error("internal: tcgen05 contraction without a split pool");
     if (((uintptr_t)L.pool & 15) != 0) throw std::runtime_error("internal: split pool not 16-byte aligned");
-    CUtensorMap m32, m16;
+    CUtensorMap m32, m64;
     make_map(&m32, L.pool, L.units, 32);
-    make_map(&m16, L.pool, L.units, 16);
-    hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m16, L.blocks, L.items, L.tasks, L.cta_off,
+    make_map(&m64, L.pool, L.units, 64);
+    hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m64, L.blocks, L.items, L.tasks, L.cta_off,
                                                           L.cta_task, L.scratch, err, wait_ns,
                                                           L.drain_terms);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }
   if (L.nreds > 0) {
-    hpsi_tc_reduce<<<dim3(L.nreds, TM / 16), TNMAX, 0, st>>>(L.blocks, L.reds, L.scratch);
+    hpsi_tc_reduce<<<dim3(L.nreds, TNMAX / 32), 256, 0, st>>>(L.blocks, L.reds, L.scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc reduce: ") + cudaGetErrorString(e));
   }

@@ -21,13 +21,15 @@ constexpr int TM = kTcTileM, TNMAX = kTcTileN;
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // tensor-pipe work of one item on a tile of width N, in units of one
-// stage-1 k-block (128 x 64 x 32 in three TF32 products), plus a fixed
-// per-chunk overhead
+// k-block of 16 at MMA width 256 (128 x 256 x 16 in three TF32 products):
+// stage 1 per super-chunk of 256 columns of psi, stage 2 per 32-column
+// piece, plus a little for the conversion of each piece
 double item_cost(int ka, int kb, int N) {
   double c = 0.0;
-  for (int jc = 0; jc < kb; jc += 64) {
-    const int kbl = std::min(2, ceil_div(kb - jc, 32));
-    c += ceil_div(ka, 32) + kbl * (N / 64.0) + 0.5;
+  for (int jc = 0; jc < kb; jc += 256) {
+    const int w = std::min(256, kb - jc);
+    c += ceil_div(ka, 16) * (((w + 15) & ~15) / 256.0);
+    for (int p = 0; p < w; p += 32) c += ceil_div(std::min(32, w - p), 16) * (N / 256.0) + 0.1;
   }
   return c;
 }
@@ -200,7 +202,7 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
         for (int c = 0; c < nch; ++c) {
           const int i0 = bk.item_begin + cuts[c], cnt = cuts[c + 1] - cuts[c];
           plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
-          double tc = 2.0;  // drain
+          double tc = 1.0;  // drain
           for (int k = i0; k < i0 + cnt; ++k) tc += item_cost(plan.items[k].ka, plan.items[k].kb, N);
           tcost.push_back(tc);
           part += (long long)TM * TNMAX;

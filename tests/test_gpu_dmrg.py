@@ -246,22 +246,34 @@ def test_eigh_batches_larger_than_one_launch(pkg):
         assert np.abs(V @ V.T - np.eye(len(w))).max() < 1e-11
 
 
-def random_hpsi_problem(rng, n_blocks, max_dim, max_items, big=False):
+def random_hpsi_problem(rng, n_blocks, max_dim, max_items, big=False, shapes=None):
     """Sector-block contraction sigma += alpha op(A) P op(B)^T with ragged
-    sizes (several 64-wide tiles and tails), both transposes, identities."""
+    sizes (several tiles and tails), both transposes, identities.  With
+    `shapes` = [(m, n, [(ka, kb), ...]), ...] the block and item sizes are
+    the given ones (no identities)."""
     A_parts, P_parts, B_parts = [], [], []
     ao = po = bo = co = 0
     blocks, items, refs = [], [], []
-    for _ in range(n_blocks):
-        m = int(rng.integers(1, max_dim))
-        n = int(rng.integers(1, max_dim))
+    if shapes is not None:
+        n_blocks = len(shapes)
+    for bi in range(n_blocks):
+        if shapes is not None:
+            m, n, kk = shapes[bi]
+        else:
+            m = int(rng.integers(1, max_dim))
+            n = int(rng.integers(1, max_dim))
+            kk = [None] * int(rng.integers(1, max_items + 1))
         ib = len(items)
         ref = np.zeros((m, n))
-        for _ in range(int(rng.integers(1, max_items + 1))):
-            a_id = int(rng.random() < 0.15)
-            b_id = int(rng.random() < 0.15) if not a_id else 0
-            ka = m if a_id else int(rng.integers(1, max_dim))
-            kb = n if b_id else int(rng.integers(1, max_dim))
+        for kab in kk:
+            if kab is not None:
+                a_id = b_id = 0
+                ka, kb = kab
+            else:
+                a_id = int(rng.random() < 0.15)
+                b_id = int(rng.random() < 0.15) if not a_id else 0
+                ka = m if a_id else int(rng.integers(1, max_dim))
+                kb = n if b_id else int(rng.integers(1, max_dim))
             ta, tb = int(rng.integers(0, 2)), int(rng.integers(0, 2))
             alpha = float(rng.standard_normal())
             Pm = rng.standard_normal((ka, kb))
@@ -323,7 +335,7 @@ def test_fused_hpsi_many_items_split_into_chunks(pkg):
 
 
 def test_fused_hpsi_tcgen05_chunks_and_tails(pkg):
-    """tcgen05 kernel (128 x 64 sigma tiles): blocks spanning several row and
+    """tcgen05 kernel (128 x 256 sigma tiles): blocks spanning several row and
     column tiles with ragged tails, hundreds of items split into chunks;
     bitwise reproducible, and equal to the mma.sync kernel within the split
     tolerance."""
@@ -341,3 +353,33 @@ def test_fused_hpsi_tcgen05_chunks_and_tails(pkg):
         got = C1[off:off + m * n].reshape(m, n)
         assert np.abs(got - ref).max() < 3e-5 * scale
         assert np.abs(got - C3[off:off + m * n].reshape(m, n)).max() < 3e-5 * scale
+
+
+@pytest.mark.parametrize("drain", [0, 1024])
+def test_fused_hpsi_tcgen05_super_chunk_edges(pkg, drain):
+    """tcgen05 kernel at the edges of its blocking: inner dimensions of psi
+    (kb) at and around the 256-column stage-1 width, the 32-column pieces and
+    the 16-deep k-blocks; ka of 1, 15, 16, 17 and more than 256; sigma tiles
+    of one column and of 256 plus a tail; drains after every item and after
+    1024 terms.  Bitwise reproducible, within the split tolerance of numpy."""
+    rng = np.random.default_rng(23)
+    shapes = [
+        (130, 257, [(1, 256), (15, 257), (16, 32), (17, 33), (300, 512), (33, 513)]),
+        (7, 1, [(16, 16), (40, 17), (5, 255), (257, 1)]),
+        (256, 300, [(64, 48), (129, 288), (31, 600), (2, 31)]),
+        (1, 16, [(260, 270)]),
+    ]
+    A, P, B, clen, blocks, items, refs = random_hpsi_problem(rng, 0, 0, 0, shapes=shapes)
+    pkg.set_kernel_tc_drain_terms(drain)
+    try:
+        C1 = np.zeros(clen)
+        C2 = np.zeros(clen)
+        pkg.ops.hpsi_contract(A, P, B, C1, blocks, items, precision=4)
+        pkg.ops.hpsi_contract(A, P, B, C2, blocks, items, precision=4)
+    finally:
+        pkg.set_kernel_tc_drain_terms(1024)
+    assert np.array_equal(C1, C2)
+    for off, m, n, ref in refs:
+        scale = np.abs(ref).max()
+        got = C1[off:off + m * n].reshape(m, n)
+        assert np.abs(got - ref).max() < 3e-5 * scale
