@@ -1447,6 +1447,27 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
                  "<=64 %.2f <=128 %.2f <=256 %.2f <=512 %.2f >512 %.2f\n",
                  terms.size(), P.blk.size(), nit, tot, hist[0] / tot, hist[1] / tot, hist[2] / tot,
                  hist[3] / tot, hist[4] / tot, hist[5] / tot, hist[6] / tot);
+    // tensor work of the tcgen05 blocking (128 x 256 sigma tiles, stage 1 in
+    // 256-column super-chunks, k-blocks of 16) over the algorithmic work
+    // (stage 1 once per row tile and group of g column tiles, g = 1, 2, 4)
+    double a1 = 0.0, a2 = 0.0, e1[3] = {0.0, 0.0, 0.0}, e2 = 0.0;
+    auto r16 = [](int x) { return (double)((x + 15) & ~15); };
+    for (size_t b = 0; b < P.blk.size(); ++b)
+      for (auto& it : per[b]) {
+        const int m = P.blk[b].rows, n = P.blk[b].cols;
+        const double mt = 128.0 * ((m + 127) / 128);
+        const int nt = (n + 255) / 256;
+        const int ka = it.A ? it.ka : m, kb = it.B ? it.kb : n;
+        a1 += (double)m * ka * kb;
+        a2 += (double)m * kb * n;
+        const double s1 = mt * r16(ka) * ((kb / 256) * 256.0 + (kb % 256 ? r16(kb % 256) : 0.0));
+        for (int q = 0; q < 3; ++q) e1[q] += s1 * ((nt + (1 << q) - 1) >> q);
+        e2 += mt * r16(kb) * (256.0 * (n / 256) + (n % 256 ? r16(n % 256) : 0.0));
+      }
+    const double am = std::max(a1, 1.0);
+    std::fprintf(stderr, "hpsi tc blocking: stage-1 work x%.2f (x%.2f, x%.2f shared by 2, 4 column tiles), stage-2 "
+                 "work x%.2f of algorithmic (stage-1 flops / all %.2f)\n", e1[0] / am, e1[1] / am, e1[2] / am,
+                 e2 / std::max(a2, 1.0), a1 / std::max(a1 + a2, 1.0));
   }
   const double tp1 = now_s();
   stats_.t_plan_items += tp1 - tp0;

@@ -539,6 +539,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;");
       float2* d = part_base + part + r;
       for (int c0 = 0; c0 < N; c0 += 32) {
+        // N is a multiple of 16: the chunk has 16 or 32 valid columns.  The
+        // partials of the chunk are all loaded before they are used, so their
+        // latencies overlap (and overlap the TMEM load).
+        const bool two = N - c0 > 16;
+        float2 a[32];
+        if (!first) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] = d[(size_t)(c0 + j) * TM];
+          if (two) {
+#pragma unroll
+            for (int j = 16; j < 32; ++j) a[j] = d[(size_t)(c0 + j) * TM];
+          }
+        }
         uint32_t v[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -550,22 +563,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(tS + lane_base + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const int nc = min(32, N - c0);
-        if (first) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nc) d[(size_t)(c0 + j) * TM] = make_float2(__uint_as_float(v[j]), 0.0f);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j >= nc) break;
-            const float x = __uint_as_float(v[j]);
-            const float2 a = d[(size_t)(c0 + j) * TM];
-            const float sum = __fadd_rn(a.x, x);
-            const float bv = __fsub_rn(sum, a.x);
-            const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
-            d[(size_t)(c0 + j) * TM] = make_float2(sum, __fadd_rn(a.y, e));
+        auto put = [&](int j) {
+          const float x = __uint_as_float(v[j]);
+          if (first) {
+            d[(size_t)(c0 + j) * TM] = make_float2(x, 0.0f);
+          } else {
+            const float sum = __fadd_rn(a[j].x, x);
+            const float bv = __fsub_rn(sum, a[j].x);
+            const float e = __fadd_rn(__fsub_rn(a[j].x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
+            d[(size_t)(c0 + j) * TM] = make_float2(sum, __fadd_rn(a[j].y, e));
           }
+        };
+#pragma unroll
+        for (int j = 0; j < 16; ++j) put(j);
+        if (two) {
+#pragma unroll
+          for (int j = 16; j < 32; ++j) put(j);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
