@@ -639,7 +639,9 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     void* pool = nullptr;
     size_t scr;
     if (tc) {
-      dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp, be->sm_count());
+      const int tc_ctas = dmrg::hpsi_tc_max_ctas();
+      dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp,
+                            tc_ctas > 0 ? tc_ctas : be->sm_count());
       tasks = tp.tasks;
       reds = tp.reds;
       scr = tp.scratch;
@@ -654,7 +656,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     size_t oj = al(orr + reds.size() * sizeof(dmrg::HpsiReduce));
     size_t oco = al(oj + (tp.op_jobs.size() + tp.psi_jobs.size()) * sizeof(dmrg::SplitJob));
     size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
-    size_t os = al(oct + tp.cta_task.size() * sizeof(int));
+    size_t os = al(oct + tp.cta_task.size() * sizeof(dmrg::TcSlot));
     char* d = (char*)be->alloc(os + scr * sizeof(double) + 256);
     if (!hb.empty()) be->copy_h2d(d + ob, hb.data(), hb.size() * sizeof(dmrg::HpsiBlock));
     if (!hi.empty()) be->copy_h2d(d + oi, hi.data(), hi.size() * sizeof(dmrg::HpsiItem));
@@ -669,13 +671,13 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
         be->split((const dmrg::SplitJob*)(d + oj), (int)jobs.size(), (float*)pool);
       }
       if (!tp.cta_off.empty()) be->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
-      if (!tp.cta_task.empty()) be->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(int));
+      if (!tp.cta_task.empty()) be->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(dmrg::TcSlot));
       dmrg::TcLaunch L;
       L.blocks = (const dmrg::HpsiBlock*)(d + ob);
       L.items = (const dmrg::TcItem*)(d + oc);
       L.tasks = (const dmrg::HpsiTask*)(d + ot);
       L.cta_off = (const int*)(d + oco);
-      L.cta_task = (const int*)(d + oct);
+      L.cta_task = (const dmrg::TcSlot*)(d + oct);
       L.ncta = (int)tp.cta_off.size() - 1;
       L.reds = (const dmrg::HpsiReduce*)(d + orr);
       L.nreds = (int)reds.size();

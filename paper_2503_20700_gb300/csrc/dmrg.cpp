@@ -1493,8 +1493,9 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   if (tc) {
     if (plan.tc_pool) be_->free(plan.tc_pool);
     plan.tc_pool = nullptr;
+    const int tc_ctas = hpsi_tc_max_ctas();
     hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp,
-                    be_->sm_count());
+                    tc_ctas > 0 ? tc_ctas : be_->sm_count());
     if (opt_.debug_bounds) {
       const std::string bad = tc_plan_check(tp, blocks);
       if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
@@ -1517,7 +1518,7 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   size_t opj = al(oj + tp.op_jobs.size() * sizeof(SplitJob));
   size_t oco = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
   size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
-  size_t os = al(oct + tp.cta_task.size() * sizeof(int));
+  size_t os = al(oct + tp.cta_task.size() * sizeof(TcSlot));
   size_t total = os + scr * sizeof(double) + 256;
   if (plan.dev) be_->free(plan.dev);
   plan.dev = be_->alloc(total);
@@ -1539,13 +1540,13 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
     be_->copy_h2d(plan.d_psi_jobs, tp.psi_jobs.data(), tp.psi_jobs.size() * sizeof(SplitJob));
   if (tc) {
     if (!tp.cta_off.empty()) be_->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
-    if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(int));
+    if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(TcSlot));
     plan.tc = TcLaunch();
     plan.tc.blocks = plan.d_blocks;
     plan.tc.items = plan.d_tcitems;
     plan.tc.tasks = plan.d_tasks;
     plan.tc.cta_off = (const int*)(d + oco);
-    plan.tc.cta_task = (const int*)(d + oct);
+    plan.tc.cta_task = (const TcSlot*)(d + oct);
     plan.tc.ncta = (int)tp.cta_off.size() - 1;
     plan.tc.reds = plan.d_reds;
     plan.tc.nreds = (int)reds.size();

@@ -1,5 +1,6 @@
 // tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh), persistent and
-// warp-specialised, with operand tiles brought in by TMA.
+// warp-specialised, with operand tiles brought in by TMA, in clusters of
+// kTcCluster CTAs.
 //
 // Per item of a task (a 128 x N, N <= 256, sigma tile) and per super-chunk
 // of up to 256 columns of psi (columns [c, c+256) of P):
@@ -9,6 +10,15 @@
 //   stage 2:  S += X op(B)(tile cols, p)^T                      (TMEM, 128 x N)
 // Stage 1 uses N = 256 (one A panel fetch per 256 columns of psi) and stage 2
 // the full tile width, so the MMAs are as wide as the tile allows.
+//
+// The CTAs of a cluster walk the same items; CTAs whose tiles have the same
+// rows (a group) need the same X, so stage 1 of the super-chunks is dealt
+// round-robin over the group, and the CTA that computes a super-chunk writes
+// its pieces into the X buffers of every CTA of the group (distributed shared
+// memory) and arrives on their piece barriers.  Each CTA's MMA issuer
+// signals the end of its reads of a piece buffer to every CTA of the cluster
+// (multicast commit), so a buffer is rewritten once the whole cluster has read
+// it.  A ghost entry (a cluster slot without a tile) only keeps that count.
 //
 // Shared memory (bytes): two X piece buffers (each hi | lo, 128 x 32, 16 KB
 // per plane, 1 KB between 8-row groups) and three 48 KB stages, each holding
@@ -23,14 +33,15 @@
 // full/empty mbarriers), 1 MMA issuer (one lane; owns the TMEM allocation),
 // 2..5 converters (TMEM lanes 32 (w % 4) .. +31: X' pieces -> alpha X' as
 // TF32 hi/lo planes, double-buffered, and the drains of S into the task's
-// partial tile of float pairs).  The MMA order issues stage 1 of the next
-// super-chunk before stage 2 of the last piece of the current one, so the
-// tensor pipe runs it while the last piece is converted.  S is drained once
+// partial tile of float pairs).  The MMA issuer runs stage 1 of this CTA's
+// next super-chunk before stage 2 of the last piece of its current one, so
+// the tensor pipe runs it while that piece is converted.  S is drained once
 // the items accumulated in FP32 since the last drain reach drain_terms terms
 // of psi's column index (sum of kb; 0: after every item) and at the end of
 // every task.  Every wait gives up after the launch's wait bound (2 s of wall
-// clock by default): the CTA then sets the error flag, waits (bounded by
-// 2 s) for its copies and MMAs in flight, frees TMEM and returns.
+// clock by default): the CTA then sets the error flag and the abort flag of
+// every CTA of the cluster, waits (bounded by 2 s) for its copies and MMAs in
+// flight, frees TMEM and leaves with the cluster.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -65,10 +76,14 @@ constexpr int A_BYTES = 16384, P_BYTES = 32768, B_BYTES = 32768;
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
 constexpr int NTHREADS = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr int C = kTcCluster;
+static_assert(C == 2, "the X piece exchange is written for groups of at most two CTAs");
+constexpr unsigned long long kDrainCopiesNs = 100000ull;  // in-flight peer copies land within this
+constexpr uint16_t kClusterMask = (uint16_t)((1u << C) - 1);
 
 // barriers
 enum { B_FULL = 0, B_EMPTY = B_FULL + NSTAGE, B_XPF = B_EMPTY + NSTAGE, B_XPE, B_XF, B_XE = B_XF + 2,
-       B_SF = B_XE + 2, B_SE, B_DONE, B_COUNT };
+       B_XA = B_XE + 2, B_SF = B_XA + 2, B_SE, B_DONE, B_COUNT };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -99,12 +114,44 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
+// one arrival on the barrier at the same offset in every CTA of the cluster,
+// once the MMAs issued so far by this thread have completed
+__device__ __forceinline__ void commit_all(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(kClusterMask)
+      : "memory");
+}
 __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void arrive_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// cluster shared address of this CTA's shared address `saddr` in CTA `rank`
+__device__ __forceinline__ uint32_t map_to(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+// copy of `bytes` of this CTA's shared memory into a peer's (cluster
+// addresses dst and its barrier), by the bulk copy engine; the peer's barrier
+// receives the bytes as transaction count
+__device__ __forceinline__ void copy_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "r"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // TMA copy of the box at (x floats, y units) of `map` into shared memory
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -119,45 +166,67 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// a probe of the phase with the given parity; CL: acquire at cluster scope
+// (the phase may have been completed by arrivals from other CTAs)
+template <bool CL>
 __device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if (CL)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
   return done != 0;
 }
 // a probe that may suspend the thread for up to ~1 us while the phase is
 // incomplete (frees the issue slot for the warps that share the scheduler)
+template <bool CL>
 __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
-      : "memory");
+  if (CL)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
   return done != 0;
 }
 // bounded wait on the phase with the given parity; false after wait_ns of
-// wall clock (0: after the first probe), or at once when another role has
-// aborted (abort != 0)
+// wall clock (0: after the first probe), or at once when a role of this CTA
+// or of another CTA of the cluster has aborted (abort != 0)
+template <bool CL = false>
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort,
                                          unsigned long long wait_ns) {
-  if (test_wait(bar, parity)) return true;
+  if (test_wait<CL>(bar, parity)) return true;
   if (wait_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    if (try_wait(bar, parity)) return true;
+    if (try_wait<CL>(bar, parity)) return true;
     if (*abort) return false;
     if (global_ns() - t0 > wait_ns) return false;
   }
 }
 // the same, with one outcome for the whole warp (the converter warps issue
 // .sync.aligned TMEM loads right after their waits)
+template <bool CL = false>
 __device__ __forceinline__ bool wait_bar_warp(uint64_t* bar, uint32_t parity, volatile int* abort,
                                               unsigned long long wait_ns) {
-  const bool ok = wait_bar(bar, parity, abort, wait_ns);
+  const bool ok = wait_bar<CL>(bar, parity, abort, wait_ns);
   return __all_sync(0xffffffffu, ok);
 }
 // byte offset of element (r, k) (k multiple of 4) in a 32-wide X plane
@@ -165,27 +234,33 @@ __device__ __forceinline__ uint32_t x_off(int r, int k) {
   return (uint32_t)(r >> 3) * SBO_X + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16;
 }
 
-// The piece sequence of one CTA: its tasks in list order, their items, the
+// The piece sequence of one CTA: its list entries in order, their items, the
 // super-chunks of 256 columns of psi of every item and their 32-column pieces.
+// Every CTA of a cluster walks the same sequence (its entries name tasks of
+// the same items).
 struct Walk {
   const HpsiBlock* blocks;
   const TcItem* items;
   const HpsiTask* tasks;
-  const int* list;
+  const TcSlot* list;
   int t, t_end;
+  int rank;  // of this CTA in the cluster
+  TcSlot sl;
   HpsiTask tk;
   int N;    // MMA width of the tile (multiple of 16)
   int ii;   // item (global index)
   int k;    // item position within the task
   int jc;   // first column of the super-chunk
   int p;    // piece within the super-chunk
+  int sct;  // super-chunk within the task
   int acc;          // sum of kb over the items since the last drain, this one included
   int drain_terms;  // drain once acc reaches it
   TcItem it;
   bool valid;
 };
 __device__ __forceinline__ void walk_task(Walk& w) {
-  w.tk = w.tasks[w.list[w.t]];
+  w.sl = w.list[w.t];
+  w.tk = w.tasks[w.sl.task];
   const HpsiBlock bk = w.blocks[w.tk.block];
   const int nvalid = min(TNMAX, bk.n - w.tk.c0);
   w.N = (nvalid + 15) & ~15;
@@ -193,21 +268,28 @@ __device__ __forceinline__ void walk_task(Walk& w) {
   w.k = 0;
   w.jc = 0;
   w.p = 0;
+  w.sct = 0;
   w.it = w.items[w.ii];
   w.acc = w.it.kb;
 }
 __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, const TcItem* items,
-                                           const HpsiTask* tasks, const int* list, int t0, int t1,
-                                           int drain_terms) {
+                                           const HpsiTask* tasks, const TcSlot* list, int t0, int t1,
+                                           int drain_terms, int rank) {
   w.drain_terms = drain_terms;
   w.blocks = blocks;
   w.items = items;
   w.tasks = tasks;
   w.list = list;
+  w.rank = rank;
   w.t = t0;
   w.t_end = t1;
   w.valid = t0 < t1;
   if (w.valid) walk_task(w);
+}
+__device__ __forceinline__ bool ghost(const Walk& w) { return w.sl.ghost != 0; }
+// stage 1 of the current super-chunk is this CTA's (dealt round-robin over the group)
+__device__ __forceinline__ bool owned(const Walk& w) {
+  return !w.sl.ghost && w.sct % w.sl.grpn == w.rank - w.sl.grp0;
 }
 __device__ __forceinline__ int sc_width(const Walk& w) { return min(W1, w.it.kb - w.jc); }
 __device__ __forceinline__ int sc_pieces(const Walk& w) { return (sc_width(w) + PW - 1) / PW; }
@@ -243,6 +325,7 @@ __device__ __forceinline__ void walk_next(Walk& w) {
     return;
   }
   w.p = 0;
+  ++w.sct;
   w.jc += W1;
   if (w.jc < w.it.kb) return;
   walk_next_item(w, drained);
@@ -252,14 +335,72 @@ __device__ __forceinline__ void walk_next_sc(Walk& w) {
   w.p = sc_pieces(w) - 1;
   walk_next(w);
 }
+// to the start of the next super-chunk whose stage 1 is this CTA's
+__device__ __forceinline__ void walk_next_owned(Walk& w) {
+  do walk_next_sc(w);
+  while (w.valid && !owned(w));
+}
+__device__ __forceinline__ void walk_first_owned(Walk& w) {
+  if (w.valid && !owned(w)) walk_next_owned(w);
+}
 __device__ __forceinline__ int s1_blocks(const Walk& w) { return (w.it.ka + 15) >> 4; }
 __device__ __forceinline__ int s2_kblocks(const Walk& w) { return min(2, (w.it.kb - w.jc - PW * w.p + 15) >> 4); }
+__device__ __forceinline__ bool same_sc(const Walk& a, const Walk& b) { return a.t == b.t && a.sct == b.sct; }
+
+// The issue order of stage 1, shared by the producer and the MMA issuer.
+// s1w is this CTA's next super-chunk to compute, `done` of its k-blocks
+// issued; `held` tells that X' holds a computed super-chunk whose last piece
+// s2w has not reached.  Before the piece at s2w:
+//  - nothing while X' is held;
+//  - the rest of stage 1 of s1w when its pieces start now, or when s2w is the
+//    last piece of this CTA's super-chunk and s1w comes right after it;
+//  - while s2w walks a super-chunk of the group's other CTA (or a ghost
+//    entry), a share of stage 1 of s1w proportional to the pieces walked, so
+//    that the tensor pipe interleaves it with those pieces.
+struct S1Order {
+  Walk w;
+  int done;
+  bool held;
+  int ht, hsct;  // the held super-chunk
+};
+__device__ __forceinline__ void s1_order_start(S1Order& o, const Walk& s2w) {
+  o.w = s2w;
+  walk_first_owned(o.w);
+  o.done = 0;
+  o.held = false;
+}
+// k-blocks of stage 1 of o.w to issue before the piece at s2w
+__device__ __forceinline__ int s1_now(S1Order& o, const Walk& s2w) {
+  if (o.held && o.ht == s2w.t && o.hsct == s2w.sct && last_piece(s2w)) o.held = false;
+  if (o.held || !o.w.valid) return 0;
+  const int nb = s1_blocks(o.w);
+  if (same_sc(o.w, s2w)) return nb - o.done;
+  if (owned(s2w)) {
+    if (!last_piece(s2w)) return 0;
+    Walk n = s2w;
+    walk_next_sc(n);
+    return (n.valid && same_sc(n, o.w)) ? nb - o.done : 0;
+  }
+  const int np = sc_pieces(s2w);
+  return max(0, (nb * (s2w.p + 1) + np - 1) / np - o.done);
+}
+// after k-blocks [done, done + k) were issued
+__device__ __forceinline__ void s1_issued(S1Order& o, const Walk& s2w, int k) {
+  o.done += k;
+  if (o.done < s1_blocks(o.w)) return;
+  o.held = true;
+  o.ht = o.w.t;
+  o.hsct = o.w.sct;
+  if (same_sc(o.w, s2w) && last_piece(s2w)) o.held = false;
+  walk_next_owned(o.w);
+  o.done = 0;
+}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     hpsi_tc_kernel(const __grid_constant__ CUtensorMap map32, const __grid_constant__ CUtensorMap map64,
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
-                   const int* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
+                   const TcSlot* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
                    unsigned long long wait_ns, int drain_terms) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[B_COUNT];
@@ -268,10 +409,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ int consumed;  // stage fills the MMA warp has waited for
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t sraw = smem_u32(smraw);
-  const uint32_t sbase = (sraw + 1023u) & ~1023u;
-  unsigned char* sgen = smraw + (sbase - sraw);
+  const uint32_t sbase = (sraw + 1023u) & ~1023u;  // the same offset in every CTA of the cluster
+  unsigned char* const sgen = smraw + (sbase - sraw);
+  const int rank = (int)cluster_rank();
   const int t0 = cta_off[blockIdx.x], t1 = cta_off[blockIdx.x + 1];
   volatile int* abort = &abort_flag;
+  // an aborting role stops the roles of every CTA of the cluster
+  auto abort_all = [&]() {
+    *abort = 1;
+    for (int j = 0; j < C; ++j)
+      if (j != rank)
+        asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(map_to(smem_u32(&abort_flag), j)),
+                     "r"(1)
+                     : "memory");
+    atomicExch(err, 1);
+  };
 
   if (tid == 0) {
     for (int i = 0; i < NSTAGE; ++i) {
@@ -281,8 +433,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XPF])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XPE])));
     for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XF + i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XE + i])));
+      // XF: one arrival (the converters of the CTA that owns the piece, or,
+      // for a piece from the peer, this CTA's converters expecting its bytes);
+      // XE: the MMA issuers of all CTAs of the cluster
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XF + i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar[B_XE + i])), "r"(C));
+      // XA: this CTA's converter threads, once they have seen the reads of
+      // two pieces back complete
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XA + i])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_SF])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_SE])));
@@ -298,6 +456,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  // the barriers of every CTA of the cluster are initialised before any
+  // arrival from a peer
+  cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tS = tmem_base + TCOL_S, tX = tmem_base + TCOL_X;
   int produced = 0;  // stage fills issued (producer lane)
@@ -313,11 +474,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         s = q % NSTAGE;
         return wait_bar(&bar[B_EMPTY + s], (uint32_t)(((q / NSTAGE) & 1) ^ 1), abort, wait_ns);
       };
-      // stage 1 of the super-chunk at w: per k-block of 16 of ka, the A tile
-      // (the tile's rows) and the P^T tile (256 rows from the super-chunk's first)
-      auto s1 = [&](const Walk& w) -> bool {
-        const int nb = s1_blocks(w);
-        for (int kk = 0; kk < nb; ++kk) {
+      // k-blocks [k0, k1) of stage 1 of the super-chunk at w: per k-block of 16
+      // of ka, the A tile (the tile's rows) and the P^T tile (256 rows from the
+      // super-chunk's first)
+      auto s1 = [&](const Walk& w, int k0, int k1) -> bool {
+        for (int kk = k0; kk < k1; ++kk) {
           int s;
           if (!acquire(s)) return false;
           const uint32_t st = sbase + OFF_STAGE + s * STAGE;
@@ -347,31 +508,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         return true;
       };
-      Walk s1w, s2w;
-      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
-      s1w = s2w;
-      if (s1w.valid) {
-        ok = s1(s1w);
-        walk_next_sc(s1w);
-      }
+      // the fill order of the MMA issuer: stage 1 in the order of s1_now,
+      // stage 2 of every piece of a tile
+      Walk s2w;
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
+      S1Order o;
+      s1_order_start(o, s2w);
       while (ok && s2w.valid) {
-        if (last_piece(s2w) && s1w.valid) {
-          if (!(ok = s1(s1w))) break;
-          walk_next_sc(s1w);
+        const int k = s1_now(o, s2w);
+        if (k > 0) {
+          if (!(ok = s1(o.w, o.done, o.done + k))) break;
+          s1_issued(o, s2w, k);
         }
-        if (!(ok = s2(s2w))) break;
+        if (!ghost(s2w) && !(ok = s2(s2w))) break;
         walk_next(s2w);
       }
-      if (!ok) {
-        *abort = 1;
-        atomicExch(err, 1);
-      }
+      if (!ok) abort_all();
       produced = q;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int q = 0, nd = 0, nsc = 0, g = 0;  // stage fills consumed, drains, super-chunks issued, pieces issued
+      int xfu0 = 0, xfu1 = 0;             // pieces received in buffers 0 and 1
       bool need_se = false, fresh = true, ok = true;
       auto take = [&](int& s) -> bool {
         s = q % NSTAGE;
@@ -379,13 +538,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         return true;
       };
-      auto s1 = [&](const Walk& w) -> bool {
-        // X' must have been read by the converters (every piece of the last super-chunk)
-        if (nsc >= 1 && !wait_bar(&bar[B_XPE], (uint32_t)((nsc - 1) & 1), abort, wait_ns)) return false;
+      // k-blocks [k0, k1) of stage 1 of the super-chunk at w
+      auto s1 = [&](const Walk& w, int k0, int k1) -> bool {
+        // X' must have been read by the converters (every piece of this CTA's last super-chunk)
+        if (k0 == 0 && nsc >= 1 && !wait_bar(&bar[B_XPE], (uint32_t)((nsc - 1) & 1), abort, wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t id = idesc_tf32(TM, (sc_width(w) + 15) & ~15);
         const int nb = s1_blocks(w);
-        for (int kk = 0; kk < nb; ++kk) {
+        for (int kk = k0; kk < k1; ++kk) {
           int s;
           if (!take(s)) return false;
           const uint32_t st = sbase + OFF_STAGE + s * STAGE;
@@ -403,13 +563,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           commit(&bar[B_EMPTY + s]);
           ++q;
         }
-        commit(&bar[B_XPF]);
-        ++nsc;
+        if (k1 == nb) {
+          commit(&bar[B_XPF]);
+          ++nsc;
+        }
         return true;
       };
       auto s2 = [&](const Walk& w) -> bool {
         const int b = g & 1;
-        if (!wait_bar(&bar[B_XF + b], (uint32_t)((g >> 1) & 1), abort, wait_ns)) return false;
+        // the converters have seen piece g - 2 read everywhere, and the piece is
+        // in this CTA's buffer b (written by whichever CTA of the group owns it)
+        if (!wait_bar(&bar[B_XA + b], (uint32_t)((g >> 1) & 1), abort, wait_ns)) return false;
+        int& xfu = b ? xfu1 : xfu0;
+        if (!wait_bar<true>(&bar[B_XF + b], (uint32_t)(xfu & 1), abort, wait_ns)) return false;
+        ++xfu;
         if (need_se) {
           if (!wait_bar(&bar[B_SE], (uint32_t)((nd - 1) & 1), abort, wait_ns)) return false;
           need_se = false;
@@ -436,7 +603,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           commit(&bar[B_EMPTY + s]);
           ++q;
         }
-        commit(&bar[B_XE + b]);
+        // buffer b of every CTA may be rewritten once all of them have read it
+        commit_all(&bar[B_XE + b]);
         ++g;
         if (drain_point(w)) {
           commit(&bar[B_SF]);
@@ -446,31 +614,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         return true;
       };
-      Walk s1w, s2w;
-      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
-      s1w = s2w;
-      if (s1w.valid) {
-        ok = s1(s1w);
-        walk_next_sc(s1w);
-      }
+      // a ghost entry computes nothing but keeps the cluster's count of the
+      // reads of every piece buffer: one arrival per piece, each once this
+      // CTA's converters have seen the previous use of the buffer complete
+      // (so that no phase takes two)
+      auto ghost_piece = [&]() -> bool {
+        const int b = g & 1;
+        if (!wait_bar(&bar[B_XA + b], (uint32_t)((g >> 1) & 1), abort, wait_ns)) return false;
+        commit_all(&bar[B_XE + b]);
+        ++g;
+        return true;
+      };
+      Walk s2w;
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
+      S1Order o;
+      s1_order_start(o, s2w);
       while (ok && s2w.valid) {
-        if (last_piece(s2w) && s1w.valid) {
-          if (!(ok = s1(s1w))) break;
-          walk_next_sc(s1w);
+        const int k = s1_now(o, s2w);
+        if (k > 0) {
+          if (!(ok = s1(o.w, o.done, o.done + k))) break;
+          s1_issued(o, s2w, k);
         }
-        if (!(ok = s2(s2w))) break;
+        if (!(ok = ghost(s2w) ? ghost_piece() : s2(s2w))) break;
         walk_next(s2w);
       }
-      if (!ok) {
-        *abort = 1;
-        atomicExch(err, 1);
-      }
+      if (!ok) abort_all();
       consumed = q;
       // every MMA issued by this thread has completed once B_DONE fires
       // (waited for also after an abort, bounded)
       commit(&bar[B_DONE]);
       const unsigned long long t0w = global_ns();
-      while (!test_wait(&bar[B_DONE], 0u) && global_ns() - t0w < kWaitNs) __nanosleep(64);
+      while (!test_wait<false>(&bar[B_DONE], 0u) && global_ns() - t0w < kWaitNs) __nanosleep(64);
     }
   } else {
     // ------------------------------------------------------------ converters
@@ -478,8 +652,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r = quarter * 32 + lane;  // TMEM lane = tile row
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     float2* const part_base = reinterpret_cast<float2*>(scratch);
-    int nd = 0, nsc = 0, g = 0;  // drains done, super-chunks and pieces converted
+    int nd = 0, nsc = 0, g = 0;  // drains done, super-chunks converted, pieces walked
     bool ok = true;
+    // the piece at w (this CTA's stage 1) into buffer g & 1 of every CTA of the group
     auto convert = [&](const Walk& w) -> bool {
       if (w.p == 0) {
         // X' of this super-chunk complete
@@ -502,11 +677,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         arrive(&bar[B_XPE]);
         ++nsc;
       }
-      // the piece buffer of two pieces back must have been read by its MMAs
       const int b = g & 1;
-      if (g >= 2 && !wait_bar_warp(&bar[B_XE + b], (uint32_t)(((g >> 1) - 1) & 1), abort, wait_ns)) return false;
       const float al = (float)w.it.alpha;
-      unsigned char* xb = sgen + OFF_X + b * XBUF;
+      unsigned char* const xl = sgen + OFF_X + b * XBUF;
 #pragma unroll
       for (int j = 0; j < PW; j += 4) {
         float4 hv, lv;
@@ -521,12 +694,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         lv.z = __uint_as_float(tf32(x2 - hv.z));
         lv.w = __uint_as_float(tf32(x3 - hv.w));
         const uint32_t o = x_off(r, j);
-        *reinterpret_cast<float4*>(xb + o) = hv;
-        *reinterpret_cast<float4*>(xb + XLO + o) = lv;
+        *reinterpret_cast<float4*>(xl + o) = hv;
+        *reinterpret_cast<float4*>(xl + XLO + o) = lv;
       }
+      // the writes are seen by the async proxy (this CTA's tensor core and the
+      // bulk copy to the group's other CTA, if any)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      arrive(&bar[B_XF + b]);
-      ++g;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (tid == 64) {
+        if (w.sl.grpn > 1) {
+          const uint32_t peer = (uint32_t)(2 * w.sl.grp0 + 1 - rank);
+          const uint32_t xb = sbase + OFF_X + b * XBUF;
+          copy_to_peer(map_to(xb, peer), xb, XBUF, map_to(smem_u32(&bar[B_XF + b]), peer));
+        }
+        arrive(&bar[B_XF + b]);
+      }
       return true;
     };
     // S (FP32, TMEM) is added to the task's partial tile of float pairs (hi,
@@ -587,7 +769,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       return true;
     };
     Walk w;
-    walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms);
+    walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
     int drains_in_task = 0, last_t = -1;
     bool pend = false, pend_first = false;
     long long pend_part = 0;
@@ -597,21 +779,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         last_t = w.t;
         drains_in_task = 0;
       }
-      if (!(ok = convert(w))) break;
+      // every CTA's MMAs have read piece g - 2 (buffer g & 1 is free in the
+      // whole cluster); waited for at every piece, in order, and acknowledged
+      // to this CTA's MMA issuer, which waits for the acknowledgement before
+      // its own reads of piece g: so no converter is two phases behind when
+      // it waits
+      const int b = g & 1;
+      if (g >= 2 && !(ok = wait_bar_warp<true>(&bar[B_XE + b], (uint32_t)(((g >> 1) - 1) & 1), abort, wait_ns)))
+        break;
+      arrive(&bar[B_XA + b]);
+      if (owned(w)) {
+        if (!(ok = convert(w))) break;
+      } else if (!ghost(w) && w.sl.grpn > 1 && tid == 64) {
+        // the piece comes from the group's other CTA: its bytes complete the phase
+        arrive_expect(&bar[B_XF + b], XBUF);
+      }
       if (pend && !(ok = drain(pend_part, pend_N, pend_first))) break;
-      pend = drain_point(w);
+      pend = !ghost(w) && drain_point(w);
       if (pend) {
         pend_part = w.tk.part;
         pend_N = w.N;
         pend_first = drains_in_task == 0;
         ++drains_in_task;
       }
+      ++g;
       walk_next(w);
     }
     if (ok && pend) ok = drain(pend_part, pend_N, pend_first);
     if (!ok) {
       *abort = 1;
-      if (lane == 0) atomicExch(err, 1);
+      if (lane == 0) abort_all();
     }
   }
   __syncthreads();
@@ -620,13 +817,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int q = consumed; q < produced; ++q) {
       uint32_t par = (uint32_t)((q / NSTAGE) & 1);
       const unsigned long long t0w = global_ns();
-      while (!test_wait(&bar[B_FULL + q % NSTAGE], par) && global_ns() - t0w < kWaitNs) __nanosleep(64);
+      while (!test_wait<false>(&bar[B_FULL + q % NSTAGE], par) && global_ns() - t0w < kWaitNs) __nanosleep(64);
     }
+  }
+  if (*abort) {
+    // after an abort a bulk copy from the peer may still be in flight into
+    // this CTA's piece buffers: give it time to land before the cluster exits
+    const unsigned long long t0w = global_ns();
+    while (global_ns() - t0w < kDrainCopiesNs) __nanosleep(1000);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
+  // no CTA leaves while a peer may still write into its shared memory or
+  // arrive on its barriers
+  cluster_sync();
 }
 
 // partial tiles are TM x TNMAX float pairs stored column by column (element
@@ -717,6 +923,44 @@ void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st) {
   if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: split launch: ") + cudaGetErrorString(e));
 }
 
+namespace {
+// launch of whole clusters of C CTAs along x
+void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int ncta, cudaStream_t st) {
+  cfg.gridDim = dim3((unsigned)ncta, 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+}  // namespace
+
+int hpsi_tc_max_ctas() {
+  static std::mutex mu;
+  static int cached[64];
+  static bool have[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[dev]) {
+    int n = 0;
+    if (ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      launch_config(cfg, attr, C, nullptr);
+      if (cudaOccupancyMaxActiveClusters(&n, (const void*)hpsi_tc_kernel, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    cached[dev] = n * C;
+    have[dev] = true;
+  }
+  return cached[dev];
+}
+
 void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st) {
   {
     cudaError_t e = ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES);
@@ -728,10 +972,13 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
     CUtensorMap m32, m64;
     make_map(&m32, L.pool, L.units, 32);
     make_map(&m64, L.pool, L.units, 64);
-    hpsi_tc_kernel<<<L.ncta, NTHREADS, SMEM_BYTES, st>>>(m32, m64, L.blocks, L.items, L.tasks, L.cta_off,
-                                                          L.cta_task, L.scratch, err, wait_ns,
-                                                          L.drain_terms);
-    cudaError_t e = cudaGetLastError();
+    if (L.ncta % C) throw std::runtime_error("internal: tcgen05 launch not in whole clusters");
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    launch_config(cfg, attr, L.ncta, st);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, hpsi_tc_kernel, m32, m64, L.blocks, L.items, L.tasks, L.cta_off,
+                                       L.cta_task, L.scratch, err, wait_ns, L.drain_terms);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }
   if (L.nreds > 0) {

@@ -13,23 +13,27 @@
 // 2 (kb G + g) holds the hi plane and unit 2 (kb G + g) + 1 the lo plane of
 // rows [8g, 8g+8) x columns [32kb, 32kb+32), each as eight 8-row x 16-byte
 // core matrices (k-core c at byte 128 c, row r at byte 16 r within it), the
-// canonical no-swizzle K-major layout of the tensor core.  A 128-row tile of
-// one k-block is therefore 32 consecutive units and a 64-row tile 16: one TMA
-// box each (a 2D tensor map over the pool with 1 KB rows).  Rows and columns
-// beyond the matrix are zero inside a plane; a box that runs past a plane
-// reads other planes' finite values, which only reach unstored output rows
-// and columns or meet zero padding.
+// canonical no-swizzle K-major layout of the tensor core.  Half a unit holds
+// one k-block of 16, so a TMA box of 128 floats by 2 R/8 units brings an R-row
+// tile of a k-block of 16 (hi and lo planes interleaved by row group).  Rows
+// and columns beyond the matrix are zero inside a plane; a box that runs past
+// a plane reads other planes' finite values, which only reach unstored output
+// rows and columns or meet zero padding.
 //
-// One CTA of the persistent kernel walks its list of tasks (a 128 x N, N <=
-// 256, tile of a sigma block and a chunk of its items).  Per item and per
-// 64-wide chunk j of psi's columns:
-//   stage 1:  X' = op(A)(tile rows, :) P(:, j)           (TMEM, 128 x 64)
-//   X = alpha X'  ->  hi/lo TF32 planes in shared memory  (converter warps)
-//   stage 2:  S += X op(B)(tile cols, j)^T               (TMEM, 128 x N)
+// The persistent kernel runs in clusters of kTcCluster CTAs.  A task is a
+// 128 x N (N <= 256) tile of a sigma block and a chunk of its items; the CTAs
+// of a cluster take tasks of the same block and chunk together (lockstep over
+// the same items), and CTAs whose tiles share their rows form a group that
+// shares stage 1.  Per item and per super-chunk of 256 columns of psi:
+//   stage 1:  X' = op(A)(tile rows, :) P(:, super-chunk)   (TMEM, 128 x 256)
+//             by one CTA of the group (super-chunks dealt round-robin)
+//   X = alpha X' per 16-column piece -> hi/lo TF32 planes, written into the
+//             shared memory of every CTA of the group
+//   stage 2:  S += X op(B)(tile cols, piece)^T             (TMEM, 128 x N)
+//             by every CTA for its own columns
 // Warp roles: one producer warp issues the TMA copies into a ring of stages,
-// one warp issues the MMAs (stage 1 of chunk j+1 before stage 2 of chunk j),
-// four warps convert X' and drain S into the task's partial tile of float
-// pairs.  Every wait is bounded.
+// one warp issues the MMAs, four warps convert X' and drain S into the task's
+// partial tile of float pairs.  Every wait is bounded.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -66,8 +70,19 @@ struct SplitJob {
 };
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
+constexpr int kTcCluster = 2;  // CTAs per cluster of the persistent launch
 constexpr int kTcUnitFloats = 256;  // one 1 KB unit
 constexpr int kTcDrainTerms = 1024;  // default FP32 accumulation length (terms) between drains
+
+// One entry of a CTA's list: the task, and the CTA's group within the
+// cluster for it (cluster ranks [grp0, grp0 + grpn), the CTAs whose tiles
+// have the same rows).  A ghost entry (a cluster slot without a tile) names a
+// task of its cluster slot, walks its items and computes nothing.
+struct TcSlot {
+  int task;
+  int grp0, grpn;
+  int ghost;
+};
 
 struct TcPlan {
   std::vector<SplitJob> op_jobs;   // operator blocks and identities (run once per plan)
@@ -75,8 +90,9 @@ struct TcPlan {
   std::vector<TcItem> items;
   std::vector<HpsiTask> tasks;     // (block, r0, c0, items, partial offset)
   std::vector<HpsiReduce> reds;    // one per tile: its chunks' partial tiles into sigma
-  std::vector<int> cta_off;        // tasks of CTA c: cta_task[cta_off[c] .. cta_off[c+1])
-  std::vector<int> cta_task;       // task indices, each CTA's list in decreasing cost
+  std::vector<int> cta_off;        // entries of CTA c: cta_task[cta_off[c] .. cta_off[c+1])
+  std::vector<TcSlot> cta_task;    // the CTAs of a cluster have lists of equal length, entry k of
+                                   // each belonging to the same block and item chunk
   size_t scratch = 0;              // 8-byte words of partial tiles (kTcTileM x kTcTileN float pairs per task)
   size_t units = 0;                // pool size in 1 KB units
   size_t pool_bytes = 0;
@@ -85,7 +101,7 @@ struct TcPlan {
 // Split planes, items, tasks and the per-CTA task lists of the fused
 // contraction of `blocks`/`items` (device pointers inside).  alloc(bytes)
 // returns the device memory of the pool; the caller owns it.  ncta: CTAs of
-// the persistent launch (0: one per SM of a 152-SM device).
+// the persistent launch, rounded down to whole clusters (0: 152).
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
                      const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta = 0);
 
@@ -95,8 +111,8 @@ struct TcLaunch {
   const TcItem* items = nullptr;
   const HpsiTask* tasks = nullptr;
   const int* cta_off = nullptr;
-  const int* cta_task = nullptr;
-  int ncta = 0;
+  const TcSlot* cta_task = nullptr;
+  int ncta = 0;  // a multiple of kTcCluster
   const HpsiReduce* reds = nullptr;
   int nreds = 0;
   double* scratch = nullptr;
@@ -117,10 +133,15 @@ void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st);
 // gives up).
 void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st);
 
+// CTAs of the persistent launch that the device runs at once (whole clusters
+// of kTcCluster CTAs, one CTA per SM); 0 without a device.
+int hpsi_tc_max_ctas();
+
 // Host-side check of a plan against its own ranges (debug_bounds): every
 // TMA box of every item inside the pool's units or its zero-filled tail,
-// every task's items and partial tile inside their lists, every CTA list a
-// permutation of the tasks.  Returns an empty string or the first violation.
+// every task's items and partial tile inside their lists, the CTA lists a
+// permutation of the tasks plus ghosts, in clusters of equal-length lists
+// whose entries agree on block and items, with consistent groups.  Returns an empty string or the first violation.
 std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& blocks);
 
 }  // namespace dmrg

@@ -20,19 +20,21 @@ constexpr int TM = kTcTileM, TNMAX = kTcTileN;
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-// tensor-pipe work of one item on a tile of width N, in units of one
-// k-block of 16 at MMA width 256 (128 x 256 x 16 in three TF32 products):
-// stage 1 per super-chunk of 256 columns of psi, stage 2 per 32-column
-// piece, plus a little for the conversion of each piece
-double item_cost(int ka, int kb, int N) {
+// tensor-pipe work of one item, in units of one k-block of 16 at MMA width
+// 256 (128 x 256 x 16 in three TF32 products): stage 1 per super-chunk of 256
+// columns of psi; stage 2 on a tile of width N per 16-column piece, plus a
+// little for the conversion of each piece
+double stage1_cost(int ka, int kb) {
   double c = 0.0;
-  for (int jc = 0; jc < kb; jc += 256) {
-    const int w = std::min(256, kb - jc);
-    c += ceil_div(ka, 16) * (((w + 15) & ~15) / 256.0);
-    for (int p = 0; p < w; p += 32) c += ceil_div(std::min(32, w - p), 16) * (N / 256.0) + 0.1;
-  }
+  for (int jc = 0; jc < kb; jc += 256) c += ceil_div(ka, 16) * (((std::min(256, kb - jc) + 15) & ~15) / 256.0);
   return c;
 }
+double stage2_cost(int kb, int N) {
+  double c = 0.0;
+  for (int p = 0; p < kb; p += 16) c += N / 256.0 + 0.05;
+  return c;
+}
+double item_cost(int ka, int kb, int N) { return stage1_cost(ka, kb) + stage2_cost(kb, N); }
 }  // namespace
 
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
@@ -177,8 +179,23 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     }
   }
   const double target = std::max(1.0, total / (4.0 * ncta));
-  std::vector<double> tcost;
+  // Cluster tasks: kTcCluster tasks of the same block and item chunk.  The
+  // column tiles of one row tile are grouped kTcCluster at a time (a group
+  // shares stage 1); the remainder groups of the rows are packed first-fit
+  // (largest first) into further cluster tasks, and slots left empty become
+  // ghosts.
+  constexpr int C = kTcCluster;
+  struct Member {
+    int task, grp0, grpn;
+  };
+  struct CTask {
+    std::vector<Member> m;  // real members in rank order (ranks 0 .. m.size()-1)
+    double cost = 0.0;
+  };
+  std::vector<CTask> ctasks;
+  std::vector<double> s1c, s2c;  // per task: stage-1 and stage-2 cost of its items
   long long part = 0;
+  const long long tile = (long long)TM * TNMAX;
   for (size_t b = 0; b < blocks.size(); ++b) {
     const HpsiBlock& bk = blocks[b];
     if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
@@ -195,44 +212,93 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     }
     cuts.push_back(bk.item_count);
     const int nch = (int)cuts.size() - 1;
-    for (int r0 = 0; r0 < bk.m; r0 += TM)
-      for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
+    const int mt = ceil_div(bk.m, TM), nt = ceil_div(bk.n, TNMAX);
+    // tasks in (tile, chunk) order: the chunks of a tile have consecutive partial tiles
+    const int t_first = (int)plan.tasks.size();
+    for (int r = 0; r < mt; ++r)
+      for (int c = 0; c < nt; ++c) {
+        const int r0 = r * TM, c0 = c * TNMAX;
         const int N = std::min(TNMAX, (std::min(TNMAX, bk.n - c0) + 15) & ~15);
         plan.reds.push_back({(int)b, r0, c0, nch, part});
-        for (int c = 0; c < nch; ++c) {
-          const int i0 = bk.item_begin + cuts[c], cnt = cuts[c + 1] - cuts[c];
+        for (int ch = 0; ch < nch; ++ch) {
+          const int i0 = bk.item_begin + cuts[ch], cnt = cuts[ch + 1] - cuts[ch];
           plan.tasks.push_back({(int)b, r0, c0, i0, cnt, part});
-          double tc = 1.0;  // drain
-          for (int k = i0; k < i0 + cnt; ++k) tc += item_cost(plan.items[k].ka, plan.items[k].kb, N);
-          tcost.push_back(tc);
-          part += (long long)TM * TNMAX;
+          double a1 = 0.0, a2 = 0.0;
+          for (int k = i0; k < i0 + cnt; ++k) {
+            a1 += stage1_cost(plan.items[k].ka, plan.items[k].kb);
+            a2 += stage2_cost(plan.items[k].kb, N);
+          }
+          s1c.push_back(a1);
+          s2c.push_back(a2);
+          part += tile;
         }
       }
+    auto task_at = [&](int r, int c, int ch) { return t_first + (r * nt + c) * nch + ch; };
+    for (int ch = 0; ch < nch; ++ch) {
+      std::vector<std::vector<int>> rem;  // remainder groups (tasks of one row)
+      for (int r = 0; r < mt; ++r)
+        for (int c = 0; c < nt; c += C) {
+          std::vector<int> g;
+          for (int q = c; q < std::min(nt, c + C); ++q) g.push_back(task_at(r, q, ch));
+          if ((int)g.size() == C) {
+            CTask ct;
+            for (int q = 0; q < C; ++q) ct.m.push_back({g[q], 0, C});
+            ctasks.push_back(ct);
+          } else {
+            rem.push_back(g);
+          }
+        }
+      std::stable_sort(rem.begin(), rem.end(), [](const auto& x, const auto& y) { return x.size() > y.size(); });
+      const size_t open0 = ctasks.size();
+      for (const auto& g : rem) {
+        size_t k = open0;
+        while (k < ctasks.size() && ctasks[k].m.size() + g.size() > (size_t)C) ++k;
+        if (k == ctasks.size()) ctasks.emplace_back();
+        const int g0 = (int)ctasks[k].m.size();
+        for (int t : g) ctasks[k].m.push_back({t, g0, (int)g.size()});
+      }
+    }
   }
   plan.scratch = (size_t)part;
-  // Persistent launch: longest task first onto the least-loaded CTA; each
-  // CTA runs its tasks in decreasing cost.
-  const int nt = (int)plan.tasks.size();
-  const int G = std::max(1, std::min(ncta, nt));
-  std::vector<int> order(nt);
+  for (CTask& ct : ctasks) {
+    double w = 0.0;
+    for (const Member& mb : ct.m) w = std::max(w, s1c[mb.task] / mb.grpn + s2c[mb.task]);
+    ct.cost = w + 1.0;  // drain
+  }
+  // Persistent launch: longest cluster task first onto the least-loaded
+  // cluster; each cluster runs its tasks in decreasing cost.
+  const int nct = (int)ctasks.size();
+  const int nclu = std::max(1, std::min(std::max(1, ncta / C), nct));
+  std::vector<int> order(nct);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tcost[a] > tcost[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctasks[a].cost > ctasks[b].cost; });
   using Load = std::pair<double, int>;
   std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
-  for (int c = 0; c < G; ++c) pq.push({0.0, c});
-  std::vector<std::vector<int>> lists(G);
+  for (int c = 0; c < nclu; ++c) pq.push({0.0, c});
+  std::vector<std::vector<int>> lists(nclu);
   for (int t : order) {
     Load l = pq.top();
     pq.pop();
     lists[l.second].push_back(t);
-    pq.push({l.first + tcost[t], l.second});
+    pq.push({l.first + ctasks[t].cost, l.second});
   }
-  plan.cta_off.assign(G + 1, 0);
-  for (int c = 0; c < G; ++c) {
-    plan.cta_off[c + 1] = plan.cta_off[c] + (int)lists[c].size();
-    plan.cta_task.insert(plan.cta_task.end(), lists[c].begin(), lists[c].end());
+  if (nct == 0) {
+    plan.cta_off.assign(1, 0);
+  } else {
+    plan.cta_off.assign((size_t)nclu * C + 1, 0);
+    for (int k = 0; k < nclu; ++k)
+      for (int j = 0; j < C; ++j) {
+        const int cta = k * C + j;
+        for (int t : lists[k]) {
+          const CTask& ct = ctasks[t];
+          if (j < (int)ct.m.size())
+            plan.cta_task.push_back({ct.m[j].task, ct.m[j].grp0, ct.m[j].grpn, 0});
+          else
+            plan.cta_task.push_back({ct.m[0].task, j, 1, 1});
+        }
+        plan.cta_off[cta + 1] = (int)plan.cta_task.size();
+      }
   }
-  if (nt == 0) plan.cta_off.assign(1, 0);
 }
 
 std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& blocks) {
@@ -264,17 +330,51 @@ std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& bloc
         (size_t)(rd.part0 + rd.nparts * tile) > plan.scratch)
       return "reduction out of range";
   }
-  if (plan.cta_off.empty() || plan.cta_off.front() != 0 || plan.cta_off.back() != (int)plan.cta_task.size() ||
-      plan.cta_task.size() != plan.tasks.size())
-    return "CTA lists do not cover the tasks";
+  const int C = kTcCluster;
+  if (plan.cta_off.empty() || plan.cta_off.front() != 0 || plan.cta_off.back() != (int)plan.cta_task.size())
+    return "CTA lists do not cover their entries";
+  const int ncta = (int)plan.cta_off.size() - 1;
+  if (plan.tasks.empty() != (ncta == 0) || ncta % C) return "CTA count not a whole number of clusters";
   std::vector<int> seen(plan.tasks.size(), 0);
-  for (size_t c = 0; c + 1 < plan.cta_off.size(); ++c) {
-    if (plan.cta_off[c + 1] <= plan.cta_off[c]) return "empty CTA list " + std::to_string(c);
-    for (int q = plan.cta_off[c]; q < plan.cta_off[c + 1]; ++q) {
-      const int t = plan.cta_task[q];
-      if (t < 0 || t >= (int)seen.size() || seen[t]++) return "CTA lists are not a permutation of the tasks";
+  for (int k = 0; k < ncta / C; ++k) {
+    const int base = k * C;
+    const int len = plan.cta_off[base + 1] - plan.cta_off[base];
+    if (len <= 0) return "empty CTA list " + std::to_string(base);
+    for (int j = 1; j < C; ++j)
+      if (plan.cta_off[base + j + 1] - plan.cta_off[base + j] != len)
+        return "cluster " + std::to_string(k) + ": lists of unequal length";
+    for (int q = 0; q < len; ++q) {
+      const TcSlot* sl[kTcCluster];
+      for (int j = 0; j < C; ++j) {
+        sl[j] = &plan.cta_task[plan.cta_off[base + j] + q];
+        if (sl[j]->task < 0 || sl[j]->task >= (int)plan.tasks.size()) return "CTA entry out of range";
+      }
+      const HpsiTask& t0 = plan.tasks[sl[0]->task];
+      for (int j = 0; j < C; ++j) {
+        const TcSlot& e = *sl[j];
+        const HpsiTask& t = plan.tasks[e.task];
+        const std::string at = "cluster " + std::to_string(k) + " entry " + std::to_string(q) + " rank " +
+                               std::to_string(j) + ": ";
+        if (t.block != t0.block || t.it_begin != t0.it_begin || t.it_count != t0.it_count)
+          return at + "items differ within the cluster";
+        if (e.ghost) {
+          if (e.grp0 != j || e.grpn != 1) return at + "ghost not alone in its group";
+          continue;
+        }
+        if (seen[e.task]++) return at + "task listed twice";
+        if (e.grpn < 1 || e.grp0 < 0 || e.grp0 > j || e.grp0 + e.grpn <= j || e.grp0 + e.grpn > C)
+          return at + "group out of range";
+        for (int i = e.grp0; i < e.grp0 + e.grpn; ++i) {
+          const TcSlot& o = *sl[i];
+          const HpsiTask& u = plan.tasks[o.task];
+          if (o.ghost || o.grp0 != e.grp0 || o.grpn != e.grpn || u.r0 != t.r0 || (i != j && u.c0 == t.c0))
+            return at + "inconsistent group";
+        }
+      }
     }
   }
+  for (size_t t = 0; t < seen.size(); ++t)
+    if (seen[t] != 1) return "task " + std::to_string(t) + " in no CTA list";
   if ((plan.units ? (size_t)plan.units * kTcUnitFloats * sizeof(float) : 0) != plan.pool_bytes)
     return "pool size mismatch";
   if (plan.units > (size_t)INT32_MAX) return "pool beyond 2^31 units";

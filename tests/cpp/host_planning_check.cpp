@@ -10,7 +10,8 @@
 //    inside the pool; the chunks of every 128 x 256 tile cover its items
 //    once, in order, each chunk with its own partial tile, one reduction per
 //    tile names all of its chunks, and every task is in exactly one CTA list
-//    of the persistent launch;
+//    of the persistent launch, whose clusters walk the same items in lockstep
+//    with groups of CTAs on the same rows;
 //  - jac_plan_batches (batched Jacobi eigensolver launches): every matrix in
 //    exactly one launch, in order; at most `cap` CTAs per launch; group sizes
 //    between the minimum (two above the shared-memory size) and the cap of
@@ -177,16 +178,43 @@ static void check_plan(unsigned seed) {
       CHECK(refers(t.Pt, Key{it.P, 1, it.kb, it.ka, it.ldp}));
       CHECK(refers(t.B, key_b(bk, it)));
     }
-  // persistent launch: every task in exactly one CTA list, no empty CTA
+  // persistent launch in clusters: lists of equal length per cluster, entry k
+  // of each naming the same block and items; every task in exactly one list
+  // (ghost entries aside); groups are contiguous ranks with the same rows and
+  // distinct columns; the plan's own check agrees
+  const int C = kTcCluster;
   const int G = (int)plan.cta_off.size() - 1;
-  CHECK(G == std::min<int>(ncta, (int)plan.tasks.size()) || (plan.tasks.empty() && G == 0));
+  CHECK(G % C == 0);
+  CHECK(plan.tasks.empty() ? G == 0 : (G >= C && G <= std::max(C, ncta / C * C)));
   std::vector<int> seen(plan.tasks.size(), 0);
-  for (int c = 0; c < G; ++c) {
-    CHECK(plan.cta_off[c + 1] > plan.cta_off[c]);
-    for (int q = plan.cta_off[c]; q < plan.cta_off[c + 1]; ++q) seen[plan.cta_task[q]]++;
+  for (int k = 0; k < G / C; ++k) {
+    const int len = plan.cta_off[k * C + 1] - plan.cta_off[k * C];
+    CHECK(len > 0);
+    for (int j = 0; j < C; ++j) CHECK(plan.cta_off[k * C + j + 1] - plan.cta_off[k * C + j] == len);
+    for (int q = 0; q < len; ++q) {
+      const TcSlot& s0 = plan.cta_task[plan.cta_off[k * C] + q];
+      CHECK(!s0.ghost);
+      for (int j = 0; j < C; ++j) {
+        const TcSlot& e = plan.cta_task[plan.cta_off[k * C + j] + q];
+        const HpsiTask& t = plan.tasks[e.task];
+        const HpsiTask& t0 = plan.tasks[s0.task];
+        CHECK(t.block == t0.block && t.it_begin == t0.it_begin && t.it_count == t0.it_count);
+        if (e.ghost) {
+          CHECK(e.grp0 == j && e.grpn == 1);
+          continue;
+        }
+        seen[e.task]++;
+        CHECK(e.grp0 <= j && j < e.grp0 + e.grpn && e.grp0 + e.grpn <= C);
+        for (int i = e.grp0; i < e.grp0 + e.grpn; ++i) {
+          const TcSlot& o = plan.cta_task[plan.cta_off[k * C + i] + q];
+          CHECK(!o.ghost && o.grp0 == e.grp0 && o.grpn == e.grpn);
+          CHECK(plan.tasks[o.task].r0 == t.r0 && (i == j || plan.tasks[o.task].c0 != t.c0));
+        }
+      }
+    }
   }
-  CHECK(plan.cta_task.size() == plan.tasks.size());
   for (int x : seen) CHECK(x == 1);
+  CHECK(tc_plan_check(plan, blocks).empty());
   // tiles, chunks, partial tiles, reductions
   std::map<std::tuple<int, int, int>, std::vector<const HpsiTask*>> chunks;
   std::set<long long> parts;
