@@ -258,7 +258,7 @@ def run_hpsi_only(args):
     step) on the synthetic sector blocks; device time from CUDA events."""
     import paper_2503_20700_gb300 as pkg
     pkg.load()
-    prec = {"split": 1, "split-tc": 4, "split-all": 1, "fp64": 0}[args.precision]
+    prec = {"split": 1, "split-tc": 4, "split-all-tc": 4, "split-all": 1, "fp64": 0}[args.precision]
     if args.hpsi_shape == "large":
         # sector dimensions of the middle bonds at D = 1024 .. 2048 (300 .. 600)
         A, P, B, clen, blocks, items, flops = hpsi_problem(7, 8, 300, 600, 30)
@@ -400,7 +400,8 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved, "peak": peak_tf,
             "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
-            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
+            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel",
+                       pkg.SPLIT_ALL_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
             "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,
             "what": "algorithmic FLOPs of the contraction launches (kernel and chunk reduction) / their "
                     "CUDA-event time; the psi splits are timed apart (split_ms)",
@@ -503,7 +504,8 @@ def run_sweep(args, pkg, prec, rank, world, dist, device):
     achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
-            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
+            "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel",
+                       pkg.SPLIT_ALL_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
             "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,
             "split_ms": s_ms, "split_launches": s_launch}
     e2e = None
@@ -555,9 +557,11 @@ def main():
                     help="--mode bond: also converge the float64 Davidson at the bond (slow at large D)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per contraction launch from an ncu capture of the same kernel")
-    ap.add_argument("--precision", default="split-tc", choices=["split", "split-tc", "split-all", "fp64"],
+    ap.add_argument("--precision", default="split-tc",
+                    choices=["split", "split-tc", "split-all-tc", "split-all", "fp64"],
                     help="split-tc: 3xTF32 H_eff psi on tcgen05, renormalisation in FP64; "
-                         "split: the same products on mma.sync; split-all: mma.sync 3xTF32 also in "
+                         "split-all-tc: the renormalisation U^T O U on tcgen05 too; "
+                         "split: the H_eff psi products on mma.sync; split-all: mma.sync 3xTF32 also in "
                          "renormalisation; fp64: all FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -577,8 +581,8 @@ def main():
     pkg.load()
     rank, world, dist = dist_init(args.gpus)
     device = int(os.environ.get("LOCAL_RANK", "0"))
-    prec = {"split": pkg.SPLIT_HPSI, "split-tc": pkg.SPLIT_HPSI_TC, "split-all": pkg.SPLIT_TF32,
-            "fp64": pkg.FP64}[args.precision]
+    prec = {"split": pkg.SPLIT_HPSI, "split-tc": pkg.SPLIT_HPSI_TC, "split-all-tc": pkg.SPLIT_ALL_TC,
+            "split-all": pkg.SPLIT_TF32, "fp64": pkg.FP64}[args.precision]
     rc = (run_bond if args.mode == "bond" else run_sweep)(args, pkg, prec, rank, world, dist, device)
     if dist is not None:
         dist.destroy_process_group()

@@ -53,11 +53,17 @@ typedef enum {
   DMRG_BF16X9 = 2,      /* reserved: BF16x9 split products (not available)   */
   DMRG_SPLIT_HPSI = 3,  /* 3xTF32 in the H_eff psi GEMMs only; renormalisation
                            and complementary-operator GEMMs in float64          */
-  DMRG_SPLIT_HPSI_TC = 4 /* as DMRG_SPLIT_HPSI, with the H_eff psi split products
+  DMRG_SPLIT_HPSI_TC = 4, /* as DMRG_SPLIT_HPSI, with the H_eff psi split products
                            issued on the tcgen05 tensor cores (TMEM
                            accumulators, 128 x 256 sigma tiles, operands
                            pre-split into TF32 hi/lo planes); a bounded wait
                            that runs out returns DMRG_ETIMEOUT              */
+  DMRG_SPLIT_ALL_TC = 5  /* as DMRG_SPLIT_HPSI_TC, with the renormalisation
+                           O' = U^T O U (Sec. II.B) also one tcgen05
+                           contraction per group of operators (operator
+                           blocks and U as TF32 plane pairs, float-pair
+                           partial sums); complementary-operator GEMMs stay
+                           float64                                           */
 } dmrg_precision;
 
 typedef struct {

@@ -17,7 +17,7 @@ LIB_NAME = "libdmrgscf.so"
 
 DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA = 0, -1, -2, -3
 DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE, DMRG_EINTERNAL = -4, -5, -6, -7
-FP64, SPLIT_TF32, SPLIT_HPSI, SPLIT_HPSI_TC = 0, 1, 3, 4
+FP64, SPLIT_TF32, SPLIT_HPSI, SPLIT_HPSI_TC, SPLIT_ALL_TC = 0, 1, 3, 4, 5
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
            -5: "ETIMEOUT", -6: "ESTATE", -7: "EINTERNAL"}

@@ -126,7 +126,8 @@ class Backend {
                     double flops) = 0;
   // The tcgen05 version of the contraction on pre-split operands (hpsi_tc.cuh),
   // and the split of float64 blocks into TF32 hi/lo planes (device job list).
-  virtual void hpsi_tc(const TcLaunch& launch, double flops) = 0;
+  // tag: profiling counter (1: H_eff psi, 0: other GEMM work)
+  virtual void hpsi_tc(const TcLaunch& launch, double flops, int tag = 1) = 0;
   virtual void split(const SplitJob* jobs, int n, float* pool) = 0;
 
   // Davidson vector algebra on contiguous float64 vectors of length len.

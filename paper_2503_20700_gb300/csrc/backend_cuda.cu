@@ -978,11 +978,11 @@ class CudaBackend : public Backend {
     if (recs.size() > 4096) drain();
   }
 
-  void hpsi_tc(const TcLaunch& L, double flops) override {
+  void hpsi_tc(const TcLaunch& L, double flops, int tag) override {
     gemm_flops += flops;
     Rec* rec = nullptr;
     if (profiling) {
-      recs.push_back(Rec{ev(), ev(), flops, 1});
+      recs.push_back(Rec{ev(), ev(), flops, tag});
       rec = &recs.back();
       CK(cudaEventRecord(rec->a, st));
     }

@@ -76,15 +76,18 @@ struct DeviceGuard {
 };
 
 bool sweep_precision_ok(int p) {
-  return p == DMRG_FP64 || p == DMRG_SPLIT_TF32 || p == DMRG_SPLIT_HPSI || p == DMRG_SPLIT_HPSI_TC;
+  return p == DMRG_FP64 || p == DMRG_SPLIT_TF32 || p == DMRG_SPLIT_HPSI || p == DMRG_SPLIT_HPSI_TC ||
+         p == DMRG_SPLIT_ALL_TC;
 }
 
 // dmrg_precision -> (H_eff psi kernel precision, renormalisation GEMM precision)
 void map_precision(int p, dmrg::Precision* hpsi, dmrg::Precision* renorm) {
-  *hpsi = p == DMRG_FP64           ? dmrg::Precision::FP64
-          : p == DMRG_SPLIT_HPSI_TC ? dmrg::Precision::TC_TF32X3
-                                    : dmrg::Precision::SPLIT_TF32;
-  *renorm = p == DMRG_SPLIT_TF32 ? dmrg::Precision::SPLIT_TF32 : dmrg::Precision::FP64;
+  *hpsi = p == DMRG_FP64                                   ? dmrg::Precision::FP64
+          : (p == DMRG_SPLIT_HPSI_TC || p == DMRG_SPLIT_ALL_TC) ? dmrg::Precision::TC_TF32X3
+                                                               : dmrg::Precision::SPLIT_TF32;
+  *renorm = p == DMRG_SPLIT_TF32     ? dmrg::Precision::SPLIT_TF32
+            : p == DMRG_SPLIT_ALL_TC ? dmrg::Precision::TC_TF32X3
+                                     : dmrg::Precision::FP64;
 }
 
 // Default initial product state: electrons spread evenly, spins coupled from
@@ -278,7 +281,8 @@ dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision,
   if (!c || !c->eng || !out) return fail(c, DMRG_EINVAL, "invalid argument");
   if (direction != 0 && direction != 1) return fail(c, DMRG_EINVAL, "direction must be 0 (L->R) or 1 (R->L)");
   if (!sweep_precision_ok(precision) || precision == DMRG_SPLIT_TF32)
-    return fail(c, DMRG_EINVAL, "precision must be DMRG_FP64, DMRG_SPLIT_HPSI or DMRG_SPLIT_HPSI_TC");
+    return fail(c, DMRG_EINVAL,
+                "precision must be DMRG_FP64, DMRG_SPLIT_HPSI, DMRG_SPLIT_HPSI_TC or DMRG_SPLIT_ALL_TC");
   if (max_iter < 1 || !(tol > 0) || min_calls < 0 || cap < 0 || (cap > 0 && !call_ms))
     return fail(c, DMRG_EINVAL, "invalid argument");
   try {

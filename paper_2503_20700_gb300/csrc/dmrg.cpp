@@ -1124,7 +1124,8 @@ void Engine::build_comp_from_normal(const Block& b, OpSet& dst, const std::vecto
           int nc = (int)std::min(panel, N - c0);
           gb.add(Y + c0, M, nc, (int)N, GemmSeg{Gdev, X + c0, K, K, (int)N, 0, 0, 1.0});
         }
-        gb.run(be_, opt_.prec_renorm);
+        // complementary operators stay float64 under the tcgen05 renormalisation
+        gb.run(be_, opt_.prec_renorm == Precision::TC_TF32X3 ? Precision::FP64 : opt_.prec_renorm);
         // place rows of Y into the targets (directly, or as adjoint)
         PlaceBuilder pb;
         const Layout& DL = dst.layout(kind_dn(kind), k2);
@@ -1155,6 +1156,64 @@ void Engine::build_comp_from_normal(const Block& b, OpSet& dst, const std::vecto
 }
 
 // ============================================================ renormalisation
+// One tcgen05 contraction sigma_b += sum alpha op(A) P op(B)^T over the given
+// blocks and items (device pointers): plan, split planes, launch, wait.
+// Counted as "other GEMM work" (profiling tag 0).
+void Engine::tc_contract(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items, double flops) {
+  if (blocks.empty() || items.empty()) return;
+  TcPlan tp;
+  void* pool = nullptr;
+  const int tc_ctas = hpsi_tc_max_ctas();
+  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return pool = be_->alloc(bytes); }, tp,
+                  tc_ctas > 0 ? tc_ctas : be_->sm_count());
+  if (opt_.debug_bounds) {
+    const std::string bad = tc_plan_check(tp, blocks);
+    if (!bad.empty()) {
+      if (pool) be_->free(pool);
+      throw std::logic_error("internal: tcgen05 plan: " + bad);
+    }
+  }
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  std::vector<SplitJob> jobs = tp.op_jobs;
+  jobs.insert(jobs.end(), tp.psi_jobs.begin(), tp.psi_jobs.end());
+  const size_t ob = 0, oc = al(blocks.size() * sizeof(HpsiBlock));
+  const size_t ot = al(oc + tp.items.size() * sizeof(TcItem));
+  const size_t orr = al(ot + tp.tasks.size() * sizeof(HpsiTask));
+  const size_t oj = al(orr + tp.reds.size() * sizeof(HpsiReduce));
+  const size_t oco = al(oj + jobs.size() * sizeof(SplitJob));
+  const size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
+  const size_t os = al(oct + tp.cta_task.size() * sizeof(TcSlot));
+  char* d = (char*)be_->alloc(os + tp.scratch * sizeof(double) + 256);
+  be_->copy_h2d(d + ob, blocks.data(), blocks.size() * sizeof(HpsiBlock));
+  if (!tp.items.empty()) be_->copy_h2d(d + oc, tp.items.data(), tp.items.size() * sizeof(TcItem));
+  if (!tp.tasks.empty()) be_->copy_h2d(d + ot, tp.tasks.data(), tp.tasks.size() * sizeof(HpsiTask));
+  if (!tp.reds.empty()) be_->copy_h2d(d + orr, tp.reds.data(), tp.reds.size() * sizeof(HpsiReduce));
+  if (!jobs.empty()) {
+    be_->copy_h2d(d + oj, jobs.data(), jobs.size() * sizeof(SplitJob));
+    be_->split((const SplitJob*)(d + oj), (int)jobs.size(), (float*)pool);
+  }
+  if (!tp.cta_off.empty()) be_->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
+  if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(TcSlot));
+  TcLaunch L;
+  L.blocks = (const HpsiBlock*)(d + ob);
+  L.items = (const TcItem*)(d + oc);
+  L.tasks = (const HpsiTask*)(d + ot);
+  L.cta_off = (const int*)(d + oco);
+  L.cta_task = (const TcSlot*)(d + oct);
+  L.ncta = tp.cta_off.empty() ? 0 : (int)tp.cta_off.size() - 1;
+  L.reds = (const HpsiReduce*)(d + orr);
+  L.nreds = (int)tp.reds.size();
+  L.scratch = (double*)(d + os);
+  L.pool = pool;
+  L.units = tp.units;
+  L.drain_terms = opt_.tc_drain_terms;
+  be_->hpsi_tc(L, flops, 0);
+  be_->sync();
+  be_->check_device_flag();
+  be_->free(d);
+  if (pool) be_->free(pool);
+}
+
 // O'(a', a) = U_a'^T O(a', a) U_a with Ut[a] = kept eigenvectors as rows.
 std::unique_ptr<Block> Engine::renormalize(Block& enl, const SavedU& U, bool switch_to_comp) {
   const std::vector<int>& kept = U.kept;
@@ -1184,7 +1243,64 @@ std::unique_ptr<Block> Engine::renormalize(Block& enl, const SavedU& U, bool swi
   // per layout: T = E U (temp), O' = U^T T
   std::map<std::pair<int, int>, std::vector<OpKey>> by;
   for (auto& k : keys) by[{kind_dn(k.kind), k.k2}].push_back(k);
+  if (opt_.prec_renorm == Precision::TC_TF32X3) {
+    // each block O'(a', a) = Ut_a' E(a', a) Ut_a^T is one item of a tcgen05
+    // contraction (op(A) = Ut_a', P = E block, op(B) = Ut_a), the operators
+    // of a layout in groups that bound the plan
+    for (auto& [lk, ks] : by) {
+      const Layout& EL = enl.ops->layout(lk.first, lk.second);
+      const Layout& NL = nb->ops->layout(lk.first, lk.second);
+      if (NL.size == 0) continue;
+      std::vector<HpsiBlock> blocks;
+      std::vector<HpsiItem> items;
+      double flops = 0.0;
+      auto flush = [&]() {
+        tc_contract(blocks, items, flops);
+        blocks.clear();
+        items.clear();
+        flops = 0.0;
+      };
+      for (size_t oi = 0; oi < ks.size(); ++oi) {
+        const double* E = enl.ops->get(ks[oi]);
+        double* O = nb->ops->get(ks[oi]);
+        if (!E || !O) continue;
+        for (size_t i = 0; i < EL.blk.size(); ++i) {
+          auto& bl = EL.blk[i];
+          const int na = map[bl.bra], nk = map[bl.ket];
+          if (na < 0 || nk < 0) continue;
+          const int ka = kept[bl.ket], kap = kept[bl.bra];
+          const int ni = NL.find(na, nk);
+          auto& nbk = NL.blk[ni];
+          HpsiBlock hb{};
+          hb.C = O + nbk.off;
+          hb.m = kap;
+          hb.n = ka;
+          hb.ldc = ka;
+          hb.item_begin = (int)items.size();
+          hb.item_count = 1;
+          HpsiItem it{};
+          it.A = ut[bl.bra];
+          it.lda = bl.rows;
+          it.transA = 0;
+          it.P = E + bl.off;
+          it.ldp = bl.cols;
+          it.B = ut[bl.ket];
+          it.ldb = bl.cols;
+          it.transB = 0;
+          it.ka = bl.rows;
+          it.kb = bl.cols;
+          it.alpha = 1.0;
+          items.push_back(it);
+          blocks.push_back(hb);
+          flops += 2.0 * kap * bl.rows * bl.cols + 2.0 * kap * bl.cols * ka;
+        }
+        if (items.size() >= 200000) flush();
+      }
+      flush();
+    }
+  }
   for (auto& [lk, ks] : by) {
+    if (opt_.prec_renorm == Precision::TC_TF32X3) break;
     const Layout& EL = enl.ops->layout(lk.first, lk.second);
     const Layout& NL = nb->ops->layout(lk.first, lk.second);
     if (NL.size == 0) continue;

@@ -320,6 +320,7 @@ class Engine {
                    const std::vector<std::pair<OpKey, struct Term>>& terms);
   void build_comp_from_normal(const Block& b, OpSet& dst, const std::vector<OpKey>& keys);
   std::unique_ptr<Block> renormalize(Block& enl, const SavedU& U, bool switch_to_comp);
+  void tc_contract(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items, double flops);
   void build_initial_right();
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);

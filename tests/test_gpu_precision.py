@@ -94,3 +94,23 @@ def test_dynamic_bond_dimension_matches_oracle(pkg, target, dmin):
             assert right[m] == orr[8 - m], (m, right[m], orr[8 - m])
             compared += 1
     assert compared >= 5
+
+
+def test_split_renormalisation_on_tcgen05_to_first_order(pkg):
+    """DMRG_SPLIT_ALL_TC: the renormalisation U^T O U as tcgen05 contractions
+    (operator blocks and U split into TF32 planes).  Unlike the split H_eff psi
+    alone, rounding of the renormalised operators enters the energy at first
+    order (Sec. II.B: every later block is built from them), so the bound
+    against the oracle is the first-order one, 2e-5 Eh at n=8, D=16; the
+    float64 renormalisation stays the default for the 1e-6 target."""
+    h, L = W.cholesky_random(8, 32, seed=20250326)
+    eri = W.eri_from_cholesky(L)
+    o = OracleDMRG(h, eri, 8, 0, D=16)
+    eo = o.sweep(3)
+    g = pkg.DMRG(h, eri=eri, n_elec=8, two_s=0, D=16, precision=pkg.SPLIT_ALL_TC, tol=1e-10)
+    g.profile(True)
+    eg = [g.sweep()[0] for _ in range(3)]
+    ms, fl, n = g.kernel_stats(0)
+    g.close()
+    assert np.abs(np.array(eg) - np.array(eo)).max() < 2e-5
+    assert n > 0 and fl > 0  # the renormalisation ran as contraction launches
