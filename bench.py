@@ -306,6 +306,32 @@ def tc_peak(prec, pk, src, pkg):
     return 1.25, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
 
 
+def profiled_traffic(args, mode_default):
+    """DRAM bytes per contraction launch for the roofline: --traffic, else, on
+    the default workload, the figure of the committed ncu launch list of the
+    same command, if that list was taken on the kernel source as it is now
+    (its sha256 is recorded in the summary); else None."""
+    if args.traffic is not None:
+        return args.traffic, "--traffic"
+    if not mode_default:
+        return None, None
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    prof = os.path.join(here, "profiles", "launch_list_cas40_D2048_bond19.md")
+    src = os.path.join(here, "paper_2503_20700_gb300", "csrc", "hpsi_tc.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, None
+    if sha not in text:
+        return None, None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            return float(line.split(":", 1)[1]), os.path.relpath(prof, here)
+    return None, None
+
+
 def parse_ramp(text):
     out = []
     for part in text.split(","):
@@ -396,10 +422,13 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     barrier(dist)
 
     pk, src = peaks()
+    default_workload = (args.workload == "cas40" and args.D == 2048 and args.bond < 0 and
+                        args.precision == "split-tc" and args.ramp == "64:4,256:4,1024:4")
+    traffic, traffic_src = profiled_traffic(args, default_workload)
     peak_tf, peak_note = tc_peak(prec, pk, src, pkg)
     achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved, "peak": peak_tf,
-            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
+            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic, "traffic_source": traffic_src,
             "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel",
                        pkg.SPLIT_ALL_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
             "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,
@@ -504,6 +533,7 @@ def run_sweep(args, pkg, prec, rank, world, dist, device):
     achieved = k_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     roof = {"bound": "tensor" if prec != pkg.FP64 else "alu", "achieved": achieved,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": args.traffic,
+            "traffic_source": "--traffic" if args.traffic is not None else None,
             "kernel": {pkg.FP64: "hpsi_f64_kernel", pkg.SPLIT_HPSI_TC: "hpsi_tc_kernel",
                        pkg.SPLIT_ALL_TC: "hpsi_tc_kernel"}.get(prec, "hpsi_tf32x3_kernel"),
             "launches": k_launch, "avg_launch_ms": k_ms / max(1, k_launch), "peak_source": peak_note,

@@ -87,3 +87,23 @@ def test_initial_state_is_aufbau_for_cholesky_workloads():
     assert sum(occ) == 8 and path[0] == 0 and occ == W.aufbau_state(wl["h"], 8, 0)[0]
     wl = bench.workload("naphthalene")
     assert bench.initial_state(wl) == (None, None)
+
+
+def test_profiled_traffic_only_for_the_profiled_kernel():
+    """The roofline's DRAM traffic comes from the committed ncu launch list
+    only while the kernel source is the one that list was taken on."""
+    import argparse
+    import hashlib
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = os.path.join(root, "paper_2503_20700_gb300", "csrc", "hpsi_tc.cu")
+    prof = os.path.join(root, "profiles", "launch_list_cas40_D2048_bond19.md")
+    a = argparse.Namespace(traffic=None)
+    v, where = bench.profiled_traffic(a, True)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if os.path.exists(prof) and sha in open(prof).read():
+        assert v is not None and v > 0 and where.endswith("launch_list_cas40_D2048_bond19.md")
+    else:
+        assert v is None
+    assert bench.profiled_traffic(a, False) == (None, None)
+    assert bench.profiled_traffic(argparse.Namespace(traffic=5.0), False) == (5.0, "--traffic")
