@@ -379,6 +379,20 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     app_ms += g.sweep_device_ms()
     t_app = time.perf_counter() - t_app0
     left, right = g.block_dims()
+    # schedule autotuning at the middle bond (split tcgen05 path): each
+    # candidate schedule computes one product of a Davidson solve of the bond
+    # and the fastest is kept for its sector histogram
+    schedule = None
+    if prec in (pkg.SPLIT_HPSI_TC, pkg.SPLIT_ALL_TC) and not args.no_autotune:
+        cands = pkg.tc_shape_candidates()
+        g.set_tc_autotune(True)
+        g.bond_solve(mid, 1, prec, max_iter=1, tol=args.tol, min_calls=len(cands), check64=False)
+        products += len(cands)
+        info = g.tc_schedule()
+        schedule = {"picked": {"tile_n": info["shape"][0], "chunks_per_cta": info["shape"][1],
+                               "order": info["shape"][2]},
+                    "candidates": [{"tile_n": c[0], "chunks_per_cta": c[1], "order": c[2], "ms": t}
+                                   for c, t in zip(cands, info["ms"])]}
     # warm-up products at the middle bond
     g.bond_solve(mid, 1, prec, max_iter=max(1, W - 1), tol=args.tol, min_calls=W, check64=False)
     # ---- timed region: K products inside the Davidson solve of the middle bond
@@ -455,6 +469,7 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
                 "dtype": "tf32x3" if prec != pkg.FP64 else "f64", "data": "synthetic",
                 "config": {"workload": f"{wl['desc']}: H_eff psi at the middle bond {mid} at D={args.D}",
                            "D": args.D, "bond": mid, "ramp": ramp_list, "approach_davidson_iters": args.approach_iters,
+                           "schedule": schedule,
                            "precision": args.precision, "davidson_tol": args.tol,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": ("operators larger than L2" if mem_peak > 4 * L2_BYTES
@@ -491,7 +506,8 @@ def run_sweep(args, pkg, prec, rank, world, dist, device):
     t_job0 = time.perf_counter()
     g = pkg.DMRG(wl["h"], eri=wl["eri"], chol=wl["chol"], n_elec=wl["n_elec"], two_s=wl["two_s"],
                  D=ds[0], e_core=wl["e_core"], precision=prec, tol=args.tol, device=device,
-                 verbose=args.verbose, occ=occ, two_s_right=path)
+                 verbose=args.verbose, occ=occ, two_s_right=path,
+                 tc_autotune=prec in (pkg.SPLIT_HPSI_TC, pkg.SPLIT_ALL_TC) and not args.no_autotune)
     flops_job = 0.0
     for d in ds:
         g.set_bond_dim(d)
@@ -595,6 +611,8 @@ def main():
                          "renormalisation; fp64: all FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="bond mode: keep the default schedule of the tcgen05 launch (no timing of candidates)")
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--verbose", type=int, default=0, help="library diagnostics on stderr (2: H_eff psi shapes)")
     ap.add_argument("--hpsi-only", action="store_true",

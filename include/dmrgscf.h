@@ -105,6 +105,16 @@ typedef struct {
                              psi's column index (sum of kb over items; 0:
                              after every item; default 1024) -- shorter is
                              slightly more accurate and slower                */
+  int tc_autotune;        /* 1: DMRG_SPLIT_HPSI_TC / DMRG_SPLIT_ALL_TC pick the
+                             schedule of each H_eff psi launch (tile width,
+                             item chunks per CTA, task order; see
+                             dmrg_tc_shape_candidates) by timing: the first
+                             products with a new sector histogram run the
+                             candidate schedules in turn (every one computes
+                             the full product) and the fastest is kept for
+                             that histogram.  0 (default): the first candidate.
+                             Results differ between schedules only by FP32
+                             summation order                                  */
 } dmrg_opts;
 
 /* Fill *o with defaults: D=64, 200 iterations, tol 1e-10, FP64, space 24,
@@ -229,6 +239,31 @@ dmrg_status dmrg_set_kernel_wait_timeout(double seconds);
 /* tc_drain_terms (see dmrg_opts) of the kernel-level dmrg_hpsi_contract,
  * process-wide; default 1024. */
 dmrg_status dmrg_set_kernel_tc_drain_terms(int terms);
+
+/*
+ * Schedules of the batched tcgen05 H_eff psi launch (Sec. II.B products, all
+ * sector blocks of one product in one persistent launch).  A schedule is
+ * {tile width N of the 128 x N sigma tiles, item chunks per CTA, task order
+ * (0: longest cluster task first onto the least-loaded cluster; 1: sigma
+ * block by sigma block)}.  dmrg_tc_shape_candidates writes the candidates
+ * the autotuner times, the default first, as triples into shapes (room for
+ * cap triples; *count receives their number).
+ */
+dmrg_status dmrg_tc_shape_candidates(int* shapes, int cap, int* count);
+
+/* Schedule candidate (index into dmrg_tc_shape_candidates) of the kernel-level
+ * dmrg_hpsi_contract with DMRG_SPLIT_HPSI_TC (process-wide; default 0). */
+dmrg_status dmrg_set_kernel_tc_shape(int candidate);
+
+/* Turns the autotuning of tc_autotune (see dmrg_opts) on or off for a
+ * context; tuned schedules already found stay cached. */
+dmrg_status dmrg_set_tc_autotune(dmrg_ctx* ctx, int on);
+
+/* The schedule of the last planned tcgen05 H_eff psi launch of ctx: shape[3]
+ * as above; ms[k] (k < min(cap, *count)) the CUDA-event time in ms of one
+ * product under candidate k for that product's sector histogram (-1: not
+ * timed, or autotuning off).  DMRG_ESTATE before the first tcgen05 product. */
+dmrg_status dmrg_tc_schedule_info(const dmrg_ctx* ctx, int* shape, double* ms, int cap, int* count);
 
 /* Change the bond dimension used by subsequent sweeps. */
 dmrg_status dmrg_set_bond_dim(dmrg_ctx* ctx, int D);

@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("debug_bounds", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("wait_timeout_s", ctypes.c_double),
                 ("trunc_target", ctypes.c_double), ("D_min", ctypes.c_int),
-                ("rq64_every_bond", ctypes.c_int), ("tc_drain_terms", ctypes.c_int)]
+                ("rq64_every_bond", ctypes.c_int), ("tc_drain_terms", ctypes.c_int),
+                ("tc_autotune", ctypes.c_int)]
 
 
 class BondResult(ctypes.Structure):
@@ -85,6 +86,14 @@ def load(path=None):
     lib.dmrg_set_wait_timeout.restype = I
     lib.dmrg_set_kernel_tc_drain_terms.argtypes = [I]
     lib.dmrg_set_kernel_tc_drain_terms.restype = I
+    lib.dmrg_tc_shape_candidates.argtypes = [ip, I, ip]
+    lib.dmrg_tc_shape_candidates.restype = I
+    lib.dmrg_set_kernel_tc_shape.argtypes = [I]
+    lib.dmrg_set_kernel_tc_shape.restype = I
+    lib.dmrg_set_tc_autotune.argtypes = [P, I]
+    lib.dmrg_set_tc_autotune.restype = I
+    lib.dmrg_tc_schedule_info.argtypes = [P, ip, dp, I, ip]
+    lib.dmrg_tc_schedule_info.restype = I
     lib.dmrg_set_kernel_wait_timeout.argtypes = [D]
     lib.dmrg_set_kernel_wait_timeout.restype = I
     lib.dmrg_set_davidson.argtypes = [P, I, D]
@@ -137,6 +146,23 @@ def set_kernel_tc_drain_terms(terms):
     _check(lib, None, lib.dmrg_set_kernel_tc_drain_terms(int(terms)))
 
 
+def tc_shape_candidates():
+    """Schedules the autotuner of the tcgen05 H_eff psi launch tries, default
+    first: a list of (tile width, item chunks per CTA, task order)."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib, None, lib.dmrg_tc_shape_candidates(None, 0, ctypes.byref(n)))
+    buf = np.zeros(3 * n.value, dtype=np.int32)
+    _check(lib, None, lib.dmrg_tc_shape_candidates(_ip(buf), n.value, ctypes.byref(n)))
+    return [tuple(int(x) for x in buf[3 * k:3 * k + 3]) for k in range(n.value)]
+
+
+def set_kernel_tc_shape(candidate):
+    """Schedule candidate of the kernel-level tcgen05 contraction (process-wide)."""
+    lib = load()
+    _check(lib, None, lib.dmrg_set_kernel_tc_shape(int(candidate)))
+
+
 def set_kernel_wait_timeout(seconds):
     """Bound of the device waits of the kernel-level entry points (process-wide)."""
     lib = load()
@@ -161,7 +187,8 @@ class DMRG:
                  tol=1e-10, precision=FP64, max_iter=200, max_space=24, verbose=0,
                  device=0, occ=None, two_s_right=None, strict_convergence=False,
                  debug_bounds=False, seed=0, hbm_budget_bytes=0, wait_timeout_s=None,
-                 trunc_target=0.0, D_min=1, rq64_every_bond=False, tc_drain_terms=None):
+                 trunc_target=0.0, D_min=1, rq64_every_bond=False, tc_drain_terms=None,
+                 tc_autotune=False):
         lib = load()
         self._lib = lib
         h = np.ascontiguousarray(h, dtype=np.float64)
@@ -183,6 +210,7 @@ class DMRG:
         o.rq64_every_bond = int(bool(rq64_every_bond))
         if tc_drain_terms is not None:
             o.tc_drain_terms = int(tc_drain_terms)
+        o.tc_autotune = int(bool(tc_autotune))
         occ_a = None if occ is None else np.ascontiguousarray(occ, dtype=np.int32)
         path_a = None if two_s_right is None else np.ascontiguousarray(two_s_right, dtype=np.int32)
         ctx = ctypes.c_void_p()
@@ -232,6 +260,19 @@ class DMRG:
 
     def set_wait_timeout(self, seconds):
         _check(self._lib, self._ctx, self._lib.dmrg_set_wait_timeout(self._ctx, float(seconds)))
+
+    def set_tc_autotune(self, on=True):
+        _check(self._lib, self._ctx, self._lib.dmrg_set_tc_autotune(self._ctx, int(bool(on))))
+
+    def tc_schedule(self):
+        """Schedule of the last planned tcgen05 product: {"shape": (tile width,
+        chunks per CTA, order), "ms": per-candidate product times (-1: not timed)}."""
+        shape = np.zeros(3, dtype=np.int32)
+        n = ctypes.c_int()
+        ms = np.full(16, -1.0)
+        _check(self._lib, self._ctx, self._lib.dmrg_tc_schedule_info(self._ctx, _ip(shape), _dp(ms), 16,
+                                                                      ctypes.byref(n)))
+        return {"shape": tuple(int(x) for x in shape), "ms": [float(x) for x in ms[:n.value]]}
 
     def set_davidson(self, max_iter, tol):
         _check(self._lib, self._ctx, self._lib.dmrg_set_davidson(self._ctx, int(max_iter), float(tol)))

@@ -153,9 +153,10 @@ class Backend {
   size_t peak_bytes = 0; // high-water mark of bytes_in_use()
   size_t window_peak = 0;  // high-water mark since the caller last reset it
   // Device-side interval on the backend stream (CUDA events): mark_begin()
-  // then mark_end() returns the elapsed milliseconds.
-  virtual void mark_begin() = 0;
-  virtual double mark_end() = 0;
+  // then mark_end() returns the elapsed milliseconds (synchronising the
+  // stream).  Two independent slots (0, 1) so that intervals can nest.
+  virtual void mark_begin(int slot = 0) = 0;
+  virtual double mark_end(int slot = 0) = 0;
   virtual void set_profile(bool on) = 0;
 
  protected:

@@ -662,16 +662,21 @@ class CudaBackend : public Backend {
     }
     recs.clear();
   }
-  cudaEvent_t mb_ = nullptr, me_ = nullptr;
-  void mark_begin() override {
-    if (!mb_) { CK(cudaEventCreate(&mb_)); CK(cudaEventCreate(&me_)); }
-    CK(cudaEventRecord(mb_, st));
+  cudaEvent_t mb_[2] = {nullptr, nullptr}, me_[2] = {nullptr, nullptr};
+  void mark_begin(int slot) override {
+    if (slot < 0 || slot > 1) throw std::logic_error("internal: event slot out of range");
+    if (!mb_[slot]) {
+      CK(cudaEventCreate(&mb_[slot]));
+      CK(cudaEventCreate(&me_[slot]));
+    }
+    CK(cudaEventRecord(mb_[slot], st));
   }
-  double mark_end() override {
-    CK(cudaEventRecord(me_, st));
-    CK(cudaEventSynchronize(me_));
+  double mark_end(int slot) override {
+    if (slot < 0 || slot > 1 || !mb_[slot]) throw std::logic_error("internal: event slot not started");
+    CK(cudaEventRecord(me_[slot], st));
+    CK(cudaEventSynchronize(me_[slot]));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, mb_, me_));
+    CK(cudaEventElapsedTime(&ms, mb_[slot], me_[slot]));
     return ms;
   }
   void set_profile(bool on) override {
@@ -708,6 +713,11 @@ class CudaBackend : public Backend {
     }
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k)
+      if (mb_[k]) {
+        cudaEventDestroy(mb_[k]);
+        cudaEventDestroy(me_[k]);
+      }
     if (dtask) cudaFreeAsync(dtask, st);
     if (part) cudaFreeAsync(part, st);
     if (dflag) cudaFreeAsync(dflag, st);

@@ -31,6 +31,8 @@ namespace {
 // wait bound of the kernel-level entry points (dmrg_set_kernel_wait_timeout)
 std::atomic<unsigned long long> g_kernel_wait_ns{2000000000ull};
 std::atomic<int> g_kernel_drain_terms{dmrg::kTcDrainTerms};
+// schedule shape of the kernel-level contraction (index into the candidates)
+std::atomic<int> g_kernel_tc_cand{0};
 thread_local std::string tl_err;
 thread_local double tl_contract_ms = 0.0;
 
@@ -137,6 +139,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->D_min = 1;
   o->rq64_every_bond = 0;
   o->tc_drain_terms = dmrg::kTcDrainTerms;
+  o->tc_autotune = 0;
 }
 
 dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const double* chol,
@@ -216,6 +219,7 @@ dmrg_status dmrg_init(dmrg_ctx** out, const double* h, const double* eri, const 
     eo.D_min = o.D_min;
     eo.rq64_every_bond = o.rq64_every_bond != 0;
     eo.tc_drain_terms = o.tc_drain_terms;
+    eo.tc_autotune = o.tc_autotune != 0;
     ctx->strict = o.strict_convergence != 0;
     ctx->eng = std::make_unique<dmrg::Engine>(ctx->be.get(), n, h, g, e_core, n_elec, two_s, eo,
                                               oc.data(), path.data());
@@ -328,6 +332,41 @@ dmrg_status dmrg_set_wait_timeout(dmrg_ctx* c, double seconds) {
 dmrg_status dmrg_set_kernel_tc_drain_terms(int terms) {
   if (terms < 0) return fail(nullptr, DMRG_EINVAL, "terms < 0");
   g_kernel_drain_terms.store(terms);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_tc_shape_candidates(int* shapes, int cap, int* count) {
+  const auto c = dmrg::tc_shape_candidates();
+  if (!count || (cap > 0 && !shapes)) return fail(nullptr, DMRG_EINVAL, "NULL argument");
+  *count = (int)c.size();
+  for (int k = 0; k < std::min(cap, (int)c.size()); ++k) {
+    shapes[3 * k] = c[k].tile_n;
+    shapes[3 * k + 1] = c[k].chunks_per_cta;
+    shapes[3 * k + 2] = c[k].order;
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_kernel_tc_shape(int candidate) {
+  if (candidate < 0 || candidate >= (int)dmrg::tc_shape_candidates().size())
+    return fail(nullptr, DMRG_EINVAL, "schedule candidate out of range");
+  g_kernel_tc_cand.store(candidate);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_set_tc_autotune(dmrg_ctx* c, int on) {
+  if (!c || !c->eng) return fail(c, DMRG_EINVAL, "invalid context");
+  c->eng->set_tc_autotune(on != 0);
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_tc_schedule_info(const dmrg_ctx* c, int* shape, double* ms, int cap, int* count) {
+  if (!c || !c->eng) return fail(nullptr, DMRG_EINVAL, "invalid context");
+  if (!shape || !count || (cap > 0 && !ms)) return fail(nullptr, DMRG_EINVAL, "NULL argument");
+  std::vector<double> t;
+  if (!c->eng->tc_schedule_info(shape, &t)) return fail(nullptr, DMRG_ESTATE, "no tcgen05 product planned yet");
+  *count = (int)t.size();
+  for (int k = 0; k < std::min(cap, (int)t.size()); ++k) ms[k] = t[k];
   return DMRG_OK;
 }
 
@@ -645,7 +684,8 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     if (tc) {
       const int tc_ctas = dmrg::hpsi_tc_max_ctas();
       dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp,
-                            tc_ctas > 0 ? tc_ctas : be->sm_count());
+                            tc_ctas > 0 ? tc_ctas : be->sm_count(),
+                            dmrg::tc_shape_candidates()[g_kernel_tc_cand.load()]);
       tasks = tp.tasks;
       reds = tp.reds;
       scr = tp.scratch;
@@ -689,6 +729,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
       L.pool = pool;
       L.units = tp.units;
       L.drain_terms = g_kernel_drain_terms.load();
+      L.tile_n = tp.shape.tile_n;
       be->hpsi_tc(L, fl);
     } else {
       be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),

@@ -1439,6 +1439,15 @@ struct HPsiPlan {
   SplitJob* d_psi_jobs = nullptr;
   int n_psi_jobs = 0;
   TcLaunch tc;  // device lists of the persistent contraction
+  // operands and schedule on the host (rescheduled while autotuning), the
+  // device lists and scratch of the current schedule, and the tuning state
+  std::unique_ptr<TcPlan> tcp;
+  std::vector<HpsiBlock> tc_blocks;
+  int tc_ncta = 0;
+  void* sched = nullptr;
+  bool tuning = false;
+  uint64_t tune_key = 0;
+  int tc_cand = 0;  // candidate of the current schedule (index into the candidate list)
   int ntasks = 0, nreds = 0;
   size_t nitems = 0;
   double flops = 0.0;
@@ -1604,21 +1613,40 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   std::vector<HpsiReduce> reds;
   plan.prec = opt_.prec;
   const bool tc = plan.prec == Precision::TC_TF32X3;
-  TcPlan tp;
-  size_t scr;
+  TcPlan tp_local;
+  TcPlan& tp = tc ? *(plan.tcp = std::make_unique<TcPlan>()) : tp_local;
+  size_t scr = 0;
   if (tc) {
     if (plan.tc_pool) be_->free(plan.tc_pool);
     plan.tc_pool = nullptr;
     const int tc_ctas = hpsi_tc_max_ctas();
-    hpsi_tc_prepare(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp,
-                    tc_ctas > 0 ? tc_ctas : be_->sm_count());
+    plan.tc_ncta = tc_ctas > 0 ? tc_ctas : be_->sm_count();
+    hpsi_tc_operands(blocks, items, [&](size_t bytes) { return plan.tc_pool = be_->alloc(bytes); }, tp);
+    plan.tc_blocks = blocks;
+    // the schedule: the default shape, or with autotuning the fastest shape
+    // of this sector histogram, or the next candidate still to be timed
+    plan.tc_cand = 0;
+    plan.tuning = false;
+    if (opt_.tc_autotune) {
+      const size_t nc = tc_shape_candidates().size();
+      plan.tune_key = tc_histogram_key(blocks, plan.tc_ncta);
+      TuneRec& rec = tune_cache_[plan.tune_key];
+      if (rec.ms.size() != nc) rec.ms.assign(nc, -1.0);
+      if (rec.best >= 0) {
+        plan.tc_cand = rec.best;
+      } else {
+        plan.tuning = true;
+        while (plan.tc_cand < (int)nc && rec.ms[plan.tc_cand] >= 0) ++plan.tc_cand;
+      }
+    }
+    hpsi_tc_schedule(blocks, tp, tc_shape_candidates()[plan.tc_cand], plan.tc_ncta);
     if (opt_.debug_bounds) {
       const std::string bad = tc_plan_check(tp, blocks);
       if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
     }
-    tasks = tp.tasks;
-    reds = tp.reds;
-    scr = tp.scratch;
+    last_tc_key_ = opt_.tc_autotune ? plan.tune_key : 0;
+    last_tc_cand_ = plan.tc_cand;
+    have_tc_plan_ = true;
   } else {
     scr = hpsi_plan_tasks(blocks, plan.prec, tasks, reds);
   }
@@ -1632,11 +1660,13 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   size_t orr = al(ot + tasks.size() * sizeof(HpsiTask));
   size_t oj = al(orr + reds.size() * sizeof(HpsiReduce));
   size_t opj = al(oj + tp.op_jobs.size() * sizeof(SplitJob));
-  size_t oco = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
-  size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
-  size_t os = al(oct + tp.cta_task.size() * sizeof(TcSlot));
+  // (the tcgen05 schedule's lists and scratch live in plan.sched)
+  size_t os = al(opj + tp.psi_jobs.size() * sizeof(SplitJob));
   size_t total = os + scr * sizeof(double) + 256;
   if (plan.dev) be_->free(plan.dev);
+  plan.dev = nullptr;
+  if (plan.sched) be_->free(plan.sched);
+  plan.sched = nullptr;
   plan.dev = be_->alloc(total);
   char* d = (char*)plan.dev;
   plan.d_blocks = (HpsiBlock*)(d + ob);
@@ -1654,30 +1684,16 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
   if (!reds.empty()) be_->copy_h2d(plan.d_reds, reds.data(), reds.size() * sizeof(HpsiReduce));
   if (!tp.psi_jobs.empty())
     be_->copy_h2d(plan.d_psi_jobs, tp.psi_jobs.data(), tp.psi_jobs.size() * sizeof(SplitJob));
-  if (tc) {
-    if (!tp.cta_off.empty()) be_->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
-    if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(TcSlot));
-    plan.tc = TcLaunch();
-    plan.tc.blocks = plan.d_blocks;
-    plan.tc.items = plan.d_tcitems;
-    plan.tc.tasks = plan.d_tasks;
-    plan.tc.cta_off = (const int*)(d + oco);
-    plan.tc.cta_task = (const TcSlot*)(d + oct);
-    plan.tc.ncta = (int)tp.cta_off.size() - 1;
-    plan.tc.reds = plan.d_reds;
-    plan.tc.nreds = (int)reds.size();
-    plan.tc.scratch = (double*)(d + os);
-    plan.tc.pool = plan.tc_pool;
-    plan.tc.units = tp.units;
-    plan.tc.drain_terms = opt_.tc_drain_terms;
-  }
+  if (tc) tc_upload_schedule(plan);
   if (!tp.op_jobs.empty()) {
     // operator blocks (and identities) are constant during Davidson: split them once
     be_->copy_h2d(d + oj, tp.op_jobs.data(), tp.op_jobs.size() * sizeof(SplitJob));
     be_->split((const SplitJob*)(d + oj), (int)tp.op_jobs.size(), (float*)plan.tc_pool);
   }
-  plan.ntasks = (int)tasks.size();
-  plan.nreds = (int)reds.size();
+  if (!tc) {
+    plan.ntasks = (int)tasks.size();
+    plan.nreds = (int)reds.size();
+  }
   plan.nitems = items.size();
   be_->sync();
   const double tp3 = now_s();
@@ -1711,11 +1727,99 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
 }
 
 
+// Device lists and scratch of the plan's current tcgen05 schedule, in an
+// allocation of their own (replaced when the plan is rescheduled).
+void Engine::tc_upload_schedule(HPsiPlan& plan) {
+  const TcPlan& tp = *plan.tcp;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t ot = 0;
+  const size_t orr = al(ot + tp.tasks.size() * sizeof(HpsiTask));
+  const size_t oco = al(orr + tp.reds.size() * sizeof(HpsiReduce));
+  const size_t oct = al(oco + tp.cta_off.size() * sizeof(int));
+  const size_t os = al(oct + tp.cta_task.size() * sizeof(TcSlot));
+  const size_t total = os + tp.scratch * sizeof(double) + 256;
+  if (plan.sched) be_->free(plan.sched);
+  plan.sched = nullptr;
+  plan.sched = be_->alloc(total);
+  char* d = (char*)plan.sched;
+  if (!tp.tasks.empty()) be_->copy_h2d(d + ot, tp.tasks.data(), tp.tasks.size() * sizeof(HpsiTask));
+  if (!tp.reds.empty()) be_->copy_h2d(d + orr, tp.reds.data(), tp.reds.size() * sizeof(HpsiReduce));
+  if (!tp.cta_off.empty()) be_->copy_h2d(d + oco, tp.cta_off.data(), tp.cta_off.size() * sizeof(int));
+  if (!tp.cta_task.empty()) be_->copy_h2d(d + oct, tp.cta_task.data(), tp.cta_task.size() * sizeof(TcSlot));
+  plan.d_tasks = (HpsiTask*)(d + ot);
+  plan.d_reds = (HpsiReduce*)(d + orr);
+  plan.scratch = (double*)(d + os);
+  plan.tc = TcLaunch();
+  plan.tc.blocks = plan.d_blocks;
+  plan.tc.items = plan.d_tcitems;
+  plan.tc.tasks = plan.d_tasks;
+  plan.tc.cta_off = (const int*)(d + oco);
+  plan.tc.cta_task = (const TcSlot*)(d + oct);
+  plan.tc.ncta = (int)tp.cta_off.size() - 1;
+  plan.tc.reds = plan.d_reds;
+  plan.tc.nreds = (int)tp.reds.size();
+  plan.tc.scratch = plan.scratch;
+  plan.tc.pool = plan.tc_pool;
+  plan.tc.units = tp.units;
+  plan.tc.drain_terms = opt_.tc_drain_terms;
+  plan.tc.tile_n = tp.shape.tile_n;
+  plan.ntasks = (int)tp.tasks.size();
+  plan.nreds = (int)tp.reds.size();
+}
+
+void Engine::tc_reschedule(HPsiPlan& plan, int candidate) {
+  be_->sync();  // the old lists and scratch may still be read by queued work
+  hpsi_tc_schedule(plan.tc_blocks, *plan.tcp, tc_shape_candidates()[candidate], plan.tc_ncta);
+  if (opt_.debug_bounds) {
+    const std::string bad = tc_plan_check(*plan.tcp, plan.tc_blocks);
+    if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
+  }
+  plan.tc_cand = candidate;
+  last_tc_cand_ = candidate;
+  tc_upload_schedule(plan);
+}
+
+bool Engine::tc_schedule_info(int shape[3], std::vector<double>* ms) const {
+  if (!have_tc_plan_ || last_tc_cand_ < 0) return false;
+  const TcShape s = tc_shape_candidates()[last_tc_cand_];
+  shape[0] = s.tile_n;
+  shape[1] = s.chunks_per_cta;
+  shape[2] = s.order;
+  if (ms) {
+    ms->assign(tc_shape_candidates().size(), -1.0);
+    auto it = tune_cache_.find(last_tc_key_);
+    if (last_tc_key_ && it != tune_cache_.end() && it->second.ms.size() == ms->size()) *ms = it->second.ms;
+  }
+  return true;
+}
+
 void Engine::apply_hpsi(HPsiPlan& plan) {
   be_->memset0(plan.out, plan.psi.size * sizeof(double));
   if (plan.prec == Precision::TC_TF32X3) {
     be_->split(plan.d_psi_jobs, plan.n_psi_jobs, (float*)plan.tc_pool);
+    if (!plan.tuning) {
+      be_->hpsi_tc(plan.tc, plan.flops);
+      return;
+    }
+    // Autotuning: every candidate schedule of this sector histogram computes
+    // one real product, timed on the device (contraction and chunk
+    // reduction); once all were timed the fastest is kept for this plan and
+    // every later plan with the same histogram.
+    be_->mark_begin(1);
     be_->hpsi_tc(plan.tc, plan.flops);
+    const double ms = be_->mark_end(1);
+    be_->check_device_flag();
+    TuneRec& rec = tune_cache_[plan.tune_key];
+    if (rec.ms[plan.tc_cand] < 0) rec.ms[plan.tc_cand] = ms;
+    int next = -1;
+    for (size_t k = 0; k < rec.ms.size() && next < 0; ++k)
+      if (rec.ms[k] < 0) next = (int)k;
+    if (next < 0) {
+      rec.best = (int)(std::min_element(rec.ms.begin(), rec.ms.end()) - rec.ms.begin());
+      plan.tuning = false;
+      next = rec.best;
+    }
+    if (next != plan.tc_cand) tc_reschedule(plan, next);
   } else {
     be_->hpsi(plan.d_blocks, plan.d_items, plan.d_tasks, plan.ntasks, plan.d_reds, plan.nreds,
               plan.scratch, plan.prec, plan.flops);
@@ -2540,6 +2644,7 @@ double Engine::optimize_bond(int i, bool l2r, double* trunc) {
   be_->free(plan.in);
   be_->free(plan.out);
   if (plan.dev) be_->free(plan.dev);
+  if (plan.sched) be_->free(plan.sched);
   if (plan.tc_pool) be_->free(plan.tc_pool);
   if (plan.diag) be_->free(plan.diag);
   bond_extra_ = be_->window_peak > bond_start ? be_->window_peak - bond_start : 0;
@@ -2683,10 +2788,14 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
     throw;
   }
   call_ms_ = nullptr;
-  // the tcgen05 operand pool is not needed past the products
+  // the tcgen05 operand pool and schedule are not needed past the products
   if (plan.tc_pool) {
     be_->free(plan.tc_pool);
     plan.tc_pool = nullptr;
+  }
+  if (plan.sched) {
+    be_->free(plan.sched);
+    plan.sched = nullptr;
   }
   {
     double c1 = 0.0, s1 = 0.0;

@@ -164,6 +164,15 @@ struct Options {
   int D_min = 1;              // lower bound of the dynamic bond dimension
   bool rq64_every_bond = false;  // split runs: float64 Rayleigh quotient at every bond
   int tc_drain_terms = 1024;      // FP32 accumulation length of the tcgen05 contraction
+  bool tc_autotune = false;  // time the candidate schedules of each sector histogram, keep the fastest
+};
+
+// Autotuning record of one sector histogram of the tcgen05 contraction: the
+// CUDA-event time of one product under each candidate schedule (-1: not yet
+// timed) and the fastest once all were timed.
+struct TuneRec {
+  std::vector<double> ms;
+  int best = -1;
 };
 
 struct SweepStats {
@@ -230,6 +239,7 @@ class Engine {
     opt_.max_davidson_iter = max_iter;
     opt_.davidson_tol = tol;
   }
+  void set_tc_autotune(bool on) { opt_.tc_autotune = on; }
   void set_precision(Precision p, Precision pr) {
     opt_.prec = p;
     opt_.prec_renorm = pr;
@@ -248,6 +258,11 @@ class Engine {
   void rdm12(double* gamma, double* Gamma);
 
   Backend* backend() const { return be_; }
+  // Schedule of the last planned tcgen05 H_eff psi product: shape = {tile
+  // width, item chunks per CTA, task order}; ms[k] = time of candidate k of
+  // tc_shape_candidates() for its sector histogram (-1: not timed); returns
+  // false when no tcgen05 product was planned yet.
+  bool tc_schedule_info(int shape[3], std::vector<double>* ms) const;
   // device and pinned-host bytes of the stored blocks, the largest one, and
   // the largest working memory of a bond beyond the stored blocks so far
   void memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra,
@@ -321,6 +336,14 @@ class Engine {
   void build_comp_from_normal(const Block& b, OpSet& dst, const std::vector<OpKey>& keys);
   std::unique_ptr<Block> renormalize(Block& enl, const SavedU& U, bool switch_to_comp);
   void tc_contract(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items, double flops);
+  // tcgen05 schedules of a planned product: device lists and scratch of the
+  // plan's current shape; rescheduling for another shape keeps the operands
+  void tc_upload_schedule(struct HPsiPlan& plan);
+  void tc_reschedule(struct HPsiPlan& plan, int candidate);
+  std::map<uint64_t, TuneRec> tune_cache_;
+  uint64_t last_tc_key_ = 0;
+  int last_tc_cand_ = -1;
+  bool have_tc_plan_ = false;
   void build_initial_right();
   void plan_hpsi(Block& Le, Block& Re, struct HPsiPlan& plan);
   void apply_hpsi(struct HPsiPlan& plan);

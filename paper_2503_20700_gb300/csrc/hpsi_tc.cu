@@ -255,6 +255,7 @@ struct Walk {
   int sct;  // super-chunk within the task
   int acc;          // sum of kb over the items since the last drain, this one included
   int drain_terms;  // drain once acc reaches it
+  int tile_n;       // column width of the plan's tiles (multiple of 16, <= TNMAX)
   TcItem it;
   bool valid;
 };
@@ -262,7 +263,7 @@ __device__ __forceinline__ void walk_task(Walk& w) {
   w.sl = w.list[w.t];
   w.tk = w.tasks[w.sl.task];
   const HpsiBlock bk = w.blocks[w.tk.block];
-  const int nvalid = min(TNMAX, bk.n - w.tk.c0);
+  const int nvalid = min(w.tile_n, bk.n - w.tk.c0);
   w.N = (nvalid + 15) & ~15;
   w.ii = w.tk.it_begin;
   w.k = 0;
@@ -274,8 +275,9 @@ __device__ __forceinline__ void walk_task(Walk& w) {
 }
 __device__ __forceinline__ void walk_start(Walk& w, const HpsiBlock* blocks, const TcItem* items,
                                            const HpsiTask* tasks, const TcSlot* list, int t0, int t1,
-                                           int drain_terms, int rank) {
+                                           int drain_terms, int tile_n, int rank) {
   w.drain_terms = drain_terms;
+  w.tile_n = tile_n;
   w.blocks = blocks;
   w.items = items;
   w.tasks = tasks;
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
                    const TcSlot* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
-                   unsigned long long wait_ns, int drain_terms) {
+                   unsigned long long wait_ns, int drain_terms, int tile_n) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[B_COUNT];
   __shared__ uint32_t tmem_base;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // the fill order of the MMA issuer: stage 1 in the order of s1_now,
       // stage 2 of every piece of a tile
       Walk s2w;
-      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, tile_n, rank);
       S1Order o;
       s1_order_start(o, s2w);
       while (ok && s2w.valid) {
@@ -626,7 +628,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         return true;
       };
       Walk s2w;
-      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
+      walk_start(s2w, blocks, items, tasks, cta_task, t0, t1, drain_terms, tile_n, rank);
       S1Order o;
       s1_order_start(o, s2w);
       while (ok && s2w.valid) {
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       return true;
     };
     Walk w;
-    walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms, rank);
+    walk_start(w, blocks, items, tasks, cta_task, t0, t1, drain_terms, tile_n, rank);
     int drains_in_task = 0, last_t = -1;
     bool pend = false, pend_first = false;
     long long pend_part = 0;
@@ -840,10 +842,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // tile over its chunks in fixed order, thread t taking row t % 128 of every
 // second column
 __global__ void hpsi_tc_reduce(const HpsiBlock* __restrict__ blocks, const HpsiReduce* __restrict__ reds,
-                               const double* __restrict__ scratch) {
+                               const double* __restrict__ scratch, int tile_n) {
   const HpsiReduce rd = reds[blockIdx.x];
   const HpsiBlock bk = blocks[rd.block];
-  const int nvalid = min(TNMAX, bk.n - rd.c0);
+  const int nvalid = min(tile_n, bk.n - rd.c0);
   const int r = threadIdx.x & (TM - 1), gr = rd.r0 + r;
   if (gr >= bk.m) return;
   const int cend = min(nvalid, (int)blockIdx.y * 32 + 32);
@@ -966,6 +968,8 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
     cudaError_t e = ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES);
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc attribute: ") + cudaGetErrorString(e));
   }
+  if (L.tile_n < 16 || L.tile_n > TNMAX || L.tile_n % 16)
+    throw std::runtime_error("internal: tcgen05 tile width not a multiple of 16 in [16, 256]");
   if (L.ncta > 0) {
     if (!L.pool || L.units == 0) throw std::runtime_error("internal: tcgen05 contraction without a split pool");
     if (((uintptr_t)L.pool & 15) != 0) throw std::runtime_error("internal: split pool not 16-byte aligned");
@@ -977,12 +981,12 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
     cudaLaunchAttribute attr[1];
     launch_config(cfg, attr, L.ncta, st);
     cudaError_t e = cudaLaunchKernelEx(&cfg, hpsi_tc_kernel, m32, m64, L.blocks, L.items, L.tasks, L.cta_off,
-                                       L.cta_task, L.scratch, err, wait_ns, L.drain_terms);
+                                       L.cta_task, L.scratch, err, wait_ns, L.drain_terms, L.tile_n);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }
   if (L.nreds > 0) {
-    hpsi_tc_reduce<<<dim3(L.nreds, TNMAX / 32), 256, 0, st>>>(L.blocks, L.reds, L.scratch);
+    hpsi_tc_reduce<<<dim3(L.nreds, (L.tile_n + 31) / 32), 256, 0, st>>>(L.blocks, L.reds, L.scratch, L.tile_n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc reduce: ") + cudaGetErrorString(e));
   }

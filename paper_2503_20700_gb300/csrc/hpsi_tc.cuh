@@ -84,7 +84,27 @@ struct TcSlot {
   int ghost;
 };
 
+// Schedule of a planned contraction: the column width of the sigma tiles
+// (multiple of 16, at most kTcTileN; stage-1 sharing is per group of tiles
+// with the same rows), the number of tasks per CTA that the item chunks aim
+// at (finer chunks: better balance, more partial tiles), and the order in
+// which cluster tasks are placed on the clusters (0: longest first onto the
+// least-loaded cluster; 1: sigma block by sigma block, the cluster tasks of
+// one block and item chunk dealt round-robin, so that the CTAs running at
+// the same time share their operands in L2).
+struct TcShape {
+  int tile_n = kTcTileN;
+  int chunks_per_cta = 4;
+  int order = 0;
+  bool operator==(const TcShape& o) const {
+    return tile_n == o.tile_n && chunks_per_cta == o.chunks_per_cta && order == o.order;
+  }
+};
+// The shapes an autotuner tries, the default first.
+std::vector<TcShape> tc_shape_candidates();
+
 struct TcPlan {
+  TcShape shape;                   // of tasks, reds and the CTA lists
   std::vector<SplitJob> op_jobs;   // operator blocks and identities (run once per plan)
   std::vector<SplitJob> psi_jobs;  // psi blocks (run before every product)
   std::vector<TcItem> items;
@@ -94,6 +114,7 @@ struct TcPlan {
   std::vector<TcSlot> cta_task;    // the CTAs of a cluster have lists of equal length, entry k of
                                    // each belonging to the same block and item chunk
   size_t scratch = 0;              // 8-byte words of partial tiles (kTcTileM x kTcTileN float pairs per task)
+  double cost = 0.0;               // modelled tensor work of the launch (busiest cluster)
   size_t units = 0;                // pool size in 1 KB units
   size_t pool_bytes = 0;
 };
@@ -103,7 +124,19 @@ struct TcPlan {
 // returns the device memory of the pool; the caller owns it.  ncta: CTAs of
 // the persistent launch, rounded down to whole clusters (0: 152).
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
-                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta = 0);
+                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta = 0,
+                     const TcShape& shape = TcShape());
+// The two phases of hpsi_tc_prepare: the operands (split jobs, pool, item
+// descriptors), which do not depend on the schedule, and the schedule
+// (tasks, reductions, CTA lists and scratch size) for a shape; a plan can be
+// rescheduled for another shape without touching its operands.
+void hpsi_tc_operands(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
+                      const std::function<void*(size_t)>& alloc, TcPlan& plan);
+void hpsi_tc_schedule(const std::vector<HpsiBlock>& blocks, TcPlan& plan, const TcShape& shape, int ncta = 0);
+// Key of the sector histogram of a contraction (block shapes in 64-row and
+// 64-column steps with their item counts on a log scale, and the CTA count):
+// contractions with equal keys share an autotuned shape.
+uint64_t tc_histogram_key(const std::vector<HpsiBlock>& blocks, int ncta);
 
 // Device-side lists and the pool of one planned contraction.
 struct TcLaunch {
@@ -122,6 +155,7 @@ struct TcLaunch {
   // tile: once the items since the last drain reach this many terms of psi's
   // column index (sum of kb), after the item (0: after every item)
   int drain_terms = kTcDrainTerms;
+  int tile_n = kTcTileN;  // column width of the tiles the plan was scheduled for
 };
 
 // Runs the split jobs (device list of n jobs) into the pool.

@@ -37,10 +37,43 @@ double stage2_cost(int kb, int N) {
 double item_cost(int ka, int kb, int N) { return stage1_cost(ka, kb) + stage2_cost(kb, N); }
 }  // namespace
 
+std::vector<TcShape> tc_shape_candidates() {
+  std::vector<TcShape> c;
+  c.push_back(TcShape{kTcTileN, 4, 0});  // the default
+  c.push_back(TcShape{kTcTileN, 8, 0});  // finer item chunks
+  c.push_back(TcShape{kTcTileN, 2, 0});  // coarser item chunks
+  c.push_back(TcShape{kTcTileN, 4, 1});  // block order
+  c.push_back(TcShape{128, 4, 0});       // narrow tiles
+  return c;
+}
+
+uint64_t tc_histogram_key(const std::vector<HpsiBlock>& blocks, int ncta) {
+  std::vector<uint64_t> h;
+  h.reserve(blocks.size());
+  for (const HpsiBlock& b : blocks) {
+    if (b.item_count <= 0 || b.m <= 0 || b.n <= 0) continue;
+    int lg = 0;
+    while ((1 << (lg + 1)) <= b.item_count) ++lg;
+    h.push_back(((uint64_t)ceil_div(b.m, 64) << 40) | ((uint64_t)ceil_div(b.n, 64) << 16) | (uint64_t)lg);
+  }
+  std::sort(h.begin(), h.end());
+  uint64_t k = 0x84222325cbf29ce4ull ^ (uint64_t)ncta;
+  for (uint64_t x : h) {
+    k ^= x + 0x9e3779b97f4a7c15ull + (k << 6) + (k >> 2);
+    k *= 0x100000001b3ull;
+  }
+  return k;
+}
+
 void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
-                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta) {
+                     const std::function<void*(size_t)>& alloc, TcPlan& plan, int ncta, const TcShape& shape) {
+  hpsi_tc_operands(blocks, items, alloc, plan);
+  hpsi_tc_schedule(blocks, plan, shape, ncta);
+}
+
+void hpsi_tc_operands(const std::vector<HpsiBlock>& blocks, const std::vector<HpsiItem>& items,
+                      const std::function<void*(size_t)>& alloc, TcPlan& plan) {
   plan = TcPlan();
-  if (ncta <= 0) ncta = 152;
   // Distinct operands (src, trans, rows, cols, ld) become split jobs, numbered
   // in first-occurrence order over the references (items in block order;
   // roles A, P^T, B).  An identity factor is the operand (nullptr, 0, d, d, -1).
@@ -160,7 +193,21 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     if (item_blk[i] < 0) {  // an item of no block: never referenced by a task
       plan.items[i] = TcItem{TcMat{}, TcMat{}, TcMat{}, items[i].ka, items[i].kb, items[i].alpha};
     }
-  // Tasks: 128 x 256 tiles, the items of a tile cut into contiguous chunks of
+}
+
+void hpsi_tc_schedule(const std::vector<HpsiBlock>& blocks, TcPlan& plan, const TcShape& shape, int ncta) {
+  if (ncta <= 0) ncta = 152;
+  const int TN = shape.tile_n;
+  if (TN < 16 || TN > TNMAX || TN % 16 || shape.chunks_per_cta < 1 || shape.order < 0 || shape.order > 1)
+    throw std::invalid_argument("tcgen05 plan: invalid schedule shape");
+  plan.shape = shape;
+  plan.tasks.clear();
+  plan.reds.clear();
+  plan.cta_off.clear();
+  plan.cta_task.clear();
+  plan.scratch = 0;
+  plan.cost = 0.0;
+  // Tasks: 128 x TN tiles, the items of a tile cut into contiguous chunks of
   // about equal tensor work, so that the launch has a few tasks per CTA.
   double total = 0.0;
   std::vector<std::vector<double>> icost(blocks.size());
@@ -168,8 +215,8 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     const HpsiBlock& bk = blocks[b];
     if (bk.item_count == 0 || bk.m == 0 || bk.n == 0) continue;
     icost[b].resize(bk.item_count);
-    for (int c0 = 0; c0 < bk.n; c0 += TNMAX) {
-      const int N = std::min(TNMAX, (std::min(TNMAX, bk.n - c0) + 15) & ~15);
+    for (int c0 = 0; c0 < bk.n; c0 += TN) {
+      const int N = std::min(TN, (std::min(TN, bk.n - c0) + 15) & ~15);
       for (int k = 0; k < bk.item_count; ++k) {
         const TcItem& t = plan.items[bk.item_begin + k];
         const double c = item_cost(t.ka, t.kb, N);
@@ -178,7 +225,7 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
       }
     }
   }
-  const double target = std::max(1.0, total / (4.0 * ncta));
+  const double target = std::max(1.0, total / ((double)shape.chunks_per_cta * ncta));
   // Cluster tasks: kTcCluster tasks of the same block and item chunk.  The
   // column tiles of one row tile are grouped kTcCluster at a time (a group
   // shares stage 1); the remainder groups of the rows are packed first-fit
@@ -193,6 +240,8 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     double cost = 0.0;
   };
   std::vector<CTask> ctasks;
+  std::vector<int> ct_block;     // sigma block of each cluster task
+  std::vector<double> blk_cost(blocks.size(), 0.0);
   std::vector<double> s1c, s2c;  // per task: stage-1 and stage-2 cost of its items
   long long part = 0;
   const long long tile = (long long)TM * TNMAX;
@@ -212,13 +261,13 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     }
     cuts.push_back(bk.item_count);
     const int nch = (int)cuts.size() - 1;
-    const int mt = ceil_div(bk.m, TM), nt = ceil_div(bk.n, TNMAX);
+    const int mt = ceil_div(bk.m, TM), nt = ceil_div(bk.n, TN);
     // tasks in (tile, chunk) order: the chunks of a tile have consecutive partial tiles
     const int t_first = (int)plan.tasks.size();
     for (int r = 0; r < mt; ++r)
       for (int c = 0; c < nt; ++c) {
-        const int r0 = r * TM, c0 = c * TNMAX;
-        const int N = std::min(TNMAX, (std::min(TNMAX, bk.n - c0) + 15) & ~15);
+        const int r0 = r * TM, c0 = c * TN;
+        const int N = std::min(TN, (std::min(TN, bk.n - c0) + 15) & ~15);
         plan.reds.push_back({(int)b, r0, c0, nch, part});
         for (int ch = 0; ch < nch; ++ch) {
           const int i0 = bk.item_begin + cuts[ch], cnt = cuts[ch + 1] - cuts[ch];
@@ -244,6 +293,7 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
             CTask ct;
             for (int q = 0; q < C; ++q) ct.m.push_back({g[q], 0, C});
             ctasks.push_back(ct);
+            ct_block.push_back((int)b);
           } else {
             rem.push_back(g);
           }
@@ -253,7 +303,10 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
       for (const auto& g : rem) {
         size_t k = open0;
         while (k < ctasks.size() && ctasks[k].m.size() + g.size() > (size_t)C) ++k;
-        if (k == ctasks.size()) ctasks.emplace_back();
+        if (k == ctasks.size()) {
+          ctasks.emplace_back();
+          ct_block.push_back((int)b);
+        }
         const int g0 = (int)ctasks[k].m.size();
         for (int t : g) ctasks[k].m.push_back({t, g0, (int)g.size()});
       }
@@ -265,13 +318,26 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     for (const Member& mb : ct.m) w = std::max(w, s1c[mb.task] / mb.grpn + s2c[mb.task]);
     ct.cost = w + 1.0;  // drain
   }
-  // Persistent launch: longest cluster task first onto the least-loaded
-  // cluster; each cluster runs its tasks in decreasing cost.
+  for (size_t k = 0; k < ctasks.size(); ++k) blk_cost[ct_block[k]] += ctasks[k].cost;
+  // Persistent launch, order 0: longest cluster task first onto the
+  // least-loaded cluster; each cluster runs its tasks in decreasing cost.
+  // Order 1: sigma blocks in decreasing total cost, the cluster tasks of a
+  // block in (item chunk, row, column) order, each onto the least-loaded
+  // cluster; the tasks running at one time then come from a short stretch of
+  // that list and share their operand tiles.
   const int nct = (int)ctasks.size();
   const int nclu = std::max(1, std::min(std::max(1, ncta / C), nct));
   std::vector<int> order(nct);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctasks[a].cost > ctasks[b].cost; });
+  if (shape.order == 0)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctasks[a].cost > ctasks[b].cost; });
+  else
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const int ba = ct_block[a], bb = ct_block[b];
+      if (ba == bb) return false;
+      if (blk_cost[ba] != blk_cost[bb]) return blk_cost[ba] > blk_cost[bb];
+      return ba < bb;
+    });
   using Load = std::pair<double, int>;
   std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
   for (int c = 0; c < nclu; ++c) pq.push({0.0, c});
@@ -281,6 +347,10 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
     pq.pop();
     lists[l.second].push_back(t);
     pq.push({l.first + ctasks[t].cost, l.second});
+  }
+  while (!pq.empty()) {
+    plan.cost = std::max(plan.cost, pq.top().first);
+    pq.pop();
   }
   if (nct == 0) {
     plan.cta_off.assign(1, 0);
@@ -302,6 +372,8 @@ void hpsi_tc_prepare(const std::vector<HpsiBlock>& blocks, const std::vector<Hps
 }
 
 std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& blocks) {
+  if (plan.shape.tile_n < 16 || plan.shape.tile_n > TNMAX || plan.shape.tile_n % 16)
+    return "tile width not a multiple of 16 in [16, 256]";
   auto fits = [&](const TcMat& m, int rows, int cols) {
     if (m.unit < 0 || m.groups != ceil_div(rows, 8)) return false;
     return (size_t)m.unit + 2 * (size_t)m.groups * (size_t)ceil_div(cols, 32) <= plan.units;
@@ -312,7 +384,7 @@ std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& bloc
     const std::string at = "task " + std::to_string(t) + ": ";
     if (tk.block < 0 || tk.block >= (int)blocks.size()) return at + "block out of range";
     const HpsiBlock& bk = blocks[tk.block];
-    if (tk.r0 < 0 || tk.r0 >= bk.m || tk.r0 % TM || tk.c0 < 0 || tk.c0 >= bk.n || tk.c0 % TNMAX)
+    if (tk.r0 < 0 || tk.r0 >= bk.m || tk.r0 % TM || tk.c0 < 0 || tk.c0 >= bk.n || tk.c0 % plan.shape.tile_n)
       return at + "tile origin out of range";
     if (tk.it_count < 1 || tk.it_begin < bk.item_begin || tk.it_begin + tk.it_count > bk.item_begin + bk.item_count ||
         tk.it_begin + tk.it_count > (int)plan.items.size())

@@ -68,7 +68,7 @@ static void check_pool() {
 
 using Key = std::tuple<const double*, int, int, int, int>;
 
-static void check_plan(unsigned seed) {
+static void check_plan(unsigned seed, const TcShape& shape) {
   std::mt19937 rng(seed);
   const int nblk = 3 + rng() % 12;
   std::vector<int> dims(nblk);
@@ -110,8 +110,31 @@ static void check_plan(unsigned seed) {
   size_t pool_bytes = 0;
   TcPlan plan;
   const int ncta = 5 + (int)(seed % 7) * 23;
-  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { pool_bytes = bytes; return (void*)pool; }, plan, ncta);
+  hpsi_tc_prepare(blocks, items, [&](size_t bytes) { pool_bytes = bytes; return (void*)pool; }, plan, ncta,
+                  shape);
+  CHECK(plan.shape == shape);
   CHECK(plan.pool_bytes == pool_bytes);
+  {
+    // a plan made for the default shape and rescheduled equals one made for
+    // this shape directly; the operands are untouched by rescheduling
+    TcPlan other;
+    hpsi_tc_prepare(blocks, items, [&](size_t) { return (void*)pool; }, other, ncta);
+    const size_t units0 = other.units;
+    const size_t items0 = other.items.size();
+    hpsi_tc_schedule(blocks, other, shape, ncta);
+    CHECK(other.units == units0 && other.items.size() == items0);
+    CHECK(other.tasks.size() == plan.tasks.size() && other.cta_task.size() == plan.cta_task.size());
+    CHECK(other.cta_off == plan.cta_off && other.scratch == plan.scratch);
+    for (size_t t = 0; t < std::min(other.tasks.size(), plan.tasks.size()); ++t)
+      CHECK(other.tasks[t].block == plan.tasks[t].block && other.tasks[t].c0 == plan.tasks[t].c0 &&
+            other.tasks[t].it_begin == plan.tasks[t].it_begin && other.tasks[t].part == plan.tasks[t].part);
+    for (size_t e = 0; e < std::min(other.cta_task.size(), plan.cta_task.size()); ++e)
+      CHECK(other.cta_task[e].task == plan.cta_task[e].task && other.cta_task[e].ghost == plan.cta_task[e].ghost);
+    // the histogram key ignores the order of the blocks
+    std::vector<HpsiBlock> rev(blocks.rbegin(), blocks.rend());
+    CHECK(tc_histogram_key(rev, ncta) == tc_histogram_key(blocks, ncta));
+    CHECK(tc_histogram_key(blocks, ncta) != tc_histogram_key(blocks, ncta + 2));
+  }
   CHECK(plan.pool_bytes == plan.units * kTcUnitFloats * sizeof(float));
   // expected jobs: first occurrences in reference order; an identity factor
   // is the operand (nullptr, 0, d, d, -1)
@@ -229,7 +252,7 @@ static void check_plan(unsigned seed) {
     const HpsiBlock& bk = blocks[b];
     if (bk.item_count == 0) continue;
     for (int r0 = 0; r0 < bk.m; r0 += kTcTileM)
-      for (int c0 = 0; c0 < bk.n; c0 += kTcTileN) {
+      for (int c0 = 0; c0 < bk.n; c0 += shape.tile_n) {
         ++tiles;
         auto& v = chunks[{b, r0, c0}];
         int next = bk.item_begin;
@@ -286,7 +309,10 @@ static void check_jacobi_batches(unsigned seed, int cap) {
 int main() {
   check_pool();
   for (unsigned s = 1; s <= 40; ++s) check_jacobi_batches(s, s % 3 ? 152 : 40);
-  for (unsigned s = 1; s <= 12; ++s) check_plan(s);
+  const std::vector<TcShape> cands = tc_shape_candidates();
+  CHECK(!cands.empty() && cands[0] == TcShape());
+  for (unsigned s = 1; s <= 12; ++s)
+    for (const TcShape& sh : cands) check_plan(s, sh);
   if (fails) {
     std::printf("%d checks failed\n", fails);
     return 1;

@@ -4,7 +4,7 @@
 // whether the planner's own check passes.  Input: the number of blocks, then
 // per block "m n items" and per item "ka kb idA idB transA transB a p b"
 // (idA/idB: identity factor; a, p, b: operand numbers, equal numbers naming
-// the same matrix).  Usage: tc_plan_dump problem.txt ncta
+// the same matrix).  Usage: tc_plan_dump problem.txt ncta [schedule candidate]
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +19,9 @@ int main(int argc, char** argv) {
   FILE* f = std::fopen(argv[1], "r");
   if (!f) return 2;
   const int ncta = std::atoi(argv[2]);
+  const int cand = argc > 3 ? std::atoi(argv[3]) : 0;
+  const std::vector<TcShape> cands = tc_shape_candidates();
+  if (cand < 0 || cand >= (int)cands.size()) return 2;
   int nb = 0;
   if (std::fscanf(f, "%d", &nb) != 1) return 3;
   std::vector<HpsiBlock> blocks;
@@ -55,10 +58,11 @@ int main(int argc, char** argv) {
   }
   std::fclose(f);
   TcPlan plan;
-  hpsi_tc_prepare(blocks, items, [](size_t) { return (void*)(uintptr_t(1) << 44); }, plan, ncta);
+  hpsi_tc_prepare(blocks, items, [](size_t) { return (void*)(uintptr_t(1) << 44); }, plan, ncta, cands[cand]);
   const std::string bad = tc_plan_check(plan, blocks);
   std::printf("check %s\n", bad.empty() ? "ok" : bad.c_str());
   std::printf("cluster %d\n", kTcCluster);
+  std::printf("tile_n %d\n", plan.shape.tile_n);
   std::printf("blocks %zu\n", blocks.size());
   for (const HpsiBlock& b : blocks) std::printf("%d %d\n", b.m, b.n);
   std::printf("items %zu\n", plan.items.size());

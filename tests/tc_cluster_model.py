@@ -34,6 +34,7 @@ def parse_plan(text):
     lines = iter(text.splitlines())
     check = next(lines).split(None, 1)[1]
     cluster = int(next(lines).split()[1])
+    tile_n = int(next(lines).split()[1])
     nb = int(next(lines).split()[1])
     blocks = [tuple(map(int, next(lines).split())) for _ in range(nb)]
     ni = int(next(lines).split()[1])
@@ -45,7 +46,8 @@ def parse_plan(text):
     for _ in range(nc):
         f = next(lines).split()
         lists.append([tuple(map(int, e.split(","))) for e in f[1:]])
-    return dict(check=check, cluster=cluster, blocks=blocks, items=items, tasks=tasks, lists=lists)
+    return dict(check=check, cluster=cluster, tile_n=tile_n, blocks=blocks, items=items, tasks=tasks,
+                lists=lists)
 
 
 class Barrier:
@@ -76,7 +78,7 @@ class Walk:
         self.sl = self.list[self.t]
         self.tk = self.plan["tasks"][self.sl[0]]
         m, n = self.plan["blocks"][self.tk[0]]
-        self.N = (min(256, n - self.tk[2]) + 15) & ~15
+        self.N = (min(self.plan["tile_n"], n - self.tk[2]) + 15) & ~15
         self.ii, self.k, self.jc, self.p, self.sct = self.tk[3], 0, 0, 0, 0
         self.it = self.plan["items"][self.ii]
         self.acc = self.it[1]

@@ -54,10 +54,10 @@ def problem(seed, n_blocks, max_dim, max_items):
     return "\n".join(out) + "\n"
 
 
-def plan_of(dumper, tmp_path, text, ncta):
+def plan_of(dumper, tmp_path, text, ncta, cand=0):
     f = tmp_path / "problem.txt"
     f.write_text(text)
-    r = subprocess.run([dumper, str(f), str(ncta)], capture_output=True, text=True, timeout=120)
+    r = subprocess.run([dumper, str(f), str(ncta), str(cand)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     plan = M.parse_plan(r.stdout)
     assert plan["check"] == "ok", plan["check"]
@@ -80,6 +80,18 @@ def test_cluster_protocol_has_no_deadlock_or_hazard(dumper, tmp_path, seed, nb, 
                 assert status == "ok", (k, sched, drain, status, info)
     if dim > 256:
         assert shared > 0  # the plans exercise groups that share stage 1
+
+
+@pytest.mark.parametrize("cand", [1, 2, 3, 4])
+def test_cluster_protocol_under_every_schedule_candidate(dumper, tmp_path, cand):
+    """The autotuner's other schedules (finer and coarser item chunks, block
+    order, 128-wide tiles) keep the protocol free of deadlocks and hazards."""
+    for seed, nb, dim, items in CASES[:3]:
+        plan = plan_of(dumper, tmp_path, problem(seed, nb, dim, items), 24, cand)
+        C = plan["cluster"]
+        for k in range(len(plan["lists"]) // C):
+            status, info = M.run_cluster(plan, k, seed=seed, drain_terms=1024)
+            assert status == "ok", (cand, seed, k, status, info)
 
 
 def test_model_finds_the_unacknowledged_protocol_faulty(dumper, tmp_path):
