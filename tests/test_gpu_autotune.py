@@ -85,7 +85,8 @@ def test_bond_solve_times_every_candidate_and_keeps_the_fastest(pkg):
     g.sweep_part(1, mid + 1)
     g.set_tc_autotune(True)
     cands = pkg.tc_shape_candidates()
-    r = g.bond_solve(mid, 1, pkg.SPLIT_HPSI_TC, max_iter=3, tol=1e-8, min_calls=len(cands) + 2,
+    # the candidates are timed on the first products of the (converging) solve
+    r = g.bond_solve(mid, 1, pkg.SPLIT_HPSI_TC, max_iter=80, tol=1e-7, min_calls=len(cands) + 2,
                      check64=True)
     info = g.tc_schedule()
     g.close()
