@@ -23,6 +23,9 @@ The oracle is plain, slow, float64 numpy/scipy code written from the paper:
   their spin-coupled forms (Eq. rdm1_su2 and the two-channel 2-RDM).
 * ``casscf`` -- orbital rotation U = exp(-kappa), integral transformation,
   the CAS-SCF energy functional and its orbital gradient (Sec. II.A).
+* ``orbital`` -- one- and two-orbital reduced density matrices, orbital
+  entropies, mutual information and the Fiedler ordering of the orbitals
+  (Sec. II "Numerical procedure", the ordering step).
 
 The kernel-level tests (grouped GEMM, fused sector contraction, eigensolver)
 compare against the plain definition written inline in the test (a numpy
