@@ -290,6 +290,71 @@ dmrg_status dmrg_energy(const dmrg_ctx* ctx, double* energy);
 dmrg_status dmrg_rdm12(dmrg_ctx* ctx, double* gamma, double* Gamma);
 
 /*
+ * Orbital entanglement for the orbital-ordering step (Sec. II "Numerical
+ * procedure": a few low-D runs give the ordering from quantum-information
+ * measures of the state).  Same state and preconditions as dmrg_rdm12.
+ *
+ * dmrg_orbital_rdms -- one- and two-orbital reduced density matrices,
+ * averaged over the 2S+1 states of the multiplet (the SU(2)-invariant
+ * reduced states).  Local states of one orbital d = 2 n_up + n_dn (0 empty,
+ * 1 down, 2 up, 3 doubly occupied), the doubly occupied one a+_up a+_dn|0>.
+ *   rho1[4p + d]                    weight of local state d of orbital p
+ *   rho2[(p*n + q)*256 + 16 a + b]  for p < q: the 16 x 16 rho_pq over the
+ *       local states a = 4 d_p + d_q (creators applied in the order p-up,
+ *       p-dn, q-up, q-dn), defined by Tr(rho_pq X) = <X> for every operator
+ *       X of those four modes; entries with p >= q are set to zero.
+ * Host buffers of n*4 and n*n*256 doubles.  A measurement pass over all
+ * bonds evaluates, in float64 on the device, the expectation values of the
+ * number and double-occupancy strings of every orbital and of 15 coupled
+ * products [X_p (x) Y_q]^0 per pair (see dmrg_orbital_rdms_from_invariants);
+ * rho_pq follows from them exactly.
+ */
+dmrg_status dmrg_orbital_rdms(dmrg_ctx* ctx, double* rho1, double* rho2);
+
+/*
+ * dmrg_orbital_entanglement -- von Neumann entropies s1[p] = -Tr rho_p ln rho_p
+ * and the mutual information mutual[p*n + q] = s_p + s_q - s_pq (natural
+ * logarithm, zero diagonal) of the same reduced states; the spectra of all
+ * rho_pq come from one batched float64 eigensolver launch.
+ */
+dmrg_status dmrg_orbital_entanglement(dmrg_ctx* ctx, double* s1, double* mutual);
+
+/*
+ * dmrg_orbital_rdms_from_invariants -- host-only: the reduced density
+ * matrices of dmrg_orbital_rdms from the expectation values they are built
+ * from.  Single-orbital strings S_0..S_8 (spinors a+ and a~ of one orbital,
+ * a+(+1/2) = a+_up, a+(-1/2) = a+_dn, a~(+1/2) = a_dn, a~(-1/2) = -a_up,
+ * coupled left to right with Clebsch-Gordan coefficients to the listed
+ * doubled intermediate ranks):
+ *   S_0 a+   S_1 a~   S_2 [a+ a~]^0   S_3 [a+ a~]^1   S_4 [a+ a+]^0
+ *   S_5 [a~ a~]^0   S_6 [[a+ a+]^0 a~]^1/2   S_7 [[a~ a~]^0 a+]^1/2
+ *   S_8 [[[a+ a+]^0 a~]^1/2 a~]^0.
+ *   inv1[2p + t]  = <S_2 of p> (t = 0), <S_8 of p> (t = 1)
+ *   inv2[(p*n + q)*15 + mu] (p < q) = <[S_a of p (x) S_b of q]^0> for
+ *       (a, b) = (2,2) (2,8) (8,2) (8,8) (3,3) (0,1) (0,7) (6,1) (6,7)
+ *                (1,0) (1,6) (7,0) (7,6) (4,5) (5,4), mu in that order.
+ * These 15, the four single-orbital scalars and the identity span the
+ * operators of two orbitals that commute with their spin and particle
+ * number; rho_pq is the member of that span with these expectation values.
+ */
+dmrg_status dmrg_orbital_rdms_from_invariants(int n, const double* inv1, const double* inv2, double* rho1,
+                                              double* rho2);
+
+/*
+ * dmrg_fiedler_order -- orbital ordering from the mutual information (the
+ * ordering of Sec. II "Numerical procedure"): the orbitals sorted by the
+ * Fiedler vector (eigenvector of the second-smallest eigenvalue, float64 on
+ * the device) of the graph Laplacian diag(I 1) - I, the minimiser of
+ * sum_pq I_pq (x_p - x_q)^2 over unit vectors orthogonal to the constant
+ * vector.  order[k] = orbital placed at site k; oriented so that order[0] <
+ * order[n-1]; equal components keep index order.  mutual: n x n symmetric
+ * host array (its diagonal is ignored); DMRG_EINVAL if it is not finite or
+ * not symmetric.  A degenerate second eigenvalue (e.g. a graph of separate
+ * components) leaves the order undetermined within that eigenspace.
+ */
+dmrg_status dmrg_fiedler_order(const double* mutual, int n, int* order, int device);
+
+/*
  * Statistics of the last sweep: total H_eff psi FLOPs (algorithmic, 2mnk per
  * product), time spent in H_eff psi (s), number of H_eff psi calls, total
  * Davidson iterations and the sweep wall time (s).  NULL outputs are skipped.

@@ -102,6 +102,14 @@ def load(path=None):
     lib.dmrg_set_bond_dim.restype = I
     lib.dmrg_set_precision.argtypes = [P, I]
     lib.dmrg_set_precision.restype = I
+    lib.dmrg_orbital_rdms.argtypes = [P, dp, dp]
+    lib.dmrg_orbital_rdms.restype = I
+    lib.dmrg_orbital_entanglement.argtypes = [P, dp, dp]
+    lib.dmrg_orbital_entanglement.restype = I
+    lib.dmrg_orbital_rdms_from_invariants.argtypes = [I, dp, dp, dp, dp]
+    lib.dmrg_orbital_rdms_from_invariants.restype = I
+    lib.dmrg_fiedler_order.argtypes = [dp, I, ip, I]
+    lib.dmrg_fiedler_order.restype = I
     lib.dmrg_energy.argtypes = [P, dp]
     lib.dmrg_energy.restype = I
     lib.dmrg_rdm12.argtypes = [P, dp, dp]
@@ -161,6 +169,30 @@ def set_kernel_tc_shape(candidate):
     """Schedule candidate of the kernel-level tcgen05 contraction (process-wide)."""
     lib = load()
     _check(lib, None, lib.dmrg_set_kernel_tc_shape(int(candidate)))
+
+
+def orbital_rdms_from_invariants(inv1, inv2):
+    """Host-only assembly of the orbital RDMs from their invariants (see
+    include/dmrgscf.h): inv1 (n, 2), inv2 (n, n, 15) -> (rho1 (n, 4), rho2
+    (n, n, 16, 16))."""
+    lib = load()
+    inv1 = np.ascontiguousarray(inv1, dtype=np.float64)
+    inv2 = np.ascontiguousarray(inv2, dtype=np.float64)
+    n = inv1.shape[0]
+    r1 = np.zeros((n, 4))
+    r2 = np.zeros((n, n, 16, 16))
+    _check(lib, None, lib.dmrg_orbital_rdms_from_invariants(n, _dp(inv1), _dp(inv2), _dp(r1), _dp(r2)))
+    return r1, r2
+
+
+def fiedler_order(mutual, device=0):
+    """Orbital order from the mutual information (Fiedler vector, on the device)."""
+    lib = load()
+    m = np.ascontiguousarray(mutual, dtype=np.float64)
+    n = m.shape[0]
+    order = np.zeros(n, dtype=np.int32)
+    _check(lib, None, lib.dmrg_fiedler_order(_dp(m), n, _ip(order), int(device)))
+    return order
 
 
 def set_kernel_wait_timeout(seconds):
@@ -298,6 +330,20 @@ class DMRG:
             self._ctx, g1.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             g2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return g1, g2
+
+    def orbital_rdms(self):
+        """(rho1 (n, 4), rho2 (n, n, 16, 16)) of the state of the last sweep."""
+        r1 = np.zeros((self.n, 4))
+        r2 = np.zeros((self.n, self.n, 16, 16))
+        _check(self._lib, self._ctx, self._lib.dmrg_orbital_rdms(self._ctx, _dp(r1), _dp(r2)))
+        return r1, r2
+
+    def orbital_entanglement(self):
+        """(one-orbital entropies (n,), mutual information (n, n))."""
+        s1 = np.zeros(self.n)
+        mi = np.zeros((self.n, self.n))
+        _check(self._lib, self._ctx, self._lib.dmrg_orbital_entanglement(self._ctx, _dp(s1), _dp(mi)))
+        return s1, mi
 
     def stats(self):
         f, s, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -1,5 +1,7 @@
 // extern "C" entry points (include/dmrgscf.h).
 #include <algorithm>
+#include <cmath>
+#include <numeric>
 #include <atomic>
 #include <cstring>
 #include <exception>
@@ -413,6 +415,39 @@ dmrg_status dmrg_rdm12(dmrg_ctx* c, double* gamma, double* Gamma) {
     c->eng->rdm12(gamma, Gamma);
   } catch (const std::exception& e) {
     return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_orbital_rdms(dmrg_ctx* c, double* rho1, double* rho2) {
+  if (!c || !c->eng || !rho1 || !rho2) return fail(c, DMRG_EINVAL, "invalid argument");
+  if (c->sweeps_done == 0) return fail(c, DMRG_ESTATE, "no sweep has run");
+  try {
+    c->eng->orbital_rdms(rho1, rho2);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_orbital_entanglement(dmrg_ctx* c, double* s1, double* mutual) {
+  if (!c || !c->eng || !s1 || !mutual) return fail(c, DMRG_EINVAL, "invalid argument");
+  if (c->sweeps_done == 0) return fail(c, DMRG_ESTATE, "no sweep has run");
+  try {
+    c->eng->orbital_entanglement(s1, mutual);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_orbital_rdms_from_invariants(int n, const double* inv1, const double* inv2, double* rho1,
+                                              double* rho2) {
+  if (n < 1 || n > 256 || !inv1 || !inv2 || !rho1 || !rho2) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  try {
+    dmrg::orbital_rdms_from_invariants(n, inv1, inv2, rho1, rho2);
+  } catch (const std::exception& e) {
+    return translate(nullptr, e);
   }
   return DMRG_OK;
 }
@@ -851,6 +886,47 @@ dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, doubl
   } catch (const std::exception& e) {
     return translate(nullptr, e);
   }
+  return DMRG_OK;
+}
+
+dmrg_status dmrg_fiedler_order(const double* mutual, int n, int* order, int device) {
+  if (!mutual || !order || n < 1 || n > 4096) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  double scale = 0.0;
+  for (size_t e = 0; e < (size_t)n * n; ++e) {
+    if (!std::isfinite(mutual[e])) return fail(nullptr, DMRG_EINVAL, "mutual information not finite");
+    scale = std::max(scale, std::abs(mutual[e]));
+  }
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < p; ++q)
+      if (std::abs(mutual[(size_t)p * n + q] - mutual[(size_t)q * n + p]) > 1e-12 * std::max(scale, 1e-300))
+        return fail(nullptr, DMRG_EINVAL, "mutual information not symmetric");
+  if (n < 3) {
+    for (int p = 0; p < n; ++p) order[p] = p;
+    return DMRG_OK;
+  }
+  // graph Laplacian L = diag(I 1) - I (diagonal of I ignored)
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      if (p != q) {
+        L[(size_t)p * n + q] = -mutual[(size_t)p * n + q];
+        L[(size_t)p * n + p] += mutual[(size_t)p * n + q];
+      }
+  std::vector<double> w(n), V((size_t)n * n);
+  const int nn[1] = {n};
+  const dmrg_status st = dmrg_eigh_batched(L.data(), nn, 1, w.data(), V.data(), device);
+  if (st != DMRG_OK) return st;
+  // eigenvalues descending: the Fiedler vector (second smallest) is row n-2;
+  // orbitals sorted by it, oriented so that the first is the smaller end
+  const double* f = &V[(size_t)(n - 2) * n];
+  std::vector<int> o(n);
+  std::iota(o.begin(), o.end(), 0);
+  std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return f[a] < f[b]; });
+  if (o.front() > o.back()) {
+    std::iota(o.begin(), o.end(), 0);
+    std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return f[a] > f[b]; });
+  }
+  std::copy(o.begin(), o.end(), order);
   return DMRG_OK;
 }
 

@@ -509,6 +509,41 @@ std::unique_ptr<Block> Engine::vacuum(bool left) {
 }
 
 // Blocking: enlarged block = b (x) site (left) or site (x) b (right).
+namespace {
+// Single-orbital operator strings of the orbital-entanglement pass: the
+// spinors a+ (dag 1) and a~ (dag 0) of one orbital coupled sequentially to
+// the doubled intermediate ranks kl.  Together with the identity they span
+// the SU(2) tensor operators of one orbital: number and double occupancy
+// (rank 0), spin (rank 1), a+ and a+ n (rank 1/2), pair creation (rank 0),
+// and the adjoints.
+struct OrbStr {
+  std::vector<int> dag, kl;
+};
+const std::vector<OrbStr>& orb_strings() {
+  static const std::vector<OrbStr> t = {
+      {{1}, {}},                  // 0  a+
+      {{0}, {}},                  // 1  a~
+      {{1, 0}, {0}},              // 2  [a+ a~]^0
+      {{1, 0}, {2}},              // 3  [a+ a~]^1
+      {{1, 1}, {0}},              // 4  [a+ a+]^0
+      {{0, 0}, {0}},              // 5  [a~ a~]^0
+      {{1, 1, 0}, {0, 1}},        // 6  [[a+ a+]^0 a~]^1/2
+      {{0, 0, 1}, {0, 1}},        // 7  [[a~ a~]^0 a+]^1/2
+      {{1, 1, 0, 0}, {0, 1, 0}},  // 8  [[[a+ a+]^0 a~]^1/2 a~]^0
+  };
+  return t;
+}
+int orb_rank(int a) { return orb_strings()[a].kl.empty() ? 1 : orb_strings()[a].kl.back(); }
+int orb_dn(int a) {
+  int d = 0;
+  for (int x : orb_strings()[a].dag) d += x ? 1 : -1;
+  return d;
+}
+constexpr int kOrbSite0 = 3000;  // OpKey.i of the strings of site p: kOrbSite0 + p
+OpKey orb_key(int site, int a) { return OpKey{K_T0 + orb_dn(a), kOrbSite0 + site, a, orb_rank(a)}; }
+bool is_orb_key(const OpKey& k) { return k.kind >= K_TM2 && k.i >= kOrbSite0; }
+}  // namespace
+
 std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   const SiteAlgebra& sa = site_algebra();
   const double t_start = now_s();
@@ -549,7 +584,15 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   else esites.insert(esites.begin(), site);
   const double t_alloc0 = now_s();
   std::vector<OpKey> keys;
-  if (rdm_mode_) {
+  if (rdm_mode_ && orb_mode_) {
+    // orbital-entanglement blocks: on the left, the single-orbital strings of
+    // every site (carried, and created for the new site); nothing on the right
+    if (b.left) {
+      for (auto& [k, ptr] : b.ops->ops)
+        if (is_orb_key(k)) keys.push_back(k);
+      for (int a = 0; a < (int)orb_strings().size(); ++a) keys.push_back(orb_key(site, a));
+    }
+  } else if (rdm_mode_) {
     // measurement blocks: the single spinors and, on normal blocks, the pairs
     for (const OpKey& k : op_keys(esites, n_, e->normal))
       if (k.kind == K_C || (e->normal && (k.kind == K_A || k.kind == K_B))) keys.push_back(k);
@@ -582,6 +625,17 @@ std::unique_ptr<Block> Engine::enlarge(const Block& b, int site) {
   };
   Operand I = op_id();
   const int s = site;
+  if (rdm_mode_ && orb_mode_) {
+    if (L) {
+      for (auto& [k, ptr] : b.ops->ops)
+        if (is_orb_key(k)) T(k, op_blk(k.kind, k.i, k.j, k.k2), op_site(sa.I), 1.0);
+      for (int a = 0; a < (int)orb_strings().size(); ++a)
+        T(orb_key(s, a), I, op_site(site_string(orb_strings()[a].dag, orb_strings()[a].kl)), 1.0);
+    }
+    stats_.t_enl_terms += now_s() - t_start;
+    place_terms(b, nullptr, *e, terms);
+    return e;
+  }
   std::vector<int> outs;
   for (int p = 0; p < n_; ++p)
     if (!in_sites(esites, p)) outs.push_back(p);
@@ -2928,7 +2982,7 @@ SweepStats Engine::sweep() {
 // against all W.
 
 struct Engine::RdmAcc {
-  std::vector<double> g1, g2;
+  std::vector<double> g1, g2, orb;
 };
 
 namespace {
@@ -3122,39 +3176,54 @@ void x_terms(int l, const int* pos, const int* dag, const std::vector<int>& kl, 
   }
 }
 
+// Request tables of the measurement pass at one bond (Engine::rdm_eval).
+struct RdmVKey {
+  int y, s, kX;
+  OpKey x;
+  int adj;
+  bool operator<(const RdmVKey& o) const {
+    if (y != o.y) return y < o.y;
+    if (s != o.s) return s < o.s;
+    if (kX != o.kX) return kX < o.kX;
+    if (adj != o.adj) return adj < o.adj;
+    return x < o.x;
+  }
+};
+struct RdmContrib {
+  size_t target;
+  int order;
+  double c;
+  int v;
+};
+
 }  // namespace
+
+struct Engine::RdmRequests {
+  std::map<std::pair<std::vector<int>, std::vector<int>>, int> s_index;
+  std::vector<SiteOp> s_ops;
+  std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, int> y_index;
+  std::vector<Operand> y_ops;
+  std::vector<std::pair<OpKey, SiteOp>> y_temps;  // site strings on the last site
+  std::map<RdmVKey, int> v_index;
+  std::vector<RdmVKey> vkeys;
+  std::vector<RdmContrib> contribs;
+};
 
 void Engine::rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rparent, const PsiLayout& P,
                       const double* psi, const std::vector<size_t>& elems, RdmAcc& acc) {
   const int n = n_;
   const size_t nn = (size_t)n * n;
   // ---------------------------------------------------------------- requests
-  struct VKey {
-    int y, s, kX;
-    OpKey x;
-    int adj;
-    bool operator<(const VKey& o) const {
-      if (y != o.y) return y < o.y;
-      if (s != o.s) return s < o.s;
-      if (kX != o.kX) return kX < o.kX;
-      if (adj != o.adj) return adj < o.adj;
-      return x < o.x;
-    }
-  };
-  struct Contrib {
-    size_t target;
-    int order;
-    double c;
-    int v;
-  };
-  std::map<std::pair<std::vector<int>, std::vector<int>>, int> s_index;
-  std::vector<SiteOp> s_ops;
-  std::map<std::tuple<int, int, std::vector<int>, std::vector<int>>, int> y_index;
-  std::vector<Operand> y_ops;
-  std::vector<std::pair<OpKey, SiteOp>> y_temps;  // site strings on the last site
-  std::map<VKey, int> v_index;
-  std::vector<VKey> vkeys;
-  std::vector<Contrib> contribs;
+  RdmRequests rq;
+  auto& s_index = rq.s_index;
+  auto& s_ops = rq.s_ops;
+  auto& y_index = rq.y_index;
+  auto& y_ops = rq.y_ops;
+  auto& y_temps = rq.y_temps;
+  auto& v_index = rq.v_index;
+  auto& vkeys = rq.vkeys;
+  auto& contribs = rq.contribs;
+  using VKey = RdmVKey;
   std::map<std::tuple<int, int, int, int, std::vector<std::pair<int, int>>>, std::vector<Variant>> vcache;
   const bool last = (i == n - 2);
   std::vector<XTerm> xt;
@@ -3237,6 +3306,22 @@ void Engine::rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rpare
       }
     }
   }
+  rdm_eval(Lb, Le, Re, Rparent, P, psi, rq, acc);
+}
+
+// Evaluation of the requests of one bond: every distinct (right operand Y,
+// site string s, coupling rank kX, stored L(i) operator x) gives
+//   <[[x (x) s]^kX (x) Y]^0>,
+// and each contribution adds c times its value to its target (order 1: the
+// 1-RDM, 2: the 2-RDM, 3: the orbital-entanglement invariants).
+void Engine::rdm_eval(Block& Lb, Block& Le, Block& Re, const Block& Rparent, const PsiLayout& P,
+                      const double* psi, RdmRequests& rq, RdmAcc& acc) {
+  auto& s_ops = rq.s_ops;
+  auto& y_ops = rq.y_ops;
+  auto& y_temps = rq.y_temps;
+  auto& vkeys = rq.vkeys;
+  auto& contribs = rq.contribs;
+  using VKey = RdmVKey;
   if (vkeys.empty()) return;
   // site strings of the last site as operators of R'
   if (!y_temps.empty()) {
@@ -3448,42 +3533,33 @@ void Engine::rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rpare
   }
   for (auto& c : contribs) {
     if (c.order == 1) acc.g1[c.target] += c.c * val[c.v];
-    else acc.g2[c.target] += c.c * val[c.v];
+    else if (c.order == 2) acc.g2[c.target] += c.c * val[c.v];
+    else acc.orb[c.target] += c.c * val[c.v];
   }
   for (double* N : Nbuf)
     if (N) be_->free(N);
   for (void* p : scratch) be_->free(p);
 }
 
-void Engine::rdm12(double* gamma, double* Gamma) {
-  if (!prev_.valid) throw std::runtime_error("state: no sweep has run");
-  drop_kept();  // the measurement pass needs the memory more than the next sweep
-  if (n_ < 3 || prev_.bond != 1 || (int)LU_.size() < 2 || !LU_[1])
-    throw std::runtime_error("state: the RDMs are taken at bond 1, the end of a full sweep");
+void Engine::measurement_walk(const std::function<void(int, Block&, Block&, Block&, const Block&,
+                                                        const PsiLayout&, const double*)>& at_bond) {
   const int n = n_;
-  const size_t nn = (size_t)n * n, n4 = nn * nn;
-  // bond of every element (1-RDM: index p*n+q; 2-RDM: nn + ((p*n+q)*n+r)*n+s)
-  std::vector<std::vector<size_t>> at(n - 1);
-  // (bond 0 is folded into bond 1, whose left block is site 0 itself)
-  for (int p = 0; p < n; ++p)
-    for (int q = 0; q < n; ++q) at[std::max(1, std::min(n - 2, std::max(p, q)))].push_back((size_t)p * n + q);
-  for (size_t t = 0; t < n4; ++t) {
-    int x[4] = {(int)(t / (nn * n)), (int)(t / nn % n), (int)(t / n % n), (int)(t % n)};
-    std::sort(x, x + 4);
-    at[std::max(1, std::min(n - 2, x[2]))].push_back(nn + t);
-  }
-  const Options saved = opt_;
-  rdm_mode_ = true;
-  opt_.prec_renorm = Precision::FP64;
-  opt_.D = 1 << 30;  // keep the whole support when moving the state
-  RdmAcc acc;
-  acc.g1.assign(nn, 0.0);
-  acc.g2.assign(n4, 0.0);
   std::vector<void*> owned;
+  auto add_identity = [&](Block& B) {
+    B.ops->allocate({kIdentityKey});
+    double* I = B.ops->get(kIdentityKey);
+    const Layout& L = B.ops->layout(0, 0);
+    if (!I || L.size == 0) return;
+    std::vector<double> h(L.size, 0.0);
+    for (auto& bl : L.blk)
+      if (bl.bra == bl.ket)
+        for (int r = 0; r < bl.rows; ++r) h[bl.off + (size_t)r * bl.cols + r] = 1.0;
+    be_->copy_h2d(I, h.data(), h.size() * sizeof(double));
+  };
   try {
     auto vac = vacuum(true);
     auto E0 = enlarge(*vac, 0);
-    {
+    if (!orb_mode_) {
       // strings of three and four operators on site 0 (elements with x3 = 0)
       std::vector<OpKey> keys;
       std::vector<std::pair<OpKey, Term>> terms;
@@ -3511,29 +3587,18 @@ void Engine::rdm12(double* gamma, double* Gamma) {
       place_terms(*vac, nullptr, *E0, terms);
     }
     std::unique_ptr<Block> Lb = renormalize(*E0, *LU_[1], false);
-    auto add_identity = [&](Block& B) {
-      B.ops->allocate({kIdentityKey});
-      double* I = B.ops->get(kIdentityKey);
-      const Layout& L = B.ops->layout(0, 0);
-      if (!I || L.size == 0) return;
-      std::vector<double> h(L.size, 0.0);
-      for (auto& bl : L.blk)
-        if (bl.bra == bl.ket)
-          for (int r = 0; r < bl.rows; ++r) h[bl.off + (size_t)r * bl.cols + r] = 1.0;
-      be_->copy_h2d(I, h.data(), h.size() * sizeof(double));
-    };
     add_identity(*Lb);
     auto Le = enlarge(*Lb, 1);
     resident(R_[n - 3].get());
     auto Re = enlarge(*R_[n - 3], 2);
     PsiLayout P = make_psi(Le->ops->basis, Re->ops->basis, n_elec_, two_s_);
-    if (P.size != prev_.len) throw std::runtime_error("internal: RDM pass layout differs from the state");
+    if (P.size != prev_.len) throw std::runtime_error("internal: measurement pass layout differs from the state");
     double* psi = (double*)be_->alloc(std::max<size_t>(P.size, 1) * sizeof(double));
     owned.push_back(psi);
     be_->copy_d2d(psi, prev_.psi, P.size * sizeof(double));
     for (int i = 1; i <= n - 2; ++i) {
       resident(R_[n - i - 2].get());
-      rdm_bond(i, *Lb, *Le, *Re, *R_[n - i - 2], P, psi, at[i], acc);
+      at_bond(i, *Lb, *Le, *Re, *R_[n - i - 2], P, psi);
       if (i == n - 2) break;
       // move the state to bond i+1, keeping its whole support
       HPsiPlan plan;
@@ -3571,15 +3636,388 @@ void Engine::rdm12(double* gamma, double* Gamma) {
     }
   } catch (...) {
     for (void* p : owned) be_->free(p);
+    throw;
+  }
+  for (void* p : owned) be_->free(p);
+}
+
+void Engine::rdm12(double* gamma, double* Gamma) {
+  if (!prev_.valid) throw std::runtime_error("state: no sweep has run");
+  drop_kept();  // the measurement pass needs the memory more than the next sweep
+  if (n_ < 3 || prev_.bond != 1 || (int)LU_.size() < 2 || !LU_[1])
+    throw std::runtime_error("state: the RDMs are taken at bond 1, the end of a full sweep");
+  const int n = n_;
+  const size_t nn = (size_t)n * n, n4 = nn * nn;
+  // bond of every element (1-RDM: index p*n+q; 2-RDM: nn + ((p*n+q)*n+r)*n+s)
+  std::vector<std::vector<size_t>> at(n - 1);
+  // (bond 0 is folded into bond 1, whose left block is site 0 itself)
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) at[std::max(1, std::min(n - 2, std::max(p, q)))].push_back((size_t)p * n + q);
+  for (size_t t = 0; t < n4; ++t) {
+    int x[4] = {(int)(t / (nn * n)), (int)(t / nn % n), (int)(t / n % n), (int)(t % n)};
+    std::sort(x, x + 4);
+    at[std::max(1, std::min(n - 2, x[2]))].push_back(nn + t);
+  }
+  const Options saved = opt_;
+  rdm_mode_ = true;
+  orb_mode_ = false;
+  opt_.prec_renorm = Precision::FP64;
+  opt_.D = 1 << 30;  // keep the whole support when moving the state
+  RdmAcc acc;
+  acc.g1.assign(nn, 0.0);
+  acc.g2.assign(n4, 0.0);
+  try {
+    measurement_walk([&](int i, Block& Lb, Block& Le, Block& Re, const Block& Rp, const PsiLayout& P,
+                         const double* psi) { rdm_bond(i, Lb, Le, Re, Rp, P, psi, at[i], acc); });
+  } catch (...) {
     rdm_mode_ = false;
     opt_ = saved;
     throw;
   }
-  for (void* p : owned) be_->free(p);
   rdm_mode_ = false;
   opt_ = saved;
   std::copy(acc.g1.begin(), acc.g1.end(), gamma);
   std::copy(acc.g2.begin(), acc.g2.end(), Gamma);
+}
+
+
+// ============================================================ orbital entanglement
+// The ordering step of Sec. II "Numerical procedure": one- and two-orbital
+// reduced density matrices of the state, from expectation values of SU(2)
+// invariants built from single-orbital strings.  For orbitals p < q the
+// invariants are [X_p (x) Y_q]^0 over the pairs (X, Y) of orb_strings() with
+// equal rank and opposite particle change, plus the single-orbital scalars
+// (number, double occupancy) of p and of q and the identity: 20 operators
+// spanning the operators of the two orbitals that commute with their total
+// spin and particle number.  The SU(2)-invariant (multiplet-averaged)
+// rho_pq is the unique matrix of that span with the measured expectation
+// values, found from the fixed Gram matrix of the 20 operators.
+namespace {
+const std::vector<std::pair<int, int>>& orb_pair_invariants() {
+  static const std::vector<std::pair<int, int>> t = {
+      {2, 2}, {2, 8}, {8, 2}, {8, 8},          // rank 0, no particle change
+      {3, 3},                                  // spin-spin
+      {0, 1}, {0, 7}, {6, 1}, {6, 7},          // rank 1/2: p gains, q loses a particle
+      {1, 0}, {1, 6}, {7, 0}, {7, 6},          // rank 1/2: q gains, p loses
+      {4, 5}, {5, 4}};                         // pair transfer
+  return t;
+}
+constexpr int kOrbScalar[2] = {2, 8};  // number and double occupancy
+
+// Fock space of `orbs` orbitals (modes up, down per orbital, Jordan-Wigner
+// order), state index sum_m occ_m 2^(M-1-m): for one orbital d = 2 n_up +
+// n_dn, for two a = 4 d_p + d_q.
+struct SmallFock {
+  int M = 0, dim = 0;
+  std::vector<std::vector<double>> cr;  // creator of each mode, dim x dim row-major
+  explicit SmallFock(int orbs) : M(2 * orbs), dim(1 << (2 * orbs)) {
+    cr.assign(M, std::vector<double>((size_t)dim * dim, 0.0));
+    for (int m = 0; m < M; ++m)
+      for (int a = 0; a < dim; ++a) {
+        const int bit = 1 << (M - 1 - m);
+        if (a & bit) continue;
+        int before = 0;
+        for (int k = 0; k < m; ++k) before += (a >> (M - 1 - k)) & 1;
+        cr[m][(size_t)(a | bit) * dim + a] = (before & 1) ? -1.0 : 1.0;
+      }
+  }
+  // spinor component (comp 0: +1/2, 1: -1/2) of a+ (dag) or a~ on orbital o:
+  // a+(+1/2) = a+_up, a+(-1/2) = a+_dn, a~(+1/2) = a_dn, a~(-1/2) = -a_up
+  std::vector<double> comp(int o, int dag, int c) const {
+    std::vector<double> r((size_t)dim * dim);
+    if (dag) return cr[2 * o + c];
+    const auto& src = cr[2 * o + (c == 0 ? 1 : 0)];
+    const double f = c == 0 ? 1.0 : -1.0;
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) r[(size_t)i * dim + j] = f * src[(size_t)j * dim + i];
+    return r;
+  }
+  // sum_mask T[mask] O_0(m_0) O_1(m_1) ... over the slots (orbital, dag)
+  std::vector<double> invariant(const std::vector<int>& orb, const std::vector<int>& dag,
+                                const std::vector<double>& T) const {
+    const int L = (int)orb.size();
+    std::vector<double> out((size_t)dim * dim, 0.0);
+    for (int mask = 0; mask < (1 << L); ++mask) {
+      if (T[mask] == 0.0) continue;
+      std::vector<double> P((size_t)dim * dim, 0.0);
+      for (int i = 0; i < dim; ++i) P[(size_t)i * dim + i] = 1.0;
+      for (int sl = 0; sl < L; ++sl) {
+        const std::vector<double> O = comp(orb[sl], dag[sl], (mask >> sl) & 1);
+        std::vector<double> Q((size_t)dim * dim, 0.0);
+        for (int i = 0; i < dim; ++i)
+          for (int k = 0; k < dim; ++k) {
+            const double pv = P[(size_t)i * dim + k];
+            if (pv == 0.0) continue;
+            for (int j = 0; j < dim; ++j) Q[(size_t)i * dim + j] += pv * O[(size_t)k * dim + j];
+          }
+        P.swap(Q);
+      }
+      for (size_t e = 0; e < out.size(); ++e) out[e] += T[mask] * P[e];
+    }
+    return out;
+  }
+};
+
+// matrix of [X_a (x) Y_b]^0 (a or b < 0: that orbital carries the identity)
+std::vector<double> orb_invariant_matrix(const SmallFock& F, int a, int b) {
+  const auto& os = orb_strings();
+  std::vector<int> orb, dag;
+  Variant v;
+  int la = 0, lb = 0;
+  if (a >= 0) {
+    la = (int)os[a].dag.size();
+    v.kl = os[a].kl;
+    for (int d : os[a].dag) orb.push_back(0), dag.push_back(d);
+  }
+  if (b >= 0) {
+    lb = (int)os[b].dag.size();
+    v.ks = os[b].kl;
+    for (int d : os[b].dag) orb.push_back(F.M == 4 ? 1 : 0), dag.push_back(d);
+  }
+  v.kX = 0;
+  if (la + lb == 0) {
+    std::vector<double> I((size_t)F.dim * F.dim, 0.0);
+    for (int i = 0; i < F.dim; ++i) I[(size_t)i * F.dim + i] = 1.0;
+    return I;
+  }
+  return F.invariant(orb, dag, tree_tensor(variant_tree(la, lb, 0, v), la + lb));
+}
+
+// inverse of a small symmetric positive definite matrix (Gauss-Jordan with
+// partial pivoting)
+std::vector<double> small_inverse(std::vector<double> A, int K) {
+  std::vector<double> X((size_t)K * K, 0.0);
+  for (int i = 0; i < K; ++i) X[(size_t)i * K + i] = 1.0;
+  double scale = 0.0;
+  for (double x : A) scale = std::max(scale, std::abs(x));
+  for (int c = 0; c < K; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < K; ++r)
+      if (std::abs(A[(size_t)r * K + c]) > std::abs(A[(size_t)piv * K + c])) piv = r;
+    if (std::abs(A[(size_t)piv * K + c]) < 1e-12 * scale)
+      throw std::logic_error("internal: orbital invariants are linearly dependent");
+    for (int j = 0; j < K; ++j) {
+      std::swap(A[(size_t)c * K + j], A[(size_t)piv * K + j]);
+      std::swap(X[(size_t)c * K + j], X[(size_t)piv * K + j]);
+    }
+    const double d = A[(size_t)c * K + c];
+    for (int j = 0; j < K; ++j) {
+      A[(size_t)c * K + j] /= d;
+      X[(size_t)c * K + j] /= d;
+    }
+    for (int r = 0; r < K; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * K + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < K; ++j) {
+        A[(size_t)r * K + j] -= f * A[(size_t)c * K + j];
+        X[(size_t)r * K + j] -= f * X[(size_t)c * K + j];
+      }
+    }
+  }
+  return X;
+}
+
+// The invariants of one and of two orbitals with their matrices and the
+// inverse Gram matrices (fixed tables, built once).
+struct OrbTables {
+  int K1 = 0, K2 = 0;
+  std::vector<std::vector<double>> M1, M2;
+  std::vector<double> G1inv, G2inv;
+  OrbTables() {
+    SmallFock F1(1), F2(2);
+    M1.push_back(orb_invariant_matrix(F1, -1, -1));
+    for (int a : kOrbScalar) M1.push_back(orb_invariant_matrix(F1, a, -1));
+    M2.push_back(orb_invariant_matrix(F2, -1, -1));
+    for (int a : kOrbScalar) M2.push_back(orb_invariant_matrix(F2, a, -1));
+    for (int b : kOrbScalar) M2.push_back(orb_invariant_matrix(F2, -1, b));
+    for (auto& [a, b] : orb_pair_invariants()) M2.push_back(orb_invariant_matrix(F2, a, b));
+    K1 = (int)M1.size();
+    K2 = (int)M2.size();
+    auto gram = [](const std::vector<std::vector<double>>& M) {
+      const int K = (int)M.size();
+      std::vector<double> G((size_t)K * K, 0.0);
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j)
+          for (size_t e = 0; e < M[i].size(); ++e) G[(size_t)i * K + j] += M[i][e] * M[j][e];
+      return G;
+    };
+    G1inv = small_inverse(gram(M1), K1);
+    G2inv = small_inverse(gram(M2), K2);
+  }
+};
+const OrbTables& orb_tables() {
+  static const OrbTables t;
+  return t;
+}
+
+// rho = sum_mu c_mu M_mu^T with G c = v (the member of the span of the
+// invariants whose expectation values are v), symmetrised
+void orb_solve(const std::vector<std::vector<double>>& M, const std::vector<double>& Ginv,
+               const std::vector<double>& v, int dim, double* rho) {
+  const int K = (int)M.size();
+  std::vector<double> c(K, 0.0);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) c[i] += Ginv[(size_t)i * K + j] * v[j];
+  std::vector<double> r((size_t)dim * dim, 0.0);
+  for (int mu = 0; mu < K; ++mu)
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) r[(size_t)i * dim + j] += c[mu] * M[mu][(size_t)j * dim + i];
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j)
+      rho[(size_t)i * dim + j] = 0.5 * (r[(size_t)i * dim + j] + r[(size_t)j * dim + i]);
+}
+}  // namespace
+
+int orbital_pair_invariant_count() { return (int)orb_pair_invariants().size(); }
+
+void orbital_rdms_from_invariants(int n, const double* inv1, const double* inv2, double* rho1, double* rho2) {
+  const OrbTables& T = orb_tables();
+  const int NP = (int)orb_pair_invariants().size();
+  std::vector<double> r4(16);
+  for (int p = 0; p < n; ++p) {
+    std::vector<double> v{1.0, inv1[2 * p], inv1[2 * p + 1]};
+    orb_solve(T.M1, T.G1inv, v, 4, r4.data());
+    for (int d = 0; d < 4; ++d) rho1[4 * p + d] = r4[5 * d];
+  }
+  std::fill(rho2, rho2 + (size_t)n * n * 256, 0.0);
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) {
+      std::vector<double> v{1.0, inv1[2 * p], inv1[2 * p + 1], inv1[2 * q], inv1[2 * q + 1]};
+      for (int mu = 0; mu < NP; ++mu) v.push_back(inv2[((size_t)p * n + q) * NP + mu]);
+      orb_solve(T.M2, T.G2inv, v, 16, rho2 + ((size_t)p * n + q) * 256);
+    }
+}
+
+void Engine::orbital_invariants(std::vector<double>& inv1, std::vector<double>& inv2) {
+  if (!prev_.valid) throw std::runtime_error("state: no sweep has run");
+  drop_kept();
+  if (n_ < 3 || prev_.bond != 1 || (int)LU_.size() < 2 || !LU_[1])
+    throw std::runtime_error("state: the orbital RDMs are taken at bond 1, the end of a full sweep");
+  const int n = n_;
+  const auto& os = orb_strings();
+  const auto& pinv = orb_pair_invariants();
+  const int NP = (int)pinv.size();
+  RdmAcc acc;
+  acc.orb.assign((size_t)n * 2 + (size_t)n * n * NP, 0.0);
+  auto t1 = [&](int p, int t) { return (size_t)p * 2 + t; };
+  auto t2 = [&](int p, int q, int mu) { return (size_t)n * 2 + ((size_t)p * n + q) * NP + mu; };
+  const Options saved = opt_;
+  rdm_mode_ = true;
+  orb_mode_ = true;
+  opt_.prec_renorm = Precision::FP64;
+  opt_.D = 1 << 30;  // keep the whole support when moving the state
+  try {
+    measurement_walk([&](int i, Block& Lb, Block& Le, Block& Re, const Block& Rp, const PsiLayout& P,
+                         const double* psi) {
+      RdmRequests rq;
+      // <[[x (x) s]^kX (x) y]^0> with x = string xa of site xp in L(i) (xa <
+      // 0: the identity), s = string sa of site i, y = string ya of the last
+      // site (last bond only; < 0: the identity); kX = rank of y
+      auto req = [&](int xp, int xa, int sa, int ya, size_t target) {
+        std::vector<int> sd, sk;
+        if (sa >= 0) sd = os[sa].dag, sk = os[sa].kl;
+        auto skey = std::make_pair(sd, sk);
+        auto si = rq.s_index.find(skey);
+        if (si == rq.s_index.end()) {
+          si = rq.s_index.emplace(skey, (int)rq.s_ops.size()).first;
+          rq.s_ops.push_back(site_string(sd, sk));
+        }
+        std::vector<int> yd, yk;
+        if (ya >= 0) yd = os[ya].dag, yk = os[ya].kl;
+        auto ykey = std::make_tuple((int)yd.size(), -1, yd, yk);
+        auto yi = rq.y_index.find(ykey);
+        if (yi == rq.y_index.end()) {
+          yi = rq.y_index.emplace(ykey, (int)rq.y_ops.size()).first;
+          if (ya < 0) {
+            rq.y_ops.push_back(op_id());
+          } else {
+            SiteOp so2 = site_string(yd, yk);
+            OpKey key{K_T0 + so2.dn, (int)rq.y_temps.size(), 0, so2.k2};
+            rq.y_temps.push_back({key, so2});
+            rq.y_ops.push_back(op_blk(key.kind, key.i, 0, key.k2));
+          }
+        }
+        const int kX = ya >= 0 ? orb_rank(ya) : 0;
+        RdmVKey vk{yi->second, si->second, kX, xa >= 0 ? orb_key(xp, xa) : kIdentityKey, 0};
+        auto vi = rq.v_index.find(vk);
+        if (vi == rq.v_index.end()) {
+          vi = rq.v_index.emplace(vk, (int)rq.vkeys.size()).first;
+          rq.vkeys.push_back(vk);
+        }
+        rq.contribs.push_back({target, 3, 1.0, vi->second});
+      };
+      for (int t = 0; t < 2; ++t) {
+        if (i == 1) req(0, kOrbScalar[t], -1, -1, t1(0, t));  // site 0 lives in L(1)
+        req(-1, -1, kOrbScalar[t], -1, t1(i, t));
+      }
+      for (int p = 0; p < i; ++p)
+        for (int mu = 0; mu < NP; ++mu) req(p, pinv[mu].first, pinv[mu].second, -1, t2(p, i, mu));
+      if (i == n - 2) {
+        for (int t = 0; t < 2; ++t) req(-1, -1, -1, kOrbScalar[t], t1(n - 1, t));
+        for (int p = 0; p < n - 2; ++p)
+          for (int mu = 0; mu < NP; ++mu) req(p, pinv[mu].first, -1, pinv[mu].second, t2(p, n - 1, mu));
+        for (int mu = 0; mu < NP; ++mu) req(-1, -1, pinv[mu].first, pinv[mu].second, t2(n - 2, n - 1, mu));
+      }
+      rdm_eval(Lb, Le, Re, Rp, P, psi, rq, acc);
+    });
+  } catch (...) {
+    rdm_mode_ = orb_mode_ = false;
+    opt_ = saved;
+    throw;
+  }
+  rdm_mode_ = orb_mode_ = false;
+  opt_ = saved;
+  inv1.assign(acc.orb.begin(), acc.orb.begin() + (size_t)n * 2);
+  inv2.assign(acc.orb.begin() + (size_t)n * 2, acc.orb.end());
+}
+
+void Engine::orbital_rdms(double* rho1, double* rho2) {
+  std::vector<double> inv1, inv2;
+  orbital_invariants(inv1, inv2);
+  orbital_rdms_from_invariants(n_, inv1.data(), inv2.data(), rho1, rho2);
+}
+
+void Engine::orbital_entanglement(double* s1, double* mutual) {
+  const int n = n_;
+  std::vector<double> r1((size_t)n * 4), r2((size_t)n * n * 256);
+  orbital_rdms(r1.data(), r2.data());
+  auto ent = [](const double* w, int m) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k)
+      if (w[k] > 1e-14) s -= w[k] * std::log(w[k]);
+    return s;
+  };
+  for (int p = 0; p < n; ++p) s1[p] = ent(&r1[4 * p], 4);  // rho_p is diagonal
+  // eigenvalues of every rho_pq: one batched float64 eigensolver launch
+  const size_t npair = (size_t)n * (n - 1) / 2;
+  std::fill(mutual, mutual + (size_t)n * n, 0.0);
+  if (npair == 0) return;
+  double* dA = (double*)be_->alloc(npair * 256 * sizeof(double));
+  double* dV = (double*)be_->alloc(npair * 256 * sizeof(double));
+  double* dw = (double*)be_->alloc(npair * 16 * sizeof(double));
+  std::vector<double> hA(npair * 256), hw(npair * 16);
+  std::vector<EighTask> tasks;
+  size_t k = 0;
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q, ++k) {
+      std::copy(&r2[((size_t)p * n + q) * 256], &r2[((size_t)p * n + q) * 256] + 256, &hA[k * 256]);
+      tasks.push_back({dA + k * 256, dw + k * 16, dV + k * 256, 16});
+    }
+  be_->copy_h2d(dA, hA.data(), hA.size() * sizeof(double));
+  be_->eigh(tasks);
+  be_->check_device_flag();
+  be_->copy_d2h(hw.data(), dw, hw.size() * sizeof(double));
+  be_->sync();
+  be_->free(dA);
+  be_->free(dV);
+  be_->free(dw);
+  k = 0;
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q, ++k) {
+      const double I = s1[p] + s1[q] - ent(&hw[k * 16], 16);
+      mutual[(size_t)p * n + q] = mutual[(size_t)q * n + p] = I;
+    }
 }
 
 }  // namespace dmrg

@@ -19,6 +19,7 @@
 //   P^k_pq, QJ_pq, QK^k_pq   complementary pair operators, p<=q outside
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -28,6 +29,8 @@
 #include "su2.hpp"
 
 namespace dmrg {
+
+struct PsiLayout;
 
 struct Sector {
   int n, j, dim, off;
@@ -256,6 +259,22 @@ class Engine {
   // (the end of a full sweep):  gamma[p*n+q] = <sum_s a+_ps a_qs>,
   // Gamma[((p*n+q)*n+r)*n+s] = <sum_st a+_ps a+_qt a_rt a_ss>.
   void rdm12(double* gamma, double* Gamma);
+  // One- and two-orbital reduced density matrices of the same state (the
+  // orbital-ordering step of Sec. II "Numerical procedure"), averaged over
+  // the 2S+1 states of the multiplet: rho1[4p + d] = weight of the local
+  // state d of orbital p (0 empty, 1 down, 2 up, 3 doubly occupied);
+  // rho2[(p n + q) 256 + 16 a + b] for p < q the 16 x 16 matrix over the
+  // local states a = 4 d_p + d_q, with Tr(rho_pq X) = <X> for operators X of
+  // the four modes of p and q (Jordan-Wigner order p-up, p-down, q-up,
+  // q-down); entries with p >= q are zero.
+  void orbital_rdms(double* rho1, double* rho2);
+  // The expectation values the orbital RDMs are assembled from: inv1[2p + t]
+  // = <number (t = 0) / double-occupancy (t = 1) string of p>, inv2[(p n + q)
+  // P + mu] (p < q) = <[X_p (x) Y_q]^0> for the P pair invariants.
+  void orbital_invariants(std::vector<double>& inv1, std::vector<double>& inv2);
+  // One-orbital entropies s1[p] = -Tr rho_p ln rho_p and mutual information
+  // mutual[p n + q] = s_p + s_q - s_pq (zero diagonal).
+  void orbital_entanglement(double* s1, double* mutual);
 
   Backend* backend() const { return be_; }
   // Schedule of the last planned tcgen05 H_eff psi product: shape = {tile
@@ -324,7 +343,16 @@ class Engine {
 
   SweepStats stats_;
   bool rdm_mode_ = false;  // blocking builds only C and the normal pairs
+  bool orb_mode_ = false;  // with rdm_mode_: left blocks carry the single-orbital strings of their sites
+  // The measurement pass: walks bonds 1..n-2 over the state of the last
+  // sweep (bond 1), calling at_bond(i, L(i), L(i) (x) site i, site i+1 (x)
+  // R, R, psi layout, psi) and moving the state with its whole support.
+  void measurement_walk(const std::function<void(int, Block&, Block&, Block&, const Block&,
+                                                 const PsiLayout&, const double*)>& at_bond);
   struct RdmAcc;
+  struct RdmRequests;
+  void rdm_eval(Block& Lb, Block& Le, Block& Re, const Block& Rparent, const struct PsiLayout& P,
+                const double* psi, RdmRequests& rq, RdmAcc& acc);
   void rdm_bond(int i, Block& Lb, Block& Le, Block& Re, const Block& Rparent, const struct PsiLayout& P,
                 const double* psi, const std::vector<size_t>& elems, RdmAcc& acc);
   void move_lr(const Prev& from, const SavedU& U, const SavedU& V, const Block& Le, const Block& Re,
@@ -370,6 +398,11 @@ class Engine {
   double sweep_seconds = 0.0;
   double sweep_device_ms = 0.0;  // CUDA-event time of the last sweep
 };
+
+// The orbital RDMs (layout of Engine::orbital_rdms) from the invariants of
+// Engine::orbital_invariants: a host computation over fixed tables.
+void orbital_rdms_from_invariants(int n, const double* inv1, const double* inv2, double* rho1, double* rho2);
+int orbital_pair_invariant_count();
 
 std::string last_error();
 void set_last_error(const std::string& e);
