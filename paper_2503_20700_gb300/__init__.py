@@ -195,6 +195,34 @@ def fiedler_order(mutual, device=0):
     return order
 
 
+def permute_orbitals(order, h, eri=None, chol=None):
+    """Integrals in a new site order: site k holds orbital order[k] (index
+    permutation only).  Returns (h, eri, chol) with None where not given."""
+    o = np.asarray(order)
+    h2 = np.ascontiguousarray(np.asarray(h)[np.ix_(o, o)])
+    e2 = None if eri is None else np.ascontiguousarray(np.asarray(eri)[np.ix_(o, o, o, o)])
+    c2 = None if chol is None else np.ascontiguousarray(np.asarray(chol)[:, o][:, :, o])
+    return h2, e2, c2
+
+
+def order_orbitals(h, eri=None, chol=None, n_elec=None, two_s=0, D_steps=(16, 32, 64), sweeps_per_step=1,
+                   device=0, **opts):
+    """The ordering step before the large runs (Sec. II "Numerical
+    procedure"): sweeps at the low bond dimensions D_steps in the given
+    order, the mutual information of the resulting state, and the orbitals
+    sorted by its Fiedler vector.  Returns (order, s1, mutual); apply the
+    order with permute_orbitals."""
+    g = DMRG(h, eri=eri, chol=chol, n_elec=n_elec, two_s=two_s, D=D_steps[0], device=device, **opts)
+    try:
+        for D in D_steps:
+            g.set_bond_dim(D)
+            g.sweep(sweeps_per_step)
+        s1, mi = g.orbital_entanglement()
+    finally:
+        g.close()
+    return fiedler_order(mi, device=device), s1, mi
+
+
 def set_kernel_wait_timeout(seconds):
     """Bound of the device waits of the kernel-level entry points (process-wide)."""
     lib = load()

@@ -87,3 +87,31 @@ def test_fiedler_order_of_a_shuffled_chain(pkg):
             assert list(order) in (list(perm), list(perm[::-1]))
     with pytest.raises(pkg.DmrgError):
         pkg.fiedler_order(np.array([[0.0, 1.0], [0.5, 0.0]]))
+
+
+def test_ordering_step_recovers_a_shuffled_chain(pkg):
+    """The ordering procedure on a Hubbard chain whose sites were shuffled:
+    the order the device finds from a D=16 state is the oracle's from the
+    same algorithm, and the reordered problem has a much lower energy at the
+    same small D."""
+    n = 8
+    h, eri, _ = W.hubbard_chain(n, t=-1.0, u=4.0)
+    perm = np.random.default_rng(3).permutation(n)
+    hs, es, _ = pkg.permute_orbitals(perm, h, eri)
+    order, s1, mi = pkg.order_orbitals(hs, eri=es, n_elec=n, two_s=0, D_steps=(16,), sweeps_per_step=2,
+                                       tol=1e-10)
+    o = OracleDMRG(hs, es, n, 0, D=16)
+    o.sweep(2)
+    os1, omi = OB.orbital_entanglement(o.states, o.psi_full, n, 0)
+    assert np.abs(mi - omi).max() < 1e-6
+    assert list(order) == list(OB.fiedler_order(omi))
+    chain = perm[order]
+    assert sum(abs(int(a) - int(b)) == 1 for a, b in zip(chain[:-1], chain[1:])) >= n - 2
+    g1 = pkg.DMRG(hs, eri=es, n_elec=n, two_s=0, D=16, tol=1e-10)
+    e_shuffled = g1.sweep(2)[0]
+    g1.close()
+    ho, eo, _ = pkg.permute_orbitals(order, hs, es)
+    g2 = pkg.DMRG(ho, eri=eo, n_elec=n, two_s=0, D=16, tol=1e-10)
+    e_ordered = g2.sweep(2)[0]
+    g2.close()
+    assert e_ordered < e_shuffled - 0.3
