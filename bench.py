@@ -390,9 +390,9 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
         products += len(cands)
         info = g.tc_schedule()
         schedule = {"picked": {"tile_n": info["shape"][0], "chunks_per_cta": info["shape"][1],
-                               "order": info["shape"][2]},
-                    "candidates": [{"tile_n": c[0], "chunks_per_cta": c[1], "order": c[2], "ms": t}
-                                   for c, t in zip(cands, info["ms"])]}
+                               "order": info["shape"][2], "cluster": info["shape"][3]},
+                    "candidates": [{"tile_n": c[0], "chunks_per_cta": c[1], "order": c[2], "cluster": c[3],
+                                    "ms": t} for c, t in zip(cands, info["ms"])]}
     # warm-up products at the middle bond
     g.bond_solve(mid, 1, prec, max_iter=max(1, W - 1), tol=args.tol, min_calls=W, check64=False)
     # ---- timed region: K products inside the Davidson solve of the middle bond

@@ -245,9 +245,10 @@ dmrg_status dmrg_set_kernel_tc_drain_terms(int terms);
  * sector blocks of one product in one persistent launch).  A schedule is
  * {tile width N of the 128 x N sigma tiles, item chunks per CTA, task order
  * (0: longest cluster task first onto the least-loaded cluster; 1: sigma
- * block by sigma block)}.  dmrg_tc_shape_candidates writes the candidates
- * the autotuner times, the default first, as triples into shapes (room for
- * cap triples; *count receives their number).
+ * block by sigma block), CTAs per cluster (2 or 4: column tiles of one row
+ * tile grouped that many at a time share stage 1)}.  dmrg_tc_shape_candidates
+ * writes the candidates the autotuner times, the default first, as groups of
+ * four ints into shapes (room for cap groups; *count receives their number).
  */
 dmrg_status dmrg_tc_shape_candidates(int* shapes, int cap, int* count);
 
@@ -259,7 +260,7 @@ dmrg_status dmrg_set_kernel_tc_shape(int candidate);
  * context; tuned schedules already found stay cached. */
 dmrg_status dmrg_set_tc_autotune(dmrg_ctx* ctx, int on);
 
-/* The schedule of the last planned tcgen05 H_eff psi launch of ctx: shape[3]
+/* The schedule of the last planned tcgen05 H_eff psi launch of ctx: shape[4]
  * as above; ms[k] (k < min(cap, *count)) the CUDA-event time in ms of one
  * product under candidate k for that product's sector histogram (-1: not
  * timed, or autotuning off).  DMRG_ESTATE before the first tcgen05 product. */

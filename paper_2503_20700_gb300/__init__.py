@@ -156,13 +156,13 @@ def set_kernel_tc_drain_terms(terms):
 
 def tc_shape_candidates():
     """Schedules the autotuner of the tcgen05 H_eff psi launch tries, default
-    first: a list of (tile width, item chunks per CTA, task order)."""
+    first: a list of (tile width, item chunks per CTA, task order, CTAs per cluster)."""
     lib = load()
     n = ctypes.c_int()
     _check(lib, None, lib.dmrg_tc_shape_candidates(None, 0, ctypes.byref(n)))
-    buf = np.zeros(3 * n.value, dtype=np.int32)
+    buf = np.zeros(4 * n.value, dtype=np.int32)
     _check(lib, None, lib.dmrg_tc_shape_candidates(_ip(buf), n.value, ctypes.byref(n)))
-    return [tuple(int(x) for x in buf[3 * k:3 * k + 3]) for k in range(n.value)]
+    return [tuple(int(x) for x in buf[4 * k:4 * k + 4]) for k in range(n.value)]
 
 
 def set_kernel_tc_shape(candidate):
@@ -326,8 +326,9 @@ class DMRG:
 
     def tc_schedule(self):
         """Schedule of the last planned tcgen05 product: {"shape": (tile width,
-        chunks per CTA, order), "ms": per-candidate product times (-1: not timed)}."""
-        shape = np.zeros(3, dtype=np.int32)
+        chunks per CTA, order, CTAs per cluster), "ms": per-candidate product
+        times (-1: not timed)}."""
+        shape = np.zeros(4, dtype=np.int32)
         n = ctypes.c_int()
         ms = np.full(16, -1.0)
         _check(self._lib, self._ctx, self._lib.dmrg_tc_schedule_info(self._ctx, _ip(shape), _dp(ms), 16,

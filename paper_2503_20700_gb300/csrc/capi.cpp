@@ -342,9 +342,10 @@ dmrg_status dmrg_tc_shape_candidates(int* shapes, int cap, int* count) {
   if (!count || (cap > 0 && !shapes)) return fail(nullptr, DMRG_EINVAL, "NULL argument");
   *count = (int)c.size();
   for (int k = 0; k < std::min(cap, (int)c.size()); ++k) {
-    shapes[3 * k] = c[k].tile_n;
-    shapes[3 * k + 1] = c[k].chunks_per_cta;
-    shapes[3 * k + 2] = c[k].order;
+    shapes[4 * k] = c[k].tile_n;
+    shapes[4 * k + 1] = c[k].chunks_per_cta;
+    shapes[4 * k + 2] = c[k].order;
+    shapes[4 * k + 3] = c[k].cluster;
   }
   return DMRG_OK;
 }
@@ -717,10 +718,10 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
     void* pool = nullptr;
     size_t scr;
     if (tc) {
-      const int tc_ctas = dmrg::hpsi_tc_max_ctas();
+      const dmrg::TcShape shape = dmrg::tc_shape_candidates()[g_kernel_tc_cand.load()];
+      const int tc_ctas = dmrg::hpsi_tc_max_ctas(shape.cluster);
       dmrg::hpsi_tc_prepare(hb, hi, [&](size_t bytes) { return pool = be->alloc(bytes); }, tp,
-                            tc_ctas > 0 ? tc_ctas : be->sm_count(),
-                            dmrg::tc_shape_candidates()[g_kernel_tc_cand.load()]);
+                            tc_ctas > 0 ? tc_ctas : be->sm_count() / shape.cluster * shape.cluster, shape);
       tasks = tp.tasks;
       reds = tp.reds;
       scr = tp.scratch;
@@ -765,6 +766,7 @@ dmrg_status dmrg_hpsi_contract(const double* A, int64_t a_len, const double* P, 
       L.units = tp.units;
       L.drain_terms = g_kernel_drain_terms.load();
       L.tile_n = tp.shape.tile_n;
+      L.cluster = tp.shape.cluster;
       be->hpsi_tc(L, fl);
     } else {
       be->hpsi((const dmrg::HpsiBlock*)(d + ob), (const dmrg::HpsiItem*)(d + oi),

@@ -1693,7 +1693,8 @@ void Engine::plan_hpsi(Block& Le, Block& Re, HPsiPlan& plan) {
         while (plan.tc_cand < (int)nc && rec.ms[plan.tc_cand] >= 0) ++plan.tc_cand;
       }
     }
-    hpsi_tc_schedule(blocks, tp, tc_shape_candidates()[plan.tc_cand], plan.tc_ncta);
+    hpsi_tc_schedule(blocks, tp, tc_shape_candidates()[plan.tc_cand],
+                     tc_ctas_for(tc_shape_candidates()[plan.tc_cand].cluster));
     if (opt_.debug_bounds) {
       const std::string bad = tc_plan_check(tp, blocks);
       if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
@@ -1817,13 +1818,20 @@ void Engine::tc_upload_schedule(HPsiPlan& plan) {
   plan.tc.units = tp.units;
   plan.tc.drain_terms = opt_.tc_drain_terms;
   plan.tc.tile_n = tp.shape.tile_n;
+  plan.tc.cluster = tp.shape.cluster;
   plan.ntasks = (int)tp.tasks.size();
   plan.nreds = (int)tp.reds.size();
 }
 
+int Engine::tc_ctas_for(int cluster) const {
+  const int m = hpsi_tc_max_ctas(cluster);
+  return m > 0 ? m : std::max(cluster, be_->sm_count() / cluster * cluster);
+}
+
 void Engine::tc_reschedule(HPsiPlan& plan, int candidate) {
   be_->sync();  // the old lists and scratch may still be read by queued work
-  hpsi_tc_schedule(plan.tc_blocks, *plan.tcp, tc_shape_candidates()[candidate], plan.tc_ncta);
+  hpsi_tc_schedule(plan.tc_blocks, *plan.tcp, tc_shape_candidates()[candidate],
+                   tc_ctas_for(tc_shape_candidates()[candidate].cluster));
   if (opt_.debug_bounds) {
     const std::string bad = tc_plan_check(*plan.tcp, plan.tc_blocks);
     if (!bad.empty()) throw std::logic_error("internal: tcgen05 plan: " + bad);
@@ -1833,12 +1841,13 @@ void Engine::tc_reschedule(HPsiPlan& plan, int candidate) {
   tc_upload_schedule(plan);
 }
 
-bool Engine::tc_schedule_info(int shape[3], std::vector<double>* ms) const {
+bool Engine::tc_schedule_info(int shape[4], std::vector<double>* ms) const {
   if (!have_tc_plan_ || last_tc_cand_ < 0) return false;
   const TcShape s = tc_shape_candidates()[last_tc_cand_];
   shape[0] = s.tile_n;
   shape[1] = s.chunks_per_cta;
   shape[2] = s.order;
+  shape[3] = s.cluster;
   if (ms) {
     ms->assign(tc_shape_candidates().size(), -1.0);
     auto it = tune_cache_.find(last_tc_key_);

@@ -278,10 +278,10 @@ class Engine {
 
   Backend* backend() const { return be_; }
   // Schedule of the last planned tcgen05 H_eff psi product: shape = {tile
-  // width, item chunks per CTA, task order}; ms[k] = time of candidate k of
+  // width, item chunks per CTA, task order, CTAs per cluster}; ms[k] = time of candidate k of
   // tc_shape_candidates() for its sector histogram (-1: not timed); returns
   // false when no tcgen05 product was planned yet.
-  bool tc_schedule_info(int shape[3], std::vector<double>* ms) const;
+  bool tc_schedule_info(int shape[4], std::vector<double>* ms) const;
   // device and pinned-host bytes of the stored blocks, the largest one, and
   // the largest working memory of a bond beyond the stored blocks so far
   void memory_detail(size_t* dev, size_t* host, size_t* max_block, size_t* max_extra,
@@ -368,6 +368,7 @@ class Engine {
   // plan's current shape; rescheduling for another shape keeps the operands
   void tc_upload_schedule(struct HPsiPlan& plan);
   void tc_reschedule(struct HPsiPlan& plan, int candidate);
+  int tc_ctas_for(int cluster) const;  // CTAs of a persistent launch in clusters of that size
   std::map<uint64_t, TuneRec> tune_cache_;
   uint64_t last_tc_key_ = 0;
   int last_tc_cand_ = -1;

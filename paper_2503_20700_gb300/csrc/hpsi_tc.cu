@@ -1,6 +1,6 @@
 // tcgen05 fused H_eff psi contraction (see hpsi_tc.cuh), persistent and
 // warp-specialised, with operand tiles brought in by TMA, in clusters of
-// kTcCluster CTAs.
+// two or four CTAs (a launch parameter of the schedule).
 //
 // Per item of a task (a 128 x N, N <= 256, sigma tile) and per super-chunk
 // of up to 256 columns of psi (columns [c, c+256) of P):
@@ -13,9 +13,10 @@
 //
 // The CTAs of a cluster walk the same items; CTAs whose tiles have the same
 // rows (a group) need the same X, so stage 1 of the super-chunks is dealt
-// round-robin over the group, and the CTA that computes a super-chunk writes
-// its pieces into the X buffers of every CTA of the group (distributed shared
-// memory) and arrives on their piece barriers.  Each CTA's MMA issuer
+// round-robin over the group (up to the cluster size), and the CTA that
+// computes a super-chunk writes its pieces into its own X buffer and, by one
+// bulk copy each, into those of the other CTAs of the group (distributed
+// shared memory), completing their piece barriers.  Each CTA's MMA issuer
 // signals the end of its reads of a piece buffer to every CTA of the cluster
 // (multicast commit), so a buffer is rewritten once the whole cluster has read
 // it.  A ghost entry (a cluster slot without a tile) only keeps that count.
@@ -76,10 +77,7 @@ constexpr int A_BYTES = 16384, P_BYTES = 32768, B_BYTES = 32768;
 constexpr uint32_t TCOL_S = 0, TCOL_X = 256;
 constexpr int NTHREADS = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr int C = kTcCluster;
-static_assert(C == 2, "the X piece exchange is written for groups of at most two CTAs");
 constexpr unsigned long long kDrainCopiesNs = 100000ull;  // in-flight peer copies land within this
-constexpr uint16_t kClusterMask = (uint16_t)((1u << C) - 1);
 
 // barriers
 enum { B_FULL = 0, B_EMPTY = B_FULL + NSTAGE, B_XPF = B_EMPTY + NSTAGE, B_XPE, B_XF, B_XE = B_XF + 2,
@@ -116,11 +114,11 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
 }
 // one arrival on the barrier at the same offset in every CTA of the cluster,
 // once the MMAs issued so far by this thread have completed
-__device__ __forceinline__ void commit_all(uint64_t* bar) {
+__device__ __forceinline__ void commit_all(uint64_t* bar, uint16_t mask) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
           smem_u32(bar)),
-      "h"(kClusterMask)
+      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void arrive(uint64_t* bar) {
@@ -403,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    const HpsiBlock* __restrict__ blocks, const TcItem* __restrict__ items,
                    const HpsiTask* __restrict__ tasks, const int* __restrict__ cta_off,
                    const TcSlot* __restrict__ cta_task, double* __restrict__ scratch, int* __restrict__ err,
-                   unsigned long long wait_ns, int drain_terms, int tile_n) {
+                   unsigned long long wait_ns, int drain_terms, int tile_n, int csize) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[B_COUNT];
   __shared__ uint32_t tmem_base;
@@ -414,12 +412,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t sbase = (sraw + 1023u) & ~1023u;  // the same offset in every CTA of the cluster
   unsigned char* const sgen = smraw + (sbase - sraw);
   const int rank = (int)cluster_rank();
+  const uint16_t cmask = (uint16_t)((1u << csize) - 1);  // every CTA of the cluster
   const int t0 = cta_off[blockIdx.x], t1 = cta_off[blockIdx.x + 1];
   volatile int* abort = &abort_flag;
   // an aborting role stops the roles of every CTA of the cluster
   auto abort_all = [&]() {
     *abort = 1;
-    for (int j = 0; j < C; ++j)
+    for (int j = 0; j < csize; ++j)
       if (j != rank)
         asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(map_to(smem_u32(&abort_flag), j)),
                      "r"(1)
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // for a piece from the peer, this CTA's converters expecting its bytes);
       // XE: the MMA issuers of all CTAs of the cluster
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[B_XF + i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar[B_XE + i])), "r"(C));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar[B_XE + i])), "r"(csize));
       // XA: this CTA's converter threads, once they have seen the reads of
       // two pieces back complete
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar[B_XA + i])));
@@ -606,7 +605,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ++q;
         }
         // buffer b of every CTA may be rewritten once all of them have read it
-        commit_all(&bar[B_XE + b]);
+        commit_all(&bar[B_XE + b], cmask);
         ++g;
         if (drain_point(w)) {
           commit(&bar[B_SF]);
@@ -623,7 +622,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       auto ghost_piece = [&]() -> bool {
         const int b = g & 1;
         if (!wait_bar(&bar[B_XA + b], (uint32_t)((g >> 1) & 1), abort, wait_ns)) return false;
-        commit_all(&bar[B_XE + b]);
+        commit_all(&bar[B_XE + b], cmask);
         ++g;
         return true;
       };
@@ -704,11 +703,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (tid == 64) {
-        if (w.sl.grpn > 1) {
-          const uint32_t peer = (uint32_t)(2 * w.sl.grp0 + 1 - rank);
-          const uint32_t xb = sbase + OFF_X + b * XBUF;
-          copy_to_peer(map_to(xb, peer), xb, XBUF, map_to(smem_u32(&bar[B_XF + b]), peer));
-        }
+        // one copy into every other CTA of the group
+        const uint32_t xb = sbase + OFF_X + b * XBUF;
+        for (int peer = w.sl.grp0; peer < w.sl.grp0 + w.sl.grpn; ++peer)
+          if (peer != rank)
+            copy_to_peer(map_to(xb, (uint32_t)peer), xb, XBUF, map_to(smem_u32(&bar[B_XF + b]), (uint32_t)peer));
         arrive(&bar[B_XF + b]);
       }
       return true;
@@ -793,7 +792,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (owned(w)) {
         if (!(ok = convert(w))) break;
       } else if (!ghost(w) && w.sl.grpn > 1 && tid == 64) {
-        // the piece comes from the group's other CTA: its bytes complete the phase
+        // the piece comes from the CTA of the group that owns it: its bytes complete the phase
         arrive_expect(&bar[B_XF + b], XBUF);
       }
       if (pend && !(ok = drain(pend_part, pend_N, pend_first))) break;
@@ -926,14 +925,14 @@ void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st) {
 }
 
 namespace {
-// launch of whole clusters of C CTAs along x
-void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int ncta, cudaStream_t st) {
+// launch of whole clusters of `cluster` CTAs along x
+void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int ncta, cudaStream_t st, int cluster) {
   cfg.gridDim = dim3((unsigned)ncta, 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -941,26 +940,27 @@ void launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int ncta,
 }
 }  // namespace
 
-int hpsi_tc_max_ctas() {
+int hpsi_tc_max_ctas(int cluster) {
   static std::mutex mu;
-  static int cached[64];
-  static bool have[64];
+  static int cached[64][kTcClusterMax + 1];
+  static bool have[64][kTcClusterMax + 1];
   int dev = 0;
+  if (cluster < 1 || cluster > kTcClusterMax) return 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lk(mu);
-  if (!have[dev]) {
+  if (!have[dev][cluster]) {
     int n = 0;
     if (ensure_smem_attr((const void*)hpsi_tc_kernel, SMEM_BYTES) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
-      launch_config(cfg, attr, C, nullptr);
+      launch_config(cfg, attr, cluster, nullptr, cluster);
       if (cudaOccupancyMaxActiveClusters(&n, (const void*)hpsi_tc_kernel, &cfg) != cudaSuccess) n = 0;
     }
     cudaGetLastError();
-    cached[dev] = n * C;
-    have[dev] = true;
+    cached[dev][cluster] = n * cluster;
+    have[dev][cluster] = true;
   }
-  return cached[dev];
+  return cached[dev][cluster];
 }
 
 void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st) {
@@ -976,12 +976,13 @@ void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cud
     CUtensorMap m32, m64;
     make_map(&m32, L.pool, L.units, 32);
     make_map(&m64, L.pool, L.units, 64);
-    if (L.ncta % C) throw std::runtime_error("internal: tcgen05 launch not in whole clusters");
+    if (L.cluster < 1 || L.cluster > kTcClusterMax || L.ncta % L.cluster)
+      throw std::runtime_error("internal: tcgen05 launch not in whole clusters");
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    launch_config(cfg, attr, L.ncta, st);
+    launch_config(cfg, attr, L.ncta, st, L.cluster);
     cudaError_t e = cudaLaunchKernelEx(&cfg, hpsi_tc_kernel, m32, m64, L.blocks, L.items, L.tasks, L.cta_off,
-                                       L.cta_task, L.scratch, err, wait_ns, L.drain_terms, L.tile_n);
+                                       L.cta_task, L.scratch, err, wait_ns, L.drain_terms, L.tile_n, L.cluster);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda: hpsi tc launch: ") + cudaGetErrorString(e));
   }

@@ -20,7 +20,7 @@
 // a plane reads other planes' finite values, which only reach unstored output
 // rows and columns or meet zero padding.
 //
-// The persistent kernel runs in clusters of kTcCluster CTAs.  A task is a
+// The persistent kernel runs in clusters of 2 or 4 CTAs.  A task is a
 // 128 x N (N <= 256) tile of a sigma block and a chunk of its items; the CTAs
 // of a cluster take tasks of the same block and chunk together (lockstep over
 // the same items), and CTAs whose tiles share their rows form a group that
@@ -70,7 +70,8 @@ struct SplitJob {
 };
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
-constexpr int kTcCluster = 2;  // CTAs per cluster of the persistent launch
+constexpr int kTcCluster = 2;     // CTAs per cluster of the persistent launch (default schedule)
+constexpr int kTcClusterMax = 4;  // largest cluster a schedule may use
 constexpr int kTcUnitFloats = 256;  // one 1 KB unit
 constexpr int kTcDrainTerms = 1024;  // default FP32 accumulation length (terms) between drains
 
@@ -91,13 +92,17 @@ struct TcSlot {
 // which cluster tasks are placed on the clusters (0: longest first onto the
 // least-loaded cluster; 1: sigma block by sigma block, the cluster tasks of
 // one block and item chunk dealt round-robin, so that the CTAs running at
-// the same time share their operands in L2).
+// the same time share their operands in L2), and the CTAs per cluster (the
+// column tiles of one row tile are grouped that many at a time and share
+// stage 1).
 struct TcShape {
   int tile_n = kTcTileN;
   int chunks_per_cta = 4;
   int order = 0;
+  int cluster = kTcCluster;
   bool operator==(const TcShape& o) const {
-    return tile_n == o.tile_n && chunks_per_cta == o.chunks_per_cta && order == o.order;
+    return tile_n == o.tile_n && chunks_per_cta == o.chunks_per_cta && order == o.order &&
+           cluster == o.cluster;
   }
 };
 // The shapes an autotuner tries, the default first.
@@ -145,7 +150,7 @@ struct TcLaunch {
   const HpsiTask* tasks = nullptr;
   const int* cta_off = nullptr;
   const TcSlot* cta_task = nullptr;
-  int ncta = 0;  // a multiple of kTcCluster
+  int ncta = 0;  // a multiple of cluster
   const HpsiReduce* reds = nullptr;
   int nreds = 0;
   double* scratch = nullptr;
@@ -156,6 +161,7 @@ struct TcLaunch {
   // column index (sum of kb), after the item (0: after every item)
   int drain_terms = kTcDrainTerms;
   int tile_n = kTcTileN;  // column width of the tiles the plan was scheduled for
+  int cluster = kTcCluster;  // CTAs per cluster the plan was scheduled for
 };
 
 // Runs the split jobs (device list of n jobs) into the pool.
@@ -168,8 +174,8 @@ void split_launch(const SplitJob* jobs, int n, float* pool, cudaStream_t st);
 void hpsi_tc_launch(const TcLaunch& L, int* err, unsigned long long wait_ns, cudaStream_t st);
 
 // CTAs of the persistent launch that the device runs at once (whole clusters
-// of kTcCluster CTAs, one CTA per SM); 0 without a device.
-int hpsi_tc_max_ctas();
+// of `cluster` CTAs, one CTA per SM); 0 without a device.
+int hpsi_tc_max_ctas(int cluster = kTcCluster);
 
 // Host-side check of a plan against its own ranges (debug_bounds): every
 // TMA box of every item inside the pool's units or its zero-filled tail,

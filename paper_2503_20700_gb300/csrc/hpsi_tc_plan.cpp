@@ -44,6 +44,7 @@ std::vector<TcShape> tc_shape_candidates() {
   c.push_back(TcShape{kTcTileN, 2, 0});  // coarser item chunks
   c.push_back(TcShape{kTcTileN, 4, 1});  // block order
   c.push_back(TcShape{128, 4, 0});       // narrow tiles
+  c.push_back(TcShape{kTcTileN, 4, 0, 4});  // clusters of four: stage 1 shared by up to four tiles
   return c;
 }
 
@@ -198,7 +199,8 @@ void hpsi_tc_operands(const std::vector<HpsiBlock>& blocks, const std::vector<Hp
 void hpsi_tc_schedule(const std::vector<HpsiBlock>& blocks, TcPlan& plan, const TcShape& shape, int ncta) {
   if (ncta <= 0) ncta = 152;
   const int TN = shape.tile_n;
-  if (TN < 16 || TN > TNMAX || TN % 16 || shape.chunks_per_cta < 1 || shape.order < 0 || shape.order > 1)
+  if (TN < 16 || TN > TNMAX || TN % 16 || shape.chunks_per_cta < 1 || shape.order < 0 || shape.order > 1 ||
+      shape.cluster < 1 || shape.cluster > kTcClusterMax)
     throw std::invalid_argument("tcgen05 plan: invalid schedule shape");
   plan.shape = shape;
   plan.tasks.clear();
@@ -226,12 +228,12 @@ void hpsi_tc_schedule(const std::vector<HpsiBlock>& blocks, TcPlan& plan, const 
     }
   }
   const double target = std::max(1.0, total / ((double)shape.chunks_per_cta * ncta));
-  // Cluster tasks: kTcCluster tasks of the same block and item chunk.  The
-  // column tiles of one row tile are grouped kTcCluster at a time (a group
+  // Cluster tasks: C tasks of the same block and item chunk.  The
+  // column tiles of one row tile are grouped C at a time (a group
   // shares stage 1); the remainder groups of the rows are packed first-fit
   // (largest first) into further cluster tasks, and slots left empty become
   // ghosts.
-  constexpr int C = kTcCluster;
+  const int C = shape.cluster;
   struct Member {
     int task, grp0, grpn;
   };
@@ -402,7 +404,8 @@ std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& bloc
         (size_t)(rd.part0 + rd.nparts * tile) > plan.scratch)
       return "reduction out of range";
   }
-  const int C = kTcCluster;
+  const int C = plan.shape.cluster;
+  if (C < 1 || C > kTcClusterMax) return "cluster size out of range";
   if (plan.cta_off.empty() || plan.cta_off.front() != 0 || plan.cta_off.back() != (int)plan.cta_task.size())
     return "CTA lists do not cover their entries";
   const int ncta = (int)plan.cta_off.size() - 1;
@@ -416,7 +419,7 @@ std::string tc_plan_check(const TcPlan& plan, const std::vector<HpsiBlock>& bloc
       if (plan.cta_off[base + j + 1] - plan.cta_off[base + j] != len)
         return "cluster " + std::to_string(k) + ": lists of unequal length";
     for (int q = 0; q < len; ++q) {
-      const TcSlot* sl[kTcCluster];
+      const TcSlot* sl[kTcClusterMax];
       for (int j = 0; j < C; ++j) {
         sl[j] = &plan.cta_task[plan.cta_off[base + j] + q];
         if (sl[j]->task < 0 || sl[j]->task >= (int)plan.tasks.size()) return "CTA entry out of range";

@@ -205,7 +205,7 @@ static void check_plan(unsigned seed, const TcShape& shape) {
   // of each naming the same block and items; every task in exactly one list
   // (ghost entries aside); groups are contiguous ranks with the same rows and
   // distinct columns; the plan's own check agrees
-  const int C = kTcCluster;
+  const int C = shape.cluster;
   const int G = (int)plan.cta_off.size() - 1;
   CHECK(G % C == 0);
   CHECK(plan.tasks.empty() ? G == 0 : (G >= C && G <= std::max(C, ncta / C * C)));

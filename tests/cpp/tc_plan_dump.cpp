@@ -61,7 +61,7 @@ int main(int argc, char** argv) {
   hpsi_tc_prepare(blocks, items, [](size_t) { return (void*)(uintptr_t(1) << 44); }, plan, ncta, cands[cand]);
   const std::string bad = tc_plan_check(plan, blocks);
   std::printf("check %s\n", bad.empty() ? "ok" : bad.c_str());
-  std::printf("cluster %d\n", kTcCluster);
+  std::printf("cluster %d\n", plan.shape.cluster);
   std::printf("tile_n %d\n", plan.shape.tile_n);
   std::printf("blocks %zu\n", blocks.size());
   for (const HpsiBlock& b : blocks) std::printf("%d %d\n", b.m, b.n);

@@ -68,14 +68,16 @@ def test_default_opts(lib):
 
 def test_schedule_candidates_listed_without_a_device(lib):
     """The autotuner's candidate schedules of the tcgen05 launch are host data:
-    the default (256-wide tiles, four item chunks per CTA, longest first)
-    comes first, every tile width is a multiple of 16 up to 256, and the
-    kernel-level shape setter rejects an index outside the list."""
+    the default (256-wide tiles, four item chunks per CTA, longest first,
+    clusters of two) comes first, every tile width is a multiple of 16 up to
+    256, clusters have two or four CTAs, and the kernel-level shape setter
+    rejects an index outside the list."""
     import paper_2503_20700_gb300 as p
     c = p.tc_shape_candidates()
-    assert c[0] == (256, 4, 0) and len(set(c)) == len(c) >= 2
-    for tn, ch, order in c:
-        assert tn % 16 == 0 and 16 <= tn <= 256 and ch >= 1 and order in (0, 1)
+    assert c[0] == (256, 4, 0, 2) and len(set(c)) == len(c) >= 2
+    assert any(cl == 4 for *_, cl in c)
+    for tn, ch, order, cl in c:
+        assert tn % 16 == 0 and 16 <= tn <= 256 and ch >= 1 and order in (0, 1) and cl in (2, 4)
     for bad in (-1, len(c)):
         with pytest.raises(p.DmrgError) as ei:
             p.set_kernel_tc_shape(bad)

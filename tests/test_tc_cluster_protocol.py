@@ -82,16 +82,21 @@ def test_cluster_protocol_has_no_deadlock_or_hazard(dumper, tmp_path, seed, nb, 
         assert shared > 0  # the plans exercise groups that share stage 1
 
 
-@pytest.mark.parametrize("cand", [1, 2, 3, 4])
+@pytest.mark.parametrize("cand", [1, 2, 3, 4, 5])
 def test_cluster_protocol_under_every_schedule_candidate(dumper, tmp_path, cand):
     """The autotuner's other schedules (finer and coarser item chunks, block
-    order, 128-wide tiles) keep the protocol free of deadlocks and hazards."""
-    for seed, nb, dim, items in CASES[:3]:
+    order, 128-wide tiles, clusters of four CTAs sharing stage 1 by groups of
+    up to four tiles) keep the protocol free of deadlocks and hazards."""
+    widest = 0
+    for seed, nb, dim, items in CASES[:4]:
         plan = plan_of(dumper, tmp_path, problem(seed, nb, dim, items), 24, cand)
         C = plan["cluster"]
+        widest = max([widest] + [e[2] for lst in plan["lists"] for e in lst])
         for k in range(len(plan["lists"]) // C):
             status, info = M.run_cluster(plan, k, seed=seed, drain_terms=1024)
             assert status == "ok", (cand, seed, k, status, info)
+    if C == 4:
+        assert widest == 4  # groups of four tiles share stage 1
 
 
 def test_model_finds_the_unacknowledged_protocol_faulty(dumper, tmp_path):
