@@ -370,6 +370,13 @@ dmrg_status dmrg_bond_energies(const dmrg_ctx* ctx, double* out, int cap, int* c
 /* Multiplet counts of the left blocks L(m), m = 0..n (-1 where not held). */
 dmrg_status dmrg_block_dims(const dmrg_ctx* ctx, int* left, int* right);
 
+/* The same blocks counted in U(1) states: every multiplet of spin S counts
+ * 2S+1.  This is the U(1) bond dimension D~ that the paper reports beside D
+ * (Sec. II.C; the D~ columns of Tables exetime and exetime-fe2s2), the
+ * dimension a calculation without spin adaptation needs for the same
+ * basis.  -1 where no block is held. */
+dmrg_status dmrg_block_dims_u1(const dmrg_ctx* ctx, int* left, int* right);
+
 /* Turn per-launch CUDA-event timing of the GEMM kernels on (1) or off (0);
  * turning it on resets the counters. */
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int on);

@@ -110,6 +110,8 @@ def load(path=None):
     lib.dmrg_orbital_rdms_from_invariants.restype = I
     lib.dmrg_fiedler_order.argtypes = [dp, I, ip, I]
     lib.dmrg_fiedler_order.restype = I
+    lib.dmrg_block_dims_u1.argtypes = [P, ip, ip]
+    lib.dmrg_block_dims_u1.restype = I
     lib.dmrg_energy.argtypes = [P, dp]
     lib.dmrg_energy.restype = I
     lib.dmrg_rdm12.argtypes = [P, dp, dp]
@@ -395,6 +397,13 @@ class DMRG:
         left = np.zeros(self.n + 1, dtype=np.int32)
         right = np.zeros(self.n + 1, dtype=np.int32)
         _check(self._lib, self._ctx, self._lib.dmrg_block_dims(self._ctx, _ip(left), _ip(right)))
+        return left, right
+
+    def block_dims_u1(self):
+        """Block dimensions in U(1) states (D~: each multiplet counts 2S+1)."""
+        left = np.zeros(self.n + 1, dtype=np.int32)
+        right = np.zeros(self.n + 1, dtype=np.int32)
+        _check(self._lib, self._ctx, self._lib.dmrg_block_dims_u1(self._ctx, _ip(left), _ip(right)))
         return left, right
 
     def profile(self, on=True):

@@ -490,6 +490,15 @@ dmrg_status dmrg_block_dims(const dmrg_ctx* c, int* left, int* right) {
   return DMRG_OK;
 }
 
+dmrg_status dmrg_block_dims_u1(const dmrg_ctx* c, int* left, int* right) {
+  if (!c || !c->eng) return fail(const_cast<dmrg_ctx*>(c), DMRG_EINVAL, "invalid context");
+  for (int m = 0; m <= c->n; ++m) {
+    if (left) left[m] = c->eng->left_dim_u1(m);
+    if (right) right[m] = c->eng->right_dim_u1(m);
+  }
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_profile(dmrg_ctx* c, int on) {
   if (!c || !c->be) return fail(c, DMRG_EINVAL, "invalid context");
   try {

@@ -494,6 +494,18 @@ int Engine::right_dim(int m) const {
   for (auto& s : R_[m]->ops->basis.sec) t += s.dim;
   return t;
 }
+int Engine::left_dim_u1(int m) const {
+  if (m < 0 || m >= (int)L_.size() || !L_[m]) return -1;
+  int t = 0;
+  for (auto& s : L_[m]->ops->basis.sec) t += s.dim * (s.j + 1);
+  return t;
+}
+int Engine::right_dim_u1(int m) const {
+  if (m < 0 || m >= (int)R_.size() || !R_[m]) return -1;
+  int t = 0;
+  for (auto& s : R_[m]->ops->basis.sec) t += s.dim * (s.j + 1);
+  return t;
+}
 
 std::unique_ptr<Block> Engine::vacuum(bool left) {
   auto b = std::make_unique<Block>();

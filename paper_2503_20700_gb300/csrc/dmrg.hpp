@@ -252,6 +252,10 @@ class Engine {
   // Multiplet count of the left block L(m) / right block R(m) (sites counted)
   int left_dim(int m) const;
   int right_dim(int m) const;
+  // the same in U(1) states (each multiplet of spin S counts 2S+1): the
+  // bond dimension D~ a non-spin-adapted calculation needs for this basis
+  int left_dim_u1(int m) const;
+  int right_dim_u1(int m) const;
   // Two-site wavefunction at the last optimised bond (for RDMs / checks)
   int last_bond() const { return last_bond_; }
   // Spin-free one- and two-particle RDMs (Eqs. onerdm, twordm) of the

@@ -83,6 +83,7 @@ def test_dynamic_bond_dimension_matches_oracle(pkg, target, dmin):
         e, tr = g.sweep()
         eg.append(e)
     left, right = g.block_dims()
+    left_u1, right_u1 = g.block_dims_u1()
     g.close()
     assert np.abs(np.array(eg) - np.array(eo)).max() < 1e-8
     # right blocks R(m) (the last m sites) of the last R->L half-sweep; the
@@ -92,6 +93,10 @@ def test_dynamic_bond_dimension_matches_oracle(pkg, target, dmin):
     for m in range(1, 8):
         if right[m] >= 0 and orr[8 - m] is not None:
             assert right[m] == orr[8 - m], (m, right[m], orr[8 - m])
+            # D~ (U(1) states, Sec. II.C): the oracle's explicit basis has one
+            # vector per state of every multiplet
+            assert right_u1[m] == o.right[8 - m].m, (m, right_u1[m], o.right[8 - m].m)
+            assert right_u1[m] >= right[m]
             compared += 1
     assert compared >= 5
 
