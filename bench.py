@@ -373,10 +373,20 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     flops_job += g.stats()["hpsi_flops"]
     products += g.stats()["hpsi_calls"]
     app_ms = g.sweep_device_ms()
+    # wall seconds per phase of the D=2048 bonds of the approach (the parts of
+    # a sweep besides the H_eff psi products: blocking, planning, decimation,
+    # renormalisation), summed over both parts
+    app_phases = dict(g.phases())
+    app_bonds = n - 2
+    app_products = g.stats()["hpsi_calls"]
     g.sweep_part(1, mid + 1)
     flops_job += g.stats()["hpsi_flops"]
     products += g.stats()["hpsi_calls"]
     app_ms += g.sweep_device_ms()
+    for k, v in g.phases().items():
+        app_phases[k] = app_phases.get(k, 0.0) + v
+    app_bonds += (n - 2) - (mid + 1) + 1
+    app_products += g.stats()["hpsi_calls"]
     t_app = time.perf_counter() - t_app0
     left, right = g.block_dims()
     # schedule autotuning at the middle bond (split tcgen05 path): each
@@ -484,6 +494,10 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
                                     "delta_e_bound": (res["residual64"] ** 2 / res["gap"]) if res["gap"] > 0 else None},
                 "fp64": fp64, "ramp_energies": ramp_energies, "ramp_seconds": t_ramp,
                 "approach_seconds": t_app, "approach_device_ms": app_ms,
+                "approach_phases": {"bonds": app_bonds, "products": app_products,
+                                    "seconds": {k: app_phases[k] for k in
+                                                ("enlarge", "plan", "davidson", "decimate", "renormalize",
+                                                 "guess")}},
                 "block_dims_left": left.tolist(), "block_dims_right": right.tolist(),
                 "wall_seconds": wall, "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
                 "kernel_ms": kernel_ms, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,

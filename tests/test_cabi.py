@@ -82,3 +82,18 @@ def test_schedule_candidates_listed_without_a_device(lib):
         with pytest.raises(p.DmrgError) as ei:
             p.set_kernel_tc_shape(bad)
         assert ei.value.status == p.DMRG_EINVAL
+
+
+def test_fiedler_order_validates_on_the_host(lib):
+    """Input checks of dmrg_fiedler_order return before any device work:
+    a non-symmetric or non-finite mutual information is rejected, and fewer
+    than three orbitals keep their order."""
+    import paper_2503_20700_gb300 as p
+    with pytest.raises(p.DmrgError) as ei:
+        p.fiedler_order(np.array([[0.0, 1.0, 0.2], [0.5, 0.0, 0.1], [0.2, 0.1, 0.0]]))
+    assert ei.value.status == p.DMRG_EINVAL
+    bad = np.zeros((3, 3))
+    bad[0, 1] = bad[1, 0] = np.nan
+    with pytest.raises(p.DmrgError):
+        p.fiedler_order(bad)
+    assert list(p.fiedler_order(np.array([[0.0, 0.3], [0.3, 0.0]]))) == [0, 1]
