@@ -559,6 +559,12 @@ dmrg_status dmrg_eigh_batched(const double* mats, const int* n, int count, doubl
  * Host arrays in and out, float64 row-major; all arithmetic on the device.
  * ---------------------------------------------------------------------- */
 
+/* Device time (ms, CUDA events on the call's stream) and algorithmic FLOPs
+ * (2mnk per product) of the grouped float64 GEMM launches of the calling
+ * thread's last casscf_* call: for casscf_transform these are all of its
+ * arithmetic (the host copies are not included). */
+dmrg_status casscf_last_kernel_ms(double* ms, double* flops);
+
 /* R = expm(-K) for the real antisymmetric K with K[p,q] = kappa_pq (p > q):
  * U = exp(-kappa^) of Sec. II.A rotates the integrals as h' = R^T h R. */
 dmrg_status casscf_rotation(const double* K, int nb, double* R, int device);

@@ -945,16 +945,21 @@ dmrg_status dmrg_fiedler_order(const double* mutual, int n, int* order, int devi
 
 // ---------------------------------------------------------------- CAS-SCF
 namespace {
+thread_local double tl_casscf_ms = 0.0, tl_casscf_flops = 0.0;
+
 template <class F>
 dmrg_status with_casscf(int device, F&& f) {
   std::string err;
   std::unique_ptr<dmrg::Backend> be(dmrg::make_cuda_backend(device, &err));
   if (be) be->set_wait_ns(g_kernel_wait_ns.load());
   if (!be) return fail(nullptr, DMRG_ECUDA, err);
+  tl_casscf_ms = tl_casscf_flops = 0.0;
   try {
+    be->set_profile(true);
     dmrg::Casscf c(be.get());
     f(c);
     be->sync();
+    be->kernel_stats(0, &tl_casscf_ms, &tl_casscf_flops, nullptr);
   } catch (const std::exception& e) {
     return translate(nullptr, e);
   }
@@ -963,6 +968,13 @@ dmrg_status with_casscf(int device, F&& f) {
 }  // namespace
 
 extern "C" {
+
+dmrg_status casscf_last_kernel_ms(double* ms, double* flops) {
+  if (!ms) return fail(nullptr, DMRG_EINVAL, "invalid argument");
+  *ms = tl_casscf_ms;
+  if (flops) *flops = tl_casscf_flops;
+  return DMRG_OK;
+}
 
 dmrg_status casscf_rotation(const double* K, int nb, double* R, int device) {
   if (!K || !R || nb < 1 || nb > 8192) return fail(nullptr, DMRG_EINVAL, "invalid argument");

@@ -180,6 +180,8 @@ def _bind_casscf(lib):
     lib.casscf_dmrg_scf.argtypes = [dp, dp, I, I, I, I, I, I, ctypes.POINTER(Opts), ctypes.POINTER(ScfOpts),
                                     dp, dp, dp, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.casscf_dmrg_scf.restype = I
+    lib.casscf_last_kernel_ms.argtypes = [dp, dp]
+    lib.casscf_last_kernel_ms.restype = I
     for f in ("casscf_rotation", "casscf_rotation_backward", "casscf_transform",
               "casscf_active_space", "casscf_orbital_gradient", "casscf_transform_backward"):
         getattr(lib, f).restype = I
@@ -195,6 +197,13 @@ def _call(name, *args):
     st = getattr(lib, name)(*args)
     if st != 0:
         raise DmrgError(st, lib.dmrg_last_error(None).decode())
+
+
+def casscf_last_kernel_ms():
+    """(device ms, algorithmic FLOPs) of the GEMM launches of the last CAS-SCF call."""
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    _call("casscf_last_kernel_ms", ctypes.byref(ms), ctypes.byref(fl))
+    return ms.value, fl.value
 
 
 def rotation(K, device=0):
