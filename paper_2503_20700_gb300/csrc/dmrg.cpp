@@ -4014,9 +4014,20 @@ void Engine::orbital_entanglement(double* s1, double* mutual) {
   const size_t npair = (size_t)n * (n - 1) / 2;
   std::fill(mutual, mutual + (size_t)n * n, 0.0);
   if (npair == 0) return;
-  double* dA = (double*)be_->alloc(npair * 256 * sizeof(double));
-  double* dV = (double*)be_->alloc(npair * 256 * sizeof(double));
-  double* dw = (double*)be_->alloc(npair * 16 * sizeof(double));
+  struct DevBufs {
+    Backend* be;
+    std::vector<void*> p;
+    ~DevBufs() {
+      for (void* q : p) be->free(q);
+    }
+    double* get(size_t n) {
+      p.push_back(be->alloc(n * sizeof(double)));
+      return (double*)p.back();
+    }
+  } bufs{be_, {}};
+  double* dA = bufs.get(npair * 256);
+  double* dV = bufs.get(npair * 256);
+  double* dw = bufs.get(npair * 16);
   std::vector<double> hA(npair * 256), hw(npair * 16);
   std::vector<EighTask> tasks;
   size_t k = 0;
@@ -4030,9 +4041,6 @@ void Engine::orbital_entanglement(double* s1, double* mutual) {
   be_->check_device_flag();
   be_->copy_d2h(hw.data(), dw, hw.size() * sizeof(double));
   be_->sync();
-  be_->free(dA);
-  be_->free(dV);
-  be_->free(dw);
   k = 0;
   for (int p = 0; p < n; ++p)
     for (int q = p + 1; q < n; ++q, ++k) {
