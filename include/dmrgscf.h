@@ -209,6 +209,18 @@ dmrg_status dmrg_bond_solve(dmrg_ctx* ctx, int bond, int direction, int precisio
                             double* call_ms, int cap);
 
 /*
+ * dmrg_bond_apply -- y = H_eff x (Sec. II.B, the two-site effective
+ * Hamiltonian without e_core) on the blocks of the last dmrg_bond_solve, in
+ * the given precision (as for dmrg_bond_solve; the schedule is the default
+ * one).  x and y: host vectors of *len doubles in the two-site layout of that
+ * bond (the layout of its Davidson vector).  With x or y NULL only *len is
+ * set to the dimension; a *len that differs from it returns DMRG_EINVAL with
+ * *len set.  DMRG_ESTATE without a bond solve since the last sweep.  For
+ * inspection: Hermiticity, linearity, products on chosen vectors.
+ */
+dmrg_status dmrg_bond_apply(dmrg_ctx* ctx, int precision, const double* x, double* y, int64_t* len);
+
+/*
  * dmrg_bond_check64 -- the float64 Rayleigh quotient (+ e_core) and
  * residual ||H_eff psi - E psi|| (||psi|| = 1) of the vector of the last
  * dmrg_bond_solve, from one float64 H_eff psi on the same blocks; *ms its

@@ -112,6 +112,8 @@ def load(path=None):
     lib.dmrg_fiedler_order.restype = I
     lib.dmrg_block_dims_u1.argtypes = [P, ip, ip]
     lib.dmrg_block_dims_u1.restype = I
+    lib.dmrg_bond_apply.argtypes = [P, I, dp, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dmrg_bond_apply.restype = I
     lib.dmrg_energy.argtypes = [P, dp]
     lib.dmrg_energy.restype = I
     lib.dmrg_rdm12.argtypes = [P, dp, dp]
@@ -311,6 +313,20 @@ class DMRG:
         out = {k: getattr(r, k) for k, _ in BondResult._fields_}
         out["call_ms"] = ms[:min(cap, r.calls)].tolist()
         return out
+
+    def bond_apply(self, x, precision=None):
+        """H_eff x on the blocks of the last bond_solve (precision default FP64);
+        x None: returns the dimension."""
+        n = ctypes.c_int64(0)
+        p = FP64 if precision is None else precision
+        if x is None:
+            _check(self._lib, self._ctx, self._lib.dmrg_bond_apply(self._ctx, p, None, None, ctypes.byref(n)))
+            return int(n.value)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        n.value = x.size
+        _check(self._lib, self._ctx, self._lib.dmrg_bond_apply(self._ctx, p, _dp(x), _dp(y), ctypes.byref(n)))
+        return y
 
     def bond_check64(self):
         """float64 Rayleigh quotient, residual, time (ms) and FLOPs of one

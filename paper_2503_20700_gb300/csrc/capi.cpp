@@ -282,6 +282,27 @@ dmrg_status dmrg_bond_check64(dmrg_ctx* c, double* energy_rq64, double* residual
   return DMRG_OK;
 }
 
+dmrg_status dmrg_bond_apply(dmrg_ctx* c, int precision, const double* x, double* y, int64_t* len) {
+  if (!c || !c->eng || !len) return fail(c, DMRG_EINVAL, "invalid argument");
+  if (!sweep_precision_ok(precision) || precision == DMRG_SPLIT_TF32)
+    return fail(c, DMRG_EINVAL,
+                "precision must be DMRG_FP64, DMRG_SPLIT_HPSI, DMRG_SPLIT_HPSI_TC or DMRG_SPLIT_ALL_TC");
+  try {
+    dmrg::Precision ph, pr;
+    map_precision(precision, &ph, &pr);
+    const size_t n = c->eng->apply_bond(ph, nullptr, nullptr);
+    if (x && y && *len != (int64_t)n) {
+      *len = (int64_t)n;
+      return fail(c, DMRG_EINVAL, "vector length differs from the two-site dimension of the bond");
+    }
+    *len = (int64_t)n;
+    if (x && y) c->eng->apply_bond(ph, x, y);
+  } catch (const std::exception& e) {
+    return translate(c, e);
+  }
+  return DMRG_OK;
+}
+
 dmrg_status dmrg_bond_solve(dmrg_ctx* c, int bond, int direction, int precision, int max_iter, double tol,
                             int min_calls, int check64, dmrg_bond_result* out, double* call_ms, int cap) {
   if (!c || !c->eng || !out) return fail(c, DMRG_EINVAL, "invalid argument");

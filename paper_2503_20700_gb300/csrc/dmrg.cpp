@@ -2909,6 +2909,44 @@ Engine::BondSolve Engine::solve_bond(int bond, bool l2r, Precision p, int max_it
   return out;
 }
 
+size_t Engine::apply_bond(Precision p, const double* x, double* y) {
+  const int bond = solve_bond_;
+  if (!solve_psi_ || bond < 0 || bond >= (int)keep_L_.size() || !keep_L_[bond] || bond >= (int)keep_R_.size() ||
+      !keep_R_[bond])
+    throw std::runtime_error("state: no bond solve to apply H_eff at");
+  Block& Le = *keep_L_[bond];
+  Block& Re = *keep_R_[bond];
+  HPsiPlan plan;
+  plan.psi = make_psi(Le.ops->basis, Re.ops->basis, n_elec_, two_s_);
+  const size_t len = plan.psi.size;
+  if (!x || !y) return len;
+  plan.in = (double*)be_->alloc(len * sizeof(double));
+  plan.out = (double*)be_->alloc(len * sizeof(double));
+  const Precision kp = opt_.prec;
+  const bool kt = opt_.tc_autotune;
+  opt_.prec = p;
+  opt_.tc_autotune = false;
+  try {
+    plan_hpsi(Le, Re, plan);
+    be_->copy_h2d(plan.in, x, len * sizeof(double));
+    apply_hpsi(plan);
+    if (plan.prec == Precision::TC_TF32X3) be_->check_device_flag();
+    be_->copy_d2h(y, plan.out, len * sizeof(double));
+    be_->sync();
+  } catch (...) {
+    opt_.prec = kp;
+    opt_.tc_autotune = kt;
+    for (void* q : {(void*)plan.in, (void*)plan.out, plan.dev, plan.sched, plan.tc_pool, (void*)plan.diag})
+      if (q) be_->free(q);
+    throw;
+  }
+  opt_.prec = kp;
+  opt_.tc_autotune = kt;
+  for (void* q : {(void*)plan.in, (void*)plan.out, plan.dev, plan.sched, plan.tc_pool, (void*)plan.diag})
+    if (q) be_->free(q);
+  return len;
+}
+
 void Engine::check_bond64(double* energy_rq64, double* residual64, double* ms, double* flops) {
   const int bond = solve_bond_;
   if (!solve_psi_ || bond < 0 || bond >= (int)keep_L_.size() || !keep_L_[bond] || bond >= (int)keep_R_.size() ||

@@ -235,6 +235,10 @@ class Engine {
   // float64 Rayleigh quotient and residual of the vector of the last
   // solve_bond (one float64 H_eff psi, timed with CUDA events: *ms)
   void check_bond64(double* energy_rq64, double* residual64, double* ms, double* flops);
+  // y = H_eff x on the blocks of the last solve_bond, in precision p (host
+  // vectors in the two-site layout of that bond); returns the dimension (and
+  // does nothing else when x or y is null)
+  size_t apply_bond(Precision p, const double* x, double* y);
   double energy() const { return energy_; }
   int n() const { return n_; }
   void set_D(int D) { opt_.D = D; }

@@ -383,3 +383,33 @@ def test_fused_hpsi_tcgen05_super_chunk_edges(pkg, drain):
         scale = np.abs(ref).max()
         got = C1[off:off + m * n].reshape(m, n)
         assert np.abs(got - ref).max() < 3e-5 * scale
+
+
+def test_heff_at_a_bond_is_symmetric_and_linear(pkg):
+    """The device H_eff at a bond, applied to chosen vectors (dmrg_bond_apply):
+    <x|H y> = <H x|y> and H(2x - 3y) = 2Hx - 3Hy in float64 to 1e-12
+    relative (the reduced multiplet basis is orthonormal, so H_eff is
+    symmetric); the split tcgen05 product on the same vector agrees with
+    float64 within the split tolerance; wrong lengths are rejected."""
+    n, mid = 10, 4
+    h, L = W.cholesky_random(n, 40, seed=4)
+    occ, path = W.aufbau_state(h, n, 0)
+    g = pkg.DMRG(h, chol=L, n_elec=n, two_s=0, D=48, tol=1e-8, occ=occ, two_s_right=path)
+    g.sweep(1)
+    g.sweep_part(0, n - 3)
+    g.sweep_part(1, mid + 1)
+    r = g.bond_solve(mid, 1, pkg.FP64, max_iter=30, tol=1e-8, min_calls=0, check64=False)
+    dim = g.bond_apply(None)
+    assert dim == r["dim"] and dim > 100
+    rng = np.random.default_rng(1)
+    x, y = rng.standard_normal(dim), rng.standard_normal(dim)
+    Hx, Hy = g.bond_apply(x), g.bond_apply(y)
+    assert abs(x @ Hy - Hx @ y) < 1e-12 * np.linalg.norm(Hx) * np.linalg.norm(y)
+    H2 = g.bond_apply(2.0 * x - 3.0 * y)
+    assert np.abs(H2 - (2.0 * Hx - 3.0 * Hy)).max() < 1e-12 * np.abs(H2).max()
+    Tx = g.bond_apply(x, pkg.SPLIT_HPSI_TC)
+    assert np.abs(Tx - Hx).max() < 3e-5 * np.abs(Hx).max()
+    with pytest.raises(pkg.DmrgError) as ei:
+        g.bond_apply(np.zeros(dim + 1))
+    assert ei.value.status == pkg.DMRG_EINVAL
+    g.close()
