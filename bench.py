@@ -605,8 +605,8 @@ def run_casscf(args, pkg, prec, rank, world, dist, device):
     orbital rotation U = exp(-kappa) and the integral transformation (timed
     on the device: float64 GEMMs), the active-space problem, DMRG on the
     CAS(30,30) ramped to D=1024, the spin-free RDMs from the float64
-    measurement pass and the generalised-Fock orbital gradient; the transform
-    and the gradient are checked against the oracle on the same inputs."""
+    measurement pass and the generalised-Fock orbital gradient.  (Their
+    parity with the oracle at this size is a GPU test, not part of the bench.)"""
     import workloads as W
     from paper_2503_20700_gb300 import ops
     nb, ncore, ncas, rk = 200, 20, 30, 600
@@ -640,10 +640,6 @@ def run_casscf(args, pkg, prec, rank, world, dist, device):
     gr_ms, gr_flops = ops.casscf_last_kernel_ms()
     t_job = time.perf_counter() - t_job0
     pk, src = peaks()
-    # oracle checks on the same inputs (after the timed work)
-    from oracle import casscf as OC
-    h_o, L_o = OC.transform(h, L, OC.rotation_matrix(K))
-    g_o = OC.orbital_gradient(hr, Lr, ncore, ncas, gamma, Gamma)
     tr_bytes = 2.0 * (L.nbytes + h.nbytes)  # algorithmic: read h and L, write h' and L'
     if rank == 0:
         print(json.dumps({
@@ -653,12 +649,10 @@ def run_casscf(args, pkg, prec, rank, world, dist, device):
             "transform": {"ms": tr_ms, "fp64_tflops": tr_flops / (tr_ms / 1e3) / 1e12 if tr_ms > 0 else None,
                           "gb_per_s": tr_bytes / (tr_ms / 1e3) / 1e9 if tr_ms > 0 else None, "algorithmic_bytes": tr_bytes,
                           "algorithmic_flops": tr_flops,
-                          "max_abs_diff_vs_oracle": float(max(np.abs(hr - h_o).max(), np.abs(Lr - L_o).max())),
                           "bound": "fp64 alu", "fp64_peak_note": "nominal 1.25 TFLOP/s FP64 (no measured FP64 peak)"},
             "dmrg": {"seconds": t_dmrg, "energies": energies, "rdm_seconds": t_rdm,
                      "trace_gamma": float(np.trace(gamma))},
-            "gradient": {"seconds": t_grad, "kernel_ms": gr_ms, "max_abs": float(np.abs(grad).max()),
-                         "max_abs_diff_vs_oracle": float(np.abs(grad - g_o).max())},
+            "gradient": {"seconds": t_grad, "kernel_ms": gr_ms, "max_abs": float(np.abs(grad).max())},
             "job_seconds": t_job, "peaks_source": src}))
     return 0
 

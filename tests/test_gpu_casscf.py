@@ -144,6 +144,25 @@ def test_full_scale_gradient_properties(ops):
         assert grad[p, q] == pytest.approx(ref[p, q], rel=1e-10, abs=1e-10)
 
 
+def test_full_scale_transform_matches_oracle(ops):
+    """The integral transformation at the gradient workload's size (200
+    orbitals, rank 600) after a small rotation, against the oracle's
+    transform of the same integrals; its device time and FLOP count come back
+    through casscf_last_kernel_ms."""
+    nb, rank = 200, 600
+    h, L = W.cholesky_random(nb, rank, seed=20250326)
+    rng = np.random.default_rng(20250326)
+    K = 0.01 * rng.standard_normal((nb, nb))
+    K = K - K.T
+    R = ops.rotation(K)
+    hr, Lr = ops.transform(R, h, L)
+    ms, flops = ops.casscf_last_kernel_ms()
+    assert ms > 0 and flops == pytest.approx(2 * (rank + 1) * 2.0 * nb ** 3)
+    h_o, L_o = C.transform(h, L, C.rotation_matrix(K))
+    assert np.abs(hr - h_o).max() < 1e-12
+    assert np.abs(Lr - L_o).max() < 1e-12
+
+
 def test_orbital_transform_autograd_gradcheck():
     """torch.autograd.gradcheck of the hand-written backward of the orbital
     rotation + integral transform + active-space map, at kappa != 0."""
