@@ -332,6 +332,13 @@ def profiled_traffic(args, mode_default):
     return None, None
 
 
+def full_sweep_estimate(seconds, bonds, n):
+    """Wall time of a full sweep (L->R over bonds 0..n-3, R->L over n-2..1:
+    2(n-2) bond steps) extrapolated from `seconds` measured over `bonds` bond
+    steps of the same bond dimension and Davidson cap."""
+    return seconds * 2.0 * (n - 2) / bonds if bonds > 0 else None
+
+
 def parse_ramp(text):
     out = []
     for part in text.split(","):
@@ -494,6 +501,12 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
                                     "delta_e_bound": (res["residual64"] ** 2 / res["gap"]) if res["gap"] > 0 else None},
                 "fp64": fp64, "ramp_energies": ramp_energies, "ramp_seconds": t_ramp,
                 "approach_seconds": t_app, "approach_device_ms": app_ms,
+                "sweep_seconds_estimate": {
+                    "value": full_sweep_estimate(t_app, app_bonds, n),
+                    "what": (f"a full sweep at D={args.D} with the approach's Davidson cap "
+                             f"({args.approach_iters} iterations per bond), extrapolated from the "
+                             f"{app_bonds} bond steps of the approach measured at that D "
+                             f"(of {2 * (n - 2)} in a sweep); not a converged sweep")},
                 "approach_phases": {"bonds": app_bonds, "products": app_products,
                                     "seconds": {k: app_phases[k] for k in
                                                 ("enlarge", "plan", "davidson", "decimate", "renormalize",

@@ -16,6 +16,13 @@ def test_ramp_ends_at_target_and_doubles():
     assert bench.ramp(16, 3) == [16, 16, 16]
 
 
+def test_full_sweep_estimate_scales_measured_bond_steps():
+    # 57 of the 76 bond steps of a 40-site sweep measured in 95 s
+    assert bench.full_sweep_estimate(95.0, 57, 40) == pytest.approx(95.0 * 76 / 57)
+    assert bench.full_sweep_estimate(10.0, 2 * (10 - 2), 10) == pytest.approx(10.0)
+    assert bench.full_sweep_estimate(1.0, 0, 10) is None
+
+
 def test_hpsi_problem_offsets_and_flops():
     A, P, B, clen, blocks, items, flops = bench.hpsi_problem(3, 4, 10, 30, 5)
     fl = 0.0
