@@ -41,7 +41,26 @@ def random8():
             "D": 12, "sweeps": 3, "e_fci": e_fci, "e_dmrg_sweeps": es}
 
 
-FIXTURES = {"naphthalene_ppp_d64": naphthalene, "random8_d12": random8}
+def ordering_hubbard8():
+    """The ordering step (Sec. II "Numerical procedure") on a Hubbard chain of
+    8 sites (t = -1, U = 4, half filling) whose sites were shuffled: two D=16
+    sweeps in the shuffled order, the orbital entropies and mutual
+    information of that state, and its Fiedler order."""
+    import numpy as np
+    from oracle import orbital as OB
+    n = 8
+    h, eri, _ = W.hubbard_chain(n, t=-1.0, u=4.0)
+    perm = np.random.default_rng(3).permutation(n)
+    hs, es = OB.permute_integrals(h, eri, perm)
+    d = OracleDMRG(hs, es, n, 0, D=16, tol=1e-10)
+    energies = d.sweep(2)
+    s1, mi = OB.orbital_entanglement(d.states, d.psi_full, n, 0)
+    return {"workload": "hubbard_chain(8, t=-1, u=4), sites shuffled by default_rng(3).permutation(8)",
+            "perm": [int(x) for x in perm], "D": 16, "sweeps": 2, "e_dmrg_sweeps": energies,
+            "s1": s1.tolist(), "mutual": mi.tolist(), "order": [int(x) for x in OB.fiedler_order(mi)]}
+
+
+FIXTURES = {"naphthalene_ppp_d64": naphthalene, "random8_d12": random8, "ordering_hubbard8": ordering_hubbard8}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(FIXTURES)

@@ -32,3 +32,16 @@ def test_stored_dmrg_energies_are_variational():
         es = d["e_dmrg_sweeps"]
         assert all(e >= d["e_fci"] - 1e-9 for e in es), name
         assert all(b <= a + 1e-9 for a, b in zip(es, es[1:])), name  # sweeps do not raise the energy
+
+
+def test_ordering_fixture_reproduces_and_recovers_the_chain():
+    """The ordering-step fixture regenerates from the oracle, and its stored
+    Fiedler order places the shuffled chain's neighbours next to each other
+    (at most one break)."""
+    stored = json.load(open(os.path.join(GOLD, "ordering_hubbard8.json")))
+    out = _make_golden().ordering_hubbard8()
+    np.testing.assert_allclose(out["s1"], stored["s1"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(out["mutual"], stored["mutual"], rtol=0, atol=1e-9)
+    assert out["order"] == stored["order"]
+    chain = [stored["perm"][k] for k in stored["order"]]
+    assert sum(abs(a - b) == 1 for a, b in zip(chain[:-1], chain[1:])) >= len(chain) - 2
