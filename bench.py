@@ -396,6 +396,7 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
     app_products += g.stats()["hpsi_calls"]
     t_app = time.perf_counter() - t_app0
     left, right = g.block_dims()
+    left_u1, right_u1 = g.block_dims_u1()  # the same blocks in U(1) states (D~)
     # schedule autotuning at the middle bond (split tcgen05 path): each
     # candidate schedule computes one product of a Davidson solve of the bond
     # and the fastest is kept for its sector histogram
@@ -512,6 +513,7 @@ def run_bond(args, pkg, prec, rank, world, dist, device):
                                                 ("enlarge", "plan", "davidson", "decimate", "renormalize",
                                                  "guess")}},
                 "block_dims_left": left.tolist(), "block_dims_right": right.tolist(),
+                "block_dims_u1_left": left_u1.tolist(), "block_dims_u1_right": right_u1.tolist(),
                 "wall_seconds": wall, "hpsi_tflops_kernel": achieved, "device_mem_peak_gb": mem_peak / 1e9,
                 "kernel_ms": kernel_ms, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "launches_before_timed": l0, "contraction_launches_before_timed": products + W,
