@@ -115,3 +115,21 @@ def test_ordering_step_recovers_a_shuffled_chain(pkg):
     e_ordered = g2.sweep(2)[0]
     g2.close()
     assert e_ordered < e_shuffled - 0.3
+
+
+@pytest.mark.parametrize("n_elec,two_s", [(3, 1), (4, 0), (2, 2)])
+def test_orbital_rdms_on_three_orbitals(pkg, n_elec, two_s):
+    """The smallest chain the pass takes: its only bond is also the last, so
+    the single-orbital values of all three sites and the pairs (0,1), (0,2),
+    (1,2) are all measured there (x in L(1), s on site 1, y on site 2)."""
+    n = 3
+    h, L = W.cholesky_random(n, 6, seed=12)
+    eri = W.eri_from_cholesky(L)
+    e, x, H = fci(h, eri, n_elec, two_s)
+    g = pkg.DMRG(h, eri=eri, n_elec=n_elec, two_s=two_s, D=64, tol=1e-12)
+    g.sweep(2)
+    r1, r2 = g.orbital_rdms()
+    g.close()
+    o1, o2 = oracle_rdms(H.ops.states, x, n, two_s)
+    assert np.abs(r1 - o1).max() < 1e-8
+    assert np.abs(r2 - o2).max() < 1e-8
